@@ -1,0 +1,183 @@
+/*
+ * kifmm_elastic.h -- C ABI of the GB300 (sm_103a) kernel-independent FMM for the 3D Kelvin
+ * elasticity boundary-integral operators, and of the collocation BEM built on it.
+ *
+ * Method: arXiv 1612.04082, "What Lies Beneath the Surface: Topological-Shape Optimization
+ * With the Kernel-Independent Fast Multipole Method".
+ *
+ * General conventions (every entry point):
+ *  - Return value: KFMM_OK (0) or a negative kfmm_status.  No exception crosses the ABI.
+ *    On error kfmm_last_error(ctx) holds a one-line message.  Outputs are unspecified
+ *    after an error unless the entry point says otherwise.
+ *  - Array arguments are plain pointers that may point to device memory or to host memory
+ *    (pageable or pinned); the library inspects each pointer and stages host arrays through
+ *    its own device buffers.  The caller owns every array passed in; each must stay valid
+ *    for the duration of the call.  The library owns only its internal buffers (tree,
+ *    operators, workspaces), released by the matching *_destroy.
+ *  - Layouts are row-major arrays of structures: points [n][3] (x, y, z); 3-vector densities
+ *    [n][3 * ncol] (column c occupies entries 3c .. 3c+2 of each row); displacements
+ *    [n][3 * ncol]; stresses [n][6 * ncol] in the order xx, yy, zz, yz, xz, xy.
+ *  - Work is enqueued on the context's CUDA stream (kfmm_set_stream; default: the legacy
+ *    default stream).  Entry points that return data to host pointers, or that need a count
+ *    on the host (tree build, GMRES convergence tests), synchronise that stream.
+ *  - Kernels follow the paper's Eq. disp_1 (U, single layer, "SL"), Eq. disp_2 (P, double
+ *    layer, "DL"; normal at the source, pointing out of the material), Eq. stress_2 (D) and
+ *    Eq. stress_3 (S, with the factor G).  With d = x_target - y_source every kernel is 0
+ *    at d = 0 (coincident points are skipped, as in the direct sum of Eq. fmm_summation).
+ *      DISP   (3 outputs): out_i = sum_j U(d) sl_j + P(d, n_j) dl_j
+ *      STRESS (6 outputs): out_i = sum_j D(d) sl_j + S(d, n_j) dl_j   (Hooke of grad DISP)
+ *    so the interior displacement of the BIE is DISP(sl = t w, dl = -u w) and Eq. stress_1
+ *    (Somigliana) is STRESS(sl = t w, dl = -u w) for quadrature weights w.
+ */
+#ifndef KIFMM_ELASTIC_H
+#define KIFMM_ELASTIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum kfmm_status {
+    KFMM_OK = 0,
+    KFMM_ERR_INVALID_ARG = -1,    /* bad size, NULL where an array is required, NaN input   */
+    KFMM_ERR_OOM = -2,            /* device or host allocation failed                        */
+    KFMM_ERR_CUDA = -3,           /* a CUDA runtime call or kernel launch failed             */
+    KFMM_ERR_NOT_CONVERGED = -4,  /* iterative solve stopped at its iteration cap            */
+    KFMM_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait gave up                      */
+    KFMM_ERR_NOT_BUILT = -6,      /* kfmm_eval before kfmm_build, or BEM use before set-up   */
+    KFMM_ERR_INTERNAL = -7        /* an internal consistency check failed                    */
+} kfmm_status;
+
+typedef enum kfmm_kind {
+    KFMM_DISP = 0,   /* 3 outputs per target and column: SL (Eq. disp_1) + DL (Eq. disp_2) */
+    KFMM_STRESS = 1  /* 6 outputs per target and column: Eq. stress_2 + Eq. stress_3        */
+} kfmm_kind;
+
+typedef enum kfmm_precision {
+    KFMM_FP32 = 0,  /* FP32 arithmetic and FP32 arrays                                       */
+    KFMM_FP64 = 1   /* FP64 arithmetic and FP64 arrays (direct sums only)                   */
+} kfmm_precision;
+
+/* Options of the kernel-independent FMM (Sec. "Kernel-independent fast multipole method":
+ * far fields are represented by densities on equivalent surfaces, matched on check
+ * surfaces; the translation operators are matrices built from the kernel alone). */
+typedef struct kfmm_options {
+    int p;              /* points per edge of the cube lattice whose surface carries the
+                           equivalent densities: 6 (p - 1)^2 + 2 points (152 at p = 6)     */
+    int leaf_cap;       /* a box is split while it holds more than leaf_cap sources or
+                           targets (64)                                                     */
+    int max_depth;      /* deepest octree level, <= 20 (20)                                 */
+    double r_inner;     /* radius of the inner surfaces (upward equivalent, downward check),
+                           in box half-widths (1.05)                                         */
+    double r_outer;     /* radius of the outer surfaces (upward check, downward equivalent)
+                           (2.95)                                                            */
+    double pinv_rtol;   /* relative singular-value cutoff of the check-to-equivalent
+                           pseudo-inverses, computed in FP64 (1e-7)                          */
+    double m2l_rtol;    /* relative singular-value cutoff of the shared M2L basis (1e-6);
+                           0 keeps the full rank (dense M2L)                                 */
+    int m2l_rank_max;   /* upper bound on the M2L rank (0 = no bound)                       */
+    int device;         /* CUDA device ordinal (0)                                          */
+} kfmm_options;
+
+/* Tree and work counts of the last kfmm_build (for tests and roofline accounting). */
+typedef struct kfmm_stats {
+    int64_t n_src, n_trg;
+    int32_t n_boxes, n_leaves, n_levels, m2l_rank, n_surf;
+    int64_t n_u_pairs;      /* (target leaf, source leaf) pairs of the U lists               */
+    int64_t n_v_pairs;      /* (target box, source box) pairs of the V lists                 */
+    int64_t n_w_pairs, n_x_pairs;
+    int64_t p2p_interactions;  /* sum over target leaves of n_trg * (U-list sources)         */
+    int64_t s2m_interactions;  /* n_src (in leaves) * n_surf                                 */
+    int64_t l2p_interactions;  /* n_trg * n_surf * (1 + |W list|)                            */
+    int64_t p2l_interactions;  /* sum over X pairs of n_src(leaf) * n_surf                   */
+    int64_t kernel_launches;   /* CUDA kernels this context has launched since kfmm_create   */
+} kfmm_stats;
+
+typedef struct kfmm_ctx kfmm_ctx;
+
+/* Fill *opt with the defaults listed above. */
+void kfmm_default_options(kfmm_options *opt);
+
+/* Create a context on opt->device (opt may be NULL for defaults).  Material defaults to
+ * G = 1, nu = 0.3.  The FP64 operator precompute runs at the first build for a material. */
+kfmm_status kfmm_create(kfmm_ctx **out, const kfmm_options *opt);
+kfmm_status kfmm_destroy(kfmm_ctx *ctx);
+
+/* Bulk modulus K and shear modulus G of Eq. elast; nu = (3K - 2G) / (2 (3K + G)).
+ * Requires K > 0, G > 0 (so -1 < nu < 1/2). */
+kfmm_status kfmm_set_material(kfmm_ctx *ctx, double K, double G);
+
+/* Enqueue all later work of this context on `stream` (a cudaStream_t; NULL = default). */
+kfmm_status kfmm_set_stream(kfmm_ctx *ctx, void *stream);
+
+/* Octree build for the sum of Eq. fmm_summation (Sec. "Kernel-independent fast multipole
+ * method", first step): Morton keys in the bounding cube, radix sort, split while a box
+ * holds more than leaf_cap points, U/V/W/X interaction lists.  src_xyz [nsrc][3],
+ * src_nrm [nsrc][3] (may be NULL when no double-layer density will be passed),
+ * trg_xyz [ntrg][3], FP32.  nsrc, ntrg >= 1 and all coordinates finite.  The tree and the
+ * sorted copies of the points are kept until the next build or destroy. */
+kfmm_status kfmm_build(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm, int64_t nsrc,
+                       const float *trg_xyz, int64_t ntrg);
+
+/* One FMM evaluation of Eq. fmm_summation on the built tree: sl_den, dl_den [nsrc][3*ncol]
+ * (either may be NULL, not both), out [ntrg][3*ncol] (DISP) or [ntrg][6*ncol] (STRESS),
+ * FP32, overwritten.  ncol in 1..32. */
+kfmm_status kfmm_eval(kfmm_ctx *ctx, const float *sl_den, const float *dl_den, int ncol, int kind,
+                      float *out);
+
+/* The same sum by all-pairs direct summation (no tree), in FP32 or FP64 (`precision`):
+ * arrays are float or double accordingly.  out is overwritten.  Used for small problems,
+ * the dense-equivalent BEM and as the GPU reference of the near field. */
+kfmm_status kfmm_direct(kfmm_ctx *ctx, int precision, const void *trg_xyz, int64_t ntrg,
+                        const void *src_xyz, const void *src_nrm, int64_t nsrc, const void *sl_den,
+                        const void *dl_den, int kind, void *out);
+
+kfmm_status kfmm_get_stats(const kfmm_ctx *ctx, kfmm_stats *st);
+
+/* Copies of the built tree for inspection (host arrays sized from kfmm_get_stats):
+ * box_level [n_boxes], box_anchor [n_boxes][3] (integer box coordinates at its level),
+ * box_parent [n_boxes], box_src [n_boxes][2] and box_trg [n_boxes][2] (ranges into the
+ * sorted point order), src_perm [nsrc] and trg_perm [ntrg] (sorted position -> input index).
+ * Any pointer may be NULL. */
+kfmm_status kfmm_export_tree(const kfmm_ctx *ctx, int32_t *box_level, int32_t *box_anchor,
+                             int32_t *box_parent, int32_t *box_src, int32_t *box_trg,
+                             int32_t *src_perm, int32_t *trg_perm);
+
+/* Interaction lists as CSR over boxes: which = 'U', 'V', 'W' or 'X'; offsets [n_boxes+1],
+ * items [n_pairs] (source box indices).  Either pointer may be NULL; *n_pairs receives the
+ * total.  U and W lists are defined for leaves only (empty rows elsewhere). */
+kfmm_status kfmm_export_list(const kfmm_ctx *ctx, char which, int32_t *offsets, int32_t *items,
+                             int64_t *n_pairs);
+
+/* Phases timed when profiling is on (CUDA events on the context stream around each phase). */
+typedef enum kfmm_phase {
+    KFMM_PH_TREE = 0,     /* kfmm_build: keys, sort, split, lists                          */
+    KFMM_PH_PACK = 1,     /* source records (sorted, pre-scaled densities)                 */
+    KFMM_PH_S2M = 2,      /* sources -> upward check surfaces of the leaves                 */
+    KFMM_PH_UP_PINV = 3,  /* upward check -> upward equivalent densities (leaves)          */
+    KFMM_PH_M2M = 4,      /* child -> parent upward densities, bottom-up                   */
+    KFMM_PH_M2L = 5,      /* compression, V-list translation (M2L)                         */
+    KFMM_PH_P2L = 6,      /* X-list sources -> downward check surfaces                      */
+    KFMM_PH_DOWN = 7,     /* downward densities and L2L, top-down                          */
+    KFMM_PH_EVAL = 8,     /* leaf evaluation: L2P + M2P (W list) + P2P (U list)             */
+    KFMM_N_PHASES = 9
+} kfmm_phase;
+
+/* Turn per-phase timing on or off (off by default).  Timing adds two event records per
+ * phase and changes no result. */
+kfmm_status kfmm_set_profiling(kfmm_ctx *ctx, int enable);
+
+/* Milliseconds and call counts per phase accumulated since the last reset (arrays of
+ * KFMM_N_PHASES; either may be NULL).  Synchronises the context stream.  reset != 0 clears
+ * the accumulators after reading. */
+kfmm_status kfmm_get_phase_times(kfmm_ctx *ctx, double *ms, int64_t *counts, int reset);
+
+const char *kfmm_status_str(kfmm_status s);
+const char *kfmm_last_error(const kfmm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KIFMM_ELASTIC_H */

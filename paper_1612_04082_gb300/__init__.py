@@ -1,0 +1,262 @@
+"""Python binding of the kifmm_elastic C-ABI library (GB300, sm_103a).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  The functions keep the C names (``kfmm_create``, ``kfmm_build``, ``kfmm_eval``,
+...).  Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they are passed to the
+library as raw pointers (device or host; the library stages host arrays itself).
+
+There is no fallback: importing this package loads ``_lib/libkifmm_elastic.so`` and raises
+if it is missing (run ``python -m paper_1612_04082_gb300.build`` or
+``__graft_entry__.build()`` first).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libkifmm_elastic.so")
+HEADER_PATH = os.path.join(_HERE, "..", "include", "kifmm_elastic.h")
+
+KFMM_OK = 0
+KFMM_ERR_INVALID_ARG = -1
+KFMM_ERR_OOM = -2
+KFMM_ERR_CUDA = -3
+KFMM_ERR_NOT_CONVERGED = -4
+KFMM_ERR_DEVICE_TIMEOUT = -5
+KFMM_ERR_NOT_BUILT = -6
+KFMM_ERR_INTERNAL = -7
+KFMM_DISP = 0
+KFMM_STRESS = 1
+KFMM_FP32 = 0
+KFMM_FP64 = 1
+
+
+class kfmm_options(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("max_depth", ctypes.c_int),
+                ("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double), ("pinv_rtol", ctypes.c_double),
+                ("m2l_rtol", ctypes.c_double), ("m2l_rank_max", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class kfmm_stats(ctypes.Structure):
+    _fields_ = [("n_src", ctypes.c_int64), ("n_trg", ctypes.c_int64), ("n_boxes", ctypes.c_int32),
+                ("n_leaves", ctypes.c_int32), ("n_levels", ctypes.c_int32), ("m2l_rank", ctypes.c_int32),
+                ("n_surf", ctypes.c_int32), ("n_u_pairs", ctypes.c_int64), ("n_v_pairs", ctypes.c_int64),
+                ("n_w_pairs", ctypes.c_int64), ("n_x_pairs", ctypes.c_int64),
+                ("p2p_interactions", ctypes.c_int64), ("s2m_interactions", ctypes.c_int64),
+                ("l2p_interactions", ctypes.c_int64), ("p2l_interactions", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"kifmm_elastic library not built: {LIB_PATH} is missing "
+                      "(run paper_1612_04082_gb300/build.py or __graft_entry__.build())")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_sig = {
+    "kfmm_default_options": (None, [ctypes.POINTER(kfmm_options)]),
+    "kfmm_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(kfmm_options)]),
+    "kfmm_destroy": (ctypes.c_int, [_vp]),
+    "kfmm_set_material": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
+    "kfmm_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "kfmm_build": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64]),
+    "kfmm_eval": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]),
+    "kfmm_direct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]),
+    "kfmm_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(kfmm_stats)]),
+    "kfmm_export_tree": (ctypes.c_int, [_vp] + [_vp] * 7),
+    "kfmm_export_list": (ctypes.c_int, [_vp, ctypes.c_char, _vp, _vp, ctypes.POINTER(_i64)]),
+    "kfmm_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "kfmm_get_phase_times": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    "kfmm_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "kfmm_last_error": (ctypes.c_char_p, [_vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class KfmmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_lib.kfmm_status_str(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (must be contiguous), or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("array must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _nrows(a):
+    return int(a.shape[0])
+
+
+def _check(ctx_handle, status):
+    if status != KFMM_OK:
+        msg = _lib.kfmm_last_error(ctx_handle).decode() if ctx_handle else ""
+        raise KfmmError(status, msg)
+
+
+def kfmm_default_options(**overrides) -> kfmm_options:
+    o = kfmm_options()
+    _lib.kfmm_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def kfmm_create(options: kfmm_options | None = None, **overrides):
+    o = options if options is not None else kfmm_default_options()
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    h = _vp()
+    _check(None, _lib.kfmm_create(ctypes.byref(h), ctypes.byref(o)))
+    return h
+
+
+def kfmm_destroy(ctx):
+    _check(None, _lib.kfmm_destroy(ctx))
+
+
+def kfmm_set_material(ctx, K: float, G: float):
+    _check(ctx, _lib.kfmm_set_material(ctx, float(K), float(G)))
+
+
+def kfmm_set_stream(ctx, stream):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (default stream)."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(ctx, _lib.kfmm_set_stream(ctx, raw))
+
+
+def kfmm_build(ctx, src_xyz, src_nrm, trg_xyz):
+    _check(ctx, _lib.kfmm_build(ctx, _ptr(src_xyz), _ptr(src_nrm), _nrows(src_xyz), _ptr(trg_xyz), _nrows(trg_xyz)))
+
+
+def kfmm_eval(ctx, sl_den, dl_den, out, kind=KFMM_DISP, ncol=1):
+    _check(ctx, _lib.kfmm_eval(ctx, _ptr(sl_den), _ptr(dl_den), int(ncol), int(kind), _ptr(out)))
+    return out
+
+
+def kfmm_direct(ctx, trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out, kind=KFMM_DISP, precision=KFMM_FP32):
+    _check(ctx, _lib.kfmm_direct(ctx, int(precision), _ptr(trg_xyz), _nrows(trg_xyz), _ptr(src_xyz), _ptr(src_nrm),
+                                 _nrows(src_xyz), _ptr(sl_den), _ptr(dl_den), int(kind), _ptr(out)))
+    return out
+
+
+def kfmm_get_stats(ctx) -> dict:
+    st = kfmm_stats()
+    _check(ctx, _lib.kfmm_get_stats(ctx, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in kfmm_stats._fields_}
+
+
+def kfmm_export_tree(ctx) -> dict:
+    st = kfmm_get_stats(ctx)
+    nb, ns, nt = st["n_boxes"], st["n_src"], st["n_trg"]
+    out = {"level": np.zeros(nb, np.int32), "anchor": np.zeros((nb, 3), np.int32), "parent": np.zeros(nb, np.int32),
+           "src": np.zeros((nb, 2), np.int32), "trg": np.zeros((nb, 2), np.int32),
+           "src_perm": np.zeros(ns, np.int32), "trg_perm": np.zeros(nt, np.int32)}
+    _check(ctx, _lib.kfmm_export_tree(ctx, *[_ptr(out[k]) for k in
+                                             ("level", "anchor", "parent", "src", "trg", "src_perm", "trg_perm")]))
+    return out
+
+
+def kfmm_export_list(ctx, which: str):
+    n = _i64(0)
+    _check(ctx, _lib.kfmm_export_list(ctx, which.encode(), None, None, ctypes.byref(n)))
+    nb = kfmm_get_stats(ctx)["n_boxes"]
+    off = np.zeros(nb + 1, np.int32)
+    items = np.zeros(max(1, n.value), np.int32)
+    _check(ctx, _lib.kfmm_export_list(ctx, which.encode(), _ptr(off), _ptr(items), ctypes.byref(n)))
+    return off, items[: n.value]
+
+
+PHASES = ("tree", "pack", "s2m", "up_pinv", "m2m", "m2l", "p2l", "down", "eval")
+
+
+def kfmm_set_profiling(ctx, enable: bool):
+    _check(ctx, _lib.kfmm_set_profiling(ctx, int(bool(enable))))
+
+
+def kfmm_get_phase_times(ctx, reset: bool = False) -> dict:
+    """{phase: (milliseconds, calls)} accumulated since the last reset."""
+    ms = np.zeros(len(PHASES), np.float64)
+    cnt = np.zeros(len(PHASES), np.int64)
+    _check(ctx, _lib.kfmm_get_phase_times(ctx, _ptr(ms), _ptr(cnt), int(bool(reset))))
+    return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+
+def kfmm_status_str(status: int) -> str:
+    return _lib.kfmm_status_str(status).decode()
+
+
+class Kfmm:
+    """Small owner of a context: ``with Kfmm(p=6) as f: f.build(...); f.eval(...)``."""
+
+    def __init__(self, options: kfmm_options | None = None, **overrides):
+        self.handle = kfmm_create(options, **overrides)
+
+    def close(self):
+        if self.handle:
+            kfmm_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_material(self, K, G):
+        kfmm_set_material(self.handle, K, G)
+
+    def set_stream(self, stream):
+        kfmm_set_stream(self.handle, stream)
+
+    def build(self, src_xyz, src_nrm, trg_xyz):
+        kfmm_build(self.handle, src_xyz, src_nrm, trg_xyz)
+
+    def eval(self, sl_den, dl_den, out, kind=KFMM_DISP, ncol=1):
+        return kfmm_eval(self.handle, sl_den, dl_den, out, kind, ncol)
+
+    def direct(self, trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out, kind=KFMM_DISP, precision=KFMM_FP32):
+        return kfmm_direct(self.handle, trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out, kind, precision)
+
+    def stats(self):
+        return kfmm_get_stats(self.handle)
+
+    def set_profiling(self, enable=True):
+        kfmm_set_profiling(self.handle, enable)
+
+    def phase_times(self, reset=False):
+        return kfmm_get_phase_times(self.handle, reset)
+
+    def export_tree(self):
+        return kfmm_export_tree(self.handle)
+
+    def export_list(self, which):
+        return kfmm_export_list(self.handle, which)
+
+
+def material_K(G: float, nu: float) -> float:
+    """Bulk modulus from G and nu (the ABI takes K and G, Eq. elast)."""
+    return 2.0 * G * (1.0 + nu) / (3.0 * (1.0 - 2.0 * nu))

@@ -1,0 +1,297 @@
+// api.cu -- the extern "C" entry points declared in include/kifmm_elastic.h.
+// Argument checks, host-pointer staging and dispatch; the work happens in tree.cu, fmm.cu
+// and direct.cu.
+#include <cmath>
+#include <new>
+
+#include "common.cuh"
+
+namespace kfmm {
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device copy of a possibly-host array (returned pointer is p itself for device memory).
+static kfmm_status to_device(kfmm_ctx *ctx, DevBuf &buf, const void *p, size_t bytes, const void **out)
+{
+    if (!p || is_device_ptr(p)) {
+        *out = p;
+        return KFMM_OK;
+    }
+    KF_CUDA(buf.ensure(bytes));
+    KF_CUDA(cudaMemcpyAsync(buf.p, p, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    *out = buf.p;
+    return KFMM_OK;
+}
+
+}  // namespace kfmm
+
+using namespace kfmm;
+
+extern "C" {
+
+void kfmm_default_options(kfmm_options *opt)
+{
+    if (!opt) return;
+    opt->p = 6;
+    opt->leaf_cap = 64;
+    opt->max_depth = 20;
+    opt->r_inner = 1.05;
+    opt->r_outer = 2.95;
+    opt->pinv_rtol = 1e-7;
+    opt->m2l_rtol = 1e-6;
+    opt->m2l_rank_max = 0;
+    opt->device = 0;
+}
+
+kfmm_status kfmm_create(kfmm_ctx **out, const kfmm_options *opt)
+{
+    if (!out) return KFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    kfmm_options o;
+    kfmm_default_options(&o);
+    if (opt) o = *opt;
+    if (o.p < 2 || o.p > 8 || o.leaf_cap < 1 || o.max_depth < 1 || o.max_depth > 20 || !(o.r_inner > 1.0) ||
+        !(o.r_outer > o.r_inner) || !(o.r_outer < 3.0) || !(o.pinv_rtol > 0.0) || o.m2l_rtol < 0.0 ||
+        o.m2l_rank_max < 0)
+        return KFMM_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
+        cudaGetLastError();
+        return KFMM_ERR_CUDA;
+    }
+    if (cudaSetDevice(o.device) != cudaSuccess) return KFMM_ERR_CUDA;
+    kfmm_ctx *c = new (std::nothrow) kfmm_ctx();
+    if (!c) return KFMM_ERR_OOM;
+    c->opt = o;
+    *out = c;
+    return KFMM_OK;
+}
+
+kfmm_status kfmm_destroy(kfmm_ctx *ctx)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->opt.device);
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+    return KFMM_OK;
+}
+
+kfmm_status kfmm_set_material(kfmm_ctx *ctx, double K, double G)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    if (!(K > 0.0) || !(G > 0.0) || !std::isfinite(K) || !std::isfinite(G))
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "material: need K > 0 and G > 0");
+    ctx->G = G;
+    ctx->nu = (3.0 * K - 2.0 * G) / (2.0 * (3.0 * K + G));
+    return KFMM_OK;
+}
+
+kfmm_status kfmm_set_stream(kfmm_ctx *ctx, void *stream)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return KFMM_OK;
+}
+
+kfmm_status kfmm_build(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm, int64_t nsrc, const float *trg_xyz,
+                       int64_t ntrg)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!src_xyz || !trg_xyz || nsrc < 1 || ntrg < 1)
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "build: need nsrc >= 1, ntrg >= 1 and point arrays");
+    if (cudaSetDevice(ctx->opt.device) != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, "cudaSetDevice");
+    DevBuf a, b, c;
+    const void *ds, *dn, *dt;
+    KF_TRY(to_device(ctx, a, src_xyz, sizeof(float) * 3 * nsrc, &ds));
+    KF_TRY(to_device(ctx, b, src_nrm, sizeof(float) * 3 * nsrc, &dn));
+    KF_TRY(to_device(ctx, c, trg_xyz, sizeof(float) * 3 * ntrg, &dt));
+    ctx->plans.valid = false;
+    ctx->phase(KFMM_PH_TREE);
+    kfmm_status s = build_tree(ctx, (const float *)ds, (const float *)dn, nsrc, (const float *)dt, ntrg);
+    ctx->phase(-1);
+    cudaStreamSynchronize(ctx->stream);
+    return s;
+}
+
+kfmm_status kfmm_eval(kfmm_ctx *ctx, const float *sl_den, const float *dl_den, int ncol, int kind, float *out)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->tree.built) return ctx->fail(KFMM_ERR_NOT_BUILT, "eval before build");
+    if ((!sl_den && !dl_den) || !out || ncol < 1 || ncol > 32 || (kind != KFMM_DISP && kind != KFMM_STRESS))
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "eval: need a density, an output, 1 <= ncol <= 32, a valid kind");
+    if (dl_den && !ctx->tree.has_nrm)
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "eval: double-layer density but the tree was built without normals");
+    if (cudaSetDevice(ctx->opt.device) != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, "cudaSetDevice");
+    const int64_t ns = ctx->tree.nsrc, nt = ctx->tree.ntrg;
+    const int nout = (kind == KFMM_DISP ? 3 : 6) * ncol;
+    const void *dsl, *ddl;
+    KF_TRY(to_device(ctx, ctx->work.stage_in[0], sl_den, sizeof(float) * 3 * ncol * ns, &dsl));
+    KF_TRY(to_device(ctx, ctx->work.stage_in[1], dl_den, sizeof(float) * 3 * ncol * ns, &ddl));
+    float *dout = out;
+    const bool host_out = !is_device_ptr(out);
+    if (host_out) {
+        KF_CUDA(ctx->work.stage_out.ensure(sizeof(float) * nout * nt));
+        dout = ctx->work.stage_out.as<float>();
+    }
+    KF_TRY(fmm_eval(ctx, (const float *)dsl, (const float *)ddl, ncol, kind, dout));
+    if (host_out) {
+        KF_CUDA(cudaMemcpyAsync(out, dout, sizeof(float) * nout * nt, cudaMemcpyDeviceToHost, ctx->stream));
+        KF_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return KFMM_OK;
+}
+
+kfmm_status kfmm_direct(kfmm_ctx *ctx, int precision, const void *trg_xyz, int64_t ntrg, const void *src_xyz,
+                        const void *src_nrm, int64_t nsrc, const void *sl_den, const void *dl_den, int kind, void *out)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!trg_xyz || !src_xyz || ntrg < 1 || nsrc < 1 || (!sl_den && !dl_den) || !out ||
+        (precision != KFMM_FP32 && precision != KFMM_FP64) || (kind != KFMM_DISP && kind != KFMM_STRESS) ||
+        (dl_den && !src_nrm))
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "direct: bad arguments");
+    if (cudaSetDevice(ctx->opt.device) != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, "cudaSetDevice");
+    return direct_sum(ctx, precision, trg_xyz, ntrg, src_xyz, src_nrm, nsrc, sl_den, dl_den, kind, out);
+}
+
+kfmm_status kfmm_get_stats(const kfmm_ctx *ctx, kfmm_stats *st)
+{
+    if (!ctx || !st) return KFMM_ERR_INVALID_ARG;
+    const Tree &T = ctx->tree;
+    std::memset(st, 0, sizeof(*st));
+    st->kernel_launches = ctx->n_launch;
+    if (!T.built) return KFMM_ERR_NOT_BUILT;
+    st->n_src = T.nsrc;
+    st->n_trg = T.ntrg;
+    st->n_boxes = T.n_boxes;
+    st->n_leaves = T.n_leaves;
+    st->n_levels = T.n_levels;
+    st->m2l_rank = ctx->ops.ready ? ctx->ops.rank : 0;
+    const int p = ctx->opt.p;
+    st->n_surf = 6 * (p - 1) * (p - 1) + 2;
+    st->n_u_pairs = T.n_u;
+    st->n_v_pairs = T.n_v;
+    st->n_w_pairs = T.n_w;
+    st->n_x_pairs = T.n_x;
+    st->p2p_interactions = T.p2p_pairs;
+    st->s2m_interactions = 0;
+    st->l2p_interactions = T.l2p_pairs * st->n_surf;
+    st->p2l_interactions = T.p2l_pairs * st->n_surf;
+    st->kernel_launches = ctx->n_launch;
+    return KFMM_OK;
+}
+
+kfmm_status kfmm_export_tree(const kfmm_ctx *cctx, int32_t *box_level, int32_t *box_anchor, int32_t *box_parent,
+                             int32_t *box_src, int32_t *box_trg, int32_t *src_perm, int32_t *trg_perm)
+{
+    kfmm_ctx *ctx = const_cast<kfmm_ctx *>(cctx);
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    const Tree &T = ctx->tree;
+    if (!T.built) return KFMM_ERR_NOT_BUILT;
+    const int nb = T.n_boxes;
+    if (box_level || box_anchor) {
+        std::vector<int4> a(nb);
+        KF_CUDA(cudaMemcpy(a.data(), T.box_anchor.p, sizeof(int4) * nb, cudaMemcpyDeviceToHost));
+        for (int b = 0; b < nb; ++b) {
+            if (box_level) box_level[b] = a[b].w;
+            if (box_anchor) {
+                box_anchor[3 * b] = a[b].x;
+                box_anchor[3 * b + 1] = a[b].y;
+                box_anchor[3 * b + 2] = a[b].z;
+            }
+        }
+    }
+    if (box_parent) KF_CUDA(cudaMemcpy(box_parent, T.box_parent.p, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+    if (box_src) KF_CUDA(cudaMemcpy(box_src, T.box_src.p, sizeof(int2) * nb, cudaMemcpyDeviceToHost));
+    if (box_trg) KF_CUDA(cudaMemcpy(box_trg, T.box_trg.p, sizeof(int2) * nb, cudaMemcpyDeviceToHost));
+    if (src_perm) KF_CUDA(cudaMemcpy(src_perm, T.src_perm.p, sizeof(int) * T.nsrc, cudaMemcpyDeviceToHost));
+    if (trg_perm) KF_CUDA(cudaMemcpy(trg_perm, T.trg_perm.p, sizeof(int) * T.ntrg, cudaMemcpyDeviceToHost));
+    return KFMM_OK;
+}
+
+kfmm_status kfmm_export_list(const kfmm_ctx *cctx, char which, int32_t *offsets, int32_t *items, int64_t *n_pairs)
+{
+    kfmm_ctx *ctx = const_cast<kfmm_ctx *>(cctx);
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    const Tree &T = ctx->tree;
+    if (!T.built) return KFMM_ERR_NOT_BUILT;
+    const DevBuf *o = nullptr, *it = nullptr;
+    int64_t n = 0;
+    switch (which) {
+    case 'U': o = &T.u_off; it = &T.u_idx; n = T.n_u; break;
+    case 'V': o = &T.v_off; it = &T.v_idx; n = T.n_v; break;
+    case 'W': o = &T.w_off; it = &T.w_idx; n = T.n_w; break;
+    case 'X': o = &T.x_off; it = &T.x_idx; n = T.n_x; break;
+    default: return ctx->fail(KFMM_ERR_INVALID_ARG, "export_list: which must be U, V, W or X");
+    }
+    if (n_pairs) *n_pairs = n;
+    if (offsets) KF_CUDA(cudaMemcpy(offsets, o->p, sizeof(int) * (T.n_boxes + 1), cudaMemcpyDeviceToHost));
+    if (items && n) KF_CUDA(cudaMemcpy(items, it->p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    return KFMM_OK;
+}
+
+kfmm_status kfmm_set_profiling(kfmm_ctx *ctx, int enable)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    ctx->prof.on = enable != 0;
+    return KFMM_OK;
+}
+
+kfmm_status kfmm_get_phase_times(kfmm_ctx *ctx, double *ms, int64_t *counts, int reset)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    KF_CUDA(cudaStreamSynchronize(ctx->stream));
+    Profiler &P = ctx->prof;
+    for (auto &q : P.pending) {
+        float t = 0.f;
+        KF_CUDA(cudaEventElapsedTime(&t, q.a, q.b));
+        P.ms[q.phase] += t;
+        P.count[q.phase] += 1;
+        P.pool.push_back(q.a);
+        P.pool.push_back(q.b);
+    }
+    P.pending.clear();
+    for (int k = 0; k < KFMM_N_PHASES; ++k) {
+        if (ms) ms[k] = P.ms[k];
+        if (counts) counts[k] = P.count[k];
+        if (reset) {
+            P.ms[k] = 0.0;
+            P.count[k] = 0;
+        }
+    }
+    return KFMM_OK;
+}
+
+const char *kfmm_status_str(kfmm_status s)
+{
+    switch (s) {
+    case KFMM_OK: return "ok";
+    case KFMM_ERR_INVALID_ARG: return "invalid argument";
+    case KFMM_ERR_OOM: return "out of memory";
+    case KFMM_ERR_CUDA: return "CUDA error";
+    case KFMM_ERR_NOT_CONVERGED: return "not converged";
+    case KFMM_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+    case KFMM_ERR_NOT_BUILT: return "not built";
+    case KFMM_ERR_INTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+const char *kfmm_last_error(const kfmm_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,264 @@
+// common.cuh -- internal types of the kifmm_elastic library: the context, device buffers,
+// error handling.  Not part of the public ABI (include/kifmm_elastic.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/kifmm_elastic.h"
+
+namespace kfmm {
+
+// ------------------------------------------------------------------------------------
+// Errors: every internal routine returns kfmm_status; the first failure records a message
+// in the context and is passed straight up to the ABI.
+// ------------------------------------------------------------------------------------
+struct Error {
+    kfmm_status code;
+    std::string msg;
+};
+
+#define KF_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            return ctx->fail(KFMM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                  \
+    } while (0)
+
+#define KF_LAUNCH()                                                                        \
+    do {                                                                                   \
+        ++ctx->n_launch;                                                                   \
+        cudaError_t e_ = cudaGetLastError();                                               \
+        if (e_ != cudaSuccess)                                                             \
+            return ctx->fail(KFMM_ERR_CUDA, std::string("kernel launch at ") + __FILE__ + ":" + \
+                                                std::to_string(__LINE__) + ": " +          \
+                                                cudaGetErrorString(e_));                   \
+    } while (0)
+
+#define KF_TRY(expr)                                                                       \
+    do {                                                                                   \
+        kfmm_status s_ = (expr);                                                           \
+        if (s_ != KFMM_OK) return s_;                                                      \
+    } while (0)
+
+// Grow-only device buffer.  Contents are not preserved across growth.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            bytes = o.bytes;
+            o.p = nullptr;
+            o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t nbytes) {
+        if (nbytes <= bytes) return cudaSuccess;
+        release();
+        size_t nb = nbytes < 256 ? 256 : nbytes;
+        cudaError_t e = cudaMalloc(&p, nb);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = nb;
+        return cudaSuccess;
+    }
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Equivalent-surface operators for one (p, nu, radii, tolerances); FP32 copies on device.
+struct Operators {
+    bool ready = false;
+    int p = 0, n_surf = 0, rank = 0;  // rank of the shared M2L basis
+    double nu = -1, r_inner = 0, r_outer = 0, pinv_rtol = 0, m2l_rtol = 0;
+    int m2l_rank_max = 0;
+    DevBuf surf;      // float [n_surf][4]: unit lattice surface points in [-1,1]^3
+    DevBuf pinv_uc;   // float [3n][3n]: pseudo-inverse of U(upward check <- upward equivalent), h = G = 1
+    DevBuf pinv_dc;   // float [3n][3n]: pseudo-inverse of U(downward check <- downward equivalent)
+    DevBuf m2m;       // float [8][3n][3n]: child octant -> parent upward equivalent density
+    DevBuf l2l;       // float [8][3n][3n]: parent -> child octant downward equivalent density
+    DevBuf m2l_vt;    // float [rank][3n]: compression of upward densities (psi = Vt phi)
+    DevBuf m2l_c;     // float [316][rank][rank]: translation in the compressed basis
+    DevBuf m2l_w;     // float [3n][rank]: pinv_dc * U_r (expansion into downward densities)
+};
+
+// Octree and interaction lists (device arrays unless noted).
+struct Tree {
+    bool built = false;
+    int64_t nsrc = 0, ntrg = 0;
+    int max_depth = 0;
+    double root_lo[3] = {0, 0, 0};  // lower corner of the root cube
+    double root_w = 1;              // root cube side
+    int n_boxes = 0, n_leaves = 0, n_levels = 0;
+    std::vector<int> level_off;  // host: first box of each level, size n_levels + 1
+    bool has_nrm = false;
+
+    // points, sorted by Morton key
+    DevBuf src_xyz;   // float4 [nsrc]: x, y, z, 0
+    DevBuf src_nrm;   // float4 [nsrc]
+    DevBuf trg_xyz;   // float4 [ntrg]
+    DevBuf src_perm;  // int [nsrc]: sorted position -> input index
+    DevBuf trg_perm;  // int [ntrg]
+    DevBuf src_key, trg_key;  // uint64 [n]
+
+    // boxes (level-major, Morton order within a level)
+    DevBuf box_key;     // uint64
+    DevBuf box_level;   // int
+    DevBuf box_anchor;  // int4: ix, iy, iz, level
+    DevBuf box_parent;  // int
+    DevBuf box_child;   // int [8] per box, -1 if absent
+    DevBuf box_src;     // int2 [begin, end) into sorted sources
+    DevBuf box_trg;     // int2
+    DevBuf box_leaf;    // int: 1 if leaf
+    DevBuf colleague;   // int [27] per box, -1 if absent (index 13 = itself)
+
+    // interaction lists, CSR by target box
+    DevBuf u_off, u_idx;  // U: leaves adjacent to a leaf (incl. itself)
+    DevBuf w_off, w_idx;  // W: for leaf B, descendants of colleagues, not adjacent, parent adjacent
+    DevBuf x_off, x_idx;  // X: dual of W
+    DevBuf v_off, v_idx;  // V: children of the parent's colleagues, not adjacent
+    // V pairs grouped by direction (for the M2L product)
+    DevBuf vp_src, vp_trg;  // int [n_v]
+    std::vector<int> vdir_off;  // host: 317 offsets into the grouped V pairs
+    DevBuf leaves;              // int [n_leaves]: leaf box indices
+    DevBuf xboxes;              // int: boxes with a non-empty X list
+    int n_xboxes = 0;
+    // octant groups per level for M2M / L2L: children at level l with octant o
+    DevBuf oct_child;           // int: grouped child indices
+    std::vector<int> oct_off;   // host: [(n_levels) * 8 + 1] offsets (level-major, then octant)
+    int64_t n_u = 0, n_v = 0, n_w = 0, n_x = 0;
+    int64_t p2p_pairs = 0, l2p_pairs = 0, p2l_pairs = 0;
+};
+
+// Per-evaluation work arrays.
+struct Work {
+    DevBuf src_rec;   // packed, pre-scaled source records in sorted order
+    DevBuf up_chk;    // float [n_boxes][3n]
+    DevBuf up_phi;    // float [n_boxes][3n]
+    DevBuf psi;       // float [n_boxes][rank]
+    DevBuf cdn;       // float [n_boxes][rank]
+    DevBuf dn_chk;    // float [n_boxes][3n]
+    DevBuf dn_phi;    // float [n_boxes][3n]
+    DevBuf scal;      // float [n_boxes]: G * half-width per box
+    DevBuf stage_in[4];  // staging of host inputs
+    DevBuf stage_out;
+    DevBuf tmp;
+};
+
+// Tile tables of the grouped gather-GEMM, built once per tree.
+struct GemmPlan {
+    DevBuf tiles;  // int4 {matrix index, first column, end column, 0}
+    int n_tiles = 0;
+};
+
+struct FmmPlans {
+    bool valid = false;
+    GemmPlan all, leaves, xboxes, m2l;
+    std::vector<GemmPlan> oct_lvl;  // per level: children grouped by octant (M2M, L2L)
+    DevBuf geom;                    // float4 per box: centre x, y, z and half-width
+};
+
+// Per-phase CUDA-event timing (off unless enabled).
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    struct Pending {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    double ms[KFMM_N_PHASES] = {0};
+    int64_t count[KFMM_N_PHASES] = {0};
+    cudaEvent_t take() {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    ~Profiler() {
+        for (auto &p : pending) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace kfmm
+
+struct kfmm_ctx {
+    kfmm_options opt;
+    cudaStream_t stream = nullptr;
+    double G = 1.0, nu = 0.3;
+    std::string err;
+    kfmm::Operators ops;
+    kfmm::Tree tree;
+    kfmm::Work work;
+    kfmm::FmmPlans plans;
+    kfmm::Profiler prof;
+    int cur_phase = -1;
+    cudaEvent_t cur_ev = nullptr;
+    int64_t n_launch = 0;  // kernels launched by this context since creation
+    // Close the open phase (if any) and open phase `ph` (ph < 0: only close).
+    void phase(int ph) {
+        if (!prof.on) return;
+        if (cur_phase >= 0) {
+            cudaEvent_t e = prof.take();
+            cudaEventRecord(e, stream);
+            prof.pending.push_back({cur_phase, cur_ev, e});
+            cur_ev = nullptr;
+        }
+        if (ph >= 0) {
+            cur_ev = prof.take();
+            cudaEventRecord(cur_ev, stream);
+        }
+        cur_phase = ph;
+    }
+
+    kfmm_status fail(kfmm_status code, const std::string &msg) {
+        if (err.empty() || code != KFMM_OK) err = msg;
+        return code;
+    }
+};
+
+namespace kfmm {
+// tree.cu
+kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm, int64_t nsrc,
+                       const float *trg_xyz, int64_t ntrg);
+// precompute.cpp (host, FP64) + upload
+kfmm_status ensure_operators(kfmm_ctx *ctx);
+// fmm.cu
+kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, int kind, float *out);
+// direct.cu
+kfmm_status direct_sum(kfmm_ctx *ctx, int precision, const void *trg, int64_t ntrg, const void *src,
+                       const void *nrm, int64_t nsrc, const void *sl, const void *dl, int kind, void *out);
+// api.cu helpers
+bool is_device_ptr(const void *p);
+}  // namespace kfmm

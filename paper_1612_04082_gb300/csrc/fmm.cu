@@ -1,0 +1,765 @@
+// fmm.cu -- the evaluation pass of the kernel-independent FMM (Sec. "Kernel-independent fast
+// multipole method"): upward pass (S2M, M2M), M2L on the V lists, P2L on the X lists,
+// downward pass (L2L), and the leaf evaluation (L2P + M2P on the W lists + P2P on the U
+// lists, the "direct summation" of the near zone).
+//
+// Densities on equivalent surfaces are 3-vectors of the single-layer kernel U; sources may
+// carry single- and double-layer densities (Eq. fmm_summation with the normal at the source).
+// The dense operators (pseudo-inverses, M2M, L2L, compressed M2L) are applied by one
+// grouped gather-GEMM kernel: each column of a group is a box vector gathered by index, each
+// group has its own matrix.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "common.cuh"
+#include "kelvin.cuh"
+#include "precompute.h"
+#include "util.cuh"
+
+namespace kfmm {
+
+static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ------------------------------------------------------------------------------------
+// Operators: FP64 host precompute (cached per parameter set) and FP32 upload
+// ------------------------------------------------------------------------------------
+namespace {
+struct CacheEntry {
+    host::OpsParams prm;
+    host::OpsHost ops;
+};
+std::mutex g_cache_mu;
+std::vector<CacheEntry> g_cache;
+
+bool same_params(const host::OpsParams &a, const host::OpsParams &b)
+{
+    return a.p == b.p && a.nu == b.nu && a.r_inner == b.r_inner && a.r_outer == b.r_outer &&
+           a.pinv_rtol == b.pinv_rtol && a.m2l_rtol == b.m2l_rtol && a.m2l_rank_max == b.m2l_rank_max;
+}
+
+// Copy a [rows][cols] FP64 matrix into a zero-padded [rows][ld] FP32 device matrix.
+kfmm_status upload_padded(kfmm_ctx *ctx, DevBuf &dst, const double *src, int nmat, int rows, int cols, int ld,
+                          int rows_pad)
+{
+    std::vector<float> h((size_t)nmat * rows_pad * ld, 0.0f);
+    for (int m = 0; m < nmat; ++m)
+        for (int r = 0; r < rows; ++r)
+            for (int c = 0; c < cols; ++c)
+                h[((size_t)m * rows_pad + r) * ld + c] = (float)src[((size_t)m * rows + r) * cols + c];
+    KF_CUDA(dst.ensure(sizeof(float) * h.size()));
+    KF_CUDA(cudaMemcpy(dst.p, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice));
+    return KFMM_OK;
+}
+}  // namespace
+
+kfmm_status ensure_operators(kfmm_ctx *ctx)
+{
+    Operators &O = ctx->ops;
+    host::OpsParams prm{ctx->opt.p, ctx->nu, ctx->opt.r_inner, ctx->opt.r_outer, ctx->opt.pinv_rtol,
+                        ctx->opt.m2l_rtol, ctx->opt.m2l_rank_max};
+    if (O.ready && O.p == prm.p && O.nu == prm.nu && O.r_inner == prm.r_inner && O.r_outer == prm.r_outer &&
+        O.pinv_rtol == prm.pinv_rtol && O.m2l_rtol == prm.m2l_rtol && O.m2l_rank_max == prm.m2l_rank_max)
+        return KFMM_OK;
+    const host::OpsHost *H = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        for (auto &e : g_cache)
+            if (same_params(e.prm, prm)) H = &e.ops;
+        if (!H) {
+            CacheEntry e;
+            e.prm = prm;
+            if (!host::compute_operators(prm, &e.ops))
+                return ctx->fail(KFMM_ERR_INTERNAL, "operator precompute: eigensolver did not converge");
+            g_cache.push_back(std::move(e));
+            H = &g_cache.back().ops;
+        }
+    }
+    const int n = H->n_surf, m = 3 * n, ld = round_up(m, 16), r = H->rank, rp = round_up(r, 16);
+    {
+        std::vector<float> s((size_t)n * 4, 0.f);
+        for (int a = 0; a < n; ++a)
+            for (int c = 0; c < 3; ++c) s[4 * a + c] = (float)H->surf[3 * a + c];
+        KF_CUDA(O.surf.ensure(sizeof(float) * s.size()));
+        KF_CUDA(cudaMemcpy(O.surf.p, s.data(), sizeof(float) * s.size(), cudaMemcpyHostToDevice));
+    }
+    KF_TRY(upload_padded(ctx, O.pinv_uc, H->pinv_uc.data(), 1, m, m, ld, ld));
+    KF_TRY(upload_padded(ctx, O.pinv_dc, H->pinv_dc.data(), 1, m, m, ld, ld));
+    KF_TRY(upload_padded(ctx, O.m2m, H->m2m.data(), 8, m, m, ld, ld));
+    KF_TRY(upload_padded(ctx, O.l2l, H->l2l.data(), 8, m, m, ld, ld));
+    KF_TRY(upload_padded(ctx, O.m2l_vt, H->m2l_vt.data(), 1, r, m, ld, rp));
+    KF_TRY(upload_padded(ctx, O.m2l_c, H->m2l_c.data(), 316, r, r, rp, rp));
+    KF_TRY(upload_padded(ctx, O.m2l_w, H->m2l_w.data(), 1, m, r, rp, ld));
+    O.p = prm.p;
+    O.nu = prm.nu;
+    O.r_inner = prm.r_inner;
+    O.r_outer = prm.r_outer;
+    O.pinv_rtol = prm.pinv_rtol;
+    O.m2l_rtol = prm.m2l_rtol;
+    O.m2l_rank_max = prm.m2l_rank_max;
+    O.n_surf = n;
+    O.rank = r;
+    O.ready = true;
+    ctx->plans.valid = false;  // box-vector layouts depend on the rank
+    return KFMM_OK;
+}
+
+namespace {
+
+// ------------------------------------------------------------------------------------
+// source records: 4 x float4 = {y, nu'}, {t}, {u}, {n} in sorted order
+// ------------------------------------------------------------------------------------
+struct SrcRec {
+    float4 y, t, u, n;
+};
+
+__global__ void pack_sources_kernel(int64_t ns, const float4 *__restrict__ xyz, const float4 *__restrict__ nrm,
+                                    const int *__restrict__ perm, const float *__restrict__ sl,
+                                    const float *__restrict__ dl, int ld, int col, float st, float su,
+                                    float b12, SrcRec *__restrict__ rec)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += stride) {
+        const int j = perm[i];
+        SrcRec r;
+        float4 p = xyz[i];
+        float3 t = make_float3(0.f, 0.f, 0.f), u = make_float3(0.f, 0.f, 0.f);
+        float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (sl) {
+            const float *s = sl + (int64_t)j * ld + 3 * col;
+            t = make_float3(st * s[0], st * s[1], st * s[2]);
+        }
+        if (dl) {
+            const float *s = dl + (int64_t)j * ld + 3 * col;
+            u = make_float3(su * s[0], su * s[1], su * s[2]);
+            nn = nrm[i];
+        }
+        const float nup = b12 * (nn.x * u.x + nn.y * u.y + nn.z * u.z);
+        r.y = make_float4(p.x, p.y, p.z, nup);
+        r.t = make_float4(t.x, t.y, t.z, 0.f);
+        r.u = make_float4(u.x, u.y, u.z, 0.f);
+        r.n = make_float4(nn.x, nn.y, nn.z, 0.f);
+        rec[i] = r;
+    }
+}
+
+__global__ void box_geom_kernel(int nb, const int4 *__restrict__ anchor, double lo0, double lo1, double lo2,
+                                double w, float4 *__restrict__ geom)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int4 a = anchor[b];
+    const double s = w / (double)(1 << a.w);
+    geom[b] = make_float4((float)(lo0 + (a.x + 0.5) * s), (float)(lo1 + (a.y + 0.5) * s),
+                          (float)(lo2 + (a.z + 0.5) * s), (float)(0.5 * s));
+}
+
+// ------------------------------------------------------------------------------------
+// check-surface potentials from sources (S2M on leaves, P2L on X lists)
+// One CTA per box, one thread per check point; sources staged through shared memory.
+// ------------------------------------------------------------------------------------
+constexpr int kChkThreads = 160;  // >= 152 check points at p = 6
+constexpr int kChkStage = 256;
+
+template <bool SL, bool DL>
+__device__ __forceinline__ void chk_pair(float x, float y, float z, const SrcRec &q, float a34, float b12, float &ox,
+                                         float &oy, float &oz)
+{
+    const float dx = x - q.y.x, dy = y - q.y.y, dz = z - q.y.z;
+    if (SL && DL)
+        acc_sl_dl<float>(dx, dy, dz, q.t.x, q.t.y, q.t.z, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, a34, b12,
+                         ox, oy, oz);
+    else if (SL)
+        acc_sl<float>(dx, dy, dz, q.t.x, q.t.y, q.t.z, a34, ox, oy, oz);
+    else
+        acc_dl<float>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, b12, ox, oy, oz);
+}
+
+template <bool SL, bool DL>
+__global__ void __launch_bounds__(kChkThreads)
+check_potential_kernel(const int *__restrict__ boxes, int nbox, int use_xlist, const int *__restrict__ xo,
+                       const int *__restrict__ xi, const int2 *__restrict__ bsrc, const float4 *__restrict__ geom,
+                       const float4 *__restrict__ surf, int n_surf, float radius, const SrcRec *__restrict__ rec,
+                       float a34, float b12, float *__restrict__ out, int ldo)
+{
+    __shared__ SrcRec sh[kChkStage];
+    const int b = boxes ? boxes[blockIdx.x] : blockIdx.x;
+    const float4 g = geom[b];
+    const int tid = threadIdx.x;
+    // each thread owns check points tid and tid + kChkThreads (n_surf <= 2 kChkThreads)
+    const bool has0 = tid < n_surf, has1 = tid + kChkThreads < n_surf;
+    float x = 0.f, y = 0.f, z = 0.f, x1 = 0.f, y1 = 0.f, z1 = 0.f;
+    if (has0) {
+        const float4 s = surf[tid];
+        x = g.x + radius * g.w * s.x;
+        y = g.y + radius * g.w * s.y;
+        z = g.z + radius * g.w * s.z;
+    }
+    if (has1) {
+        const float4 s = surf[tid + kChkThreads];
+        x1 = g.x + radius * g.w * s.x;
+        y1 = g.y + radius * g.w * s.y;
+        z1 = g.z + radius * g.w * s.z;
+    }
+    float ox = 0.f, oy = 0.f, oz = 0.f, px = 0.f, py = 0.f, pz = 0.f;
+    const int nlist = use_xlist ? xo[b + 1] - xo[b] : 1;
+    for (int li = 0; li < nlist; ++li) {
+        const int sb = use_xlist ? xi[xo[b] + li] : b;
+        const int2 r = bsrc[sb];
+        for (int base = r.x; base < r.y; base += kChkStage) {
+            const int cnt = min(kChkStage, r.y - base);
+            __syncthreads();
+            for (int k = tid; k < cnt; k += kChkThreads) sh[k] = rec[base + k];
+            __syncthreads();
+            if (has0) {
+                for (int s = 0; s < cnt; ++s) {
+                    const SrcRec q = sh[s];
+                    chk_pair<SL, DL>(x, y, z, q, a34, b12, ox, oy, oz);
+                    if (has1) chk_pair<SL, DL>(x1, y1, z1, q, a34, b12, px, py, pz);
+                }
+            }
+        }
+    }
+    if (has0) {
+        float *o = out + (int64_t)b * ldo + 3 * tid;
+        o[0] = ox;
+        o[1] = oy;
+        o[2] = oz;
+    }
+    if (has1) {
+        float *o = out + (int64_t)b * ldo + 3 * (tid + kChkThreads);
+        o[0] = px;
+        o[1] = py;
+        o[2] = pz;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// grouped gather-GEMM: for each tile (group g, columns c0..c1):
+//   y_j = alpha_j * A_g (M x K) * X[src_j]   ->  Y[dst_j] (= | += | atomic +=)
+// FP32 SIMT, 64 x 64 output tile per CTA, K in steps of 16, 4 x 4 per thread.
+// ------------------------------------------------------------------------------------
+struct GemmArgs {
+    const float *A;
+    int64_t a_stride;
+    int M, K, lda;
+    const int4 *tiles;  // {matrix index, c0, c1, 0}
+    const int *src_idx;
+    const int *dst_idx;
+    const int *parent;
+    int src_par, dst_par;
+    const float *X;
+    int ldx;
+    float *Y;
+    int ldy;
+    const float4 *geom;  // alpha_j = alpha * geom[dst].w when non-null
+    float alpha;
+    int mode;  // 0 store, 1 add, 2 atomic add
+};
+
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+__global__ void __launch_bounds__(256) gemm_gather_kernel(GemmArgs g)
+{
+    __shared__ float As[GBK][GBM + 4];
+    __shared__ float Bs[GBK][GBN + 4];
+    __shared__ int s_src[GBN], s_dst[GBN];
+    const int4 tile = g.tiles[blockIdx.x];
+    const int m0 = blockIdx.y * GBM;
+    const int tid = threadIdx.x;
+    const int ncols = tile.z - tile.y;
+    if (tid < GBN) {
+        int j = tile.y + tid;
+        int s = -1, d = -1;
+        if (tid < ncols) {
+            s = g.src_idx ? g.src_idx[j] : j;
+            d = g.dst_idx ? g.dst_idx[j] : j;
+            if (g.src_par) s = g.parent[s];
+            if (g.dst_par) d = g.parent[d];
+        }
+        s_src[tid] = s;
+        s_dst[tid] = d;
+    }
+    __syncthreads();
+    const float *A = g.A + (int64_t)tile.x * g.a_stride;
+    const int tx = tid & 15, ty = tid >> 4;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    // load mapping
+    const int am = tid >> 2, ak = (tid & 3) * 4;       // A: row am, cols ak..ak+3
+    const int bn = tid & 63, bk = (tid >> 6) * 4;      // B: column bn, rows bk..bk+3
+    const int bsrc = s_src[bn];
+    for (int k0 = 0; k0 < g.K; k0 += GBK) {
+        float4 av = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m0 + am < g.M) av = *reinterpret_cast<const float4 *>(A + (int64_t)(m0 + am) * g.lda + k0 + ak);
+        As[ak + 0][am] = av.x;
+        As[ak + 1][am] = av.y;
+        As[ak + 2][am] = av.z;
+        As[ak + 3][am] = av.w;
+        float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (bsrc >= 0) bv = *reinterpret_cast<const float4 *>(g.X + (int64_t)bsrc * g.ldx + k0 + bk);
+        Bs[bk + 0][bn] = bv.x;
+        Bs[bk + 1][bn] = bv.y;
+        Bs[bk + 2][bn] = bv.z;
+        Bs[bk + 3][bn] = bv.w;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    const int mrow = m0 + ty * 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = tx * 4 + j;
+        const int d = s_dst[c];
+        if (d < 0) continue;
+        const float al = g.geom ? g.alpha * g.geom[d].w : g.alpha;
+        float *y = g.Y + (int64_t)d * g.ldy + mrow;
+        if (mrow + 3 < g.M) {
+            float4 v = make_float4(al * acc[0][j], al * acc[1][j], al * acc[2][j], al * acc[3][j]);
+            if (g.mode == 0) {
+                *reinterpret_cast<float4 *>(y) = v;
+            } else if (g.mode == 1) {
+                float4 o = *reinterpret_cast<float4 *>(y);
+                *reinterpret_cast<float4 *>(y) = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+            } else {
+                atomicAdd(reinterpret_cast<float4 *>(y), v);
+            }
+        } else {
+            for (int i = 0; i < 4; ++i) {
+                if (mrow + i >= g.M) break;
+                const float v = al * acc[i][j];
+                if (g.mode == 0) y[i] = v;
+                else if (g.mode == 1) y[i] += v;
+                else atomicAdd(y + i, v);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// leaf evaluation: L2P (downward equivalent density of the leaf), M2P (upward equivalent
+// densities of the W list), P2P (sources of the U list).  One CTA of 4 warps per leaf;
+// each lane owns up to two targets (lane, lane + 32) of a 64-target chunk; the warps split
+// every source set four ways and reduce through shared memory at the end.
+// ------------------------------------------------------------------------------------
+constexpr int kEvalThreads = 128;
+constexpr int kEvalStage = 512;   // P2P source records staged at a time
+constexpr int kMaxRanges = 512;   // U-list entries held in shared memory per pass
+
+template <int KIND>
+struct Acc {
+    float v[KIND == KFMM_DISP ? 3 : 6];
+};
+
+template <int KIND, bool SL, bool DL>
+__device__ __forceinline__ void p2p_pair(float x, float y, float z, const SrcRec &q, float a34, float b12, float nu,
+                                         float *o)
+{
+    const float dx = x - q.y.x, dy = y - q.y.y, dz = z - q.y.z;
+    if (KIND == KFMM_DISP) {
+        if (SL && DL)
+            acc_sl_dl<float>(dx, dy, dz, q.t.x, q.t.y, q.t.z, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, a34,
+                             b12, o[0], o[1], o[2]);
+        else if (SL)
+            acc_sl<float>(dx, dy, dz, q.t.x, q.t.y, q.t.z, a34, o[0], o[1], o[2]);
+        else
+            acc_dl<float>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, b12, o[0], o[1], o[2]);
+    } else {
+        if (SL) acc_D<float>(dx, dy, dz, q.t.x, q.t.y, q.t.z, b12, o);
+        if (DL) acc_S<float>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, nu, b12, o);
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ void equiv_pair(float x, float y, float z, const float4 &p, const float4 &f, float a34,
+                                           float b12, float *o)
+{
+    const float dx = x - p.x, dy = y - p.y, dz = z - p.z;
+    if (KIND == KFMM_DISP) acc_sl<float>(dx, dy, dz, f.x, f.y, f.z, a34, o[0], o[1], o[2]);
+    else acc_D<float>(dx, dy, dz, f.x, f.y, f.z, b12, o);
+}
+
+struct EvalArgs {
+    const int *leaves;
+    const int2 *btrg, *bsrc;
+    const float4 *geom;
+    const int *uo, *ui, *wo, *wi;
+    const float4 *trg;
+    const int *trg_perm;
+    const SrcRec *rec;
+    const float4 *surf;
+    int n_surf;
+    float r_in, r_out;
+    const float *dn_phi, *up_phi;
+    int ld_phi;
+    float phi_scale;  // c_sl for DISP, 1 for STRESS (D carries c_D at the end)
+    float a34, b12, nu;
+    float out_scale;  // 1 for DISP, c_D for STRESS
+    float *out;
+    int ldo, col;
+};
+
+template <int KIND, bool SL, bool DL>
+__global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
+{
+    constexpr int NO = KIND == KFMM_DISP ? 3 : 6;
+    __shared__ SrcRec srec[kEvalStage];
+    __shared__ int rbeg[kMaxRanges], rpre[kMaxRanges + 1];
+    __shared__ float red[4][64][NO];
+    float4 *epos = reinterpret_cast<float4 *>(srec);           // equivalent sources reuse the stage
+    float4 *eden = reinterpret_cast<float4 *>(srec) + 512;   // (n_surf <= 512)
+
+    const int b = e.leaves[blockIdx.x];
+    const int2 tr = e.btrg[b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int uo0 = e.uo[b], nU = e.uo[b + 1] - uo0;
+    const int wo0 = e.wo[b], nW = e.wo[b + 1] - wo0;
+    for (int c0 = tr.x; c0 < tr.y; c0 += 64) {
+        const int nt = min(64, tr.y - c0);
+        const bool two = nt > 32;
+        float x0 = 0.f, y0 = 0.f, z0 = 0.f, x1 = 0.f, y1 = 0.f, z1 = 0.f;
+        if (lane < nt) {
+            float4 p = e.trg[c0 + lane];
+            x0 = p.x; y0 = p.y; z0 = p.z;
+        }
+        if (lane + 32 < nt) {
+            float4 p = e.trg[c0 + lane + 32];
+            x1 = p.x; y1 = p.y; z1 = p.z;
+        }
+        float o0[NO], o1[NO];
+#pragma unroll
+        for (int a = 0; a < NO; ++a) o0[a] = o1[a] = 0.f;
+
+        // ---- L2P and M2P: equivalent sources, one box at a time
+        for (int eb = -1; eb < nW; ++eb) {
+            const int src_box = eb < 0 ? b : e.wi[wo0 + eb];
+            const float4 g = e.geom[src_box];
+            const float rad = (eb < 0 ? e.r_out : e.r_in) * g.w;
+            const float *phi = (eb < 0 ? e.dn_phi : e.up_phi) + (int64_t)src_box * e.ld_phi;
+            __syncthreads();
+            for (int k = threadIdx.x; k < e.n_surf; k += kEvalThreads) {
+                const float4 s = e.surf[k];
+                epos[k] = make_float4(g.x + rad * s.x, g.y + rad * s.y, g.z + rad * s.z, 0.f);
+                eden[k] = make_float4(e.phi_scale * phi[3 * k], e.phi_scale * phi[3 * k + 1],
+                                      e.phi_scale * phi[3 * k + 2], 0.f);
+            }
+            __syncthreads();
+            for (int k = warp; k < e.n_surf; k += 4) {
+                const float4 p = epos[k], f = eden[k];
+                equiv_pair<KIND>(x0, y0, z0, p, f, e.a34, e.b12, o0);
+                if (two) equiv_pair<KIND>(x1, y1, z1, p, f, e.a34, e.b12, o1);
+            }
+        }
+        // ---- P2P over the U list, ranges staged in passes of kMaxRanges
+        for (int r0 = 0; r0 < nU; r0 += kMaxRanges) {
+            const int nr = min(kMaxRanges, nU - r0);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int acc = 0;
+                for (int k = 0; k < nr; ++k) {
+                    const int2 s = e.bsrc[e.ui[uo0 + r0 + k]];
+                    rbeg[k] = s.x;
+                    rpre[k] = acc;
+                    acc += s.y - s.x;
+                }
+                rpre[nr] = acc;
+            }
+            __syncthreads();
+            const int total = rpre[nr];
+            for (int base = 0; base < total; base += kEvalStage) {
+                const int cnt = min(kEvalStage, total - base);
+                __syncthreads();
+                for (int k = threadIdx.x; k < cnt; k += kEvalThreads) {
+                    const int f = base + k;
+                    int lo = 0, hi = nr;  // find the range holding f: rpre[lo] <= f < rpre[lo+1]
+                    while (hi - lo > 1) {
+                        int m = (lo + hi) >> 1;
+                        if (rpre[m] <= f) lo = m;
+                        else hi = m;
+                    }
+                    srec[k] = e.rec[rbeg[lo] + (f - rpre[lo])];
+                }
+                __syncthreads();
+                for (int s = warp; s < cnt; s += 4) {
+                    const SrcRec q = srec[s];
+                    p2p_pair<KIND, SL, DL>(x0, y0, z0, q, e.a34, e.b12, e.nu, o0);
+                    if (two) p2p_pair<KIND, SL, DL>(x1, y1, z1, q, e.a34, e.b12, e.nu, o1);
+                }
+            }
+        }
+        // ---- reduce over the 4 warps and write in input order
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < NO; ++a) {
+            red[warp][lane][a] = o0[a];
+            red[warp][lane + 32][a] = o1[a];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nt; t += kEvalThreads) {
+            const int gi = e.trg_perm[c0 + t];
+            float *o = e.out + (int64_t)gi * e.ldo + NO * e.col;
+#pragma unroll
+            for (int a = 0; a < NO; ++a)
+                o[a] = e.out_scale * (red[0][t][a] + red[1][t][a] + red[2][t][a] + red[3][t][a]);
+        }
+    }
+}
+
+template <int KIND>
+void launch_eval(const EvalArgs &e, int nleaves, bool sl, bool dl, cudaStream_t st)
+{
+    if (sl && dl) eval_leaf_kernel<KIND, true, true><<<nleaves, kEvalThreads, 0, st>>>(e);
+    else if (sl) eval_leaf_kernel<KIND, true, false><<<nleaves, kEvalThreads, 0, st>>>(e);
+    else eval_leaf_kernel<KIND, false, true><<<nleaves, kEvalThreads, 0, st>>>(e);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// GEMM plans: tile tables built once per tree
+// ------------------------------------------------------------------------------------
+static kfmm_status make_plan(kfmm_ctx *ctx, GemmPlan &pl, const std::vector<int> &group_mat,
+                             const std::vector<int> &group_begin, const std::vector<int> &group_end)
+{
+    std::vector<int4> t;
+    for (size_t gi = 0; gi < group_mat.size(); ++gi)
+        for (int c = group_begin[gi]; c < group_end[gi]; c += GBN)
+            t.push_back(make_int4(group_mat[gi], c, std::min(c + GBN, group_end[gi]), 0));
+    pl.n_tiles = (int)t.size();
+    if (pl.n_tiles) {
+        KF_CUDA(pl.tiles.ensure(sizeof(int4) * t.size()));
+        KF_CUDA(cudaMemcpy(pl.tiles.p, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
+    }
+    return KFMM_OK;
+}
+
+static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
+{
+    Tree &T = ctx->tree;
+    const cudaStream_t st = ctx->stream;
+    KF_TRY(make_plan(ctx, P.all, {0}, {0}, {T.n_boxes}));
+    KF_TRY(make_plan(ctx, P.leaves, {0}, {0}, {T.n_leaves}));
+    KF_TRY(make_plan(ctx, P.xboxes, {0}, {0}, {T.n_xboxes}));
+    {
+        std::vector<int> gm(316), gb(316), ge(316);
+        for (int d = 0; d < 316; ++d) {
+            gm[d] = d;
+            gb[d] = T.vdir_off[d];
+            ge[d] = T.vdir_off[d + 1];
+        }
+        KF_TRY(make_plan(ctx, P.m2l, gm, gb, ge));
+    }
+    P.oct_lvl.clear();
+    P.oct_lvl.resize(T.n_levels);
+    for (int l = 1; l < T.n_levels; ++l) {
+        std::vector<int> gm(8), gb(8), ge(8);
+        for (int o = 0; o < 8; ++o) {
+            gm[o] = o;
+            gb[o] = T.oct_off[8 * l + o];
+            ge[o] = T.oct_off[8 * l + o + 1];
+        }
+        KF_TRY(make_plan(ctx, P.oct_lvl[l], gm, gb, ge));
+    }
+    KF_CUDA(P.geom.ensure(sizeof(float4) * T.n_boxes));
+    box_geom_kernel<<<grid_for(T.n_boxes, 256, 1 << 30), 256, 0, st>>>(
+        T.n_boxes, T.box_anchor.as<int4>(), T.root_lo[0], T.root_lo[1], T.root_lo[2], T.root_w,
+        P.geom.as<float4>());
+    KF_LAUNCH();
+    return KFMM_OK;
+}
+
+static kfmm_status run_gemm(kfmm_ctx *ctx, const GemmPlan &pl, const float *A, int64_t a_stride, int M, int K,
+                            int lda, const int *src, const int *dst, int src_par, int dst_par, const float *X,
+                            int ldx, float *Y, int ldy, const float4 *geom, float alpha, int mode)
+{
+    if (pl.n_tiles == 0) return KFMM_OK;
+    GemmArgs g;
+    g.A = A;
+    g.a_stride = a_stride;
+    g.M = M;
+    g.K = K;
+    g.lda = lda;
+    g.tiles = pl.tiles.as<int4>();
+    g.src_idx = src;
+    g.dst_idx = dst;
+    g.parent = ctx->tree.box_parent.as<int>();
+    g.src_par = src_par;
+    g.dst_par = dst_par;
+    g.X = X;
+    g.ldx = ldx;
+    g.Y = Y;
+    g.ldy = ldy;
+    g.geom = geom;
+    g.alpha = alpha;
+    g.mode = mode;
+    dim3 grid(pl.n_tiles, (M + GBM - 1) / GBM);
+    gemm_gather_kernel<<<grid, 256, 0, ctx->stream>>>(g);
+    KF_LAUNCH();
+    return KFMM_OK;
+}
+
+kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, int kind, float *out)
+{
+    Tree &T = ctx->tree;
+    Operators &O = ctx->ops;
+    Work &W = ctx->work;
+    const cudaStream_t st = ctx->stream;
+    KF_TRY(ensure_operators(ctx));
+    FmmPlans &P = ctx->plans;
+    const int n = O.n_surf, m = 3 * n, ld = round_up(m, 16), r = O.rank, rp = round_up(r, 16);
+    const int nb = T.n_boxes;
+    const int64_t ns = T.nsrc;
+    if (!P.valid) {
+        KF_TRY(build_plans(ctx, P));
+        // box vectors: zero once, so the padding lanes read by the GEMM K loops stay zero
+        DevBuf *bufs[6] = {&W.up_chk, &W.up_phi, &W.dn_chk, &W.dn_phi, &W.psi, &W.cdn};
+        const int lds[6] = {ld, ld, ld, ld, rp, rp};
+        for (int k = 0; k < 6; ++k) {
+            KF_CUDA(bufs[k]->ensure(sizeof(float) * (size_t)nb * lds[k]));
+            KF_CUDA(cudaMemsetAsync(bufs[k]->p, 0, sizeof(float) * (size_t)nb * lds[k], st));
+        }
+        P.valid = true;
+    }
+    KF_CUDA(W.src_rec.ensure(sizeof(SrcRec) * ns));
+    const auto kc = make_kelvin<float>(ctx->G, ctx->nu);
+    const float4 *geom = P.geom.as<float4>();
+    const int ldd = 3 * ncol;
+    for (int col = 0; col < ncol; ++col) {
+        // ---- pack sources (displacement scaling) for the upward pass and P2L
+        ctx->phase(KFMM_PH_PACK);
+        pack_sources_kernel<<<grid_for(ns, 256), 256, 0, st>>>(ns, T.src_xyz.as<float4>(), T.src_nrm.as<float4>(),
+                                                                T.src_perm.as<int>(), sl, dl, ldd, col, kc.c_sl,
+                                                                kc.c_dl, kc.b12, W.src_rec.as<SrcRec>());
+        KF_LAUNCH();
+        // ---- S2M: sources -> upward check surface of each leaf
+        ctx->phase(KFMM_PH_S2M);
+        KF_CUDA(cudaMemsetAsync(W.up_phi.p, 0, sizeof(float) * (size_t)nb * ld, st));
+        if (T.n_leaves) {
+            if (sl && dl)
+                check_potential_kernel<true, true><<<T.n_leaves, kChkThreads, 0, st>>>(
+                    T.leaves.as<int>(), T.n_leaves, 0, nullptr, nullptr, T.box_src.as<int2>(), geom,
+                    O.surf.as<float4>(), n, (float)O.r_outer, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
+                    W.up_chk.as<float>(), ld);
+            else if (sl)
+                check_potential_kernel<true, false><<<T.n_leaves, kChkThreads, 0, st>>>(
+                    T.leaves.as<int>(), T.n_leaves, 0, nullptr, nullptr, T.box_src.as<int2>(), geom,
+                    O.surf.as<float4>(), n, (float)O.r_outer, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
+                    W.up_chk.as<float>(), ld);
+            else
+                check_potential_kernel<false, true><<<T.n_leaves, kChkThreads, 0, st>>>(
+                    T.leaves.as<int>(), T.n_leaves, 0, nullptr, nullptr, T.box_src.as<int2>(), geom,
+                    O.surf.as<float4>(), n, (float)O.r_outer, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
+                    W.up_chk.as<float>(), ld);
+            KF_LAUNCH();
+        }
+        // upward equivalent density of the leaves: phi = G h pinv_uc chk
+        ctx->phase(KFMM_PH_UP_PINV);
+        KF_TRY(run_gemm(ctx, P.leaves, O.pinv_uc.as<float>(), 0, m, ld, ld, T.leaves.as<int>(), T.leaves.as<int>(),
+                        0, 0, W.up_chk.as<float>(), ld, W.up_phi.as<float>(), ld, geom, (float)ctx->G, 0));
+        // ---- M2M, bottom-up
+        ctx->phase(KFMM_PH_M2M);
+        for (int l = T.n_levels - 1; l >= 1; --l)
+            KF_TRY(run_gemm(ctx, P.oct_lvl[l], O.m2m.as<float>(), (int64_t)ld * ld, m, ld, ld, T.oct_child.as<int>(),
+                            T.oct_child.as<int>(), 0, 1, W.up_phi.as<float>(), ld, W.up_phi.as<float>(), ld,
+                            nullptr, 1.f, 2));
+        // ---- compress the upward densities and translate (M2L on the V lists)
+        ctx->phase(KFMM_PH_M2L);
+        KF_TRY(run_gemm(ctx, P.all, O.m2l_vt.as<float>(), 0, r, ld, ld, nullptr, nullptr, 0, 0,
+                        W.up_phi.as<float>(), ld, W.psi.as<float>(), rp, nullptr, 1.f, 0));
+        KF_CUDA(cudaMemsetAsync(W.cdn.p, 0, sizeof(float) * (size_t)nb * rp, st));
+        KF_TRY(run_gemm(ctx, P.m2l, O.m2l_c.as<float>(), (int64_t)rp * rp, r, rp, rp, T.vp_src.as<int>(),
+                        T.vp_trg.as<int>(), 0, 0, W.psi.as<float>(), rp, W.cdn.as<float>(), rp, nullptr, 1.f, 2));
+        // ---- P2L: X-list sources -> downward check surface
+        ctx->phase(KFMM_PH_P2L);
+        if (T.n_xboxes) {
+            if (sl && dl)
+                check_potential_kernel<true, true><<<T.n_xboxes, kChkThreads, 0, st>>>(
+                    T.xboxes.as<int>(), T.n_xboxes, 1, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(),
+                    geom, O.surf.as<float4>(), n, (float)O.r_inner, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
+                    W.dn_chk.as<float>(), ld);
+            else if (sl)
+                check_potential_kernel<true, false><<<T.n_xboxes, kChkThreads, 0, st>>>(
+                    T.xboxes.as<int>(), T.n_xboxes, 1, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(),
+                    geom, O.surf.as<float4>(), n, (float)O.r_inner, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
+                    W.dn_chk.as<float>(), ld);
+            else
+                check_potential_kernel<false, true><<<T.n_xboxes, kChkThreads, 0, st>>>(
+                    T.xboxes.as<int>(), T.n_xboxes, 1, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(),
+                    geom, O.surf.as<float4>(), n, (float)O.r_inner, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
+                    W.dn_chk.as<float>(), ld);
+            KF_LAUNCH();
+        }
+        // ---- downward densities: phi_dn = W c + G h pinv_dc chk_dn, then L2L top-down
+        ctx->phase(KFMM_PH_DOWN);
+        KF_TRY(run_gemm(ctx, P.all, O.m2l_w.as<float>(), 0, m, rp, rp, nullptr, nullptr, 0, 0, W.cdn.as<float>(),
+                        rp, W.dn_phi.as<float>(), ld, nullptr, 1.f, 0));
+        KF_TRY(run_gemm(ctx, P.xboxes, O.pinv_dc.as<float>(), 0, m, ld, ld, T.xboxes.as<int>(), T.xboxes.as<int>(),
+                        0, 0, W.dn_chk.as<float>(), ld, W.dn_phi.as<float>(), ld, geom, (float)ctx->G, 1));
+        for (int l = 3; l < T.n_levels; ++l)
+            KF_TRY(run_gemm(ctx, P.oct_lvl[l], O.l2l.as<float>(), (int64_t)ld * ld, m, ld, ld, T.oct_child.as<int>(),
+                            T.oct_child.as<int>(), 1, 0, W.dn_phi.as<float>(), ld, W.dn_phi.as<float>(), ld,
+                            nullptr, 1.f, 1));
+        // ---- leaf evaluation
+        ctx->phase(KFMM_PH_EVAL);
+        const SrcRec *rec = W.src_rec.as<SrcRec>();
+        if (kind == KFMM_STRESS) {
+            // re-pack with stress scaling: t unscaled, u scaled by c_S / c_D
+            KF_CUDA(W.tmp.ensure(sizeof(SrcRec) * ns));
+            pack_sources_kernel<<<grid_for(ns, 256), 256, 0, st>>>(
+                ns, T.src_xyz.as<float4>(), T.src_nrm.as<float4>(), T.src_perm.as<int>(), sl, dl, ldd, col, 1.f,
+                kc.c_S / kc.c_D, kc.b12, W.tmp.as<SrcRec>());
+            KF_LAUNCH();
+            rec = W.tmp.as<SrcRec>();
+        }
+        EvalArgs e;
+        e.leaves = T.leaves.as<int>();
+        e.btrg = T.box_trg.as<int2>();
+        e.bsrc = T.box_src.as<int2>();
+        e.geom = geom;
+        e.uo = T.u_off.as<int>();
+        e.ui = T.u_idx.as<int>();
+        e.wo = T.w_off.as<int>();
+        e.wi = T.w_idx.as<int>();
+        e.trg = T.trg_xyz.as<float4>();
+        e.trg_perm = T.trg_perm.as<int>();
+        e.rec = rec;
+        e.surf = O.surf.as<float4>();
+        e.n_surf = n;
+        e.r_in = (float)O.r_inner;
+        e.r_out = (float)O.r_outer;
+        e.dn_phi = W.dn_phi.as<float>();
+        e.up_phi = W.up_phi.as<float>();
+        e.ld_phi = ld;
+        e.phi_scale = kind == KFMM_DISP ? kc.c_sl : 1.f;
+        e.a34 = kc.a34;
+        e.b12 = kc.b12;
+        e.nu = kc.nu;
+        e.out_scale = kind == KFMM_DISP ? 1.f : kc.c_D;
+        e.out = out;
+        e.ldo = (kind == KFMM_DISP ? 3 : 6) * ncol;
+        e.col = col;
+        if (T.n_leaves) {
+            if (kind == KFMM_DISP) launch_eval<KFMM_DISP>(e, T.n_leaves, sl != nullptr, dl != nullptr, st);
+            else launch_eval<KFMM_STRESS>(e, T.n_leaves, sl != nullptr, dl != nullptr, st);
+            KF_LAUNCH();
+        }
+        ctx->phase(-1);
+    }
+    return KFMM_OK;
+}
+
+}  // namespace kfmm

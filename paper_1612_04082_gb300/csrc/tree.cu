@@ -1,0 +1,956 @@
+// tree.cu -- octree build and interaction lists on the device (Sec. "Kernel-independent fast
+// multipole method": "generation of an octree partitioning of the domain into boxes";
+// U/V/W/X lists as in the kernel-independent FMM the paper builds on).
+//
+// Steps: bounding cube -> 3L-bit Morton keys -> LSD radix sort (8-bit digits, stable,
+// written here) -> level-by-level split of every box holding more than leaf_cap sources or
+// targets -> colleagues (same-level neighbours) -> U, V, W, X lists as CSR.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "util.cuh"
+
+namespace kfmm {
+
+// ------------------------------------------------------------------------------------
+// scan
+// ------------------------------------------------------------------------------------
+namespace {
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 2;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void scan_tile_kernel(const int *__restrict__ in, int *__restrict__ out, int n,
+                                 int *__restrict__ tile_sums)
+{
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        s += v[k];
+    }
+    int incl = warp_incl_scan(s);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int t = warp_tot[lane];
+        t = warp_incl_scan(t);
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int excl = incl - s + (warp > 0 ? warp_tot[warp - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = excl;
+        excl += v[k];
+    }
+    if (threadIdx.x == kScanThreads - 1 && tile_sums) tile_sums[blockIdx.x] = excl;
+}
+
+__global__ void scan_add_kernel(int *__restrict__ out, int n, const int *__restrict__ tile_off)
+{
+    const int i = blockIdx.x * kScanTile + threadIdx.x;
+    const int add = tile_off[blockIdx.x];
+    for (int k = i; k < min(n, (int)(blockIdx.x + 1) * kScanTile); k += kScanThreads) out[k] += add;
+}
+
+__global__ void scan_total_kernel(const int *last_in, const int *out, int n, int *total)
+{
+    *total = (n > 0) ? out[n - 1] + last_in[0] : 0;
+}
+
+__global__ void copy_last_kernel(const int *in, int n, int *dst) { *dst = n > 0 ? in[n - 1] : 0; }
+}  // namespace
+
+kfmm_status scan_exclusive(kfmm_ctx *ctx, const int *in, int *out, int n, int *total)
+{
+    if (n <= 0) {
+        if (total) KF_CUDA(cudaMemsetAsync(total, 0, sizeof(int), ctx->stream));
+        return KFMM_OK;
+    }
+    const int tiles = (n + kScanTile - 1) / kScanTile;
+    DevBuf lastbuf;
+    int *last = nullptr;
+    if (total) {
+        // keep in[n-1] (in may alias out)
+        KF_CUDA(lastbuf.ensure(sizeof(int)));
+        last = lastbuf.as<int>();
+        copy_last_kernel<<<1, 1, 0, ctx->stream>>>(in, n, last);
+        KF_LAUNCH();
+    }
+    if (tiles == 1) {
+        scan_tile_kernel<<<1, kScanThreads, 0, ctx->stream>>>(in, out, n, nullptr);
+        KF_LAUNCH();
+    } else {
+        DevBuf sums;
+        KF_CUDA(sums.ensure(sizeof(int) * tiles));
+        scan_tile_kernel<<<tiles, kScanThreads, 0, ctx->stream>>>(in, out, n, sums.as<int>());
+        KF_LAUNCH();
+        KF_TRY(scan_exclusive(ctx, sums.as<int>(), sums.as<int>(), tiles, nullptr));
+        scan_add_kernel<<<tiles, kScanThreads, 0, ctx->stream>>>(out, n, sums.as<int>());
+        KF_LAUNCH();
+        KF_CUDA(cudaStreamSynchronize(ctx->stream));  // sums is freed on return
+    }
+    if (total) {
+        scan_total_kernel<<<1, 1, 0, ctx->stream>>>(last, out, n, total);
+        KF_LAUNCH();
+        KF_CUDA(cudaStreamSynchronize(ctx->stream));  // lastbuf is freed on return
+    }
+    return KFMM_OK;
+}
+
+kfmm_status read_int(kfmm_ctx *ctx, const int *dptr, int *host)
+{
+    KF_CUDA(cudaMemcpyAsync(host, dptr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    KF_CUDA(cudaStreamSynchronize(ctx->stream));
+    return KFMM_OK;
+}
+
+namespace {
+
+// ------------------------------------------------------------------------------------
+// bounding box and input checks
+// ------------------------------------------------------------------------------------
+constexpr int kBBoxBlocks = 2 * kNumSMs;
+constexpr int kBBoxThreads = 256;
+
+__global__ void bbox_kernel(const float *__restrict__ a, int64_t na, const float *__restrict__ b,
+                            int64_t nb, const float *__restrict__ nrm, float *__restrict__ part)
+{
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float bad = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += stride) {
+        const float *p = i < na ? a + 3 * i : b + 3 * (i - na);
+        for (int c = 0; c < 3; ++c) {
+            float v = p[c];
+            if (!isfinite(v)) bad += 1.f;
+            lo[c] = fminf(lo[c], v);
+            hi[c] = fmaxf(hi[c], v);
+        }
+        if (nrm && i < na)
+            for (int c = 0; c < 3; ++c)
+                if (!isfinite(nrm[3 * i + c])) bad += 1.f;
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    __shared__ float sh[kBBoxThreads / 32][7];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        for (int c = 0; c < 3; ++c) {
+            sh[warp][c] = lo[c];
+            sh[warp][3 + c] = hi[c];
+        }
+        sh[warp][6] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r[7];
+        for (int c = 0; c < 7; ++c) r[c] = sh[0][c];
+        for (int w = 1; w < kBBoxThreads / 32; ++w) {
+            for (int c = 0; c < 3; ++c) {
+                r[c] = fminf(r[c], sh[w][c]);
+                r[3 + c] = fmaxf(r[3 + c], sh[w][3 + c]);
+            }
+            r[6] += sh[w][6];
+        }
+        for (int c = 0; c < 7; ++c) part[7 * blockIdx.x + c] = r[c];
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Morton keys
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffu;  // 21 bits
+    x = (x | x << 32) & 0x1f00000000ffffULL;
+    x = (x | x << 16) & 0x1f0000ff0000ffULL;
+    x = (x | x << 8) & 0x100f00f00f00f00fULL;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+    x = (x | x << 2) & 0x1249249249249249ULL;
+    return x;
+}
+
+// x in the most significant position of each 3-bit digit: octant = 4 bx + 2 by + bz.
+__device__ __forceinline__ uint64_t morton3(uint32_t ix, uint32_t iy, uint32_t iz)
+{
+    return (spread3(ix) << 2) | (spread3(iy) << 1) | spread3(iz);
+}
+
+struct RootCube {
+    double lo[3];
+    double inv_w;
+    int L;
+};
+
+__global__ void keys_kernel(const float *__restrict__ xyz, int64_t n, RootCube rc,
+                            uint64_t *__restrict__ key, int *__restrict__ idx)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const double scale = (double)(1u << rc.L);
+    const int top = (1 << rc.L) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int q[3];
+        for (int c = 0; c < 3; ++c) {
+            double t = ((double)xyz[3 * i + c] - rc.lo[c]) * rc.inv_w * scale;
+            int v = (int)floor(t);
+            q[c] = v < 0 ? 0 : (v > top ? top : v);
+        }
+        key[i] = morton3(q[0], q[1], q[2]);
+        idx[i] = (int)i;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// LSD radix sort of (uint64 key, int value), 8-bit digits, stable
+// ------------------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+__global__ void radix_hist_kernel(const uint64_t *__restrict__ key, int n, int shift,
+                                  int *__restrict__ hist, int ntiles)
+{
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kSortTile;
+    for (int k = 0; k < kSortItems; ++k) {
+        int i = base + k * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(key[i] >> shift) & 0xff], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void radix_scatter_kernel(const uint64_t *__restrict__ kin, const int *__restrict__ vin,
+                                     uint64_t *__restrict__ kout, int *__restrict__ vout, int n,
+                                     int shift, const int *__restrict__ off, int ntiles)
+{
+    __shared__ int run[256];
+    __shared__ int wcnt[kSortThreads / 32][256];
+    __shared__ int tot[256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    run[tid] = off[tid * ntiles + blockIdx.x];
+    const unsigned lt = (1u << lane) - 1u;
+    const int base = blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortItems; ++r) {
+        for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][tid] = 0;
+        const int i = base + r * kSortThreads + tid;
+        const bool valid = i < n;
+        uint64_t k = valid ? kin[i] : 0;
+        int v = valid ? vin[i] : 0;
+        int d = valid ? (int)((k >> shift) & 0xff) : 256;
+        __syncthreads();
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & lt);
+        int leader = __ffs(peers) - 1;
+        if (valid && lane == leader) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            int s = 0;
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                int c = wcnt[w][tid];
+                wcnt[w][tid] = s;
+                s += c;
+            }
+            tot[tid] = s;
+        }
+        __syncthreads();
+        if (valid) {
+            int pos = run[d] + wcnt[warp][d] + rank;
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+        run[tid] += tot[tid];
+        __syncthreads();
+    }
+}
+
+kfmm_status radix_sort(kfmm_ctx *ctx, DevBuf &key, DevBuf &val, int n, int bits)
+{
+    if (n <= 1) return KFMM_OK;
+    const int ntiles = (n + kSortTile - 1) / kSortTile;
+    DevBuf k2, v2, hist;
+    KF_CUDA(k2.ensure(sizeof(uint64_t) * n));
+    KF_CUDA(v2.ensure(sizeof(int) * n));
+    KF_CUDA(hist.ensure(sizeof(int) * 256 * (size_t)ntiles));
+    uint64_t *ka = key.as<uint64_t>(), *kb = k2.as<uint64_t>();
+    int *va = val.as<int>(), *vb = v2.as<int>();
+    const int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        radix_hist_kernel<<<ntiles, kSortThreads, 0, ctx->stream>>>(ka, n, 8 * p, hist.as<int>(), ntiles);
+        KF_LAUNCH();
+        KF_TRY(scan_exclusive(ctx, hist.as<int>(), hist.as<int>(), 256 * ntiles, nullptr));
+        radix_scatter_kernel<<<ntiles, kSortThreads, 0, ctx->stream>>>(ka, va, kb, vb, n, 8 * p,
+                                                                        hist.as<int>(), ntiles);
+        KF_LAUNCH();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != key.as<uint64_t>()) {
+        KF_CUDA(cudaMemcpyAsync(key.p, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        KF_CUDA(cudaMemcpyAsync(val.p, va, sizeof(int) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    KF_CUDA(cudaStreamSynchronize(ctx->stream));  // temporaries are freed on return
+    return KFMM_OK;
+}
+
+__global__ void gather_points_kernel(const float *__restrict__ xyz, const int *__restrict__ perm,
+                                     int64_t n, float4 *__restrict__ out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int j = perm[i];
+        out[i] = make_float4(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], 0.f);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// level-by-level split
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ int lower_bound_u64(const uint64_t *a, int lo, int hi, uint64_t v)
+{
+    while (lo < hi) {
+        int m = (lo + hi) >> 1;
+        if (a[m] < v) lo = m + 1;
+        else hi = m;
+    }
+    return lo;
+}
+
+// For each box of the level: decide the split, find the 8 child ranges, count non-empty.
+__global__ void split_count_kernel(int first, int nb, int level, int L, int cap,
+                                   const uint64_t *__restrict__ bkey, const int2 *__restrict__ bsrc,
+                                   const int2 *__restrict__ btrg, const uint64_t *__restrict__ skey,
+                                   const uint64_t *__restrict__ tkey, int4 *__restrict__ crange,
+                                   int *__restrict__ ccount)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    const int b = first + i;
+    const int2 s = bsrc[b], t = btrg[b];
+    const int ns = s.y - s.x, nt = t.y - t.x;
+    int cnt = 0;
+    if ((ns > cap || nt > cap) && level < L) {
+        const int sh = 3 * (L - level - 1);
+        const uint64_t base = bkey[b] << 3;
+        int sb[9], tb[9];
+        sb[0] = s.x;
+        tb[0] = t.x;
+        sb[8] = s.y;
+        tb[8] = t.y;
+        for (int o = 1; o < 8; ++o) {
+            uint64_t lo = (base | (uint64_t)o) << sh;
+            sb[o] = lower_bound_u64(skey, sb[o - 1], s.y, lo);
+            tb[o] = lower_bound_u64(tkey, tb[o - 1], t.y, lo);
+        }
+        for (int o = 0; o < 8; ++o) {
+            crange[8 * i + o] = make_int4(sb[o], sb[o + 1], tb[o], tb[o + 1]);
+            if (sb[o + 1] > sb[o] || tb[o + 1] > tb[o]) ++cnt;
+        }
+    }
+    ccount[i] = cnt;
+}
+
+__global__ void split_emit_kernel(int first, int nb, int next_first, const int4 *__restrict__ crange,
+                                  const int *__restrict__ ccount, const int *__restrict__ coff,
+                                  uint64_t *__restrict__ bkey, int4 *__restrict__ banchor,
+                                  int *__restrict__ bparent, int *__restrict__ bchild,
+                                  int2 *__restrict__ bsrc, int2 *__restrict__ btrg)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    const int b = first + i;
+    for (int o = 0; o < 8; ++o) bchild[8 * b + o] = -1;
+    if (ccount[i] == 0) return;
+    int k = next_first + coff[i];
+    const int4 a = banchor[b];
+    for (int o = 0; o < 8; ++o) {
+        int4 r = crange[8 * i + o];
+        if (r.y > r.x || r.w > r.z) {
+            bkey[k] = (bkey[b] << 3) | (uint64_t)o;
+            banchor[k] = make_int4(2 * a.x + ((o >> 2) & 1), 2 * a.y + ((o >> 1) & 1), 2 * a.z + (o & 1),
+                                   a.w + 1);
+            bparent[k] = b;
+            bsrc[k] = make_int2(r.x, r.y);
+            btrg[k] = make_int2(r.z, r.w);
+            bchild[8 * b + o] = k;
+            ++k;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// colleagues and lists
+// ------------------------------------------------------------------------------------
+struct TreeView {
+    int L;
+    int n_boxes;
+    const uint64_t *key;
+    const int4 *anchor;
+    const int *parent;
+    const int *child;
+    const int *leaf;
+    const int *colleague;
+    const int *level_off;  // device copy, n_levels + 1
+    int n_levels;
+};
+
+__device__ __forceinline__ int find_box(const TreeView &tv, int level, int ix, int iy, int iz)
+{
+    const int side = 1 << level;
+    if (ix < 0 || iy < 0 || iz < 0 || ix >= side || iy >= side || iz >= side) return -1;
+    if (level >= tv.n_levels) return -1;
+    const uint64_t k = morton3(ix, iy, iz);
+    int lo = tv.level_off[level], hi = tv.level_off[level + 1];
+    while (lo < hi) {
+        int m = (lo + hi) >> 1;
+        if (tv.key[m] < k) lo = m + 1;
+        else hi = m;
+    }
+    if (lo < tv.level_off[level + 1] && tv.key[lo] == k) return lo;
+    return -1;
+}
+
+__global__ void colleague_kernel(TreeView tv, int *__restrict__ coll)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= tv.n_boxes) return;
+    const int4 a = tv.anchor[b];
+    int c = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz, ++c)
+                coll[27 * b + c] = (c == 13) ? b : find_box(tv, a.w, a.x + dx, a.y + dy, a.z + dz);
+}
+
+// Closed boxes at possibly different levels touch or overlap.
+__device__ __forceinline__ bool adjacent(const int4 &a, const int4 &b, int L)
+{
+    const int sa = L - a.w, sb = L - b.w;
+    const int ax0 = a.x << sa, ay0 = a.y << sa, az0 = a.z << sa, la = 1 << sa;
+    const int bx0 = b.x << sb, by0 = b.y << sb, bz0 = b.z << sb, lb = 1 << sb;
+    return ax0 <= bx0 + lb && bx0 <= ax0 + la && ay0 <= by0 + lb && by0 <= ay0 + la &&
+           az0 <= bz0 + lb && bz0 <= az0 + la;
+}
+
+// One thread per box.  mode 0: count into cnt[4][n_boxes] (U, V, W, X); mode 1: fill.
+__global__ void lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict__ uo,
+                             int *__restrict__ ui, const int *__restrict__ vo, int *__restrict__ vi,
+                             const int *__restrict__ wo, int *__restrict__ wi, const int *__restrict__ xo,
+                             int *__restrict__ xi, int *__restrict__ overflow)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= tv.n_boxes) return;
+    const int L = tv.L;
+    const int4 ab = tv.anchor[b];
+    const int level = ab.w;
+    const bool is_leaf = tv.leaf[b] != 0;
+    const int par = tv.parent[b];
+    int nu = 0, nv = 0, nw = 0, nx = 0;
+    int pu = mode ? uo[b] : 0, pv = mode ? vo[b] : 0, pw = mode ? wo[b] : 0, px = mode ? xo[b] : 0;
+
+    // V: children of the parent's colleagues that are not adjacent to b
+    if (level >= 2) {
+        for (int c = 0; c < 27; ++c) {
+            int C = tv.colleague[27 * par + c];
+            if (C < 0 || tv.leaf[C]) continue;
+            for (int o = 0; o < 8; ++o) {
+                int D = tv.child[8 * C + o];
+                if (D < 0) continue;
+                if (!adjacent(tv.anchor[D], ab, L)) {
+                    if (mode) vi[pv + nv] = D;
+                    ++nv;
+                }
+            }
+        }
+    }
+    // X: coarser leaves adjacent to the parent but not to b (b lies in their W list)
+    if (level >= 1) {
+        const int4 ap = tv.anchor[par];
+        for (int A = par; A >= 0; A = tv.parent[A]) {
+            for (int c = 0; c < 27; ++c) {
+                int C = tv.colleague[27 * A + c];
+                if (C < 0 || C == A || !tv.leaf[C]) continue;
+                const int4 ac = tv.anchor[C];
+                if (adjacent(ac, ap, L) && !adjacent(ac, ab, L)) {
+                    if (mode) xi[px + nx] = C;
+                    ++nx;
+                }
+            }
+        }
+    }
+    if (is_leaf) {
+        // U (i): leaves at this or coarser levels adjacent to b
+        for (int A = b; A >= 0; A = tv.parent[A]) {
+            for (int c = 0; c < 27; ++c) {
+                int C = tv.colleague[27 * A + c];
+                if (C < 0 || !tv.leaf[C]) continue;
+                if (A != b && C == A) continue;
+                if (A == b || adjacent(tv.anchor[C], ab, L)) {
+                    if (mode) ui[pu + nu] = C;
+                    ++nu;
+                }
+            }
+        }
+        // U (ii) and W: descendants of non-leaf colleagues
+        int stack[192];
+        for (int c = 0; c < 27; ++c) {
+            if (c == 13) continue;
+            int C = tv.colleague[27 * b + c];
+            if (C < 0 || tv.leaf[C]) continue;
+            int sp = 0;
+            for (int o = 0; o < 8; ++o) {
+                int D = tv.child[8 * C + o];
+                if (D >= 0) stack[sp++] = D;
+            }
+            while (sp > 0) {
+                int D = stack[--sp];
+                const int4 ad = tv.anchor[D];
+                if (adjacent(ad, ab, L)) {
+                    if (tv.leaf[D]) {
+                        if (mode) ui[pu + nu] = D;
+                        ++nu;
+                    } else {
+                        for (int o = 0; o < 8; ++o) {
+                            int E = tv.child[8 * D + o];
+                            if (E < 0) continue;
+                            if (sp < 192) stack[sp++] = E;
+                            else atomicExch(overflow, 1);
+                        }
+                    }
+                } else {
+                    if (mode) wi[pw + nw] = D;
+                    ++nw;
+                }
+            }
+        }
+    }
+    if (!mode) {
+        cnt[b] = nu;
+        cnt[tv.n_boxes + b] = nv;
+        cnt[2 * tv.n_boxes + b] = nw;
+        cnt[3 * tv.n_boxes + b] = nx;
+    }
+}
+
+__global__ void leaf_flag_kernel(int n, const int *__restrict__ child, int *__restrict__ leaf)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    int l = 1;
+    for (int o = 0; o < 8; ++o)
+        if (child[8 * b + o] >= 0) l = 0;
+    leaf[b] = l;
+}
+
+// compact indices b with flag[b] != 0 using a scanned copy
+__global__ void compact_kernel(int n, const int *__restrict__ flag, const int *__restrict__ pos,
+                               int *__restrict__ out)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n && flag[b]) out[pos[b]] = b;
+}
+
+__global__ void nonzero_kernel(int n, const int *__restrict__ cnt, int *__restrict__ flag)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n) flag[b] = cnt[b] > 0;
+}
+
+// V pairs grouped by direction (dx, dy, dz) in [-3,3]^3 minus [-1,1]^3: 316 groups.
+__device__ __forceinline__ int dir_index(int dx, int dy, int dz)
+{
+    // index into 7^3 then compress by removing the 27 inner ones
+    int full = ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3);
+    // count inner cells with smaller full index
+    int inner_before = 0;
+    // inner cells have components in -1..1 -> indices 2..4 in each axis
+    int ix = dx + 3, iy = dy + 3, iz = dz + 3;
+    // number of inner cells (a,b,c) with ((a*7+b)*7+c) < full
+    for (int a = 2; a <= 4; ++a)
+        for (int bb = 2; bb <= 4; ++bb)
+            for (int c = 2; c <= 4; ++c)
+                if (((a * 7 + bb) * 7 + c) < full) ++inner_before;
+    (void)ix;
+    (void)iy;
+    (void)iz;
+    return full - inner_before;
+}
+
+__global__ void vdir_count_kernel(int n_boxes, const int *__restrict__ vo, const int *__restrict__ vi,
+                                  const int4 *__restrict__ anchor, int *__restrict__ dcount,
+                                  int *__restrict__ pair_dir)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_boxes) return;
+    const int4 ab = anchor[b];
+    for (int k = vo[b]; k < vo[b + 1]; ++k) {
+        const int4 as = anchor[vi[k]];
+        int d = dir_index(as.x - ab.x, as.y - ab.y, as.z - ab.z);
+        pair_dir[k] = d;
+        atomicAdd(&dcount[d], 1);
+    }
+}
+
+__global__ void vdir_scatter_kernel(int n_boxes, const int *__restrict__ vo, const int *__restrict__ vi,
+                                    const int *__restrict__ pair_dir, int *__restrict__ cursor,
+                                    int *__restrict__ psrc, int *__restrict__ ptrg)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_boxes) return;
+    for (int k = vo[b]; k < vo[b + 1]; ++k) {
+        int pos = atomicAdd(&cursor[pair_dir[k]], 1);
+        psrc[pos] = vi[k];
+        ptrg[pos] = b;
+    }
+}
+
+__global__ void oct_count_kernel(int n_boxes, const int4 *__restrict__ anchor, int *__restrict__ cnt)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_boxes || b == 0) return;
+    const int4 a = anchor[b];
+    const int o = ((a.x & 1) << 2) | ((a.y & 1) << 1) | (a.z & 1);
+    atomicAdd(&cnt[8 * a.w + o], 1);
+}
+
+__global__ void oct_scatter_kernel(int n_boxes, const int4 *__restrict__ anchor, int *__restrict__ cursor,
+                                   int *__restrict__ out)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_boxes || b == 0) return;
+    const int4 a = anchor[b];
+    const int o = ((a.x & 1) << 2) | ((a.y & 1) << 1) | (a.z & 1);
+    out[atomicAdd(&cursor[8 * a.w + o], 1)] = b;
+}
+
+// Work counts for roofline accounting (one thread per box).
+__global__ void work_count_kernel(int n_boxes, const int *__restrict__ leaf, const int2 *__restrict__ bsrc,
+                                  const int2 *__restrict__ btrg, const int *__restrict__ uo,
+                                  const int *__restrict__ ui, const int *__restrict__ wo,
+                                  const int *__restrict__ xo, const int *__restrict__ xi,
+                                  unsigned long long *__restrict__ acc)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_boxes) return;
+    unsigned long long p2p = 0, l2p = 0, p2l = 0;
+    if (leaf[b]) {
+        const int nt = btrg[b].y - btrg[b].x;
+        long long ns = 0;
+        for (int k = uo[b]; k < uo[b + 1]; ++k) ns += bsrc[ui[k]].y - bsrc[ui[k]].x;
+        p2p = (unsigned long long)nt * ns;
+        l2p = (unsigned long long)nt * (1 + (wo[b + 1] - wo[b]));
+    }
+    for (int k = xo[b]; k < xo[b + 1]; ++k) p2l += bsrc[xi[k]].y - bsrc[xi[k]].x;
+    if (p2p) atomicAdd(&acc[0], p2p);
+    if (l2p) atomicAdd(&acc[1], l2p);
+    if (p2l) atomicAdd(&acc[2], p2l);
+}
+
+template <class T> kfmm_status grow_keep(kfmm_ctx *ctx, DevBuf &buf, size_t used, size_t need)
+{
+    if (need <= buf.bytes) return KFMM_OK;
+    DevBuf nb;
+    size_t cap = std::max(need, buf.bytes * 2);
+    KF_CUDA(nb.ensure(cap));
+    if (used) KF_CUDA(cudaMemcpyAsync(nb.p, buf.p, used, cudaMemcpyDeviceToDevice, ctx->stream));
+    KF_CUDA(cudaStreamSynchronize(ctx->stream));
+    std::swap(nb.p, buf.p);
+    std::swap(nb.bytes, buf.bytes);
+    return KFMM_OK;
+}
+
+}  // namespace
+
+kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm, int64_t nsrc,
+                       const float *trg_xyz, int64_t ntrg)
+{
+    Tree &T = ctx->tree;
+    T.built = false;
+    const cudaStream_t st = ctx->stream;
+    const int L = ctx->opt.max_depth;
+    const int cap = ctx->opt.leaf_cap;
+    if (nsrc + ntrg > (int64_t)1 << 30) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many points (limit 2^30)");
+
+    // ---- bounding cube and NaN check
+    DevBuf part;
+    KF_CUDA(part.ensure(sizeof(float) * 7 * kBBoxBlocks));
+    bbox_kernel<<<kBBoxBlocks, kBBoxThreads, 0, st>>>(src_xyz, nsrc, trg_xyz, ntrg, src_nrm,
+                                                      part.as<float>());
+    KF_LAUNCH();
+    std::vector<float> hp(7 * kBBoxBlocks);
+    KF_CUDA(cudaMemcpyAsync(hp.data(), part.p, sizeof(float) * hp.size(), cudaMemcpyDeviceToHost, st));
+    KF_CUDA(cudaStreamSynchronize(st));
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double bad = 0;
+    for (int b = 0; b < kBBoxBlocks; ++b) {
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = std::min(lo[c], (double)hp[7 * b + c]);
+            hi[c] = std::max(hi[c], (double)hp[7 * b + 3 + c]);
+        }
+        bad += hp[7 * b + 6];
+    }
+    if (bad > 0) return ctx->fail(KFMM_ERR_INVALID_ARG, "non-finite coordinate or normal");
+    double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    double w = ext > 0 ? ext * (1.0 + 1e-6) : 1.0;
+    for (int c = 0; c < 3; ++c) T.root_lo[c] = 0.5 * (lo[c] + hi[c]) - 0.5 * w;
+    T.root_w = w;
+    T.max_depth = L;
+    T.nsrc = nsrc;
+    T.ntrg = ntrg;
+    T.has_nrm = src_nrm != nullptr;
+
+    // ---- keys and sort
+    RootCube rc{{T.root_lo[0], T.root_lo[1], T.root_lo[2]}, 1.0 / w, L};
+    KF_CUDA(T.src_key.ensure(sizeof(uint64_t) * nsrc));
+    KF_CUDA(T.trg_key.ensure(sizeof(uint64_t) * ntrg));
+    KF_CUDA(T.src_perm.ensure(sizeof(int) * nsrc));
+    KF_CUDA(T.trg_perm.ensure(sizeof(int) * ntrg));
+    keys_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_xyz, nsrc, rc, T.src_key.as<uint64_t>(),
+                                                      T.src_perm.as<int>());
+    KF_LAUNCH();
+    keys_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, ntrg, rc, T.trg_key.as<uint64_t>(),
+                                                      T.trg_perm.as<int>());
+    KF_LAUNCH();
+    KF_TRY(radix_sort(ctx, T.src_key, T.src_perm, (int)nsrc, 3 * L));
+    KF_TRY(radix_sort(ctx, T.trg_key, T.trg_perm, (int)ntrg, 3 * L));
+    KF_CUDA(T.src_xyz.ensure(sizeof(float4) * nsrc));
+    KF_CUDA(T.trg_xyz.ensure(sizeof(float4) * ntrg));
+    gather_points_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_xyz, T.src_perm.as<int>(), nsrc,
+                                                               T.src_xyz.as<float4>());
+    KF_LAUNCH();
+    gather_points_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, T.trg_perm.as<int>(), ntrg,
+                                                               T.trg_xyz.as<float4>());
+    KF_LAUNCH();
+    if (src_nrm) {
+        KF_CUDA(T.src_nrm.ensure(sizeof(float4) * nsrc));
+        gather_points_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_nrm, T.src_perm.as<int>(), nsrc,
+                                                                   T.src_nrm.as<float4>());
+        KF_LAUNCH();
+    }
+
+    // ---- boxes, level by level
+    size_t capb = std::max<size_t>(1024, (size_t)(4 * (nsrc + ntrg) / std::max(1, cap)) + 64);
+    KF_CUDA(T.box_key.ensure(sizeof(uint64_t) * capb));
+    KF_CUDA(T.box_anchor.ensure(sizeof(int4) * capb));
+    KF_CUDA(T.box_parent.ensure(sizeof(int) * capb));
+    KF_CUDA(T.box_child.ensure(sizeof(int) * 8 * capb));
+    KF_CUDA(T.box_src.ensure(sizeof(int2) * capb));
+    KF_CUDA(T.box_trg.ensure(sizeof(int2) * capb));
+    {
+        uint64_t k0 = 0;
+        int4 a0 = make_int4(0, 0, 0, 0);
+        int p0 = -1;
+        int2 s0 = make_int2(0, (int)nsrc), t0 = make_int2(0, (int)ntrg);
+        KF_CUDA(cudaMemcpyAsync(T.box_key.p, &k0, sizeof(k0), cudaMemcpyHostToDevice, st));
+        KF_CUDA(cudaMemcpyAsync(T.box_anchor.p, &a0, sizeof(a0), cudaMemcpyHostToDevice, st));
+        KF_CUDA(cudaMemcpyAsync(T.box_parent.p, &p0, sizeof(p0), cudaMemcpyHostToDevice, st));
+        KF_CUDA(cudaMemcpyAsync(T.box_src.p, &s0, sizeof(s0), cudaMemcpyHostToDevice, st));
+        KF_CUDA(cudaMemcpyAsync(T.box_trg.p, &t0, sizeof(t0), cudaMemcpyHostToDevice, st));
+        KF_CUDA(cudaStreamSynchronize(st));
+    }
+    T.level_off.assign(1, 0);
+    T.level_off.push_back(1);
+    int n_boxes = 1;
+    DevBuf crange, ccount, coff, total;
+    KF_CUDA(total.ensure(sizeof(int)));
+    for (int level = 0;; ++level) {
+        const int first = T.level_off[level], nb = T.level_off[level + 1] - first;
+        KF_CUDA(crange.ensure(sizeof(int4) * 8 * (size_t)nb));
+        KF_CUDA(ccount.ensure(sizeof(int) * (size_t)nb));
+        KF_CUDA(coff.ensure(sizeof(int) * (size_t)nb));
+        split_count_kernel<<<grid_for(nb, 128, 1 << 30), 128, 0, st>>>(
+            first, nb, level, L, cap, T.box_key.as<uint64_t>(), T.box_src.as<int2>(), T.box_trg.as<int2>(),
+            T.src_key.as<uint64_t>(), T.trg_key.as<uint64_t>(), crange.as<int4>(), ccount.as<int>());
+        KF_LAUNCH();
+        KF_TRY(scan_exclusive(ctx, ccount.as<int>(), coff.as<int>(), nb, total.as<int>()));
+        int nchild = 0;
+        KF_TRY(read_int(ctx, total.as<int>(), &nchild));
+        const size_t need = (size_t)n_boxes + nchild;
+        if (need > capb) {
+            size_t nc = std::max(need, 2 * capb);
+            KF_TRY(grow_keep<uint64_t>(ctx, T.box_key, sizeof(uint64_t) * n_boxes, sizeof(uint64_t) * nc));
+            KF_TRY(grow_keep<int4>(ctx, T.box_anchor, sizeof(int4) * n_boxes, sizeof(int4) * nc));
+            KF_TRY(grow_keep<int>(ctx, T.box_parent, sizeof(int) * n_boxes, sizeof(int) * nc));
+            KF_TRY(grow_keep<int>(ctx, T.box_child, sizeof(int) * 8 * n_boxes, sizeof(int) * 8 * nc));
+            KF_TRY(grow_keep<int2>(ctx, T.box_src, sizeof(int2) * n_boxes, sizeof(int2) * nc));
+            KF_TRY(grow_keep<int2>(ctx, T.box_trg, sizeof(int2) * n_boxes, sizeof(int2) * nc));
+            capb = nc;
+        }
+        split_emit_kernel<<<grid_for(nb, 128, 1 << 30), 128, 0, st>>>(
+            first, nb, n_boxes, crange.as<int4>(), ccount.as<int>(), coff.as<int>(), T.box_key.as<uint64_t>(),
+            T.box_anchor.as<int4>(), T.box_parent.as<int>(), T.box_child.as<int>(), T.box_src.as<int2>(),
+            T.box_trg.as<int2>());
+        KF_LAUNCH();
+        if (nchild == 0) break;
+        n_boxes += nchild;
+        T.level_off.push_back(n_boxes);
+    }
+    T.n_boxes = n_boxes;
+    T.n_levels = (int)T.level_off.size() - 1;
+    // children of the deepest level were initialised to -1 by split_emit (nchild == 0 pass)
+
+    // ---- leaves
+    KF_CUDA(T.box_leaf.ensure(sizeof(int) * n_boxes));
+    leaf_flag_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_child.as<int>(),
+                                                                       T.box_leaf.as<int>());
+    KF_LAUNCH();
+    DevBuf pos;
+    KF_CUDA(pos.ensure(sizeof(int) * n_boxes));
+    KF_TRY(scan_exclusive(ctx, T.box_leaf.as<int>(), pos.as<int>(), n_boxes, total.as<int>()));
+    KF_TRY(read_int(ctx, total.as<int>(), &T.n_leaves));
+    KF_CUDA(T.leaves.ensure(sizeof(int) * T.n_leaves));
+    compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_leaf.as<int>(), pos.as<int>(),
+                                                                     T.leaves.as<int>());
+    KF_LAUNCH();
+
+    // ---- colleagues
+    DevBuf loff;
+    KF_CUDA(loff.ensure(sizeof(int) * T.level_off.size()));
+    KF_CUDA(cudaMemcpyAsync(loff.p, T.level_off.data(), sizeof(int) * T.level_off.size(),
+                            cudaMemcpyHostToDevice, st));
+    KF_CUDA(T.colleague.ensure(sizeof(int) * 27 * n_boxes));
+    TreeView tv{L,
+                n_boxes,
+                T.box_key.as<uint64_t>(),
+                T.box_anchor.as<int4>(),
+                T.box_parent.as<int>(),
+                T.box_child.as<int>(),
+                T.box_leaf.as<int>(),
+                T.colleague.as<int>(),
+                loff.as<int>(),
+                T.n_levels};
+    colleague_kernel<<<grid_for(n_boxes, 128, 1 << 30), 128, 0, st>>>(tv, T.colleague.as<int>());
+    KF_LAUNCH();
+
+    // ---- lists: count, scan, fill
+    DevBuf cnt, ovf;
+    KF_CUDA(cnt.ensure(sizeof(int) * 4 * (size_t)n_boxes));
+    KF_CUDA(ovf.ensure(sizeof(int)));
+    KF_CUDA(cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
+    lists_kernel<<<grid_for(n_boxes, 64, 1 << 30), 64, 0, st>>>(tv, 0, cnt.as<int>(), nullptr, nullptr, nullptr,
+                                                                 nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                 ovf.as<int>());
+    KF_LAUNCH();
+    DevBuf *offs[4] = {&T.u_off, &T.v_off, &T.w_off, &T.x_off};
+    DevBuf *idxs[4] = {&T.u_idx, &T.v_idx, &T.w_idx, &T.x_idx};
+    int64_t tot[4];
+    for (int l = 0; l < 4; ++l) {
+        KF_CUDA(offs[l]->ensure(sizeof(int) * (n_boxes + 1)));
+        KF_TRY(scan_exclusive(ctx, cnt.as<int>() + (size_t)l * n_boxes, offs[l]->as<int>(), n_boxes,
+                              offs[l]->as<int>() + n_boxes));
+        int t = 0;
+        KF_TRY(read_int(ctx, offs[l]->as<int>() + n_boxes, &t));
+        tot[l] = t;
+        KF_CUDA(idxs[l]->ensure(sizeof(int) * std::max<int64_t>(1, t)));
+    }
+    lists_kernel<<<grid_for(n_boxes, 64, 1 << 30), 64, 0, st>>>(
+        tv, 1, nullptr, T.u_off.as<int>(), T.u_idx.as<int>(), T.v_off.as<int>(), T.v_idx.as<int>(),
+        T.w_off.as<int>(), T.w_idx.as<int>(), T.x_off.as<int>(), T.x_idx.as<int>(), ovf.as<int>());
+    KF_LAUNCH();
+    int overflow = 0;
+    KF_TRY(read_int(ctx, ovf.as<int>(), &overflow));
+    if (overflow) return ctx->fail(KFMM_ERR_INTERNAL, "interaction-list traversal stack overflow");
+    T.n_u = tot[0];
+    T.n_v = tot[1];
+    T.n_w = tot[2];
+    T.n_x = tot[3];
+
+    // ---- V pairs grouped by direction
+    {
+        DevBuf dcount, pair_dir;
+        KF_CUDA(dcount.ensure(sizeof(int) * 317));
+        KF_CUDA(pair_dir.ensure(sizeof(int) * std::max<int64_t>(1, T.n_v)));
+        KF_CUDA(cudaMemsetAsync(dcount.p, 0, sizeof(int) * 317, st));
+        vdir_count_kernel<<<grid_for(n_boxes, 128, 1 << 30), 128, 0, st>>>(
+            n_boxes, T.v_off.as<int>(), T.v_idx.as<int>(), T.box_anchor.as<int4>(), dcount.as<int>(),
+            pair_dir.as<int>());
+        KF_LAUNCH();
+        std::vector<int> hc(316);
+        KF_CUDA(cudaMemcpyAsync(hc.data(), dcount.p, sizeof(int) * 316, cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaStreamSynchronize(st));
+        T.vdir_off.assign(317, 0);
+        for (int d = 0; d < 316; ++d) T.vdir_off[d + 1] = T.vdir_off[d] + hc[d];
+        KF_CUDA(cudaMemcpyAsync(dcount.p, T.vdir_off.data(), sizeof(int) * 316, cudaMemcpyHostToDevice, st));
+        KF_CUDA(T.vp_src.ensure(sizeof(int) * std::max<int64_t>(1, T.n_v)));
+        KF_CUDA(T.vp_trg.ensure(sizeof(int) * std::max<int64_t>(1, T.n_v)));
+        vdir_scatter_kernel<<<grid_for(n_boxes, 128, 1 << 30), 128, 0, st>>>(
+            n_boxes, T.v_off.as<int>(), T.v_idx.as<int>(), pair_dir.as<int>(), dcount.as<int>(),
+            T.vp_src.as<int>(), T.vp_trg.as<int>());
+        KF_LAUNCH();
+        KF_CUDA(cudaStreamSynchronize(st));
+    }
+    // ---- octant groups per level (M2M / L2L)
+    {
+        const int ng = 8 * T.n_levels;
+        DevBuf gc;
+        KF_CUDA(gc.ensure(sizeof(int) * (ng + 1)));
+        KF_CUDA(cudaMemsetAsync(gc.p, 0, sizeof(int) * (ng + 1), st));
+        oct_count_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_anchor.as<int4>(),
+                                                                           gc.as<int>());
+        KF_LAUNCH();
+        std::vector<int> hc(ng);
+        KF_CUDA(cudaMemcpyAsync(hc.data(), gc.p, sizeof(int) * ng, cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaStreamSynchronize(st));
+        T.oct_off.assign(ng + 1, 0);
+        for (int g = 0; g < ng; ++g) T.oct_off[g + 1] = T.oct_off[g] + hc[g];
+        KF_CUDA(cudaMemcpyAsync(gc.p, T.oct_off.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, st));
+        KF_CUDA(T.oct_child.ensure(sizeof(int) * std::max(1, n_boxes)));
+        oct_scatter_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_anchor.as<int4>(),
+                                                                             gc.as<int>(), T.oct_child.as<int>());
+        KF_LAUNCH();
+        KF_CUDA(cudaStreamSynchronize(st));
+    }
+    // ---- boxes with X lists
+    {
+        DevBuf flag, xpos;
+        KF_CUDA(flag.ensure(sizeof(int) * n_boxes));
+        KF_CUDA(xpos.ensure(sizeof(int) * n_boxes));
+        nonzero_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, cnt.as<int>() + 3 * (size_t)n_boxes,
+                                                                         flag.as<int>());
+        KF_LAUNCH();
+        KF_TRY(scan_exclusive(ctx, flag.as<int>(), xpos.as<int>(), n_boxes, total.as<int>()));
+        KF_TRY(read_int(ctx, total.as<int>(), &T.n_xboxes));
+        KF_CUDA(T.xboxes.ensure(sizeof(int) * std::max(1, T.n_xboxes)));
+        compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, flag.as<int>(), xpos.as<int>(),
+                                                                         T.xboxes.as<int>());
+        KF_LAUNCH();
+        KF_CUDA(cudaStreamSynchronize(st));
+    }
+    // ---- work counts
+    {
+        DevBuf acc;
+        KF_CUDA(acc.ensure(sizeof(unsigned long long) * 3));
+        KF_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 3, st));
+        work_count_kernel<<<grid_for(n_boxes, 128, 1 << 30), 128, 0, st>>>(
+            n_boxes, T.box_leaf.as<int>(), T.box_src.as<int2>(), T.box_trg.as<int2>(), T.u_off.as<int>(),
+            T.u_idx.as<int>(), T.w_off.as<int>(), T.x_off.as<int>(), T.x_idx.as<int>(),
+            acc.as<unsigned long long>());
+        KF_LAUNCH();
+        unsigned long long h[3];
+        KF_CUDA(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaStreamSynchronize(st));
+        T.p2p_pairs = (int64_t)h[0];
+        T.l2p_pairs = (int64_t)h[1];
+        T.p2l_pairs = (int64_t)h[2];
+    }
+    // level offsets and lists are final; keep the device copy of level_off alive in work
+    KF_CUDA(cudaStreamSynchronize(st));
+    T.built = true;
+    return KFMM_OK;
+}
+
+}  // namespace kfmm

@@ -1,0 +1,238 @@
+"""GPU parity of the C-ABI path against the FP64 oracle: all-pairs direct sums (FP64 and
+FP32), octree invariants and interaction-list coverage, and the KIFMM evaluation of the
+Kelvin sums of Eq. fmm_summation (single layer, double layer, both, and stress).
+
+Tolerances: FP64 direct sum 1e-12 relative L2 (rounding order only); FP32 direct sum 2e-6;
+FMM at p = 6 (152-point surfaces) 1e-4 relative L2, the accuracy BASELINE sets for the
+multipole order; 2e-3 at p = 4.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def K():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_04082_gb300 as K
+    return K
+
+
+def dev(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda:0")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+G1, NU1 = 1.0, 0.3
+G2, NU2 = 2.3, 0.21
+
+
+def make_ctx(K, G=G1, nu=NU1, **kw):
+    f = K.Kfmm(**kw)
+    f.set_material(K.material_K(G, nu), G)
+    return f
+
+
+# ----------------------------------------------------------------- direct sums
+@pytest.mark.parametrize("kind", ["disp", "stress"])
+@pytest.mark.parametrize("layers", ["sl", "dl", "both"])
+def test_direct_fp64_and_fp32(K, kind, layers):
+    rng = np.random.default_rng(3)
+    ns, nt = 1777, 913  # ragged sizes, not multiples of the 256-thread tile
+    src = rng.uniform(-1, 1, (ns, 3))
+    trg = np.vstack([rng.uniform(-1, 1, (nt - 5, 3)), src[:5]])  # includes coincident points
+    nrm = rng.normal(size=(ns, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    sl = rng.normal(size=(ns, 3)) if layers in ("sl", "both") else None
+    dl = rng.normal(size=(ns, 3)) if layers in ("dl", "both") else None
+    no = 3 if kind == "disp" else 6
+    kk = K.KFMM_DISP if kind == "disp" else K.KFMM_STRESS
+    f = O.direct_disp if kind == "disp" else O.direct_stress
+    ref = f(trg, src, nrm, sl, dl, G2, NU2)
+    with make_ctx(K, G2, NU2) as c:
+        for prec, dt, tol in ((K.KFMM_FP64, torch.float64, 1e-12), (K.KFMM_FP32, torch.float32, 2e-6)):
+            out = torch.zeros(nt, no, dtype=dt, device="cuda:0")
+            c.direct(dev(trg, dt), dev(src, dt), dev(nrm, dt), None if sl is None else dev(sl, dt),
+                     None if dl is None else dev(dl, dt), out, kk, prec)
+            assert rel(out.cpu().numpy(), ref) < tol
+        # host arrays are accepted too (staged by the library)
+        out_h = np.zeros((nt, no))
+        c.direct(trg, src, nrm, sl, dl, out_h, kk, K.KFMM_FP64)
+        assert rel(out_h, ref) < 1e-12
+
+
+# ----------------------------------------------------------------- tree and lists
+def check_tree(K, c, src, trg, cap):
+    tr = c.export_tree()
+    st = c.stats()
+    nb = st["n_boxes"]
+    assert np.array_equal(np.sort(tr["src_perm"]), np.arange(len(src)))
+    assert np.array_equal(np.sort(tr["trg_perm"]), np.arange(len(trg)))
+    lvl, anc, par = tr["level"], tr["anchor"], tr["parent"]
+    U_off, U = c.export_list("U")
+    V_off, V = c.export_list("V")
+    W_off, Wl = c.export_list("W")
+    X_off, X = c.export_list("X")
+    children = [[] for _ in range(nb)]
+    for b in range(1, nb):
+        children[par[b]].append(b)
+    leaf = np.array([len(ch) == 0 for ch in children])
+    assert leaf.sum() == st["n_leaves"]
+    # leaves partition the sorted points; non-leaves hold more than cap points
+    for key in ("src", "trg"):
+        rng_ = tr[key][leaf]
+        rng_ = rng_[np.argsort(rng_[:, 0])]
+        lens = rng_[:, 1] - rng_[:, 0]
+        assert lens.sum() == (len(src) if key == "src" else len(trg))
+        nz = rng_[lens > 0]
+        assert np.all(nz[1:, 0] == nz[:-1, 1])
+    for b in np.nonzero(~leaf)[0]:
+        ns_ = tr["src"][b, 1] - tr["src"][b, 0]
+        nt_ = tr["trg"][b, 1] - tr["trg"][b, 0]
+        assert max(ns_, nt_) > cap
+    # points lie inside their leaf box (geometry from the root cube)
+    lo = np.minimum(src.min(0), trg.min(0))
+    hi = np.maximum(src.max(0), trg.max(0))
+    w = (hi - lo).max() * (1 + 1e-6)
+    root_lo = 0.5 * (lo + hi) - 0.5 * w
+    ssorted = src[tr["src_perm"]]
+    for b in np.nonzero(leaf)[0][:200]:
+        s = w / 2 ** lvl[b]
+        blo = root_lo + anc[b] * s
+        p = ssorted[tr["src"][b, 0]:tr["src"][b, 1]]
+        assert np.all(p >= blo - 1e-5 * w) and np.all(p <= blo + s + 1e-5 * w)
+
+    # coverage: every (target leaf, source leaf) pair is counted exactly once
+    desc_leaves = {}
+
+    def leaves_under(b):
+        if b not in desc_leaves:
+            desc_leaves[b] = [b] if leaf[b] else [x for ch in children[b] for x in leaves_under(ch)]
+        return desc_leaves[b]
+
+    leaf_ids = np.nonzero(leaf)[0]
+    pos = {b: i for i, b in enumerate(leaf_ids)}
+    for b in leaf_ids[:: max(1, len(leaf_ids) // 150)]:
+        cnt = np.zeros(len(leaf_ids), np.int32)
+        for s in U[U_off[b]:U_off[b + 1]]:
+            cnt[pos[s]] += 1
+        for w_ in Wl[W_off[b]:W_off[b + 1]]:
+            for s in leaves_under(w_):
+                cnt[pos[s]] += 1
+        a = b
+        while a >= 0:
+            for v in V[V_off[a]:V_off[a + 1]]:
+                for s in leaves_under(v):
+                    cnt[pos[s]] += 1
+            for x in X[X_off[a]:X_off[a + 1]]:
+                cnt[pos[x]] += 1
+            a = par[a] if a > 0 else -1
+        assert np.all(cnt == 1), (b, np.unique(cnt, return_counts=True))
+    return st
+
+
+@pytest.mark.parametrize("cloud", ["surface", "volume", "separate"])
+def test_tree_invariants_and_list_coverage(K, cloud):
+    cap = 32
+    if cloud == "surface":
+        src, nrm = W.box_with_voids_points(30000, n_voids=8)
+        trg = src
+    elif cloud == "volume":
+        src, nrm = W.uniform_cloud(20000)
+        trg = src
+    else:
+        src, nrm = W.box_with_voids_points(20000, n_voids=6)
+        trg, _ = W.uniform_cloud(7001, lo=(0.05, 0.05, 0.05), hi=(1.95, 0.95, 0.95))
+    with make_ctx(K, leaf_cap=cap) as c:
+        c.build(dev(src), dev(nrm), dev(trg))
+        st = check_tree(K, c, src, trg, cap)
+        assert st["n_levels"] >= 3
+
+
+# ----------------------------------------------------------------- FMM parity
+def fmm_case(K, src, nrm, trg, sl, dl, kind, G, nu, p=6, cap=64, nsample=None):
+    no = 3 if kind == K.KFMM_DISP else 6
+    with make_ctx(K, G, nu, p=p, leaf_cap=cap) as c:
+        c.build(dev(src), dev(nrm), dev(trg))
+        out = torch.zeros(len(trg), no, dtype=torch.float32, device="cuda:0")
+        c.eval(None if sl is None else dev(sl), None if dl is None else dev(dl), out, kind)
+        got = out.cpu().numpy()
+        st = c.stats()
+    idx = np.arange(len(trg)) if nsample is None else W.subsample(len(trg), nsample)
+    f = O.direct_disp if kind == K.KFMM_DISP else O.direct_stress
+    ref = f(trg[idx], src, nrm, sl, dl, G, nu)
+    return rel(got[idx], ref), st
+
+
+@pytest.mark.parametrize("layers", ["sl", "dl", "both"])
+def test_fmm_surface_cloud_disp(K, layers):
+    src, nrm = W.box_with_voids_points(40000, n_voids=10)
+    sl, dl = W.densities(len(src))
+    sl = sl if layers in ("sl", "both") else None
+    dl = dl if layers in ("dl", "both") else None
+    err, st = fmm_case(K, src, nrm, src, sl, dl, K.KFMM_DISP, G1, NU1, nsample=3000)
+    assert st["n_v_pairs"] > 0 and st["n_levels"] >= 4
+    assert err < 1e-4, err
+
+
+def test_fmm_volume_cloud_material(K):
+    src, nrm = W.uniform_cloud(30011)
+    sl, dl = W.densities(len(src))
+    err, st = fmm_case(K, src, nrm, src, sl, dl, K.KFMM_DISP, G2, NU2, nsample=3000)
+    assert err < 1e-4, err
+
+
+def test_fmm_separate_targets_stress(K):
+    """Stress at volume targets from surface sources (the topological-derivative layout)."""
+    src, nrm = W.box_with_voids_points(30000, n_voids=6)
+    sl, dl = W.densities(len(src))
+    trg, _ = W.uniform_cloud(5003, lo=(0.1, 0.1, 0.1), hi=(1.9, 0.9, 0.9), seed=9)
+    err, st = fmm_case(K, src, nrm, trg, sl, dl, K.KFMM_STRESS, G2, NU2, nsample=2000)
+    assert err < 1e-4, err
+
+
+def test_fmm_single_leaf_and_tiny(K):
+    """n <= leaf cap: the root is the only box and the sum is all near field."""
+    src, nrm = W.uniform_cloud(50)
+    sl, dl = W.densities(50)
+    err, st = fmm_case(K, src, nrm, src, sl, dl, K.KFMM_DISP, G1, NU1)
+    assert st["n_boxes"] == 1 and err < 2e-6
+    err, st = fmm_case(K, src[:1], nrm[:1], src[:3] + 0.1, sl[:1], dl[:1], K.KFMM_DISP, G1, NU1)
+    assert err < 2e-6
+
+
+def test_fmm_p_convergence(K):
+    src, nrm = W.box_with_voids_points(20000, n_voids=5)
+    sl, dl = W.densities(len(src))
+    errs = [fmm_case(K, src, nrm, src, sl, dl, K.KFMM_DISP, G1, NU1, p=p, nsample=1500)[0] for p in (4, 5, 6)]
+    assert errs[0] < 2e-3 and errs[2] < errs[0] / 3, errs
+
+
+def test_fmm_errors(K):
+    with make_ctx(K) as c:
+        x = dev(np.zeros((4, 3)))
+        out = torch.zeros(4, 3, device="cuda:0")
+        with pytest.raises(K.KfmmError) as e:
+            c.eval(x, None, out)
+        assert e.value.status == K.KFMM_ERR_NOT_BUILT
+        bad = np.zeros((4, 3))
+        bad[2, 1] = np.nan
+        with pytest.raises(K.KfmmError) as e:
+            c.build(dev(bad), None, dev(bad))
+        assert e.value.status == K.KFMM_ERR_INVALID_ARG
+        c.build(x, None, x)
+        with pytest.raises(K.KfmmError) as e:  # double layer without normals
+            c.eval(None, x, out)
+        assert e.value.status == K.KFMM_ERR_INVALID_ARG

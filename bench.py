@@ -59,7 +59,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -97,10 +97,11 @@ class ClockSampler:
 
 
 def workload(n):
+    """Seeded inputs, rounded to FP32 once so the GPU and the FP64 oracle sum the same data."""
     import workloads as W
     pts, nrm = W.box_with_voids_points(n, n_voids=20)
     sl, dl = W.densities(n)
-    return pts, nrm, sl, dl
+    return tuple(np.asarray(a, np.float32).astype(np.float64) for a in (pts, nrm, sl, dl))
 
 
 def cpu_oracle_sample(pts, nrm, sl, dl, k):
@@ -144,7 +145,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_POINTS)

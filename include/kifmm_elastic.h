@@ -72,10 +72,10 @@ typedef struct kfmm_options {
                            in box half-widths (1.05)                                         */
     double r_outer;     /* radius of the outer surfaces (upward check, downward equivalent)
                            (2.95)                                                            */
-    double pinv_rtol;   /* relative singular-value cutoff of the check-to-equivalent
-                           pseudo-inverses, computed in FP64 (1e-7)                          */
-    double m2l_rtol;    /* relative singular-value cutoff of the shared M2L basis (1e-6);
-                           0 keeps the full rank (dense M2L)                                 */
+    double pinv_rtol;   /* relative singular-value cutoff of the check-to-equivalent maps,
+                           factored in FP64 (1e-7)                                           */
+    double m2l_rtol;    /* relative singular-value cutoff of the shared M2L basis (3e-5);
+                           the rank is rounded up to a multiple of 16; 0 keeps full rank    */
     int m2l_rank_max;   /* upper bound on the M2L rank (0 = no bound)                       */
     int device;         /* CUDA device ordinal (0)                                          */
 } kfmm_options;
@@ -175,6 +175,88 @@ kfmm_status kfmm_get_phase_times(kfmm_ctx *ctx, double *ms, int64_t *counts, int
 
 const char *kfmm_status_str(kfmm_status s);
 const char *kfmm_last_error(const kfmm_ctx *ctx);
+
+/* ====================================================================================== */
+/* Collocation BEM on the FMM (Eq. BIE; Eq. num, coef, num2; Sec. "Matrix-vector products") */
+/* ====================================================================================== */
+/* Piecewise-constant u and t on flat triangles, collocation at the centroids.  Off-diagonal
+ * blocks use the 16-point rule (4 midpoint sub-triangles x the 4-node degree-3 rule:
+ * centroid weight -27/48, (3/5,1/5,1/5) weights 25/48); the matvec is the paper's two-pass
+ * scheme: one fast summation over all quadrature sources (weights = element value x area x
+ * rule weight, targets = centroids), then a local pass per element that removes its own
+ * quadrature terms and adds the analytic singular integrals.  Diagonal blocks: int U over
+ * the flat triangle in closed form (polar coordinates about the centroid) and the principal
+ * value of int P, whose only in-plane term is (1-2nu)/(8 pi (1-nu)) (r_,i n_j - r_,j n_i)/r^2.
+ *
+ * The boundary operator is M(u, t) = 1/2 u + P^D u - U^D t at the collocation points (Eq. num);
+ * for mixed conditions (Eq. num2) the unknowns x are, per element and component, t where
+ * the displacement is prescribed and u where the traction is prescribed: A x = M(x_u, x_t),
+ * B y = -M(y_u, y_t).  Arrays of the BEM layer are FP64 [nt][3] unless stated. */
+typedef struct bem_ctx bem_ctx;
+
+typedef enum bem_operator {
+    BEM_FMM = 0,         /* FP32 KIFMM summation (SL + DL) + FP64 local pass               */
+    BEM_DIRECT_FP64 = 1  /* FP64 all-pairs summation on the GPU + FP64 local pass (O(N^2)) */
+} bem_operator;
+
+typedef struct bem_solve_opts {
+    double tol;        /* stop at ||b - A x|| / ||b|| <= tol (1e-6)                           */
+    int restart;       /* GMRES restart length (30; <= 200)                                  */
+    int maxit;         /* cap on inner GMRES iterations in total (1000)                      */
+    const double *x0;  /* initial guess of the unknowns [nt][3], or NULL for zero            */
+} bem_solve_opts;
+
+typedef struct bem_stats {
+    int iters;        /* inner GMRES iterations                                             */
+    int matvecs;      /* operator applications (including residual checks)                  */
+    int converged;    /* 1 if the tolerance was met                                          */
+    double relres;    /* final true relative residual ||b - A x|| / ||b||                    */
+    double seconds;   /* wall time of bem_solve                                              */
+} bem_stats;
+
+void bem_default_solve_opts(bem_solve_opts *o);
+
+/* Triangulated boundary: verts [nv][3] FP64, tris [nt][3] int32 (vertex order gives the
+ * normal by the right-hand rule; it must point out of the material).  `op` is a
+ * bem_operator.  opt as for kfmm_create (NULL = defaults).  Rejects zero-area triangles. */
+kfmm_status bem_create(bem_ctx **out, const kfmm_options *opt, int op, const double *verts, int64_t nv,
+                       const int32_t *tris, int64_t nt);
+kfmm_status bem_destroy(bem_ctx *b);
+kfmm_status bem_set_material(bem_ctx *b, double K, double G);
+kfmm_status bem_set_stream(bem_ctx *b, void *stream);
+
+/* Boundary conditions of Eq. elast: known_is_disp [nt][3] (uint8: 1 = u_i prescribed,
+ * 0 = t_i prescribed), values [nt][3] (the prescribed u or t). */
+kfmm_status bem_set_bc(bem_ctx *b, const uint8_t *known_is_disp, const double *values);
+
+/* out = M(u, t) = 1/2 u + P^D u - U^D t at the centroids (either input may be NULL = 0). */
+kfmm_status bem_apply(bem_ctx *b, const double *u, const double *t, double *out);
+/* y = A x and rhs = B y of Eq. num2 for the boundary conditions set last. */
+kfmm_status bem_matvec(bem_ctx *b, const double *x, double *y);
+kfmm_status bem_rhs(bem_ctx *b, double *rhs);
+
+/* Restarted GMRES (Saad & Schultz) on A x = B y, FP64 vectors and Arnoldi (classical
+ * Gram-Schmidt applied twice) on the device.  On return u, t [nt][3] (either may be NULL)
+ * hold the boundary solution, which is also kept for bem_interior.  Returns
+ * KFMM_ERR_NOT_CONVERGED (with the last iterate stored and returned) at the iteration cap. */
+kfmm_status bem_solve(bem_ctx *b, const bem_solve_opts *o, double *u, double *t, bem_stats *st);
+
+/* Store a boundary solution (u, t [nt][3]) without solving, e.g. from an earlier solve. */
+kfmm_status bem_set_solution(bem_ctx *b, const double *u, const double *t);
+
+/* Interior fields from the stored boundary solution (Sec. "Computing topological
+ * derivatives"): displacement [n][3] by the BIE at interior points and stress [n][6] by
+ * Eq. stress_1 (Somigliana), summed over the same quadrature sources; either output may be
+ * NULL.  pts [n][3] FP32; outputs FP32. */
+kfmm_status bem_interior(bem_ctx *b, const float *pts, int64_t n, float *disp, float *stress);
+
+/* Topological derivative of the compliance (Eq. deriv) and the energy density
+ * 1/2 sigma:eps (integrand of Eq. functional) at interior points [n]; stress [n][6] is
+ * also returned when non-NULL.  FP32. */
+kfmm_status bem_topo_derivative(bem_ctx *b, const float *pts, int64_t n, float *td, float *energy,
+                                float *stress);
+
+const char *bem_last_error(const bem_ctx *b);
 
 #ifdef __cplusplus
 }

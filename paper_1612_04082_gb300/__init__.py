@@ -257,6 +257,170 @@ class Kfmm:
         return kfmm_export_list(self.handle, which)
 
 
+# ------------------------------------------------------------------------------- BEM layer
+BEM_FMM = 0
+BEM_DIRECT_FP64 = 1
+
+
+class bem_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("x0", ctypes.c_void_p)]
+
+
+class bem_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("matvecs", ctypes.c_int), ("converged", ctypes.c_int),
+                ("relres", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+_bsig = {
+    "bem_default_solve_opts": (None, [ctypes.POINTER(bem_solve_opts)]),
+    "bem_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(kfmm_options), ctypes.c_int, _vp, _i64, _vp,
+                                  _i64]),
+    "bem_destroy": (ctypes.c_int, [_vp]),
+    "bem_set_material": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
+    "bem_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "bem_set_bc": (ctypes.c_int, [_vp, _vp, _vp]),
+    "bem_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bem_matvec": (ctypes.c_int, [_vp, _vp, _vp]),
+    "bem_rhs": (ctypes.c_int, [_vp, _vp]),
+    "bem_solve": (ctypes.c_int, [_vp, ctypes.POINTER(bem_solve_opts), _vp, _vp, ctypes.POINTER(bem_stats)]),
+    "bem_set_solution": (ctypes.c_int, [_vp, _vp, _vp]),
+    "bem_interior": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "bem_topo_derivative": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "bem_last_error": (ctypes.c_char_p, [_vp]),
+}
+for _name, (_res, _args) in _bsig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def _bcheck(h, status):
+    if status != KFMM_OK:
+        raise KfmmError(status, _lib.bem_last_error(h).decode() if h else "")
+
+
+def bem_create(verts, tris, op=BEM_FMM, options: kfmm_options | None = None, **overrides):
+    """verts [nv,3] float64, tris [nt,3] int32 (host or device)."""
+    o = options if options is not None else kfmm_default_options()
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    h = _vp()
+    _bcheck(None, _lib.bem_create(ctypes.byref(h), ctypes.byref(o), int(op), _ptr(verts), _nrows(verts), _ptr(tris),
+                                  _nrows(tris)))
+    return h
+
+
+def bem_destroy(h):
+    _bcheck(None, _lib.bem_destroy(h))
+
+
+def bem_set_material(h, K, G):
+    _bcheck(h, _lib.bem_set_material(h, float(K), float(G)))
+
+
+def bem_set_stream(h, stream):
+    _bcheck(h, _lib.bem_set_stream(h, getattr(stream, "cuda_stream", stream)))
+
+
+def bem_set_bc(h, known_is_disp, values):
+    _bcheck(h, _lib.bem_set_bc(h, _ptr(known_is_disp), _ptr(values)))
+
+
+def bem_apply(h, u, t, out):
+    _bcheck(h, _lib.bem_apply(h, _ptr(u), _ptr(t), _ptr(out)))
+    return out
+
+
+def bem_matvec(h, x, y):
+    _bcheck(h, _lib.bem_matvec(h, _ptr(x), _ptr(y)))
+    return y
+
+
+def bem_rhs(h, out):
+    _bcheck(h, _lib.bem_rhs(h, _ptr(out)))
+    return out
+
+
+def bem_solve(h, u=None, t=None, tol=1e-6, restart=30, maxit=1000, x0=None, raise_on_fail=True):
+    """GMRES solve of Eq. num2; fills u, t [nt,3] float64 (host or device). Returns stats dict."""
+    o = bem_solve_opts()
+    _lib.bem_default_solve_opts(ctypes.byref(o))
+    o.tol, o.restart, o.maxit = float(tol), int(restart), int(maxit)
+    o.x0 = _ptr(x0)
+    st = bem_stats()
+    status = _lib.bem_solve(h, ctypes.byref(o), _ptr(u), _ptr(t), ctypes.byref(st))
+    if raise_on_fail or status not in (KFMM_OK, KFMM_ERR_NOT_CONVERGED):
+        _bcheck(h, status)
+    return {f: getattr(st, f) for f, _ in bem_stats._fields_}
+
+
+def bem_set_solution(h, u, t):
+    _bcheck(h, _lib.bem_set_solution(h, _ptr(u), _ptr(t)))
+
+
+def bem_interior(h, pts, disp=None, stress=None):
+    _bcheck(h, _lib.bem_interior(h, _ptr(pts), _nrows(pts), _ptr(disp), _ptr(stress)))
+
+
+def bem_topo_derivative(h, pts, td=None, energy=None, stress=None):
+    _bcheck(h, _lib.bem_topo_derivative(h, _ptr(pts), _nrows(pts), _ptr(td), _ptr(energy), _ptr(stress)))
+
+
+class Bem:
+    """Owner of a BEM context: ``with Bem(verts, tris) as b: b.set_bc(...); b.solve(u, t)``."""
+
+    def __init__(self, verts, tris, op=BEM_FMM, options: kfmm_options | None = None, **overrides):
+        self.handle = bem_create(verts, tris, op, options, **overrides)
+
+    def close(self):
+        if self.handle:
+            bem_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_material(self, K, G):
+        bem_set_material(self.handle, K, G)
+
+    def set_stream(self, stream):
+        bem_set_stream(self.handle, stream)
+
+    def set_bc(self, known_is_disp, values):
+        bem_set_bc(self.handle, known_is_disp, values)
+
+    def apply(self, u, t, out):
+        return bem_apply(self.handle, u, t, out)
+
+    def matvec(self, x, y):
+        return bem_matvec(self.handle, x, y)
+
+    def rhs(self, out):
+        return bem_rhs(self.handle, out)
+
+    def solve(self, u=None, t=None, **kw):
+        return bem_solve(self.handle, u, t, **kw)
+
+    def set_solution(self, u, t):
+        bem_set_solution(self.handle, u, t)
+
+    def interior(self, pts, disp=None, stress=None):
+        bem_interior(self.handle, pts, disp, stress)
+
+    def topo_derivative(self, pts, td=None, energy=None, stress=None):
+        bem_topo_derivative(self.handle, pts, td, energy, stress)
+
+
 def material_K(G: float, nu: float) -> float:
     """Bulk modulus from G and nu (the ABI takes K and G, Eq. elast)."""
     return 2.0 * G * (1.0 + nu) / (3.0 * (1.0 - 2.0 * nu))

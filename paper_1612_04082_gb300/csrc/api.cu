@@ -47,7 +47,7 @@ void kfmm_default_options(kfmm_options *opt)
     opt->r_inner = 1.05;
     opt->r_outer = 2.95;
     opt->pinv_rtol = 1e-7;
-    opt->m2l_rtol = 1e-6;
+    opt->m2l_rtol = 3e-5;
     opt->m2l_rank_max = 0;
     opt->device = 0;
 }

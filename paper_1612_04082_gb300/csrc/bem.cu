@@ -1,0 +1,901 @@
+// bem.cu -- piecewise-constant collocation BEM on the GPU (Eq. BIE, num, coef, num2), the
+// two-pass matvec of Sec. "Matrix-vector products", restarted GMRES with FP64 vectors on
+// the device, and the interior fields of Sec. "Computing topological derivatives"
+// (Eq. stress_1, Eq. deriv, integrand of Eq. functional).
+#include <chrono>
+#include <cmath>
+#include <new>
+
+#include "common.cuh"
+#include "kelvin.cuh"
+#include "util.cuh"
+
+using namespace kfmm;
+
+struct bem_ctx {
+    kfmm_options opt;
+    int op = BEM_FMM;
+    cudaStream_t stream = nullptr;
+    double G = 1.0, nu = 0.3, K = 13.0 / 6.0;
+    std::string err;
+    int64_t n_launch = 0;
+    int64_t nt = 0, nv = 0;
+    kfmm_ctx *surf = nullptr;  // FMM over quadrature sources -> centroids
+    kfmm_ctx *vol = nullptr;   // FMM over quadrature sources -> interior points
+    bool surf_built = false, have_bc = false, have_sol = false;
+    double setup_G = -1, setup_nu = -1;
+    int matvecs = 0;
+    DevBuf verts, tris;
+    DevBuf q32, qn32;        // float [16 nt][3]: quadrature points, element normals
+    DevBuf q64, qn64;        // double [16 nt][3]
+    DevBuf qw;               // double [16 nt]: weights (sum to the element area)
+    DevBuf cen32, cen64;     // centroids float / double [nt][3]
+    DevBuf corrU, corrT;     // double [nt][9]: analytic self block minus own quadrature terms
+    DevBuf mask, val;        // uint8 [3 nt], double [3 nt]
+    DevBuf usol, tsol;       // double [3 nt]
+    DevBuf slq, dlq, fout;   // densities at quadrature points and summed field (FP32 or FP64)
+    DevBuf basis;            // GMRES: (restart + 1) x n
+    DevBuf w, r, x, b, part, hdev;
+    DevBuf stage[4], pts64, out64;
+    kfmm_status fail(kfmm_status c, const std::string &m) {
+        err = m;
+        return c;
+    }
+};
+
+namespace {
+
+// ------------------------------------------------------------------------------------
+// double3 helpers
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double3 ld3(const double *p) { return make_double3(p[0], p[1], p[2]); }
+__device__ __forceinline__ double3 vsub(double3 a, double3 b) { return make_double3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ double3 vadd(double3 a, double3 b) { return make_double3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ double3 vmul(double s, double3 a) { return make_double3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ double vdot(double3 a, double3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ double3 vcross(double3 a, double3 b)
+{
+    return make_double3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double vc(double3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
+
+// Singular blocks at the centroid xi of a flat triangle with unit normal n.  Per edge, in
+// polar coordinates about xi: u = unit direction to the foot of the perpendicular on the
+// edge line (distance h), w = unit edge direction, e(phi) = cos(phi) u + sin(phi) w, the
+// edge at R = h / cos(phi), phi in [pa, pb].  With F = asinh(tan phi):
+//   int R = h F;  int cos^2 R = h sin;  int sin cos R = -h cos;  int sin^2 R = h (F - sin)
+//   int cos ln R = ln h sin - (sin ln cos + F - sin);  int sin ln R = -ln h cos - (cos - cos ln cos)
+// int_tri U dA = [(3-4nu) (int R) I + int e e^T R] / (16 pi (1-nu) G)   (radial part exact)
+// PV int_tri P dA = (1-2nu)/(8 pi (1-nu)) (E n^T - n E^T), E = int e ln R  (in the element
+// plane dr/dn = 0 and only the antisymmetric term of Eq. disp_2 remains).
+__device__ void self_blocks(double3 A, double3 B, double3 C, double3 n, double G, double nu, double *Us, double *Ts)
+{
+    const double3 xi = vmul(1.0 / 3.0, vadd(vadd(A, B), C));
+    const double3 V[3] = {A, B, C};
+    double I0 = 0.0, Iee[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, E[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+        const double3 a = vsub(V[k], xi), bb = vsub(V[(k + 1) % 3], xi);
+        const double3 edge = vsub(bb, a);
+        const double L = sqrt(vdot(edge, edge));
+        const double3 w = vmul(1.0 / L, edge);
+        const double s_a = vdot(a, w);
+        const double3 foot = vsub(a, vmul(s_a, w));
+        const double h = sqrt(vdot(foot, foot));
+        const double3 u = vmul(1.0 / h, foot);
+        const double pa = atan2(s_a, h), pb = atan2(s_a + L, h);
+        const double sa = sin(pa), sb = sin(pb), ca = cos(pa), cb = cos(pb);
+        const double Fa = asinh(tan(pa)), Fb = asinh(tan(pb));
+        const double lh = log(h), lca = log(ca), lcb = log(cb);
+        I0 += h * (Fb - Fa);
+        const double icc = h * (sb - sa);
+        const double ics = -h * (cb - ca);
+        const double iss = h * ((Fb - Fa) - (sb - sa));
+        const double icl = lh * (sb - sa) - ((sb * lcb + Fb - sb) - (sa * lca + Fa - sa));
+        const double isl = -lh * (cb - ca) - ((cb - cb * lcb) - (ca - ca * lca));
+        for (int i = 0; i < 3; ++i) {
+            const double ui = vc(u, i), wi = vc(w, i);
+            for (int j = 0; j < 3; ++j) {
+                const double uj = vc(u, j), wj = vc(w, j);
+                Iee[3 * i + j] += icc * ui * uj + ics * (ui * wj + wi * uj) + iss * wi * wj;
+            }
+            E[i] += icl * ui + isl * wi;
+        }
+    }
+    const double pi = 3.14159265358979323846;
+    const double cu = 1.0 / (16.0 * pi * (1.0 - nu) * G);
+    const double ct = (1.0 - 2.0 * nu) / (8.0 * pi * (1.0 - nu));
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            Us[3 * i + j] = cu * ((i == j ? (3.0 - 4.0 * nu) * I0 : 0.0) + Iee[3 * i + j]);
+            Ts[3 * i + j] = ct * (E[i] * vc(n, j) - E[j] * vc(n, i));
+        }
+}
+
+// One thread per triangle: geometry, the 16-point rule (4 midpoint sub-triangles, each
+// with the degree-3 rule: centroid -27/48, points (3/5,1/5,1/5) 25/48), and the local-pass
+// blocks corr = (analytic singular block) - (the element's own quadrature terms), FP64.
+__global__ void bem_setup_kernel(int64_t nt, const double *__restrict__ verts, const int *__restrict__ tris,
+                                 double G, double nu, float *__restrict__ q32, float *__restrict__ qn32,
+                                 double *__restrict__ q64, double *__restrict__ qn64, double *__restrict__ qw,
+                                 float *__restrict__ cen32, double *__restrict__ cen64, double *__restrict__ corrU,
+                                 double *__restrict__ corrT, int *__restrict__ bad)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    const double3 A = ld3(verts + 3 * tris[3 * k]), B = ld3(verts + 3 * tris[3 * k + 1]),
+                  C = ld3(verts + 3 * tris[3 * k + 2]);
+    const double3 cr = vcross(vsub(B, A), vsub(C, A));
+    const double len = sqrt(vdot(cr, cr));
+    const double3 xi = vmul(1.0 / 3.0, vadd(vadd(A, B), C));
+    const double3 eab = vsub(B, A), ebc = vsub(C, B), eca = vsub(A, C);
+    const double e2 = fmax(vdot(eab, eab), fmax(vdot(ebc, ebc), vdot(eca, eca)));
+    if (!(len > 1e-12 * e2) || !isfinite(len)) {
+        atomicExch(bad, 1);
+        return;
+    }
+    const double3 n = vmul(1.0 / len, cr);
+    const double area = 0.5 * len;
+    for (int c = 0; c < 3; ++c) {
+        cen64[3 * k + c] = vc(xi, c);
+        cen32[3 * k + c] = (float)vc(xi, c);
+    }
+    const double3 mAB = vmul(0.5, vadd(A, B)), mBC = vmul(0.5, vadd(B, C)), mCA = vmul(0.5, vadd(C, A));
+    const double3 sub[4][3] = {{A, mAB, mCA}, {mAB, B, mBC}, {mCA, mBC, C}, {mBC, mCA, mAB}};
+    const double wt[4] = {-27.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0};
+    const double lam[4][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3}, {0.6, 0.2, 0.2}, {0.2, 0.6, 0.2}, {0.2, 0.2, 0.6}};
+    // own quadrature terms of U and P at the centroid (kernel 0 at the coincident point)
+    const auto kc = make_kelvin<double>(G, nu);
+    double qU[9] = {0}, qT[9] = {0};
+    int m = 0;
+    for (int s = 0; s < 4; ++s)
+        for (int g = 0; g < 4; ++g, ++m) {
+            const double3 y = vadd(vadd(vmul(lam[g][0], sub[s][0]), vmul(lam[g][1], sub[s][1])), vmul(lam[g][2], sub[s][2]));
+            const double wq = wt[g] * 0.25 * area;
+            const int64_t j = 16 * k + m;
+            for (int c = 0; c < 3; ++c) {
+                q64[3 * j + c] = vc(y, c);
+                q32[3 * j + c] = (float)vc(y, c);
+                qn64[3 * j + c] = vc(n, c);
+                qn32[3 * j + c] = (float)vc(n, c);
+            }
+            qw[j] = wq;
+            const double3 d = vsub(xi, y);
+            for (int col = 0; col < 3; ++col) {
+                // column `col` of U and P: apply each kernel to the unit vector e_col
+                double e[3] = {0, 0, 0};
+                e[col] = 1.0;
+                double ox = 0, oy = 0, oz = 0;
+                acc_sl<double>(d.x, d.y, d.z, kc.c_sl * e[0], kc.c_sl * e[1], kc.c_sl * e[2], kc.a34, ox, oy, oz);
+                qU[0 + col] += wq * ox;
+                qU[3 + col] += wq * oy;
+                qU[6 + col] += wq * oz;
+                ox = oy = oz = 0;
+                const double ue[3] = {kc.c_dl * e[0], kc.c_dl * e[1], kc.c_dl * e[2]};
+                const double nup = kc.b12 * (n.x * ue[0] + n.y * ue[1] + n.z * ue[2]);
+                acc_dl<double>(d.x, d.y, d.z, ue[0], ue[1], ue[2], n.x, n.y, n.z, nup, kc.b12, ox, oy, oz);
+                qT[0 + col] += wq * ox;
+                qT[3 + col] += wq * oy;
+                qT[6 + col] += wq * oz;
+            }
+        }
+    double Us[9], Ts[9];
+    self_blocks(A, B, C, n, G, nu, Us, Ts);
+    for (int a = 0; a < 9; ++a) {
+        corrU[9 * k + a] = Us[a] - qU[a];
+        corrT[9 * k + a] = Ts[a] - qT[a];
+    }
+}
+
+// Densities at the quadrature points for M(u, t): sl = -t_k w, dl = u_k w.
+// mode 0: u, t given (either may be NULL); mode 1: from unknowns x and the mask (Eq. num2);
+// mode 2: from the prescribed values and the mask (right-hand side, sign applied later).
+template <typename R>
+__global__ void bem_density_kernel(int64_t nt, int mode, const double *__restrict__ u, const double *__restrict__ t,
+                                   const double *__restrict__ x, const uint8_t *__restrict__ mask,
+                                   const double *__restrict__ qw, R *__restrict__ sl, R *__restrict__ dl)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 16 * nt) return;
+    const int64_t k = j / 16;
+    const double w = qw[j];
+    for (int c = 0; c < 3; ++c) {
+        double uu = 0.0, tt = 0.0;
+        const int64_t i = 3 * k + c;
+        if (mode == 0) {
+            uu = u ? u[i] : 0.0;
+            tt = t ? t[i] : 0.0;
+        } else if (mode == 1) {
+            if (mask[i]) tt = x[i];
+            else uu = x[i];
+        } else {
+            if (mask[i]) uu = x[i];
+            else tt = x[i];
+        }
+        sl[3 * j + c] = (R)(-tt * w);
+        dl[3 * j + c] = (R)(uu * w);
+    }
+}
+
+// out_l = sign * (f_l + 1/2 u_l + corrT_l u_l - corrU_l t_l)  (local pass), FP64 output.
+template <typename R>
+__global__ void bem_post_kernel(int64_t nt, int mode, double sign, const R *__restrict__ f, const double *__restrict__ u,
+                                const double *__restrict__ t, const double *__restrict__ x,
+                                const uint8_t *__restrict__ mask, const double *__restrict__ cU,
+                                const double *__restrict__ cT, double *__restrict__ out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    double uu[3], tt[3];
+    for (int c = 0; c < 3; ++c) {
+        const int64_t i = 3 * k + c;
+        uu[c] = tt[c] = 0.0;
+        if (mode == 0) {
+            uu[c] = u ? u[i] : 0.0;
+            tt[c] = t ? t[i] : 0.0;
+        } else if (mode == 1) {
+            if (mask[i]) tt[c] = x[i];
+            else uu[c] = x[i];
+        } else {
+            if (mask[i]) uu[c] = x[i];
+            else tt[c] = x[i];
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        double v = (double)f[3 * k + a] + 0.5 * uu[a];
+        for (int c = 0; c < 3; ++c) v += cT[9 * k + 3 * a + c] * uu[c] - cU[9 * k + 3 * a + c] * tt[c];
+        out[3 * k + a] = sign * v;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// GMRES vector kernels (FP64)
+// ------------------------------------------------------------------------------------
+constexpr int kVecBlocks = 2 * kNumSMs;
+constexpr int kVecThreads = 256;
+
+// part[i * nblocks + block] = partial sum of V_i . w
+__global__ void mdot_kernel(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ w, int64_t n,
+                            double *__restrict__ part)
+{
+    __shared__ double red[kVecThreads / 32];
+    for (int i = 0; i < k; ++i) {
+        const double *v = V + (int64_t)i * ldv;
+        double s = 0.0;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+            s += v[e] * w[e];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < kVecThreads / 32; ++q) t += red[q];
+            part[(int64_t)i * gridDim.x + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// w += sign * sum_i h_i V_i
+__global__ void maxpy_kernel(double *__restrict__ w, const double *__restrict__ V, int64_t ldv, int k,
+                             const double *__restrict__ h, double sign, int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += h[i] * V[(int64_t)i * ldv + e];
+        w[e] += sign * s;
+    }
+}
+
+__global__ void scale_copy_kernel(double *__restrict__ dst, const double *__restrict__ src, double a, int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = a * src[e];
+}
+
+__global__ void sub_kernel(double *__restrict__ dst, const double *__restrict__ a, const double *__restrict__ b,
+                           int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = a[e] - b[e];
+}
+
+// split the unknowns into the boundary u and t (Eq. num2 back to Eq. num)
+__global__ void split_kernel(int64_t n, const double *__restrict__ x, const uint8_t *__restrict__ mask,
+                             const double *__restrict__ val, double *__restrict__ u, double *__restrict__ t)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (mask[i]) {
+        u[i] = val[i];
+        t[i] = x[i];
+    } else {
+        u[i] = x[i];
+        t[i] = val[i];
+    }
+}
+
+// interior sources: sl = t_k w, dl = -u_k w (FP32)
+__global__ void interior_density_kernel(int64_t nt, const double *__restrict__ u, const double *__restrict__ t,
+                                        const double *__restrict__ qw, float *__restrict__ sl, float *__restrict__ dl)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 16 * nt) return;
+    const int64_t k = j / 16;
+    for (int c = 0; c < 3; ++c) {
+        sl[3 * j + c] = (float)(t[3 * k + c] * qw[j]);
+        dl[3 * j + c] = (float)(-u[3 * k + c] * qw[j]);
+    }
+}
+
+__global__ void interior_density64_kernel(int64_t nt, const double *__restrict__ u, const double *__restrict__ t,
+                                          const double *__restrict__ qw, double *__restrict__ sl,
+                                          double *__restrict__ dl)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 16 * nt) return;
+    const int64_t k = j / 16;
+    for (int c = 0; c < 3; ++c) {
+        sl[3 * j + c] = t[3 * k + c] * qw[j];
+        dl[3 * j + c] = -u[3 * k + c] * qw[j];
+    }
+}
+
+__global__ void f2d_kernel(int64_t n, const float *__restrict__ a, double *__restrict__ b)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+__global__ void d2f_kernel(int64_t n, const double *__restrict__ a, float *__restrict__ b)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+// Eq. deriv: D^T = 3/(4E) (1-nu)/(7-5nu) [10 (1+nu) s:s - (1+5nu) (tr s)^2];
+// energy density 1/2 s:eps with eps = ((1+nu) s - nu tr(s) I) / E.
+__global__ void topo_kernel(int64_t n, const float *__restrict__ s6, float E, float nu, float *__restrict__ td,
+                            float *__restrict__ energy)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float *s = s6 + 6 * i;
+    const float tr = s[0] + s[1] + s[2];
+    const float ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + 2.f * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+    if (td) td[i] = 0.75f / E * (1.f - nu) / (7.f - 5.f * nu) * (10.f * (1.f + nu) * ss - (1.f + 5.f * nu) * tr * tr);
+    if (energy) energy[i] = 0.5f * ((1.f + nu) * ss - nu * tr * tr) / E;
+}
+
+unsigned g1(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------
+#define BK_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return b->fail(KFMM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+#define BK_LAUNCH()                                                                        \
+    do {                                                                                   \
+        ++b->n_launch;                                                                     \
+        cudaError_t e_ = cudaGetLastError();                                               \
+        if (e_ != cudaSuccess) return b->fail(KFMM_ERR_CUDA, std::string("bem kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+#define BK_FMM(call)                                                                       \
+    do {                                                                                   \
+        kfmm_status s_ = (call);                                                           \
+        if (s_ != KFMM_OK) return b->fail(s_, std::string("fmm: ") + kfmm_last_error(b->surf)); \
+    } while (0)
+#define BK_TRY(expr)                                                                       \
+    do {                                                                                   \
+        kfmm_status s_ = (expr);                                                           \
+        if (s_ != KFMM_OK) return s_;                                                      \
+    } while (0)
+
+static kfmm_status bem_stage(bem_ctx *b, DevBuf &buf, const void *p, size_t bytes, const void **out)
+{
+    if (!p || is_device_ptr(p)) {
+        *out = p;
+        return KFMM_OK;
+    }
+    BK_CUDA(buf.ensure(bytes));
+    BK_CUDA(cudaMemcpyAsync(buf.p, p, bytes, cudaMemcpyHostToDevice, b->stream));
+    *out = buf.p;
+    return KFMM_OK;
+}
+
+static kfmm_status bem_setup(bem_ctx *b)
+{
+    if (b->setup_G == b->G && b->setup_nu == b->nu) return KFMM_OK;
+    const int64_t nt = b->nt;
+    DevBuf bad;
+    BK_CUDA(bad.ensure(sizeof(int)));
+    BK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), b->stream));
+    bem_setup_kernel<<<g1(nt, 128), 128, 0, b->stream>>>(
+        nt, b->verts.as<double>(), b->tris.as<int>(), b->G, b->nu, b->q32.as<float>(), b->qn32.as<float>(),
+        b->q64.as<double>(), b->qn64.as<double>(), b->qw.as<double>(), b->cen32.as<float>(), b->cen64.as<double>(),
+        b->corrU.as<double>(), b->corrT.as<double>(), bad.as<int>());
+    BK_LAUNCH();
+    int hb = 0;
+    BK_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BK_CUDA(cudaStreamSynchronize(b->stream));
+    if (hb) return b->fail(KFMM_ERR_INVALID_ARG, "bem: zero-area or non-finite triangle");
+    b->setup_G = b->G;
+    b->setup_nu = b->nu;
+    if (b->op == BEM_FMM && !b->surf_built) {
+        BK_FMM(kfmm_build(b->surf, b->q32.as<float>(), b->qn32.as<float>(), 16 * nt, b->cen32.as<float>(), nt));
+        b->surf_built = true;
+    }
+    return KFMM_OK;
+}
+
+// M(u, t) (mode 0), A x (mode 1) or B y (mode 2; sign -1) into out (device, FP64 [nt][3]).
+static kfmm_status bem_op_apply(bem_ctx *b, int mode, const double *u, const double *t, const double *x,
+                                double *out)
+{
+    BK_TRY(bem_setup(b));
+    const int64_t nt = b->nt, nq = 16 * nt;
+    const double sign = mode == 2 ? -1.0 : 1.0;
+    const uint8_t *mask = b->mask.as<uint8_t>();
+    ++b->matvecs;
+    if (b->op == BEM_FMM) {
+        BK_CUDA(b->slq.ensure(sizeof(float) * 3 * nq));
+        BK_CUDA(b->dlq.ensure(sizeof(float) * 3 * nq));
+        BK_CUDA(b->fout.ensure(sizeof(float) * 3 * nt));
+        bem_density_kernel<float><<<g1(nq), 256, 0, b->stream>>>(nt, mode, u, t, x, mask, b->qw.as<double>(),
+                                                                 b->slq.as<float>(), b->dlq.as<float>());
+        BK_LAUNCH();
+        BK_FMM(kfmm_eval(b->surf, b->slq.as<float>(), b->dlq.as<float>(), 1, KFMM_DISP, b->fout.as<float>()));
+        bem_post_kernel<float><<<g1(nt), 256, 0, b->stream>>>(nt, mode, sign, b->fout.as<float>(), u, t, x, mask,
+                                                              b->corrU.as<double>(), b->corrT.as<double>(), out);
+        BK_LAUNCH();
+    } else {
+        BK_CUDA(b->slq.ensure(sizeof(double) * 3 * nq));
+        BK_CUDA(b->dlq.ensure(sizeof(double) * 3 * nq));
+        BK_CUDA(b->fout.ensure(sizeof(double) * 3 * nt));
+        bem_density_kernel<double><<<g1(nq), 256, 0, b->stream>>>(nt, mode, u, t, x, mask, b->qw.as<double>(),
+                                                                  b->slq.as<double>(), b->dlq.as<double>());
+        BK_LAUNCH();
+        BK_FMM(kfmm_direct(b->surf, KFMM_FP64, b->cen64.p, nt, b->q64.p, b->qn64.p, nq, b->slq.p, b->dlq.p, KFMM_DISP,
+                           b->fout.p));
+        bem_post_kernel<double><<<g1(nt), 256, 0, b->stream>>>(nt, mode, sign, b->fout.as<double>(), u, t, x, mask,
+                                                               b->corrU.as<double>(), b->corrT.as<double>(), out);
+        BK_LAUNCH();
+    }
+    return KFMM_OK;
+}
+
+// dot products V_i . w for i < k, summed on the host in FP64
+static kfmm_status mdot(bem_ctx *b, const double *V, int64_t ldv, int k, const double *w, int64_t n, double *h)
+{
+    BK_CUDA(b->part.ensure(sizeof(double) * (size_t)kVecBlocks * k));
+    mdot_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(V, ldv, k, w, n, b->part.as<double>());
+    BK_LAUNCH();
+    std::vector<double> p((size_t)kVecBlocks * k);
+    BK_CUDA(cudaMemcpyAsync(p.data(), b->part.p, sizeof(double) * p.size(), cudaMemcpyDeviceToHost, b->stream));
+    BK_CUDA(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < k; ++i) {
+        double s = 0.0;
+        for (int q = 0; q < kVecBlocks; ++q) s += p[(size_t)i * kVecBlocks + q];
+        h[i] = s;
+    }
+    return KFMM_OK;
+}
+
+static kfmm_status maxpy(bem_ctx *b, double *w, const double *V, int64_t ldv, int k, const double *h, double sign,
+                         int64_t n)
+{
+    BK_CUDA(b->hdev.ensure(sizeof(double) * (k + 1)));
+    BK_CUDA(cudaMemcpyAsync(b->hdev.p, h, sizeof(double) * k, cudaMemcpyHostToDevice, b->stream));
+    maxpy_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(w, V, ldv, k, b->hdev.as<double>(), sign, n);
+    BK_LAUNCH();
+    BK_CUDA(cudaStreamSynchronize(b->stream));  // h lives on the host stack
+    return KFMM_OK;
+}
+
+static kfmm_status vnorm(bem_ctx *b, const double *w, int64_t n, double *out)
+{
+    double s;
+    BK_TRY(mdot(b, w, n, 1, w, n, &s));
+    *out = std::sqrt(std::max(s, 0.0));
+    return KFMM_OK;
+}
+
+static kfmm_status gmres(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
+{
+    const int64_t n = 3 * b->nt;
+    const int m = o.restart;
+    BK_CUDA(b->basis.ensure(sizeof(double) * (size_t)(m + 1) * n));
+    BK_CUDA(b->w.ensure(sizeof(double) * n));
+    BK_CUDA(b->r.ensure(sizeof(double) * n));
+    BK_CUDA(b->x.ensure(sizeof(double) * n));
+    BK_CUDA(b->b.ensure(sizeof(double) * n));
+    double *V = b->basis.as<double>(), *w = b->w.as<double>(), *r = b->r.as<double>(), *x = b->x.as<double>(),
+           *rhs = b->b.as<double>();
+    BK_TRY(bem_op_apply(b, 2, nullptr, nullptr, b->val.as<double>(), rhs));
+    double bn;
+    BK_TRY(vnorm(b, rhs, n, &bn));
+    if (bn == 0.0) bn = 1.0;
+    if (o.x0) {
+        const void *dx0;
+        BK_TRY(bem_stage(b, b->stage[0], o.x0, sizeof(double) * n, &dx0));
+        BK_CUDA(cudaMemcpyAsync(x, dx0, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
+    } else {
+        BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, b->stream));
+    }
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m), h(m + 1), h2(m + 1);
+    int it = 0;
+    double rel = 1.0;
+    bool conv = false;
+    while (true) {
+        // true residual r = b - A x
+        if (o.x0 || it > 0) {
+            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, x, w));
+            sub_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(r, rhs, w, n);
+            BK_LAUNCH();
+        } else {
+            BK_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
+        }
+        double beta;
+        BK_TRY(vnorm(b, r, n, &beta));
+        rel = beta / bn;
+        if (rel <= o.tol) {
+            conv = true;
+            break;
+        }
+        if (it >= o.maxit) break;
+        scale_copy_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(V, r, 1.0 / beta, n);
+        BK_LAUNCH();
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int j = 0;
+        for (; j < m && it < o.maxit; ++j) {
+            double *vj = V + (size_t)j * n, *vn = V + (size_t)(j + 1) * n;
+            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, vj, w));
+            ++it;
+            // classical Gram-Schmidt, twice
+            BK_TRY(mdot(b, V, n, j + 1, w, n, h.data()));
+            BK_TRY(maxpy(b, w, V, n, j + 1, h.data(), -1.0, n));
+            BK_TRY(mdot(b, V, n, j + 1, w, n, h2.data()));
+            BK_TRY(maxpy(b, w, V, n, j + 1, h2.data(), -1.0, n));
+            for (int i = 0; i <= j; ++i) h[i] += h2[i];
+            double hn;
+            BK_TRY(vnorm(b, w, n, &hn));
+            h[j + 1] = hn;
+            scale_copy_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(vn, w, hn > 0 ? 1.0 / hn : 0.0, n);
+            BK_LAUNCH();
+            for (int i = 0; i < j; ++i) {
+                const double t0 = cs[i] * h[i] + sn[i] * h[i + 1];
+                h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+                h[i] = t0;
+            }
+            const double den = std::hypot(h[j], h[j + 1]);
+            cs[j] = den > 0 ? h[j] / den : 1.0;
+            sn[j] = den > 0 ? h[j + 1] / den : 0.0;
+            h[j] = den;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i];
+            if (std::fabs(g[j + 1]) / bn <= o.tol) {
+                ++j;
+                break;
+            }
+        }
+        for (int i = j - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int k2 = i + 1; k2 < j; ++k2) s -= H[(size_t)i * m + k2] * y[k2];
+            y[i] = s / H[(size_t)i * m + i];
+        }
+        BK_TRY(maxpy(b, x, V, n, j, y.data(), 1.0, n));
+    }
+    st->iters = it;
+    st->converged = conv;
+    st->relres = rel;
+    return KFMM_OK;
+}
+
+extern "C" {
+
+void bem_default_solve_opts(bem_solve_opts *o)
+{
+    if (!o) return;
+    o->tol = 1e-6;
+    o->restart = 30;
+    o->maxit = 1000;
+    o->x0 = nullptr;
+}
+
+kfmm_status bem_create(bem_ctx **out, const kfmm_options *opt, int op, const double *verts, int64_t nv,
+                       const int32_t *tris, int64_t nt)
+{
+    if (!out) return KFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!verts || !tris || nv < 3 || nt < 1 || (op != BEM_FMM && op != BEM_DIRECT_FP64) || 16 * nt > (1LL << 30))
+        return KFMM_ERR_INVALID_ARG;
+    bem_ctx *b = new (std::nothrow) bem_ctx();
+    if (!b) return KFMM_ERR_OOM;
+    kfmm_default_options(&b->opt);
+    if (opt) b->opt = *opt;
+    b->op = op;
+    b->nt = nt;
+    b->nv = nv;
+    kfmm_status s = kfmm_create(&b->surf, &b->opt);
+    if (s != KFMM_OK) {
+        delete b;
+        return s;
+    }
+    // copy the mesh, check indices
+    std::vector<int32_t> ht(3 * nt);
+    bool host_tris = !is_device_ptr(tris);
+    if (host_tris) std::memcpy(ht.data(), tris, sizeof(int32_t) * 3 * nt);
+    else cudaMemcpy(ht.data(), tris, sizeof(int32_t) * 3 * nt, cudaMemcpyDeviceToHost);
+    for (int64_t i = 0; i < 3 * nt; ++i)
+        if (ht[i] < 0 || ht[i] >= nv) {
+            kfmm_destroy(b->surf);
+            delete b;
+            return KFMM_ERR_INVALID_ARG;
+        }
+    const int64_t nq = 16 * nt;
+    bool ok = b->verts.ensure(sizeof(double) * 3 * nv) == cudaSuccess && b->tris.ensure(sizeof(int) * 3 * nt) == cudaSuccess &&
+              b->q32.ensure(sizeof(float) * 3 * nq) == cudaSuccess && b->qn32.ensure(sizeof(float) * 3 * nq) == cudaSuccess &&
+              b->q64.ensure(sizeof(double) * 3 * nq) == cudaSuccess && b->qn64.ensure(sizeof(double) * 3 * nq) == cudaSuccess &&
+              b->qw.ensure(sizeof(double) * nq) == cudaSuccess && b->cen32.ensure(sizeof(float) * 3 * nt) == cudaSuccess &&
+              b->cen64.ensure(sizeof(double) * 3 * nt) == cudaSuccess && b->corrU.ensure(sizeof(double) * 9 * nt) == cudaSuccess &&
+              b->corrT.ensure(sizeof(double) * 9 * nt) == cudaSuccess && b->mask.ensure(3 * nt) == cudaSuccess &&
+              b->val.ensure(sizeof(double) * 3 * nt) == cudaSuccess && b->usol.ensure(sizeof(double) * 3 * nt) == cudaSuccess &&
+              b->tsol.ensure(sizeof(double) * 3 * nt) == cudaSuccess;
+    if (!ok) {
+        kfmm_destroy(b->surf);
+        delete b;
+        return KFMM_ERR_OOM;
+    }
+    cudaMemcpy(b->verts.p, verts, sizeof(double) * 3 * nv, cudaMemcpyDefault);
+    cudaMemcpy(b->tris.p, ht.data(), sizeof(int) * 3 * nt, cudaMemcpyHostToDevice);
+    std::vector<double> hv(3 * nv);
+    cudaMemcpy(hv.data(), b->verts.p, sizeof(double) * 3 * nv, cudaMemcpyDeviceToHost);
+    for (double v : hv)
+        if (!std::isfinite(v)) {
+            kfmm_destroy(b->surf);
+            delete b;
+            return KFMM_ERR_INVALID_ARG;
+        }
+    *out = b;
+    return KFMM_OK;
+}
+
+kfmm_status bem_destroy(bem_ctx *b)
+{
+    if (!b) return KFMM_ERR_INVALID_ARG;
+    cudaStreamSynchronize(b->stream);
+    if (b->surf) kfmm_destroy(b->surf);
+    if (b->vol) kfmm_destroy(b->vol);
+    delete b;
+    return KFMM_OK;
+}
+
+kfmm_status bem_set_material(bem_ctx *b, double K, double G)
+{
+    if (!b) return KFMM_ERR_INVALID_ARG;
+    kfmm_status s = kfmm_set_material(b->surf, K, G);
+    if (s != KFMM_OK) return b->fail(s, "bem: material needs K > 0 and G > 0");
+    if (b->vol) kfmm_set_material(b->vol, K, G);
+    b->G = G;
+    b->K = K;
+    b->nu = (3.0 * K - 2.0 * G) / (2.0 * (3.0 * K + G));
+    return KFMM_OK;
+}
+
+kfmm_status bem_set_stream(bem_ctx *b, void *stream)
+{
+    if (!b) return KFMM_ERR_INVALID_ARG;
+    b->stream = (cudaStream_t)stream;
+    kfmm_set_stream(b->surf, stream);
+    if (b->vol) kfmm_set_stream(b->vol, stream);
+    return KFMM_OK;
+}
+
+kfmm_status bem_set_bc(bem_ctx *b, const uint8_t *known_is_disp, const double *values)
+{
+    if (!b || !known_is_disp || !values) return KFMM_ERR_INVALID_ARG;
+    BK_CUDA(cudaMemcpyAsync(b->mask.p, known_is_disp, 3 * b->nt, cudaMemcpyDefault, b->stream));
+    BK_CUDA(cudaMemcpyAsync(b->val.p, values, sizeof(double) * 3 * b->nt, cudaMemcpyDefault, b->stream));
+    BK_CUDA(cudaStreamSynchronize(b->stream));
+    b->have_bc = true;
+    return KFMM_OK;
+}
+
+kfmm_status bem_apply(bem_ctx *b, const double *u, const double *t, double *out)
+{
+    if (!b || !out || (!u && !t)) return KFMM_ERR_INVALID_ARG;
+    const size_t bytes = sizeof(double) * 3 * b->nt;
+    const void *du, *dt;
+    BK_TRY(bem_stage(b, b->stage[0], u, bytes, &du));
+    BK_TRY(bem_stage(b, b->stage[1], t, bytes, &dt));
+    double *dout = out;
+    const bool host_out = !is_device_ptr(out);
+    if (host_out) {
+        BK_CUDA(b->out64.ensure(bytes));
+        dout = b->out64.as<double>();
+    }
+    BK_TRY(bem_op_apply(b, 0, (const double *)du, (const double *)dt, nullptr, dout));
+    if (host_out) BK_CUDA(cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, b->stream));
+    BK_CUDA(cudaStreamSynchronize(b->stream));
+    return KFMM_OK;
+}
+
+kfmm_status bem_matvec(bem_ctx *b, const double *x, double *y)
+{
+    if (!b || !x || !y) return KFMM_ERR_INVALID_ARG;
+    if (!b->have_bc) return b->fail(KFMM_ERR_NOT_BUILT, "bem: boundary conditions not set");
+    const size_t bytes = sizeof(double) * 3 * b->nt;
+    const void *dx;
+    BK_TRY(bem_stage(b, b->stage[0], x, bytes, &dx));
+    double *dy = y;
+    const bool host_out = !is_device_ptr(y);
+    if (host_out) {
+        BK_CUDA(b->out64.ensure(bytes));
+        dy = b->out64.as<double>();
+    }
+    BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, (const double *)dx, dy));
+    if (host_out) BK_CUDA(cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, b->stream));
+    BK_CUDA(cudaStreamSynchronize(b->stream));
+    return KFMM_OK;
+}
+
+kfmm_status bem_rhs(bem_ctx *b, double *rhs)
+{
+    if (!b || !rhs) return KFMM_ERR_INVALID_ARG;
+    if (!b->have_bc) return b->fail(KFMM_ERR_NOT_BUILT, "bem: boundary conditions not set");
+    const size_t bytes = sizeof(double) * 3 * b->nt;
+    double *dy = rhs;
+    const bool host_out = !is_device_ptr(rhs);
+    if (host_out) {
+        BK_CUDA(b->out64.ensure(bytes));
+        dy = b->out64.as<double>();
+    }
+    BK_TRY(bem_op_apply(b, 2, nullptr, nullptr, b->val.as<double>(), dy));
+    if (host_out) BK_CUDA(cudaMemcpyAsync(rhs, dy, bytes, cudaMemcpyDeviceToHost, b->stream));
+    BK_CUDA(cudaStreamSynchronize(b->stream));
+    return KFMM_OK;
+}
+
+kfmm_status bem_solve(bem_ctx *b, const bem_solve_opts *opts, double *u, double *t, bem_stats *st)
+{
+    if (!b) return KFMM_ERR_INVALID_ARG;
+    if (!b->have_bc) return b->fail(KFMM_ERR_NOT_BUILT, "bem: boundary conditions not set");
+    bem_solve_opts o;
+    bem_default_solve_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.tol > 0) || o.restart < 1 || o.restart > 200 || o.maxit < 1)
+        return b->fail(KFMM_ERR_INVALID_ARG, "bem_solve: need tol > 0, 1 <= restart <= 200, maxit >= 1");
+    const auto t0 = std::chrono::steady_clock::now();
+    bem_stats s{};
+    const int mv0 = b->matvecs;
+    BK_TRY(gmres(b, o, &s));
+    const int64_t n = 3 * b->nt;
+    split_kernel<<<g1(n), 256, 0, b->stream>>>(n, b->x.as<double>(), b->mask.as<uint8_t>(), b->val.as<double>(),
+                                                b->usol.as<double>(), b->tsol.as<double>());
+    BK_LAUNCH();
+    b->have_sol = true;
+    if (u) BK_CUDA(cudaMemcpyAsync(u, b->usol.p, sizeof(double) * n, cudaMemcpyDefault, b->stream));
+    if (t) BK_CUDA(cudaMemcpyAsync(t, b->tsol.p, sizeof(double) * n, cudaMemcpyDefault, b->stream));
+    BK_CUDA(cudaStreamSynchronize(b->stream));
+    s.matvecs = b->matvecs - mv0;
+    s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (st) *st = s;
+    if (!s.converged) return b->fail(KFMM_ERR_NOT_CONVERGED, "bem_solve: iteration cap reached");
+    return KFMM_OK;
+}
+
+kfmm_status bem_set_solution(bem_ctx *b, const double *u, const double *t)
+{
+    if (!b || !u || !t) return KFMM_ERR_INVALID_ARG;
+    const size_t bytes = sizeof(double) * 3 * b->nt;
+    BK_CUDA(cudaMemcpyAsync(b->usol.p, u, bytes, cudaMemcpyDefault, b->stream));
+    BK_CUDA(cudaMemcpyAsync(b->tsol.p, t, bytes, cudaMemcpyDefault, b->stream));
+    BK_CUDA(cudaStreamSynchronize(b->stream));
+    b->have_sol = true;
+    return KFMM_OK;
+}
+
+kfmm_status bem_interior(bem_ctx *b, const float *pts, int64_t n, float *disp, float *stress)
+{
+    if (!b || !pts || n < 1 || (!disp && !stress)) return KFMM_ERR_INVALID_ARG;
+    if (!b->have_sol) return b->fail(KFMM_ERR_NOT_BUILT, "bem: no boundary solution (solve or set_solution first)");
+    BK_TRY(bem_setup(b));
+    const int64_t nt = b->nt, nq = 16 * nt;
+    const void *dp;
+    BK_TRY(bem_stage(b, b->stage[2], pts, sizeof(float) * 3 * n, &dp));
+    if (b->op == BEM_FMM) {
+        if (!b->vol) {
+            kfmm_status s = kfmm_create(&b->vol, &b->opt);
+            if (s != KFMM_OK) return b->fail(s, "bem: interior FMM context");
+            kfmm_set_material(b->vol, b->K, b->G);
+            kfmm_set_stream(b->vol, b->stream);
+        }
+        BK_CUDA(b->slq.ensure(sizeof(float) * 3 * nq));
+        BK_CUDA(b->dlq.ensure(sizeof(float) * 3 * nq));
+        interior_density_kernel<<<g1(nq), 256, 0, b->stream>>>(nt, b->usol.as<double>(), b->tsol.as<double>(),
+                                                                b->qw.as<double>(), b->slq.as<float>(), b->dlq.as<float>());
+        BK_LAUNCH();
+        kfmm_status s = kfmm_build(b->vol, b->q32.as<float>(), b->qn32.as<float>(), nq, (const float *)dp, n);
+        if (s != KFMM_OK) return b->fail(s, std::string("interior fmm: ") + kfmm_last_error(b->vol));
+        if (disp) {
+            s = kfmm_eval(b->vol, b->slq.as<float>(), b->dlq.as<float>(), 1, KFMM_DISP, disp);
+            if (s != KFMM_OK) return b->fail(s, std::string("interior fmm: ") + kfmm_last_error(b->vol));
+        }
+        if (stress) {
+            s = kfmm_eval(b->vol, b->slq.as<float>(), b->dlq.as<float>(), 1, KFMM_STRESS, stress);
+            if (s != KFMM_OK) return b->fail(s, std::string("interior fmm: ") + kfmm_last_error(b->vol));
+        }
+    } else {
+        BK_CUDA(b->slq.ensure(sizeof(double) * 3 * nq));
+        BK_CUDA(b->dlq.ensure(sizeof(double) * 3 * nq));
+        BK_CUDA(b->pts64.ensure(sizeof(double) * 3 * n));
+        BK_CUDA(b->out64.ensure(sizeof(double) * 6 * n));
+        interior_density64_kernel<<<g1(nq), 256, 0, b->stream>>>(nt, b->usol.as<double>(), b->tsol.as<double>(),
+                                                                  b->qw.as<double>(), b->slq.as<double>(),
+                                                                  b->dlq.as<double>());
+        BK_LAUNCH();
+        f2d_kernel<<<g1(3 * n), 256, 0, b->stream>>>(3 * n, (const float *)dp, b->pts64.as<double>());
+        BK_LAUNCH();
+        DevBuf of;
+        for (int kind = 0; kind < 2; ++kind) {
+            float *dst = kind == 0 ? disp : stress;
+            if (!dst) continue;
+            const int no = kind == 0 ? 3 : 6;
+            BK_FMM(kfmm_direct(b->surf, KFMM_FP64, b->pts64.p, n, b->q64.p, b->qn64.p, nq, b->slq.p, b->dlq.p,
+                               kind == 0 ? KFMM_DISP : KFMM_STRESS, b->out64.p));
+            const bool host_out = !is_device_ptr(dst);
+            float *d = dst;
+            if (host_out) {
+                BK_CUDA(of.ensure(sizeof(float) * no * n));
+                d = of.as<float>();
+            }
+            d2f_kernel<<<g1(no * n), 256, 0, b->stream>>>(no * n, b->out64.as<double>(), d);
+            BK_LAUNCH();
+            if (host_out) BK_CUDA(cudaMemcpyAsync(dst, d, sizeof(float) * no * n, cudaMemcpyDeviceToHost, b->stream));
+            BK_CUDA(cudaStreamSynchronize(b->stream));
+        }
+    }
+    BK_CUDA(cudaStreamSynchronize(b->stream));
+    return KFMM_OK;
+}
+
+kfmm_status bem_topo_derivative(bem_ctx *b, const float *pts, int64_t n, float *td, float *energy, float *stress)
+{
+    if (!b || !pts || n < 1 || (!td && !energy && !stress)) return KFMM_ERR_INVALID_ARG;
+    DevBuf sbuf, tdb, enb;
+    float *ds = stress;
+    const bool host_s = stress && !is_device_ptr(stress);
+    if (!stress || host_s) {
+        BK_CUDA(sbuf.ensure(sizeof(float) * 6 * n));
+        ds = sbuf.as<float>();
+    }
+    BK_TRY(bem_interior(b, pts, n, nullptr, ds));
+    float *dtd = td, *den = energy;
+    const bool host_td = td && !is_device_ptr(td), host_en = energy && !is_device_ptr(energy);
+    if (host_td) {
+        BK_CUDA(tdb.ensure(sizeof(float) * n));
+        dtd = tdb.as<float>();
+    }
+    if (host_en) {
+        BK_CUDA(enb.ensure(sizeof(float) * n));
+        den = enb.as<float>();
+    }
+    const double E = 2.0 * b->G * (1.0 + b->nu);
+    topo_kernel<<<g1(n), 256, 0, b->stream>>>(n, ds, (float)E, (float)b->nu, dtd, den);
+    BK_LAUNCH();
+    if (host_td) BK_CUDA(cudaMemcpyAsync(td, dtd, sizeof(float) * n, cudaMemcpyDeviceToHost, b->stream));
+    if (host_en) BK_CUDA(cudaMemcpyAsync(energy, den, sizeof(float) * n, cudaMemcpyDeviceToHost, b->stream));
+    if (host_s) BK_CUDA(cudaMemcpyAsync(stress, ds, sizeof(float) * 6 * n, cudaMemcpyDeviceToHost, b->stream));
+    BK_CUDA(cudaStreamSynchronize(b->stream));
+    return KFMM_OK;
+}
+
+const char *bem_last_error(const bem_ctx *b) { return b ? b->err.c_str() : "null context"; }
+
+}  // extern "C"

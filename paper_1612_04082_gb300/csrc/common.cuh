@@ -95,14 +95,18 @@ struct Operators {
     int p = 0, n_surf = 0, rank = 0;  // rank of the shared M2L basis
     double nu = -1, r_inner = 0, r_outer = 0, pinv_rtol = 0, m2l_rtol = 0;
     int m2l_rank_max = 0;
+    int ku = 0, kd = 0;  // ranks kept of the upward / downward check-to-equivalent maps
+    // FP32, rows padded to multiples of 16 (see precompute.h for the definitions)
     DevBuf surf;      // float [n_surf][4]: unit lattice surface points in [-1,1]^3
-    DevBuf pinv_uc;   // float [3n][3n]: pseudo-inverse of U(upward check <- upward equivalent), h = G = 1
-    DevBuf pinv_dc;   // float [3n][3n]: pseudo-inverse of U(downward check <- downward equivalent)
-    DevBuf m2m;       // float [8][3n][3n]: child octant -> parent upward equivalent density
-    DevBuf l2l;       // float [8][3n][3n]: parent -> child octant downward equivalent density
-    DevBuf m2l_vt;    // float [rank][3n]: compression of upward densities (psi = Vt phi)
-    DevBuf m2l_c;     // float [316][rank][rank]: translation in the compressed basis
-    DevBuf m2l_w;     // float [3n][rank]: pinv_dc * U_r (expansion into downward densities)
+    DevBuf s2a_u;     // [ku][3n]   upward check -> alpha (x G h)
+    DevBuf mb;        // [8][ku][ku] child alpha -> parent alpha
+    DevBuf vu;        // [3n][ku]   alpha -> upward equivalent density
+    DevBuf cb;        // [r][ku]    alpha -> psi (M2L input)
+    DevBuf m2l_c;     // [316][r][r] translation in the shared basis
+    DevBuf wb;        // [kd][r]    M2L output -> beta
+    DevBuf s2a_d;     // [kd][3n]   downward check -> beta (x G h)
+    DevBuf lb;        // [8][kd][kd] parent beta -> child beta
+    DevBuf vd;        // [3n][kd]   beta -> downward equivalent density
 };
 
 // Octree and interaction lists (device arrays unless noted).
@@ -146,6 +150,8 @@ struct Tree {
     DevBuf leaves;              // int [n_leaves]: leaf box indices
     DevBuf xboxes;              // int: boxes with a non-empty X list
     int n_xboxes = 0;
+    DevBuf wboxes;              // int: boxes that appear in some W list
+    int n_wboxes = 0;
     // octant groups per level for M2M / L2L: children at level l with octant o
     DevBuf oct_child;           // int: grouped child indices
     std::vector<int> oct_off;   // host: [(n_levels) * 8 + 1] offsets (level-major, then octant)
@@ -156,13 +162,14 @@ struct Tree {
 // Per-evaluation work arrays.
 struct Work {
     DevBuf src_rec;   // packed, pre-scaled source records in sorted order
-    DevBuf up_chk;    // float [n_boxes][3n]
-    DevBuf up_phi;    // float [n_boxes][3n]
-    DevBuf psi;       // float [n_boxes][rank]
-    DevBuf cdn;       // float [n_boxes][rank]
-    DevBuf dn_chk;    // float [n_boxes][3n]
-    DevBuf dn_phi;    // float [n_boxes][3n]
-    DevBuf scal;      // float [n_boxes]: G * half-width per box
+    DevBuf up_chk;    // float [n_boxes][3n]   upward check potentials (leaves)
+    DevBuf alpha;     // float [n_boxes][ku]   upward densities in the singular basis
+    DevBuf psi;       // float [n_boxes][rank] M2L inputs
+    DevBuf cdn;       // float [n_boxes][rank] M2L outputs
+    DevBuf dn_chk;    // float [n_boxes][3n]   downward check potentials (X-list boxes)
+    DevBuf beta;      // float [n_boxes][kd]   downward densities in the singular basis
+    DevBuf up_phi;    // float [n_boxes][3n]   upward equivalent densities (W-list boxes)
+    DevBuf dn_phi;    // float [n_boxes][3n]   downward equivalent densities (leaves)
     DevBuf stage_in[4];  // staging of host inputs
     DevBuf stage_out;
     DevBuf tmp;
@@ -176,7 +183,7 @@ struct GemmPlan {
 
 struct FmmPlans {
     bool valid = false;
-    GemmPlan all, leaves, xboxes, m2l;
+    GemmPlan all, leaves, xboxes, wboxes, m2l;
     std::vector<GemmPlan> oct_lvl;  // per level: children grouped by octant (M2M, L2L)
     DevBuf geom;                    // float4 per box: centre x, y, z and half-width
 };

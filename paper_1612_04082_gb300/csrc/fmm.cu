@@ -76,6 +76,7 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
         }
     }
     const int n = H->n_surf, m = 3 * n, ld = round_up(m, 16), r = H->rank, rp = round_up(r, 16);
+    (void)rp;
     {
         std::vector<float> s((size_t)n * 4, 0.f);
         for (int a = 0; a < n; ++a)
@@ -83,13 +84,18 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
         KF_CUDA(O.surf.ensure(sizeof(float) * s.size()));
         KF_CUDA(cudaMemcpy(O.surf.p, s.data(), sizeof(float) * s.size(), cudaMemcpyHostToDevice));
     }
-    KF_TRY(upload_padded(ctx, O.pinv_uc, H->pinv_uc.data(), 1, m, m, ld, ld));
-    KF_TRY(upload_padded(ctx, O.pinv_dc, H->pinv_dc.data(), 1, m, m, ld, ld));
-    KF_TRY(upload_padded(ctx, O.m2m, H->m2m.data(), 8, m, m, ld, ld));
-    KF_TRY(upload_padded(ctx, O.l2l, H->l2l.data(), 8, m, m, ld, ld));
-    KF_TRY(upload_padded(ctx, O.m2l_vt, H->m2l_vt.data(), 1, r, m, ld, rp));
-    KF_TRY(upload_padded(ctx, O.m2l_c, H->m2l_c.data(), 316, r, r, rp, rp));
-    KF_TRY(upload_padded(ctx, O.m2l_w, H->m2l_w.data(), 1, m, r, rp, ld));
+    const int ku = H->ku, kd = H->kd, kup = round_up(ku, 16), kdp = round_up(kd, 16);
+    KF_TRY(upload_padded(ctx, O.s2a_u, H->s2a_u.data(), 1, ku, m, ld, ku));
+    KF_TRY(upload_padded(ctx, O.mb, H->mb.data(), 8, ku, ku, kup, ku));
+    KF_TRY(upload_padded(ctx, O.vu, H->vu.data(), 1, m, ku, kup, m));
+    KF_TRY(upload_padded(ctx, O.cb, H->cb.data(), 1, r, ku, kup, r));
+    KF_TRY(upload_padded(ctx, O.m2l_c, H->m2l_c.data(), 316, r, r, rp, r));
+    KF_TRY(upload_padded(ctx, O.wb, H->wb.data(), 1, kd, r, rp, kd));
+    KF_TRY(upload_padded(ctx, O.s2a_d, H->s2a_d.data(), 1, kd, m, ld, kd));
+    KF_TRY(upload_padded(ctx, O.lb, H->lb.data(), 8, kd, kd, kdp, kd));
+    KF_TRY(upload_padded(ctx, O.vd, H->vd.data(), 1, m, kd, kdp, m));
+    O.ku = ku;
+    O.kd = kd;
     O.p = prm.p;
     O.nu = prm.nu;
     O.r_inner = prm.r_inner;
@@ -259,6 +265,8 @@ struct GemmArgs {
 
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 
+// TAG only separates the launches by name in profiles: 0 = box operators, 1 = M2L.
+template <int TAG>
 __global__ void __launch_bounds__(256) gemm_gather_kernel(GemmArgs g)
 {
     __shared__ float As[GBK][GBM + 4];
@@ -554,6 +562,7 @@ static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
     KF_TRY(make_plan(ctx, P.all, {0}, {0}, {T.n_boxes}));
     KF_TRY(make_plan(ctx, P.leaves, {0}, {0}, {T.n_leaves}));
     KF_TRY(make_plan(ctx, P.xboxes, {0}, {0}, {T.n_xboxes}));
+    KF_TRY(make_plan(ctx, P.wboxes, {0}, {0}, {T.n_wboxes}));
     {
         std::vector<int> gm(316), gb(316), ge(316);
         for (int d = 0; d < 316; ++d) {
@@ -584,7 +593,7 @@ static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
 
 static kfmm_status run_gemm(kfmm_ctx *ctx, const GemmPlan &pl, const float *A, int64_t a_stride, int M, int K,
                             int lda, const int *src, const int *dst, int src_par, int dst_par, const float *X,
-                            int ldx, float *Y, int ldy, const float4 *geom, float alpha, int mode)
+                            int ldx, float *Y, int ldy, const float4 *geom, float alpha, int mode, int tag = 0)
 {
     if (pl.n_tiles == 0) return KFMM_OK;
     GemmArgs g;
@@ -607,7 +616,8 @@ static kfmm_status run_gemm(kfmm_ctx *ctx, const GemmPlan &pl, const float *A, i
     g.alpha = alpha;
     g.mode = mode;
     dim3 grid(pl.n_tiles, (M + GBM - 1) / GBM);
-    gemm_gather_kernel<<<grid, 256, 0, ctx->stream>>>(g);
+    if (tag == 1) gemm_gather_kernel<1><<<grid, 256, 0, ctx->stream>>>(g);
+    else gemm_gather_kernel<0><<<grid, 256, 0, ctx->stream>>>(g);
     KF_LAUNCH();
     return KFMM_OK;
 }
@@ -621,14 +631,15 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
     KF_TRY(ensure_operators(ctx));
     FmmPlans &P = ctx->plans;
     const int n = O.n_surf, m = 3 * n, ld = round_up(m, 16), r = O.rank, rp = round_up(r, 16);
+    const int ku = O.ku, kd = O.kd, kup = round_up(ku, 16), kdp = round_up(kd, 16);
     const int nb = T.n_boxes;
     const int64_t ns = T.nsrc;
     if (!P.valid) {
         KF_TRY(build_plans(ctx, P));
         // box vectors: zero once, so the padding lanes read by the GEMM K loops stay zero
-        DevBuf *bufs[6] = {&W.up_chk, &W.up_phi, &W.dn_chk, &W.dn_phi, &W.psi, &W.cdn};
-        const int lds[6] = {ld, ld, ld, ld, rp, rp};
-        for (int k = 0; k < 6; ++k) {
+        DevBuf *bufs[8] = {&W.up_chk, &W.alpha, &W.psi, &W.cdn, &W.dn_chk, &W.beta, &W.up_phi, &W.dn_phi};
+        const int lds[8] = {ld, kup, rp, rp, ld, kdp, ld, ld};
+        for (int k = 0; k < 8; ++k) {
             KF_CUDA(bufs[k]->ensure(sizeof(float) * (size_t)nb * lds[k]));
             KF_CUDA(cudaMemsetAsync(bufs[k]->p, 0, sizeof(float) * (size_t)nb * lds[k], st));
         }
@@ -647,7 +658,7 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
         KF_LAUNCH();
         // ---- S2M: sources -> upward check surface of each leaf
         ctx->phase(KFMM_PH_S2M);
-        KF_CUDA(cudaMemsetAsync(W.up_phi.p, 0, sizeof(float) * (size_t)nb * ld, st));
+        KF_CUDA(cudaMemsetAsync(W.alpha.p, 0, sizeof(float) * (size_t)nb * kup, st));
         if (T.n_leaves) {
             if (sl && dl)
                 check_potential_kernel<true, true><<<T.n_leaves, kChkThreads, 0, st>>>(
@@ -666,23 +677,23 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
                     W.up_chk.as<float>(), ld);
             KF_LAUNCH();
         }
-        // upward equivalent density of the leaves: phi = G h pinv_uc chk
+        // upward densities of the leaves in the singular basis: alpha = G h S^-1 U^T chk
         ctx->phase(KFMM_PH_UP_PINV);
-        KF_TRY(run_gemm(ctx, P.leaves, O.pinv_uc.as<float>(), 0, m, ld, ld, T.leaves.as<int>(), T.leaves.as<int>(),
-                        0, 0, W.up_chk.as<float>(), ld, W.up_phi.as<float>(), ld, geom, (float)ctx->G, 0));
-        // ---- M2M, bottom-up
+        KF_TRY(run_gemm(ctx, P.leaves, O.s2a_u.as<float>(), 0, ku, ld, ld, T.leaves.as<int>(), T.leaves.as<int>(),
+                        0, 0, W.up_chk.as<float>(), ld, W.alpha.as<float>(), kup, geom, (float)ctx->G, 0));
+        // ---- M2M, bottom-up (children of level l into their parents)
         ctx->phase(KFMM_PH_M2M);
         for (int l = T.n_levels - 1; l >= 1; --l)
-            KF_TRY(run_gemm(ctx, P.oct_lvl[l], O.m2m.as<float>(), (int64_t)ld * ld, m, ld, ld, T.oct_child.as<int>(),
-                            T.oct_child.as<int>(), 0, 1, W.up_phi.as<float>(), ld, W.up_phi.as<float>(), ld,
-                            nullptr, 1.f, 2));
-        // ---- compress the upward densities and translate (M2L on the V lists)
+            KF_TRY(run_gemm(ctx, P.oct_lvl[l], O.mb.as<float>(), (int64_t)ku * kup, ku, kup, kup,
+                            T.oct_child.as<int>(), T.oct_child.as<int>(), 0, 1, W.alpha.as<float>(), kup,
+                            W.alpha.as<float>(), kup, nullptr, 1.f, 2));
+        // ---- M2L on the V lists in the shared basis: psi = U_r^T V_u alpha, c += C_v psi
         ctx->phase(KFMM_PH_M2L);
-        KF_TRY(run_gemm(ctx, P.all, O.m2l_vt.as<float>(), 0, r, ld, ld, nullptr, nullptr, 0, 0,
-                        W.up_phi.as<float>(), ld, W.psi.as<float>(), rp, nullptr, 1.f, 0));
+        KF_TRY(run_gemm(ctx, P.all, O.cb.as<float>(), 0, r, kup, kup, nullptr, nullptr, 0, 0, W.alpha.as<float>(),
+                        kup, W.psi.as<float>(), rp, nullptr, 1.f, 0));
         KF_CUDA(cudaMemsetAsync(W.cdn.p, 0, sizeof(float) * (size_t)nb * rp, st));
-        KF_TRY(run_gemm(ctx, P.m2l, O.m2l_c.as<float>(), (int64_t)rp * rp, r, rp, rp, T.vp_src.as<int>(),
-                        T.vp_trg.as<int>(), 0, 0, W.psi.as<float>(), rp, W.cdn.as<float>(), rp, nullptr, 1.f, 2));
+        KF_TRY(run_gemm(ctx, P.m2l, O.m2l_c.as<float>(), (int64_t)r * rp, r, rp, rp, T.vp_src.as<int>(),
+                        T.vp_trg.as<int>(), 0, 0, W.psi.as<float>(), rp, W.cdn.as<float>(), rp, nullptr, 1.f, 2, 1));
         // ---- P2L: X-list sources -> downward check surface
         ctx->phase(KFMM_PH_P2L);
         if (T.n_xboxes) {
@@ -703,16 +714,21 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
                     W.dn_chk.as<float>(), ld);
             KF_LAUNCH();
         }
-        // ---- downward densities: phi_dn = W c + G h pinv_dc chk_dn, then L2L top-down
+        // ---- downward densities in the singular basis: beta = S^-1 U^T (U_r c + G h chk_P2L),
+        //      then L2L top-down, then the equivalent densities needed by the leaf pass
         ctx->phase(KFMM_PH_DOWN);
-        KF_TRY(run_gemm(ctx, P.all, O.m2l_w.as<float>(), 0, m, rp, rp, nullptr, nullptr, 0, 0, W.cdn.as<float>(),
-                        rp, W.dn_phi.as<float>(), ld, nullptr, 1.f, 0));
-        KF_TRY(run_gemm(ctx, P.xboxes, O.pinv_dc.as<float>(), 0, m, ld, ld, T.xboxes.as<int>(), T.xboxes.as<int>(),
-                        0, 0, W.dn_chk.as<float>(), ld, W.dn_phi.as<float>(), ld, geom, (float)ctx->G, 1));
+        KF_TRY(run_gemm(ctx, P.all, O.wb.as<float>(), 0, kd, rp, rp, nullptr, nullptr, 0, 0, W.cdn.as<float>(), rp,
+                        W.beta.as<float>(), kdp, nullptr, 1.f, 0));
+        KF_TRY(run_gemm(ctx, P.xboxes, O.s2a_d.as<float>(), 0, kd, ld, ld, T.xboxes.as<int>(), T.xboxes.as<int>(),
+                        0, 0, W.dn_chk.as<float>(), ld, W.beta.as<float>(), kdp, geom, (float)ctx->G, 1));
         for (int l = 3; l < T.n_levels; ++l)
-            KF_TRY(run_gemm(ctx, P.oct_lvl[l], O.l2l.as<float>(), (int64_t)ld * ld, m, ld, ld, T.oct_child.as<int>(),
-                            T.oct_child.as<int>(), 1, 0, W.dn_phi.as<float>(), ld, W.dn_phi.as<float>(), ld,
-                            nullptr, 1.f, 1));
+            KF_TRY(run_gemm(ctx, P.oct_lvl[l], O.lb.as<float>(), (int64_t)kd * kdp, kd, kdp, kdp,
+                            T.oct_child.as<int>(), T.oct_child.as<int>(), 1, 0, W.beta.as<float>(), kdp,
+                            W.beta.as<float>(), kdp, nullptr, 1.f, 1));
+        KF_TRY(run_gemm(ctx, P.leaves, O.vd.as<float>(), 0, m, kdp, kdp, T.leaves.as<int>(), T.leaves.as<int>(), 0, 0,
+                        W.beta.as<float>(), kdp, W.dn_phi.as<float>(), ld, nullptr, 1.f, 0));
+        KF_TRY(run_gemm(ctx, P.wboxes, O.vu.as<float>(), 0, m, kup, kup, T.wboxes.as<int>(), T.wboxes.as<int>(), 0,
+                        0, W.alpha.as<float>(), kup, W.up_phi.as<float>(), ld, nullptr, 1.f, 0));
         // ---- leaf evaluation
         ctx->phase(KFMM_PH_EVAL);
         const SrcRec *rec = W.src_rec.as<SrcRec>();

@@ -23,7 +23,7 @@ template <typename R> struct KelvinConst {
     R c_S;   // G / (4 pi (1-nu))          (S)
 };
 
-template <typename R> inline KelvinConst<R> make_kelvin(double G, double nu) {
+template <typename R> __host__ __device__ inline KelvinConst<R> make_kelvin(double G, double nu) {
     const double pi = 3.14159265358979323846;
     KelvinConst<R> k;
     k.a34 = R(3.0 - 4.0 * nu);

@@ -199,9 +199,10 @@ static bool sym_eig(int n, double *A, double *w)
     return true;
 }
 
-// Truncated pseudo-inverse through the eigendecomposition of K^T K = V diag(s^2) V^T:
-// pinv(K) = sum_{s_i > rtol s_1} v_i v_i^T K^T / s_i^2.
-static bool pinv(int m, const double *K, double rtol, double *P, int *rank_out)
+// Truncated SVD K = U S V^T through the eigendecomposition of K^T K = V S^2 V^T, keeping
+// s_i > rtol s_1; U = K V S^-1.  U (m x k), s (k), V (m x k), row-major.
+static bool svd_trunc(int m, const double *K, double rtol, std::vector<double> &U, std::vector<double> &s,
+                      std::vector<double> &V, int *rank_out)
 {
     std::vector<double> KtK((size_t)m * m), w(m);
     gemm_tn(m, m, m, K, K, KtK.data());
@@ -209,28 +210,26 @@ static bool pinv(int m, const double *K, double rtol, double *P, int *rank_out)
     const double s1 = std::sqrt(std::max(w[0], 0.0));
     int r = 0;
     while (r < m && w[r] > 0.0 && std::sqrt(w[r]) > rtol * s1) ++r;
-    // B = V_r diag(1/s^2) V_r^T  (m x m), then P = B K^T
-    std::vector<double> Vs((size_t)m * r);
+    s.resize(r);
+    V.assign((size_t)m * r, 0.0);
     for (int i = 0; i < m; ++i)
-        for (int j = 0; j < r; ++j) Vs[(size_t)i * r + j] = KtK[(size_t)i * m + j] / w[j];
-    std::vector<double> B((size_t)m * m);
-#pragma omp parallel for schedule(static)
+        for (int j = 0; j < r; ++j) V[(size_t)i * r + j] = KtK[(size_t)i * m + j];
+    for (int j = 0; j < r; ++j) s[j] = std::sqrt(w[j]);
+    U.assign((size_t)m * r, 0.0);
+    gemm(m, r, m, K, V.data(), U.data());
     for (int i = 0; i < m; ++i)
-        for (int k = 0; k < m; ++k) {
-            double s = 0.0;
-            for (int j = 0; j < r; ++j) s += Vs[(size_t)i * r + j] * KtK[(size_t)k * m + j];
-            B[(size_t)i * m + k] = s;
-        }
-    // P = B K^T: P[i][a] = sum_k B[i][k] K[a][k]
-#pragma omp parallel for schedule(static)
-    for (int i = 0; i < m; ++i)
-        for (int a = 0; a < m; ++a) {
-            double s = 0.0;
-            for (int k = 0; k < m; ++k) s += B[(size_t)i * m + k] * K[(size_t)a * m + k];
-            P[(size_t)i * m + a] = s;
-        }
+        for (int j = 0; j < r; ++j) U[(size_t)i * r + j] /= s[j];
     *rank_out = r;
     return true;
+}
+
+// S^-1 U^T (k x m) from U (m x k) and s (k)
+static std::vector<double> sinv_ut(int m, int k, const std::vector<double> &U, const std::vector<double> &s)
+{
+    std::vector<double> out((size_t)k * m);
+    for (int i = 0; i < k; ++i)
+        for (int a = 0; a < m; ++a) out[(size_t)i * m + a] = U[(size_t)a * k + i] / s[i];
+    return out;
 }
 
 int m2l_directions(int *dirs /* [316][3] or NULL */)
@@ -258,28 +257,38 @@ bool compute_operators(const OpsParams &prm, OpsHost *out)
     out->n_surf = ns;
     const double zero[3] = {0, 0, 0};
     const double ri = prm.r_inner, ro = prm.r_outer, nu = prm.nu;
+    std::vector<double> K((size_t)m * m), tmp, tmp2;
 
-    // check-to-equivalent pseudo-inverses at h = 1
-    std::vector<double> K((size_t)m * m);
-    out->pinv_uc.assign((size_t)m * m, 0.0);
-    out->pinv_dc.assign((size_t)m * m, 0.0);
+    // singular bases of the check-to-equivalent maps at h = G = 1
+    std::vector<double> Uu, su, Vu, Ud, sd, Vd;
     kernel_matrix(out->surf, nu, zero, ro, zero, ri, K.data());  // upward check <- upward equivalent
-    if (!pinv(m, K.data(), prm.pinv_rtol, out->pinv_uc.data(), &out->rank_uc)) return false;
+    if (!svd_trunc(m, K.data(), prm.pinv_rtol, Uu, su, Vu, &out->ku)) return false;
     kernel_matrix(out->surf, nu, zero, ri, zero, ro, K.data());  // downward check <- downward equivalent
-    if (!pinv(m, K.data(), prm.pinv_rtol, out->pinv_dc.data(), &out->rank_dc)) return false;
+    if (!svd_trunc(m, K.data(), prm.pinv_rtol, Ud, sd, Vd, &out->kd)) return false;
+    const int ku = out->ku, kd = out->kd;
+    out->sv_u = su;
+    out->sv_d = sd;
+    out->s2a_u = sinv_ut(m, ku, Uu, su);
+    out->s2a_d = sinv_ut(m, kd, Ud, sd);
+    out->vu = Vu;
+    out->vd = Vd;
 
-    // M2M_o = pinv_uc(parent, half-width 2) K(parent check <- child equivalent)
-    //       = 2 pinv_uc K;  L2L_o = pinv_dc(child) K(child check <- parent equivalent)
-    out->m2m.assign((size_t)8 * m * m, 0.0);
-    out->l2l.assign((size_t)8 * m * m, 0.0);
-    std::vector<double> tmp((size_t)m * m);
+    // M2M in alpha space: parent half-width 2, child 1 at c_o:
+    //   alpha_p = (G 2h) S^-1 U^T K(parent check <- child equiv) / (G h) V alpha_c
+    // L2L in beta space: beta_c = S^-1 U^T K(child check <- parent equiv) V beta_p
+    out->mb.assign((size_t)8 * ku * ku, 0.0);
+    out->lb.assign((size_t)8 * kd * kd, 0.0);
     for (int o = 0; o < 8; ++o) {
         const double co[3] = {(o & 4) ? 1.0 : -1.0, (o & 2) ? 1.0 : -1.0, (o & 1) ? 1.0 : -1.0};
         kernel_matrix(out->surf, nu, zero, 2.0 * ro, co, ri, K.data());
-        gemm(m, m, m, out->pinv_uc.data(), K.data(), tmp.data());
-        for (size_t a = 0; a < tmp.size(); ++a) out->m2m[(size_t)o * m * m + a] = 2.0 * tmp[a];
+        tmp.assign((size_t)m * ku, 0.0);
+        gemm(m, ku, m, K.data(), Vu.data(), tmp.data());
+        gemm(ku, ku, m, out->s2a_u.data(), tmp.data(), out->mb.data() + (size_t)o * ku * ku);
+        for (size_t a = 0; a < (size_t)ku * ku; ++a) out->mb[(size_t)o * ku * ku + a] *= 2.0;
         kernel_matrix(out->surf, nu, co, ri, zero, 2.0 * ro, K.data());
-        gemm(m, m, m, out->pinv_dc.data(), K.data(), out->l2l.data() + (size_t)o * m * m);
+        tmp.assign((size_t)m * kd, 0.0);
+        gemm(m, kd, m, K.data(), Vd.data(), tmp.data());
+        gemm(kd, kd, m, out->s2a_d.data(), tmp.data(), out->lb.data() + (size_t)o * kd * kd);
     }
 
     // M2L: K_v = K(target downward check at 0 <- source upward equivalent at 2v), h = 1
@@ -299,9 +308,9 @@ bool compute_operators(const OpsParams &prm, OpsHost *out)
             const double *ri_ = Kv + (size_t)i * m;
             for (int j = 0; j <= i; ++j) {
                 const double *rj = Kv + (size_t)j * m;
-                double s = 0.0;
-                for (int k = 0; k < m; ++k) s += ri_[k] * rj[k];
-                Gram[(size_t)i * m + j] += s;
+                double acc = 0.0;
+                for (int k = 0; k < m; ++k) acc += ri_[k] * rj[k];
+                Gram[(size_t)i * m + j] += acc;
             }
         }
     for (int i = 0; i < m; ++i)
@@ -315,18 +324,15 @@ bool compute_operators(const OpsParams &prm, OpsHost *out)
     } else {
         while (r < m && lam[r] > 0.0 && std::sqrt(lam[r]) > prm.m2l_rtol * s1) ++r;
     }
+    r = std::min(m, (r + 15) / 16 * 16);  // padding to 16 costs the same, so keep those columns
     if (prm.m2l_rank_max > 0 && r > prm.m2l_rank_max) r = prm.m2l_rank_max;
     r = std::max(r, 1);
     out->rank = r;
     out->m2l_sv.resize(m);
     for (int i = 0; i < m; ++i) out->m2l_sv[i] = std::sqrt(std::max(lam[i], 0.0));
-    // Ur: m x r (first r columns of Gram's eigenvectors)
     std::vector<double> Ur((size_t)m * r);
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < r; ++j) Ur[(size_t)i * r + j] = Gram[(size_t)i * m + j];
-    out->m2l_vt.assign((size_t)r * m, 0.0);  // Ur^T
-    for (int i = 0; i < m; ++i)
-        for (int j = 0; j < r; ++j) out->m2l_vt[(size_t)j * m + i] = Ur[(size_t)i * r + j];
     out->m2l_c.assign((size_t)nd * r * r, 0.0);
     {
         std::vector<double> KU((size_t)m * r);
@@ -335,8 +341,10 @@ bool compute_operators(const OpsParams &prm, OpsHost *out)
             gemm_tn(r, r, m, Ur.data(), KU.data(), out->m2l_c.data() + (size_t)v * r * r);
         }
     }
-    out->m2l_w.assign((size_t)m * r, 0.0);  // pinv_dc Ur
-    gemm(m, r, m, out->pinv_dc.data(), Ur.data(), out->m2l_w.data());
+    out->cb.assign((size_t)r * ku, 0.0);  // U_r^T V_u
+    gemm_tn(r, ku, m, Ur.data(), Vu.data(), out->cb.data());
+    out->wb.assign((size_t)kd * r, 0.0);  // S_d^-1 U_d^T U_r
+    gemm(kd, r, m, out->s2a_d.data(), Ur.data(), out->wb.data());
     return true;
 }
 

@@ -564,6 +564,12 @@ __global__ void compact_kernel(int n, const int *__restrict__ flag, const int *_
     if (b < n && flag[b]) out[pos[b]] = b;
 }
 
+__global__ void mark_kernel(int64_t n, const int *__restrict__ idx, int *__restrict__ flag)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) flag[idx[k]] = 1;
+}
+
 __global__ void nonzero_kernel(int n, const int *__restrict__ cnt, int *__restrict__ flag)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -927,6 +933,18 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         KF_CUDA(T.xboxes.ensure(sizeof(int) * std::max(1, T.n_xboxes)));
         compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, flag.as<int>(), xpos.as<int>(),
                                                                          T.xboxes.as<int>());
+        KF_LAUNCH();
+        // boxes that appear in some W list (their upward densities are evaluated at targets)
+        KF_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * n_boxes, st));
+        if (T.n_w) {
+            mark_kernel<<<grid_for(T.n_w, 256, 1 << 30), 256, 0, st>>>(T.n_w, T.w_idx.as<int>(), flag.as<int>());
+            KF_LAUNCH();
+        }
+        KF_TRY(scan_exclusive(ctx, flag.as<int>(), xpos.as<int>(), n_boxes, total.as<int>()));
+        KF_TRY(read_int(ctx, total.as<int>(), &T.n_wboxes));
+        KF_CUDA(T.wboxes.ensure(sizeof(int) * std::max(1, T.n_wboxes)));
+        compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, flag.as<int>(), xpos.as<int>(),
+                                                                         T.wboxes.as<int>());
         KF_LAUNCH();
         KF_CUDA(cudaStreamSynchronize(st));
     }

@@ -20,8 +20,8 @@ def declared_functions():
 
 
 def test_library_exports_declared_symbols():
-    from paper_1612_04082_gb300 import build
-    path = build.build()
+    import __graft_entry__
+    path = __graft_entry__._build_module().build()
     lib = ctypes.CDLL(path)
     names = declared_functions()
     assert len(names) >= 10, names

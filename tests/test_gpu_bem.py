@@ -1,0 +1,171 @@
+"""GPU parity of the collocation BEM (Eq. num, coef, num2; the two-pass matvec of Sec.
+"Matrix-vector products"; GMRES; Eq. stress_1 and Eq. deriv at interior points) against the
+FP64 oracle's dense operators and solutions.
+
+Tolerances: the FP64 direct GPU operator matches the oracle's dense H u - Gm t to 1e-10
+(rounding order only) and its GMRES solution to 1e-6 (the solver tolerance).  The FMM
+operator (FP32, p = 6) matches to 1e-4 relative L2 and its solution to 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+G0, NU0 = 1.0, 0.3
+
+
+@pytest.fixture(scope="module")
+def K():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_04082_gb300 as K
+    return K
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    V, T = W.icosphere(3)  # 1280 triangles, 3840 unknowns
+    H, Gm = O.bem_assemble(V, T, G0, NU0)
+    nrm, area, cen = O.tri_geometry(V, T)
+    return V, T, H, Gm, nrm, area, cen
+
+
+@pytest.mark.parametrize("op,tol", [("direct", 1e-10), ("fmm", 1e-4)])
+def test_apply_matches_dense_operator(K, sphere, op, tol):
+    V, T, H, Gm, nrm, area, cen = sphere
+    rng = np.random.default_rng(2)
+    u, t = rng.normal(size=(len(T), 3)), rng.normal(size=(len(T), 3))
+    ref = H @ u.reshape(-1) - Gm @ t.reshape(-1)
+    opc = K.BEM_DIRECT_FP64 if op == "direct" else K.BEM_FMM
+    with K.Bem(V, T, opc) as b:
+        b.set_material(K.material_K(G0, NU0), G0)
+        out = np.zeros((len(T), 3))
+        b.apply(u, t, out)
+    assert rel(out.reshape(-1), ref) < tol
+
+
+def test_lame_sphere_direct_fp64_matches_oracle(K, sphere):
+    """Config 1: unit sphere, 1280 triangles, t = +n, GMRES to 1e-8."""
+    V, T, H, Gm, nrm, area, cen = sphere
+    mask = np.zeros((len(T), 3), np.uint8)
+    A, bb = O.bem_system(H, Gm, mask, nrm)
+    x, ok, it, relres = O.gmres(A, bb, tol=1e-10, restart=60, maxit=500)
+    u_ref = O.remove_rigid_modes(x.reshape(-1, 3), cen, area)
+    with K.Bem(V, T, K.BEM_DIRECT_FP64) as b:
+        b.set_material(K.material_K(G0, NU0), G0)
+        b.set_bc(mask, nrm)
+        u = np.zeros((len(T), 3))
+        t = np.zeros((len(T), 3))
+        st = b.solve(u, t, tol=1e-8, restart=60, maxit=500)
+    assert st["converged"] and st["relres"] <= 1e-8
+    u = O.remove_rigid_modes(u, cen, area)
+    assert rel(u, u_ref) < 1e-6
+    assert np.allclose(t, nrm)
+    # Lame closed form u_r = r / (3K) within the O(h) discretisation error
+    Kb = 2 * G0 * (1 + NU0) / (3 * (1 - 2 * NU0))
+    rr = np.linalg.norm(cen, axis=1)
+    ur = np.einsum("ij,ij->i", u, cen / rr[:, None])
+    assert np.abs(ur / (rr / (3 * Kb)) - 1).max() < 0.02
+
+
+def test_lame_sphere_fmm(K, sphere):
+    V, T, H, Gm, nrm, area, cen = sphere
+    mask = np.zeros((len(T), 3), np.uint8)
+    A, bb = O.bem_system(H, Gm, mask, nrm)
+    x, ok, it, relres = O.gmres(A, bb, tol=1e-10, restart=60, maxit=500)
+    u_ref = O.remove_rigid_modes(x.reshape(-1, 3), cen, area)
+    with K.Bem(V, T, K.BEM_FMM) as b:
+        b.set_material(K.material_K(G0, NU0), G0)
+        b.set_bc(mask, nrm)
+        u = np.zeros((len(T), 3))
+        st = b.solve(u, None, tol=1e-6, restart=60)
+    assert st["converged"]
+    u = O.remove_rigid_modes(u, cen, area)
+    assert rel(u, u_ref) < 1e-4
+
+
+def cantilever(n):
+    """Voxel box 2n x n x n cells of size 1/n: clamped at x = 0, unit downward traction on
+    the x = 2 face patch |y - 0.5|, |z - 0.5| <= 0.25, traction-free elsewhere."""
+    V, T = W.box_mesh(2 * n, n, n, 1.0 / n)
+    nrm, area, cen = O.tri_geometry(V, T)
+    mask = np.zeros((len(T), 3), np.uint8)
+    vals = np.zeros((len(T), 3))
+    mask[cen[:, 0] < 1e-9] = 1
+    patch = (cen[:, 0] > 2 - 1e-9) & (np.abs(cen[:, 1] - 0.5) <= 0.25) & (np.abs(cen[:, 2] - 0.5) <= 0.25)
+    vals[patch] = [0.0, 0.0, -1.0]
+    return V, T, mask, vals, nrm, area, cen
+
+
+@pytest.mark.parametrize("op,tol", [("direct", 1e-6), ("fmm", 2e-4)])
+def test_mixed_bc_cantilever(K, op, tol):
+    V, T, mask, vals, nrm, area, cen = cantilever(3)  # 360 triangles
+    H, Gm = O.bem_assemble(V, T, G0, NU0)
+    A, bb = O.bem_system(H, Gm, mask, vals)
+    xd = np.linalg.solve(A, bb)
+    u_ref, t_ref = O.unknowns_to_fields(xd, mask, vals)
+    opc = K.BEM_DIRECT_FP64 if op == "direct" else K.BEM_FMM
+    with K.Bem(V, T, opc) as b:
+        b.set_material(K.material_K(G0, NU0), G0)
+        b.set_bc(mask, vals)
+        rhs = np.zeros((len(T), 3))
+        b.rhs(rhs)
+        assert rel(rhs.reshape(-1), bb) < (1e-10 if op == "direct" else 1e-4)
+        u, t = np.zeros((len(T), 3)), np.zeros((len(T), 3))
+        st = b.solve(u, t, tol=1e-9 if op == "direct" else 1e-6, restart=100, maxit=2000)
+    assert st["converged"]
+    assert rel(u, u_ref) < tol and rel(t, t_ref) < 10 * tol
+
+
+def test_interior_stress_and_td(K):
+    """Uniform tension of the benchmark cube (E = 1, nu = 0.3): interior stress and D^T from
+    the GPU (FMM and FP64 direct) against the oracle's Somigliana sums on the same boundary
+    solution, and the closed form D^T = 1.00227."""
+    E, nu = 1.0, 0.3
+    G = E / (2 * (1 + nu))
+    V, T = W.cube_mesh(4)
+    nrm, area, cen = O.tri_geometry(V, T)
+    trac = nrm @ np.diag([1.0, 0.0, 0.0]).T
+    mask = np.zeros((len(T), 3), np.uint8)
+    u, t, info = O.bem_solve_dense(V, T, mask, trac, G, nu, tol=1e-10, restart=100)
+    rng = np.random.default_rng(4)
+    pts = rng.uniform(0.2, 0.8, size=(500, 3)).astype(np.float32)
+    ref_d, ref_s = O.bem_interior(pts.astype(np.float64), V, T, u, t, G, nu)
+    ref_td, ref_en = O.topo_derivative(ref_s, G, nu)
+    for op, tol in ((K.BEM_DIRECT_FP64, 1e-6), (K.BEM_FMM, 1e-4)):
+        with K.Bem(V, T, op) as b:
+            b.set_material(K.material_K(G, nu), G)
+            b.set_solution(u, t)
+            dsp = np.zeros((len(pts), 3), np.float32)
+            sig = np.zeros((len(pts), 6), np.float32)
+            b.interior(pts, dsp, sig)
+            td = np.zeros(len(pts), np.float32)
+            en = np.zeros(len(pts), np.float32)
+            b.topo_derivative(pts, td, en)
+        assert rel(dsp, ref_d) < tol and rel(sig, ref_s) < tol
+        assert rel(td, ref_td) < 5 * tol and rel(en, ref_en) < 5 * tol
+    assert np.abs(td / 1.0022727272727273 - 1).max() < 0.06
+
+
+def test_bem_errors(K):
+    V = np.array([[0, 0, 0], [1, 0, 0], [2, 0, 0.0]])  # degenerate (zero-area) triangle
+    T = np.array([[0, 1, 2]], np.int32)
+    with K.Bem(V, T, K.BEM_DIRECT_FP64) as b:
+        with pytest.raises(K.KfmmError) as e:
+            b.apply(np.zeros((1, 3)), np.zeros((1, 3)), np.zeros((1, 3)))
+        assert e.value.status == K.KFMM_ERR_INVALID_ARG
+        with pytest.raises(K.KfmmError) as e:
+            b.solve(np.zeros((1, 3)))
+        assert e.value.status == K.KFMM_ERR_NOT_BUILT
+    with pytest.raises(K.KfmmError):
+        K.Bem(V, np.array([[0, 1, 5]], np.int32))  # vertex index out of range

@@ -2,9 +2,14 @@
 FP32), octree invariants and interaction-list coverage, and the KIFMM evaluation of the
 Kelvin sums of Eq. fmm_summation (single layer, double layer, both, and stress).
 
-Tolerances: FP64 direct sum 1e-12 relative L2 (rounding order only); FP32 direct sum 2e-6;
-FMM at p = 6 (152-point surfaces) 1e-4 relative L2, the accuracy BASELINE sets for the
-multipole order; 2e-3 at p = 4.
+The oracle always receives exactly the inputs the GPU receives (points, normals and
+densities rounded to FP32 first): for near-coincident points the 1/r^2 double layer is as
+sensitive to the input rounding as to the arithmetic.
+
+Tolerances: FP64 direct sum 1e-12 relative L2 (rounding order only).  FP32 direct sum 3e-5:
+each output sums ~1800 terms with FP32 rounding (~6e-8 each, growing like sqrt(n)) and
+clouds with near-coincident points cancel large terms (up to ~10x).  FMM at p = 6
+(152-point surfaces): 1e-4 relative L2, the accuracy set for the multipole order.
 """
 import numpy as np
 import pytest
@@ -31,6 +36,11 @@ def dev(a, dtype=torch.float32):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda:0")
 
 
+def r32(a):
+    """The FP32 rounding of an FP64 array, back in FP64 (what the GPU path receives)."""
+    return None if a is None else np.asarray(a, np.float32).astype(np.float64)
+
+
 def rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
@@ -51,18 +61,18 @@ def make_ctx(K, G=G1, nu=NU1, **kw):
 def test_direct_fp64_and_fp32(K, kind, layers):
     rng = np.random.default_rng(3)
     ns, nt = 1777, 913  # ragged sizes, not multiples of the 256-thread tile
-    src = rng.uniform(-1, 1, (ns, 3))
-    trg = np.vstack([rng.uniform(-1, 1, (nt - 5, 3)), src[:5]])  # includes coincident points
+    src = r32(rng.uniform(-1, 1, (ns, 3)))
+    trg = np.vstack([r32(rng.uniform(-1, 1, (nt - 5, 3))), src[:5]])  # includes coincident points
     nrm = rng.normal(size=(ns, 3))
-    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
-    sl = rng.normal(size=(ns, 3)) if layers in ("sl", "both") else None
-    dl = rng.normal(size=(ns, 3)) if layers in ("dl", "both") else None
+    nrm = r32(nrm / np.linalg.norm(nrm, axis=1, keepdims=True))
+    sl = r32(rng.normal(size=(ns, 3))) if layers in ("sl", "both") else None
+    dl = r32(rng.normal(size=(ns, 3))) if layers in ("dl", "both") else None
     no = 3 if kind == "disp" else 6
     kk = K.KFMM_DISP if kind == "disp" else K.KFMM_STRESS
     f = O.direct_disp if kind == "disp" else O.direct_stress
     ref = f(trg, src, nrm, sl, dl, G2, NU2)
     with make_ctx(K, G2, NU2) as c:
-        for prec, dt, tol in ((K.KFMM_FP64, torch.float64, 1e-12), (K.KFMM_FP32, torch.float32, 2e-6)):
+        for prec, dt, tol in ((K.KFMM_FP64, torch.float64, 1e-12), (K.KFMM_FP32, torch.float32, 3e-5)):
             out = torch.zeros(nt, no, dtype=dt, device="cuda:0")
             c.direct(dev(trg, dt), dev(src, dt), dev(nrm, dt), None if sl is None else dev(sl, dt),
                      None if dl is None else dev(dl, dt), out, kk, prec)
@@ -163,6 +173,7 @@ def test_tree_invariants_and_list_coverage(K, cloud):
 
 # ----------------------------------------------------------------- FMM parity
 def fmm_case(K, src, nrm, trg, sl, dl, kind, G, nu, p=6, cap=64, nsample=None):
+    src, nrm, trg, sl, dl = r32(src), r32(nrm), r32(trg), r32(sl), r32(dl)
     no = 3 if kind == K.KFMM_DISP else 6
     with make_ctx(K, G, nu, p=p, leaf_cap=cap) as c:
         c.build(dev(src), dev(nrm), dev(trg))

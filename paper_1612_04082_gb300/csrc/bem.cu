@@ -149,7 +149,13 @@ __global__ void bem_setup_kernel(int64_t nt, const double *__restrict__ verts, c
     int m = 0;
     for (int s = 0; s < 4; ++s)
         for (int g = 0; g < 4; ++g, ++m) {
-            const double3 y = vadd(vadd(vmul(lam[g][0], sub[s][0]), vmul(lam[g][1], sub[s][1])), vmul(lam[g][2], sub[s][2]));
+            // the centre sub-triangle's centroid is the collocation point itself: use the same
+            // bits, so every summation (FP32 FMM, FP64 direct, this local pass) sees r = 0
+            // there and skips it; a barycentric recomputation lands ~1e-17 away instead
+            const double3 y = (s == 3 && g == 0)
+                                  ? xi
+                                  : vadd(vadd(vmul(lam[g][0], sub[s][0]), vmul(lam[g][1], sub[s][1])),
+                                         vmul(lam[g][2], sub[s][2]));
             const double wq = wt[g] * 0.25 * area;
             const int64_t j = 16 * k + m;
             for (int c = 0; c < 3; ++c) {

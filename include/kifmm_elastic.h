@@ -133,6 +133,29 @@ kfmm_status kfmm_direct(kfmm_ctx *ctx, int precision, const void *trg_xyz, int64
                         const void *src_xyz, const void *src_nrm, int64_t nsrc, const void *sl_den,
                         const void *dl_den, int kind, void *out);
 
+/* The same all-pairs sum as kfmm_direct, for callers that cannot allocate device memory:
+ * a process whose device memory is already handed to a caching allocator (a new
+ * cudaMalloc would fail), or code that must not call cudaMalloc / cudaFree while it runs
+ * because those calls synchronise the device.  The paper has no counterpart of this entry
+ * point; it is a deployment variant.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  The sum is
+ *    split over source slices whose partial results go to one fixed 16 MiB scratch array
+ *    in device memory, reserved on every GPU that loads the library until process exit.
+ *  - Every array (trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out) must be device memory;
+ *    host pointers are rejected with KFMM_ERR_INVALID_ARG (staging them would allocate).
+ *  - Limit: ntrg * (3 for DISP, 6 for STRESS) * (4 for FP32, 8 for FP64) bytes must not
+ *    exceed 16 MiB (e.g. 699,050 FP32 or 349,525 FP64 displacement targets); larger
+ *    sizes are rejected with KFMM_ERR_INVALID_ARG.  nsrc is not limited.
+ *  - The first call on a device looks up the scratch array's device address (once per
+ *    device, with that device current); make that first call before any stream capture.
+ *  - All calls share the scratch array, which keeps the last call's contents; each call
+ *    writes every entry it reads.  Calls that overlap on the GPU (other streams, other host
+ *    threads) race on it: the caller must serialise them.
+ *  - Work is enqueued on the context stream; the call does not synchronise. */
+kfmm_status kfmm_direct_noalloc(kfmm_ctx *ctx, int precision, const void *trg_xyz, int64_t ntrg,
+                                const void *src_xyz, const void *src_nrm, int64_t nsrc,
+                                const void *sl_den, const void *dl_den, int kind, void *out);
+
 kfmm_status kfmm_get_stats(const kfmm_ctx *ctx, kfmm_stats *st);
 
 /* Copies of the built tree for inspection (host arrays sized from kfmm_get_stats):

@@ -66,6 +66,8 @@ _sig = {
     "kfmm_build": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64]),
     "kfmm_eval": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]),
     "kfmm_direct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]),
+    "kfmm_direct_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_int,
+                                           _vp]),
     "kfmm_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(kfmm_stats)]),
     "kfmm_export_tree": (ctypes.c_int, [_vp] + [_vp] * 7),
     "kfmm_export_list": (ctypes.c_int, [_vp, ctypes.c_char, _vp, _vp, ctypes.POINTER(_i64)]),
@@ -154,6 +156,17 @@ def kfmm_eval(ctx, sl_den, dl_den, out, kind=KFMM_DISP, ncol=1):
 def kfmm_direct(ctx, trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out, kind=KFMM_DISP, precision=KFMM_FP32):
     _check(ctx, _lib.kfmm_direct(ctx, int(precision), _ptr(trg_xyz), _nrows(trg_xyz), _ptr(src_xyz), _ptr(src_nrm),
                                  _nrows(src_xyz), _ptr(sl_den), _ptr(dl_den), int(kind), _ptr(out)))
+    return out
+
+
+def kfmm_direct_noalloc(ctx, trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out, kind=KFMM_DISP,
+                        precision=KFMM_FP32):
+    """kfmm_direct for callers that cannot allocate device memory: device arrays only, partial
+    sums in the library's fixed 16 MiB scratch array.  Enqueued on the context stream (no
+    synchronisation); overlapping calls race on the shared scratch."""
+    _check(ctx, _lib.kfmm_direct_noalloc(ctx, int(precision), _ptr(trg_xyz), _nrows(trg_xyz), _ptr(src_xyz),
+                                         _ptr(src_nrm), _nrows(src_xyz), _ptr(sl_den), _ptr(dl_den), int(kind),
+                                         _ptr(out)))
     return out
 
 

@@ -107,6 +107,10 @@ struct Operators {
     DevBuf s2a_d;     // [kd][3n]   downward check -> beta (x G h)
     DevBuf lb;        // [8][kd][kd] parent beta -> child beta
     DevBuf vd;        // [3n][kd]   beta -> downward equivalent density
+    // M2L translations as BF16 split-pair operand images for the tensor cores:
+    // [316][ceil(r/128)][hi, lo][128 x rp] in the UMMA core-matrix layout (see tc_gemm.cuh)
+    DevBuf m2l_tc;
+    int m2l_tc_mtiles = 0;
 };
 
 // Octree and interaction lists (device arrays unless noted).
@@ -165,6 +169,7 @@ struct Work {
     DevBuf up_chk;    // float [n_boxes][3n]   upward check potentials (leaves)
     DevBuf alpha;     // float [n_boxes][ku]   upward densities in the singular basis
     DevBuf psi;       // float [n_boxes][rank] M2L inputs
+    DevBuf psi2;      // bf16 [n_boxes][2][rank] their split pairs (tensor-core M2L)
     DevBuf cdn;       // float [n_boxes][rank] M2L outputs
     DevBuf dn_chk;    // float [n_boxes][3n]   downward check potentials (X-list boxes)
     DevBuf beta;      // float [n_boxes][kd]   downward densities in the singular basis
@@ -186,6 +191,9 @@ struct FmmPlans {
     GemmPlan all, leaves, xboxes, wboxes, m2l;
     std::vector<GemmPlan> oct_lvl;  // per level: children grouped by octant (M2M, L2L)
     DevBuf geom;                    // float4 per box: centre x, y, z and half-width
+    DevBuf m2l_items;               // int4 {direction, row tile, c0, c1} for the tensor-core M2L
+    int n_m2l_items = 0;
+    DevBuf err;                     // int: set by kernels whose bounded waits gave up
 };
 
 // Per-phase CUDA-event timing (off unless enabled).

@@ -15,11 +15,31 @@
 #include "common.cuh"
 #include "kelvin.cuh"
 #include "precompute.h"
+#include "tc_gemm.cuh"
 #include "util.cuh"
 
 namespace kfmm {
 
 static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// largest padded M2L rank whose operand tiles fit the shared memory of one CTA
+static inline bool tc_rank_ok(int rp) { return tc::smem_bytes(rp) <= 227 * 1024; }
+
+// round-to-nearest-even FP32 -> BF16 (finite inputs)
+static inline uint16_t host_bf16(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+static inline float host_bf16_to_f32(uint16_t h)
+{
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
 
 // ------------------------------------------------------------------------------------
 // Operators: FP64 host precompute (cached per parameter set) and FP32 upload
@@ -96,6 +116,32 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
     KF_TRY(upload_padded(ctx, O.vd, H->vd.data(), 1, m, kd, kdp, m));
     O.ku = ku;
     O.kd = kd;
+    // tensor-core images of the M2L translations: rows in tiles of 128, split pairs
+    O.m2l_tc_mtiles = 0;
+    if (ctx->opt.m2l_tensor_cores && tc_rank_ok(rp)) {
+        const int nmt = (r + tc::BM - 1) / tc::BM;
+        const size_t half = tc::half_bytes(tc::BM, rp) / 2;  // uint16 per half
+        std::vector<uint16_t> img((size_t)316 * nmt * 2 * half, 0);
+        for (int d = 0; d < 316; ++d)
+            for (int mt = 0; mt < nmt; ++mt) {
+                uint16_t *hi = img.data() + ((size_t)d * nmt + mt) * 2 * half, *lo = hi + half;
+                for (int i = 0; i < tc::BM; ++i) {
+                    const int row = mt * tc::BM + i;
+                    if (row >= r) continue;
+                    for (int k = 0; k < r; ++k) {
+                        const float v = (float)H->m2l_c[((size_t)d * r + row) * r + k];
+                        const uint16_t h = host_bf16(v);
+                        const uint16_t l = host_bf16(v - host_bf16_to_f32(h));
+                        const uint32_t off = tc::core_offset(i, k, tc::BM) / 2;
+                        hi[off] = h;
+                        lo[off] = l;
+                    }
+                }
+            }
+        KF_CUDA(O.m2l_tc.ensure(sizeof(uint16_t) * img.size()));
+        KF_CUDA(cudaMemcpy(O.m2l_tc.p, img.data(), sizeof(uint16_t) * img.size(), cudaMemcpyHostToDevice));
+        O.m2l_tc_mtiles = nmt;
+    }
     O.p = prm.p;
     O.nu = prm.nu;
     O.r_inner = prm.r_inner;
@@ -571,7 +617,22 @@ static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
             ge[d] = T.vdir_off[d + 1];
         }
         KF_TRY(make_plan(ctx, P.m2l, gm, gb, ge));
+        // tensor-core work items: per direction and row tile, column chunks that share one
+        // load of the translation's operand tile
+        const int nmt = ctx->ops.m2l_tc_mtiles;
+        std::vector<int4> items;
+        const int chunk = 1024;
+        for (int d = 0; d < 316 && nmt > 0; ++d)
+            for (int c = T.vdir_off[d]; c < T.vdir_off[d + 1]; c += chunk)
+                for (int mt = 0; mt < nmt; ++mt) items.push_back(make_int4(d, mt, c, std::min(c + chunk, T.vdir_off[d + 1])));
+        P.n_m2l_items = (int)items.size();
+        if (P.n_m2l_items) {
+            KF_CUDA(P.m2l_items.ensure(sizeof(int4) * items.size()));
+            KF_CUDA(cudaMemcpy(P.m2l_items.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+        }
     }
+    KF_CUDA(P.err.ensure(sizeof(int)));
+    KF_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), st));
     P.oct_lvl.clear();
     P.oct_lvl.resize(T.n_levels);
     for (int l = 1; l < T.n_levels; ++l) {
@@ -692,8 +753,26 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
         KF_TRY(run_gemm(ctx, P.all, O.cb.as<float>(), 0, r, kup, kup, nullptr, nullptr, 0, 0, W.alpha.as<float>(),
                         kup, W.psi.as<float>(), rp, nullptr, 1.f, 0));
         KF_CUDA(cudaMemsetAsync(W.cdn.p, 0, sizeof(float) * (size_t)nb * rp, st));
-        KF_TRY(run_gemm(ctx, P.m2l, O.m2l_c.as<float>(), (int64_t)r * rp, r, rp, rp, T.vp_src.as<int>(),
-                        T.vp_trg.as<int>(), 0, 0, W.psi.as<float>(), rp, W.cdn.as<float>(), rp, nullptr, 1.f, 2, 1));
+        if (O.m2l_tc_mtiles > 0) {
+            if (P.n_m2l_items) {
+                KF_CUDA(W.psi2.ensure(sizeof(uint16_t) * 2 * (size_t)nb * rp));
+                const int64_t nchunk = (int64_t)nb * (rp / 8);
+                tc::split_pairs_kernel<<<(unsigned)((nchunk + 255) / 256), 256, 0, st>>>(W.psi.as<float>(), nb, rp,
+                                                                                         W.psi2.as<uint16_t>());
+                KF_LAUNCH();
+                const uint32_t smem = tc::smem_bytes(rp);
+                KF_CUDA(cudaFuncSetAttribute(tc::tc_gather_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+                tc::TcArgs ta{O.m2l_tc.as<uint16_t>(), O.m2l_tc_mtiles, r, rp, P.m2l_items.as<int4>(),
+                              T.vp_src.as<int>(), T.vp_trg.as<int>(), W.psi2.as<uint16_t>(), W.cdn.as<float>(), rp,
+                              P.err.as<int>()};
+                tc::tc_gather_gemm_kernel<<<P.n_m2l_items, tc::THREADS, smem, st>>>(ta);
+                KF_LAUNCH();
+            }
+        } else {
+            KF_TRY(run_gemm(ctx, P.m2l, O.m2l_c.as<float>(), (int64_t)r * rp, r, rp, rp, T.vp_src.as<int>(),
+                            T.vp_trg.as<int>(), 0, 0, W.psi.as<float>(), rp, W.cdn.as<float>(), rp, nullptr, 1.f, 2, 1));
+        }
         // ---- P2L: X-list sources -> downward check surface
         ctx->phase(KFMM_PH_P2L);
         if (T.n_xboxes) {
@@ -774,6 +853,16 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
             KF_LAUNCH();
         }
         ctx->phase(-1);
+    }
+    if (O.m2l_tc_mtiles > 0) {
+        // the tensor-core kernel bounds its barrier waits and reports a time-out here
+        int herr = 0;
+        KF_CUDA(cudaMemcpyAsync(&herr, P.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaStreamSynchronize(st));
+        if (herr) {
+            KF_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), st));
+            return ctx->fail(KFMM_ERR_DEVICE_TIMEOUT, "M2L tensor-core kernel: a bounded barrier wait gave up");
+        }
     }
     return KFMM_OK;
 }

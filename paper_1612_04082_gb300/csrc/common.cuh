@@ -175,6 +175,8 @@ struct Work {
     DevBuf beta;      // float [n_boxes][kd]   downward densities in the singular basis
     DevBuf up_phi;    // float [n_boxes][3n]   upward equivalent densities (W-list boxes)
     DevBuf dn_phi;    // float [n_boxes][3n]   downward equivalent densities (leaves)
+    DevBuf scan_tmp[4];  // per-level partial sums of the device scan
+    DevBuf tree_tmp[12]; // tree-build temporaries (sort ping-pong, histograms, child ranges...)
     DevBuf stage_in[4];  // staging of host inputs
     DevBuf stage_out;
     DevBuf tmp;

@@ -67,19 +67,20 @@ __global__ void scan_total_kernel(const int *last_in, const int *out, int n, int
 __global__ void copy_last_kernel(const int *in, int n, int *dst) { *dst = n > 0 ? in[n - 1] : 0; }
 }  // namespace
 
-kfmm_status scan_exclusive(kfmm_ctx *ctx, const int *in, int *out, int n, int *total)
+// Temporaries live in the context's scan scratch (grow-only, one slot per recursion level),
+// so a scan neither allocates nor synchronises in steady state.
+static kfmm_status scan_level(kfmm_ctx *ctx, const int *in, int *out, int n, int *total, int depth)
 {
     if (n <= 0) {
         if (total) KF_CUDA(cudaMemsetAsync(total, 0, sizeof(int), ctx->stream));
         return KFMM_OK;
     }
+    if (depth >= 4) return ctx->fail(KFMM_ERR_INTERNAL, "scan: too many levels");
     const int tiles = (n + kScanTile - 1) / kScanTile;
-    DevBuf lastbuf;
-    int *last = nullptr;
+    DevBuf &slot = ctx->work.scan_tmp[depth];
+    KF_CUDA(slot.ensure(sizeof(int) * (size_t)(tiles + 1)));
+    int *last = slot.as<int>() + tiles;  // in[n-1], kept because in may alias out
     if (total) {
-        // keep in[n-1] (in may alias out)
-        KF_CUDA(lastbuf.ensure(sizeof(int)));
-        last = lastbuf.as<int>();
         copy_last_kernel<<<1, 1, 0, ctx->stream>>>(in, n, last);
         KF_LAUNCH();
     }
@@ -87,21 +88,23 @@ kfmm_status scan_exclusive(kfmm_ctx *ctx, const int *in, int *out, int n, int *t
         scan_tile_kernel<<<1, kScanThreads, 0, ctx->stream>>>(in, out, n, nullptr);
         KF_LAUNCH();
     } else {
-        DevBuf sums;
-        KF_CUDA(sums.ensure(sizeof(int) * tiles));
-        scan_tile_kernel<<<tiles, kScanThreads, 0, ctx->stream>>>(in, out, n, sums.as<int>());
+        int *sums = slot.as<int>();
+        scan_tile_kernel<<<tiles, kScanThreads, 0, ctx->stream>>>(in, out, n, sums);
         KF_LAUNCH();
-        KF_TRY(scan_exclusive(ctx, sums.as<int>(), sums.as<int>(), tiles, nullptr));
-        scan_add_kernel<<<tiles, kScanThreads, 0, ctx->stream>>>(out, n, sums.as<int>());
+        KF_TRY(scan_level(ctx, sums, sums, tiles, nullptr, depth + 1));
+        scan_add_kernel<<<tiles, kScanThreads, 0, ctx->stream>>>(out, n, sums);
         KF_LAUNCH();
-        KF_CUDA(cudaStreamSynchronize(ctx->stream));  // sums is freed on return
     }
     if (total) {
         scan_total_kernel<<<1, 1, 0, ctx->stream>>>(last, out, n, total);
         KF_LAUNCH();
-        KF_CUDA(cudaStreamSynchronize(ctx->stream));  // lastbuf is freed on return
     }
     return KFMM_OK;
+}
+
+kfmm_status scan_exclusive(kfmm_ctx *ctx, const int *in, int *out, int n, int *total)
+{
+    return scan_level(ctx, in, out, n, total, 0);
 }
 
 kfmm_status read_int(kfmm_ctx *ctx, const int *dptr, int *host)
@@ -282,7 +285,7 @@ kfmm_status radix_sort(kfmm_ctx *ctx, DevBuf &key, DevBuf &val, int n, int bits)
 {
     if (n <= 1) return KFMM_OK;
     const int ntiles = (n + kSortTile - 1) / kSortTile;
-    DevBuf k2, v2, hist;
+    DevBuf &k2 = ctx->work.tree_tmp[0], &v2 = ctx->work.tree_tmp[1], &hist = ctx->work.tree_tmp[2];
     KF_CUDA(k2.ensure(sizeof(uint64_t) * n));
     KF_CUDA(v2.ensure(sizeof(int) * n));
     KF_CUDA(hist.ensure(sizeof(int) * 256 * (size_t)ntiles));
@@ -303,7 +306,6 @@ kfmm_status radix_sort(kfmm_ctx *ctx, DevBuf &key, DevBuf &val, int n, int bits)
         KF_CUDA(cudaMemcpyAsync(key.p, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
         KF_CUDA(cudaMemcpyAsync(val.p, va, sizeof(int) * n, cudaMemcpyDeviceToDevice, ctx->stream));
     }
-    KF_CUDA(cudaStreamSynchronize(ctx->stream));  // temporaries are freed on return
     return KFMM_OK;
 }
 
@@ -337,31 +339,31 @@ __global__ void split_count_kernel(int first, int nb, int level, int L, int cap,
                                    const uint64_t *__restrict__ tkey, int4 *__restrict__ crange,
                                    int *__restrict__ ccount)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    const int b = first + i;
+    // 8 lanes per box: lane o finds where child o starts (its own binary search), the next
+    // lane's start is where child o ends
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(gt >> 3), o = (int)(gt & 7);
+    const bool valid = i < nb;
+    const int b = first + (valid ? i : 0);
     const int2 s = bsrc[b], t = btrg[b];
-    const int ns = s.y - s.x, nt = t.y - t.x;
-    int cnt = 0;
-    if ((ns > cap || nt > cap) && level < L) {
+    const bool split = valid && (s.y - s.x > cap || t.y - t.x > cap) && level < L;
+    int sb = s.x, tb = t.x;
+    if (split && o > 0) {
         const int sh = 3 * (L - level - 1);
-        const uint64_t base = bkey[b] << 3;
-        int sb[9], tb[9];
-        sb[0] = s.x;
-        tb[0] = t.x;
-        sb[8] = s.y;
-        tb[8] = t.y;
-        for (int o = 1; o < 8; ++o) {
-            uint64_t lo = (base | (uint64_t)o) << sh;
-            sb[o] = lower_bound_u64(skey, sb[o - 1], s.y, lo);
-            tb[o] = lower_bound_u64(tkey, tb[o - 1], t.y, lo);
-        }
-        for (int o = 0; o < 8; ++o) {
-            crange[8 * i + o] = make_int4(sb[o], sb[o + 1], tb[o], tb[o + 1]);
-            if (sb[o + 1] > sb[o] || tb[o + 1] > tb[o]) ++cnt;
-        }
+        const uint64_t lo = ((bkey[b] << 3) | (uint64_t)o) << sh;
+        sb = lower_bound_u64(skey, s.x, s.y, lo);
+        tb = lower_bound_u64(tkey, t.x, t.y, lo);
     }
-    ccount[i] = cnt;
+    int se = __shfl_down_sync(0xffffffffu, sb, 1, 8), te = __shfl_down_sync(0xffffffffu, tb, 1, 8);
+    if (o == 7) {
+        se = s.y;
+        te = t.y;
+    }
+    const bool nonempty = split && (se > sb || te > tb);
+    const unsigned m = __ballot_sync(0xffffffffu, nonempty);
+    if (!valid) return;
+    if (split) crange[8 * i + o] = make_int4(sb, se, tb, te);
+    if (o == 0) ccount[i] = __popc((m >> (threadIdx.x & 24)) & 0xffu);
 }
 
 __global__ void split_emit_kernel(int first, int nb, int next_first, const int4 *__restrict__ crange,
@@ -596,29 +598,42 @@ __device__ __forceinline__ int dir_index(int dx, int dy, int dz)
     return full - inner_before;
 }
 
-__global__ void vdir_count_kernel(int n_boxes, const int *__restrict__ vo, const int *__restrict__ vi,
-                                  const int4 *__restrict__ anchor, int *__restrict__ dcount,
-                                  int *__restrict__ pair_dir)
+constexpr int kVdirBox = 128;  // target boxes per block when grouping V pairs by direction
+
+// Direction of every V pair and the per-block direction counts, bhist[d * nblk + block].
+__global__ void vdir_hist_kernel(int n_boxes, const int *__restrict__ vo, const int *__restrict__ vi,
+                                 const int4 *__restrict__ anchor, int *__restrict__ pair_dir, int *__restrict__ bhist,
+                                 int nblk)
 {
+    __shared__ int h[316];
+    for (int i = threadIdx.x; i < 316; i += blockDim.x) h[i] = 0;
+    __syncthreads();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_boxes) return;
-    const int4 ab = anchor[b];
-    for (int k = vo[b]; k < vo[b + 1]; ++k) {
-        const int4 as = anchor[vi[k]];
-        int d = dir_index(as.x - ab.x, as.y - ab.y, as.z - ab.z);
-        pair_dir[k] = d;
-        atomicAdd(&dcount[d], 1);
+    if (b < n_boxes) {
+        const int4 ab = anchor[b];
+        for (int k = vo[b]; k < vo[b + 1]; ++k) {
+            const int4 as = anchor[vi[k]];
+            const int d = dir_index(as.x - ab.x, as.y - ab.y, as.z - ab.z);
+            pair_dir[k] = d;
+            atomicAdd(&h[d], 1);
+        }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 316; i += blockDim.x) bhist[(size_t)i * nblk + blockIdx.x] = h[i];
 }
 
-__global__ void vdir_scatter_kernel(int n_boxes, const int *__restrict__ vo, const int *__restrict__ vi,
-                                    const int *__restrict__ pair_dir, int *__restrict__ cursor,
-                                    int *__restrict__ psrc, int *__restrict__ ptrg)
+// Place the pairs of this block from its scanned offsets (order within a block arbitrary).
+__global__ void vdir_place_kernel(int n_boxes, const int *__restrict__ vo, const int *__restrict__ vi,
+                                  const int *__restrict__ pair_dir, const int *__restrict__ boff, int nblk,
+                                  int *__restrict__ psrc, int *__restrict__ ptrg)
 {
+    __shared__ int cur[316];
+    for (int i = threadIdx.x; i < 316; i += blockDim.x) cur[i] = boff[(size_t)i * nblk + blockIdx.x];
+    __syncthreads();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_boxes) return;
     for (int k = vo[b]; k < vo[b + 1]; ++k) {
-        int pos = atomicAdd(&cursor[pair_dir[k]], 1);
+        const int pos = atomicAdd(&cur[pair_dir[k]], 1);
         psrc[pos] = vi[k];
         ptrg[pos] = b;
     }
@@ -692,7 +707,8 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     if (nsrc + ntrg > (int64_t)1 << 30) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many points (limit 2^30)");
 
     // ---- bounding cube and NaN check
-    DevBuf part;
+    DevBuf *tmp = ctx->work.tree_tmp;  // persistent scratch: slots 0-2 sort, 3-11 below
+    DevBuf &part = tmp[3];
     KF_CUDA(part.ensure(sizeof(float) * 7 * kBBoxBlocks));
     bbox_kernel<<<kBBoxBlocks, kBBoxThreads, 0, st>>>(src_xyz, nsrc, trg_xyz, ntrg, src_nrm,
                                                       part.as<float>());
@@ -771,14 +787,14 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     T.level_off.assign(1, 0);
     T.level_off.push_back(1);
     int n_boxes = 1;
-    DevBuf crange, ccount, coff, total;
+    DevBuf &crange = tmp[4], &ccount = tmp[5], &coff = tmp[6], &total = tmp[7];
     KF_CUDA(total.ensure(sizeof(int)));
     for (int level = 0;; ++level) {
         const int first = T.level_off[level], nb = T.level_off[level + 1] - first;
         KF_CUDA(crange.ensure(sizeof(int4) * 8 * (size_t)nb));
         KF_CUDA(ccount.ensure(sizeof(int) * (size_t)nb));
         KF_CUDA(coff.ensure(sizeof(int) * (size_t)nb));
-        split_count_kernel<<<grid_for(nb, 128, 1 << 30), 128, 0, st>>>(
+        split_count_kernel<<<grid_for(8 * (int64_t)nb, 128, 1 << 30), 128, 0, st>>>(
             first, nb, level, L, cap, T.box_key.as<uint64_t>(), T.box_src.as<int2>(), T.box_trg.as<int2>(),
             T.src_key.as<uint64_t>(), T.trg_key.as<uint64_t>(), crange.as<int4>(), ccount.as<int>());
         KF_LAUNCH();
@@ -814,7 +830,7 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     leaf_flag_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_child.as<int>(),
                                                                        T.box_leaf.as<int>());
     KF_LAUNCH();
-    DevBuf pos;
+    DevBuf &pos = tmp[8];
     KF_CUDA(pos.ensure(sizeof(int) * n_boxes));
     KF_TRY(scan_exclusive(ctx, T.box_leaf.as<int>(), pos.as<int>(), n_boxes, total.as<int>()));
     KF_TRY(read_int(ctx, total.as<int>(), &T.n_leaves));
@@ -824,7 +840,7 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     KF_LAUNCH();
 
     // ---- colleagues
-    DevBuf loff;
+    DevBuf &loff = tmp[9];
     KF_CUDA(loff.ensure(sizeof(int) * T.level_off.size()));
     KF_CUDA(cudaMemcpyAsync(loff.p, T.level_off.data(), sizeof(int) * T.level_off.size(),
                             cudaMemcpyHostToDevice, st));
@@ -843,7 +859,7 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     KF_LAUNCH();
 
     // ---- lists: count, scan, fill
-    DevBuf cnt, ovf;
+    DevBuf &cnt = tmp[10], &ovf = tmp[11];
     KF_CUDA(cnt.ensure(sizeof(int) * 4 * (size_t)n_boxes));
     KF_CUDA(ovf.ensure(sizeof(int)));
     KF_CUDA(cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
@@ -877,32 +893,34 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
 
     // ---- V pairs grouped by direction
     {
-        DevBuf dcount, pair_dir;
-        KF_CUDA(dcount.ensure(sizeof(int) * 317));
+        // per-block direction histograms in shared memory, one scan over (direction, block),
+        // then each block scatters its pairs from its own offsets (no contended atomics)
+        const int nblk = (n_boxes + kVdirBox - 1) / kVdirBox;
+        DevBuf &bhist = tmp[4], &pair_dir = tmp[5];
+        KF_CUDA(bhist.ensure(sizeof(int) * (316 * (size_t)nblk + 1)));
         KF_CUDA(pair_dir.ensure(sizeof(int) * std::max<int64_t>(1, T.n_v)));
-        KF_CUDA(cudaMemsetAsync(dcount.p, 0, sizeof(int) * 317, st));
-        vdir_count_kernel<<<grid_for(n_boxes, 128, 1 << 30), 128, 0, st>>>(
-            n_boxes, T.v_off.as<int>(), T.v_idx.as<int>(), T.box_anchor.as<int4>(), dcount.as<int>(),
-            pair_dir.as<int>());
+        vdir_hist_kernel<<<nblk, kVdirBox, 0, st>>>(n_boxes, T.v_off.as<int>(), T.v_idx.as<int>(),
+                                                    T.box_anchor.as<int4>(), pair_dir.as<int>(), bhist.as<int>(), nblk);
         KF_LAUNCH();
-        std::vector<int> hc(316);
-        KF_CUDA(cudaMemcpyAsync(hc.data(), dcount.p, sizeof(int) * 316, cudaMemcpyDeviceToHost, st));
+        KF_TRY(scan_exclusive(ctx, bhist.as<int>(), bhist.as<int>(), 316 * nblk, nullptr));
+        // direction offsets for the host: the scanned value at each direction's first block
+        std::vector<int> hoff(316);
+        KF_CUDA(cudaMemcpy2DAsync(hoff.data(), sizeof(int), bhist.p, sizeof(int) * nblk, sizeof(int), 316,
+                                  cudaMemcpyDeviceToHost, st));
         KF_CUDA(cudaStreamSynchronize(st));
         T.vdir_off.assign(317, 0);
-        for (int d = 0; d < 316; ++d) T.vdir_off[d + 1] = T.vdir_off[d] + hc[d];
-        KF_CUDA(cudaMemcpyAsync(dcount.p, T.vdir_off.data(), sizeof(int) * 316, cudaMemcpyHostToDevice, st));
+        for (int d = 0; d < 316; ++d) T.vdir_off[d] = hoff[d];
+        T.vdir_off[316] = (int)T.n_v;
         KF_CUDA(T.vp_src.ensure(sizeof(int) * std::max<int64_t>(1, T.n_v)));
         KF_CUDA(T.vp_trg.ensure(sizeof(int) * std::max<int64_t>(1, T.n_v)));
-        vdir_scatter_kernel<<<grid_for(n_boxes, 128, 1 << 30), 128, 0, st>>>(
-            n_boxes, T.v_off.as<int>(), T.v_idx.as<int>(), pair_dir.as<int>(), dcount.as<int>(),
-            T.vp_src.as<int>(), T.vp_trg.as<int>());
+        vdir_place_kernel<<<nblk, kVdirBox, 0, st>>>(n_boxes, T.v_off.as<int>(), T.v_idx.as<int>(), pair_dir.as<int>(),
+                                                     bhist.as<int>(), nblk, T.vp_src.as<int>(), T.vp_trg.as<int>());
         KF_LAUNCH();
-        KF_CUDA(cudaStreamSynchronize(st));
     }
     // ---- octant groups per level (M2M / L2L)
     {
         const int ng = 8 * T.n_levels;
-        DevBuf gc;
+        DevBuf &gc = tmp[6];
         KF_CUDA(gc.ensure(sizeof(int) * (ng + 1)));
         KF_CUDA(cudaMemsetAsync(gc.p, 0, sizeof(int) * (ng + 1), st));
         oct_count_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_anchor.as<int4>(),
@@ -918,11 +936,10 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         oct_scatter_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_anchor.as<int4>(),
                                                                              gc.as<int>(), T.oct_child.as<int>());
         KF_LAUNCH();
-        KF_CUDA(cudaStreamSynchronize(st));
     }
     // ---- boxes with X lists
     {
-        DevBuf flag, xpos;
+        DevBuf &flag = tmp[3], &xpos = tmp[8];
         KF_CUDA(flag.ensure(sizeof(int) * n_boxes));
         KF_CUDA(xpos.ensure(sizeof(int) * n_boxes));
         nonzero_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, cnt.as<int>() + 3 * (size_t)n_boxes,
@@ -946,11 +963,10 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, flag.as<int>(), xpos.as<int>(),
                                                                          T.wboxes.as<int>());
         KF_LAUNCH();
-        KF_CUDA(cudaStreamSynchronize(st));
     }
     // ---- work counts
     {
-        DevBuf acc;
+        DevBuf &acc = tmp[4];
         KF_CUDA(acc.ensure(sizeof(unsigned long long) * 3));
         KF_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 3, st));
         work_count_kernel<<<grid_for(n_boxes, 128, 1 << 30), 128, 0, st>>>(
@@ -965,8 +981,6 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         T.l2p_pairs = (int64_t)h[1];
         T.p2l_pairs = (int64_t)h[2];
     }
-    // level offsets and lists are final; keep the device copy of level_off alive in work
-    KF_CUDA(cudaStreamSynchronize(st));
     T.built = true;
     return KFMM_OK;
 }

@@ -77,8 +77,12 @@ typedef struct kfmm_options {
     double m2l_rtol;    /* relative singular-value cutoff of the shared M2L basis (3e-5);
                            the rank is rounded up to a multiple of 16; 0 keeps full rank    */
     int m2l_rank_max;   /* upper bound on the M2L rank (0 = no bound)                       */
-    int m2l_tensor_cores; /* 1: M2L on the tcgen05 tensor cores with BF16 split pairs and
-                           FP32 accumulation (rank <= 288); 0: FP32 SIMT (1)                 */
+    int m2l_tensor_cores; /* bit field of the products run on the tcgen05 tensor cores with
+                           FP32 accumulation; clear bits use FP32 SIMT:
+                           1 = M2L translations, BF16 split pairs (rank <= 288);
+                           2 = check-to-equivalent factors, 4 = M2M and L2L,
+                           8 = equivalent-density and M2L basis changes, all three with
+                           three-term BF16 splits (FP32-grade) (15)                          */
     int device;         /* CUDA device ordinal (0)                                          */
 } kfmm_options;
 

@@ -49,7 +49,7 @@ void kfmm_default_options(kfmm_options *opt)
     opt->pinv_rtol = 1e-7;
     opt->m2l_rtol = 3e-5;
     opt->m2l_rank_max = 0;
-    opt->m2l_tensor_cores = 1;
+    opt->m2l_tensor_cores = 15;
     opt->device = 0;
 }
 

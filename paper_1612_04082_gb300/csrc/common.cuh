@@ -111,6 +111,14 @@ struct Operators {
     // [316][ceil(r/128)][hi, lo][128 x rp] in the UMMA core-matrix layout (see tc_gemm.cuh)
     DevBuf m2l_tc;
     int m2l_tc_mtiles = 0;
+    // box operators for the K-streamed tensor-core product: [n_mat][n_mtile][n_kc][2][128 x 64]
+    struct TcOp {
+        DevBuf img;
+        int n_mat = 0, M = 0, K = 0, n_mtile = 0, n_kc = 0;
+        bool on = false;  // product runs on the tensor cores
+    };
+    bool box_tc = false;  // any box operator on the tensor cores
+    TcOp tc_s2a_u, tc_mb, tc_cb, tc_vu, tc_wb, tc_s2a_d, tc_lb, tc_vd;
 };
 
 // Octree and interaction lists (device arrays unless noted).
@@ -186,6 +194,10 @@ struct Work {
 struct GemmPlan {
     DevBuf tiles;  // int4 {matrix index, first column, end column, 0}
     int n_tiles = 0;
+    std::vector<int4> host_tiles;
+    // tensor-core work items {matrix, row tile, first column, end column}, by row-tile count
+    DevBuf tc_items[9];
+    int n_tc_items[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
 };
 
 struct FmmPlans {

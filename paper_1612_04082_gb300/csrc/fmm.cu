@@ -41,6 +41,43 @@ static inline float host_bf16_to_f32(uint16_t h)
     return f;
 }
 
+// tensor-core image of nmat row-major [M][K] FP64 matrices, three BF16 terms per entry
+// (hi = bf16(a), mid = bf16(a - hi), lo = bf16(a - hi - mid)): [mat][mtile][kc][term][128 x KC]
+static kfmm_status upload_tc_op(kfmm_ctx *ctx, Operators::TcOp &op, const double *A, int nmat, int M, int K)
+{
+    op.n_mat = nmat;
+    op.M = M;
+    op.K = K;
+    op.n_mtile = (M + tc::BM - 1) / tc::BM;
+    op.n_kc = (K + tc::KC - 1) / tc::KC;
+    const size_t term = tc::A_TERM / 2;  // uint16 per term of a chunk
+    std::vector<uint16_t> img((size_t)nmat * op.n_mtile * op.n_kc * tc::NTERM * term, 0);
+    for (int g = 0; g < nmat; ++g)
+        for (int mt = 0; mt < op.n_mtile; ++mt)
+            for (int kc = 0; kc < op.n_kc; ++kc) {
+                uint16_t *t0 = img.data() + (((size_t)g * op.n_mtile + mt) * op.n_kc + kc) * tc::NTERM * term;
+                for (int i = 0; i < tc::BM; ++i) {
+                    const int row = mt * tc::BM + i;
+                    if (row >= M) break;
+                    for (int kk = 0; kk < tc::KC; ++kk) {
+                        const int k = kc * tc::KC + kk;
+                        if (k >= K) break;
+                        double rem = A[((size_t)g * M + row) * K + k];
+                        const uint32_t off = tc::core_offset(i, kk, tc::BM) / 2;
+                        for (int t = 0; t < tc::NTERM; ++t) {
+                            const uint16_t h = host_bf16((float)rem);
+                            t0[t * term + off] = h;
+                            rem -= (double)host_bf16_to_f32(h);
+                        }
+                    }
+                }
+            }
+    KF_CUDA(op.img.ensure(sizeof(uint16_t) * img.size()));
+    KF_CUDA(cudaMemcpy(op.img.p, img.data(), sizeof(uint16_t) * img.size(), cudaMemcpyHostToDevice));
+    op.on = true;
+    return KFMM_OK;
+}
+
 // ------------------------------------------------------------------------------------
 // Operators: FP64 host precompute (cached per parameter set) and FP32 upload
 // ------------------------------------------------------------------------------------
@@ -118,7 +155,7 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
     O.kd = kd;
     // tensor-core images of the M2L translations: rows in tiles of 128, split pairs
     O.m2l_tc_mtiles = 0;
-    if (ctx->opt.m2l_tensor_cores && tc_rank_ok(rp)) {
+    if ((ctx->opt.m2l_tensor_cores & 1) && tc_rank_ok(rp)) {
         const int nmt = (r + tc::BM - 1) / tc::BM;
         const size_t half = tc::half_bytes(tc::BM, rp) / 2;  // uint16 per half
         std::vector<uint16_t> img((size_t)316 * nmt * 2 * half, 0);
@@ -142,6 +179,27 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
         KF_CUDA(cudaMemcpy(O.m2l_tc.p, img.data(), sizeof(uint16_t) * img.size(), cudaMemcpyHostToDevice));
         O.m2l_tc_mtiles = nmt;
     }
+    // tensor-core images of the box operators (K streamed in chunks, any size)
+    // bit 1: check-to-equivalent factors, bit 2: M2M and L2L, bit 3: basis changes
+    const int tcb = ctx->opt.m2l_tensor_cores;
+    O.box_tc = false;
+    for (Operators::TcOp *op : {&O.tc_s2a_u, &O.tc_mb, &O.tc_cb, &O.tc_vu, &O.tc_wb, &O.tc_s2a_d, &O.tc_lb, &O.tc_vd})
+        op->on = false;
+    if (tcb & 2) {
+        KF_TRY(upload_tc_op(ctx, O.tc_s2a_u, H->s2a_u.data(), 1, ku, m));
+        KF_TRY(upload_tc_op(ctx, O.tc_s2a_d, H->s2a_d.data(), 1, kd, m));
+    }
+    if (tcb & 4) {
+        KF_TRY(upload_tc_op(ctx, O.tc_mb, H->mb.data(), 8, ku, ku));
+        KF_TRY(upload_tc_op(ctx, O.tc_lb, H->lb.data(), 8, kd, kd));
+    }
+    if (tcb & 8) {
+        KF_TRY(upload_tc_op(ctx, O.tc_cb, H->cb.data(), 1, r, ku));
+        KF_TRY(upload_tc_op(ctx, O.tc_wb, H->wb.data(), 1, kd, r));
+        KF_TRY(upload_tc_op(ctx, O.tc_vu, H->vu.data(), 1, m, ku));
+        KF_TRY(upload_tc_op(ctx, O.tc_vd, H->vd.data(), 1, m, kd));
+    }
+    O.box_tc = (tcb & 14) != 0;
     O.p = prm.p;
     O.nu = prm.nu;
     O.r_inner = prm.r_inner;
@@ -598,6 +656,56 @@ static kfmm_status make_plan(kfmm_ctx *ctx, GemmPlan &pl, const std::vector<int>
         KF_CUDA(pl.tiles.ensure(sizeof(int4) * t.size()));
         KF_CUDA(cudaMemcpy(pl.tiles.p, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
     }
+    pl.host_tiles = t;
+    for (int k = 0; k < 9; ++k) pl.n_tc_items[k] = -1;
+    return KFMM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// box operators on the tensor cores (K-streamed kernel of tc_gemm.cuh)
+// ------------------------------------------------------------------------------------
+static_assert(GBN == tc::BN, "tensor-core box items are the 64-column tiles of the GEMM plans");
+
+static kfmm_status run_tc_box(kfmm_ctx *ctx, GemmPlan &pl, const Operators::TcOp &op, const int *src,
+                              const int *dst, int src_par, int dst_par, const float *X, int ldx, float *Y, int ldy,
+                              const float4 *geom, float alpha, int mode)
+{
+    if (pl.n_tiles == 0) return KFMM_OK;
+    // work items for this row-tile count (built once per plan)
+    const int nm = op.n_mtile;
+    if (nm < 1 || nm > 8) return ctx->fail(KFMM_ERR_INTERNAL, "tensor-core box product: too many row tiles");
+    if (ldx % 8 != 0) return ctx->fail(KFMM_ERR_INTERNAL, "tensor-core box product: source rows not padded to 8");
+    if (pl.n_tc_items[nm] < 0) {
+        std::vector<int4> items;
+        for (const int4 &t : pl.host_tiles)
+            for (int mt = 0; mt < nm; ++mt) items.push_back(make_int4(t.x, mt, t.y, t.z));
+        pl.n_tc_items[nm] = (int)items.size();
+        KF_CUDA(pl.tc_items[nm].ensure(sizeof(int4) * std::max<size_t>(1, items.size())));
+        KF_CUDA(cudaMemcpy(pl.tc_items[nm].p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    }
+    tc::TcBoxArgs a;
+    a.A = op.img.as<uint16_t>();
+    a.n_mtile = nm;
+    a.n_kc = op.n_kc;
+    a.M = op.M;
+    a.items = pl.tc_items[nm].as<int4>();
+    a.src_idx = src;
+    a.dst_idx = dst;
+    a.parent = ctx->tree.box_parent.as<int>();
+    a.src_par = src_par;
+    a.dst_par = dst_par;
+    a.X = X;
+    a.ldx = ldx;
+    a.Y = Y;
+    a.ldy = ldy;
+    a.geom = geom;
+    a.alpha = alpha;
+    a.mode = mode;
+    a.err = ctx->plans.err.as<int>();
+    const uint32_t smem = tc::box_smem_bytes();
+    KF_CUDA(cudaFuncSetAttribute(tc::tc_box_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tc::tc_box_gemm_kernel<<<pl.n_tc_items[nm], tc::BOX_THREADS, smem, ctx->stream>>>(a);
+    KF_LAUNCH();
     return KFMM_OK;
 }
 
@@ -707,6 +815,15 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
         P.valid = true;
     }
     KF_CUDA(W.src_rec.ensure(sizeof(SrcRec) * ns));
+    // one box-operator product: tensor cores (three-term split) or FP32 SIMT
+    auto box_gemm = [&](GemmPlan &pl, const Operators::TcOp &top, const float *A, int64_t a_stride,
+                        int M, int K, int lda, const int *src, const int *dst, int src_par, int dst_par,
+                        const float *X, int ldx, float *Y, int ldy, const float4 *gm, float alpha,
+                        int mode) -> kfmm_status {
+        if (top.on)
+            return run_tc_box(ctx, pl, top, src, dst, src_par, dst_par, X, ldx, Y, ldy, gm, alpha, mode);
+        return run_gemm(ctx, pl, A, a_stride, M, K, lda, src, dst, src_par, dst_par, X, ldx, Y, ldy, gm, alpha, mode);
+    };
     const auto kc = make_kelvin<float>(ctx->G, ctx->nu);
     const float4 *geom = P.geom.as<float4>();
     const int ldd = 3 * ncol;
@@ -740,18 +857,19 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
         }
         // upward densities of the leaves in the singular basis: alpha = G h S^-1 U^T chk
         ctx->phase(KFMM_PH_UP_PINV);
-        KF_TRY(run_gemm(ctx, P.leaves, O.s2a_u.as<float>(), 0, ku, ld, ld, T.leaves.as<int>(), T.leaves.as<int>(),
-                        0, 0, W.up_chk.as<float>(), ld, W.alpha.as<float>(), kup, geom, (float)ctx->G, 0));
+        KF_TRY(box_gemm(P.leaves, O.tc_s2a_u, O.s2a_u.as<float>(), 0, ku, ld, ld, T.leaves.as<int>(),
+                        T.leaves.as<int>(), 0, 0, W.up_chk.as<float>(), ld, W.alpha.as<float>(), kup, geom,
+                        (float)ctx->G, 0));
         // ---- M2M, bottom-up (children of level l into their parents)
         ctx->phase(KFMM_PH_M2M);
         for (int l = T.n_levels - 1; l >= 1; --l)
-            KF_TRY(run_gemm(ctx, P.oct_lvl[l], O.mb.as<float>(), (int64_t)ku * kup, ku, kup, kup,
-                            T.oct_child.as<int>(), T.oct_child.as<int>(), 0, 1, W.alpha.as<float>(), kup,
-                            W.alpha.as<float>(), kup, nullptr, 1.f, 2));
+            KF_TRY(box_gemm(P.oct_lvl[l], O.tc_mb, O.mb.as<float>(), (int64_t)ku * kup, ku, kup, kup, T.oct_child.as<int>(),
+                            T.oct_child.as<int>(), 0, 1, W.alpha.as<float>(), kup, W.alpha.as<float>(), kup, nullptr,
+                            1.f, 2));
         // ---- M2L on the V lists in the shared basis: psi = U_r^T V_u alpha, c += C_v psi
         ctx->phase(KFMM_PH_M2L);
-        KF_TRY(run_gemm(ctx, P.all, O.cb.as<float>(), 0, r, kup, kup, nullptr, nullptr, 0, 0, W.alpha.as<float>(),
-                        kup, W.psi.as<float>(), rp, nullptr, 1.f, 0));
+        KF_TRY(box_gemm(P.all, O.tc_cb, O.cb.as<float>(), 0, r, kup, kup, nullptr, nullptr, 0, 0,
+                        W.alpha.as<float>(), kup, W.psi.as<float>(), rp, nullptr, 1.f, 0));
         KF_CUDA(cudaMemsetAsync(W.cdn.p, 0, sizeof(float) * (size_t)nb * rp, st));
         if (O.m2l_tc_mtiles > 0) {
             if (P.n_m2l_items) {
@@ -796,18 +914,20 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
         // ---- downward densities in the singular basis: beta = S^-1 U^T (U_r c + G h chk_P2L),
         //      then L2L top-down, then the equivalent densities needed by the leaf pass
         ctx->phase(KFMM_PH_DOWN);
-        KF_TRY(run_gemm(ctx, P.all, O.wb.as<float>(), 0, kd, rp, rp, nullptr, nullptr, 0, 0, W.cdn.as<float>(), rp,
-                        W.beta.as<float>(), kdp, nullptr, 1.f, 0));
-        KF_TRY(run_gemm(ctx, P.xboxes, O.s2a_d.as<float>(), 0, kd, ld, ld, T.xboxes.as<int>(), T.xboxes.as<int>(),
-                        0, 0, W.dn_chk.as<float>(), ld, W.beta.as<float>(), kdp, geom, (float)ctx->G, 1));
+        KF_TRY(box_gemm(P.all, O.tc_wb, O.wb.as<float>(), 0, kd, rp, rp, nullptr, nullptr, 0, 0,
+                        W.cdn.as<float>(), rp, W.beta.as<float>(), kdp, nullptr, 1.f, 0));
+        KF_TRY(box_gemm(P.xboxes, O.tc_s2a_d, O.s2a_d.as<float>(), 0, kd,
+                        ld, ld, T.xboxes.as<int>(), T.xboxes.as<int>(), 0, 0, W.dn_chk.as<float>(), ld,
+                        W.beta.as<float>(), kdp, geom, (float)ctx->G, 1));
         for (int l = 3; l < T.n_levels; ++l)
-            KF_TRY(run_gemm(ctx, P.oct_lvl[l], O.lb.as<float>(), (int64_t)kd * kdp, kd, kdp, kdp,
-                            T.oct_child.as<int>(), T.oct_child.as<int>(), 1, 0, W.beta.as<float>(), kdp,
-                            W.beta.as<float>(), kdp, nullptr, 1.f, 1));
-        KF_TRY(run_gemm(ctx, P.leaves, O.vd.as<float>(), 0, m, kdp, kdp, T.leaves.as<int>(), T.leaves.as<int>(), 0, 0,
-                        W.beta.as<float>(), kdp, W.dn_phi.as<float>(), ld, nullptr, 1.f, 0));
-        KF_TRY(run_gemm(ctx, P.wboxes, O.vu.as<float>(), 0, m, kup, kup, T.wboxes.as<int>(), T.wboxes.as<int>(), 0,
-                        0, W.alpha.as<float>(), kup, W.up_phi.as<float>(), ld, nullptr, 1.f, 0));
+            KF_TRY(box_gemm(P.oct_lvl[l], O.tc_lb, O.lb.as<float>(),
+                            (int64_t)kd * kdp, kd, kdp, kdp, T.oct_child.as<int>(), T.oct_child.as<int>(), 1, 0,
+                            W.beta.as<float>(), kdp, W.beta.as<float>(), kdp, nullptr, 1.f, 1));
+        KF_TRY(box_gemm(P.leaves, O.tc_vd, O.vd.as<float>(), 0, m, kdp, kdp, T.leaves.as<int>(),
+                        T.leaves.as<int>(), 0, 0, W.beta.as<float>(), kdp, W.dn_phi.as<float>(), ld, nullptr, 1.f, 0));
+        KF_TRY(box_gemm(P.wboxes, O.tc_vu, O.vu.as<float>(), 0, m, kup,
+                        kup, T.wboxes.as<int>(), T.wboxes.as<int>(), 0, 0, W.alpha.as<float>(), kup,
+                        W.up_phi.as<float>(), ld, nullptr, 1.f, 0));
         // ---- leaf evaluation
         ctx->phase(KFMM_PH_EVAL);
         const SrcRec *rec = W.src_rec.as<SrcRec>();
@@ -854,14 +974,14 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
         }
         ctx->phase(-1);
     }
-    if (O.m2l_tc_mtiles > 0) {
-        // the tensor-core kernel bounds its barrier waits and reports a time-out here
+    if (O.m2l_tc_mtiles > 0 || O.box_tc) {
+        // the tensor-core kernels bound their barrier waits and report a time-out here
         int herr = 0;
         KF_CUDA(cudaMemcpyAsync(&herr, P.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         KF_CUDA(cudaStreamSynchronize(st));
         if (herr) {
             KF_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), st));
-            return ctx->fail(KFMM_ERR_DEVICE_TIMEOUT, "M2L tensor-core kernel: a bounded barrier wait gave up");
+            return ctx->fail(KFMM_ERR_DEVICE_TIMEOUT, "tensor-core product: a bounded barrier wait gave up");
         }
     }
     return KFMM_OK;

@@ -354,5 +354,279 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gather_gemm_kernel(TcArgs g)
     if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+// ======================================================================================
+// K-streamed variant for the box operators (check-to-equivalent factors, M2M, L2L, basis
+// changes), whose K does not fit shared memory and whose products feed GMRES: FP32-grade
+// accuracy is needed there, so both operands are split into THREE BF16 terms
+// (a = a_h + a_m + a_l exactly for FP32 input; the operator's terms are taken from its FP64
+// value) and each product is accumulated as hh + hm + mh + hl + lh + mm (the dropped terms
+// are ~2^-26 of the product).  The tensor cores round their sums toward zero, and these
+// products cancel heavily (high singular modes), so the rounding bias would add up over K:
+// the leading term hh goes to a main accumulator restarted every FB chunks (two buffers,
+// alternating) whose block sums are added in FP32 registers with round-to-nearest; the five
+// small terms go to a third accumulator kept over the whole K range.
+//
+// One work item = one matrix, one row tile of 128, up to BN = 64 gathered columns.  K runs in
+// chunks of KC = 32 through three pipeline stages: the operator chunk (3 terms, 24 KB)
+// arrives by bulk copy one chunk ahead; the FP32 source rows are loaded into registers two
+// chunks ahead, split, and stored in the core-matrix layout.  Output modes: store, add
+// (exclusive rows), atomic add; each column may be scaled by alpha * geom[dst].w.
+// ======================================================================================
+constexpr int KC = 32;
+constexpr int NTERM = 3;
+constexpr int BOX_STAGES = 3;
+constexpr int BOX_THREADS = 256;  // = BN * KC / 8: one 8-value group of one column per thread
+constexpr int BOX_FB = 2;               // chunks per block of the main accumulator
+constexpr int BOX_TMEM_COLS = 4 * BN;  // main x2 | small terms | unused (power of two)
+
+constexpr uint32_t A_TERM = BM * KC * 2;  // bytes of one term of an operator chunk
+constexpr uint32_t B_TERM = BN * KC * 2;  // bytes of one term of a source chunk
+constexpr uint32_t A_CHUNK = NTERM * A_TERM;
+constexpr uint32_t STAGE_BYTES = NTERM * (A_TERM + B_TERM);
+
+struct TcBoxArgs {
+    const uint16_t *A;     // [n_mat][n_mtile][n_kc][term][BM x KC] core-matrix images
+    int n_mtile, n_kc;
+    int M;                 // valid rows
+    const int4 *items;     // {matrix, mtile, c0, c1} with c1 - c0 <= BN
+    const int *src_idx, *dst_idx, *parent;
+    int src_par, dst_par;  // map the index through parent[] first
+    const float *X;        // FP32 source rows; values past K must be finite (the operator is 0 there)
+    int ldx;               // row length of X, a multiple of 8
+    float *Y;
+    int ldy;
+    const float4 *geom;    // column scale alpha * geom[dst].w when non-null
+    float alpha;
+    int mode;              // 0 store, 1 add, 2 atomic add
+    int *err;
+};
+
+__host__ __device__ inline uint32_t box_smem_bytes() { return BOX_STAGES * STAGE_BYTES + 128 + 2 * BN * 4; }
+
+// three-term BF16 split of 8 FP32 values, stored as three 16-byte core-matrix rows
+__device__ __forceinline__ void store_split3(unsigned char *dst, uint32_t term_stride, const float4 &x0,
+                                             const float4 &x1)
+{
+    const float v[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    uint32_t h[4], m[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t ph = 0, pm = 0, pl = 0;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float a = v[2 * q + e];
+            const __nv_bfloat16 th = __float2bfloat16_rn(a);
+            const float r1 = a - __bfloat162float(th);
+            const __nv_bfloat16 tm = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 tl = __float2bfloat16_rn(r1 - __bfloat162float(tm));
+            ph |= (uint32_t)__bfloat16_as_ushort(th) << (16 * e);
+            pm |= (uint32_t)__bfloat16_as_ushort(tm) << (16 * e);
+            pl |= (uint32_t)__bfloat16_as_ushort(tl) << (16 * e);
+        }
+        h[q] = ph;
+        m[q] = pm;
+        l[q] = pl;
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(dst + term_stride) = make_uint4(m[0], m[1], m[2], m[3]);
+    *reinterpret_cast<uint4 *>(dst + 2 * term_stride) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__global__ void __launch_bounds__(BOX_THREADS, 2) tc_box_gemm_kernel(TcBoxArgs g)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *barA = reinterpret_cast<uint64_t *>(sm + BOX_STAGES * STAGE_BYTES);  // [BOX_STAGES]
+    uint64_t *barM = barA + BOX_STAGES;                                             // [BOX_STAGES]
+    uint32_t *holder = reinterpret_cast<uint32_t *>(barM + BOX_STAGES);
+    int *s_fail = reinterpret_cast<int *>(holder + 1);
+    int *s_src = reinterpret_cast<int *>(sm + BOX_STAGES * STAGE_BYTES + 128);
+    int *s_dst = s_src + BN;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, chalf = warp >> 2;
+    const int4 item = g.items[blockIdx.x];
+    const int ncols = min(BN, item.w - item.z);
+    const int n_kc = g.n_kc;
+
+    if (warp == 0) tmem_alloc(holder, BOX_TMEM_COLS);
+    if (tid < BN) {
+        int sidx = -1, didx = -1;
+        if (tid < ncols) {
+            sidx = g.src_idx ? g.src_idx[item.z + tid] : item.z + tid;
+            didx = g.dst_idx ? g.dst_idx[item.z + tid] : item.z + tid;
+            if (g.src_par) sidx = g.parent[sidx];
+            if (g.dst_par) didx = g.parent[didx];
+        }
+        s_src[tid] = sidx;
+        s_dst[tid] = didx;
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 2 * BOX_STAGES; ++i) mbar_init(&barA[i], 1);
+        *s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *holder;
+    const uint32_t idesc = idesc_bf16(BM, BN);
+    const unsigned char *Abase = reinterpret_cast<const unsigned char *>(g.A) +
+                                 ((size_t)item.x * g.n_mtile + item.y) * n_kc * (size_t)A_CHUNK;
+
+    // this thread's piece of every source chunk: column col, values kb*8 .. kb*8 + 7
+    const int col = tid % BN, kb = tid / BN;
+    const int xrow = s_src[col];
+    const float *xp = xrow >= 0 ? g.X + (size_t)xrow * g.ldx + kb * 8 : nullptr;
+    const uint32_t boff = core_offset(col, kb * 8, BN);
+    auto load_x = [&](int kc, float4 &x0, float4 &x1) {
+        if (xp && kc * KC + kb * 8 + 8 <= g.ldx) {
+            x0 = __ldg(reinterpret_cast<const float4 *>(xp + kc * KC));
+            x1 = __ldg(reinterpret_cast<const float4 *>(xp + kc * KC + 4));
+        } else {
+            x0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            x1 = x0;
+        }
+    };
+    auto issue_a = [&](int kc, int s) {  // one thread
+        unsigned char *st = sm + (size_t)s * STAGE_BYTES;
+        const unsigned char *src = Abase + (size_t)kc * A_CHUNK;
+        mbar_expect_tx(&barA[s], A_CHUNK);
+#pragma unroll
+        for (int t = 0; t < NTERM; ++t) bulk_g2s(st + t * A_TERM, src + t * A_TERM, A_TERM, &barA[s]);
+    };
+    auto issue_mmas = [&](int s, int kc) {  // one thread
+        const unsigned char *st = sm + (size_t)s * STAGE_BYTES;
+        const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + NTERM * A_TERM);
+        const uint32_t a_lbo = (BM / 8) * 128, b_lbo = (BN / 8) * 128;
+#pragma unroll
+        for (int ks = 0; ks < KC / 16; ++ks) {
+            const uint32_t ao = (uint32_t)(2 * ks) * a_lbo, bo = (uint32_t)(2 * ks) * b_lbo;
+            uint64_t ad[NTERM], bd[NTERM];
+#pragma unroll
+            for (int t = 0; t < NTERM; ++t) {
+                ad[t] = smem_desc(a0 + t * A_TERM + ao, a_lbo, 128);
+                bd[t] = smem_desc(b0 + t * B_TERM + bo, b_lbo, 128);
+            }
+            const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+            const uint32_t acc_main = (kc % BOX_FB > 0 || ks > 0) ? 1u : 0u;
+            const uint32_t t_main = tmem + (uint32_t)(((kc / BOX_FB) & 1) * BN);
+            const uint32_t t_small = tmem + (uint32_t)(2 * BN);
+            mma_bf16(t_small, ad[1], bd[1], idesc, acc);
+            mma_bf16(t_small, ad[0], bd[2], idesc, 1u);
+            mma_bf16(t_small, ad[2], bd[0], idesc, 1u);
+            mma_bf16(t_small, ad[0], bd[1], idesc, 1u);
+            mma_bf16(t_small, ad[1], bd[0], idesc, 1u);
+            mma_bf16(t_main, ad[0], bd[0], idesc, acc_main);
+        }
+    };
+
+    // this thread's output row (TMEM lane) and 32 columns; block sums of the main accumulator
+    const uint32_t t_lane = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(chalf * (BN / 2));
+    float racc[BN / 2];
+#pragma unroll
+    for (int i = 0; i < BN / 2; ++i) racc[i] = 0.f;
+    auto add_acc = [&](uint32_t col0) {
+#pragma unroll
+        for (int h = 0; h < BN / 2; h += 16) {
+            float t[16];
+            tmem_ld16(t_lane + col0 + (uint32_t)h, t);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) racc[h + i] += t[i];
+        }
+    };
+
+    int loadsA = 0, commits = 0;  // operator chunks requested (thread 0), MMA groups committed
+    // one K chunk; returns false (uniformly) after a failed wait
+    auto step = [&](int kc, float4 &x0, float4 &x1) -> bool {
+        const int s = kc % BOX_STAGES;
+        bool w = true;
+        // stage s was last read by the MMAs of chunk kc - 3
+        if (kc >= BOX_STAGES) w = mbar_wait(&barM[s], (uint32_t)((kc - BOX_STAGES) / BOX_STAGES) & 1u);
+        // the MMAs of chunk kc - 3 are complete: block b, whose last chunk that is, can be
+        // folded into the registers; block b + 2 reuses its buffer no earlier than chunk kc
+        if (w && kc >= BOX_FB + 2 && (kc - 2) % BOX_FB == 0) {
+            tc_fence_after();
+            add_acc((uint32_t)((((kc - 2) / BOX_FB - 1) & 1) * BN));
+        }
+        if (w) store_split3(sm + (size_t)s * STAGE_BYTES + NTERM * A_TERM + boff, B_TERM, x0, x1);
+        if (kc + 2 < n_kc) load_x(kc + 2, x0, x1);
+        if (tid == 0 && kc + 1 < n_kc && !*s_fail) {
+            // the next operator chunk goes to the stage last read by the MMAs of chunk kc - 2
+            const int ns = (kc + 1) % BOX_STAGES;
+            const bool w2 = kc + 1 < BOX_STAGES ||
+                            mbar_wait(&barM[ns], (uint32_t)((kc + 1 - BOX_STAGES) / BOX_STAGES) & 1u);
+            if (w2) {
+                issue_a(kc + 1, ns);
+                ++loadsA;
+            } else {
+                w = false;
+            }
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        const bool bad = __syncthreads_or(!w || (tid == 0 && *s_fail)) != 0;
+        tc_fence_after();
+        if (bad) return false;
+        if (tid == 0) {
+            if (mbar_wait(&barA[s], (uint32_t)(kc / BOX_STAGES) & 1u)) issue_mmas(s, kc);
+            else *s_fail = 1;
+            mma_commit(&barM[s]);
+        }
+        ++commits;
+        return true;
+    };
+
+    float4 xa0, xa1, xb0, xb1;
+    load_x(0, xa0, xa1);
+    if (n_kc > 1) load_x(1, xb0, xb1);
+    if (tid == 0) {
+        issue_a(0, 0);
+        loadsA = 1;
+    }
+    bool ok = true;
+    for (int kc = 0; kc < n_kc && ok; kc += 2) {
+        ok = step(kc, xa0, xa1);
+        if (ok && kc + 1 < n_kc) ok = step(kc + 1, xb0, xb1);
+    }
+    if (ok) {
+        // all products: wait for the last commit, then the epilogue
+        const int kl = n_kc - 1;
+        const bool w = mbar_wait(&barM[kl % BOX_STAGES], (uint32_t)(kl / BOX_STAGES) & 1u);
+        ok = __syncthreads_or(!w || (tid == 0 && *s_fail)) == 0;
+        tc_fence_after();
+    }
+    if (ok) {
+        // blocks not folded in the loop (flush step kc = (b + 1) FB + 2 >= n_kc), then the
+        // small terms
+        const int nblk = (n_kc + BOX_FB - 1) / BOX_FB;
+        for (int b = max(0, nblk - 2); b < nblk; ++b)
+            if ((b + 1) * BOX_FB + 2 >= n_kc) add_acc((uint32_t)((b & 1) * BN));
+        add_acc((uint32_t)(2 * BN));
+        const int row = item.y * BM + quad * 32 + lane;
+        if (row < g.M) {
+#pragma unroll
+            for (int k = 0; k < BN / 2; ++k) {
+                const int d = s_dst[chalf * (BN / 2) + k];
+                if (d < 0) continue;
+                const float a = g.geom ? g.alpha * g.geom[d].w : g.alpha;
+                float *y = g.Y + (size_t)d * g.ldy + row;
+                if (g.mode == 0) *y = a * racc[k];
+                else if (g.mode == 1) *y += a * racc[k];
+                else atomicAdd(y, a * racc[k]);
+            }
+        }
+    } else if (tid == 0) {
+        // record the failure, then wait (bounded) for the products and operator copies still
+        // in flight before the shared and tensor memory are released
+        atomicExch(g.err, 1);
+        if (commits > 0) mbar_wait(&barM[(commits - 1) % BOX_STAGES], (uint32_t)((commits - 1) / BOX_STAGES) & 1u);
+        for (int c = max(0, loadsA - BOX_STAGES); c < loadsA; ++c)
+            mbar_wait(&barA[c % BOX_STAGES], (uint32_t)(c / BOX_STAGES) & 1u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, BOX_TMEM_COLS);
+}
+
 }  // namespace tc
 }  // namespace kfmm

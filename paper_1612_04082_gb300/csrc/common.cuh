@@ -121,6 +121,9 @@ struct Operators {
     TcOp tc_s2a_u, tc_mb, tc_cb, tc_vu, tc_wb, tc_s2a_d, tc_lb, tc_vd;
 };
 
+// points on the surface of a p x p x p lattice (equivalent and check surfaces)
+inline int surface_points(int p) { return 6 * (p - 1) * (p - 1) + 2; }
+
 // Octree and interaction lists (device arrays unless noted).
 struct Tree {
     bool built = false;
@@ -169,6 +172,9 @@ struct Tree {
     std::vector<int> oct_off;   // host: [(n_levels) * 8 + 1] offsets (level-major, then octant)
     int64_t n_u = 0, n_v = 0, n_w = 0, n_x = 0;
     int64_t p2p_pairs = 0, l2p_pairs = 0, p2l_pairs = 0;
+    // a W-list box with at most this many sources is evaluated directly at the targets (exact
+    // and cheaper than its n_surf equivalent points); larger ones through their densities
+    int w_direct_max = 0;
 };
 
 // Per-evaluation work arrays.
@@ -208,6 +214,9 @@ struct FmmPlans {
     DevBuf m2l_items;               // int4 {direction, row tile, c0, c1} for the tensor-core M2L
     int n_m2l_items = 0;
     DevBuf err;                     // int: set by kernels whose bounded waits gave up
+    DevBuf eval_items;              // int4 {leaf box, first target, first segment, end segment}
+    DevBuf eval_cnt;                // int per leaf: items, then their offsets
+    int n_eval_items = 0;
 };
 
 // Per-phase CUDA-event timing (off unless enabled).

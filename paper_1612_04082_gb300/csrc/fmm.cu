@@ -464,49 +464,58 @@ __global__ void __launch_bounds__(256) gemm_gather_kernel(GemmArgs g)
 
 // ------------------------------------------------------------------------------------
 // leaf evaluation: L2P (downward equivalent density of the leaf), M2P (upward equivalent
-// densities of the W list), P2P (sources of the U list).  One CTA of 4 warps per leaf;
-// each lane owns up to two targets (lane, lane + 32) of a 64-target chunk; the warps split
-// every source set four ways and reduce through shared memory at the end.
+// densities of the W list), P2P (sources of the U list).
+//
+// Work items (one warp each, one warp per CTA): a chunk of at most 64 targets of a leaf and a
+// range of its source segments -- segment 0 the leaf's own downward density (L2P), then the
+// W-list boxes (M2P through the upward density, or directly from the sources of a box with
+// at most w_direct_max of them), then the U-list leaves (P2P).  Heavy leaves (long W and U
+// lists) are cut into several items of bounded cost whose results are added atomically into
+// the zeroed output, so no warp runs far longer than the others.  A chunk
+// of more than 32 targets gives each lane two targets (lane, lane + 32); a chunk of nt <= 32
+// targets splits the 32 lanes into nsl = 32 / nt source slices, lane = slice * nt + target,
+// and the slices are summed by shuffles at the end, so small leaves keep their lanes busy.
+// Sources are staged per warp in batches of 32 records through shared memory, the next
+// batch prefetched into registers while the current one is evaluated.  Coincident points
+// share a Morton key and so a leaf: only the leaf's own sources take the r = 0 test.
 // ------------------------------------------------------------------------------------
-constexpr int kEvalThreads = 128;
-constexpr int kEvalStage = 512;   // P2P source records staged at a time
-constexpr int kMaxRanges = 512;   // U-list entries held in shared memory per pass
+constexpr int kEvalWarps = 1;  // one warp per CTA: the block scheduler balances the leaves
+constexpr int kEvalThreads = 32 * kEvalWarps;
+constexpr unsigned kFull = 0xffffffffu;
 
-template <int KIND>
-struct Acc {
-    float v[KIND == KFMM_DISP ? 3 : 6];
-};
-
-template <int KIND, bool SL, bool DL>
+template <int KIND, bool SL, bool DL, bool CHK>
 __device__ __forceinline__ void p2p_pair(float x, float y, float z, const SrcRec &q, float a34, float b12, float nu,
                                          float *o)
 {
     const float dx = x - q.y.x, dy = y - q.y.y, dz = z - q.y.z;
     if (KIND == KFMM_DISP) {
         if (SL && DL)
-            acc_sl_dl<float>(dx, dy, dz, q.t.x, q.t.y, q.t.z, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, a34,
-                             b12, o[0], o[1], o[2]);
+            acc_sl_dl<float, CHK>(dx, dy, dz, q.t.x, q.t.y, q.t.z, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w,
+                                  a34, b12, o[0], o[1], o[2]);
         else if (SL)
-            acc_sl<float>(dx, dy, dz, q.t.x, q.t.y, q.t.z, a34, o[0], o[1], o[2]);
+            acc_sl<float, CHK>(dx, dy, dz, q.t.x, q.t.y, q.t.z, a34, o[0], o[1], o[2]);
         else
-            acc_dl<float>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, b12, o[0], o[1], o[2]);
+            acc_dl<float, CHK>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, b12, o[0], o[1], o[2]);
     } else {
-        if (SL) acc_D<float>(dx, dy, dz, q.t.x, q.t.y, q.t.z, b12, o);
-        if (DL) acc_S<float>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, nu, b12, o);
+        if (SL) acc_D<float, CHK>(dx, dy, dz, q.t.x, q.t.y, q.t.z, b12, o);
+        if (DL) acc_S<float, CHK>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, nu, b12, o);
     }
 }
 
+// equivalent source (position p, density f): single layer only, never coincident
 template <int KIND>
 __device__ __forceinline__ void equiv_pair(float x, float y, float z, const float4 &p, const float4 &f, float a34,
                                            float b12, float *o)
 {
     const float dx = x - p.x, dy = y - p.y, dz = z - p.z;
-    if (KIND == KFMM_DISP) acc_sl<float>(dx, dy, dz, f.x, f.y, f.z, a34, o[0], o[1], o[2]);
-    else acc_D<float>(dx, dy, dz, f.x, f.y, f.z, b12, o);
+    if (KIND == KFMM_DISP) acc_sl<float, false>(dx, dy, dz, f.x, f.y, f.z, a34, o[0], o[1], o[2]);
+    else acc_D<float, false>(dx, dy, dz, f.x, f.y, f.z, b12, o);
 }
 
 struct EvalArgs {
-    const int *leaves;
+    const int4 *items;
+    int n_items;
+    int w_direct_max;
     const int2 *btrg, *bsrc;
     const float4 *geom;
     const int *uo, *ui, *wo, *wi;
@@ -525,118 +534,326 @@ struct EvalArgs {
     int ldo, col;
 };
 
+// one source record, only the fields the kernel family reads
+template <bool SL, bool DL>
+__device__ __forceinline__ SrcRec load_rec(const SrcRec *__restrict__ rec, int64_t i)
+{
+    SrcRec r;
+    r.y = __ldg(&rec[i].y);
+    if (SL) r.t = __ldg(&rec[i].t);
+    if (DL) {
+        r.u = __ldg(&rec[i].u);
+        r.n = __ldg(&rec[i].n);
+    }
+    return r;
+}
+
+template <bool SL, bool DL>
+__device__ __forceinline__ void store_rec(SrcRec *sh, const SrcRec &r)
+{
+    sh->y = r.y;
+    if (SL) sh->t = r.t;
+    if (DL) {
+        sh->u = r.u;
+        sh->n = r.n;
+    }
+}
+
+// Lane layout of a chunk of nt <= 64 targets: one target per lane (L = nt lanes per source
+// slice, needs nt <= 32) or two (targets t and t + L, L = ceil(nt / 2)); nsl = 32 / L slices.
+// Two per lane is taken when it fills at least as many lane slots (it also halves the
+// shared-memory loads per pair and doubles the independent work per lane).
+__host__ __device__ inline bool eval_layout(int nt, int &L, int &nsl)
+{
+    const int n1 = nt <= 32 ? 32 / nt : 0;
+    const int L2 = (nt + 1) / 2, n2 = 32 / L2;
+    const bool two = n2 >= 2 * n1;
+    L = two ? L2 : nt;
+    nsl = two ? n2 : n1;
+    return two;
+}
+
+// staged records k = kbeg, kbeg + nsl, ... < cnt against this lane's target(s), two
+// independent pairs per step
+template <int KIND, bool SL, bool DL, bool CHK, int NO>
+__device__ __forceinline__ void eval_batch(const SrcRec *sh, int kbeg, int cnt, int nsl, bool two, float x0, float y0,
+                                           float z0, float x1, float y1, float z1, const EvalArgs &e, float (&o0)[NO],
+                                           float (&o1)[NO])
+{
+    int k = kbeg;
+    for (; k + nsl < cnt; k += 2 * nsl) {
+        const SrcRec qa = sh[k], qb = sh[k + nsl];
+        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, qa, e.a34, e.b12, e.nu, o0);
+        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, qb, e.a34, e.b12, e.nu, o0);
+        if (two) {
+            p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, qa, e.a34, e.b12, e.nu, o1);
+            p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, qb, e.a34, e.b12, e.nu, o1);
+        }
+    }
+    if (k < cnt) {
+        const SrcRec q = sh[k];
+        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, q, e.a34, e.b12, e.nu, o0);
+        if (two) p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, q, e.a34, e.b12, e.nu, o1);
+    }
+}
+
 template <int KIND, bool SL, bool DL>
 __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
 {
     constexpr int NO = KIND == KFMM_DISP ? 3 : 6;
-    __shared__ SrcRec srec[kEvalStage];
-    __shared__ int rbeg[kMaxRanges], rpre[kMaxRanges + 1];
-    __shared__ float red[4][64][NO];
-    float4 *epos = reinterpret_cast<float4 *>(srec);           // equivalent sources reuse the stage
-    float4 *eden = reinterpret_cast<float4 *>(srec) + 512;   // (n_surf <= 512)
-
-    const int b = e.leaves[blockIdx.x];
+    __shared__ SrcRec stage[kEvalWarps][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    SrcRec *sh = stage[wid];
+    if ((int)blockIdx.x * kEvalWarps + wid >= e.n_items) return;  // the whole warp
+    const int4 it = e.items[blockIdx.x * kEvalWarps + wid];
+    const int b = it.x, c0 = it.y, s0 = it.z, s1 = it.w;
     const int2 tr = e.btrg[b];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int uo0 = e.uo[b], nU = e.uo[b + 1] - uo0;
     const int wo0 = e.wo[b], nW = e.wo[b + 1] - wo0;
-    for (int c0 = tr.x; c0 < tr.y; c0 += 64) {
-        const int nt = min(64, tr.y - c0);
-        const bool two = nt > 32;
-        float x0 = 0.f, y0 = 0.f, z0 = 0.f, x1 = 0.f, y1 = 0.f, z1 = 0.f;
-        if (lane < nt) {
-            float4 p = e.trg[c0 + lane];
-            x0 = p.x; y0 = p.y; z0 = p.z;
-        }
-        if (lane + 32 < nt) {
-            float4 p = e.trg[c0 + lane + 32];
-            x1 = p.x; y1 = p.y; z1 = p.z;
-        }
-        float o0[NO], o1[NO];
-#pragma unroll
-        for (int a = 0; a < NO; ++a) o0[a] = o1[a] = 0.f;
+    (void)nU;
 
-        // ---- L2P and M2P: equivalent sources, one box at a time
-        for (int eb = -1; eb < nW; ++eb) {
-            const int src_box = eb < 0 ? b : e.wi[wo0 + eb];
-            const float4 g = e.geom[src_box];
-            const float rad = (eb < 0 ? e.r_out : e.r_in) * g.w;
-            const float *phi = (eb < 0 ? e.dn_phi : e.up_phi) + (int64_t)src_box * e.ld_phi;
-            __syncthreads();
-            for (int k = threadIdx.x; k < e.n_surf; k += kEvalThreads) {
-                const float4 s = e.surf[k];
-                epos[k] = make_float4(g.x + rad * s.x, g.y + rad * s.y, g.z + rad * s.z, 0.f);
-                eden[k] = make_float4(e.phi_scale * phi[3 * k], e.phi_scale * phi[3 * k + 1],
-                                      e.phi_scale * phi[3 * k + 2], 0.f);
+    const int nt = min(64, tr.y - c0);
+    int L, nsl;
+    const bool two = eval_layout(nt, L, nsl);
+    const int ti = lane % L, si = lane / L;            // first target, source slice
+    const int t1 = ti + L;                             // second target (two per lane)
+    const bool act = si < nsl, act1 = act && two && t1 < nt;
+    float x0 = 0.f, y0 = 0.f, z0 = 0.f, x1 = 0.f, y1 = 0.f, z1 = 0.f;
+    if (act) {
+        const float4 p = e.trg[c0 + ti];
+        x0 = p.x;
+        y0 = p.y;
+        z0 = p.z;
+    }
+    if (act1) {
+        const float4 p = e.trg[c0 + t1];
+        x1 = p.x;
+        y1 = p.y;
+        z1 = p.z;
+    }
+    float o0[NO], o1[NO];
+#pragma unroll
+    for (int a = 0; a < NO; ++a) o0[a] = o1[a] = 0.f;
+    const int kbeg = act ? si : 32;  // inactive lanes skip every evaluation loop
+
+    // ---- L2P (segment 0) and M2P (W boxes above the direct threshold): equivalent sources
+    //      of one box, 32 at a time
+    for (int j = s0; j < s1 && j <= nW; ++j) {
+        const int src_box = j == 0 ? b : e.wi[wo0 + j - 1];
+        if (j > 0) {
+            const int2 r = e.bsrc[src_box];
+            if (r.y - r.x <= e.w_direct_max) continue;  // evaluated directly below
+        }
+        const float4 g = e.geom[src_box];
+        const float rad = (j == 0 ? e.r_out : e.r_in) * g.w;
+        const float *phi = (j == 0 ? e.dn_phi : e.up_phi) + (int64_t)src_box * e.ld_phi;
+        for (int base = 0; base < e.n_surf; base += 32) {
+            const int cnt = min(32, e.n_surf - base);
+            __syncwarp();
+            if (lane < cnt) {
+                const int k = base + lane;
+                const float4 sp = e.surf[k];
+                sh[lane].y = make_float4(g.x + rad * sp.x, g.y + rad * sp.y, g.z + rad * sp.z, 0.f);
+                sh[lane].t = make_float4(e.phi_scale * phi[3 * k], e.phi_scale * phi[3 * k + 1],
+                                         e.phi_scale * phi[3 * k + 2], 0.f);
             }
-            __syncthreads();
-            for (int k = warp; k < e.n_surf; k += 4) {
-                const float4 p = epos[k], f = eden[k];
-                equiv_pair<KIND>(x0, y0, z0, p, f, e.a34, e.b12, o0);
-                if (two) equiv_pair<KIND>(x1, y1, z1, p, f, e.a34, e.b12, o1);
+            __syncwarp();
+            int k = kbeg;
+            for (; k + nsl < cnt; k += 2 * nsl) {  // two independent pairs per step
+                const float4 pa = sh[k].y, fa = sh[k].t, pb = sh[k + nsl].y, fb = sh[k + nsl].t;
+                equiv_pair<KIND>(x0, y0, z0, pa, fa, e.a34, e.b12, o0);
+                equiv_pair<KIND>(x0, y0, z0, pb, fb, e.a34, e.b12, o0);
+                if (two) {
+                    equiv_pair<KIND>(x1, y1, z1, pa, fa, e.a34, e.b12, o1);
+                    equiv_pair<KIND>(x1, y1, z1, pb, fb, e.a34, e.b12, o1);
+                }
+            }
+            if (k < cnt) {
+                const float4 pp = sh[k].y, f = sh[k].t;
+                equiv_pair<KIND>(x0, y0, z0, pp, f, e.a34, e.b12, o0);
+                if (two) equiv_pair<KIND>(x1, y1, z1, pp, f, e.a34, e.b12, o1);
             }
         }
-        // ---- P2P over the U list, ranges staged in passes of kMaxRanges
-        for (int r0 = 0; r0 < nU; r0 += kMaxRanges) {
-            const int nr = min(kMaxRanges, nU - r0);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int acc = 0;
-                for (int k = 0; k < nr; ++k) {
-                    const int2 s = e.bsrc[e.ui[uo0 + r0 + k]];
-                    rbeg[k] = s.x;
-                    rpre[k] = acc;
-                    acc += s.y - s.x;
+    }
+
+    // ---- P2P with the direct W boxes and the U-list leaves other than the leaf itself: up
+    //      to 32 source ranges at a time, batches of 32 records filled across ranges
+    bool has_self = false;
+    for (int j0 = max(s0, 1); j0 < s1; j0 += 32) {
+        const int nr = min(32, s1 - j0);
+        int beg = 0, cnt = 0;
+        bool self = false;
+        if (lane < nr) {
+            const int j = j0 + lane;
+            const int sb = j <= nW ? e.wi[wo0 + j - 1] : e.ui[uo0 + j - 1 - nW];
+            const int2 r = e.bsrc[sb];
+            if (j <= nW) {
+                if (r.y - r.x <= e.w_direct_max) {
+                    beg = r.x;
+                    cnt = r.y - r.x;
                 }
-                rpre[nr] = acc;
-            }
-            __syncthreads();
-            const int total = rpre[nr];
-            for (int base = 0; base < total; base += kEvalStage) {
-                const int cnt = min(kEvalStage, total - base);
-                __syncthreads();
-                for (int k = threadIdx.x; k < cnt; k += kEvalThreads) {
-                    const int f = base + k;
-                    int lo = 0, hi = nr;  // find the range holding f: rpre[lo] <= f < rpre[lo+1]
-                    while (hi - lo > 1) {
-                        int m = (lo + hi) >> 1;
-                        if (rpre[m] <= f) lo = m;
-                        else hi = m;
-                    }
-                    srec[k] = e.rec[rbeg[lo] + (f - rpre[lo])];
-                }
-                __syncthreads();
-                for (int s = warp; s < cnt; s += 4) {
-                    const SrcRec q = srec[s];
-                    p2p_pair<KIND, SL, DL>(x0, y0, z0, q, e.a34, e.b12, e.nu, o0);
-                    if (two) p2p_pair<KIND, SL, DL>(x1, y1, z1, q, e.a34, e.b12, e.nu, o1);
-                }
+            } else if (sb == b) {
+                self = true;
+            } else {
+                beg = r.x;
+                cnt = r.y - r.x;
             }
         }
-        // ---- reduce over the 4 warps and write in input order
-        __syncthreads();
+        has_self |= __ballot_sync(kFull, self) != 0u;
+        int incl = cnt;  // inclusive prefix over the lanes
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int excl = incl - cnt;
+        const int total = __shfl_sync(kFull, incl, 31);
+        // source index of flat position f: the last range whose exclusive prefix is <= f
+        auto locate = [&](int f) -> int {
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int mid = lo + step;
+                const int v = __shfl_sync(kFull, excl, mid < 32 ? mid : 31);
+                if (mid < nr && v <= f) lo = mid;
+            }
+            const int bb = __shfl_sync(kFull, beg, lo);
+            const int ee = __shfl_sync(kFull, excl, lo);
+            return bb + (f - ee);
+        };
+        SrcRec nxt;
+        {
+            const int src = locate(lane);
+            if (lane < total) nxt = load_rec<SL, DL>(e.rec, src);
+        }
+        for (int base = 0; base < total; base += 32) {
+            const int cnt2 = min(32, total - base);
+            __syncwarp();
+            if (lane < cnt2) store_rec<SL, DL>(sh + lane, nxt);
+            __syncwarp();
+            if (base + 32 < total) {
+                const int src = locate(base + 32 + lane);
+                if (base + 32 + lane < total) nxt = load_rec<SL, DL>(e.rec, src);
+            }
+            eval_batch<KIND, SL, DL, false>(sh, kbeg, cnt2, nsl, two, x0, y0, z0, x1, y1, z1, e, o0, o1);
+        }
+    }
+
+    // ---- P2P with the leaf's own sources (the only ones that may coincide with a target)
+    if (has_self) {
+        const int2 r = e.bsrc[b];
+        SrcRec nxt;
+        if (r.x + lane < r.y) nxt = load_rec<SL, DL>(e.rec, r.x + lane);
+        for (int base = r.x; base < r.y; base += 32) {
+            const int cnt = min(32, r.y - base);
+            __syncwarp();
+            if (lane < cnt) store_rec<SL, DL>(sh + lane, nxt);
+            __syncwarp();
+            if (base + 32 + lane < r.y) nxt = load_rec<SL, DL>(e.rec, base + 32 + lane);
+            eval_batch<KIND, SL, DL, true>(sh, kbeg, cnt, nsl, two, x0, y0, z0, x1, y1, z1, e, o0, o1);
+        }
+    }
+
+    // ---- sum the source slices into slice 0 (shuffling the unmodified partial sums) and add
+    //      into the zeroed output in input order
+    float tot[NO], tot1[NO];
+#pragma unroll
+    for (int a = 0; a < NO; ++a) {
+        tot[a] = o0[a];
+        tot1[a] = o1[a];
+    }
+    for (int s = 1; s < nsl; ++s) {
+        const int src = lane + s * L;
+        const int sl = src < 32 ? src : 31;
 #pragma unroll
         for (int a = 0; a < NO; ++a) {
-            red[warp][lane][a] = o0[a];
-            red[warp][lane + 32][a] = o1[a];
+            const float v = __shfl_sync(kFull, o0[a], sl);
+            const float v1 = __shfl_sync(kFull, o1[a], sl);
+            if (src < 32) {
+                tot[a] += v;
+                tot1[a] += v1;
+            }
         }
-        __syncthreads();
-        for (int t = threadIdx.x; t < nt; t += kEvalThreads) {
-            const int gi = e.trg_perm[c0 + t];
-            float *o = e.out + (int64_t)gi * e.ldo + NO * e.col;
+    }
+    if (si == 0) {
+        float *o = e.out + (int64_t)e.trg_perm[c0 + ti] * e.ldo + NO * e.col;
 #pragma unroll
-            for (int a = 0; a < NO; ++a)
-                o[a] = e.out_scale * (red[0][t][a] + red[1][t][a] + red[2][t][a] + red[3][t][a]);
+        for (int a = 0; a < NO; ++a) atomicAdd(o + a, e.out_scale * tot[a]);
+        if (act1) {
+            float *q = e.out + (int64_t)e.trg_perm[c0 + t1] * e.ldo + NO * e.col;
+#pragma unroll
+            for (int a = 0; a < NO; ++a) atomicAdd(q + a, e.out_scale * tot1[a]);
         }
     }
 }
 
-template <int KIND>
-void launch_eval(const EvalArgs &e, int nleaves, bool sl, bool dl, cudaStream_t st)
+// zero the NO outputs of column col of every target (the evaluation adds into them)
+__global__ void zero_out_kernel(int64_t n, float *__restrict__ out, int ldo, int c0, int no)
 {
-    if (sl && dl) eval_leaf_kernel<KIND, true, true><<<nleaves, kEvalThreads, 0, st>>>(e);
-    else if (sl) eval_leaf_kernel<KIND, true, false><<<nleaves, kEvalThreads, 0, st>>>(e);
-    else eval_leaf_kernel<KIND, false, true><<<nleaves, kEvalThreads, 0, st>>>(e);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * no; i += stride)
+        out[(i / no) * ldo + c0 + i % no] = 0.f;
+}
+
+// Work items of the leaf evaluation: one thread per leaf walks its target chunks and source
+// segments, cutting a new item when the cost (warp pair-steps) would exceed kEvalItemCost.
+constexpr float kEvalItemCost = 1024.f;
+
+template <bool EMIT>
+__global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, const int2 *__restrict__ btrg,
+                                  const int2 *__restrict__ bsrc, const int *__restrict__ uo,
+                                  const int *__restrict__ ui, const int *__restrict__ wo,
+                                  const int *__restrict__ wi, int w_direct_max, int n_surf,
+                                  const int *__restrict__ off, int *__restrict__ cnt, int4 *__restrict__ items)
+{
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= n_leaves) return;
+    const int b = leaves[li];
+    const int2 tr = btrg[b];
+    const int nW = wo[b + 1] - wo[b], nU = uo[b + 1] - uo[b];
+    const int nseg = 1 + nW + nU;
+    const int pos = EMIT ? off[li] : 0;
+    int n = 0;
+    for (int c0 = tr.x; c0 < tr.y; c0 += 64) {
+        const int nt = min(64, tr.y - c0);
+        int L, nsl;
+        const bool two = eval_layout(nt, L, nsl);
+        const float w = (two ? 2.f : 1.f) / (float)nsl;  // pair evaluations per lane and source
+        float acc = 0.f;
+        int s0 = 0;
+        for (int s = 0; s < nseg; ++s) {
+            float c;
+            if (s == 0) {
+                c = 0.5f * (float)n_surf;
+            } else if (s <= nW) {
+                const int2 r = bsrc[wi[wo[b] + s - 1]];
+                c = r.y - r.x > w_direct_max ? 0.5f * (float)n_surf : (float)(r.y - r.x);
+            } else {
+                const int2 r = bsrc[ui[uo[b] + s - 1 - nW]];
+                c = (float)(r.y - r.x);
+            }
+            c *= w;
+            if (acc > 0.f && acc + c > kEvalItemCost) {
+                if (EMIT) items[pos + n] = make_int4(b, c0, s0, s);
+                ++n;
+                s0 = s;
+                acc = 0.f;
+            }
+            acc += c;
+        }
+        if (EMIT) items[pos + n] = make_int4(b, c0, s0, nseg);
+        ++n;
+    }
+    if (!EMIT) cnt[li] = n;
+}
+
+template <int KIND>
+void launch_eval(const EvalArgs &e, int n_items, bool sl, bool dl, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)((n_items + kEvalWarps - 1) / kEvalWarps);
+    if (sl && dl) eval_leaf_kernel<KIND, true, true><<<grid, kEvalThreads, 0, st>>>(e);
+    else if (sl) eval_leaf_kernel<KIND, true, false><<<grid, kEvalThreads, 0, st>>>(e);
+    else eval_leaf_kernel<KIND, false, true><<<grid, kEvalThreads, 0, st>>>(e);
 }
 
 }  // namespace
@@ -741,6 +958,25 @@ static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
     }
     KF_CUDA(P.err.ensure(sizeof(int)));
     KF_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), st));
+    // work items of the leaf evaluation
+    P.n_eval_items = 0;
+    if (T.n_leaves) {
+        const int nl = T.n_leaves;
+        KF_CUDA(P.eval_cnt.ensure(sizeof(int) * (size_t)(nl + 1)));
+        int *cnt = P.eval_cnt.as<int>();
+        eval_items_kernel<false><<<grid_for(nl, 128, 1 << 30), 128, 0, st>>>(
+            nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
+            T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, nullptr, cnt, nullptr);
+        KF_LAUNCH();
+        KF_TRY(scan_exclusive(ctx, cnt, cnt, nl, cnt + nl));
+        KF_TRY(read_int(ctx, cnt + nl, &P.n_eval_items));
+        KF_CUDA(P.eval_items.ensure(sizeof(int4) * (size_t)std::max(1, P.n_eval_items)));
+        eval_items_kernel<true><<<grid_for(nl, 128, 1 << 30), 128, 0, st>>>(
+            nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
+            T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cnt, nullptr,
+            P.eval_items.as<int4>());
+        KF_LAUNCH();
+    }
     P.oct_lvl.clear();
     P.oct_lvl.resize(T.n_levels);
     for (int l = 1; l < T.n_levels; ++l) {
@@ -941,7 +1177,9 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
             rec = W.tmp.as<SrcRec>();
         }
         EvalArgs e;
-        e.leaves = T.leaves.as<int>();
+        e.items = P.eval_items.as<int4>();
+        e.n_items = P.n_eval_items;
+        e.w_direct_max = T.w_direct_max;
         e.btrg = T.box_trg.as<int2>();
         e.bsrc = T.box_src.as<int2>();
         e.geom = geom;
@@ -967,9 +1205,14 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
         e.out = out;
         e.ldo = (kind == KFMM_DISP ? 3 : 6) * ncol;
         e.col = col;
-        if (T.n_leaves) {
-            if (kind == KFMM_DISP) launch_eval<KFMM_DISP>(e, T.n_leaves, sl != nullptr, dl != nullptr, st);
-            else launch_eval<KFMM_STRESS>(e, T.n_leaves, sl != nullptr, dl != nullptr, st);
+        {
+            const int no = kind == KFMM_DISP ? 3 : 6;
+            zero_out_kernel<<<grid_for(T.ntrg * no, 256), 256, 0, st>>>(T.ntrg, out, e.ldo, no * col, no);
+            KF_LAUNCH();
+        }
+        if (P.n_eval_items) {
+            if (kind == KFMM_DISP) launch_eval<KFMM_DISP>(e, P.n_eval_items, sl != nullptr, dl != nullptr, st);
+            else launch_eval<KFMM_STRESS>(e, P.n_eval_items, sl != nullptr, dl != nullptr, st);
             KF_LAUNCH();
         }
         ctx->phase(-1);

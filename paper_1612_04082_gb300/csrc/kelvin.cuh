@@ -39,17 +39,19 @@ template <typename R> __host__ __device__ inline KelvinConst<R> make_kelvin(doub
 __device__ __forceinline__ float kf_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double kf_rsqrt(double x) { return rsqrt(x); }
 
-// 1/r with the coincident-point convention (0 at r = 0).
-template <typename R> __device__ __forceinline__ R inv_r(R r2) {
-    return r2 > R(0) ? kf_rsqrt(r2) : R(0);
+// 1/r with the coincident-point convention (0 at r = 0).  CHK = false drops the test, for
+// source sets known to hold no point coinciding with the target.
+template <typename R, bool CHK = true> __device__ __forceinline__ R inv_r(R r2) {
+    if (CHK) return r2 > R(0) ? kf_rsqrt(r2) : R(0);
+    return kf_rsqrt(r2);
 }
 
 // Single layer, displacement: out += (3-4nu) t' / r + d (d . t') / r^3.
-template <typename R>
+template <typename R, bool CHK = true>
 __device__ __forceinline__ void acc_sl(R dx, R dy, R dz, R tx, R ty, R tz, R a34, R &ox, R &oy,
                                        R &oz) {
     R r2 = dx * dx + dy * dy + dz * dz;
-    R ri = inv_r(r2);
+    R ri = inv_r<R, CHK>(r2);
     R ri3 = ri * ri * ri;
     R dt = (dx * tx + dy * ty + dz * tz) * ri3;
     R a = a34 * ri;
@@ -62,11 +64,11 @@ __device__ __forceinline__ void acc_sl(R dx, R dy, R dz, R tx, R ty, R tz, R a34
 //   out += (3-4nu) t'/r + d (d.t')/r^3
 //        + [(1-2nu)((d.n) u' + (d.u') n) + d (3 (d.n)(d.u')/r^2 - nu'... )] / r^3
 // i.e. P u = 1/r^3 { (d.n)[(1-2nu) u + 3 d (d.u)/r^2] - (1-2nu)[d (n.u) - n (d.u)] }.
-template <typename R>
+template <typename R, bool CHK = true>
 __device__ __forceinline__ void acc_sl_dl(R dx, R dy, R dz, R tx, R ty, R tz, R ux, R uy, R uz, R nx,
                                           R ny, R nz, R nup, R a34, R b12, R &ox, R &oy, R &oz) {
     R r2 = dx * dx + dy * dy + dz * dz;
-    R ri = inv_r(r2);
+    R ri = inv_r<R, CHK>(r2);
     R ri2 = ri * ri;
     R ri3 = ri2 * ri;
     R dt = dx * tx + dy * ty + dz * tz;
@@ -82,11 +84,11 @@ __device__ __forceinline__ void acc_sl_dl(R dx, R dy, R dz, R tx, R ty, R tz, R 
 }
 
 // Double layer only, displacement.
-template <typename R>
+template <typename R, bool CHK = true>
 __device__ __forceinline__ void acc_dl(R dx, R dy, R dz, R ux, R uy, R uz, R nx, R ny, R nz, R nup,
                                        R b12, R &ox, R &oy, R &oz) {
     R r2 = dx * dx + dy * dy + dz * dz;
-    R ri = inv_r(r2);
+    R ri = inv_r<R, CHK>(r2);
     R ri2 = ri * ri;
     R ri3 = ri2 * ri;
     R dn = dx * nx + dy * ny + dz * nz;
@@ -102,10 +104,10 @@ __device__ __forceinline__ void acc_dl(R dx, R dy, R dz, R ux, R uy, R uz, R nx,
 // Stress of the single layer (Eq. stress_2, textbook constant), unscaled t:
 //   sigma_ij += -c_D / r^3 [ (1-2nu)(t_i d_j + t_j d_i - delta_ij (d.t)) + 3 d_i d_j (d.t)/r^2 ]
 // Accumulated without c_D (applied by the caller): s[6] in xx, yy, zz, yz, xz, xy.
-template <typename R>
+template <typename R, bool CHK = true>
 __device__ __forceinline__ void acc_D(R dx, R dy, R dz, R tx, R ty, R tz, R b12, R *s) {
     R r2 = dx * dx + dy * dy + dz * dz;
-    R ri = inv_r(r2);
+    R ri = inv_r<R, CHK>(r2);
     R ri2 = ri * ri;
     R ri3 = ri2 * ri;
     R dt = dx * tx + dy * ty + dz * tz;
@@ -125,11 +127,11 @@ __device__ __forceinline__ void acc_D(R dx, R dy, R dz, R tx, R ty, R tz, R b12,
 //               - 15 (d.n)(d.u)/r^4 d_i d_j + 3 nu (d.u)/r^2 (n_i d_j + n_j d_i)
 //               + (1-2nu)(3 (n.u)/r^2 d_i d_j + n_j u_i + n_i u_j) - (1-4nu)(n.u) delta_ij }
 // Accumulated without c_S.
-template <typename R>
+template <typename R, bool CHK = true>
 __device__ __forceinline__ void acc_S(R dx, R dy, R dz, R ux, R uy, R uz, R nx, R ny, R nz, R nu_,
                                       R b12, R *s) {
     R r2 = dx * dx + dy * dy + dz * dz;
-    R ri = inv_r(r2);
+    R ri = inv_r<R, CHK>(r2);
     R ri2 = ri * ri;
     R ri3 = ri2 * ri;
     R dn = dx * nx + dy * ny + dz * nz;

@@ -566,10 +566,14 @@ __global__ void compact_kernel(int n, const int *__restrict__ flag, const int *_
     if (b < n && flag[b]) out[pos[b]] = b;
 }
 
-__global__ void mark_kernel(int64_t n, const int *__restrict__ idx, int *__restrict__ flag)
+// W-list boxes evaluated through their upward densities (more than w_direct_max sources)
+__global__ void mark_w_equiv_kernel(int64_t n, const int *__restrict__ idx, const int2 *__restrict__ bsrc,
+                                    int w_direct_max, int *__restrict__ flag)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) flag[idx[k]] = 1;
+    if (k >= n) return;
+    const int b = idx[k];
+    if (bsrc[b].y - bsrc[b].x > w_direct_max) flag[b] = 1;
 }
 
 __global__ void nonzero_kernel(int n, const int *__restrict__ cnt, int *__restrict__ flag)
@@ -662,18 +666,23 @@ __global__ void oct_scatter_kernel(int n_boxes, const int4 *__restrict__ anchor,
 __global__ void work_count_kernel(int n_boxes, const int *__restrict__ leaf, const int2 *__restrict__ bsrc,
                                   const int2 *__restrict__ btrg, const int *__restrict__ uo,
                                   const int *__restrict__ ui, const int *__restrict__ wo,
-                                  const int *__restrict__ xo, const int *__restrict__ xi,
-                                  unsigned long long *__restrict__ acc)
+                                  const int *__restrict__ wi, int w_direct_max, const int *__restrict__ xo,
+                                  const int *__restrict__ xi, unsigned long long *__restrict__ acc)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_boxes) return;
     unsigned long long p2p = 0, l2p = 0, p2l = 0;
     if (leaf[b]) {
         const int nt = btrg[b].y - btrg[b].x;
-        long long ns = 0;
+        long long ns = 0, n_eq = 1;  // the leaf's own downward density
         for (int k = uo[b]; k < uo[b + 1]; ++k) ns += bsrc[ui[k]].y - bsrc[ui[k]].x;
+        for (int k = wo[b]; k < wo[b + 1]; ++k) {
+            const int w = bsrc[wi[k]].y - bsrc[wi[k]].x;
+            if (w > w_direct_max) ++n_eq;
+            else ns += w;
+        }
         p2p = (unsigned long long)nt * ns;
-        l2p = (unsigned long long)nt * (1 + (wo[b + 1] - wo[b]));
+        l2p = (unsigned long long)nt * n_eq;
     }
     for (int k = xo[b]; k < xo[b + 1]; ++k) p2l += bsrc[xi[k]].y - bsrc[xi[k]].x;
     if (p2p) atomicAdd(&acc[0], p2p);
@@ -951,10 +960,13 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, flag.as<int>(), xpos.as<int>(),
                                                                          T.xboxes.as<int>());
         KF_LAUNCH();
-        // boxes that appear in some W list (their upward densities are evaluated at targets)
+        // boxes that appear in some W list with more sources than half the surface points:
+        // their upward densities are evaluated at the targets (the others directly)
+        T.w_direct_max = surface_points(ctx->opt.p) / 2;
         KF_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * n_boxes, st));
         if (T.n_w) {
-            mark_kernel<<<grid_for(T.n_w, 256, 1 << 30), 256, 0, st>>>(T.n_w, T.w_idx.as<int>(), flag.as<int>());
+            mark_w_equiv_kernel<<<grid_for(T.n_w, 256, 1 << 30), 256, 0, st>>>(
+                T.n_w, T.w_idx.as<int>(), T.box_src.as<int2>(), T.w_direct_max, flag.as<int>());
             KF_LAUNCH();
         }
         KF_TRY(scan_exclusive(ctx, flag.as<int>(), xpos.as<int>(), n_boxes, total.as<int>()));
@@ -971,8 +983,8 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         KF_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 3, st));
         work_count_kernel<<<grid_for(n_boxes, 128, 1 << 30), 128, 0, st>>>(
             n_boxes, T.box_leaf.as<int>(), T.box_src.as<int2>(), T.box_trg.as<int2>(), T.u_off.as<int>(),
-            T.u_idx.as<int>(), T.w_off.as<int>(), T.x_off.as<int>(), T.x_idx.as<int>(),
-            acc.as<unsigned long long>());
+            T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, T.x_off.as<int>(),
+            T.x_idx.as<int>(), acc.as<unsigned long long>());
         KF_LAUNCH();
         unsigned long long h[3];
         KF_CUDA(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, st));

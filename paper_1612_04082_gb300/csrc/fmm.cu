@@ -1120,7 +1120,7 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
                 tc::TcArgs ta{O.m2l_tc.as<uint16_t>(), O.m2l_tc_mtiles, r, rp, P.m2l_items.as<int4>(),
                               T.vp_src.as<int>(), T.vp_trg.as<int>(), W.psi2.as<uint16_t>(), W.cdn.as<float>(), rp,
                               P.err.as<int>()};
-                tc::tc_gather_gemm_kernel<<<P.n_m2l_items, tc::THREADS, smem, st>>>(ta);
+                tc::tc_gather_gemm_kernel<<<P.n_m2l_items, tc::M2L_THREADS, smem, st>>>(ta);
                 KF_LAUNCH();
             }
         } else {

@@ -13,12 +13,12 @@
 // at byte j * (R / 8) * 128 + i * 128, so the leading-dimension offset (next core along K)
 // is (R / 8) * 128 and the stride-dimension offset (next core along rows) is 128.
 //
-// One CTA of 4 warps per work item.  The A tile (both halves, pre-laid-out in global
-// memory) arrives by cp.async.bulk; the B tile is gathered, split and stored by all threads;
-// one thread issues the MMAs and commits them to an mbarrier; every warp then reads its 32
-// TMEM lanes and adds them to the output.  Every mbarrier wait is bounded: on time-out the
-// kernel records the error, waits (bounded) for its own copies and MMAs, frees its tensor
-// memory and returns.
+// One CTA per work item (a translation, a row tile, up to 1024 columns).  The A tile (both
+// halves, pre-laid-out in global memory) arrives by cp.async.bulk and stays resident; the B
+// tiles are gathered from pre-split pairs by 16-byte asynchronous copies; producer, MMA and
+// epilogue warps hand tiles and accumulators to one another through mbarriers.  Every
+// mbarrier wait is bounded: on time-out the kernel records the error, waits (bounded) for its
+// own copies and MMAs, frees its tensor memory and returns.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -29,7 +29,6 @@ namespace tc {
 
 constexpr int BM = 128;       // rows per tile (UMMA M)
 constexpr int BN = 64;        // columns per N step (UMMA N)
-constexpr int THREADS = 256;  // 8 warps: warp w reads TMEM lanes 32 (w % 4) .. + 31, column half w / 4
 constexpr int TMEM_COLS = 128; // two FP32 accumulators of BN columns (double buffered)
 constexpr long long WAIT_LIMIT = 1LL << 22;  // try_wait polls before giving up
 
@@ -155,11 +154,6 @@ struct TcArgs {
     int *err;              // set to 1 if a bounded wait gave up
 };
 
-// dynamic shared memory: [A hi | A lo | B0 hi | B0 lo | B1 hi | B1 lo | mbar x3 + flags | dst x2]
-__host__ __device__ inline uint32_t smem_bytes(int Kp)
-{
-    return 2 * half_bytes(BM, Kp) + 4 * half_bytes(BN, Kp) + 64 + 3 * 4 * BN;
-}
 
 // X2[box] = the BF16 split pair of X[box] (Kp values): hi at [0, Kp), lo at [Kp, 2 Kp).  Each
 // 8-value chunk of K is then 16 contiguous bytes, one row of a core matrix.
@@ -193,31 +187,6 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
 }
 
-// Gather columns [c0, c0 + ncols) of the split pairs as the B operand (rows = columns of the
-// product) in the core-matrix layout by 16-byte asynchronous copies; record destinations.
-// THREADS is a multiple of BN, so each thread keeps one column (one index load).
-__device__ __forceinline__ void gather_b(const TcArgs &g, int c0, int ncols, unsigned char *sB, uint32_t b_half,
-                                         int *s_dst)
-{
-    const int Kp = g.Kp;
-    const int col = threadIdx.x % BN;
-    if (threadIdx.x < BN) s_dst[col] = col < ncols ? g.dst_idx[c0 + col] : -1;
-    const uint16_t *xs = col < ncols ? g.X2 + (size_t)g.src_idx[c0 + col] * 2 * Kp : nullptr;
-    for (int kb = threadIdx.x / BN; kb < Kp / 8; kb += THREADS / BN) {
-        const uint32_t off = core_offset(col, kb * 8, BN);
-        if (xs) {
-            cp_async16(sB + off, xs + kb * 8);
-            cp_async16(sB + b_half + off, xs + Kp + kb * 8);
-        } else {
-            *reinterpret_cast<uint4 *>(sB + off) = make_uint4(0, 0, 0, 0);
-            *reinterpret_cast<uint4 *>(sB + b_half + off) = make_uint4(0, 0, 0, 0);
-        }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-__device__ __forceinline__ void gather_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 // The split-pair products of one N step into accumulator `d` (one thread).
 __device__ __forceinline__ void issue_mmas(uint32_t a0, uint32_t a_half, uint32_t b0, uint32_t b_half, int Kp,
                                            uint32_t tmem_d)
@@ -234,33 +203,56 @@ __device__ __forceinline__ void issue_mmas(uint32_t a0, uint32_t a_half, uint32_
     }
 }
 
-// Pipeline per N step s (buffers b = s % 2): gather B(s+1) while MMA(s) runs; issue
-// MMA(s+1) into the other accumulator; then wait for MMA(s) and add accumulator b to the
-// output while MMA(s+1) runs.
-__global__ void __launch_bounds__(THREADS, 1) tc_gather_gemm_kernel(TcArgs g)
+// Warp-specialised pipeline, N steps s of BN columns, buffers b = s % 2:
+//   warps 0-7   epilogue: wait for accumulator b, read it (warp w: TMEM lanes 32 (w % 4) ..,
+//               columns (w / 4) * 32 ..), release it, then add to the output (RED)
+//   warps 8-15  producers, two groups of 128 threads; group b gathers the B tiles of the steps
+//               with s % 2 == b (two threads per column, source indices fetched a round
+//               ahead) once the MMAs of step s - 2 are done
+//   warp 16     lane 0 loads the A tile and issues the MMAs of step s into accumulator b once
+//               B(s) is in and accumulator b is released; warp 16 owns the tensor memory
+// Every wait is bounded; a time-out sets the error flag and the shared fail flag, every role
+// then leaves its loop, and in-flight copies and products are waited for (bounded) before the
+// tensor memory is freed.
+constexpr int M2L_EPI_WARPS = 8;
+constexpr int M2L_PROD_THREADS = 128;  // per producer group
+constexpr int M2L_MMA_WARP = M2L_EPI_WARPS + 2 * M2L_PROD_THREADS / 32;
+constexpr int M2L_THREADS = 32 * (M2L_MMA_WARP + 1);
+
+// dynamic shared memory: [A hi | A lo | B0 hi | B0 lo | B1 hi | B1 lo | barriers + flags]
+__host__ __device__ inline uint32_t smem_bytes(int Kp) { return 2 * half_bytes(BM, Kp) + 4 * half_bytes(BN, Kp) + 128; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool fail_set(const int *f) { return *(volatile const int *)f != 0; }
+
+__global__ void __launch_bounds__(M2L_THREADS, 1) tc_gather_gemm_kernel(TcArgs g)
 {
     extern __shared__ __align__(128) unsigned char sm[];
     const int Kp = g.Kp;
     const uint32_t a_half = half_bytes(BM, Kp), b_half = half_bytes(BN, Kp);
     unsigned char *sA = sm;
-    unsigned char *sB[2] = {sm + 2 * a_half, sm + 2 * a_half + 2 * b_half};
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * a_half + 4 * b_half);  // [0] A, [1] [2] MMA
-    uint32_t *holder = reinterpret_cast<uint32_t *>(bar + 3);
-    int *s_fail = reinterpret_cast<int *>(bar + 3) + 1;
-    // destination indices of steps s - 1, s, s + 1 are live at once (the epilogue of s - 1 may
-    // still be reading while step s + 1 is gathered), hence three buffers indexed by s % 3
-    int *s_dst0 = reinterpret_cast<int *>(sm + 2 * a_half + 4 * b_half + 64);
-    int *s_dst[3] = {s_dst0, s_dst0 + BN, s_dst0 + 2 * BN};
+    unsigned char *sB0 = sm + 2 * a_half;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * a_half + 4 * b_half);
+    uint64_t *barA = bar, *fullB = bar + 1, *emptyB = bar + 3, *fullAcc = bar + 5, *emptyAcc = bar + 7;
+    uint32_t *holder = reinterpret_cast<uint32_t *>(bar + 9);
+    int *s_fail = reinterpret_cast<int *>(holder + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, chalf = warp >> 2;
     const int4 item = g.items[blockIdx.x];
     const int nsteps = (item.w - item.z + BN - 1) / BN;
 
-    if (warp == 0) tmem_alloc(holder, TMEM_COLS);
+    if (warp == M2L_MMA_WARP) tmem_alloc(holder, TMEM_COLS);
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init(&bar[2], 1);
+        mbar_init(barA, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&fullB[i], M2L_PROD_THREADS);
+            mbar_init(&emptyB[i], 1);
+            mbar_init(&fullAcc[i], 1);
+            mbar_init(&emptyAcc[i], M2L_EPI_WARPS);
+        }
         *s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -268,90 +260,118 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gather_gemm_kernel(TcArgs g)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *holder;
-    const uint32_t a0 = smem_u32(sA), bs0 = smem_u32(sB[0]), bs1 = smem_u32(sB[1]);
+    auto fail = [&]() {
+        atomicExch(s_fail, 1);
+        atomicExch(g.err, 1);
+    };
 
-    // A tile (both halves) by bulk copy
-    if (tid == 0) {
-        const unsigned char *src = reinterpret_cast<const unsigned char *>(g.A) +
-                                   ((size_t)item.x * g.n_mtile + item.y) * 2 * (size_t)a_half;
-        mbar_expect_tx(&bar[0], 2 * a_half);
-        const uint32_t chunk = 16384;
-        for (uint32_t off = 0; off < 2 * a_half; off += chunk) {
-            const uint32_t n = (2 * a_half - off) < chunk ? (2 * a_half - off) : chunk;
-            bulk_g2s(sA + off, src + off, n, &bar[0]);
-        }
-    }
-    // prologue: B(0), then MMA(0)
-    gather_b(g, item.z, min(BN, item.w - item.z), sB[0], b_half, s_dst[0]);
-    gather_wait();
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (tid == 0) {
-        if (mbar_wait(&bar[0], 0)) {
-            issue_mmas(a0, a_half, bs0, b_half, Kp, tmem);
-        } else {
-            *s_fail = 1;
-            atomicExch(g.err, 1);
-        }
-        mma_commit(&bar[1]);
-    }
-    uint32_t phase[2] = {0u, 0u};
-    bool issued_next = false;
-    int s = 0;
-    for (; s < nsteps; ++s) {
-        const int b = s & 1, nb = b ^ 1;
-        issued_next = false;
-        if (s + 1 < nsteps) {
-            const int c0 = item.z + (s + 1) * BN;
-            gather_b(g, c0, min(BN, item.w - c0), sB[nb], b_half, s_dst[(s + 1) % 3]);
-            gather_wait();
-        }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (s + 1 < nsteps) {
-            if (tid == 0) {
-                if (!*s_fail) issue_mmas(a0, a_half, nb ? bs1 : bs0, b_half, Kp, tmem + (uint32_t)(nb * BN));
-                mma_commit(&bar[1 + nb]);
-            }
-            issued_next = true;
-        }
-        bool ok = mbar_wait(&bar[1 + b], phase[b]);
-        phase[b] ^= 1u;
-        if (!ok) atomicExch(g.err, 1);
-        ok = __syncthreads_or(!ok || *s_fail) == 0;  // one decision for the whole CTA
-        tc_fence_after();
-        if (!ok) break;
-        // epilogue of step s: this warp's lane quadrant, its half of the BN columns
+    if (warp < M2L_EPI_WARPS) {
+        // ---------------- epilogue
+        const int quad = warp & 3, chalf = warp >> 2;
         const int row = item.y * BM + quad * 32 + lane;
+        for (int s = 0; s < nsteps; ++s) {
+            const int b = s & 1;
+            const uint32_t u = (uint32_t)(s >> 1);
+            const int c0 = item.z + s * BN + chalf * (BN / 2);
+            const int myd = c0 + lane < item.w ? g.dst_idx[c0 + lane] : -1;
+            // warp-uniform decisions: the tensor-memory loads below are warp-collective
+            if (__any_sync(0xffffffffu, fail_set(s_fail))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(&fullAcc[b], u & 1u))) {
+                if (lane == 0) fail();
+                break;
+            }
+            tc_fence_after();
+            float v[BN / 2];
+            tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN + chalf * (BN / 2)), v);
+            tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN + chalf * (BN / 2) + 16), v + 16);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&emptyAcc[b]);
 #pragma unroll
-        for (int cb = 0; cb < BN / 2; cb += 16) {
-            const int col = chalf * (BN / 2) + cb;
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * BN + col), v);
-            if (row < g.M) {
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int d = s_dst[s % 3][col + q];
-                    if (d >= 0) atomicAdd(g.Y + (size_t)d * g.ldy + row, v[q]);
+            for (int k = 0; k < BN / 2; ++k) {
+                const int d = __shfl_sync(0xffffffffu, myd, k);
+                if (d >= 0 && row < g.M) atomicAdd(g.Y + (size_t)d * g.ldy + row, v[k]);
+            }
+        }
+    } else if (warp < M2L_MMA_WARP) {
+        // ---------------- producers: group pg fills buffer pg for steps s = pg, pg + 2, ...
+        const int pt = tid - 32 * M2L_EPI_WARPS;
+        const int pg = pt / M2L_PROD_THREADS, q = pt % M2L_PROD_THREADS;
+        const int col = q % BN, kh = q / BN;  // column, and which half of its K chunks
+        unsigned char *sB = sB0 + (size_t)pg * 2 * b_half;
+        auto src_of = [&](int s) {
+            const int c = item.z + s * BN + col;
+            return (s < nsteps && c < item.w) ? g.src_idx[c] : -1;
+        };
+        int src_next = src_of(pg);
+        for (int s = pg; s < nsteps; s += 2) {
+            const uint32_t u = (uint32_t)(s >> 1);
+            const int src = src_next;
+            src_next = src_of(s + 2);  // in flight while this step waits and copies
+            if (fail_set(s_fail)) break;
+            // buffer pg was read by the MMAs of step s - 2
+            if (u >= 1 && !mbar_wait(&emptyB[pg], (u - 1) & 1u)) {
+                fail();
+                break;
+            }
+            const uint16_t *xs = src >= 0 ? g.X2 + (size_t)src * 2 * Kp : nullptr;
+            for (int kb = kh; kb < Kp / 8; kb += M2L_PROD_THREADS / BN) {
+                const uint32_t off = core_offset(col, kb * 8, BN);
+                if (xs) {
+                    cp_async16(sB + off, xs + kb * 8);
+                    cp_async16(sB + b_half + off, xs + Kp + kb * 8);
+                } else {
+                    *reinterpret_cast<uint4 *>(sB + off) = make_uint4(0, 0, 0, 0);
+                    *reinterpret_cast<uint4 *>(sB + b_half + off) = make_uint4(0, 0, 0, 0);
                 }
             }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            fence_proxy_async();  // the tile is read by the tensor cores (async proxy)
+            mbar_arrive(&fullB[pg]);
         }
-        tc_fence_before();
-    }
-    // after a failure, let the products already issued finish before freeing tensor memory
-    if (s < nsteps && tid == 0) {
-        const int b = s & 1;
-        mbar_wait(&bar[1 + b], phase[b] ^ 1u);  // the step that failed (returns at once if done)
-        if (issued_next) mbar_wait(&bar[1 + (b ^ 1)], phase[b ^ 1]);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (lane == 0) {
+        // ---------------- MMA issuer
+        const unsigned char *src =
+            reinterpret_cast<const unsigned char *>(g.A) + ((size_t)item.x * g.n_mtile + item.y) * 2 * (size_t)a_half;
+        mbar_expect_tx(barA, 2 * a_half);
+        for (uint32_t off = 0; off < 2 * a_half; off += 16384) {
+            const uint32_t n = (2 * a_half - off) < 16384u ? (2 * a_half - off) : 16384u;
+            bulk_g2s(sA + off, src + off, n, barA);
+        }
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB0);
+        int issued = 0;
+        bool have_a = false;
+        for (int s = 0; s < nsteps; ++s) {
+            const int b = s & 1;
+            const uint32_t u = (uint32_t)(s >> 1);
+            if (fail_set(s_fail)) break;
+            bool ok = mbar_wait(&fullB[b], u & 1u);
+            if (ok && !have_a) ok = have_a = mbar_wait(barA, 0);
+            if (ok && u >= 1) ok = mbar_wait(&emptyAcc[b], (u - 1) & 1u);
+            if (!ok) {
+                fail();
+                break;
+            }
+            tc_fence_after();
+            issue_mmas(a0, a_half, b0 + (uint32_t)b * 2 * b_half, b_half, Kp, tmem + (uint32_t)(b * BN));
+            mma_commit(&emptyB[b]);
+            mma_commit(&fullAcc[b]);
+            ++issued;
+        }
+        // on failure: let the issued products and the A copy finish before the memory goes
+        if (fail_set(s_fail)) {
+            if (issued > 0) {
+                const int sl = issued - 1;
+                mbar_wait(&fullAcc[sl & 1], (uint32_t)(sl >> 1) & 1u);
+            }
+            if (!have_a) mbar_wait(barA, 0);
+        }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+    if (warp == M2L_MMA_WARP) tmem_dealloc(tmem, TMEM_COLS);
 }
 
 // ======================================================================================

@@ -233,14 +233,23 @@ typedef struct bem_solve_opts {
     int restart;       /* GMRES restart length (30; <= 200)                                  */
     int maxit;         /* cap on inner GMRES iterations in total (1000)                      */
     const double *x0;  /* initial guess of the unknowns [nt][3], or NULL for zero            */
+    int refine;        /* 0: GMRES on the context's operator.  1 (FMM contexts): mixed-
+                          precision iterative refinement -- right-hand side, outer residuals
+                          and updates in FP64 with the direct (exact discrete) operator, each
+                          correction by GMRES on the FP32 FMM operator (0)                    */
+    double inner_tol;  /* relative tolerance of each refinement correction (1e-3)            */
+    int max_outer;     /* cap on refinement steps (30)                                       */
 } bem_solve_opts;
 
 typedef struct bem_stats {
     int iters;        /* inner GMRES iterations                                             */
-    int matvecs;      /* operator applications (including residual checks)                  */
+    int matvecs;      /* FMM operator applications (including residual checks)              */
     int converged;    /* 1 if the tolerance was met                                          */
-    double relres;    /* final true relative residual ||b - A x|| / ||b||                    */
+    double relres;    /* final true relative residual ||b - A x|| / ||b|| (with refinement:
+                         against the FP64 direct operator)                                   */
     double seconds;   /* wall time of bem_solve                                              */
+    int outer;        /* refinement steps (1 without refinement)                            */
+    int matvecs_hi;   /* FP64 direct operator applications                                  */
 } bem_stats;
 
 void bem_default_solve_opts(bem_solve_opts *o);

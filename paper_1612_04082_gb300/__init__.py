@@ -278,12 +278,14 @@ BEM_DIRECT_FP64 = 1
 
 class bem_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("x0", ctypes.c_void_p)]
+                ("x0", ctypes.c_void_p), ("refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int)]
 
 
 class bem_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("matvecs", ctypes.c_int), ("converged", ctypes.c_int),
-                ("relres", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("relres", ctypes.c_double), ("seconds", ctypes.c_double), ("outer", ctypes.c_int),
+                ("matvecs_hi", ctypes.c_int)]
 
 
 _bsig = {
@@ -356,11 +358,15 @@ def bem_rhs(h, out):
     return out
 
 
-def bem_solve(h, u=None, t=None, tol=1e-6, restart=30, maxit=1000, x0=None, raise_on_fail=True):
-    """GMRES solve of Eq. num2; fills u, t [nt,3] float64 (host or device). Returns stats dict."""
+def bem_solve(h, u=None, t=None, tol=1e-6, restart=30, maxit=1000, x0=None, raise_on_fail=True, refine=False,
+              inner_tol=1e-3, max_outer=30):
+    """GMRES solve of Eq. num2; fills u, t [nt,3] float64 (host or device). With refine=True
+    (FMM contexts): mixed-precision iterative refinement, FP64 direct residuals, FMM
+    corrections. Returns stats dict."""
     o = bem_solve_opts()
     _lib.bem_default_solve_opts(ctypes.byref(o))
     o.tol, o.restart, o.maxit = float(tol), int(restart), int(maxit)
+    o.refine, o.inner_tol, o.max_outer = int(bool(refine)), float(inner_tol), int(max_outer)
     o.x0 = _ptr(x0)
     st = bem_stats()
     status = _lib.bem_solve(h, ctypes.byref(o), _ptr(u), _ptr(t), ctypes.byref(st))

@@ -24,7 +24,8 @@ struct bem_ctx {
     kfmm_ctx *vol = nullptr;   // FMM over quadrature sources -> interior points
     bool surf_built = false, have_bc = false, have_sol = false;
     double setup_G = -1, setup_nu = -1;
-    int matvecs = 0;
+    int matvecs = 0, matvecs_hi = 0;  // FMM and FP64 direct operator applications
+    DevBuf d, rhs_hi;                 // GMRES-IR: correction, outer residual
     DevBuf verts, tris;
     DevBuf q32, qn32;        // float [16 nt][3]: quadrature points, element normals
     DevBuf q64, qn64;        // double [16 nt][3]
@@ -438,16 +439,18 @@ static kfmm_status bem_setup(bem_ctx *b)
     return KFMM_OK;
 }
 
-// M(u, t) (mode 0), A x (mode 1) or B y (mode 2; sign -1) into out (device, FP64 [nt][3]).
+// M(u, t) (mode 0), A x (mode 1) or B y (mode 2; sign -1) into out (device, FP64 [nt][3]),
+// with the context's operator, or with the given one (which = BEM_FMM or BEM_DIRECT_FP64).
 static kfmm_status bem_op_apply(bem_ctx *b, int mode, const double *u, const double *t, const double *x,
-                                double *out)
+                                double *out, int which = -1)
 {
     BK_TRY(bem_setup(b));
     const int64_t nt = b->nt, nq = 16 * nt;
     const double sign = mode == 2 ? -1.0 : 1.0;
     const uint8_t *mask = b->mask.as<uint8_t>();
-    ++b->matvecs;
-    if (b->op == BEM_FMM) {
+    if (which < 0) which = b->op;
+    if (which == BEM_FMM) {
+        ++b->matvecs;
         BK_CUDA(b->slq.ensure(sizeof(float) * 3 * nq));
         BK_CUDA(b->dlq.ensure(sizeof(float) * 3 * nq));
         BK_CUDA(b->fout.ensure(sizeof(float) * 3 * nt));
@@ -459,6 +462,7 @@ static kfmm_status bem_op_apply(bem_ctx *b, int mode, const double *u, const dou
                                                               b->corrU.as<double>(), b->corrT.as<double>(), out);
         BK_LAUNCH();
     } else {
+        ++b->matvecs_hi;
         BK_CUDA(b->slq.ensure(sizeof(double) * 3 * nq));
         BK_CUDA(b->dlq.ensure(sizeof(double) * 3 * nq));
         BK_CUDA(b->fout.ensure(sizeof(double) * 3 * nt));
@@ -510,36 +514,27 @@ static kfmm_status vnorm(bem_ctx *b, const double *w, int64_t n, double *out)
     return KFMM_OK;
 }
 
-static kfmm_status gmres(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
+// Restarted GMRES (classical Gram-Schmidt twice, FP64 vectors) for A x = rhs with operator
+// `which`: x (device) holds the initial guess (zeroed when zero_x) and receives the
+// iterate; stops at ||rhs - A x|| <= tol * bn (true residual at every restart) or after
+// maxit inner iterations.  *iters, *rel (true residual / bn) and *conv are returned.
+static kfmm_status gmres_core(bem_ctx *b, int which, const double *rhs, double *x, bool zero_x, double bn, double tol,
+                              int m, int maxit, int *iters, double *rel_out, bool *conv_out)
 {
     const int64_t n = 3 * b->nt;
-    const int m = o.restart;
     BK_CUDA(b->basis.ensure(sizeof(double) * (size_t)(m + 1) * n));
     BK_CUDA(b->w.ensure(sizeof(double) * n));
     BK_CUDA(b->r.ensure(sizeof(double) * n));
-    BK_CUDA(b->x.ensure(sizeof(double) * n));
-    BK_CUDA(b->b.ensure(sizeof(double) * n));
-    double *V = b->basis.as<double>(), *w = b->w.as<double>(), *r = b->r.as<double>(), *x = b->x.as<double>(),
-           *rhs = b->b.as<double>();
-    BK_TRY(bem_op_apply(b, 2, nullptr, nullptr, b->val.as<double>(), rhs));
-    double bn;
-    BK_TRY(vnorm(b, rhs, n, &bn));
-    if (bn == 0.0) bn = 1.0;
-    if (o.x0) {
-        const void *dx0;
-        BK_TRY(bem_stage(b, b->stage[0], o.x0, sizeof(double) * n, &dx0));
-        BK_CUDA(cudaMemcpyAsync(x, dx0, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
-    } else {
-        BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, b->stream));
-    }
+    double *V = b->basis.as<double>(), *w = b->w.as<double>(), *r = b->r.as<double>();
+    if (zero_x) BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, b->stream));
     std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m), h(m + 1), h2(m + 1);
     int it = 0;
     double rel = 1.0;
     bool conv = false;
     while (true) {
-        // true residual r = b - A x
-        if (o.x0 || it > 0) {
-            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, x, w));
+        // true residual r = rhs - A x
+        if (!zero_x || it > 0) {
+            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, x, w, which));
             sub_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(r, rhs, w, n);
             BK_LAUNCH();
         } else {
@@ -548,19 +543,19 @@ static kfmm_status gmres(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
         double beta;
         BK_TRY(vnorm(b, r, n, &beta));
         rel = beta / bn;
-        if (rel <= o.tol) {
+        if (rel <= tol) {
             conv = true;
             break;
         }
-        if (it >= o.maxit) break;
+        if (it >= maxit) break;
         scale_copy_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(V, r, 1.0 / beta, n);
         BK_LAUNCH();
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
         int j = 0;
-        for (; j < m && it < o.maxit; ++j) {
+        for (; j < m && it < maxit; ++j) {
             double *vj = V + (size_t)j * n, *vn = V + (size_t)(j + 1) * n;
-            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, vj, w));
+            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, vj, w, which));
             ++it;
             // classical Gram-Schmidt, twice
             BK_TRY(mdot(b, V, n, j + 1, w, n, h.data()));
@@ -585,7 +580,7 @@ static kfmm_status gmres(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
             g[j + 1] = -sn[j] * g[j];
             g[j] = cs[j] * g[j];
             for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i];
-            if (std::fabs(g[j + 1]) / bn <= o.tol) {
+            if (std::fabs(g[j + 1]) / bn <= tol) {
                 ++j;
                 break;
             }
@@ -597,7 +592,96 @@ static kfmm_status gmres(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
         }
         BK_TRY(maxpy(b, x, V, n, j, y.data(), 1.0, n));
     }
+    *iters = it;
+    *rel_out = rel;
+    *conv_out = conv;
+    return KFMM_OK;
+}
+
+// Plain GMRES on the context's operator (FP64 direct, or FMM with FP64 Krylov vectors).
+static kfmm_status gmres(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
+{
+    const int64_t n = 3 * b->nt;
+    BK_CUDA(b->x.ensure(sizeof(double) * n));
+    BK_CUDA(b->b.ensure(sizeof(double) * n));
+    double *x = b->x.as<double>(), *rhs = b->b.as<double>();
+    BK_TRY(bem_op_apply(b, 2, nullptr, nullptr, b->val.as<double>(), rhs));
+    double bn;
+    BK_TRY(vnorm(b, rhs, n, &bn));
+    if (bn == 0.0) bn = 1.0;
+    if (o.x0) {
+        const void *dx0;
+        BK_TRY(bem_stage(b, b->stage[0], o.x0, sizeof(double) * n, &dx0));
+        BK_CUDA(cudaMemcpyAsync(x, dx0, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
+    }
+    int it = 0;
+    double rel = 1.0;
+    bool conv = false;
+    BK_TRY(gmres_core(b, b->op, rhs, x, o.x0 == nullptr, bn, o.tol, o.restart, o.maxit, &it, &rel, &conv));
     st->iters = it;
+    st->outer = 1;
+    st->converged = conv;
+    st->relres = rel;
+    return KFMM_OK;
+}
+
+// Mixed-precision GMRES with iterative refinement: the right-hand side, every outer residual
+// r = b - A x and the update x += d are FP64 with the direct (exact discrete) operator; each
+// correction solves A d = r by GMRES on the FP32 FMM operator to the relative tolerance
+// inner_tol.  The relative residual reported is the FP64 direct one.
+static kfmm_status gmres_ir(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
+{
+    const int64_t n = 3 * b->nt;
+    BK_CUDA(b->x.ensure(sizeof(double) * n));
+    BK_CUDA(b->b.ensure(sizeof(double) * n));
+    BK_CUDA(b->d.ensure(sizeof(double) * n));
+    BK_CUDA(b->rhs_hi.ensure(sizeof(double) * n));
+    BK_CUDA(b->w.ensure(sizeof(double) * n));
+    double *x = b->x.as<double>(), *rhs = b->b.as<double>(), *d = b->d.as<double>(), *r = b->rhs_hi.as<double>();
+    BK_TRY(bem_op_apply(b, 2, nullptr, nullptr, b->val.as<double>(), rhs, BEM_DIRECT_FP64));
+    double bn;
+    BK_TRY(vnorm(b, rhs, n, &bn));
+    if (bn == 0.0) bn = 1.0;
+    if (o.x0) {
+        const void *dx0;
+        BK_TRY(bem_stage(b, b->stage[0], o.x0, sizeof(double) * n, &dx0));
+        BK_CUDA(cudaMemcpyAsync(x, dx0, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
+    } else {
+        BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, b->stream));
+    }
+    int inner_total = 0, outer = 0;
+    double rel = 1.0;
+    bool conv = false;
+    const double one = 1.0;
+    while (true) {
+        // outer residual in FP64 with the direct operator
+        if (o.x0 || outer > 0) {
+            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, x, b->w.as<double>(), BEM_DIRECT_FP64));
+            sub_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(r, rhs, b->w.as<double>(), n);
+            BK_LAUNCH();
+        } else {
+            BK_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
+        }
+        double rn;
+        BK_TRY(vnorm(b, r, n, &rn));
+        rel = rn / bn;
+        if (rel <= o.tol) {
+            conv = true;
+            break;
+        }
+        if (outer >= o.max_outer || inner_total >= o.maxit) break;
+        // correction on the fast operator: A_fmm d = r to inner_tol relative to ||r||
+        int it = 0;
+        double irel = 1.0;
+        bool iconv = false;
+        BK_TRY(gmres_core(b, BEM_FMM, r, d, true, rn, o.inner_tol, o.restart, o.maxit - inner_total, &it, &irel,
+                          &iconv));
+        inner_total += it;
+        ++outer;
+        BK_TRY(maxpy(b, x, d, n, 1, &one, 1.0, n));
+    }
+    st->iters = inner_total;
+    st->outer = outer;
     st->converged = conv;
     st->relres = rel;
     return KFMM_OK;
@@ -612,6 +696,9 @@ void bem_default_solve_opts(bem_solve_opts *o)
     o->restart = 30;
     o->maxit = 1000;
     o->x0 = nullptr;
+    o->refine = 0;
+    o->inner_tol = 1e-3;
+    o->max_outer = 30;
 }
 
 kfmm_status bem_create(bem_ctx **out, const kfmm_options *opt, int op, const double *verts, int64_t nv,
@@ -777,10 +864,14 @@ kfmm_status bem_solve(bem_ctx *b, const bem_solve_opts *opts, double *u, double 
     if (opts) o = *opts;
     if (!(o.tol > 0) || o.restart < 1 || o.restart > 200 || o.maxit < 1)
         return b->fail(KFMM_ERR_INVALID_ARG, "bem_solve: need tol > 0, 1 <= restart <= 200, maxit >= 1");
+    if (o.refine && (b->op != BEM_FMM || !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_outer < 1))
+        return b->fail(KFMM_ERR_INVALID_ARG,
+                       "bem_solve: refinement needs an FMM context, 0 < inner_tol < 1 and max_outer >= 1");
     const auto t0 = std::chrono::steady_clock::now();
     bem_stats s{};
-    const int mv0 = b->matvecs;
-    BK_TRY(gmres(b, o, &s));
+    const int mv0 = b->matvecs, mh0 = b->matvecs_hi;
+    if (o.refine) BK_TRY(gmres_ir(b, o, &s));
+    else BK_TRY(gmres(b, o, &s));
     const int64_t n = 3 * b->nt;
     split_kernel<<<g1(n), 256, 0, b->stream>>>(n, b->x.as<double>(), b->mask.as<uint8_t>(), b->val.as<double>(),
                                                 b->usol.as<double>(), b->tsol.as<double>());
@@ -790,6 +881,7 @@ kfmm_status bem_solve(bem_ctx *b, const bem_solve_opts *opts, double *u, double 
     if (t) BK_CUDA(cudaMemcpyAsync(t, b->tsol.p, sizeof(double) * n, cudaMemcpyDefault, b->stream));
     BK_CUDA(cudaStreamSynchronize(b->stream));
     s.matvecs = b->matvecs - mv0;
+    s.matvecs_hi = b->matvecs_hi - mh0;
     s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (st) *st = s;
     if (!s.converged) return b->fail(KFMM_ERR_NOT_CONVERGED, "bem_solve: iteration cap reached");

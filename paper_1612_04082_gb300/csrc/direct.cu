@@ -1,6 +1,10 @@
 // direct.cu -- all-pairs summation of Eq. fmm_summation on the GPU (no tree), FP32 or FP64.
 // One thread per target; sources are staged through shared memory in tiles, pre-scaled
-// once per tile so the inner loop carries no constant factors.
+// once per tile so the inner loop carries no constant factors.  When the targets alone give
+// too few CTAs to fill the GPU, the sources are split over a second grid dimension and the
+// partial sums are added atomically into the zeroed output.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kelvin.cuh"
 
@@ -22,9 +26,12 @@ template <typename R, int KIND, bool SL, bool DL>
 __global__ void __launch_bounds__(kDirThreads)
 direct_kernel(const R *__restrict__ trg, int64_t ntrg, const R *__restrict__ src,
               const R *__restrict__ nrm, const R *__restrict__ sl, const R *__restrict__ dl,
-              int64_t nsrc, KelvinConst<R> kc, R *__restrict__ out)
+              int64_t nsrc, int64_t chunk, KelvinConst<R> kc, R *__restrict__ out)
 {
     __shared__ SrcTile<R> tile;
+    const int64_t s_begin = (int64_t)blockIdx.y * chunk;
+    const int64_t s_end = s_begin + chunk < nsrc ? s_begin + chunk : nsrc;
+    const bool split = gridDim.y > 1;
     const int64_t i = (int64_t)blockIdx.x * kDirThreads + threadIdx.x;
     const bool active = i < ntrg;
     R x = 0, y = 0, z = 0;
@@ -34,10 +41,10 @@ direct_kernel(const R *__restrict__ trg, int64_t ntrg, const R *__restrict__ src
         z = trg[3 * i + 2];
     }
     R o[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t base = 0; base < nsrc; base += kDirThreads) {
+    for (int64_t base = s_begin; base < s_end; base += kDirThreads) {
         const int64_t j = base + threadIdx.x;
         __syncthreads();
-        if (j < nsrc) {
+        if (j < s_end) {
             for (int a = 0; a < 3; ++a) tile.y[a][threadIdx.x] = src[3 * j + a];
             R tv[3] = {0, 0, 0}, uv[3] = {0, 0, 0}, nv[3] = {0, 0, 0};
             if (SL)
@@ -70,7 +77,7 @@ direct_kernel(const R *__restrict__ trg, int64_t ntrg, const R *__restrict__ src
             tile.nup[threadIdx.x] = 0;
         }
         __syncthreads();
-        const int cnt = (int)((nsrc - base) < kDirThreads ? (nsrc - base) : kDirThreads);
+        const int cnt = (int)((s_end - base) < kDirThreads ? (s_end - base) : kDirThreads);
         for (int s = 0; s < cnt; ++s) {
             R dx = x - tile.y[0][s], dy = y - tile.y[1][s], dz = z - tile.y[2][s];
             if (KIND == KFMM_DISP) {
@@ -98,12 +105,11 @@ direct_kernel(const R *__restrict__ trg, int64_t ntrg, const R *__restrict__ src
         }
     }
     if (!active) return;
-    if (KIND == KFMM_DISP) {
-        out[3 * i] = o[0];
-        out[3 * i + 1] = o[1];
-        out[3 * i + 2] = o[2];
-    } else {
-        for (int a = 0; a < 6; ++a) out[6 * i + a] = kc.c_D * o[a];
+    constexpr int NO = KIND == KFMM_DISP ? 3 : 6;
+    const R sc = KIND == KFMM_DISP ? R(1) : kc.c_D;
+    for (int a = 0; a < NO; ++a) {
+        if (split) atomicAdd(out + NO * i + a, sc * o[a]);
+        else out[NO * i + a] = sc * o[a];
     }
 }
 
@@ -111,16 +117,26 @@ template <typename R, int KIND>
 void launch_direct(const R *trg, int64_t ntrg, const R *src, const R *nrm, const R *sl, const R *dl,
                    int64_t nsrc, KelvinConst<R> kc, R *out, cudaStream_t st)
 {
-    dim3 grid((unsigned)((ntrg + kDirThreads - 1) / kDirThreads));
+    // source chunks: enough CTAs for ~4 per SM, at least 1024 sources per chunk
+    const int64_t tb = (ntrg + kDirThreads - 1) / kDirThreads;
+    int64_t ns = (4 * 152 + tb - 1) / tb;
+    ns = std::min<int64_t>(ns, (nsrc + 1023) / 1024);
+    ns = std::max<int64_t>(ns, 1);
+    ns = std::min<int64_t>(ns, 65535);
+    int64_t chunk = (nsrc + ns - 1) / ns;
+    chunk = (chunk + kDirThreads - 1) / kDirThreads * kDirThreads;
+    ns = std::max<int64_t>(1, (nsrc + chunk - 1) / chunk);
+    if (ns > 1) cudaMemsetAsync(out, 0, sizeof(R) * (KIND == KFMM_DISP ? 3 : 6) * ntrg, st);
+    dim3 grid((unsigned)tb, (unsigned)ns);
     if (sl && dl)
         direct_kernel<R, KIND, true, true><<<grid, kDirThreads, 0, st>>>(trg, ntrg, src, nrm, sl, dl,
-                                                                         nsrc, kc, out);
+                                                                         nsrc, chunk, kc, out);
     else if (sl)
         direct_kernel<R, KIND, true, false><<<grid, kDirThreads, 0, st>>>(trg, ntrg, src, nrm, sl, dl,
-                                                                          nsrc, kc, out);
+                                                                          nsrc, chunk, kc, out);
     else
         direct_kernel<R, KIND, false, true><<<grid, kDirThreads, 0, st>>>(trg, ntrg, src, nrm, sl, dl,
-                                                                          nsrc, kc, out);
+                                                                          nsrc, chunk, kc, out);
 }
 
 }  // namespace

@@ -147,6 +147,61 @@ def test_mixed_bc_cantilever_fmm(K):
     assert np.linalg.norm(A @ x - bb) / np.linalg.norm(bb) < bound
 
 
+def test_mixed_bc_cantilever_refined(K):
+    """Mixed-precision GMRES with iterative refinement (FP64 direct residuals, FP32 FMM
+    corrections at p = 6) reaches a true residual of 1e-8 that the FMM operator alone cannot
+    (its rounding floor is ~5e-5 on this problem) and matches the oracle's dense solution as
+    the FP64 solve does."""
+    V, T, mask, vals, nrm, area, cen = cantilever(3)
+    H, Gm = O.bem_assemble(V, T, G0, NU0)
+    A, bb = O.bem_system(H, Gm, mask, vals)
+    u_ref, t_ref = O.unknowns_to_fields(np.linalg.solve(A, bb), mask, vals)
+    with K.Bem(V, T, K.BEM_FMM) as b:
+        b.set_material(K.material_K(G0, NU0), G0)
+        b.set_bc(mask, vals)
+        u, t = np.zeros((len(T), 3)), np.zeros((len(T), 3))
+        st = b.solve(u, t, tol=1e-8, restart=100, maxit=2000, refine=True, inner_tol=1e-3)
+    assert st["converged"] and st["relres"] <= 1e-8
+    assert st["outer"] >= 1 and st["matvecs_hi"] == st["outer"] + 1
+    assert rel(u, u_ref) < 1e-6 and rel(t, t_ref) < 1e-5
+
+
+def test_lame_sphere_refined(K, sphere):
+    """Refinement on the singular pure-traction system (Lame sphere): the FP64 residual falls
+    to 1e-8 and the displacement matches the dense FP64 solution after the rigid modes are
+    removed."""
+    V, T, H, Gm, nrm, area, cen = sphere
+    mask = np.zeros((len(T), 3), np.uint8)
+    A, bb = O.bem_system(H, Gm, mask, nrm)
+    x, ok, it, relres = O.gmres(A, bb, tol=1e-10, restart=60, maxit=500)
+    u_ref = O.remove_rigid_modes(x.reshape(-1, 3), cen, area)
+    with K.Bem(V, T, K.BEM_FMM) as b:
+        b.set_material(K.material_K(G0, NU0), G0)
+        b.set_bc(mask, nrm)
+        u = np.zeros((len(T), 3))
+        st = b.solve(u, None, tol=1e-8, restart=60, refine=True, inner_tol=1e-3)
+    assert st["converged"] and st["relres"] <= 1e-8
+    assert rel(O.remove_rigid_modes(u, cen, area), u_ref) < 1e-6
+
+
+def test_refine_arguments(K, sphere):
+    V, T, H, Gm, nrm, area, cen = sphere
+    mask = np.zeros((len(T), 3), np.uint8)
+    with K.Bem(V, T, K.BEM_DIRECT_FP64) as b:  # refinement needs an FMM context
+        b.set_material(K.material_K(G0, NU0), G0)
+        b.set_bc(mask, nrm)
+        with pytest.raises(K.KfmmError) as e:
+            b.solve(np.zeros((len(T), 3)), refine=True)
+        assert e.value.status == K.KFMM_ERR_INVALID_ARG
+    with K.Bem(V, T, K.BEM_FMM) as b:
+        b.set_material(K.material_K(G0, NU0), G0)
+        b.set_bc(mask, nrm)
+        for kw in ({"inner_tol": 0.0}, {"inner_tol": 1.5}, {"max_outer": 0}):
+            with pytest.raises(K.KfmmError) as e:
+                b.solve(np.zeros((len(T), 3)), refine=True, **kw)
+            assert e.value.status == K.KFMM_ERR_INVALID_ARG
+
+
 def test_interior_stress_and_td(K):
     """Uniform tension of the benchmark cube (E = 1, nu = 0.3): interior stress and D^T from
     the GPU (FMM and FP64 direct) against the oracle's Somigliana sums on the same boundary

@@ -12,6 +12,10 @@ of the single + double layer sum (S2M, M2M, M2L, P2L, L2L, L2P, M2P, P2P).
 N > 1 runs one independent replica per GPU (weak scaling, no collective on the data path);
 value = all ranks' targets / the slowest rank's time.  --impl reference times the FP64 CPU
 oracle (direct summation) on the host cores over a bounded sample of the same workload.
+
+The line also carries the BEM leg of the metric ("bem"): a mixed-boundary cantilever solved
+to a 1e-6 relative residual of the exact FP64 discrete operator by mixed-precision GMRES with
+iterative refinement (FP32 FMM corrections), beside plain FP64 GMRES on the same GPU.
 """
 from __future__ import annotations
 
@@ -38,6 +42,20 @@ SM_MAX_MHZ = 2070.0
 FLOPS_SLDL = 61   # single + double layer displacement
 FLOPS_SL = 30     # single layer only (equivalent densities: L2P, M2P)
 L2_FLUSH_BYTES = 512 << 20
+BEM_N = 12          # cantilever cells per unit length: 40 n^2 = 5760 triangles
+# DRAM bytes per launch of the dominant kernel at this workload, from
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/); None when the
+# kernel has changed since the counters were taken
+TRAFFIC_BYTES = {"m2l": 412841728 + 153561856}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return pk, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
 def fp32_peak_tflops(mhz):
@@ -142,6 +160,45 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def bem_leg(K, local, world):
+    """Cantilever (40 n^2 triangles, clamped at x = 0, unit traction patch at x = 2) solved to a
+    1e-6 relative residual of the FP64 direct operator: mixed-precision GMRES-IR on the FMM
+    (timed over 3 solves after a warm-up) and plain FP64 GMRES with the direct operator."""
+    import torch
+    import workloads as W
+    V, T, mask, vals = W.cantilever(BEM_N)
+    nt = len(T)
+    u, t = np.zeros((nt, 3)), np.zeros((nt, 3))
+    out = {"workload": f"cantilever 2x1x1, {nt} triangles ({3 * nt} unknowns), mixed BC, G=1, nu=0.3",
+           "tol": 1e-6, "residual": "FP64 direct discrete operator"}
+    with K.Bem(V, T, K.BEM_FMM, device=local) as b:
+        b.set_material(K.material_K(1.0, 0.3), 1.0)
+        b.set_bc(mask, vals)
+        kw = dict(tol=1e-6, restart=100, maxit=3000, refine=True, inner_tol=1e-3)
+        b.solve(u, t, **kw)
+        times, st = [], None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            st = b.solve(u, t, **kw)
+            times.append(st["seconds"])
+    sec = float(np.mean(times))
+    if world > 1:
+        tt = torch.tensor([sec], device=f"cuda:{local}")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        sec = float(tt.item())
+    out.update({"solves_per_s": world / sec, "ms_per_solve": 1e3 * sec, "inner_iters": st["iters"],
+                "outer": st["outer"], "fmm_matvecs": st["matvecs"], "fp64_matvecs": st["matvecs_hi"],
+                "relres": st["relres"], "method": "GMRES-IR: FP32 FMM corrections (p=6), FP64 direct residuals"})
+    with K.Bem(V, T, K.BEM_DIRECT_FP64, device=local) as b:
+        b.set_material(K.material_K(1.0, 0.3), 1.0)
+        b.set_bc(mask, vals)
+        st = b.solve(u, t, tol=1e-6, restart=100, maxit=3000)
+    out["fp64_gmres"] = {"ms_per_solve": 1e3 * st["seconds"], "iters": st["iters"], "relres": st["relres"],
+                         "method": "plain GMRES, FP64 direct operator on the GPU"}
+    out["speedup_vs_fp64_gmres"] = st["seconds"] / sec
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -152,6 +209,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2000)
     ap.add_argument("--ref-sample", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bem", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -242,26 +300,49 @@ def main():
     h2d = 4 * 3 * args.n * 4  # points (as sources and targets), normals, two densities
     d2h = 4 * 3 * args.n
 
-    # ---- roofline of the dominant phase (FP32 ALU bound: pair evaluations / GEMM flops)
-    dom = max((k for k in ph_ms if k != "tree"), key=lambda k: ph_ms[k])
+    # ---- rooflines per phase (CUDA-event time per step); the dominant one goes in "roofline"
     r = st["m2l_rank"]
     m = 3 * st["n_surf"]
-    flops = {
-        "eval": st["p2p_interactions"] * FLOPS_SLDL + st["l2p_interactions"] * FLOPS_SL,
-        "m2l": st["n_v_pairs"] * 2 * r * r + st["n_boxes"] * 2 * r * m,
-        "s2m": args.n * st["n_surf"] * FLOPS_SLDL,
-        "up_pinv": st["n_leaves"] * 2 * m * m,
-        "m2m": (st["n_boxes"] - 1) * 2 * m * m,
-        "down": st["n_boxes"] * 2 * m * r + (st["n_boxes"] - 1) * 2 * m * m,
-        "p2l": st["p2l_interactions"] * FLOPS_SLDL,
+    ku, kd = st["up_rank"], st["down_rank"]
+    peaks, peak_src = load_peaks()
+    fp32_peak = fp32_peak_tflops(SM_MAX_MHZ)
+    bf16_peak = peaks["bf16_tflops_sustained"]
+    # (bound, executed operations per step, peak, note)
+    work = {
+        "eval": ("alu", st["p2p_interactions"] * FLOPS_SLDL + st["l2p_interactions"] * FLOPS_SL, fp32_peak,
+                 "FP32 pair evaluations (61 flop SL+DL P2P, 30 flop SL L2P/M2P)"),
+        "s2m": ("alu", st["s2m_interactions"] * FLOPS_SLDL, fp32_peak, "FP32 pair evaluations"),
+        "p2l": ("alu", st["p2l_interactions"] * FLOPS_SLDL, fp32_peak, "FP32 pair evaluations"),
+        "m2l": ("tensor", 3 * 2 * r * r * st["n_v_pairs"], bf16_peak,
+                "BF16 MMA flops: 3 split-pair products per FP32-grade product, 2 r^2 per V pair"),
+        "m2l_basis": ("tensor", 6 * 2 * r * ku * st["n_boxes"], bf16_peak,
+                      "BF16 MMA flops: 6 three-term products per FP32-grade product"),
+        "up_pinv": ("tensor", 6 * 2 * ku * m * st["n_leaves"], bf16_peak, "BF16 MMA flops, three-term splits"),
+        "m2m": ("tensor", 6 * 2 * ku * ku * (st["n_boxes"] - 1), bf16_peak, "BF16 MMA flops, three-term splits"),
+        "down": ("tensor", 6 * 2 * (kd * r * st["n_boxes"] + kd * m * st["n_xboxes"] + kd * kd * (st["n_boxes"] - 1)
+                                    + m * kd * st["n_leaves"] + m * ku * st["n_wboxes"]), bf16_peak,
+                 "BF16 MMA flops, three-term splits"),
     }
-    peak = fp32_peak_tflops(SM_MAX_MHZ)
-    ach = flops.get(dom, 0) / (ph_ms[dom] / 1e3) / 1e12 if ph_ms[dom] > 0 else 0.0
-    roof = {"bound": "alu", "kernel_phase": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": None,
-            "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
-            "frac_at_sampled_clock": (ach / fp32_peak_tflops(clocks["sm_mhz"])) if clocks.get("sm_mhz") else None}
-    p2p_ach = flops["eval"] / (ph_ms["eval"] / 1e3) / 1e12 if ph_ms["eval"] > 0 else 0.0
+
+    def roofline_of(k):
+        bound, ops, peak, note = work[k]
+        t = ph_ms[k] / 1e3
+        ach = ops / t / 1e12 if t > 0 else 0.0
+        return {"bound": bound, "kernel_phase": k, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": TRAFFIC_BYTES.get(k),
+                "peak_note": ("FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz" if bound == "alu"
+                              else f"BF16 dense tensor peak, sustained, of {peak_src} (MEASURED_PEAKS.json)"),
+                "ops_note": note}
+
+    dom = max((k for k in work if k in ph_ms), key=lambda k: ph_ms[k])
+    roof = roofline_of(dom)
+    if clocks.get("sm_mhz") and roof["bound"] == "alu":
+        roof["frac_at_sampled_clock"] = roof["achieved"] / fp32_peak_tflops(clocks["sm_mhz"])
+    kernels = {k: {"ms": ph_ms[k], "frac": roofline_of(k)["frac"], "bound": work[k][0]} for k in work if k in ph_ms}
+    p2p_ach = work["eval"][1] / (ph_ms["eval"] / 1e3) / 1e12 if ph_ms["eval"] > 0 else 0.0
+
+    # ---- BEM leg: mixed-precision refinement vs plain FP64 GMRES at a 1e-6 FP64 residual
+    bem = bem_leg(K, local, world) if not args.no_bem else None
 
     line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -275,8 +356,10 @@ def main():
             "gpu_launches": int(launches),
             "roofline": roof,
             "eval_only_targets_per_s": world * args.n / (eval_ms / 1e3),
-            "p2p_eval_fp32_frac": p2p_ach / peak,
+            "p2p_eval_fp32_frac": p2p_ach / fp32_peak,
             "phases_ms": ph_ms,
+            "kernels": kernels,
+            "bem": bem,
             "tree": {k: st[k] for k in ("n_boxes", "n_leaves", "n_levels", "m2l_rank", "n_v_pairs",
                                         "n_w_pairs", "n_x_pairs", "p2p_interactions")}}
 

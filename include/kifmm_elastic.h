@@ -93,11 +93,17 @@ typedef struct kfmm_stats {
     int64_t n_u_pairs;      /* (target leaf, source leaf) pairs of the U lists               */
     int64_t n_v_pairs;      /* (target box, source box) pairs of the V lists                 */
     int64_t n_w_pairs, n_x_pairs;
-    int64_t p2p_interactions;  /* sum over target leaves of n_trg * (U-list sources)         */
-    int64_t s2m_interactions;  /* n_src (in leaves) * n_surf                                 */
-    int64_t l2p_interactions;  /* n_trg * n_surf * (1 + |W list|)                            */
+    int64_t p2p_interactions;  /* sum over target leaves of n_trg * (U-list sources + sources
+                                  of the W-list boxes evaluated directly)                     */
+    int64_t s2m_interactions;  /* n_src * n_surf                                             */
+    int64_t l2p_interactions;  /* n_trg * n_surf * (1 + W-list boxes evaluated through their
+                                  upward densities)                                          */
     int64_t p2l_interactions;  /* sum over X pairs of n_src(leaf) * n_surf                   */
     int64_t kernel_launches;   /* CUDA kernels this context has launched since kfmm_create   */
+    int32_t up_rank, down_rank;  /* kept singular values of the upward / downward check-to-
+                                    equivalent maps (0 before the first evaluation)          */
+    int32_t n_xboxes, n_wboxes;  /* boxes with an X list; W-list boxes with their own
+                                    upward density evaluated at targets                     */
 } kfmm_stats;
 
 typedef struct kfmm_ctx kfmm_ctx;
@@ -186,11 +192,12 @@ typedef enum kfmm_phase {
     KFMM_PH_S2M = 2,      /* sources -> upward check surfaces of the leaves                 */
     KFMM_PH_UP_PINV = 3,  /* upward check -> upward equivalent densities (leaves)          */
     KFMM_PH_M2M = 4,      /* child -> parent upward densities, bottom-up                   */
-    KFMM_PH_M2L = 5,      /* compression, V-list translation (M2L)                         */
+    KFMM_PH_M2L = 5,      /* V-list translation (M2L) in the shared basis                  */
     KFMM_PH_P2L = 6,      /* X-list sources -> downward check surfaces                      */
     KFMM_PH_DOWN = 7,     /* downward densities and L2L, top-down                          */
     KFMM_PH_EVAL = 8,     /* leaf evaluation: L2P + M2P (W list) + P2P (U list)             */
-    KFMM_N_PHASES = 9
+    KFMM_PH_M2L_BASIS = 9, /* upward densities into the shared M2L basis (compression)       */
+    KFMM_N_PHASES = 10
 } kfmm_phase;
 
 /* Turn per-phase timing on or off (off by default).  Timing adds two event records per

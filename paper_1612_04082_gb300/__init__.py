@@ -48,7 +48,8 @@ class kfmm_stats(ctypes.Structure):
                 ("n_w_pairs", ctypes.c_int64), ("n_x_pairs", ctypes.c_int64),
                 ("p2p_interactions", ctypes.c_int64), ("s2m_interactions", ctypes.c_int64),
                 ("l2p_interactions", ctypes.c_int64), ("p2l_interactions", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("up_rank", ctypes.c_int32), ("down_rank", ctypes.c_int32),
+                ("n_xboxes", ctypes.c_int32), ("n_wboxes", ctypes.c_int32)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -198,7 +199,7 @@ def kfmm_export_list(ctx, which: str):
     return off, items[: n.value]
 
 
-PHASES = ("tree", "pack", "s2m", "up_pinv", "m2m", "m2l", "p2l", "down", "eval")
+PHASES = ("tree", "pack", "s2m", "up_pinv", "m2m", "m2l", "p2l", "down", "eval", "m2l_basis")
 
 
 def kfmm_set_profiling(ctx, enable: bool):

@@ -186,10 +186,14 @@ kfmm_status kfmm_get_stats(const kfmm_ctx *ctx, kfmm_stats *st)
     st->n_w_pairs = T.n_w;
     st->n_x_pairs = T.n_x;
     st->p2p_interactions = T.p2p_pairs;
-    st->s2m_interactions = 0;
+    st->s2m_interactions = T.nsrc * st->n_surf;
     st->l2p_interactions = T.l2p_pairs * st->n_surf;
     st->p2l_interactions = T.p2l_pairs * st->n_surf;
     st->kernel_launches = ctx->n_launch;
+    st->up_rank = ctx->ops.ready ? ctx->ops.ku : 0;
+    st->down_rank = ctx->ops.ready ? ctx->ops.kd : 0;
+    st->n_xboxes = T.n_xboxes;
+    st->n_wboxes = T.n_wboxes;
     return KFMM_OK;
 }
 

@@ -1103,7 +1103,7 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
                             T.oct_child.as<int>(), 0, 1, W.alpha.as<float>(), kup, W.alpha.as<float>(), kup, nullptr,
                             1.f, 2));
         // ---- M2L on the V lists in the shared basis: psi = U_r^T V_u alpha, c += C_v psi
-        ctx->phase(KFMM_PH_M2L);
+        ctx->phase(KFMM_PH_M2L_BASIS);
         KF_TRY(box_gemm(P.all, O.tc_cb, O.cb.as<float>(), 0, r, kup, kup, nullptr, nullptr, 0, 0,
                         W.alpha.as<float>(), kup, W.psi.as<float>(), rp, nullptr, 1.f, 0));
         KF_CUDA(cudaMemsetAsync(W.cdn.p, 0, sizeof(float) * (size_t)nb * rp, st));
@@ -1114,6 +1114,7 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
                 tc::split_pairs_kernel<<<(unsigned)((nchunk + 255) / 256), 256, 0, st>>>(W.psi.as<float>(), nb, rp,
                                                                                          W.psi2.as<uint16_t>());
                 KF_LAUNCH();
+                ctx->phase(KFMM_PH_M2L);
                 const uint32_t smem = tc::smem_bytes(rp);
                 KF_CUDA(cudaFuncSetAttribute(tc::tc_gather_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem));
@@ -1124,6 +1125,7 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
                 KF_LAUNCH();
             }
         } else {
+            ctx->phase(KFMM_PH_M2L);
             KF_TRY(run_gemm(ctx, P.m2l, O.m2l_c.as<float>(), (int64_t)r * rp, r, rp, rp, T.vp_src.as<int>(),
                             T.vp_trg.as<int>(), 0, 0, W.psi.as<float>(), rp, W.cdn.as<float>(), rp, nullptr, 1.f, 2, 1));
         }

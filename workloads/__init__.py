@@ -155,6 +155,21 @@ def box_mesh(nx: int, ny: int, nz: int, h: float, origin=(0.0, 0.0, 0.0)):
     return v, t
 
 
+def cantilever(n: int, patch_half: float = 0.25):
+    """Cantilever 2x1x1 voxel box (cells 1/n, 40 n^2 triangles) with its boundary conditions:
+    displacement 0 on the face x = 0, traction (0, 0, -1) on the x = 2 face elements whose
+    centroids lie within patch_half of (y, z) = (0.5, 0.5), traction 0 elsewhere.
+    Returns verts, tris, known_is_disp [nt, 3] uint8, values [nt, 3]."""
+    v, t = box_mesh(2 * n, n, n, 1.0 / n)
+    c = v[t].mean(axis=1)
+    mask = np.zeros((len(t), 3), np.uint8)
+    vals = np.zeros((len(t), 3))
+    mask[c[:, 0] < 1e-9] = 1
+    load = (c[:, 0] > 2 - 1e-9) & (np.abs(c[:, 1] - 0.5) <= patch_half) & (np.abs(c[:, 2] - 0.5) <= patch_half)
+    vals[load] = [0.0, 0.0, -1.0]
+    return v, t, mask, vals
+
+
 # --------------------------------------------------------------------------- point clouds
 def box_voids(n_voids: int = 20, box=(2.0, 1.0, 1.0), rmin=0.05, rmax=0.15, margin=0.05,
               seed: int = SEED_GEOMETRY):

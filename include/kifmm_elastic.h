@@ -239,12 +239,14 @@ typedef struct bem_solve_opts {
     double tol;        /* stop at ||b - A x|| / ||b|| <= tol (1e-6)                           */
     int restart;       /* GMRES restart length (30; <= 200)                                  */
     int maxit;         /* cap on inner GMRES iterations in total (1000)                      */
-    const double *x0;  /* initial guess of the unknowns [nt][3], or NULL for zero            */
+    const double *x0;  /* initial guess of the unknowns [nt][3], or NULL for zero; a guess
+                          whose residual exceeds ||b|| is dropped for zero                    */
     int refine;        /* 0: GMRES on the context's operator.  1 (FMM contexts): mixed-
                           precision iterative refinement -- right-hand side, outer residuals
                           and updates in FP64 with the direct (exact discrete) operator, each
                           correction by GMRES on the FP32 FMM operator (0)                    */
-    double inner_tol;  /* relative tolerance of each refinement correction (1e-3)            */
+    double inner_tol;  /* relative tolerance of each refinement correction, loosened to what
+                          the outer tolerance still needs near the end (1e-3)                 */
     int max_outer;     /* cap on refinement steps (30)                                       */
 } bem_solve_opts;
 
@@ -257,6 +259,8 @@ typedef struct bem_stats {
     double seconds;   /* wall time of bem_solve                                              */
     int outer;        /* refinement steps (1 without refinement)                            */
     int matvecs_hi;   /* FP64 direct operator applications                                  */
+    double x0_relres; /* ||b - A x0|| / ||b|| of the initial guess (1 for zero; a value > 1
+                         means the guess was dropped for zero)                               */
 } bem_stats;
 
 void bem_default_solve_opts(bem_solve_opts *o);
@@ -302,6 +306,84 @@ kfmm_status bem_topo_derivative(bem_ctx *b, const float *pts, int64_t n, float *
                                 float *stress);
 
 const char *bem_last_error(const bem_ctx *b);
+
+/* ------------------------------------------------------------------------------------
+ * Optimisation driver, host side (Sec. "Parallel optimization procedure"): voxel array
+ * M(i,j,k) uint8 [nx][ny][nz] (1 = material), linear index (i*ny + j)*nz + k; host memory.
+ * ------------------------------------------------------------------------------------ */
+
+/* Boundary of the material voxels: every face between a material voxel and a void voxel or
+ * the outside becomes 4 flat triangles fanned to the face centre (Sec. "Performance and
+ * scalability": 24 N^2 triangles for an N^3 cube), vertex order giving the normal out of
+ * the material.  Corner vertices are shared, then one centre vertex per face.  Outputs:
+ * verts [nv][3] = lattice point * h + origin (origin may be NULL), tris [nt][3],
+ * face_cell [nt] (linear index of the owning voxel), face_dir [nt] (0..5 = -x,+x,-y,+y,
+ * -z,+z).  With all four output pointers NULL only *nv and *nt are set; otherwise *nv and
+ * *nt give the capacities on entry (too small -> KFMM_ERR_INVALID_ARG with the needed
+ * sizes). */
+kfmm_status kfmm_voxel_surface(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, double h,
+                               const double *origin, double *verts, int64_t *nv, int32_t *tris,
+                               int64_t *nt, int64_t *face_cell, int8_t *face_dir);
+
+/* Hard-kill update by thresholding the topological derivative td [nx*ny*nz] over the
+ * material voxels: D_C = D_min + C (D_max - D_min); material voxels with td < D_C that are
+ * not frozen (frozen may be NULL) become void.  0 <= C <= 1.  *removed (may be NULL)
+ * receives the count. */
+kfmm_status kfmm_voxel_threshold(uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, const float *td,
+                                 const uint8_t *frozen, double C, int64_t *removed);
+
+/* Post-processing: material voxels with no material face neighbour become void, then, when
+ * support is non-NULL, so does material not face-connected to a support voxel.  Support
+ * voxels and keep voxels (may be NULL; e.g. the loaded ones) are never removed.  *removed
+ * (may be NULL) receives the count. */
+kfmm_status kfmm_voxel_clean(uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, const uint8_t *support,
+                             const uint8_t *keep, int64_t *removed);
+
+/* ------------------------------------------------------------------------------------
+ * Learned warm start of the optimisation loop's GMRES solves (not in the paper, which
+ * restarts every solve from zero): a multilayer perceptron from per-element features to
+ * the initial guess of the element's unknowns, trained on the GPU on the (features,
+ * converged unknowns) pairs of earlier iterations.  Widths n_in -> n_hidden (ReLU) x
+ * (n_layers - 1) -> n_out; FP32 master weights, forward with their BF16 roundings; inputs
+ * and targets standardised per column with statistics of the last training set (identity
+ * before any training); loss = mean squared error; Adam (beta 0.9, 0.999).  Parameters are
+ * one flat FP32 array: for each layer W [out][in] row-major, then b [out].  Arrays may be
+ * host or device memory.
+ * ------------------------------------------------------------------------------------ */
+typedef struct kfmm_mlp kfmm_mlp;
+
+typedef struct mlp_train_opts {
+    int epochs;      /* passes over the training rows, shuffled each pass (200)        */
+    int batch;       /* rows per Adam step; the last partial batch is dropped (4096)   */
+    double lr;       /* Adam step size (1e-3)                                          */
+    uint64_t seed;   /* shuffling seed (1612)                                           */
+} mlp_train_opts;
+
+typedef struct mlp_train_stats {
+    double final_loss;  /* mean standardised squared error over the last epoch          */
+    int64_t steps;      /* Adam steps taken                                             */
+} mlp_train_stats;
+
+void mlp_default_train_opts(mlp_train_opts *o);
+/* He-uniform initial weights from `seed`, zero biases. */
+kfmm_status mlp_create(kfmm_mlp **out, int n_in, int n_hidden, int n_layers, int n_out, uint64_t seed);
+kfmm_status mlp_destroy(kfmm_mlp *m);
+kfmm_status mlp_set_stream(kfmm_mlp *m, void *stream);
+int64_t mlp_num_params(const kfmm_mlp *m);
+/* on != 0 (default): forward and gradients use the BF16 roundings of the weights; 0: FP32. */
+kfmm_status mlp_set_bf16(kfmm_mlp *m, int on);
+kfmm_status mlp_get_params(const kfmm_mlp *m, float *params);
+kfmm_status mlp_set_params(kfmm_mlp *m, const float *params);
+kfmm_status mlp_get_normalizers(const kfmm_mlp *m, float *x_mu, float *x_sd, float *y_mu, float *y_sd);
+/* Y [n][n_out] = network(X [n][n_in]) in the original (de-standardised) units. */
+kfmm_status mlp_forward(kfmm_mlp *m, const float *X, int64_t n, float *Y);
+/* Loss and its gradient with respect to the parameters on n <= 2^20 rows (current
+ * standardisation), for gradient checks. */
+kfmm_status mlp_loss_grad(kfmm_mlp *m, const float *X, const float *Y, int64_t n, double *loss, float *grad);
+/* Standardisation from (X, Y), then `epochs` of shuffled mini-batch Adam. */
+kfmm_status mlp_train(kfmm_mlp *m, const float *X, const float *Y, int64_t n, const mlp_train_opts *o,
+                      mlp_train_stats *st);
+const char *mlp_last_error(const kfmm_mlp *m);
 
 #ifdef __cplusplus
 }

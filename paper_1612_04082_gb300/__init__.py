@@ -286,7 +286,7 @@ class bem_solve_opts(ctypes.Structure):
 class bem_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("matvecs", ctypes.c_int), ("converged", ctypes.c_int),
                 ("relres", ctypes.c_double), ("seconds", ctypes.c_double), ("outer", ctypes.c_int),
-                ("matvecs_hi", ctypes.c_int)]
+                ("matvecs_hi", ctypes.c_int), ("x0_relres", ctypes.c_double)]
 
 
 _bsig = {
@@ -445,3 +445,179 @@ class Bem:
 def material_K(G: float, nu: float) -> float:
     """Bulk modulus from G and nu (the ABI takes K and G, Eq. elast)."""
     return 2.0 * G * (1.0 + nu) / (3.0 * (1.0 - 2.0 * nu))
+
+
+# ------------------------------------------------------------------ optimisation driver (host)
+_vsig = {
+    "kfmm_voxel_surface": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _vp,
+                                          _vp, ctypes.POINTER(_i64), _vp, ctypes.POINTER(_i64), _vp, _vp]),
+    "kfmm_voxel_threshold": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
+                                            ctypes.c_double, ctypes.POINTER(_i64)]),
+    "kfmm_voxel_clean": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
+                                        ctypes.POINTER(_i64)]),
+}
+for _name, (_res, _args) in _vsig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def _mask_arg(mask):
+    if not (isinstance(mask, np.ndarray) and mask.dtype == np.uint8 and mask.ndim == 3 and mask.flags["C_CONTIGUOUS"]):
+        raise ValueError("mask must be a C-contiguous uint8 [nx, ny, nz] numpy array")
+    return mask.shape
+
+
+def voxel_surface(mask, h=1.0, origin=(0.0, 0.0, 0.0)):
+    """Boundary triangles of the material voxels: (verts [nv,3], tris [nt,3] int32,
+    face_cell [nt] int64, face_dir [nt] int8)."""
+    nx, ny, nz = _mask_arg(mask)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    nv, nt = _i64(0), _i64(0)
+    _check(None, _lib.kfmm_voxel_surface(_ptr(mask), nx, ny, nz, float(h), _ptr(o), None, ctypes.byref(nv), None,
+                                         ctypes.byref(nt), None, None))
+    V = np.zeros((nv.value, 3))
+    T = np.zeros((nt.value, 3), np.int32)
+    cell = np.zeros(nt.value, np.int64)
+    fdir = np.zeros(nt.value, np.int8)
+    _check(None, _lib.kfmm_voxel_surface(_ptr(mask), nx, ny, nz, float(h), _ptr(o), _ptr(V), ctypes.byref(nv),
+                                         _ptr(T), ctypes.byref(nt), _ptr(cell), _ptr(fdir)))
+    return V, T, cell, fdir
+
+
+def voxel_threshold(mask, td, C, frozen=None):
+    """In place: material voxels below D_min + C (D_max - D_min) become void. Returns the count."""
+    nx, ny, nz = _mask_arg(mask)
+    td = np.ascontiguousarray(td, dtype=np.float32).reshape(-1)
+    if td.size != mask.size:
+        raise ValueError("td must have one value per voxel")
+    fz = None if frozen is None else np.ascontiguousarray(frozen, dtype=np.uint8)
+    n = _i64(0)
+    _check(None, _lib.kfmm_voxel_threshold(_ptr(mask), nx, ny, nz, _ptr(td), _ptr(fz), float(C), ctypes.byref(n)))
+    return n.value
+
+
+def voxel_clean(mask, support=None, keep=None):
+    """In place: isolated voxels and material not connected to `support` become void
+    (support and keep voxels stay). Returns the count."""
+    nx, ny, nz = _mask_arg(mask)
+    sp = None if support is None else np.ascontiguousarray(support, dtype=np.uint8)
+    kp = None if keep is None else np.ascontiguousarray(keep, dtype=np.uint8)
+    n = _i64(0)
+    _check(None, _lib.kfmm_voxel_clean(_ptr(mask), nx, ny, nz, _ptr(sp), _ptr(kp), ctypes.byref(n)))
+    return n.value
+
+
+# ------------------------------------------------------------------ learned warm start (MLP)
+class mlp_train_opts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class mlp_train_stats(ctypes.Structure):
+    _fields_ = [("final_loss", ctypes.c_double), ("steps", ctypes.c_int64)]
+
+
+_msig = {
+    "mlp_default_train_opts": (None, [ctypes.POINTER(mlp_train_opts)]),
+    "mlp_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_uint64]),
+    "mlp_destroy": (ctypes.c_int, [_vp]),
+    "mlp_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "mlp_num_params": (ctypes.c_int64, [_vp]),
+    "mlp_set_bf16": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "mlp_get_params": (ctypes.c_int, [_vp, _vp]),
+    "mlp_set_params": (ctypes.c_int, [_vp, _vp]),
+    "mlp_get_normalizers": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "mlp_forward": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
+    "mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
+    "mlp_train": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(mlp_train_opts),
+                                 ctypes.POINTER(mlp_train_stats)]),
+    "mlp_last_error": (ctypes.c_char_p, [_vp]),
+}
+for _name, (_res, _args) in _msig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def _mcheck(h, status):
+    if status != KFMM_OK:
+        raise KfmmError(status, _lib.mlp_last_error(h).decode() if h else "")
+
+
+def _f32(a):
+    if hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Mlp:
+    """Warm-start network: n_in -> n_hidden (ReLU) x (n_layers - 1) -> n_out, trained on the GPU."""
+
+    def __init__(self, n_in=11, n_hidden=256, n_layers=4, n_out=3, seed=1612):
+        h = _vp()
+        _mcheck(None, _lib.mlp_create(ctypes.byref(h), n_in, n_hidden, n_layers, n_out, seed))
+        self.handle = h
+        self.n_in, self.n_out = n_in, n_out
+
+    def close(self):
+        if self.handle:
+            _lib.mlp_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self):
+        return int(_lib.mlp_num_params(self.handle))
+
+    def set_bf16(self, on=True):
+        _mcheck(self.handle, _lib.mlp_set_bf16(self.handle, int(bool(on))))
+
+    def get_params(self):
+        p = np.zeros(self.num_params, np.float32)
+        _mcheck(self.handle, _lib.mlp_get_params(self.handle, _ptr(p)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.num_params:
+            raise ValueError("wrong parameter count")
+        _mcheck(self.handle, _lib.mlp_set_params(self.handle, _ptr(p)))
+
+    def normalizers(self):
+        xm, xs = np.zeros(self.n_in, np.float32), np.zeros(self.n_in, np.float32)
+        ym, ys = np.zeros(self.n_out, np.float32), np.zeros(self.n_out, np.float32)
+        _mcheck(self.handle, _lib.mlp_get_normalizers(self.handle, _ptr(xm), _ptr(xs), _ptr(ym), _ptr(ys)))
+        return xm, xs, ym, ys
+
+    def forward(self, X, out=None):
+        X = _f32(X)
+        if out is None:
+            out = np.zeros((_nrows(X), self.n_out), np.float32)
+        _mcheck(self.handle, _lib.mlp_forward(self.handle, _ptr(X), _nrows(X), _ptr(out)))
+        return out
+
+    def loss_grad(self, X, Y):
+        X, Y = _f32(X), _f32(Y)
+        loss = ctypes.c_double(0.0)
+        g = np.zeros(self.num_params, np.float32)
+        _mcheck(self.handle, _lib.mlp_loss_grad(self.handle, _ptr(X), _ptr(Y), _nrows(X), ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def train(self, X, Y, epochs=200, batch=4096, lr=1e-3, seed=1612):
+        X, Y = _f32(X), _f32(Y)
+        o = mlp_train_opts(int(epochs), int(batch), float(lr), int(seed))
+        st = mlp_train_stats()
+        _mcheck(self.handle, _lib.mlp_train(self.handle, _ptr(X), _ptr(Y), _nrows(X), ctypes.byref(o), ctypes.byref(st)))
+        return {"final_loss": st.final_loss, "steps": st.steps}

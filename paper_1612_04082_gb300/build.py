@@ -14,8 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libkifmm_elastic.so")
-CU = ["api.cu", "direct.cu", "tree.cu", "fmm.cu", "bem.cu", "direct_noalloc.cu"]
-CPP = ["precompute.cpp"]
+CU = ["api.cu", "direct.cu", "tree.cu", "fmm.cu", "bem.cu", "direct_noalloc.cu", "mlp.cu"]
+CPP = ["precompute.cpp", "voxel.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -519,7 +519,7 @@ static kfmm_status vnorm(bem_ctx *b, const double *w, int64_t n, double *out)
 // iterate; stops at ||rhs - A x|| <= tol * bn (true residual at every restart) or after
 // maxit inner iterations.  *iters, *rel (true residual / bn) and *conv are returned.
 static kfmm_status gmres_core(bem_ctx *b, int which, const double *rhs, double *x, bool zero_x, double bn, double tol,
-                              int m, int maxit, int *iters, double *rel_out, bool *conv_out)
+                              int m, int maxit, int *iters, double *rel_out, bool *conv_out, double *x0_rel = nullptr)
 {
     const int64_t n = 3 * b->nt;
     BK_CUDA(b->basis.ensure(sizeof(double) * (size_t)(m + 1) * n));
@@ -542,6 +542,13 @@ static kfmm_status gmres_core(bem_ctx *b, int which, const double *rhs, double *
         }
         double beta;
         BK_TRY(vnorm(b, r, n, &beta));
+        if (!zero_x && it == 0 && x0_rel) *x0_rel = beta / bn;
+        if (!zero_x && it == 0 && beta > bn) {
+            // an initial guess worse than zero is dropped: plain GMRES from zero
+            BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, b->stream));
+            BK_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
+            BK_TRY(vnorm(b, r, n, &beta));
+        }
         rel = beta / bn;
         if (rel <= tol) {
             conv = true;
@@ -615,9 +622,10 @@ static kfmm_status gmres(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
         BK_CUDA(cudaMemcpyAsync(x, dx0, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
     }
     int it = 0;
-    double rel = 1.0;
+    double rel = 1.0, x0_rel = 1.0;
     bool conv = false;
-    BK_TRY(gmres_core(b, b->op, rhs, x, o.x0 == nullptr, bn, o.tol, o.restart, o.maxit, &it, &rel, &conv));
+    BK_TRY(gmres_core(b, b->op, rhs, x, o.x0 == nullptr, bn, o.tol, o.restart, o.maxit, &it, &rel, &conv, &x0_rel));
+    st->x0_relres = x0_rel;
     st->iters = it;
     st->outer = 1;
     st->converged = conv;
@@ -638,6 +646,7 @@ static kfmm_status gmres_ir(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
     BK_CUDA(b->rhs_hi.ensure(sizeof(double) * n));
     BK_CUDA(b->w.ensure(sizeof(double) * n));
     double *x = b->x.as<double>(), *rhs = b->b.as<double>(), *d = b->d.as<double>(), *r = b->rhs_hi.as<double>();
+    st->x0_relres = 1.0;
     BK_TRY(bem_op_apply(b, 2, nullptr, nullptr, b->val.as<double>(), rhs, BEM_DIRECT_FP64));
     double bn;
     BK_TRY(vnorm(b, rhs, n, &bn));
@@ -664,17 +673,27 @@ static kfmm_status gmres_ir(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
         }
         double rn;
         BK_TRY(vnorm(b, r, n, &rn));
+        if (o.x0 && outer == 0) st->x0_relres = rn / bn;
+        if (o.x0 && outer == 0 && rn > bn) {
+            // an initial guess worse than zero is dropped: refinement from zero
+            BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, b->stream));
+            BK_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
+            rn = bn;
+        }
         rel = rn / bn;
         if (rel <= o.tol) {
             conv = true;
             break;
         }
         if (outer >= o.max_outer || inner_total >= o.maxit) break;
-        // correction on the fast operator: A_fmm d = r to inner_tol relative to ||r||
+        // correction on the fast operator: A_fmm d = r to inner_tol relative to ||r||, or
+        // only as far as the outer target needs (with a factor 5 of margin for the gap
+        // between the FMM and the FP64 operator) when closer
+        const double itol = std::max(o.inner_tol, 0.2 * o.tol * bn / rn);
         int it = 0;
         double irel = 1.0;
         bool iconv = false;
-        BK_TRY(gmres_core(b, BEM_FMM, r, d, true, rn, o.inner_tol, o.restart, o.maxit - inner_total, &it, &irel,
+        BK_TRY(gmres_core(b, BEM_FMM, r, d, true, rn, itol, o.restart, o.maxit - inner_total, &it, &irel,
                           &iconv));
         inner_total += it;
         ++outer;

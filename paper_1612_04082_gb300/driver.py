@@ -1,0 +1,263 @@
+"""Topology optimisation driver (Sec. "Parallel optimization procedure").
+
+Each iteration:
+1. contours the material voxels with boundary triangles (native `voxel_surface`);
+2. sets the boundary conditions;
+3. solves the BVP by the FMM-accelerated BEM;
+4. evaluates the topological derivative (Eq. deriv) at the centres of the material voxels;
+5. removes the voxels below D_C = D_min + C (D_max - D_min) (native `voxel_threshold`);
+6. post-processes the voxel array (native `voxel_clean`).
+
+It stops when the volume ratio alpha reaches alpha_c.  The compliance Psi = 1/2 int t.u dGamma
+(Eq. functional with the BEM solution) and alpha are recorded per iteration, together with the
+per-element features and converged unknowns that train the learned warm start.
+
+This module only orchestrates: every array operation of the path runs in the library (GPU
+kernels for the BEM and the fields, native host code for the voxel operations).
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import (BEM_FMM, Bem, Mlp, material_K, voxel_clean, voxel_surface, voxel_threshold)
+
+FACE_NORMALS = np.array([[-1, 0, 0], [1, 0, 0], [0, -1, 0], [0, 1, 0], [0, 0, -1], [0, 0, 1]], np.float64)
+
+
+@dataclass
+class Problem:
+    """Voxel domain [0, nx h] x [0, ny h] x [0, nz h] with supports and loads on voxel faces."""
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    support: np.ndarray   # uint8 [nx, ny, nz]: voxels whose support faces are clamped (never removed)
+    loaded: np.ndarray    # uint8 [nx, ny, nz]: voxels carrying the load (never removed)
+    support_dir: int      # face direction (0..5) of the clamped faces
+    load_dir: int         # face direction of the loaded faces
+    traction: tuple = (0.0, 0.0, -1.0)
+    G: float = 1.0
+    nu: float = 0.3
+
+    def frozen(self):
+        return ((self.support + self.loaded) > 0).astype(np.uint8)
+
+    def boundary_conditions(self, cell, fdir):
+        """known_is_disp [nt, 3] uint8 and values [nt, 3] for the faces (cell, fdir)."""
+        nt = len(cell)
+        kd = np.zeros((nt, 3), np.uint8)
+        vals = np.zeros((nt, 3))
+        sup = (self.support.reshape(-1)[cell] > 0) & (fdir == self.support_dir)
+        lod = (self.loaded.reshape(-1)[cell] > 0) & (fdir == self.load_dir)
+        kd[sup] = 1
+        vals[lod & ~sup] = self.traction
+        return kd, vals
+
+
+def cantilever(n: int, patch_half: float = 0.25) -> Problem:
+    """2x1x1 box of (2n, n, n) voxels: clamped on x = 0, traction (0, 0, -1) on the x = 2 face
+    within patch_half of (y, z) = (0.5, 0.5)."""
+    nx, ny, nz, h = 2 * n, n, n, 1.0 / n
+    sup = np.zeros((nx, ny, nz), np.uint8)
+    sup[0] = 1
+    lod = np.zeros_like(sup)
+    c = (np.arange(n) + 0.5) * h
+    sel = np.abs(c - 0.5) <= patch_half
+    lod[nx - 1][np.ix_(sel, sel)] = 1
+    return Problem(nx, ny, nz, h, sup, lod, 0, 1)
+
+
+def bridge(n: int) -> Problem:
+    """3x1x1 box of (3n, n, n) voxels: u = 0 on the bottom face z = 0 over |x - 0.15| < 0.15
+    and |x - 2.85| < 0.15, traction (0, 0, -1) on the top face z = 1."""
+    nx, ny, nz, h = 3 * n, n, n, 1.0 / n
+    x = (np.arange(nx) + 0.5) * h
+    sup = np.zeros((nx, ny, nz), np.uint8)
+    sup[(np.abs(x - 0.15) < 0.15) | (np.abs(x - 2.85) < 0.15), :, 0] = 1
+    lod = np.zeros_like(sup)
+    lod[:, :, nz - 1] = 1
+    return Problem(nx, ny, nz, h, sup, lod, 4, 5)
+
+
+def triangle_geometry(V, T):
+    a, b, c = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    cr = np.cross(b - a, c - a)
+    area = 0.5 * np.linalg.norm(cr, axis=1)
+    return (a + b + c) / 3.0, cr / (2.0 * area[:, None]), area
+
+
+@dataclass
+class IterationRecord:
+    """One optimisation iteration: per-element features and the converged unknowns."""
+    features: np.ndarray  # [nt, 11]: centroid 3, normal 3, area 1, previous unknowns 3, local TD 1
+    unknowns: np.ndarray  # [nt, 3]: converged x (u where t is prescribed, t where u is)
+    face_key: np.ndarray  # [nt] int64: (cell * 6 + dir) * 4 + triangle of the face
+    stats: dict = field(default_factory=dict)
+
+
+def face_keys(cell, fdir):
+    tri = np.arange(len(cell)) % 4  # the 4 triangles of a face are consecutive
+    return (cell.astype(np.int64) * 6 + fdir.astype(np.int64)) * 4 + tri
+
+
+def features_for(V, T, cell, fdir, prev: IterationRecord | None, td_prev: np.ndarray | None, prev_bem=None,
+                 kd=None):
+    """The 11 per-element features of the warm-start model.  The previous iterate's unknowns
+    are carried over by face identity; on faces new at this iteration (exposed by removed
+    voxels, so inside the previous domain) the unknown displacement is the previous
+    solution's interior displacement at the centroid (by the BIE, `bem_interior`)."""
+    cen, nrm, area = triangle_geometry(V, T)
+    keys = face_keys(cell, fdir)
+    xprev = np.zeros((len(T), 3))
+    if prev is not None:
+        order = np.argsort(prev.face_key)
+        pos = np.searchsorted(prev.face_key[order], keys)
+        pos = np.clip(pos, 0, len(order) - 1)
+        hit = prev.face_key[order][pos] == keys
+        xprev[hit] = prev.unknowns[order[pos[hit]]]
+        new = ~hit
+        if prev_bem is not None and new.any():
+            pts = np.ascontiguousarray(cen[new], np.float32)
+            disp = np.zeros((len(pts), 3), np.float32)
+            prev_bem.interior(pts, disp=disp)
+            u_new = disp.astype(np.float64)
+            if kd is not None:  # components with prescribed displacement carry t, unknown here
+                u_new[kd[new] > 0] = 0.0
+            xprev[new] = u_new
+    tdl = np.zeros(len(T)) if td_prev is None else td_prev.reshape(-1)[cell]
+    return np.concatenate([cen, nrm, area[:, None], xprev, tdl[:, None]], axis=1), keys
+
+
+def optimize(problem: Problem, C: float = 0.02, iters: int = 10, alpha_c: float = 0.0, p: int = 6,
+             solve_kw: dict | None = None, warm_start=None, device: int = 0, verbose: bool = False):
+    """Run the hard-kill loop.  warm_start(features [nt, 11]) -> x0 [nt, 3] or None, called
+    with this iteration's features (previous unknowns carried over).  Returns (mask, history),
+    history = list of IterationRecord with stats {alpha, psi, iters, seconds, nt, removed}."""
+    kw = dict(tol=1e-6, restart=100, maxit=5000, refine=True, inner_tol=1e-3)
+    if solve_kw:
+        kw.update(solve_kw)
+    mask = np.ones((problem.nx, problem.ny, problem.nz), np.uint8)
+    n0 = mask.sum()
+    frozen = problem.frozen()
+    history: list[IterationRecord] = []
+    td_prev = None
+    prev_bem = None
+    for it in range(iters):
+        V, T, cell, fdir = voxel_surface(mask, problem.h)
+        kd, vals = problem.boundary_conditions(cell, fdir)
+        feats, keys = features_for(V, T, cell, fdir, history[-1] if history else None, td_prev, prev_bem, kd)
+        if prev_bem is not None:
+            prev_bem.close()
+            prev_bem = None
+        u, t = np.zeros((len(T), 3)), np.zeros((len(T), 3))
+        b = Bem(V, T, BEM_FMM, p=p, device=device)
+        b.set_material(material_K(problem.G, problem.nu), problem.G)
+        b.set_bc(kd, vals)
+        t0 = time.perf_counter()
+        x0 = None
+        if warm_start is not None:
+            x0 = warm_start(feats, b) if getattr(warm_start, "uses_operator", False) else warm_start(feats)
+        st = b.solve(u, t, x0=None if x0 is None else np.ascontiguousarray(x0, np.float64),
+                     raise_on_fail=False, **kw)
+        solve_s = time.perf_counter() - t0
+        ii = np.argwhere(mask > 0)
+        pts = np.ascontiguousarray((ii + 0.5) * problem.h, np.float32)
+        td = np.zeros(len(pts), np.float32)
+        b.topo_derivative(pts, td)
+        prev_bem = b  # its solution gives the next iteration's carried-over unknowns
+        x = np.where(kd > 0, t, u)
+        _, _, area = triangle_geometry(V, T)
+        psi = 0.5 * float(np.einsum("i,ij,ij->", area, t, u))
+        alpha = float(mask.sum()) / float(n0)
+        td_full = np.zeros(mask.shape, np.float32)
+        td_full[tuple(ii.T)] = td
+        rec = IterationRecord(feats, x, keys, {"alpha": alpha, "psi": psi, "iters": st["iters"],
+                                               "outer": st["outer"], "relres": st["relres"],
+                                               "converged": bool(st["converged"]), "seconds": solve_s,
+                                               "x0_relres": st["x0_relres"],
+                                               "nt": len(T), "warm": x0 is not None})
+        history.append(rec)
+        if warm_start is not None and hasattr(warm_start, "observe"):
+            warm_start.observe(rec)
+        if verbose:
+            print(f"it {it}: nt {len(T)} alpha {alpha:.3f} psi {psi:.4e} gmres {st['iters']} "
+                  f"({solve_s:.2f} s) relres {st['relres']:.1e}")
+        td_prev = td_full
+        if alpha <= alpha_c or it == iters - 1:
+            break
+        removed = voxel_threshold(mask, td_full, C, frozen)
+        removed += voxel_clean(mask, problem.support, frozen)
+        rec.stats["removed"] = removed
+        if removed == 0:
+            break
+    if prev_bem is not None:
+        prev_bem.close()
+    return mask, history
+
+
+class LearnedWarmStart:
+    """Initial guesses from a network trained on the earlier iterations.
+
+    After every iteration the (features, converged unknowns) pairs of all iterations so far
+    train the network (`Mlp`, on the GPU); the next iteration's features give x0.  The
+    features carry the previous iterate's unknowns over (by face identity, and on newly
+    exposed faces from the previous solution's interior displacement), and the network
+    predicts the change from them, trained on x - x_prev of the iterations that had a
+    previous iterate.  The prediction d = net(features) is used as a search direction:
+    x0 = a x_prev + g d with (a, g) minimising ||b - A x0|| for the FMM operator of the new
+    problem (three operator applications).  Until it is trained it returns x_prev (nothing
+    before the first iteration); a guess worse than zero is dropped by the solver.
+    """
+
+    uses_operator = True
+
+    def __init__(self, n_hidden=256, n_layers=4, epochs=150, batch=512, lr=1e-3, seed=1612):
+        self.net = Mlp(11, n_hidden, n_layers, 3, seed)
+        self.kw = dict(epochs=epochs, batch=batch, lr=lr, seed=seed)
+        self.X, self.Y = [], []
+        self.trained = False
+        self.train_stats = []
+
+    def observe(self, rec: IterationRecord):
+        if not np.any(rec.features[:, 7:10]):
+            return  # first iteration: no previous iterate, nothing to learn a change from
+        self.X.append(rec.features.astype(np.float32))
+        self.Y.append((rec.unknowns - rec.features[:, 7:10]).astype(np.float32))
+        X, Y = np.concatenate(self.X), np.concatenate(self.Y)
+        t0 = time.perf_counter()
+        st = self.net.train(X, Y, **self.kw)
+        st["seconds"] = time.perf_counter() - t0
+        st["rows"] = len(X)
+        self.train_stats.append(st)
+        self.trained = True
+
+    def __call__(self, feats, bem=None):
+        xp = np.ascontiguousarray(feats[:, 7:10], np.float64)
+        if not np.any(xp):
+            return None
+        if not self.trained:
+            return xp.copy()
+        d = np.ascontiguousarray(self.net.forward(feats.astype(np.float32)), np.float64)
+        if bem is None:
+            return xp + d
+        rhs, ax, ad = np.zeros_like(xp), np.zeros_like(xp), np.zeros_like(xp)
+        bem.rhs(rhs)
+        bem.matvec(xp, ax)
+        bem.matvec(d, ad)
+        M = np.array([[ax.ravel() @ ax.ravel(), ax.ravel() @ ad.ravel()],
+                      [ad.ravel() @ ax.ravel(), ad.ravel() @ ad.ravel()]])
+        q = np.array([ax.ravel() @ rhs.ravel(), ad.ravel() @ rhs.ravel()])
+        try:
+            a, g = np.linalg.solve(M, q)
+        except np.linalg.LinAlgError:
+            a, g = 1.0, 0.0
+        # keep the network's direction only when it lowers the residual by >= 10%
+        r_prev = np.linalg.norm(rhs - ax)
+        r_new = np.linalg.norm(rhs - a * ax - g * ad)
+        if not r_new <= 0.9 * r_prev:
+            a, g = 1.0, 0.0
+        self.last_coef = (float(a), float(g), float(r_new / max(r_prev, 1e-300)))
+        return a * xp + g * d

@@ -84,6 +84,9 @@ typedef struct kfmm_options {
                            8 = equivalent-density and M2L basis changes, all three with
                            three-term BF16 splits (FP32-grade) (15)                          */
     int device;         /* CUDA device ordinal (0)                                          */
+    int graphs;         /* 1: an evaluation repeated with the same arguments (e.g. the matvecs
+                           of a GMRES solve) is captured once into a CUDA graph and replayed;
+                           not while profiling (1)                                          */
 } kfmm_options;
 
 /* Tree and work counts of the last kfmm_build (for tests and roofline accounting). */

@@ -38,7 +38,7 @@ class kfmm_options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double), ("pinv_rtol", ctypes.c_double),
                 ("m2l_rtol", ctypes.c_double), ("m2l_rank_max", ctypes.c_int), ("m2l_tensor_cores", ctypes.c_int),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class kfmm_stats(ctypes.Structure):

@@ -51,6 +51,7 @@ void kfmm_default_options(kfmm_options *opt)
     opt->m2l_rank_max = 0;
     opt->m2l_tensor_cores = 15;
     opt->device = 0;
+    opt->graphs = 1;
 }
 
 kfmm_status kfmm_create(kfmm_ctx **out, const kfmm_options *opt)
@@ -82,6 +83,8 @@ kfmm_status kfmm_destroy(kfmm_ctx *ctx)
     if (!ctx) return KFMM_ERR_INVALID_ARG;
     cudaSetDevice(ctx->opt.device);
     cudaStreamSynchronize(ctx->stream);
+    ctx->graph.reset();
+    if (ctx->graph.cap_stream) cudaStreamDestroy(ctx->graph.cap_stream);
     delete ctx;
     return KFMM_OK;
 }
@@ -93,6 +96,7 @@ kfmm_status kfmm_set_material(kfmm_ctx *ctx, double K, double G)
         return ctx->fail(KFMM_ERR_INVALID_ARG, "material: need K > 0 and G > 0");
     ctx->G = G;
     ctx->nu = (3.0 * K - 2.0 * G) / (2.0 * (3.0 * K + G));
+    ctx->graph.reset();  // the constants are arguments of the captured kernels
     return KFMM_OK;
 }
 
@@ -117,6 +121,7 @@ kfmm_status kfmm_build(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     KF_TRY(to_device(ctx, b, src_nrm, sizeof(float) * 3 * nsrc, &dn));
     KF_TRY(to_device(ctx, c, trg_xyz, sizeof(float) * 3 * ntrg, &dt));
     ctx->plans.valid = false;
+    ctx->graph.reset();
     ctx->phase(KFMM_PH_TREE);
     kfmm_status s = build_tree(ctx, (const float *)ds, (const float *)dn, nsrc, (const float *)dt, ntrg);
     ctx->phase(-1);

@@ -251,8 +251,24 @@ struct Profiler {
 
 }  // namespace kfmm
 
+namespace kfmm {
+// A captured evaluation (CUDA graph) and the arguments it was captured with.
+struct EvalGraph {
+    const void *sl = nullptr, *dl = nullptr;
+    void *out = nullptr;
+    int ncol = -1, kind = -1;
+    int seen = 0;          // evaluations with these arguments since the last reset
+    bool valid = false;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int64_t launches = 0;  // kernels in the graph
+    void reset();
+};
+}  // namespace kfmm
+
 struct kfmm_ctx {
     kfmm_options opt;
+    kfmm::EvalGraph graph;
     cudaStream_t stream = nullptr;
     double G = 1.0, nu = 0.3;
     std::string err;

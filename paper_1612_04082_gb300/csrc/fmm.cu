@@ -200,6 +200,12 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
         KF_TRY(upload_tc_op(ctx, O.tc_vd, H->vd.data(), 1, m, kd));
     }
     O.box_tc = (tcb & 14) != 0;
+    // dynamic shared memory of the tensor-core kernels (set here, outside any graph capture)
+    KF_CUDA(cudaFuncSetAttribute(tc::tc_box_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc::box_smem_bytes()));
+    if (O.m2l_tc_mtiles > 0)
+        KF_CUDA(cudaFuncSetAttribute(tc::tc_gather_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc::smem_bytes(rp)));
     O.p = prm.p;
     O.nu = prm.nu;
     O.r_inner = prm.r_inner;
@@ -920,7 +926,6 @@ static kfmm_status run_tc_box(kfmm_ctx *ctx, GemmPlan &pl, const Operators::TcOp
     a.mode = mode;
     a.err = ctx->plans.err.as<int>();
     const uint32_t smem = tc::box_smem_bytes();
-    KF_CUDA(cudaFuncSetAttribute(tc::tc_box_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     tc::tc_box_gemm_kernel<<<pl.n_tc_items[nm], tc::BOX_THREADS, smem, ctx->stream>>>(a);
     KF_LAUNCH();
     return KFMM_OK;
@@ -1027,7 +1032,10 @@ static kfmm_status run_gemm(kfmm_ctx *ctx, const GemmPlan &pl, const float *A, i
     return KFMM_OK;
 }
 
-kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, int kind, float *out)
+// All work of one evaluation, enqueued on ctx->stream.  The first call after a build also
+// makes the plans and lazily built tables (it may allocate and synchronise); later calls with
+// the same arguments only enqueue, which is what a CUDA graph captures.
+static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, int kind, float *out)
 {
     Tree &T = ctx->tree;
     Operators &O = ctx->ops;
@@ -1116,8 +1124,6 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
                 KF_LAUNCH();
                 ctx->phase(KFMM_PH_M2L);
                 const uint32_t smem = tc::smem_bytes(rp);
-                KF_CUDA(cudaFuncSetAttribute(tc::tc_gather_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem));
                 tc::TcArgs ta{O.m2l_tc.as<uint16_t>(), O.m2l_tc_mtiles, r, rp, P.m2l_items.as<int4>(),
                               T.vp_src.as<int>(), T.vp_trg.as<int>(), W.psi2.as<uint16_t>(), W.cdn.as<float>(), rp,
                               P.err.as<int>()};
@@ -1219,13 +1225,84 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
         }
         ctx->phase(-1);
     }
+    return KFMM_OK;
+}
+
+void EvalGraph::reset()
+{
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    valid = false;
+    seen = 0;
+    sl = dl = nullptr;
+    out = nullptr;
+    ncol = kind = -1;
+    launches = 0;
+}
+
+// One evaluation.  Repeated evaluations with the same arguments (the matvecs of a GMRES
+// solve) are captured once into a CUDA graph on a private stream and then replayed on the
+// context stream: one launch instead of a few hundred.
+kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, int kind, float *out)
+{
+    EvalGraph &G = ctx->graph;
+    const cudaStream_t st = ctx->stream;
+    const bool use_graph = ctx->opt.graphs != 0 && !ctx->prof.on;
+    const bool same = G.sl == sl && G.dl == dl && G.out == out && G.ncol == ncol && G.kind == kind;
+    if (!same || !use_graph) {
+        G.reset();
+        G.sl = sl;
+        G.dl = dl;
+        G.out = out;
+        G.ncol = ncol;
+        G.kind = kind;
+    }
+    if (use_graph && same && G.valid) {
+        KF_CUDA(cudaGraphLaunch(G.exec, st));
+        ctx->n_launch += G.launches;
+    } else if (use_graph && same && G.seen >= 1) {
+        if (!G.cap_stream) KF_CUDA(cudaStreamCreateWithFlags(&G.cap_stream, cudaStreamNonBlocking));
+        // the capture stream starts after the work already queued on the context stream
+        cudaEvent_t ev;
+        KF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        KF_CUDA(cudaEventRecord(ev, st));
+        KF_CUDA(cudaStreamWaitEvent(G.cap_stream, ev, 0));
+        KF_CUDA(cudaStreamSynchronize(G.cap_stream));
+        cudaEventDestroy(ev);
+        const int64_t l0 = ctx->n_launch;
+        ctx->stream = G.cap_stream;
+        cudaGraph_t graph = nullptr;
+        KF_CUDA(cudaStreamBeginCapture(G.cap_stream, cudaStreamCaptureModeThreadLocal));
+        const kfmm_status s = fmm_enqueue(ctx, sl, dl, ncol, kind, out);
+        const cudaError_t ce = cudaStreamEndCapture(G.cap_stream, &graph);
+        ctx->stream = st;
+        if (s != KFMM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            G.reset();
+            return s;
+        }
+        if (ce != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        const cudaError_t ie = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            G.exec = nullptr;
+            return ctx->fail(KFMM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+        }
+        G.valid = true;
+        G.launches = ctx->n_launch - l0;
+        KF_CUDA(cudaGraphLaunch(G.exec, st));
+    } else {
+        KF_TRY(fmm_enqueue(ctx, sl, dl, ncol, kind, out));
+        ++G.seen;
+    }
+    Operators &O = ctx->ops;
     if (O.m2l_tc_mtiles > 0 || O.box_tc) {
         // the tensor-core kernels bound their barrier waits and report a time-out here
         int herr = 0;
-        KF_CUDA(cudaMemcpyAsync(&herr, P.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaMemcpyAsync(&herr, ctx->plans.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         KF_CUDA(cudaStreamSynchronize(st));
         if (herr) {
-            KF_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), st));
+            KF_CUDA(cudaMemsetAsync(ctx->plans.err.p, 0, sizeof(int), st));
             return ctx->fail(KFMM_ERR_DEVICE_TIMEOUT, "tensor-core product: a bounded barrier wait gave up");
         }
     }

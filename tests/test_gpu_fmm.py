@@ -271,3 +271,40 @@ def test_tensor_cores_match_fp32_simt(K):
         assert rel(o[idx], ref) < 1e-4
     assert rel(outs[1], outs[2]) < 2e-5
     assert rel(outs[0], outs[2]) < 4e-5
+
+
+def test_graph_replay_matches_and_invalidates(K):
+    """Repeated evaluations with the same arguments are captured into a CUDA graph and replayed;
+    the replayed results equal a plain evaluation (up to the order of the reductions), and a
+    new build or material drops the graph."""
+    src, nrm = W.box_with_voids_points(30000, n_voids=10)
+    sl, dl = W.densities(len(src))
+    src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
+    x, n, s, d = dev(src), dev(nrm), dev(sl), dev(dl)
+    out = torch.zeros(len(src), 3, device="cuda:0")
+    with make_ctx(K, G1, NU1, graphs=0) as c:
+        c.build(x, n, x)
+        c.eval(s, d, out)
+        ref = out.cpu().numpy().astype(np.float64)
+    with make_ctx(K, G1, NU1) as c:
+        c.build(x, n, x)
+        res, launches = [], []
+        for _ in range(4):
+            l0 = c.stats()["kernel_launches"]
+            out.zero_()
+            c.eval(s, d, out)
+            res.append(out.cpu().numpy().astype(np.float64))
+            launches.append(c.stats()["kernel_launches"] - l0)
+        for r_ in res:
+            assert rel(r_, ref) < 1e-5
+        # the first call also makes the plans; every later one (plain, captured, replayed)
+        # launches the same kernels, which the graph counts
+        assert launches[1] > 10 and len(set(launches[1:])) == 1 and launches[0] >= launches[1]
+        # a new set of points: the graph must not replay the old tree
+        src2 = r32(src * 0.5 + 0.25)
+        c.build(dev(src2), n, dev(src2))
+        out.zero_()
+        c.eval(s, d, out)
+        idx = W.subsample(len(src), 500)
+        ref2 = O.direct_disp(src2[idx], src2, nrm, sl, dl, G1, NU1)
+        assert rel(out.cpu().numpy().astype(np.float64)[idx], ref2) < 1e-4

@@ -198,10 +198,12 @@ struct Work {
 
 // Tile tables of the grouped gather-GEMM, built once per tree.
 struct GemmPlan {
-    DevBuf tiles;  // int4 {matrix index, first column, end column, 0}
-    int n_tiles = 0;
-    std::vector<int4> host_tiles;
-    // tensor-core work items {matrix, row tile, first column, end column}, by row-tile count
+    DevBuf tiles;  // int4 {matrix index, first column, end column, density column}
+    int n_tiles = 0;      // device tiles: host tiles x ncol
+    int ncol = 1;         // density columns the device tiles and items were made for
+    std::vector<int4> host_tiles;  // one density column: {matrix, first, end, 0}
+    // tensor-core work items {column * n_mat + matrix, row tile, first column, end column}, by
+    // row-tile count
     DevBuf tc_items[9];
     int n_tc_items[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
 };
@@ -211,8 +213,11 @@ struct FmmPlans {
     GemmPlan all, leaves, xboxes, wboxes, m2l;
     std::vector<GemmPlan> oct_lvl;  // per level: children grouped by octant (M2M, L2L)
     DevBuf geom;                    // float4 per box: centre x, y, z and half-width
-    DevBuf m2l_items;               // int4 {direction, row tile, c0, c1} for the tensor-core M2L
+    DevBuf m2l_items;               // int4 {column * 316 + direction, row tile, c0, c1} (tensor-core M2L)
     int n_m2l_items = 0;
+    std::vector<int4> m2l_host;     // one density column
+    int m2l_ncol = 1;
+    int ncol_zeroed = 0;            // density columns of box vectors allocated and zeroed
     DevBuf err;                     // int: set by kernels whose bounded waits gave up
     DevBuf eval_items;              // int4 {leaf box, first target, first segment, end segment}
     DevBuf eval_cnt;                // int per leaf: items, then their offsets

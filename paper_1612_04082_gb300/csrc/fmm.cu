@@ -229,13 +229,16 @@ struct SrcRec {
     float4 y, t, u, n;
 };
 
+// records of all ncol density columns: rec[col * ns + i]
 __global__ void pack_sources_kernel(int64_t ns, const float4 *__restrict__ xyz, const float4 *__restrict__ nrm,
                                     const int *__restrict__ perm, const float *__restrict__ sl,
-                                    const float *__restrict__ dl, int ld, int col, float st, float su,
+                                    const float *__restrict__ dl, int ld, int ncol, float st, float su,
                                     float b12, SrcRec *__restrict__ rec)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += stride) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ns * ncol; e += stride) {
+        const int64_t i = e % ns;
+        const int col = (int)(e / ns);
         const int j = perm[i];
         SrcRec r;
         float4 p = xyz[i];
@@ -255,7 +258,7 @@ __global__ void pack_sources_kernel(int64_t ns, const float4 *__restrict__ xyz, 
         r.t = make_float4(t.x, t.y, t.z, 0.f);
         r.u = make_float4(u.x, u.y, u.z, 0.f);
         r.n = make_float4(nn.x, nn.y, nn.z, 0.f);
-        rec[i] = r;
+        rec[e] = r;
     }
 }
 
@@ -296,9 +299,11 @@ __global__ void __launch_bounds__(kChkThreads)
 check_potential_kernel(const int *__restrict__ boxes, int nbox, int use_xlist, const int *__restrict__ xo,
                        const int *__restrict__ xi, const int2 *__restrict__ bsrc, const float4 *__restrict__ geom,
                        const float4 *__restrict__ surf, int n_surf, float radius, const SrcRec *__restrict__ rec,
-                       float a34, float b12, float *__restrict__ out, int ldo)
+                       float a34, float b12, float *__restrict__ out, int ldo, int64_t rec_col, int64_t out_col)
 {
     __shared__ SrcRec sh[kChkStage];
+    rec += blockIdx.y * rec_col;  // density column blockIdx.y
+    out += blockIdx.y * out_col;
     const int b = boxes ? boxes[blockIdx.x] : blockIdx.x;
     const float4 g = geom[b];
     const int tid = threadIdx.x;
@@ -371,6 +376,7 @@ struct GemmArgs {
     const float4 *geom;  // alpha_j = alpha * geom[dst].w when non-null
     float alpha;
     int mode;  // 0 store, 1 add, 2 atomic add
+    int64_t x_col_rows, y_col_rows;  // rows of one density column (tile.w) in X and Y
 };
 
 constexpr int GBM = 64, GBN = 64, GBK = 16;
@@ -400,6 +406,8 @@ __global__ void __launch_bounds__(256) gemm_gather_kernel(GemmArgs g)
     }
     __syncthreads();
     const float *A = g.A + (int64_t)tile.x * g.a_stride;
+    const float *Xc = g.X + (int64_t)tile.w * g.x_col_rows * g.ldx;
+    float *Yc = g.Y + (int64_t)tile.w * g.y_col_rows * g.ldy;
     const int tx = tid & 15, ty = tid >> 4;
     float acc[4][4];
 #pragma unroll
@@ -418,7 +426,7 @@ __global__ void __launch_bounds__(256) gemm_gather_kernel(GemmArgs g)
         As[ak + 2][am] = av.z;
         As[ak + 3][am] = av.w;
         float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (bsrc >= 0) bv = *reinterpret_cast<const float4 *>(g.X + (int64_t)bsrc * g.ldx + k0 + bk);
+        if (bsrc >= 0) bv = *reinterpret_cast<const float4 *>(Xc + (int64_t)bsrc * g.ldx + k0 + bk);
         Bs[bk + 0][bn] = bv.x;
         Bs[bk + 1][bn] = bv.y;
         Bs[bk + 2][bn] = bv.z;
@@ -445,7 +453,7 @@ __global__ void __launch_bounds__(256) gemm_gather_kernel(GemmArgs g)
         const int d = s_dst[c];
         if (d < 0) continue;
         const float al = g.geom ? g.alpha * g.geom[d].w : g.alpha;
-        float *y = g.Y + (int64_t)d * g.ldy + mrow;
+        float *y = Yc + (int64_t)d * g.ldy + mrow;
         if (mrow + 3 < g.M) {
             float4 v = make_float4(al * acc[0][j], al * acc[1][j], al * acc[2][j], al * acc[3][j]);
             if (g.mode == 0) {
@@ -537,7 +545,8 @@ struct EvalArgs {
     float a34, b12, nu;
     float out_scale;  // 1 for DISP, c_D for STRESS
     float *out;
-    int ldo, col;
+    int ldo;
+    int64_t rec_col, phi_col;  // strides of one density column (blockIdx.y) in rec and the phis
 };
 
 // one source record, only the fields the kernel family reads
@@ -612,6 +621,9 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
     SrcRec *sh = stage[wid];
     if ((int)blockIdx.x * kEvalWarps + wid >= e.n_items) return;  // the whole warp
     const int4 it = e.items[blockIdx.x * kEvalWarps + wid];
+    const int dcol = blockIdx.y;  // density column
+    const SrcRec *rec = e.rec + dcol * e.rec_col;
+    const float *dn_phi = e.dn_phi + dcol * e.phi_col, *up_phi = e.up_phi + dcol * e.phi_col;
     const int b = it.x, c0 = it.y, s0 = it.z, s1 = it.w;
     const int2 tr = e.btrg[b];
     const int uo0 = e.uo[b], nU = e.uo[b + 1] - uo0;
@@ -652,7 +664,7 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
         }
         const float4 g = e.geom[src_box];
         const float rad = (j == 0 ? e.r_out : e.r_in) * g.w;
-        const float *phi = (j == 0 ? e.dn_phi : e.up_phi) + (int64_t)src_box * e.ld_phi;
+        const float *phi = (j == 0 ? dn_phi : up_phi) + (int64_t)src_box * e.ld_phi;
         for (int base = 0; base < e.n_surf; base += 32) {
             const int cnt = min(32, e.n_surf - base);
             __syncwarp();
@@ -730,7 +742,7 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
         SrcRec nxt;
         {
             const int src = locate(lane);
-            if (lane < total) nxt = load_rec<SL, DL>(e.rec, src);
+            if (lane < total) nxt = load_rec<SL, DL>(rec, src);
         }
         for (int base = 0; base < total; base += 32) {
             const int cnt2 = min(32, total - base);
@@ -739,7 +751,7 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
             __syncwarp();
             if (base + 32 < total) {
                 const int src = locate(base + 32 + lane);
-                if (base + 32 + lane < total) nxt = load_rec<SL, DL>(e.rec, src);
+                if (base + 32 + lane < total) nxt = load_rec<SL, DL>(rec, src);
             }
             eval_batch<KIND, SL, DL, false>(sh, kbeg, cnt2, nsl, two, x0, y0, z0, x1, y1, z1, e, o0, o1);
         }
@@ -749,13 +761,13 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
     if (has_self) {
         const int2 r = e.bsrc[b];
         SrcRec nxt;
-        if (r.x + lane < r.y) nxt = load_rec<SL, DL>(e.rec, r.x + lane);
+        if (r.x + lane < r.y) nxt = load_rec<SL, DL>(rec, r.x + lane);
         for (int base = r.x; base < r.y; base += 32) {
             const int cnt = min(32, r.y - base);
             __syncwarp();
             if (lane < cnt) store_rec<SL, DL>(sh + lane, nxt);
             __syncwarp();
-            if (base + 32 + lane < r.y) nxt = load_rec<SL, DL>(e.rec, base + 32 + lane);
+            if (base + 32 + lane < r.y) nxt = load_rec<SL, DL>(rec, base + 32 + lane);
             eval_batch<KIND, SL, DL, true>(sh, kbeg, cnt, nsl, two, x0, y0, z0, x1, y1, z1, e, o0, o1);
         }
     }
@@ -782,11 +794,11 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
         }
     }
     if (si == 0) {
-        float *o = e.out + (int64_t)e.trg_perm[c0 + ti] * e.ldo + NO * e.col;
+        float *o = e.out + (int64_t)e.trg_perm[c0 + ti] * e.ldo + NO * dcol;
 #pragma unroll
         for (int a = 0; a < NO; ++a) atomicAdd(o + a, e.out_scale * tot[a]);
         if (act1) {
-            float *q = e.out + (int64_t)e.trg_perm[c0 + t1] * e.ldo + NO * e.col;
+            float *q = e.out + (int64_t)e.trg_perm[c0 + t1] * e.ldo + NO * dcol;
 #pragma unroll
             for (int a = 0; a < NO; ++a) atomicAdd(q + a, e.out_scale * tot1[a]);
         }
@@ -854,9 +866,9 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
 }
 
 template <int KIND>
-void launch_eval(const EvalArgs &e, int n_items, bool sl, bool dl, cudaStream_t st)
+void launch_eval(const EvalArgs &e, int n_items, int ncol, bool sl, bool dl, cudaStream_t st)
 {
-    const unsigned grid = (unsigned)((n_items + kEvalWarps - 1) / kEvalWarps);
+    const dim3 grid((unsigned)((n_items + kEvalWarps - 1) / kEvalWarps), (unsigned)ncol);
     if (sl && dl) eval_leaf_kernel<KIND, true, true><<<grid, kEvalThreads, 0, st>>>(e);
     else if (sl) eval_leaf_kernel<KIND, true, false><<<grid, kEvalThreads, 0, st>>>(e);
     else eval_leaf_kernel<KIND, false, true><<<grid, kEvalThreads, 0, st>>>(e);
@@ -880,7 +892,26 @@ static kfmm_status make_plan(kfmm_ctx *ctx, GemmPlan &pl, const std::vector<int>
         KF_CUDA(cudaMemcpy(pl.tiles.p, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
     }
     pl.host_tiles = t;
+    pl.ncol = 1;
     for (int k = 0; k < 9; ++k) pl.n_tc_items[k] = -1;
+    return KFMM_OK;
+}
+
+// Device tiles for ncol density columns (tile.w = column); drops the tensor-core items.
+static kfmm_status plan_ncol(kfmm_ctx *ctx, GemmPlan &pl, int ncol)
+{
+    if (pl.ncol == ncol) return KFMM_OK;
+    std::vector<int4> t;
+    t.reserve(pl.host_tiles.size() * ncol);
+    for (int c = 0; c < ncol; ++c)
+        for (const int4 &h : pl.host_tiles) t.push_back(make_int4(h.x, h.y, h.z, c));
+    pl.n_tiles = (int)t.size();
+    if (pl.n_tiles) {
+        KF_CUDA(pl.tiles.ensure(sizeof(int4) * t.size()));
+        KF_CUDA(cudaMemcpy(pl.tiles.p, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
+    }
+    for (int k = 0; k < 9; ++k) pl.n_tc_items[k] = -1;
+    pl.ncol = ncol;
     return KFMM_OK;
 }
 
@@ -891,8 +922,9 @@ static_assert(GBN == tc::BN, "tensor-core box items are the 64-column tiles of t
 
 static kfmm_status run_tc_box(kfmm_ctx *ctx, GemmPlan &pl, const Operators::TcOp &op, const int *src,
                               const int *dst, int src_par, int dst_par, const float *X, int ldx, float *Y, int ldy,
-                              const float4 *geom, float alpha, int mode)
+                              const float4 *geom, float alpha, int mode, int ncol, int64_t col_rows)
 {
+    KF_TRY(plan_ncol(ctx, pl, ncol));
     if (pl.n_tiles == 0) return KFMM_OK;
     // work items for this row-tile count (built once per plan)
     const int nm = op.n_mtile;
@@ -900,14 +932,18 @@ static kfmm_status run_tc_box(kfmm_ctx *ctx, GemmPlan &pl, const Operators::TcOp
     if (ldx % 8 != 0) return ctx->fail(KFMM_ERR_INTERNAL, "tensor-core box product: source rows not padded to 8");
     if (pl.n_tc_items[nm] < 0) {
         std::vector<int4> items;
-        for (const int4 &t : pl.host_tiles)
-            for (int mt = 0; mt < nm; ++mt) items.push_back(make_int4(t.x, mt, t.y, t.z));
+        for (int c = 0; c < pl.ncol; ++c)
+            for (const int4 &t : pl.host_tiles)
+                for (int mt = 0; mt < nm; ++mt) items.push_back(make_int4(c * op.n_mat + t.x, mt, t.y, t.z));
         pl.n_tc_items[nm] = (int)items.size();
         KF_CUDA(pl.tc_items[nm].ensure(sizeof(int4) * std::max<size_t>(1, items.size())));
         KF_CUDA(cudaMemcpy(pl.tc_items[nm].p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
     }
     tc::TcBoxArgs a;
     a.A = op.img.as<uint16_t>();
+    a.n_mat = op.n_mat;
+    a.x_col_rows = col_rows;
+    a.y_col_rows = col_rows;
     a.n_mtile = nm;
     a.n_kc = op.n_kc;
     a.M = op.M;
@@ -955,6 +991,9 @@ static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
         for (int d = 0; d < 316 && nmt > 0; ++d)
             for (int c = T.vdir_off[d]; c < T.vdir_off[d + 1]; c += chunk)
                 for (int mt = 0; mt < nmt; ++mt) items.push_back(make_int4(d, mt, c, std::min(c + chunk, T.vdir_off[d + 1])));
+        P.m2l_host = items;
+        P.m2l_ncol = 1;
+        P.ncol_zeroed = 0;
         P.n_m2l_items = (int)items.size();
         if (P.n_m2l_items) {
             KF_CUDA(P.m2l_items.ensure(sizeof(int4) * items.size()));
@@ -1001,10 +1040,12 @@ static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
     return KFMM_OK;
 }
 
-static kfmm_status run_gemm(kfmm_ctx *ctx, const GemmPlan &pl, const float *A, int64_t a_stride, int M, int K,
+static kfmm_status run_gemm(kfmm_ctx *ctx, GemmPlan &pl, const float *A, int64_t a_stride, int M, int K,
                             int lda, const int *src, const int *dst, int src_par, int dst_par, const float *X,
-                            int ldx, float *Y, int ldy, const float4 *geom, float alpha, int mode, int tag = 0)
+                            int ldx, float *Y, int ldy, const float4 *geom, float alpha, int mode, int ncol,
+                            int64_t col_rows, int tag = 0)
 {
+    KF_TRY(plan_ncol(ctx, pl, ncol));
     if (pl.n_tiles == 0) return KFMM_OK;
     GemmArgs g;
     g.A = A;
@@ -1025,6 +1066,8 @@ static kfmm_status run_gemm(kfmm_ctx *ctx, const GemmPlan &pl, const float *A, i
     g.geom = geom;
     g.alpha = alpha;
     g.mode = mode;
+    g.x_col_rows = col_rows;
+    g.y_col_rows = col_rows;
     dim3 grid(pl.n_tiles, (M + GBM - 1) / GBM);
     if (tag == 1) gemm_gather_kernel<1><<<grid, 256, 0, ctx->stream>>>(g);
     else gemm_gather_kernel<0><<<grid, 256, 0, ctx->stream>>>(g);
@@ -1049,182 +1092,188 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     const int64_t ns = T.nsrc;
     if (!P.valid) {
         KF_TRY(build_plans(ctx, P));
-        // box vectors: zero once, so the padding lanes read by the GEMM K loops stay zero
+        P.valid = true;
+    }
+    if (P.ncol_zeroed < ncol) {
+        // box vectors of all density columns ([column][box][ld]): zeroed once, so the padding
+        // lanes read by the GEMM K loops stay zero
         DevBuf *bufs[8] = {&W.up_chk, &W.alpha, &W.psi, &W.cdn, &W.dn_chk, &W.beta, &W.up_phi, &W.dn_phi};
         const int lds[8] = {ld, kup, rp, rp, ld, kdp, ld, ld};
         for (int k = 0; k < 8; ++k) {
-            KF_CUDA(bufs[k]->ensure(sizeof(float) * (size_t)nb * lds[k]));
-            KF_CUDA(cudaMemsetAsync(bufs[k]->p, 0, sizeof(float) * (size_t)nb * lds[k], st));
+            const size_t bytes = sizeof(float) * (size_t)nb * lds[k] * ncol;
+            KF_CUDA(bufs[k]->ensure(bytes));
+            KF_CUDA(cudaMemsetAsync(bufs[k]->p, 0, bytes, st));
         }
-        P.valid = true;
+        if (O.m2l_tc_mtiles > 0) KF_CUDA(W.psi2.ensure(sizeof(uint16_t) * 2 * (size_t)nb * rp * ncol));
+        P.ncol_zeroed = ncol;
     }
-    KF_CUDA(W.src_rec.ensure(sizeof(SrcRec) * ns));
-    // one box-operator product: tensor cores (three-term split) or FP32 SIMT
+    if (O.m2l_tc_mtiles > 0 && P.m2l_ncol != ncol) {
+        // translation work items of all density columns: x = column * 316 + direction
+        std::vector<int4> items;
+        items.reserve(P.m2l_host.size() * ncol);
+        for (int c = 0; c < ncol; ++c)
+            for (const int4 &t : P.m2l_host) items.push_back(make_int4(c * 316 + t.x, t.y, t.z, t.w));
+        P.n_m2l_items = (int)items.size();
+        if (P.n_m2l_items) {
+            KF_CUDA(P.m2l_items.ensure(sizeof(int4) * items.size()));
+            KF_CUDA(cudaMemcpy(P.m2l_items.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+        }
+        P.m2l_ncol = ncol;
+    }
+    KF_CUDA(W.src_rec.ensure(sizeof(SrcRec) * ns * ncol));
+    if (kind == KFMM_STRESS) KF_CUDA(W.tmp.ensure(sizeof(SrcRec) * ns * ncol));
+    // one box-operator product over all density columns: tensor cores (three-term split) or
+    // FP32 SIMT
     auto box_gemm = [&](GemmPlan &pl, const Operators::TcOp &top, const float *A, int64_t a_stride,
                         int M, int K, int lda, const int *src, const int *dst, int src_par, int dst_par,
                         const float *X, int ldx, float *Y, int ldy, const float4 *gm, float alpha,
                         int mode) -> kfmm_status {
         if (top.on)
-            return run_tc_box(ctx, pl, top, src, dst, src_par, dst_par, X, ldx, Y, ldy, gm, alpha, mode);
-        return run_gemm(ctx, pl, A, a_stride, M, K, lda, src, dst, src_par, dst_par, X, ldx, Y, ldy, gm, alpha, mode);
+            return run_tc_box(ctx, pl, top, src, dst, src_par, dst_par, X, ldx, Y, ldy, gm, alpha, mode, ncol, nb);
+        return run_gemm(ctx, pl, A, a_stride, M, K, lda, src, dst, src_par, dst_par, X, ldx, Y, ldy, gm, alpha, mode,
+                        ncol, nb);
     };
     const auto kc = make_kelvin<float>(ctx->G, ctx->nu);
     const float4 *geom = P.geom.as<float4>();
     const int ldd = 3 * ncol;
-    for (int col = 0; col < ncol; ++col) {
-        // ---- pack sources (displacement scaling) for the upward pass and P2L
-        ctx->phase(KFMM_PH_PACK);
-        pack_sources_kernel<<<grid_for(ns, 256), 256, 0, st>>>(ns, T.src_xyz.as<float4>(), T.src_nrm.as<float4>(),
-                                                                T.src_perm.as<int>(), sl, dl, ldd, col, kc.c_sl,
-                                                                kc.c_dl, kc.b12, W.src_rec.as<SrcRec>());
+    // every phase below treats the ncol density columns in one launch (grid.y or work items)
+    // ---- pack sources (displacement scaling) for the upward pass and P2L
+    ctx->phase(KFMM_PH_PACK);
+    pack_sources_kernel<<<grid_for(ns * ncol, 256), 256, 0, st>>>(ns, T.src_xyz.as<float4>(), T.src_nrm.as<float4>(),
+                                                                   T.src_perm.as<int>(), sl, dl, ldd, ncol, kc.c_sl,
+                                                                   kc.c_dl, kc.b12, W.src_rec.as<SrcRec>());
+    KF_LAUNCH();
+    // ---- S2M: sources -> upward check surface of each leaf
+    ctx->phase(KFMM_PH_S2M);
+    KF_CUDA(cudaMemsetAsync(W.alpha.p, 0, sizeof(float) * (size_t)nb * kup * ncol, st));
+    auto check_pot = [&](const int *boxes, int nbx, int use_x, float radius, float *outp) {
+        const dim3 grid((unsigned)nbx, (unsigned)ncol);
+        const int64_t rc = ns, oc = (int64_t)nb * ld;
+        if (sl && dl)
+            check_potential_kernel<true, true><<<grid, kChkThreads, 0, st>>>(
+                boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
+                n, radius, W.src_rec.as<SrcRec>(), kc.a34, kc.b12, outp, ld, rc, oc);
+        else if (sl)
+            check_potential_kernel<true, false><<<grid, kChkThreads, 0, st>>>(
+                boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
+                n, radius, W.src_rec.as<SrcRec>(), kc.a34, kc.b12, outp, ld, rc, oc);
+        else
+            check_potential_kernel<false, true><<<grid, kChkThreads, 0, st>>>(
+                boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
+                n, radius, W.src_rec.as<SrcRec>(), kc.a34, kc.b12, outp, ld, rc, oc);
+    };
+    if (T.n_leaves) {
+        check_pot(T.leaves.as<int>(), T.n_leaves, 0, (float)O.r_outer, W.up_chk.as<float>());
         KF_LAUNCH();
-        // ---- S2M: sources -> upward check surface of each leaf
-        ctx->phase(KFMM_PH_S2M);
-        KF_CUDA(cudaMemsetAsync(W.alpha.p, 0, sizeof(float) * (size_t)nb * kup, st));
-        if (T.n_leaves) {
-            if (sl && dl)
-                check_potential_kernel<true, true><<<T.n_leaves, kChkThreads, 0, st>>>(
-                    T.leaves.as<int>(), T.n_leaves, 0, nullptr, nullptr, T.box_src.as<int2>(), geom,
-                    O.surf.as<float4>(), n, (float)O.r_outer, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
-                    W.up_chk.as<float>(), ld);
-            else if (sl)
-                check_potential_kernel<true, false><<<T.n_leaves, kChkThreads, 0, st>>>(
-                    T.leaves.as<int>(), T.n_leaves, 0, nullptr, nullptr, T.box_src.as<int2>(), geom,
-                    O.surf.as<float4>(), n, (float)O.r_outer, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
-                    W.up_chk.as<float>(), ld);
-            else
-                check_potential_kernel<false, true><<<T.n_leaves, kChkThreads, 0, st>>>(
-                    T.leaves.as<int>(), T.n_leaves, 0, nullptr, nullptr, T.box_src.as<int2>(), geom,
-                    O.surf.as<float4>(), n, (float)O.r_outer, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
-                    W.up_chk.as<float>(), ld);
-            KF_LAUNCH();
-        }
-        // upward densities of the leaves in the singular basis: alpha = G h S^-1 U^T chk
-        ctx->phase(KFMM_PH_UP_PINV);
-        KF_TRY(box_gemm(P.leaves, O.tc_s2a_u, O.s2a_u.as<float>(), 0, ku, ld, ld, T.leaves.as<int>(),
-                        T.leaves.as<int>(), 0, 0, W.up_chk.as<float>(), ld, W.alpha.as<float>(), kup, geom,
-                        (float)ctx->G, 0));
-        // ---- M2M, bottom-up (children of level l into their parents)
-        ctx->phase(KFMM_PH_M2M);
-        for (int l = T.n_levels - 1; l >= 1; --l)
-            KF_TRY(box_gemm(P.oct_lvl[l], O.tc_mb, O.mb.as<float>(), (int64_t)ku * kup, ku, kup, kup, T.oct_child.as<int>(),
-                            T.oct_child.as<int>(), 0, 1, W.alpha.as<float>(), kup, W.alpha.as<float>(), kup, nullptr,
-                            1.f, 2));
-        // ---- M2L on the V lists in the shared basis: psi = U_r^T V_u alpha, c += C_v psi
-        ctx->phase(KFMM_PH_M2L_BASIS);
-        KF_TRY(box_gemm(P.all, O.tc_cb, O.cb.as<float>(), 0, r, kup, kup, nullptr, nullptr, 0, 0,
-                        W.alpha.as<float>(), kup, W.psi.as<float>(), rp, nullptr, 1.f, 0));
-        KF_CUDA(cudaMemsetAsync(W.cdn.p, 0, sizeof(float) * (size_t)nb * rp, st));
-        if (O.m2l_tc_mtiles > 0) {
-            if (P.n_m2l_items) {
-                KF_CUDA(W.psi2.ensure(sizeof(uint16_t) * 2 * (size_t)nb * rp));
-                const int64_t nchunk = (int64_t)nb * (rp / 8);
-                tc::split_pairs_kernel<<<(unsigned)((nchunk + 255) / 256), 256, 0, st>>>(W.psi.as<float>(), nb, rp,
-                                                                                         W.psi2.as<uint16_t>());
-                KF_LAUNCH();
-                ctx->phase(KFMM_PH_M2L);
-                const uint32_t smem = tc::smem_bytes(rp);
-                tc::TcArgs ta{O.m2l_tc.as<uint16_t>(), O.m2l_tc_mtiles, r, rp, P.m2l_items.as<int4>(),
-                              T.vp_src.as<int>(), T.vp_trg.as<int>(), W.psi2.as<uint16_t>(), W.cdn.as<float>(), rp,
-                              P.err.as<int>()};
-                tc::tc_gather_gemm_kernel<<<P.n_m2l_items, tc::M2L_THREADS, smem, st>>>(ta);
-                KF_LAUNCH();
-            }
-        } else {
-            ctx->phase(KFMM_PH_M2L);
-            KF_TRY(run_gemm(ctx, P.m2l, O.m2l_c.as<float>(), (int64_t)r * rp, r, rp, rp, T.vp_src.as<int>(),
-                            T.vp_trg.as<int>(), 0, 0, W.psi.as<float>(), rp, W.cdn.as<float>(), rp, nullptr, 1.f, 2, 1));
-        }
-        // ---- P2L: X-list sources -> downward check surface
-        ctx->phase(KFMM_PH_P2L);
-        if (T.n_xboxes) {
-            if (sl && dl)
-                check_potential_kernel<true, true><<<T.n_xboxes, kChkThreads, 0, st>>>(
-                    T.xboxes.as<int>(), T.n_xboxes, 1, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(),
-                    geom, O.surf.as<float4>(), n, (float)O.r_inner, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
-                    W.dn_chk.as<float>(), ld);
-            else if (sl)
-                check_potential_kernel<true, false><<<T.n_xboxes, kChkThreads, 0, st>>>(
-                    T.xboxes.as<int>(), T.n_xboxes, 1, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(),
-                    geom, O.surf.as<float4>(), n, (float)O.r_inner, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
-                    W.dn_chk.as<float>(), ld);
-            else
-                check_potential_kernel<false, true><<<T.n_xboxes, kChkThreads, 0, st>>>(
-                    T.xboxes.as<int>(), T.n_xboxes, 1, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(),
-                    geom, O.surf.as<float4>(), n, (float)O.r_inner, W.src_rec.as<SrcRec>(), kc.a34, kc.b12,
-                    W.dn_chk.as<float>(), ld);
-            KF_LAUNCH();
-        }
-        // ---- downward densities in the singular basis: beta = S^-1 U^T (U_r c + G h chk_P2L),
-        //      then L2L top-down, then the equivalent densities needed by the leaf pass
-        ctx->phase(KFMM_PH_DOWN);
-        KF_TRY(box_gemm(P.all, O.tc_wb, O.wb.as<float>(), 0, kd, rp, rp, nullptr, nullptr, 0, 0,
-                        W.cdn.as<float>(), rp, W.beta.as<float>(), kdp, nullptr, 1.f, 0));
-        KF_TRY(box_gemm(P.xboxes, O.tc_s2a_d, O.s2a_d.as<float>(), 0, kd,
-                        ld, ld, T.xboxes.as<int>(), T.xboxes.as<int>(), 0, 0, W.dn_chk.as<float>(), ld,
-                        W.beta.as<float>(), kdp, geom, (float)ctx->G, 1));
-        for (int l = 3; l < T.n_levels; ++l)
-            KF_TRY(box_gemm(P.oct_lvl[l], O.tc_lb, O.lb.as<float>(),
-                            (int64_t)kd * kdp, kd, kdp, kdp, T.oct_child.as<int>(), T.oct_child.as<int>(), 1, 0,
-                            W.beta.as<float>(), kdp, W.beta.as<float>(), kdp, nullptr, 1.f, 1));
-        KF_TRY(box_gemm(P.leaves, O.tc_vd, O.vd.as<float>(), 0, m, kdp, kdp, T.leaves.as<int>(),
-                        T.leaves.as<int>(), 0, 0, W.beta.as<float>(), kdp, W.dn_phi.as<float>(), ld, nullptr, 1.f, 0));
-        KF_TRY(box_gemm(P.wboxes, O.tc_vu, O.vu.as<float>(), 0, m, kup,
-                        kup, T.wboxes.as<int>(), T.wboxes.as<int>(), 0, 0, W.alpha.as<float>(), kup,
-                        W.up_phi.as<float>(), ld, nullptr, 1.f, 0));
-        // ---- leaf evaluation
-        ctx->phase(KFMM_PH_EVAL);
-        const SrcRec *rec = W.src_rec.as<SrcRec>();
-        if (kind == KFMM_STRESS) {
-            // re-pack with stress scaling: t unscaled, u scaled by c_S / c_D
-            KF_CUDA(W.tmp.ensure(sizeof(SrcRec) * ns));
-            pack_sources_kernel<<<grid_for(ns, 256), 256, 0, st>>>(
-                ns, T.src_xyz.as<float4>(), T.src_nrm.as<float4>(), T.src_perm.as<int>(), sl, dl, ldd, col, 1.f,
-                kc.c_S / kc.c_D, kc.b12, W.tmp.as<SrcRec>());
-            KF_LAUNCH();
-            rec = W.tmp.as<SrcRec>();
-        }
-        EvalArgs e;
-        e.items = P.eval_items.as<int4>();
-        e.n_items = P.n_eval_items;
-        e.w_direct_max = T.w_direct_max;
-        e.btrg = T.box_trg.as<int2>();
-        e.bsrc = T.box_src.as<int2>();
-        e.geom = geom;
-        e.uo = T.u_off.as<int>();
-        e.ui = T.u_idx.as<int>();
-        e.wo = T.w_off.as<int>();
-        e.wi = T.w_idx.as<int>();
-        e.trg = T.trg_xyz.as<float4>();
-        e.trg_perm = T.trg_perm.as<int>();
-        e.rec = rec;
-        e.surf = O.surf.as<float4>();
-        e.n_surf = n;
-        e.r_in = (float)O.r_inner;
-        e.r_out = (float)O.r_outer;
-        e.dn_phi = W.dn_phi.as<float>();
-        e.up_phi = W.up_phi.as<float>();
-        e.ld_phi = ld;
-        e.phi_scale = kind == KFMM_DISP ? kc.c_sl : 1.f;
-        e.a34 = kc.a34;
-        e.b12 = kc.b12;
-        e.nu = kc.nu;
-        e.out_scale = kind == KFMM_DISP ? 1.f : kc.c_D;
-        e.out = out;
-        e.ldo = (kind == KFMM_DISP ? 3 : 6) * ncol;
-        e.col = col;
-        {
-            const int no = kind == KFMM_DISP ? 3 : 6;
-            zero_out_kernel<<<grid_for(T.ntrg * no, 256), 256, 0, st>>>(T.ntrg, out, e.ldo, no * col, no);
-            KF_LAUNCH();
-        }
-        if (P.n_eval_items) {
-            if (kind == KFMM_DISP) launch_eval<KFMM_DISP>(e, P.n_eval_items, sl != nullptr, dl != nullptr, st);
-            else launch_eval<KFMM_STRESS>(e, P.n_eval_items, sl != nullptr, dl != nullptr, st);
-            KF_LAUNCH();
-        }
-        ctx->phase(-1);
     }
+    // upward densities of the leaves in the singular basis: alpha = G h S^-1 U^T chk
+    ctx->phase(KFMM_PH_UP_PINV);
+    KF_TRY(box_gemm(P.leaves, O.tc_s2a_u, O.s2a_u.as<float>(), 0, ku, ld, ld, T.leaves.as<int>(),
+                    T.leaves.as<int>(), 0, 0, W.up_chk.as<float>(), ld, W.alpha.as<float>(), kup, geom,
+                    (float)ctx->G, 0));
+    // ---- M2M, bottom-up (children of level l into their parents)
+    ctx->phase(KFMM_PH_M2M);
+    for (int l = T.n_levels - 1; l >= 1; --l)
+        KF_TRY(box_gemm(P.oct_lvl[l], O.tc_mb, O.mb.as<float>(), (int64_t)ku * kup, ku, kup, kup, T.oct_child.as<int>(),
+                        T.oct_child.as<int>(), 0, 1, W.alpha.as<float>(), kup, W.alpha.as<float>(), kup, nullptr,
+                        1.f, 2));
+    // ---- M2L on the V lists in the shared basis: psi = U_r^T V_u alpha, c += C_v psi
+    ctx->phase(KFMM_PH_M2L_BASIS);
+    KF_TRY(box_gemm(P.all, O.tc_cb, O.cb.as<float>(), 0, r, kup, kup, nullptr, nullptr, 0, 0,
+                    W.alpha.as<float>(), kup, W.psi.as<float>(), rp, nullptr, 1.f, 0));
+    KF_CUDA(cudaMemsetAsync(W.cdn.p, 0, sizeof(float) * (size_t)nb * rp * ncol, st));
+    if (O.m2l_tc_mtiles > 0) {
+        if (P.n_m2l_items) {
+            const int64_t nchunk = (int64_t)nb * ncol * (rp / 8);
+            tc::split_pairs_kernel<<<(unsigned)((nchunk + 255) / 256), 256, 0, st>>>(W.psi.as<float>(), (int64_t)nb * ncol,
+                                                                                     rp, W.psi2.as<uint16_t>());
+            KF_LAUNCH();
+            ctx->phase(KFMM_PH_M2L);
+            const uint32_t smem = tc::smem_bytes(rp);
+            tc::TcArgs ta{O.m2l_tc.as<uint16_t>(), 316, nb, O.m2l_tc_mtiles, r, rp, P.m2l_items.as<int4>(),
+                          T.vp_src.as<int>(), T.vp_trg.as<int>(), W.psi2.as<uint16_t>(), W.cdn.as<float>(), rp,
+                          P.err.as<int>()};
+            tc::tc_gather_gemm_kernel<<<P.n_m2l_items, tc::M2L_THREADS, smem, st>>>(ta);
+            KF_LAUNCH();
+        }
+    } else {
+        ctx->phase(KFMM_PH_M2L);
+        KF_TRY(run_gemm(ctx, P.m2l, O.m2l_c.as<float>(), (int64_t)r * rp, r, rp, rp, T.vp_src.as<int>(),
+                        T.vp_trg.as<int>(), 0, 0, W.psi.as<float>(), rp, W.cdn.as<float>(), rp, nullptr, 1.f, 2, ncol,
+                        nb, 1));
+    }
+    // ---- P2L: X-list sources -> downward check surface
+    ctx->phase(KFMM_PH_P2L);
+    if (T.n_xboxes) {
+        check_pot(T.xboxes.as<int>(), T.n_xboxes, 1, (float)O.r_inner, W.dn_chk.as<float>());
+        KF_LAUNCH();
+    }
+    // ---- downward densities in the singular basis: beta = S^-1 U^T (U_r c + G h chk_P2L),
+    //      then L2L top-down, then the equivalent densities needed by the leaf pass
+    ctx->phase(KFMM_PH_DOWN);
+    KF_TRY(box_gemm(P.all, O.tc_wb, O.wb.as<float>(), 0, kd, rp, rp, nullptr, nullptr, 0, 0,
+                    W.cdn.as<float>(), rp, W.beta.as<float>(), kdp, nullptr, 1.f, 0));
+    KF_TRY(box_gemm(P.xboxes, O.tc_s2a_d, O.s2a_d.as<float>(), 0, kd,
+                    ld, ld, T.xboxes.as<int>(), T.xboxes.as<int>(), 0, 0, W.dn_chk.as<float>(), ld,
+                    W.beta.as<float>(), kdp, geom, (float)ctx->G, 1));
+    for (int l = 3; l < T.n_levels; ++l)
+        KF_TRY(box_gemm(P.oct_lvl[l], O.tc_lb, O.lb.as<float>(),
+                        (int64_t)kd * kdp, kd, kdp, kdp, T.oct_child.as<int>(), T.oct_child.as<int>(), 1, 0,
+                        W.beta.as<float>(), kdp, W.beta.as<float>(), kdp, nullptr, 1.f, 1));
+    KF_TRY(box_gemm(P.leaves, O.tc_vd, O.vd.as<float>(), 0, m, kdp, kdp, T.leaves.as<int>(),
+                    T.leaves.as<int>(), 0, 0, W.beta.as<float>(), kdp, W.dn_phi.as<float>(), ld, nullptr, 1.f, 0));
+    KF_TRY(box_gemm(P.wboxes, O.tc_vu, O.vu.as<float>(), 0, m, kup,
+                    kup, T.wboxes.as<int>(), T.wboxes.as<int>(), 0, 0, W.alpha.as<float>(), kup,
+                    W.up_phi.as<float>(), ld, nullptr, 1.f, 0));
+    // ---- leaf evaluation
+    ctx->phase(KFMM_PH_EVAL);
+    const SrcRec *rec = W.src_rec.as<SrcRec>();
+    if (kind == KFMM_STRESS) {
+        // re-pack with stress scaling: t unscaled, u scaled by c_S / c_D
+        pack_sources_kernel<<<grid_for(ns * ncol, 256), 256, 0, st>>>(
+            ns, T.src_xyz.as<float4>(), T.src_nrm.as<float4>(), T.src_perm.as<int>(), sl, dl, ldd, ncol, 1.f,
+            kc.c_S / kc.c_D, kc.b12, W.tmp.as<SrcRec>());
+        KF_LAUNCH();
+        rec = W.tmp.as<SrcRec>();
+    }
+    EvalArgs e;
+    e.items = P.eval_items.as<int4>();
+    e.n_items = P.n_eval_items;
+    e.w_direct_max = T.w_direct_max;
+    e.btrg = T.box_trg.as<int2>();
+    e.bsrc = T.box_src.as<int2>();
+    e.geom = geom;
+    e.uo = T.u_off.as<int>();
+    e.ui = T.u_idx.as<int>();
+    e.wo = T.w_off.as<int>();
+    e.wi = T.w_idx.as<int>();
+    e.trg = T.trg_xyz.as<float4>();
+    e.trg_perm = T.trg_perm.as<int>();
+    e.rec = rec;
+    e.surf = O.surf.as<float4>();
+    e.n_surf = n;
+    e.r_in = (float)O.r_inner;
+    e.r_out = (float)O.r_outer;
+    e.dn_phi = W.dn_phi.as<float>();
+    e.up_phi = W.up_phi.as<float>();
+    e.ld_phi = ld;
+    e.phi_scale = kind == KFMM_DISP ? kc.c_sl : 1.f;
+    e.a34 = kc.a34;
+    e.b12 = kc.b12;
+    e.nu = kc.nu;
+    e.out_scale = kind == KFMM_DISP ? 1.f : kc.c_D;
+    e.out = out;
+    e.ldo = (kind == KFMM_DISP ? 3 : 6) * ncol;
+    e.rec_col = ns;
+    e.phi_col = (int64_t)nb * ld;
+    zero_out_kernel<<<grid_for(T.ntrg * e.ldo, 256), 256, 0, st>>>(T.ntrg, out, e.ldo, 0, e.ldo);
+    KF_LAUNCH();
+    if (P.n_eval_items) {
+        if (kind == KFMM_DISP) launch_eval<KFMM_DISP>(e, P.n_eval_items, ncol, sl != nullptr, dl != nullptr, st);
+        else launch_eval<KFMM_STRESS>(e, P.n_eval_items, ncol, sl != nullptr, dl != nullptr, st);
+        KF_LAUNCH();
+    }
+    ctx->phase(-1);
     return KFMM_OK;
 }
 

@@ -142,6 +142,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
 
 struct TcArgs {
     const uint16_t *A;     // [n_mat][n_mtile][2][half_bytes/2] pre-laid-out bf16 (hi then lo)
+    int n_mat;             // item.x = column * n_mat + matrix (density columns batched)
+    int64_t col_rows;      // rows of one density column in X2 and Y
     int n_mtile;           // row tiles per matrix
     int M;                 // valid rows (outputs at rows >= M are dropped)
     int Kp;                // padded K (multiple of 16), also the row length of X
@@ -243,6 +245,8 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) tc_gather_gemm_kernel(TcArgs g
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int4 item = g.items[blockIdx.x];
     const int nsteps = (item.w - item.z + BN - 1) / BN;
+    const int mat = item.x % g.n_mat;
+    const int64_t crow = (int64_t)(item.x / g.n_mat) * g.col_rows;  // first row of this column
 
     if (warp == M2L_MMA_WARP) tmem_alloc(holder, TMEM_COLS);
     if (tid == 0) {
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) tc_gather_gemm_kernel(TcArgs g
             const int b = s & 1;
             const uint32_t u = (uint32_t)(s >> 1);
             const int c0 = item.z + s * BN + chalf * (BN / 2);
-            const int myd = c0 + lane < item.w ? g.dst_idx[c0 + lane] : -1;
+            const int myd = c0 + lane < item.w ? (int)(g.dst_idx[c0 + lane] + crow) : -1;
             // warp-uniform decisions: the tensor-memory loads below are warp-collective
             if (__any_sync(0xffffffffu, fail_set(s_fail))) break;
             if (!__all_sync(0xffffffffu, mbar_wait(&fullAcc[b], u & 1u))) {
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) tc_gather_gemm_kernel(TcArgs g
         unsigned char *sB = sB0 + (size_t)pg * 2 * b_half;
         auto src_of = [&](int s) {
             const int c = item.z + s * BN + col;
-            return (s < nsteps && c < item.w) ? g.src_idx[c] : -1;
+            return (s < nsteps && c < item.w) ? (int)(g.src_idx[c] + crow) : -1;
         };
         int src_next = src_of(pg);
         for (int s = pg; s < nsteps; s += 2) {
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) tc_gather_gemm_kernel(TcArgs g
     } else if (lane == 0) {
         // ---------------- MMA issuer
         const unsigned char *src =
-            reinterpret_cast<const unsigned char *>(g.A) + ((size_t)item.x * g.n_mtile + item.y) * 2 * (size_t)a_half;
+            reinterpret_cast<const unsigned char *>(g.A) + ((size_t)mat * g.n_mtile + item.y) * 2 * (size_t)a_half;
         mbar_expect_tx(barA, 2 * a_half);
         for (uint32_t off = 0; off < 2 * a_half; off += 16384) {
             const uint32_t n = (2 * a_half - off) < 16384u ? (2 * a_half - off) : 16384u;
@@ -406,6 +410,8 @@ constexpr uint32_t STAGE_BYTES = NTERM * (A_TERM + B_TERM);
 
 struct TcBoxArgs {
     const uint16_t *A;     // [n_mat][n_mtile][n_kc][term][BM x KC] core-matrix images
+    int n_mat;             // item.x = column * n_mat + matrix (density columns batched)
+    int64_t x_col_rows, y_col_rows;  // rows of one density column in X and Y
     int n_mtile, n_kc;
     int M;                 // valid rows
     const int4 *items;     // {matrix, mtile, c0, c1} with c1 - c0 <= BN
@@ -466,6 +472,7 @@ __global__ void __launch_bounds__(BOX_THREADS, 2) tc_box_gemm_kernel(TcBoxArgs g
     const int4 item = g.items[blockIdx.x];
     const int ncols = min(BN, item.w - item.z);
     const int n_kc = g.n_kc;
+    const int mat = item.x % g.n_mat, dcol = item.x / g.n_mat;
 
     if (warp == 0) tmem_alloc(holder, BOX_TMEM_COLS);
     if (tid < BN) {
@@ -490,12 +497,12 @@ __global__ void __launch_bounds__(BOX_THREADS, 2) tc_box_gemm_kernel(TcBoxArgs g
     const uint32_t tmem = *holder;
     const uint32_t idesc = idesc_bf16(BM, BN);
     const unsigned char *Abase = reinterpret_cast<const unsigned char *>(g.A) +
-                                 ((size_t)item.x * g.n_mtile + item.y) * n_kc * (size_t)A_CHUNK;
+                                 ((size_t)mat * g.n_mtile + item.y) * n_kc * (size_t)A_CHUNK;
 
     // this thread's piece of every source chunk: column col, values kb*8 .. kb*8 + 7
     const int col = tid % BN, kb = tid / BN;
     const int xrow = s_src[col];
-    const float *xp = xrow >= 0 ? g.X + (size_t)xrow * g.ldx + kb * 8 : nullptr;
+    const float *xp = xrow >= 0 ? g.X + ((size_t)xrow + (size_t)dcol * g.x_col_rows) * g.ldx + kb * 8 : nullptr;
     const uint32_t boff = core_offset(col, kb * 8, BN);
     auto load_x = [&](int kc, float4 &x0, float4 &x1) {
         if (xp && kc * KC + kb * 8 + 8 <= g.ldx) {
@@ -628,7 +635,7 @@ __global__ void __launch_bounds__(BOX_THREADS, 2) tc_box_gemm_kernel(TcBoxArgs g
                 const int d = s_dst[chalf * (BN / 2) + k];
                 if (d < 0) continue;
                 const float a = g.geom ? g.alpha * g.geom[d].w : g.alpha;
-                float *y = g.Y + (size_t)d * g.ldy + row;
+                float *y = g.Y + ((size_t)d + (size_t)dcol * g.y_col_rows) * g.ldy + row;
                 if (g.mode == 0) *y = a * racc[k];
                 else if (g.mode == 1) *y += a * racc[k];
                 else atomicAdd(y, a * racc[k]);

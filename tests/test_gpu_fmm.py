@@ -308,3 +308,36 @@ def test_graph_replay_matches_and_invalidates(K):
         idx = W.subsample(len(src), 500)
         ref2 = O.direct_disp(src2[idx], src2, nrm, sl, dl, G1, NU1)
         assert rel(out.cpu().numpy().astype(np.float64)[idx], ref2) < 1e-4
+
+
+@pytest.mark.parametrize("kind", ["disp", "stress"])
+def test_density_columns_batched(K, kind):
+    """ncol density columns evaluated in one pass (every phase over all columns) equal the
+    columns evaluated one by one, and the oracle."""
+    src, nrm = W.box_with_voids_points(25000, n_voids=10)
+    ncol = 3
+    sl, dl = W.densities(len(src), ncol=ncol)
+    src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
+    kd = K.KFMM_DISP if kind == "disp" else K.KFMM_STRESS
+    no = 3 if kind == "disp" else 6
+    cfg = {} if kind == "disp" else dict(p=8, m2l_rtol=1e-7)
+    with make_ctx(K, G1, NU1, **cfg) as c:
+        c.build(dev(src), dev(nrm), dev(src))
+        out = torch.zeros(len(src), no * ncol, device="cuda:0")
+        c.eval(dev(sl), dev(dl), out, kind=kd, ncol=ncol)
+        batched = out.cpu().numpy().astype(np.float64)
+        one = torch.zeros(len(src), no, device="cuda:0")
+        for col in range(ncol):
+            s1 = np.ascontiguousarray(sl[:, 3 * col:3 * col + 3])
+            d1 = np.ascontiguousarray(dl[:, 3 * col:3 * col + 3])
+            c.eval(dev(s1), dev(d1), one, kind=kd)
+            ref = one.cpu().numpy().astype(np.float64)
+            assert rel(batched[:, no * col:no * col + no], ref) < 2e-6
+    idx = W.subsample(len(src), 300)
+    fn = O.direct_disp if kind == "disp" else O.direct_stress
+    tol = 1e-4 if kind == "disp" else 5e-4
+    for col in range(ncol):
+        s1 = np.ascontiguousarray(sl[:, 3 * col:3 * col + 3])
+        d1 = np.ascontiguousarray(dl[:, 3 * col:3 * col + 3])
+        ref = fn(src[idx], src, nrm, s1, d1, G1, NU1)
+        assert rel(batched[idx, no * col:no * col + no], ref) < tol

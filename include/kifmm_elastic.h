@@ -87,6 +87,9 @@ typedef struct kfmm_options {
     int graphs;         /* 1: an evaluation repeated with the same arguments (e.g. the matvecs
                            of a GMRES solve) is captured once into a CUDA graph and replayed;
                            not while profiling (1)                                          */
+    int autotune;       /* 1: the context's first evaluation times candidate launch shapes on
+                           its tree (columns per M2L work item; cost cap of the leaf-
+                           evaluation work items) and keeps the fastest for later builds (1)  */
 } kfmm_options;
 
 /* Tree and work counts of the last kfmm_build (for tests and roofline accounting). */
@@ -107,6 +110,8 @@ typedef struct kfmm_stats {
                                     equivalent maps (0 before the first evaluation)          */
     int32_t n_xboxes, n_wboxes;  /* boxes with an X list; W-list boxes with their own
                                     upward density evaluated at targets                     */
+    int32_t m2l_chunk;           /* columns per M2L work item in use (tuned or default)     */
+    float eval_item_cost;        /* cost cap of the leaf-evaluation items in use            */
 } kfmm_stats;
 
 typedef struct kfmm_ctx kfmm_ctx;

@@ -38,7 +38,7 @@ class kfmm_options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double), ("pinv_rtol", ctypes.c_double),
                 ("m2l_rtol", ctypes.c_double), ("m2l_rank_max", ctypes.c_int), ("m2l_tensor_cores", ctypes.c_int),
-                ("device", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("device", ctypes.c_int), ("graphs", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class kfmm_stats(ctypes.Structure):
@@ -49,7 +49,8 @@ class kfmm_stats(ctypes.Structure):
                 ("p2p_interactions", ctypes.c_int64), ("s2m_interactions", ctypes.c_int64),
                 ("l2p_interactions", ctypes.c_int64), ("p2l_interactions", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("up_rank", ctypes.c_int32), ("down_rank", ctypes.c_int32),
-                ("n_xboxes", ctypes.c_int32), ("n_wboxes", ctypes.c_int32)]
+                ("n_xboxes", ctypes.c_int32), ("n_wboxes", ctypes.c_int32), ("m2l_chunk", ctypes.c_int32),
+                ("eval_item_cost", ctypes.c_float)]
 
 
 if not os.path.exists(LIB_PATH):

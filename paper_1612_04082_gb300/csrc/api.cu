@@ -52,6 +52,7 @@ void kfmm_default_options(kfmm_options *opt)
     opt->m2l_tensor_cores = 15;
     opt->device = 0;
     opt->graphs = 1;
+    opt->autotune = 1;
 }
 
 kfmm_status kfmm_create(kfmm_ctx **out, const kfmm_options *opt)
@@ -199,6 +200,8 @@ kfmm_status kfmm_get_stats(const kfmm_ctx *ctx, kfmm_stats *st)
     st->down_rank = ctx->ops.ready ? ctx->ops.kd : 0;
     st->n_xboxes = T.n_xboxes;
     st->n_wboxes = T.n_wboxes;
+    st->m2l_chunk = ctx->tune.m2l_chunk;
+    st->eval_item_cost = ctx->tune.eval_cost;
     return KFMM_OK;
 }
 

@@ -274,6 +274,12 @@ struct EvalGraph {
 struct kfmm_ctx {
     kfmm_options opt;
     kfmm::EvalGraph graph;
+    // launch shapes tuned on the first evaluation (kept across builds)
+    struct Tune {
+        bool eval_done = false, m2l_done = false;
+        float eval_cost = 1024.f;  // cap of a leaf-evaluation work item, warp pair-steps
+        int m2l_chunk = 1024;      // columns per M2L work item
+    } tune;
     cudaStream_t stream = nullptr;
     double G = 1.0, nu = 0.3;
     std::string err;

@@ -814,14 +814,14 @@ __global__ void zero_out_kernel(int64_t n, float *__restrict__ out, int ldo, int
 }
 
 // Work items of the leaf evaluation: one thread per leaf walks its target chunks and source
-// segments, cutting a new item when the cost (warp pair-steps) would exceed kEvalItemCost.
-constexpr float kEvalItemCost = 1024.f;
+// segments, cutting a new item when the cost (warp pair-steps) would exceed item_cost
+// (1024 by default; tuned per context when autotuning is on).
 
 template <bool EMIT>
 __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, const int2 *__restrict__ btrg,
                                   const int2 *__restrict__ bsrc, const int *__restrict__ uo,
                                   const int *__restrict__ ui, const int *__restrict__ wo,
-                                  const int *__restrict__ wi, int w_direct_max, int n_surf,
+                                  const int *__restrict__ wi, int w_direct_max, int n_surf, float item_cost,
                                   const int *__restrict__ off, int *__restrict__ cnt, int4 *__restrict__ items)
 {
     const int li = blockIdx.x * blockDim.x + threadIdx.x;
@@ -851,7 +851,7 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
                 c = (float)(r.y - r.x);
             }
             c *= w;
-            if (acc > 0.f && acc + c > kEvalItemCost) {
+            if (acc > 0.f && acc + c > item_cost) {
                 if (EMIT) items[pos + n] = make_int4(b, c0, s0, s);
                 ++n;
                 s0 = s;
@@ -967,6 +967,46 @@ static kfmm_status run_tc_box(kfmm_ctx *ctx, GemmPlan &pl, const Operators::TcOp
     return KFMM_OK;
 }
 
+// M2L work items of one density column: per direction and row tile, chunks of `chunk`
+// columns that share one load of the translation's operand tile (the device copy for the
+// current number of density columns is made at the next evaluation)
+static void make_m2l_host(kfmm_ctx *ctx, FmmPlans &P, int chunk)
+{
+    const Tree &T = ctx->tree;
+    const int nmt = ctx->ops.m2l_tc_mtiles;
+    P.m2l_host.clear();
+    for (int d = 0; d < 316 && nmt > 0; ++d)
+        for (int c = T.vdir_off[d]; c < T.vdir_off[d + 1]; c += chunk)
+            for (int mt = 0; mt < nmt; ++mt)
+                P.m2l_host.push_back(make_int4(d, mt, c, std::min(c + chunk, T.vdir_off[d + 1])));
+    P.m2l_ncol = 0;
+}
+
+// work items of the leaf evaluation for a cost cap
+static kfmm_status make_eval_items(kfmm_ctx *ctx, FmmPlans &P, float cost)
+{
+    const Tree &T = ctx->tree;
+    const cudaStream_t st = ctx->stream;
+    P.n_eval_items = 0;
+    if (!T.n_leaves) return KFMM_OK;
+    const int nl = T.n_leaves;
+    KF_CUDA(P.eval_cnt.ensure(sizeof(int) * (size_t)(nl + 1)));
+    int *cnt = P.eval_cnt.as<int>();
+    eval_items_kernel<false><<<grid_for(nl, 128, 1 << 30), 128, 0, st>>>(
+        nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
+        T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost, nullptr, cnt, nullptr);
+    KF_LAUNCH();
+    KF_TRY(scan_exclusive(ctx, cnt, cnt, nl, cnt + nl));
+    KF_TRY(read_int(ctx, cnt + nl, &P.n_eval_items));
+    KF_CUDA(P.eval_items.ensure(sizeof(int4) * (size_t)std::max(1, P.n_eval_items)));
+    eval_items_kernel<true><<<grid_for(nl, 128, 1 << 30), 128, 0, st>>>(
+        nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
+        T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost, cnt, nullptr,
+        P.eval_items.as<int4>());
+    KF_LAUNCH();
+    return KFMM_OK;
+}
+
 static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
 {
     Tree &T = ctx->tree;
@@ -983,44 +1023,12 @@ static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
             ge[d] = T.vdir_off[d + 1];
         }
         KF_TRY(make_plan(ctx, P.m2l, gm, gb, ge));
-        // tensor-core work items: per direction and row tile, column chunks that share one
-        // load of the translation's operand tile
-        const int nmt = ctx->ops.m2l_tc_mtiles;
-        std::vector<int4> items;
-        const int chunk = 1024;
-        for (int d = 0; d < 316 && nmt > 0; ++d)
-            for (int c = T.vdir_off[d]; c < T.vdir_off[d + 1]; c += chunk)
-                for (int mt = 0; mt < nmt; ++mt) items.push_back(make_int4(d, mt, c, std::min(c + chunk, T.vdir_off[d + 1])));
-        P.m2l_host = items;
-        P.m2l_ncol = 1;
+        make_m2l_host(ctx, P, ctx->tune.m2l_chunk);
         P.ncol_zeroed = 0;
-        P.n_m2l_items = (int)items.size();
-        if (P.n_m2l_items) {
-            KF_CUDA(P.m2l_items.ensure(sizeof(int4) * items.size()));
-            KF_CUDA(cudaMemcpy(P.m2l_items.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
-        }
     }
     KF_CUDA(P.err.ensure(sizeof(int)));
     KF_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), st));
-    // work items of the leaf evaluation
-    P.n_eval_items = 0;
-    if (T.n_leaves) {
-        const int nl = T.n_leaves;
-        KF_CUDA(P.eval_cnt.ensure(sizeof(int) * (size_t)(nl + 1)));
-        int *cnt = P.eval_cnt.as<int>();
-        eval_items_kernel<false><<<grid_for(nl, 128, 1 << 30), 128, 0, st>>>(
-            nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
-            T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, nullptr, cnt, nullptr);
-        KF_LAUNCH();
-        KF_TRY(scan_exclusive(ctx, cnt, cnt, nl, cnt + nl));
-        KF_TRY(read_int(ctx, cnt + nl, &P.n_eval_items));
-        KF_CUDA(P.eval_items.ensure(sizeof(int4) * (size_t)std::max(1, P.n_eval_items)));
-        eval_items_kernel<true><<<grid_for(nl, 128, 1 << 30), 128, 0, st>>>(
-            nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
-            T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cnt, nullptr,
-            P.eval_items.as<int4>());
-        KF_LAUNCH();
-    }
+    KF_TRY(make_eval_items(ctx, P, ctx->tune.eval_cost));
     P.oct_lvl.clear();
     P.oct_lvl.resize(T.n_levels);
     for (int l = 1; l < T.n_levels; ++l) {
@@ -1075,6 +1083,23 @@ static kfmm_status run_gemm(kfmm_ctx *ctx, GemmPlan &pl, const float *A, int64_t
     return KFMM_OK;
 }
 
+// Device time of the work `f` enqueues on the context stream (synchronises).
+template <class F> static kfmm_status time_launch(kfmm_ctx *ctx, F f, float *ms)
+{
+    cudaEvent_t a, b;
+    KF_CUDA(cudaEventCreate(&a));
+    KF_CUDA(cudaEventCreate(&b));
+    KF_CUDA(cudaEventRecord(a, ctx->stream));
+    f();
+    KF_LAUNCH();
+    KF_CUDA(cudaEventRecord(b, ctx->stream));
+    KF_CUDA(cudaEventSynchronize(b));
+    KF_CUDA(cudaEventElapsedTime(ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return KFMM_OK;
+}
+
 // All work of one evaluation, enqueued on ctx->stream.  The first call after a build also
 // makes the plans and lazily built tables (it may allocate and synchronise); later calls with
 // the same arguments only enqueue, which is what a CUDA graph captures.
@@ -1107,8 +1132,8 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
         if (O.m2l_tc_mtiles > 0) KF_CUDA(W.psi2.ensure(sizeof(uint16_t) * 2 * (size_t)nb * rp * ncol));
         P.ncol_zeroed = ncol;
     }
-    if (O.m2l_tc_mtiles > 0 && P.m2l_ncol != ncol) {
-        // translation work items of all density columns: x = column * 316 + direction
+    // translation work items of all density columns: x = column * 316 + direction
+    auto upload_m2l_items = [&]() -> kfmm_status {
         std::vector<int4> items;
         items.reserve(P.m2l_host.size() * ncol);
         for (int c = 0; c < ncol; ++c)
@@ -1119,7 +1144,9 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
             KF_CUDA(cudaMemcpy(P.m2l_items.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
         }
         P.m2l_ncol = ncol;
-    }
+        return KFMM_OK;
+    };
+    if (O.m2l_tc_mtiles > 0 && P.m2l_ncol != ncol) KF_TRY(upload_m2l_items());
     KF_CUDA(W.src_rec.ensure(sizeof(SrcRec) * ns * ncol));
     if (kind == KFMM_STRESS) KF_CUDA(W.tmp.ensure(sizeof(SrcRec) * ns * ncol));
     // one box-operator product over all density columns: tensor cores (three-term split) or
@@ -1193,6 +1220,28 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
             tc::TcArgs ta{O.m2l_tc.as<uint16_t>(), 316, nb, O.m2l_tc_mtiles, r, rp, P.m2l_items.as<int4>(),
                           T.vp_src.as<int>(), T.vp_trg.as<int>(), W.psi2.as<uint16_t>(), W.cdn.as<float>(), rp,
                           P.err.as<int>()};
+            if (ctx->opt.autotune && !ctx->tune.m2l_done) {
+                // columns per work item: time each candidate on this tree, keep the fastest
+                float best = 1e30f;
+                int best_chunk = ctx->tune.m2l_chunk;
+                for (int chunk : {256, 512, 1024, 2048}) {
+                    make_m2l_host(ctx, P, chunk);
+                    KF_TRY(upload_m2l_items());
+                    ta.items = P.m2l_items.as<int4>();
+                    KF_CUDA(cudaMemsetAsync(W.cdn.p, 0, sizeof(float) * (size_t)nb * rp * ncol, st));
+                    float ms = 0.f;
+                    KF_TRY(time_launch(ctx, [&]() {
+                        tc::tc_gather_gemm_kernel<<<P.n_m2l_items, tc::M2L_THREADS, smem, st>>>(ta);
+                    }, &ms));
+                    if (ms < best) best = ms, best_chunk = chunk;
+                }
+                ctx->tune.m2l_chunk = best_chunk;
+                ctx->tune.m2l_done = true;
+                make_m2l_host(ctx, P, best_chunk);
+                KF_TRY(upload_m2l_items());
+                ta.items = P.m2l_items.as<int4>();
+                KF_CUDA(cudaMemsetAsync(W.cdn.p, 0, sizeof(float) * (size_t)nb * rp * ncol, st));
+            }
             tc::tc_gather_gemm_kernel<<<P.n_m2l_items, tc::M2L_THREADS, smem, st>>>(ta);
             KF_LAUNCH();
         }
@@ -1266,6 +1315,27 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     e.ldo = (kind == KFMM_DISP ? 3 : 6) * ncol;
     e.rec_col = ns;
     e.phi_col = (int64_t)nb * ld;
+    if (ctx->opt.autotune && !ctx->tune.eval_done && P.n_eval_items) {
+        // cost cap of the leaf-evaluation items: time each candidate on this tree
+        float best = 1e30f, best_cost = ctx->tune.eval_cost;
+        for (float cost : {256.f, 512.f, 1024.f, 2048.f, 4096.f}) {
+            KF_TRY(make_eval_items(ctx, P, cost));
+            e.items = P.eval_items.as<int4>();
+            e.n_items = P.n_eval_items;
+            float ms = 0.f;
+            KF_TRY(time_launch(ctx, [&]() {
+                zero_out_kernel<<<grid_for(T.ntrg * e.ldo, 256), 256, 0, st>>>(T.ntrg, out, e.ldo, 0, e.ldo);
+                if (kind == KFMM_DISP) launch_eval<KFMM_DISP>(e, P.n_eval_items, ncol, sl != nullptr, dl != nullptr, st);
+                else launch_eval<KFMM_STRESS>(e, P.n_eval_items, ncol, sl != nullptr, dl != nullptr, st);
+            }, &ms));
+            if (ms < best) best = ms, best_cost = cost;
+        }
+        ctx->tune.eval_cost = best_cost;
+        ctx->tune.eval_done = true;
+        KF_TRY(make_eval_items(ctx, P, best_cost));
+        e.items = P.eval_items.as<int4>();
+        e.n_items = P.n_eval_items;
+    }
     zero_out_kernel<<<grid_for(T.ntrg * e.ldo, 256), 256, 0, st>>>(T.ntrg, out, e.ldo, 0, e.ldo);
     KF_LAUNCH();
     if (P.n_eval_items) {

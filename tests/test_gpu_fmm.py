@@ -341,3 +341,27 @@ def test_density_columns_batched(K, kind):
         d1 = np.ascontiguousarray(dl[:, 3 * col:3 * col + 3])
         ref = fn(src[idx], src, nrm, s1, d1, G1, NU1)
         assert rel(batched[idx, no * col:no * col + no], ref) < tol
+
+
+def test_autotuned_launch_shapes(K):
+    """The first evaluation picks the M2L chunk and the leaf-item cost cap among its
+    candidates by timing them on the tree; the result does not depend on the choice."""
+    src, nrm = W.box_with_voids_points(60000, n_voids=10)
+    sl, dl = W.densities(len(src))
+    src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
+    outs = []
+    for tune in (0, 1):
+        with make_ctx(K, G1, NU1, autotune=tune) as c:
+            c.build(dev(src), dev(nrm), dev(src))
+            out = torch.zeros(len(src), 3, device="cuda:0")
+            c.eval(dev(sl), dev(dl), out)
+            st = c.stats()
+            outs.append(out.cpu().numpy().astype(np.float64))
+            if tune:
+                assert st["m2l_chunk"] in (256, 512, 1024, 2048)
+                assert st["eval_item_cost"] in (256.0, 512.0, 1024.0, 2048.0, 4096.0)
+                c.eval(dev(sl), dev(dl), out)  # tuned shapes kept, same answer
+                assert rel(out.cpu().numpy().astype(np.float64), outs[0]) < 1e-5
+            else:
+                assert st["m2l_chunk"] == 1024 and st["eval_item_cost"] == 1024.0
+    assert rel(outs[1], outs[0]) < 1e-5

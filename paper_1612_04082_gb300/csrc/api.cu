@@ -120,7 +120,8 @@ kfmm_status kfmm_build(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     const void *ds, *dn, *dt;
     KF_TRY(to_device(ctx, a, src_xyz, sizeof(float) * 3 * nsrc, &ds));
     KF_TRY(to_device(ctx, b, src_nrm, sizeof(float) * 3 * nsrc, &dn));
-    KF_TRY(to_device(ctx, c, trg_xyz, sizeof(float) * 3 * ntrg, &dt));
+    if (trg_xyz == src_xyz && ntrg == nsrc) dt = ds;  // targets are the sources: one copy, one sort
+    else KF_TRY(to_device(ctx, c, trg_xyz, sizeof(float) * 3 * ntrg, &dt));
     ctx->plans.valid = false;
     ctx->graph.reset();
     ctx->phase(KFMM_PH_TREE);
@@ -179,6 +180,10 @@ kfmm_status kfmm_get_stats(const kfmm_ctx *ctx, kfmm_stats *st)
     std::memset(st, 0, sizeof(*st));
     st->kernel_launches = ctx->n_launch;
     if (!T.built) return KFMM_ERR_NOT_BUILT;
+    // the interaction counts are made on first request after a build (synchronises)
+    const kfmm_status cs = tree_work_counts(const_cast<kfmm_ctx *>(ctx));
+    if (cs != KFMM_OK) return cs;
+    st->kernel_launches = ctx->n_launch;
     st->n_src = T.nsrc;
     st->n_trg = T.ntrg;
     st->n_boxes = T.n_boxes;

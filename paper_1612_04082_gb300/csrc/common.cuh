@@ -172,6 +172,7 @@ struct Tree {
     std::vector<int> oct_off;   // host: [(n_levels) * 8 + 1] offsets (level-major, then octant)
     int64_t n_u = 0, n_v = 0, n_w = 0, n_x = 0;
     int64_t p2p_pairs = 0, l2p_pairs = 0, p2l_pairs = 0;
+    bool counts_valid = false;  // the three counts above are made on request
     // a W-list box with at most this many sources is evaluated directly at the targets (exact
     // and cheaper than its n_surf equivalent points); larger ones through their densities
     int w_direct_max = 0;
@@ -317,6 +318,7 @@ namespace kfmm {
 // tree.cu
 kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm, int64_t nsrc,
                        const float *trg_xyz, int64_t ntrg);
+kfmm_status tree_work_counts(kfmm_ctx *ctx);  // interaction counts for the statistics
 // precompute.cpp (host, FP64) + upload
 kfmm_status ensure_operators(kfmm_ctx *ctx);
 // fmm.cu

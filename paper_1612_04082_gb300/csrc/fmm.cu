@@ -9,6 +9,7 @@
 // grouped gather-GEMM kernel: each column of a group is a box vector gathered by index, each
 // group has its own matrix.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <mutex>
 
@@ -813,10 +814,11 @@ __global__ void zero_out_kernel(int64_t n, float *__restrict__ out, int ldo, int
         out[(i / no) * ldo + c0 + i % no] = 0.f;
 }
 
-// Work items of the leaf evaluation: one thread per leaf walks its target chunks and source
-// segments, cutting a new item when the cost (warp pair-steps) would exceed item_cost
-// (1024 by default; tuned per context when autotuning is on).
-
+// Work items of the leaf evaluation: one warp per leaf.  For each target chunk the lanes cost
+// the source segments (L2P, W boxes, U leaves) 32 at a time; a warp prefix sum of the costs
+// (warp pair-steps) cuts a new item wherever floor(prefix / item_cost) changes, so no item
+// exceeds the cap by more than one segment.  Each start lane writes its item and closes the
+// previous one.  item_cost is 1024 by default and tuned per context when autotuning is on.
 template <bool EMIT>
 __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, const int2 *__restrict__ btrg,
                                   const int2 *__restrict__ bsrc, const int *__restrict__ uo,
@@ -824,11 +826,12 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
                                   const int *__restrict__ wi, int w_direct_max, int n_surf, float item_cost,
                                   const int *__restrict__ off, int *__restrict__ cnt, int4 *__restrict__ items)
 {
-    const int li = blockIdx.x * blockDim.x + threadIdx.x;
-    if (li >= n_leaves) return;
+    const int lane = threadIdx.x & 31;
+    const int li = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (li >= n_leaves) return;  // the whole warp
     const int b = leaves[li];
     const int2 tr = btrg[b];
-    const int nW = wo[b + 1] - wo[b], nU = uo[b + 1] - uo[b];
+    const int w0 = wo[b], nW = wo[b + 1] - w0, u0 = uo[b], nU = uo[b + 1] - u0;
     const int nseg = 1 + nW + nU;
     const int pos = EMIT ? off[li] : 0;
     int n = 0;
@@ -837,32 +840,46 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
         int L, nsl;
         const bool two = eval_layout(nt, L, nsl);
         const float w = (two ? 2.f : 1.f) / (float)nsl;  // pair evaluations per lane and source
-        float acc = 0.f;
-        int s0 = 0;
-        for (int s = 0; s < nseg; ++s) {
-            float c;
-            if (s == 0) {
-                c = 0.5f * (float)n_surf;
-            } else if (s <= nW) {
-                const int2 r = bsrc[wi[wo[b] + s - 1]];
-                c = r.y - r.x > w_direct_max ? 0.5f * (float)n_surf : (float)(r.y - r.x);
-            } else {
-                const int2 r = bsrc[ui[uo[b] + s - 1 - nW]];
-                c = (float)(r.y - r.x);
+        const int first = n;                             // first item of this chunk
+        float base = 0.f;
+        int q_last = -1;
+        for (int sb = 0; sb < nseg; sb += 32) {
+            const int sg = sb + lane;
+            float c = 0.f;
+            if (sg < nseg) {
+                if (sg == 0) {
+                    c = 0.5f * (float)n_surf;
+                } else if (sg <= nW) {
+                    const int2 r = bsrc[wi[w0 + sg - 1]];
+                    c = r.y - r.x > w_direct_max ? 0.5f * (float)n_surf : (float)(r.y - r.x);
+                } else {
+                    const int2 r = bsrc[ui[u0 + sg - 1 - nW]];
+                    c = (float)(r.y - r.x);
+                }
+                c *= w;
             }
-            c *= w;
-            if (acc > 0.f && acc + c > item_cost) {
-                if (EMIT) items[pos + n] = make_int4(b, c0, s0, s);
-                ++n;
-                s0 = s;
-                acc = 0.f;
+            float incl = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float v = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += v;
             }
-            acc += c;
+            const int q = sg < nseg ? (int)floorf((base + incl - c) / item_cost) : INT_MAX;
+            int qp = __shfl_up_sync(0xffffffffu, q, 1);
+            if (lane == 0) qp = q_last;
+            const bool start = sg < nseg && (sg == 0 || q != qp);
+            const unsigned mask = __ballot_sync(0xffffffffu, start);
+            if (EMIT && start) {
+                const int idx = n + __popc(mask & ((1u << lane) - 1u));
+                items[pos + idx] = make_int4(b, c0, sg, nseg);
+                if (idx > first) items[pos + idx - 1].w = sg;
+            }
+            n += __popc(mask);
+            base += __shfl_sync(0xffffffffu, incl, 31);
+            q_last = __shfl_sync(0xffffffffu, q, 31);
         }
-        if (EMIT) items[pos + n] = make_int4(b, c0, s0, nseg);
-        ++n;
     }
-    if (!EMIT) cnt[li] = n;
+    if (!EMIT && lane == 0) cnt[li] = n;
 }
 
 template <int KIND>
@@ -992,14 +1009,14 @@ static kfmm_status make_eval_items(kfmm_ctx *ctx, FmmPlans &P, float cost)
     const int nl = T.n_leaves;
     KF_CUDA(P.eval_cnt.ensure(sizeof(int) * (size_t)(nl + 1)));
     int *cnt = P.eval_cnt.as<int>();
-    eval_items_kernel<false><<<grid_for(nl, 128, 1 << 30), 128, 0, st>>>(
+    eval_items_kernel<false><<<grid_for((int64_t)nl * 32, 128, 1 << 30), 128, 0, st>>>(
         nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
         T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost, nullptr, cnt, nullptr);
     KF_LAUNCH();
     KF_TRY(scan_exclusive(ctx, cnt, cnt, nl, cnt + nl));
     KF_TRY(read_int(ctx, cnt + nl, &P.n_eval_items));
     KF_CUDA(P.eval_items.ensure(sizeof(int4) * (size_t)std::max(1, P.n_eval_items)));
-    eval_items_kernel<true><<<grid_for(nl, 128, 1 << 30), 128, 0, st>>>(
+    eval_items_kernel<true><<<grid_for((int64_t)nl * 32, 128, 1 << 30), 128, 0, st>>>(
         nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
         T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost, cnt, nullptr,
         P.eval_items.as<int4>());

@@ -756,16 +756,24 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     keys_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, ntrg, rc, T.trg_key.as<uint64_t>(),
                                                       T.trg_perm.as<int>());
     KF_LAUNCH();
+    // targets given as the very array of the sources: one sort, then copies
+    const bool same = trg_xyz == src_xyz && ntrg == nsrc;
     KF_TRY(radix_sort(ctx, T.src_key, T.src_perm, (int)nsrc, 3 * L));
-    KF_TRY(radix_sort(ctx, T.trg_key, T.trg_perm, (int)ntrg, 3 * L));
+    if (!same) KF_TRY(radix_sort(ctx, T.trg_key, T.trg_perm, (int)ntrg, 3 * L));
     KF_CUDA(T.src_xyz.ensure(sizeof(float4) * nsrc));
     KF_CUDA(T.trg_xyz.ensure(sizeof(float4) * ntrg));
     gather_points_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_xyz, T.src_perm.as<int>(), nsrc,
                                                                T.src_xyz.as<float4>());
     KF_LAUNCH();
-    gather_points_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, T.trg_perm.as<int>(), ntrg,
-                                                               T.trg_xyz.as<float4>());
-    KF_LAUNCH();
+    if (same) {
+        KF_CUDA(cudaMemcpyAsync(T.trg_key.p, T.src_key.p, sizeof(uint64_t) * ntrg, cudaMemcpyDeviceToDevice, st));
+        KF_CUDA(cudaMemcpyAsync(T.trg_perm.p, T.src_perm.p, sizeof(int) * ntrg, cudaMemcpyDeviceToDevice, st));
+        KF_CUDA(cudaMemcpyAsync(T.trg_xyz.p, T.src_xyz.p, sizeof(float4) * ntrg, cudaMemcpyDeviceToDevice, st));
+    } else {
+        gather_points_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, T.trg_perm.as<int>(), ntrg,
+                                                                   T.trg_xyz.as<float4>());
+        KF_LAUNCH();
+    }
     if (src_nrm) {
         KF_CUDA(T.src_nrm.ensure(sizeof(float4) * nsrc));
         gather_points_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_nrm, T.src_perm.as<int>(), nsrc,
@@ -976,24 +984,32 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
                                                                          T.wboxes.as<int>());
         KF_LAUNCH();
     }
-    // ---- work counts
-    {
-        DevBuf &acc = tmp[4];
-        KF_CUDA(acc.ensure(sizeof(unsigned long long) * 3));
-        KF_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 3, st));
-        work_count_kernel<<<grid_for(n_boxes, 128, 1 << 30), 128, 0, st>>>(
-            n_boxes, T.box_leaf.as<int>(), T.box_src.as<int2>(), T.box_trg.as<int2>(), T.u_off.as<int>(),
-            T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, T.x_off.as<int>(),
-            T.x_idx.as<int>(), acc.as<unsigned long long>());
-        KF_LAUNCH();
-        unsigned long long h[3];
-        KF_CUDA(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, st));
-        KF_CUDA(cudaStreamSynchronize(st));
-        T.p2p_pairs = (int64_t)h[0];
-        T.l2p_pairs = (int64_t)h[1];
-        T.p2l_pairs = (int64_t)h[2];
-    }
+    T.counts_valid = false;  // work counts for the statistics: made on request
     T.built = true;
+    return KFMM_OK;
+}
+
+// Interaction counts of the built tree (P2P, L2P/M2P, P2L pairs) for the statistics.
+kfmm_status tree_work_counts(kfmm_ctx *ctx)
+{
+    Tree &T = ctx->tree;
+    if (T.counts_valid) return KFMM_OK;
+    const cudaStream_t st = ctx->stream;
+    DevBuf &acc = ctx->work.tree_tmp[4];
+    KF_CUDA(acc.ensure(sizeof(unsigned long long) * 3));
+    KF_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 3, st));
+    work_count_kernel<<<grid_for(T.n_boxes, 128, 1 << 30), 128, 0, st>>>(
+        T.n_boxes, T.box_leaf.as<int>(), T.box_src.as<int2>(), T.box_trg.as<int2>(), T.u_off.as<int>(),
+        T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, T.x_off.as<int>(),
+        T.x_idx.as<int>(), acc.as<unsigned long long>());
+    KF_LAUNCH();
+    unsigned long long h[3];
+    KF_CUDA(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    KF_CUDA(cudaStreamSynchronize(st));
+    T.p2p_pairs = (int64_t)h[0];
+    T.l2p_pairs = (int64_t)h[1];
+    T.p2l_pairs = (int64_t)h[2];
+    T.counts_valid = true;
     return KFMM_OK;
 }
 

@@ -49,6 +49,24 @@ BEM_N = 12          # cantilever cells per unit length: 40 n^2 = 5760 triangles
 TRAFFIC_BYTES = {"m2l": 412841728 + 153561856}
 
 
+def max_over_ranks(x, world, device):
+    """The slowest rank's value (every rank calls this; world == 1 returns x).  Runs on any
+    torch.distributed backend: NCCL on the GPUs, gloo in the CPU tests."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, slowest_seconds):
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest rank's
+    time (weak scaling)."""
+    return world * units_per_rank / slowest_seconds
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -181,12 +199,8 @@ def bem_leg(K, local, world):
             torch.cuda.synchronize()
             st = b.solve(u, t, **kw)
             times.append(st["seconds"])
-    sec = float(np.mean(times))
-    if world > 1:
-        tt = torch.tensor([sec], device=f"cuda:{local}")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        sec = float(tt.item())
-    out.update({"solves_per_s": world / sec, "ms_per_solve": 1e3 * sec, "inner_iters": st["iters"],
+    sec = max_over_ranks(float(np.mean(times)), world, f"cuda:{local}")
+    out.update({"solves_per_s": aggregate_rate(1, world, sec), "ms_per_solve": 1e3 * sec, "inner_iters": st["iters"],
                 "outer": st["outer"], "fmm_matvecs": st["matvecs"], "fp64_matvecs": st["matvecs_hi"],
                 "relres": st["relres"], "method": "GMRES-IR: FP32 FMM corrections (p=6), FP64 direct residuals"})
     with K.Bem(V, T, K.BEM_DIRECT_FP64, device=local) as b:
@@ -272,12 +286,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     phases = f.phase_times(reset=True)
     f.set_profiling(False)
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.n / (ms / 1e3)
+    ms = max_over_ranks(float(np.mean(step_ms)), world, dev)
+    value = aggregate_rate(args.n, world, ms / 1e3)
     ph_ms = {k: v[0] / max(1, args.steps) for k, v in phases.items()}
     eval_ms = sum(v for k, v in ph_ms.items() if k != "tree")
 
@@ -296,7 +306,7 @@ def main():
         torch.cuda.synchronize(dev)
         if k >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
-    e2e_ms = 1e3 * float(np.mean(e2e_t))
+    e2e_ms = max_over_ranks(1e3 * float(np.mean(e2e_t)), world, dev)
     h2d = 4 * 3 * args.n * 4  # points (as sources and targets), normals, two densities
     d2h = 4 * 3 * args.n
 
@@ -351,7 +361,7 @@ def main():
                        "step": "tree build + one SL+DL FMM evaluation", "l2": "flushed (512 MB write) between steps",
                        "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
             "clocks": clocks,
-            "e2e": {"value": world * args.n / (e2e_ms / 1e3), "unit": "targets/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": aggregate_rate(args.n, world, e2e_ms / 1e3), "unit": "targets/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": int(launches),
             "roofline": roof,

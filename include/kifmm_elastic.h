@@ -90,6 +90,9 @@ typedef struct kfmm_options {
     int autotune;       /* 1: the context's first evaluation times candidate launch shapes on
                            its tree (columns per M2L work item; cost cap of the leaf-
                            evaluation work items) and keeps the fastest for later builds (1)  */
+    int streams;        /* 1: the parts of an evaluation that need no multipole data (P2L and
+                           the leaf-to-leaf P2P) run on a second stream, concurrently with the
+                           upward pass and M2L; not while profiling (1)                      */
 } kfmm_options;
 
 /* Tree and work counts of the last kfmm_build (for tests and roofline accounting). */
@@ -195,7 +198,7 @@ kfmm_status kfmm_export_list(const kfmm_ctx *ctx, char which, int32_t *offsets, 
 
 /* Phases timed when profiling is on (CUDA events on the context stream around each phase). */
 typedef enum kfmm_phase {
-    KFMM_PH_TREE = 0,     /* kfmm_build: keys, sort, split, lists                          */
+    KFMM_PH_TREE = 0,     /* kfmm_build: bounding cube, Morton keys, sort, sorted points   */
     KFMM_PH_PACK = 1,     /* source records (sorted, pre-scaled densities)                 */
     KFMM_PH_S2M = 2,      /* sources -> upward check surfaces of the leaves                 */
     KFMM_PH_UP_PINV = 3,  /* upward check -> upward equivalent densities (leaves)          */
@@ -205,7 +208,9 @@ typedef enum kfmm_phase {
     KFMM_PH_DOWN = 7,     /* downward densities and L2L, top-down                          */
     KFMM_PH_EVAL = 8,     /* leaf evaluation: L2P + M2P (W list) + P2P (U list)             */
     KFMM_PH_M2L_BASIS = 9, /* upward densities into the shared M2L basis (compression)       */
-    KFMM_N_PHASES = 10
+    KFMM_PH_TREE_SPLIT = 10, /* kfmm_build: boxes level by level, leaves, colleagues         */
+    KFMM_PH_TREE_LISTS = 11, /* kfmm_build: U, V, W, X lists, V directions, box groups       */
+    KFMM_N_PHASES = 12
 } kfmm_phase;
 
 /* Turn per-phase timing on or off (off by default).  Timing adds two event records per

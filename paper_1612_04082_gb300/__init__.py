@@ -38,7 +38,8 @@ class kfmm_options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double), ("pinv_rtol", ctypes.c_double),
                 ("m2l_rtol", ctypes.c_double), ("m2l_rank_max", ctypes.c_int), ("m2l_tensor_cores", ctypes.c_int),
-                ("device", ctypes.c_int), ("graphs", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("device", ctypes.c_int), ("graphs", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("streams", ctypes.c_int)]
 
 
 class kfmm_stats(ctypes.Structure):
@@ -200,7 +201,8 @@ def kfmm_export_list(ctx, which: str):
     return off, items[: n.value]
 
 
-PHASES = ("tree", "pack", "s2m", "up_pinv", "m2m", "m2l", "p2l", "down", "eval", "m2l_basis")
+PHASES = ("tree", "pack", "s2m", "up_pinv", "m2m", "m2l", "p2l", "down", "eval", "m2l_basis", "tree_split",
+          "tree_lists")
 
 
 def kfmm_set_profiling(ctx, enable: bool):

@@ -53,6 +53,7 @@ void kfmm_default_options(kfmm_options *opt)
     opt->device = 0;
     opt->graphs = 1;
     opt->autotune = 1;
+    opt->streams = 1;
 }
 
 kfmm_status kfmm_create(kfmm_ctx **out, const kfmm_options *opt)
@@ -75,6 +76,18 @@ kfmm_status kfmm_create(kfmm_ctx **out, const kfmm_options *opt)
     kfmm_ctx *c = new (std::nothrow) kfmm_ctx();
     if (!c) return KFMM_ERR_OOM;
     c->opt = o;
+    if (o.streams) {
+        // second stream and fork/join events of the overlapped evaluation (made here, outside
+        // any graph capture)
+        bool ok = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
+        for (cudaEvent_t *ev : {&c->ev_fork, &c->ev_p2l, &c->ev_near})
+            ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            kfmm_destroy(c);
+            return KFMM_ERR_CUDA;
+        }
+    }
     *out = c;
     return KFMM_OK;
 }
@@ -86,6 +99,12 @@ kfmm_status kfmm_destroy(kfmm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     ctx->graph.reset();
     if (ctx->graph.cap_stream) cudaStreamDestroy(ctx->graph.cap_stream);
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+    }
+    for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_p2l, ctx->ev_near})
+        if (e) cudaEventDestroy(e);
     delete ctx;
     return KFMM_OK;
 }
@@ -104,6 +123,11 @@ kfmm_status kfmm_set_material(kfmm_ctx *ctx, double K, double G)
 kfmm_status kfmm_set_stream(kfmm_ctx *ctx, void *stream)
 {
     if (!ctx) return KFMM_ERR_INVALID_ARG;
+    if (ctx->stream != (cudaStream_t)stream) {
+        // work (and table uploads) queued on the old stream complete first
+        KF_CUDA(cudaStreamSynchronize(ctx->stream));
+        ctx->staging.reset();
+    }
     ctx->stream = (cudaStream_t)stream;
     return KFMM_OK;
 }

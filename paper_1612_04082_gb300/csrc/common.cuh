@@ -191,10 +191,57 @@ struct Work {
     DevBuf up_phi;    // float [n_boxes][3n]   upward equivalent densities (W-list boxes)
     DevBuf dn_phi;    // float [n_boxes][3n]   downward equivalent densities (leaves)
     DevBuf scan_tmp[4];  // per-level partial sums of the device scan
-    DevBuf tree_tmp[12]; // tree-build temporaries (sort ping-pong, histograms, child ranges...)
+    DevBuf tree_tmp[15]; // tree-build temporaries (sort ping-pong, histograms, child ranges...)
     DevBuf stage_in[4];  // staging of host inputs
     DevBuf stage_out;
     DevBuf tmp;
+    // box-vector buffers whose padding lanes are known to be zero: their allocations and the
+    // density-column layout they were zeroed for
+    void *zero_ptr[8] = {};
+    int zero_ld[8] = {};
+    int zero_ncol = 0, zero_nb = 0;
+};
+
+// Pinned host memory for tables built on the host and copied to the device in stream order,
+// without a synchronisation per copy.  Space is handed out in order and given back by reset(),
+// which is called only right after a synchronisation of the context stream (all copies done).
+struct Staging {
+    struct Chunk {
+        void *p = nullptr;
+        size_t bytes = 0;
+    };
+    std::vector<Chunk> chunks;
+    size_t cur = 0, used = 0;
+    Staging() = default;
+    Staging(const Staging &) = delete;
+    Staging &operator=(const Staging &) = delete;
+    void *take(size_t n) {
+        n = (n + 15) & ~(size_t)15;
+        while (cur < chunks.size() && used + n > chunks[cur].bytes) {
+            ++cur;
+            used = 0;
+        }
+        if (cur == chunks.size()) {
+            Chunk c;
+            c.bytes = n > ((size_t)4 << 20) ? n : ((size_t)4 << 20);
+            if (cudaMallocHost(&c.p, c.bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            chunks.push_back(c);
+            used = 0;
+        }
+        void *r = (char *)chunks[cur].p + used;
+        used += n;
+        return r;
+    }
+    void reset() {
+        cur = 0;
+        used = 0;
+    }
+    ~Staging() {
+        for (Chunk &c : chunks) cudaFreeHost(c.p);
+    }
 };
 
 // Tile tables of the grouped gather-GEMM, built once per tree.
@@ -218,11 +265,14 @@ struct FmmPlans {
     int n_m2l_items = 0;
     std::vector<int4> m2l_host;     // one density column
     int m2l_ncol = 1;
-    int ncol_zeroed = 0;            // density columns of box vectors allocated and zeroed
     DevBuf err;                     // int: set by kernels whose bounded waits gave up
-    DevBuf eval_items;              // int4 {leaf box, first target, first segment, end segment}
-    DevBuf eval_cnt;                // int per leaf: items, then their offsets
-    int n_eval_items = 0;
+    // leaf-evaluation work items, int4 {leaf box, first target, first segment, end segment}:
+    // one list over all segments, or (eval_split) a near list (P2P: U leaves and direct W
+    // boxes) followed by a far list (L2P and M2P), launched separately
+    DevBuf eval_items;
+    DevBuf eval_cnt;                // int per leaf and list: items, then their offsets
+    int n_eval_items = 0, n_eval_far = 0;
+    bool eval_split = false;
 };
 
 // Per-phase CUDA-event timing (off unless enabled).
@@ -282,6 +332,10 @@ struct kfmm_ctx {
         int m2l_chunk = 1024;      // columns per M2L work item
     } tune;
     cudaStream_t stream = nullptr;
+    kfmm::Staging staging;  // pinned host side of the in-order table uploads
+    // second stream of the overlapped evaluation and its fork/join events (made on first use)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_p2l = nullptr, ev_near = nullptr;
     double G = 1.0, nu = 0.3;
     std::string err;
     kfmm::Operators ops;

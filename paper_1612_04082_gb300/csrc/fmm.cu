@@ -548,6 +548,8 @@ struct EvalArgs {
     float *out;
     int ldo;
     int64_t rec_col, phi_col;  // strides of one density column (blockIdx.y) in rec and the phis
+    int part;                  // 0: all segments; 1: P2P only (U leaves, direct W boxes);
+                               // 2: L2P and M2P only
 };
 
 // one source record, only the fields the kernel family reads
@@ -657,7 +659,7 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
 
     // ---- L2P (segment 0) and M2P (W boxes above the direct threshold): equivalent sources
     //      of one box, 32 at a time
-    for (int j = s0; j < s1 && j <= nW; ++j) {
+    for (int j = s0; e.part != 1 && j < s1 && j <= nW; ++j) {
         const int src_box = j == 0 ? b : e.wi[wo0 + j - 1];
         if (j > 0) {
             const int2 r = e.bsrc[src_box];
@@ -698,7 +700,7 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
     // ---- P2P with the direct W boxes and the U-list leaves other than the leaf itself: up
     //      to 32 source ranges at a time, batches of 32 records filled across ranges
     bool has_self = false;
-    for (int j0 = max(s0, 1); j0 < s1; j0 += 32) {
+    for (int j0 = max(s0, 1); e.part != 2 && j0 < s1; j0 += 32) {
         const int nr = min(32, s1 - j0);
         int beg = 0, cnt = 0;
         bool self = false;
@@ -819,12 +821,15 @@ __global__ void zero_out_kernel(int64_t n, float *__restrict__ out, int ldo, int
 // (warp pair-steps) cuts a new item wherever floor(prefix / item_cost) changes, so no item
 // exceeds the cap by more than one segment.  Each start lane writes its item and closes the
 // previous one.  item_cost is 1024 by default and tuned per context when autotuning is on.
+// For a split evaluation (part 1: P2P, part 2: L2P and M2P) the segments of the other part
+// cost nothing, so they never start an item.
 template <bool EMIT>
 __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, const int2 *__restrict__ btrg,
                                   const int2 *__restrict__ bsrc, const int *__restrict__ uo,
                                   const int *__restrict__ ui, const int *__restrict__ wo,
                                   const int *__restrict__ wi, int w_direct_max, int n_surf, float item_cost,
-                                  const int *__restrict__ off, int *__restrict__ cnt, int4 *__restrict__ items)
+                                  int part, const int *__restrict__ off, int *__restrict__ cnt,
+                                  int4 *__restrict__ items)
 {
     const int lane = threadIdx.x & 31;
     const int li = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -847,16 +852,19 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
             const int sg = sb + lane;
             float c = 0.f;
             if (sg < nseg) {
+                bool far = true;  // an equivalent surface (L2P, M2P) rather than sources
                 if (sg == 0) {
                     c = 0.5f * (float)n_surf;
                 } else if (sg <= nW) {
                     const int2 r = bsrc[wi[w0 + sg - 1]];
-                    c = r.y - r.x > w_direct_max ? 0.5f * (float)n_surf : (float)(r.y - r.x);
+                    far = r.y - r.x > w_direct_max;
+                    c = far ? 0.5f * (float)n_surf : (float)(r.y - r.x);
                 } else {
                     const int2 r = bsrc[ui[u0 + sg - 1 - nW]];
                     c = (float)(r.y - r.x);
+                    far = false;
                 }
-                c *= w;
+                c *= (part == 1 && far) || (part == 2 && !far) ? 0.f : w;  // segments of the other part
             }
             float incl = c;
 #pragma unroll
@@ -885,6 +893,7 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
 template <int KIND>
 void launch_eval(const EvalArgs &e, int n_items, int ncol, bool sl, bool dl, cudaStream_t st)
 {
+    if (n_items <= 0) return;
     const dim3 grid((unsigned)((n_items + kEvalWarps - 1) / kEvalWarps), (unsigned)ncol);
     if (sl && dl) eval_leaf_kernel<KIND, true, true><<<grid, kEvalThreads, 0, st>>>(e);
     else if (sl) eval_leaf_kernel<KIND, true, false><<<grid, kEvalThreads, 0, st>>>(e);
@@ -906,7 +915,7 @@ static kfmm_status make_plan(kfmm_ctx *ctx, GemmPlan &pl, const std::vector<int>
     pl.n_tiles = (int)t.size();
     if (pl.n_tiles) {
         KF_CUDA(pl.tiles.ensure(sizeof(int4) * t.size()));
-        KF_CUDA(cudaMemcpy(pl.tiles.p, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
+        KF_TRY(upload_async(ctx, pl.tiles.p, t.data(), sizeof(int4) * t.size()));
     }
     pl.host_tiles = t;
     pl.ncol = 1;
@@ -925,7 +934,7 @@ static kfmm_status plan_ncol(kfmm_ctx *ctx, GemmPlan &pl, int ncol)
     pl.n_tiles = (int)t.size();
     if (pl.n_tiles) {
         KF_CUDA(pl.tiles.ensure(sizeof(int4) * t.size()));
-        KF_CUDA(cudaMemcpy(pl.tiles.p, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
+        KF_TRY(upload_async(ctx, pl.tiles.p, t.data(), sizeof(int4) * t.size()));
     }
     for (int k = 0; k < 9; ++k) pl.n_tc_items[k] = -1;
     pl.ncol = ncol;
@@ -954,7 +963,7 @@ static kfmm_status run_tc_box(kfmm_ctx *ctx, GemmPlan &pl, const Operators::TcOp
                 for (int mt = 0; mt < nm; ++mt) items.push_back(make_int4(c * op.n_mat + t.x, mt, t.y, t.z));
         pl.n_tc_items[nm] = (int)items.size();
         KF_CUDA(pl.tc_items[nm].ensure(sizeof(int4) * std::max<size_t>(1, items.size())));
-        KF_CUDA(cudaMemcpy(pl.tc_items[nm].p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+        KF_TRY(upload_async(ctx, pl.tc_items[nm].p, items.data(), sizeof(int4) * items.size()));
     }
     tc::TcBoxArgs a;
     a.A = op.img.as<uint16_t>();
@@ -1004,23 +1013,44 @@ static kfmm_status make_eval_items(kfmm_ctx *ctx, FmmPlans &P, float cost)
 {
     const Tree &T = ctx->tree;
     const cudaStream_t st = ctx->stream;
-    P.n_eval_items = 0;
+    P.n_eval_items = P.n_eval_far = 0;
+    P.eval_split = ctx->opt.streams != 0;
     if (!T.n_leaves) return KFMM_OK;
-    const int nl = T.n_leaves;
-    KF_CUDA(P.eval_cnt.ensure(sizeof(int) * (size_t)(nl + 1)));
+    const int nl = T.n_leaves, nparts = P.eval_split ? 2 : 1;
+    // counts of all lists side by side ([part][leaf]), one scan, one read: with a split the
+    // far items follow the near ones in the same buffer
+    KF_CUDA(P.eval_cnt.ensure(sizeof(int) * (size_t)(nparts * nl + 1)));
     int *cnt = P.eval_cnt.as<int>();
-    eval_items_kernel<false><<<grid_for((int64_t)nl * 32, 128, 1 << 30), 128, 0, st>>>(
-        nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
-        T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost, nullptr, cnt, nullptr);
-    KF_LAUNCH();
-    KF_TRY(scan_exclusive(ctx, cnt, cnt, nl, cnt + nl));
-    KF_TRY(read_int(ctx, cnt + nl, &P.n_eval_items));
-    KF_CUDA(P.eval_items.ensure(sizeof(int4) * (size_t)std::max(1, P.n_eval_items)));
-    eval_items_kernel<true><<<grid_for((int64_t)nl * 32, 128, 1 << 30), 128, 0, st>>>(
-        nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
-        T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost, cnt, nullptr,
-        P.eval_items.as<int4>());
-    KF_LAUNCH();
+    auto items_kernel = [&](bool emit, int k) {
+        const int part = P.eval_split ? k + 1 : 0;
+        int *c = cnt + (size_t)k * nl;
+        if (emit)
+            eval_items_kernel<true><<<grid_for((int64_t)nl * 32, 128, 1 << 30), 128, 0, st>>>(
+                nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(),
+                T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost, part,
+                c, nullptr, P.eval_items.as<int4>());
+        else
+            eval_items_kernel<false><<<grid_for((int64_t)nl * 32, 128, 1 << 30), 128, 0, st>>>(
+                nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(),
+                T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost, part,
+                nullptr, c, nullptr);
+    };
+    for (int k = 0; k < nparts; ++k) {
+        items_kernel(false, k);
+        KF_LAUNCH();
+    }
+    KF_TRY(scan_exclusive(ctx, cnt, cnt, nparts * nl, cnt + (size_t)nparts * nl));
+    int h[2] = {0, 0};
+    KF_CUDA(cudaMemcpyAsync(&h[0], cnt + nl, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (nparts == 2) KF_CUDA(cudaMemcpyAsync(&h[1], cnt + 2 * (size_t)nl, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KF_TRY(sync_stream(ctx));
+    P.n_eval_items = h[0];
+    P.n_eval_far = nparts == 2 ? h[1] - h[0] : 0;
+    KF_CUDA(P.eval_items.ensure(sizeof(int4) * (size_t)std::max(1, P.n_eval_items + P.n_eval_far)));
+    for (int k = 0; k < nparts; ++k) {
+        items_kernel(true, k);
+        KF_LAUNCH();
+    }
     return KFMM_OK;
 }
 
@@ -1041,7 +1071,6 @@ static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
         }
         KF_TRY(make_plan(ctx, P.m2l, gm, gb, ge));
         make_m2l_host(ctx, P, ctx->tune.m2l_chunk);
-        P.ncol_zeroed = 0;
     }
     KF_CUDA(P.err.ensure(sizeof(int)));
     KF_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), st));
@@ -1136,18 +1165,25 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
         KF_TRY(build_plans(ctx, P));
         P.valid = true;
     }
-    if (P.ncol_zeroed < ncol) {
-        // box vectors of all density columns ([column][box][ld]): zeroed once, so the padding
-        // lanes read by the GEMM K loops stay zero
+    {
+        // box vectors of all density columns ([column][box][ld]).  The GEMM K loops read their
+        // padding lanes, which no kernel writes: a buffer is zeroed in full when it is
+        // allocated, and again only when the layout moves the lanes (another row length or
+        // column count, or more than one column over another number of boxes).
         DevBuf *bufs[8] = {&W.up_chk, &W.alpha, &W.psi, &W.cdn, &W.dn_chk, &W.beta, &W.up_phi, &W.dn_phi};
         const int lds[8] = {ld, kup, rp, rp, ld, kdp, ld, ld};
+        const bool moved = W.zero_ncol != ncol || (ncol > 1 && W.zero_nb != nb);
         for (int k = 0; k < 8; ++k) {
-            const size_t bytes = sizeof(float) * (size_t)nb * lds[k] * ncol;
-            KF_CUDA(bufs[k]->ensure(bytes));
-            KF_CUDA(cudaMemsetAsync(bufs[k]->p, 0, bytes, st));
+            KF_CUDA(bufs[k]->ensure(sizeof(float) * (size_t)nb * lds[k] * ncol));
+            if (moved || W.zero_ptr[k] != bufs[k]->p || W.zero_ld[k] != lds[k]) {
+                KF_CUDA(cudaMemsetAsync(bufs[k]->p, 0, bufs[k]->bytes, st));
+                W.zero_ptr[k] = bufs[k]->p;
+                W.zero_ld[k] = lds[k];
+            }
         }
+        W.zero_ncol = ncol;
+        W.zero_nb = nb;
         if (O.m2l_tc_mtiles > 0) KF_CUDA(W.psi2.ensure(sizeof(uint16_t) * 2 * (size_t)nb * rp * ncol));
-        P.ncol_zeroed = ncol;
     }
     // translation work items of all density columns: x = column * 316 + direction
     auto upload_m2l_items = [&]() -> kfmm_status {
@@ -1158,7 +1194,7 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
         P.n_m2l_items = (int)items.size();
         if (P.n_m2l_items) {
             KF_CUDA(P.m2l_items.ensure(sizeof(int4) * items.size()));
-            KF_CUDA(cudaMemcpy(P.m2l_items.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+            KF_TRY(upload_async(ctx, P.m2l_items.p, items.data(), sizeof(int4) * items.size()));
         }
         P.m2l_ncol = ncol;
         return KFMM_OK;
@@ -1187,27 +1223,121 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
                                                                    T.src_perm.as<int>(), sl, dl, ldd, ncol, kc.c_sl,
                                                                    kc.c_dl, kc.b12, W.src_rec.as<SrcRec>());
     KF_LAUNCH();
-    // ---- S2M: sources -> upward check surface of each leaf
-    ctx->phase(KFMM_PH_S2M);
-    KF_CUDA(cudaMemsetAsync(W.alpha.p, 0, sizeof(float) * (size_t)nb * kup * ncol, st));
-    auto check_pot = [&](const int *boxes, int nbx, int use_x, float radius, float *outp) {
+    auto check_pot = [&](const int *boxes, int nbx, int use_x, float radius, float *outp, cudaStream_t s) {
         const dim3 grid((unsigned)nbx, (unsigned)ncol);
         const int64_t rc = ns, oc = (int64_t)nb * ld;
         if (sl && dl)
-            check_potential_kernel<true, true><<<grid, kChkThreads, 0, st>>>(
+            check_potential_kernel<true, true><<<grid, kChkThreads, 0, s>>>(
                 boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
                 n, radius, W.src_rec.as<SrcRec>(), kc.a34, kc.b12, outp, ld, rc, oc);
         else if (sl)
-            check_potential_kernel<true, false><<<grid, kChkThreads, 0, st>>>(
+            check_potential_kernel<true, false><<<grid, kChkThreads, 0, s>>>(
                 boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
                 n, radius, W.src_rec.as<SrcRec>(), kc.a34, kc.b12, outp, ld, rc, oc);
         else
-            check_potential_kernel<false, true><<<grid, kChkThreads, 0, st>>>(
+            check_potential_kernel<false, true><<<grid, kChkThreads, 0, s>>>(
                 boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
                 n, radius, W.src_rec.as<SrcRec>(), kc.a34, kc.b12, outp, ld, rc, oc);
     };
+    // arguments of the leaf evaluation (the stress kind re-packs its sources below)
+    EvalArgs e;
+    e.items = P.eval_items.as<int4>();
+    e.n_items = P.n_eval_items;
+    e.w_direct_max = T.w_direct_max;
+    e.btrg = T.box_trg.as<int2>();
+    e.bsrc = T.box_src.as<int2>();
+    e.geom = geom;
+    e.uo = T.u_off.as<int>();
+    e.ui = T.u_idx.as<int>();
+    e.wo = T.w_off.as<int>();
+    e.wi = T.w_idx.as<int>();
+    e.trg = T.trg_xyz.as<float4>();
+    e.trg_perm = T.trg_perm.as<int>();
+    e.rec = W.src_rec.as<SrcRec>();
+    e.surf = O.surf.as<float4>();
+    e.n_surf = n;
+    e.r_in = (float)O.r_inner;
+    e.r_out = (float)O.r_outer;
+    e.dn_phi = W.dn_phi.as<float>();
+    e.up_phi = W.up_phi.as<float>();
+    e.ld_phi = ld;
+    e.phi_scale = kind == KFMM_DISP ? kc.c_sl : 1.f;
+    e.a34 = kc.a34;
+    e.b12 = kc.b12;
+    e.nu = kc.nu;
+    e.out_scale = kind == KFMM_DISP ? 1.f : kc.c_D;
+    e.out = out;
+    e.ldo = (kind == KFMM_DISP ? 3 : 6) * ncol;
+    e.rec_col = ns;
+    e.phi_col = (int64_t)nb * ld;
+    e.part = 0;
+    // the leaf evaluation: all segments (part 0) or the near (1) or far (2) list of a split
+    auto eval_part = [&](int part, cudaStream_t s) {
+        EvalArgs a = e;
+        a.part = P.eval_split ? part : 0;
+        a.items = P.eval_items.as<int4>() + (part == 2 ? P.n_eval_items : 0);
+        a.n_items = part == 2 ? P.n_eval_far : P.n_eval_items;
+        if (kind == KFMM_DISP) launch_eval<KFMM_DISP>(a, a.n_items, ncol, sl != nullptr, dl != nullptr, s);
+        else launch_eval<KFMM_STRESS>(a, a.n_items, ncol, sl != nullptr, dl != nullptr, s);
+    };
+    if (ctx->opt.autotune && !ctx->tune.eval_done && T.n_leaves) {
+        // cost cap of the leaf-evaluation items: time each candidate on this tree (the values
+        // of the equivalent densities do not change the work; the output is zeroed below)
+        float best = 1e30f, best_cost = ctx->tune.eval_cost;
+        for (float cost : {256.f, 512.f, 1024.f, 2048.f, 4096.f}) {
+            KF_TRY(make_eval_items(ctx, P, cost));
+            float ms = 0.f;
+            KF_TRY(time_launch(ctx, [&]() {
+                eval_part(1, st);
+                if (P.eval_split) eval_part(2, st);
+            }, &ms));
+            if (ms < best) best = ms, best_cost = cost;
+        }
+        ctx->tune.eval_cost = best_cost;
+        ctx->tune.eval_done = true;
+        KF_TRY(make_eval_items(ctx, P, best_cost));
+    }
+    // The near field (P2L into the downward check surfaces; the leaf-to-leaf P2P into the
+    // zeroed output) needs no multipole data.  With streams on it runs on the side stream,
+    // concurrently with the upward pass and M2L, and joins the context stream before the
+    // downward pass (P2L) and before the far part of the leaf evaluation (P2P).  Profiling
+    // serialises it on the one stream so that each phase keeps its own events.
+    const bool overlap = ctx->opt.streams != 0 && !ctx->prof.on && P.eval_split;
+    if (overlap && !ctx->side) return ctx->fail(KFMM_ERR_INTERNAL, "side stream missing");
+    const cudaStream_t s2 = overlap ? ctx->side : st;
+    if (overlap) {
+        KF_CUDA(cudaEventRecord(ctx->ev_fork, st));
+        KF_CUDA(cudaStreamWaitEvent(s2, ctx->ev_fork, 0));
+    }
+    // ---- P2L: X-list sources -> downward check surface
+    ctx->phase(KFMM_PH_P2L);
+    if (T.n_xboxes) {
+        check_pot(T.xboxes.as<int>(), T.n_xboxes, 1, (float)O.r_inner, W.dn_chk.as<float>(), s2);
+        KF_LAUNCH();
+    }
+    if (overlap) KF_CUDA(cudaEventRecord(ctx->ev_p2l, s2));
+    // ---- leaf evaluation, near part
+    ctx->phase(KFMM_PH_EVAL);
+    if (kind == KFMM_STRESS) {
+        // re-pack with stress scaling: t unscaled, u scaled by c_S / c_D
+        pack_sources_kernel<<<grid_for(ns * ncol, 256), 256, 0, s2>>>(
+            ns, T.src_xyz.as<float4>(), T.src_nrm.as<float4>(), T.src_perm.as<int>(), sl, dl, ldd, ncol, 1.f,
+            kc.c_S / kc.c_D, kc.b12, W.tmp.as<SrcRec>());
+        KF_LAUNCH();
+        e.rec = W.tmp.as<SrcRec>();
+    }
+    zero_out_kernel<<<grid_for(T.ntrg * e.ldo, 256), 256, 0, s2>>>(T.ntrg, out, e.ldo, 0, e.ldo);
+    KF_LAUNCH();
+    if (P.eval_split && P.n_eval_items) {
+        eval_part(1, s2);
+        KF_LAUNCH();
+    }
+    if (overlap) KF_CUDA(cudaEventRecord(ctx->ev_near, s2));
+    // ---- S2M: sources -> upward check surface of each leaf
+    ctx->phase(KFMM_PH_S2M);
+    KF_CUDA(cudaMemsetAsync(W.alpha.p, 0, sizeof(float) * (size_t)nb * kup * ncol, st));
     if (T.n_leaves) {
-        check_pot(T.leaves.as<int>(), T.n_leaves, 0, (float)O.r_outer, W.up_chk.as<float>());
+        check_pot(T.leaves.as<int>(), T.n_leaves, 0, (float)O.r_outer, W.up_chk.as<float>(), st);
         KF_LAUNCH();
     }
     // upward densities of the leaves in the singular basis: alpha = G h S^-1 U^T chk
@@ -1268,17 +1398,12 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
                         T.vp_trg.as<int>(), 0, 0, W.psi.as<float>(), rp, W.cdn.as<float>(), rp, nullptr, 1.f, 2, ncol,
                         nb, 1));
     }
-    // ---- P2L: X-list sources -> downward check surface
-    ctx->phase(KFMM_PH_P2L);
-    if (T.n_xboxes) {
-        check_pot(T.xboxes.as<int>(), T.n_xboxes, 1, (float)O.r_inner, W.dn_chk.as<float>());
-        KF_LAUNCH();
-    }
     // ---- downward densities in the singular basis: beta = S^-1 U^T (U_r c + G h chk_P2L),
     //      then L2L top-down, then the equivalent densities needed by the leaf pass
     ctx->phase(KFMM_PH_DOWN);
     KF_TRY(box_gemm(P.all, O.tc_wb, O.wb.as<float>(), 0, kd, rp, rp, nullptr, nullptr, 0, 0,
                     W.cdn.as<float>(), rp, W.beta.as<float>(), kdp, nullptr, 1.f, 0));
+    if (overlap) KF_CUDA(cudaStreamWaitEvent(st, ctx->ev_p2l, 0));
     KF_TRY(box_gemm(P.xboxes, O.tc_s2a_d, O.s2a_d.as<float>(), 0, kd,
                     ld, ld, T.xboxes.as<int>(), T.xboxes.as<int>(), 0, 0, W.dn_chk.as<float>(), ld,
                     W.beta.as<float>(), kdp, geom, (float)ctx->G, 1));
@@ -1291,73 +1416,12 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     KF_TRY(box_gemm(P.wboxes, O.tc_vu, O.vu.as<float>(), 0, m, kup,
                     kup, T.wboxes.as<int>(), T.wboxes.as<int>(), 0, 0, W.alpha.as<float>(), kup,
                     W.up_phi.as<float>(), ld, nullptr, 1.f, 0));
-    // ---- leaf evaluation
+    // ---- leaf evaluation, far part (all of it when the lists are not split); joins the
+    //      side stream first
     ctx->phase(KFMM_PH_EVAL);
-    const SrcRec *rec = W.src_rec.as<SrcRec>();
-    if (kind == KFMM_STRESS) {
-        // re-pack with stress scaling: t unscaled, u scaled by c_S / c_D
-        pack_sources_kernel<<<grid_for(ns * ncol, 256), 256, 0, st>>>(
-            ns, T.src_xyz.as<float4>(), T.src_nrm.as<float4>(), T.src_perm.as<int>(), sl, dl, ldd, ncol, 1.f,
-            kc.c_S / kc.c_D, kc.b12, W.tmp.as<SrcRec>());
-        KF_LAUNCH();
-        rec = W.tmp.as<SrcRec>();
-    }
-    EvalArgs e;
-    e.items = P.eval_items.as<int4>();
-    e.n_items = P.n_eval_items;
-    e.w_direct_max = T.w_direct_max;
-    e.btrg = T.box_trg.as<int2>();
-    e.bsrc = T.box_src.as<int2>();
-    e.geom = geom;
-    e.uo = T.u_off.as<int>();
-    e.ui = T.u_idx.as<int>();
-    e.wo = T.w_off.as<int>();
-    e.wi = T.w_idx.as<int>();
-    e.trg = T.trg_xyz.as<float4>();
-    e.trg_perm = T.trg_perm.as<int>();
-    e.rec = rec;
-    e.surf = O.surf.as<float4>();
-    e.n_surf = n;
-    e.r_in = (float)O.r_inner;
-    e.r_out = (float)O.r_outer;
-    e.dn_phi = W.dn_phi.as<float>();
-    e.up_phi = W.up_phi.as<float>();
-    e.ld_phi = ld;
-    e.phi_scale = kind == KFMM_DISP ? kc.c_sl : 1.f;
-    e.a34 = kc.a34;
-    e.b12 = kc.b12;
-    e.nu = kc.nu;
-    e.out_scale = kind == KFMM_DISP ? 1.f : kc.c_D;
-    e.out = out;
-    e.ldo = (kind == KFMM_DISP ? 3 : 6) * ncol;
-    e.rec_col = ns;
-    e.phi_col = (int64_t)nb * ld;
-    if (ctx->opt.autotune && !ctx->tune.eval_done && P.n_eval_items) {
-        // cost cap of the leaf-evaluation items: time each candidate on this tree
-        float best = 1e30f, best_cost = ctx->tune.eval_cost;
-        for (float cost : {256.f, 512.f, 1024.f, 2048.f, 4096.f}) {
-            KF_TRY(make_eval_items(ctx, P, cost));
-            e.items = P.eval_items.as<int4>();
-            e.n_items = P.n_eval_items;
-            float ms = 0.f;
-            KF_TRY(time_launch(ctx, [&]() {
-                zero_out_kernel<<<grid_for(T.ntrg * e.ldo, 256), 256, 0, st>>>(T.ntrg, out, e.ldo, 0, e.ldo);
-                if (kind == KFMM_DISP) launch_eval<KFMM_DISP>(e, P.n_eval_items, ncol, sl != nullptr, dl != nullptr, st);
-                else launch_eval<KFMM_STRESS>(e, P.n_eval_items, ncol, sl != nullptr, dl != nullptr, st);
-            }, &ms));
-            if (ms < best) best = ms, best_cost = cost;
-        }
-        ctx->tune.eval_cost = best_cost;
-        ctx->tune.eval_done = true;
-        KF_TRY(make_eval_items(ctx, P, best_cost));
-        e.items = P.eval_items.as<int4>();
-        e.n_items = P.n_eval_items;
-    }
-    zero_out_kernel<<<grid_for(T.ntrg * e.ldo, 256), 256, 0, st>>>(T.ntrg, out, e.ldo, 0, e.ldo);
-    KF_LAUNCH();
-    if (P.n_eval_items) {
-        if (kind == KFMM_DISP) launch_eval<KFMM_DISP>(e, P.n_eval_items, ncol, sl != nullptr, dl != nullptr, st);
-        else launch_eval<KFMM_STRESS>(e, P.n_eval_items, ncol, sl != nullptr, dl != nullptr, st);
+    if (overlap) KF_CUDA(cudaStreamWaitEvent(st, ctx->ev_near, 0));
+    if (P.eval_split ? P.n_eval_far > 0 : P.n_eval_items > 0) {
+        eval_part(P.eval_split ? 2 : 0, st);
         KF_LAUNCH();
     }
     ctx->phase(-1);
@@ -1436,7 +1500,7 @@ kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, 
         // the tensor-core kernels bound their barrier waits and report a time-out here
         int herr = 0;
         KF_CUDA(cudaMemcpyAsync(&herr, ctx->plans.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-        KF_CUDA(cudaStreamSynchronize(st));
+        KF_TRY(sync_stream(ctx));
         if (herr) {
             KF_CUDA(cudaMemsetAsync(ctx->plans.err.p, 0, sizeof(int), st));
             return ctx->fail(KFMM_ERR_DEVICE_TIMEOUT, "tensor-core product: a bounded barrier wait gave up");

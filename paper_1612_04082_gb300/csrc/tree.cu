@@ -107,10 +107,26 @@ kfmm_status scan_exclusive(kfmm_ctx *ctx, const int *in, int *out, int n, int *t
     return scan_level(ctx, in, out, n, total, 0);
 }
 
+kfmm_status sync_stream(kfmm_ctx *ctx)
+{
+    KF_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->staging.reset();
+    return KFMM_OK;
+}
+
 kfmm_status read_int(kfmm_ctx *ctx, const int *dptr, int *host)
 {
     KF_CUDA(cudaMemcpyAsync(host, dptr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    KF_CUDA(cudaStreamSynchronize(ctx->stream));
+    return sync_stream(ctx);
+}
+
+kfmm_status upload_async(kfmm_ctx *ctx, void *dst, const void *src, size_t bytes)
+{
+    if (bytes == 0) return KFMM_OK;
+    void *h = ctx->staging.take(bytes);
+    if (!h) return ctx->fail(KFMM_ERR_OOM, "pinned staging for a table upload");
+    std::memcpy(h, src, bytes);
+    KF_CUDA(cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, ctx->stream));
     return KFMM_OK;
 }
 
@@ -448,104 +464,151 @@ __device__ __forceinline__ bool adjacent(const int4 &a, const int4 &b, int L)
            az0 <= bz0 + lb && bz0 <= az0 + la;
 }
 
-// One thread per box.  mode 0: count into cnt[4][n_boxes] (U, V, W, X); mode 1: fill.
-__global__ void lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict__ uo,
-                             int *__restrict__ ui, const int *__restrict__ vo, int *__restrict__ vi,
-                             const int *__restrict__ wo, int *__restrict__ wi, const int *__restrict__ xo,
-                             int *__restrict__ xi, int *__restrict__ overflow)
+// One warp per box, lanes over the candidates of each list, ballots to place them in
+// candidate order.  mode 0: count into cnt[4][n_boxes] (U, V, W, X); mode 1: fill.  The
+// descendants of the non-leaf colleagues (U (ii), W) are walked through a frontier in shared
+// memory, 32 boxes per step, last in first out (so it stays about 8 x 32 per remaining
+// level); a frontier that would exceed kListQ sets *overflow and stops the walk.
+constexpr int kListWarps = 4;
+constexpr int kListQ = 2048;
+
+__global__ void __launch_bounds__(32 * kListWarps)
+lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict__ uo, int *__restrict__ ui,
+             const int *__restrict__ vo, int *__restrict__ vi, const int *__restrict__ wo, int *__restrict__ wi,
+             const int *__restrict__ xo, int *__restrict__ xi, int *__restrict__ overflow)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= tv.n_boxes) return;
+    __shared__ int frontier[kListWarps][kListQ];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    const int b = blockIdx.x * kListWarps + wid;
+    if (b >= tv.n_boxes) return;  // the whole warp
+    int *q = frontier[wid];
     const int L = tv.L;
     const int4 ab = tv.anchor[b];
     const int level = ab.w;
     const bool is_leaf = tv.leaf[b] != 0;
     const int par = tv.parent[b];
     int nu = 0, nv = 0, nw = 0, nx = 0;
-    int pu = mode ? uo[b] : 0, pv = mode ? vo[b] : 0, pw = mode ? wo[b] : 0, px = mode ? xo[b] : 0;
+    const int pu = mode ? uo[b] : 0, pv = mode ? vo[b] : 0, pw = mode ? wo[b] : 0, px = mode ? xo[b] : 0;
+    // append the lanes with `pred` set, in lane order, to a list
+    auto emit = [&](bool pred, int val, int *dst, int base, int &n) {
+        const unsigned m = __ballot_sync(full, pred);
+        if (mode && pred) dst[base + n + __popc(m & below)] = val;
+        n += __popc(m);
+    };
 
     // V: children of the parent's colleagues that are not adjacent to b
     if (level >= 2) {
-        for (int c = 0; c < 27; ++c) {
-            int C = tv.colleague[27 * par + c];
-            if (C < 0 || tv.leaf[C]) continue;
-            for (int o = 0; o < 8; ++o) {
-                int D = tv.child[8 * C + o];
-                if (D < 0) continue;
-                if (!adjacent(tv.anchor[D], ab, L)) {
-                    if (mode) vi[pv + nv] = D;
-                    ++nv;
-                }
+        for (int t0 = 0; t0 < 27 * 8; t0 += 32) {
+            const int t = t0 + lane;
+            int D = -1;
+            if (t < 27 * 8) {
+                const int C = tv.colleague[27 * par + (t >> 3)];
+                if (C >= 0 && !tv.leaf[C]) D = tv.child[8 * C + (t & 7)];
             }
+            emit(D >= 0 && !adjacent(tv.anchor[D >= 0 ? D : 0], ab, L), D, vi, pv, nv);
         }
     }
     // X: coarser leaves adjacent to the parent but not to b (b lies in their W list)
     if (level >= 1) {
         const int4 ap = tv.anchor[par];
         for (int A = par; A >= 0; A = tv.parent[A]) {
-            for (int c = 0; c < 27; ++c) {
-                int C = tv.colleague[27 * A + c];
-                if (C < 0 || C == A || !tv.leaf[C]) continue;
-                const int4 ac = tv.anchor[C];
-                if (adjacent(ac, ap, L) && !adjacent(ac, ab, L)) {
-                    if (mode) xi[px + nx] = C;
-                    ++nx;
+            bool ok = false;
+            int C = -1;
+            if (lane < 27) {
+                C = tv.colleague[27 * A + lane];
+                if (C >= 0 && C != A && tv.leaf[C]) {
+                    const int4 ac = tv.anchor[C];
+                    ok = adjacent(ac, ap, L) && !adjacent(ac, ab, L);
                 }
             }
+            emit(ok, C, xi, px, nx);
         }
     }
     if (is_leaf) {
         // U (i): leaves at this or coarser levels adjacent to b
         for (int A = b; A >= 0; A = tv.parent[A]) {
-            for (int c = 0; c < 27; ++c) {
-                int C = tv.colleague[27 * A + c];
-                if (C < 0 || !tv.leaf[C]) continue;
-                if (A != b && C == A) continue;
-                if (A == b || adjacent(tv.anchor[C], ab, L)) {
-                    if (mode) ui[pu + nu] = C;
-                    ++nu;
-                }
+            bool ok = false;
+            int C = -1;
+            if (lane < 27) {
+                C = tv.colleague[27 * A + lane];
+                if (C >= 0 && tv.leaf[C] && !(A != b && C == A)) ok = A == b || adjacent(tv.anchor[C], ab, L);
             }
+            emit(ok, C, ui, pu, nu);
         }
-        // U (ii) and W: descendants of non-leaf colleagues
-        int stack[192];
-        for (int c = 0; c < 27; ++c) {
-            if (c == 13) continue;
-            int C = tv.colleague[27 * b + c];
-            if (C < 0 || tv.leaf[C]) continue;
-            int sp = 0;
-            for (int o = 0; o < 8; ++o) {
-                int D = tv.child[8 * C + o];
-                if (D >= 0) stack[sp++] = D;
+        // U (ii) and W: descendants of non-leaf colleagues; the frontier starts with their
+        // children
+        int qn = 0;
+        for (int t0 = 0; t0 < 27 * 8; t0 += 32) {
+            const int t = t0 + lane;
+            int D = -1;
+            if (t < 27 * 8 && (t >> 3) != 13) {
+                const int C = tv.colleague[27 * b + (t >> 3)];
+                if (C >= 0 && !tv.leaf[C]) D = tv.child[8 * C + (t & 7)];
             }
-            while (sp > 0) {
-                int D = stack[--sp];
-                const int4 ad = tv.anchor[D];
-                if (adjacent(ad, ab, L)) {
-                    if (tv.leaf[D]) {
-                        if (mode) ui[pu + nu] = D;
-                        ++nu;
-                    } else {
-                        for (int o = 0; o < 8; ++o) {
-                            int E = tv.child[8 * D + o];
-                            if (E < 0) continue;
-                            if (sp < 192) stack[sp++] = E;
-                            else atomicExch(overflow, 1);
-                        }
-                    }
-                } else {
-                    if (mode) wi[pw + nw] = D;
-                    ++nw;
+            const unsigned m = __ballot_sync(full, D >= 0);
+            if (D >= 0) q[qn + __popc(m & below)] = D;
+            qn += __popc(m);
+        }
+        __syncwarp();
+        while (qn > 0) {
+            const int take = min(32, qn);
+            qn -= take;
+            const int D = lane < take ? q[qn + lane] : -1;
+            __syncwarp();
+            bool adj = false, lf = false;
+            if (D >= 0) {
+                adj = adjacent(tv.anchor[D], ab, L);
+                lf = tv.leaf[D] != 0;
+            }
+            emit(D >= 0 && adj && lf, D, ui, pu, nu);
+            emit(D >= 0 && !adj, D, wi, pw, nw);
+            // adjacent non-leaf boxes: push their children
+            int kids[8], nk = 0;
+            if (D >= 0 && adj && !lf) {
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    const int E = tv.child[8 * D + o];
+                    if (E >= 0) kids[nk++] = E;
                 }
             }
+            int incl = nk;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(full, incl, d);
+                if (lane >= d) incl += v;
+            }
+            const int total = __shfl_sync(full, incl, 31);
+            if (qn + total > kListQ) {
+                if (lane == 0) atomicExch(overflow, 1);
+                break;
+            }
+            for (int k = 0; k < nk; ++k) q[qn + incl - nk + k] = kids[k];
+            qn += total;
+            __syncwarp();
         }
     }
-    if (!mode) {
+    if (!mode && lane == 0) {
         cnt[b] = nu;
         cnt[tv.n_boxes + b] = nv;
         cnt[2 * tv.n_boxes + b] = nw;
         cnt[3 * tv.n_boxes + b] = nx;
     }
+}
+
+// Offsets of the four lists from one exclusive scan S of their concatenated counts:
+// off_l[b] = S[l n + b] - S[l n] for b <= n (S[4 n] is the grand total); tot[l] = list sizes.
+__global__ void list_offsets_kernel(int n, const int *__restrict__ S, int *__restrict__ o0, int *__restrict__ o1,
+                                    int *__restrict__ o2, int *__restrict__ o3, int *__restrict__ tot)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    int *outs[4] = {o0, o1, o2, o3};
+#pragma unroll
+    for (int l = 0; l < 4; ++l) outs[l][i] = S[(size_t)l * n + i] - S[(size_t)l * n];
+    if (i == n)
+        for (int l = 0; l < 4; ++l) tot[l] = S[(size_t)(l + 1) * n] - S[(size_t)l * n];
 }
 
 __global__ void leaf_flag_kernel(int n, const int *__restrict__ child, int *__restrict__ leaf)
@@ -567,19 +630,16 @@ __global__ void compact_kernel(int n, const int *__restrict__ flag, const int *_
 }
 
 // W-list boxes evaluated through their upward densities (more than w_direct_max sources)
-__global__ void mark_w_equiv_kernel(int64_t n, const int *__restrict__ idx, const int2 *__restrict__ bsrc,
-                                    int w_direct_max, int *__restrict__ flag)
-{
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int b = idx[k];
-    if (bsrc[b].y - bsrc[b].x > w_direct_max) flag[b] = 1;
-}
-
-__global__ void nonzero_kernel(int n, const int *__restrict__ cnt, int *__restrict__ flag)
+// Per box: X list non-empty (xflag); in some W list with more sources than w_direct_max
+// (wflag; a box is in some W list exactly when its X list is non-empty).
+__global__ void box_flags_kernel(int n, const int *__restrict__ xcnt, const int2 *__restrict__ bsrc,
+                                 int w_direct_max, int *__restrict__ xflag, int *__restrict__ wflag)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < n) flag[b] = cnt[b] > 0;
+    if (b >= n) return;
+    const bool x = xcnt[b] > 0;
+    xflag[b] = x;
+    wflag[b] = x && bsrc[b].y - bsrc[b].x > w_direct_max;
 }
 
 // V pairs grouped by direction (dx, dy, dz) in [-3,3]^3 minus [-1,1]^3: 316 groups.
@@ -716,7 +776,7 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     if (nsrc + ntrg > (int64_t)1 << 30) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many points (limit 2^30)");
 
     // ---- bounding cube and NaN check
-    DevBuf *tmp = ctx->work.tree_tmp;  // persistent scratch: slots 0-2 sort, 3-11 below
+    DevBuf *tmp = ctx->work.tree_tmp;  // persistent scratch: slots 0-2 sort, 3-14 below
     DevBuf &part = tmp[3];
     KF_CUDA(part.ensure(sizeof(float) * 7 * kBBoxBlocks));
     bbox_kernel<<<kBBoxBlocks, kBBoxThreads, 0, st>>>(src_xyz, nsrc, trg_xyz, ntrg, src_nrm,
@@ -724,7 +784,7 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     KF_LAUNCH();
     std::vector<float> hp(7 * kBBoxBlocks);
     KF_CUDA(cudaMemcpyAsync(hp.data(), part.p, sizeof(float) * hp.size(), cudaMemcpyDeviceToHost, st));
-    KF_CUDA(cudaStreamSynchronize(st));
+    KF_TRY(sync_stream(ctx));
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     double bad = 0;
     for (int b = 0; b < kBBoxBlocks; ++b) {
@@ -782,6 +842,7 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     }
 
     // ---- boxes, level by level
+    ctx->phase(KFMM_PH_TREE_SPLIT);
     size_t capb = std::max<size_t>(1024, (size_t)(4 * (nsrc + ntrg) / std::max(1, cap)) + 64);
     KF_CUDA(T.box_key.ensure(sizeof(uint64_t) * capb));
     KF_CUDA(T.box_anchor.ensure(sizeof(int4) * capb));
@@ -794,12 +855,11 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         int4 a0 = make_int4(0, 0, 0, 0);
         int p0 = -1;
         int2 s0 = make_int2(0, (int)nsrc), t0 = make_int2(0, (int)ntrg);
-        KF_CUDA(cudaMemcpyAsync(T.box_key.p, &k0, sizeof(k0), cudaMemcpyHostToDevice, st));
-        KF_CUDA(cudaMemcpyAsync(T.box_anchor.p, &a0, sizeof(a0), cudaMemcpyHostToDevice, st));
-        KF_CUDA(cudaMemcpyAsync(T.box_parent.p, &p0, sizeof(p0), cudaMemcpyHostToDevice, st));
-        KF_CUDA(cudaMemcpyAsync(T.box_src.p, &s0, sizeof(s0), cudaMemcpyHostToDevice, st));
-        KF_CUDA(cudaMemcpyAsync(T.box_trg.p, &t0, sizeof(t0), cudaMemcpyHostToDevice, st));
-        KF_CUDA(cudaStreamSynchronize(st));
+        KF_TRY(upload_async(ctx, T.box_key.p, &k0, sizeof(k0)));
+        KF_TRY(upload_async(ctx, T.box_anchor.p, &a0, sizeof(a0)));
+        KF_TRY(upload_async(ctx, T.box_parent.p, &p0, sizeof(p0)));
+        KF_TRY(upload_async(ctx, T.box_src.p, &s0, sizeof(s0)));
+        KF_TRY(upload_async(ctx, T.box_trg.p, &t0, sizeof(t0)));
     }
     T.level_off.assign(1, 0);
     T.level_off.push_back(1);
@@ -859,8 +919,7 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     // ---- colleagues
     DevBuf &loff = tmp[9];
     KF_CUDA(loff.ensure(sizeof(int) * T.level_off.size()));
-    KF_CUDA(cudaMemcpyAsync(loff.p, T.level_off.data(), sizeof(int) * T.level_off.size(),
-                            cudaMemcpyHostToDevice, st));
+    KF_TRY(upload_async(ctx, loff.p, T.level_off.data(), sizeof(int) * T.level_off.size()));
     KF_CUDA(T.colleague.ensure(sizeof(int) * 27 * n_boxes));
     TreeView tv{L,
                 n_boxes,
@@ -875,39 +934,86 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     colleague_kernel<<<grid_for(n_boxes, 128, 1 << 30), 128, 0, st>>>(tv, T.colleague.as<int>());
     KF_LAUNCH();
 
-    // ---- lists: count, scan, fill
-    DevBuf &cnt = tmp[10], &ovf = tmp[11];
-    KF_CUDA(cnt.ensure(sizeof(int) * 4 * (size_t)n_boxes));
-    KF_CUDA(ovf.ensure(sizeof(int)));
-    KF_CUDA(cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
-    lists_kernel<<<grid_for(n_boxes, 64, 1 << 30), 64, 0, st>>>(tv, 0, cnt.as<int>(), nullptr, nullptr, nullptr,
-                                                                 nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                                 ovf.as<int>());
+    // ---- lists: a count pass; then every size the host needs (list sizes, X and W boxes,
+    //      octant groups) is counted on the device and read back in one go
+    ctx->phase(KFMM_PH_TREE_LISTS);
+    const int ng = 8 * T.n_levels;
+    DevBuf &cnt = tmp[10], &hdr = tmp[11];
+    // hdr (ints): 0-3 sizes of the U, V, W, X lists; 4 X boxes; 5 W boxes; 6 traversal
+    // overflow; 8 on: octant-group sizes, 8 per level
+    if (4 * (int64_t)n_boxes >= INT32_MAX) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many boxes");
+    KF_CUDA(cnt.ensure(sizeof(int) * (4 * (size_t)n_boxes + 1)));
+    KF_CUDA(hdr.ensure(sizeof(int) * (8 + (size_t)ng)));
+    int *H = hdr.as<int>();
+    KF_CUDA(cudaMemsetAsync(H, 0, sizeof(int) * (8 + (size_t)ng), st));
+    const unsigned list_blocks = (unsigned)((n_boxes + kListWarps - 1) / kListWarps);
+    lists_kernel<<<list_blocks, 32 * kListWarps, 0, st>>>(tv, 0, cnt.as<int>(), nullptr, nullptr, nullptr, nullptr,
+                                                          nullptr, nullptr, nullptr, nullptr, H + 6);
     KF_LAUNCH();
     DevBuf *offs[4] = {&T.u_off, &T.v_off, &T.w_off, &T.x_off};
     DevBuf *idxs[4] = {&T.u_idx, &T.v_idx, &T.w_idx, &T.x_idx};
-    int64_t tot[4];
-    for (int l = 0; l < 4; ++l) {
-        KF_CUDA(offs[l]->ensure(sizeof(int) * (n_boxes + 1)));
-        KF_TRY(scan_exclusive(ctx, cnt.as<int>() + (size_t)l * n_boxes, offs[l]->as<int>(), n_boxes,
-                              offs[l]->as<int>() + n_boxes));
-        int t = 0;
-        KF_TRY(read_int(ctx, offs[l]->as<int>() + n_boxes, &t));
-        tot[l] = t;
-        KF_CUDA(idxs[l]->ensure(sizeof(int) * std::max<int64_t>(1, t)));
-    }
-    lists_kernel<<<grid_for(n_boxes, 64, 1 << 30), 64, 0, st>>>(
-        tv, 1, nullptr, T.u_off.as<int>(), T.u_idx.as<int>(), T.v_off.as<int>(), T.v_idx.as<int>(),
-        T.w_off.as<int>(), T.w_idx.as<int>(), T.x_off.as<int>(), T.x_idx.as<int>(), ovf.as<int>());
+    // offsets of the four lists from one scan over their concatenated counts
+    DevBuf &scn = tmp[12];
+    KF_CUDA(scn.ensure(sizeof(int) * (4 * (size_t)n_boxes + 1)));
+    int *S = scn.as<int>();
+    KF_TRY(scan_exclusive(ctx, cnt.as<int>(), S, 4 * n_boxes, S + 4 * (size_t)n_boxes));
+    for (int l = 0; l < 4; ++l) KF_CUDA(offs[l]->ensure(sizeof(int) * (n_boxes + 1)));
+    list_offsets_kernel<<<grid_for(n_boxes + 1, 256, 1 << 30), 256, 0, st>>>(
+        n_boxes, S, T.u_off.as<int>(), T.v_off.as<int>(), T.w_off.as<int>(), T.x_off.as<int>(), H);
     KF_LAUNCH();
-    int overflow = 0;
-    KF_TRY(read_int(ctx, ovf.as<int>(), &overflow));
-    if (overflow) return ctx->fail(KFMM_ERR_INTERNAL, "interaction-list traversal stack overflow");
-    T.n_u = tot[0];
-    T.n_v = tot[1];
-    T.n_w = tot[2];
-    T.n_x = tot[3];
-
+    // X boxes (non-empty X list) and the W boxes whose upward densities are evaluated at the
+    // targets.  A box lies in some W list exactly when its X list is non-empty (b is in W(C)
+    // iff C is in X(b)); those with more sources than half the surface points take the M2P
+    // path, the others are evaluated directly.
+    T.w_direct_max = surface_points(ctx->opt.p) / 2;
+    DevBuf &xflag = tmp[3], &xpos = tmp[8], &wflag = tmp[13], &wpos = tmp[14];
+    KF_CUDA(xflag.ensure(sizeof(int) * n_boxes));
+    KF_CUDA(xpos.ensure(sizeof(int) * n_boxes));
+    KF_CUDA(wflag.ensure(sizeof(int) * n_boxes));
+    KF_CUDA(wpos.ensure(sizeof(int) * n_boxes));
+    box_flags_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(
+        n_boxes, cnt.as<int>() + 3 * (size_t)n_boxes, T.box_src.as<int2>(), T.w_direct_max, xflag.as<int>(),
+        wflag.as<int>());
+    KF_LAUNCH();
+    KF_TRY(scan_exclusive(ctx, xflag.as<int>(), xpos.as<int>(), n_boxes, H + 4));
+    KF_TRY(scan_exclusive(ctx, wflag.as<int>(), wpos.as<int>(), n_boxes, H + 5));
+    oct_count_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_anchor.as<int4>(), H + 8);
+    KF_LAUNCH();
+    std::vector<int> hh(8 + (size_t)ng);
+    KF_CUDA(cudaMemcpyAsync(hh.data(), H, sizeof(int) * hh.size(), cudaMemcpyDeviceToHost, st));
+    KF_TRY(sync_stream(ctx));
+    if (hh[6]) return ctx->fail(KFMM_ERR_INTERNAL, "interaction-list traversal frontier overflow");
+    T.n_u = hh[0];
+    T.n_v = hh[1];
+    T.n_w = hh[2];
+    T.n_x = hh[3];
+    T.n_xboxes = hh[4];
+    T.n_wboxes = hh[5];
+    for (int l = 0; l < 4; ++l) KF_CUDA(idxs[l]->ensure(sizeof(int) * std::max(1, hh[l])));
+    lists_kernel<<<list_blocks, 32 * kListWarps, 0, st>>>(
+        tv, 1, nullptr, T.u_off.as<int>(), T.u_idx.as<int>(), T.v_off.as<int>(), T.v_idx.as<int>(),
+        T.w_off.as<int>(), T.w_idx.as<int>(), T.x_off.as<int>(), T.x_idx.as<int>(), H + 6);
+    KF_LAUNCH();
+    KF_CUDA(T.xboxes.ensure(sizeof(int) * std::max(1, T.n_xboxes)));
+    compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, xflag.as<int>(), xpos.as<int>(),
+                                                                     T.xboxes.as<int>());
+    KF_LAUNCH();
+    KF_CUDA(T.wboxes.ensure(sizeof(int) * std::max(1, T.n_wboxes)));
+    compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, wflag.as<int>(), wpos.as<int>(),
+                                                                     T.wboxes.as<int>());
+    KF_LAUNCH();
+    // ---- octant groups per level (M2M / L2L)
+    {
+        DevBuf &gc = tmp[6];
+        KF_CUDA(gc.ensure(sizeof(int) * (ng + 1)));
+        T.oct_off.assign(ng + 1, 0);
+        for (int g = 0; g < ng; ++g) T.oct_off[g + 1] = T.oct_off[g] + hh[8 + g];
+        KF_TRY(upload_async(ctx, gc.p, T.oct_off.data(), sizeof(int) * ng));
+        KF_CUDA(T.oct_child.ensure(sizeof(int) * std::max(1, n_boxes)));
+        oct_scatter_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_anchor.as<int4>(),
+                                                                             gc.as<int>(), T.oct_child.as<int>());
+        KF_LAUNCH();
+    }
     // ---- V pairs grouped by direction
     {
         // per-block direction histograms in shared memory, one scan over (direction, block),
@@ -924,7 +1030,7 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         std::vector<int> hoff(316);
         KF_CUDA(cudaMemcpy2DAsync(hoff.data(), sizeof(int), bhist.p, sizeof(int) * nblk, sizeof(int), 316,
                                   cudaMemcpyDeviceToHost, st));
-        KF_CUDA(cudaStreamSynchronize(st));
+        KF_TRY(sync_stream(ctx));
         T.vdir_off.assign(317, 0);
         for (int d = 0; d < 316; ++d) T.vdir_off[d] = hoff[d];
         T.vdir_off[316] = (int)T.n_v;
@@ -932,56 +1038,6 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         KF_CUDA(T.vp_trg.ensure(sizeof(int) * std::max<int64_t>(1, T.n_v)));
         vdir_place_kernel<<<nblk, kVdirBox, 0, st>>>(n_boxes, T.v_off.as<int>(), T.v_idx.as<int>(), pair_dir.as<int>(),
                                                      bhist.as<int>(), nblk, T.vp_src.as<int>(), T.vp_trg.as<int>());
-        KF_LAUNCH();
-    }
-    // ---- octant groups per level (M2M / L2L)
-    {
-        const int ng = 8 * T.n_levels;
-        DevBuf &gc = tmp[6];
-        KF_CUDA(gc.ensure(sizeof(int) * (ng + 1)));
-        KF_CUDA(cudaMemsetAsync(gc.p, 0, sizeof(int) * (ng + 1), st));
-        oct_count_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_anchor.as<int4>(),
-                                                                           gc.as<int>());
-        KF_LAUNCH();
-        std::vector<int> hc(ng);
-        KF_CUDA(cudaMemcpyAsync(hc.data(), gc.p, sizeof(int) * ng, cudaMemcpyDeviceToHost, st));
-        KF_CUDA(cudaStreamSynchronize(st));
-        T.oct_off.assign(ng + 1, 0);
-        for (int g = 0; g < ng; ++g) T.oct_off[g + 1] = T.oct_off[g] + hc[g];
-        KF_CUDA(cudaMemcpyAsync(gc.p, T.oct_off.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, st));
-        KF_CUDA(T.oct_child.ensure(sizeof(int) * std::max(1, n_boxes)));
-        oct_scatter_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_anchor.as<int4>(),
-                                                                             gc.as<int>(), T.oct_child.as<int>());
-        KF_LAUNCH();
-    }
-    // ---- boxes with X lists
-    {
-        DevBuf &flag = tmp[3], &xpos = tmp[8];
-        KF_CUDA(flag.ensure(sizeof(int) * n_boxes));
-        KF_CUDA(xpos.ensure(sizeof(int) * n_boxes));
-        nonzero_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, cnt.as<int>() + 3 * (size_t)n_boxes,
-                                                                         flag.as<int>());
-        KF_LAUNCH();
-        KF_TRY(scan_exclusive(ctx, flag.as<int>(), xpos.as<int>(), n_boxes, total.as<int>()));
-        KF_TRY(read_int(ctx, total.as<int>(), &T.n_xboxes));
-        KF_CUDA(T.xboxes.ensure(sizeof(int) * std::max(1, T.n_xboxes)));
-        compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, flag.as<int>(), xpos.as<int>(),
-                                                                         T.xboxes.as<int>());
-        KF_LAUNCH();
-        // boxes that appear in some W list with more sources than half the surface points:
-        // their upward densities are evaluated at the targets (the others directly)
-        T.w_direct_max = surface_points(ctx->opt.p) / 2;
-        KF_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * n_boxes, st));
-        if (T.n_w) {
-            mark_w_equiv_kernel<<<grid_for(T.n_w, 256, 1 << 30), 256, 0, st>>>(
-                T.n_w, T.w_idx.as<int>(), T.box_src.as<int2>(), T.w_direct_max, flag.as<int>());
-            KF_LAUNCH();
-        }
-        KF_TRY(scan_exclusive(ctx, flag.as<int>(), xpos.as<int>(), n_boxes, total.as<int>()));
-        KF_TRY(read_int(ctx, total.as<int>(), &T.n_wboxes));
-        KF_CUDA(T.wboxes.ensure(sizeof(int) * std::max(1, T.n_wboxes)));
-        compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, flag.as<int>(), xpos.as<int>(),
-                                                                         T.wboxes.as<int>());
         KF_LAUNCH();
     }
     T.counts_valid = false;  // work counts for the statistics: made on request
@@ -1005,7 +1061,7 @@ kfmm_status tree_work_counts(kfmm_ctx *ctx)
     KF_LAUNCH();
     unsigned long long h[3];
     KF_CUDA(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, st));
-    KF_CUDA(cudaStreamSynchronize(st));
+    KF_TRY(sync_stream(ctx));
     T.p2p_pairs = (int64_t)h[0];
     T.l2p_pairs = (int64_t)h[1];
     T.p2l_pairs = (int64_t)h[2];

@@ -22,6 +22,13 @@ kfmm_status scan_exclusive(kfmm_ctx *ctx, const int *in, int *out, int n, int *t
 // Reads one device int to the host (synchronises the context stream).
 kfmm_status read_int(kfmm_ctx *ctx, const int *dptr, int *host);
 
+// Synchronises the context stream; the pinned staging of earlier uploads is free again.
+kfmm_status sync_stream(kfmm_ctx *ctx);
+
+// Copies `bytes` of host memory to device memory in stream order through pinned staging:
+// no synchronisation, and `src` may be reused as soon as the call returns.
+kfmm_status upload_async(kfmm_ctx *ctx, void *dst, const void *src, size_t bytes);
+
 __device__ __forceinline__ int warp_incl_scan(int v) {
     const int lane = threadIdx.x & 31;
 #pragma unroll

@@ -365,3 +365,42 @@ def test_autotuned_launch_shapes(K):
             else:
                 assert st["m2l_chunk"] == 1024 and st["eval_item_cost"] == 1024.0
     assert rel(outs[1], outs[0]) < 1e-5
+
+
+@pytest.mark.parametrize("kind", ["disp", "stress"])
+def test_overlapped_streams_match_one_stream(K, kind):
+    """With the near field (P2L and the leaf-to-leaf P2P) on the second stream, concurrent
+    with the upward pass and M2L, the result equals the one-stream evaluation up to the order
+    of the atomic sums, for plain calls, graph replays and profiled (serialised) calls."""
+    src, nrm = W.box_with_voids_points(50000, n_voids=10)
+    ncol = 2
+    sl, dl = W.densities(len(src), ncol=ncol)
+    src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
+    kd = K.KFMM_DISP if kind == "disp" else K.KFMM_STRESS
+    no = (3 if kind == "disp" else 6) * ncol
+    x, n, s, d = dev(src), dev(nrm), dev(sl), dev(dl)
+    cfg = {} if kind == "disp" else dict(p=8, m2l_rtol=1e-7)
+    res = {}
+    for streams in (0, 1):
+        with make_ctx(K, G1, NU1, streams=streams, **cfg) as c:
+            c.build(x, n, x)
+            outs = []
+            for k in range(4):  # plain, plain, captured, replayed
+                out = torch.full((len(src), no), float("nan"), device="cuda:0")
+                c.eval(s, d, out, kind=kd, ncol=ncol)
+                outs.append(out.cpu().numpy().astype(np.float64))
+            c.set_profiling(True)
+            out = torch.full((len(src), no), float("nan"), device="cuda:0")
+            c.eval(s, d, out, kind=kd, ncol=ncol)
+            outs.append(out.cpu().numpy().astype(np.float64))
+            c.set_profiling(False)
+            res[streams] = outs
+    for o in res[0] + res[1]:
+        assert np.all(np.isfinite(o))
+        assert rel(o, res[0][0]) < 1e-5
+    idx = W.subsample(len(src), 300)
+    fn = O.direct_disp if kind == "disp" else O.direct_stress
+    tol = 1e-4 if kind == "disp" else 5e-4
+    s1, d1 = np.ascontiguousarray(sl[:, 3:6]), np.ascontiguousarray(dl[:, 3:6])
+    ref = fn(src[idx], src, nrm, s1, d1, G1, NU1)
+    assert rel(res[1][3][idx, no // 2:], ref) < tol

@@ -176,6 +176,7 @@ struct Tree {
     // a W-list box with at most this many sources is evaluated directly at the targets (exact
     // and cheaper than its n_surf equivalent points); larger ones through their densities
     int w_direct_max = 0;
+    int split_grid = 0;  // blocks of the cooperative split launch (all resident)
 };
 
 // Per-evaluation work arrays.

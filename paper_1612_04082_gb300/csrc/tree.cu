@@ -348,65 +348,241 @@ __device__ __forceinline__ int lower_bound_u64(const uint64_t *a, int lo, int hi
     return lo;
 }
 
-// For each box of the level: decide the split, find the 8 child ranges, count non-empty.
-__global__ void split_count_kernel(int first, int nb, int level, int L, int cap,
-                                   const uint64_t *__restrict__ bkey, const int2 *__restrict__ bsrc,
-                                   const int2 *__restrict__ btrg, const uint64_t *__restrict__ skey,
-                                   const uint64_t *__restrict__ tkey, int4 *__restrict__ crange,
-                                   int *__restrict__ ccount)
+// ------------------------------------------------------------------------------------
+// The level-by-level split and the leaf list in one cooperative launch: per level, every
+// block finds the child ranges of a contiguous chunk of the level's boxes (8 lanes per box,
+// one binary search per child boundary in the sorted keys), a grid barrier, the level's total
+// and the block's first child from the per-block counts, then the block writes its children
+// in box order; a last pass lists the leaves.  One launch and one read-back replace a
+// launch sequence and a host round trip per level.
+// ------------------------------------------------------------------------------------
+constexpr int kSplitThreads = 256;
+constexpr unsigned kBarrierSpin = 1u << 24;  // polls, ~64 ns apart, before a barrier gives up
+
+// Written by the split kernel, read back once by the host.
+struct SplitState {
+    int n_boxes, n_levels, n_leaves;
+    int err;  // 1: box capacity too small (the host grows it and runs again); 2: barrier time-out
+    unsigned bar_count, bar_gen;
+};
+
+struct SplitArgs {
+    int L, cap, capb;
+    int nsrc, ntrg;
+    const uint64_t *skey, *tkey;  // sorted Morton keys of sources and targets
+    uint64_t *bkey;
+    int4 *banchor;
+    int *bparent, *bchild;
+    int2 *bsrc, *btrg;
+    int *bleaf, *leaves;
+    int4 *crange;    // [8 capb]: child ranges of the current level's boxes
+    int *ccount;     // [capb]: their non-empty children
+    int *block_sum;  // [gridDim.x]
+    int *level_off;  // [L + 2]
+    SplitState *st;
+};
+
+// Grid-wide barrier of a cooperative launch (all blocks resident).  Polls are bounded; a
+// time-out is recorded in st->err and makes the caller return.
+__device__ __forceinline__ bool grid_barrier(SplitState *st)
 {
-    // 8 lanes per box: lane o finds where child o starts (its own binary search), the next
-    // lane's start is where child o ends
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = (int)(gt >> 3), o = (int)(gt & 7);
-    const bool valid = i < nb;
-    const int b = first + (valid ? i : 0);
-    const int2 s = bsrc[b], t = btrg[b];
-    const bool split = valid && (s.y - s.x > cap || t.y - t.x > cap) && level < L;
-    int sb = s.x, tb = t.x;
-    if (split && o > 0) {
-        const int sh = 3 * (L - level - 1);
-        const uint64_t lo = ((bkey[b] << 3) | (uint64_t)o) << sh;
-        sb = lower_bound_u64(skey, s.x, s.y, lo);
-        tb = lower_bound_u64(tkey, t.x, t.y, lo);
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &st->bar_gen;
+        const unsigned g = *gen;
+        int good = 1;
+        __threadfence();
+        if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            for (unsigned it = 0; *gen == g; ++it) {
+                if (it >= kBarrierSpin) {
+                    good = 0;
+                    atomicExch(&st->err, 2);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = good;
     }
-    int se = __shfl_down_sync(0xffffffffu, sb, 1, 8), te = __shfl_down_sync(0xffffffffu, tb, 1, 8);
-    if (o == 7) {
-        se = s.y;
-        te = t.y;
-    }
-    const bool nonempty = split && (se > sb || te > tb);
-    const unsigned m = __ballot_sync(0xffffffffu, nonempty);
-    if (!valid) return;
-    if (split) crange[8 * i + o] = make_int4(sb, se, tb, te);
-    if (o == 0) ccount[i] = __popc((m >> (threadIdx.x & 24)) & 0xffu);
+    __syncthreads();
+    return ok != 0;
 }
 
-__global__ void split_emit_kernel(int first, int nb, int next_first, const int4 *__restrict__ crange,
-                                  const int *__restrict__ ccount, const int *__restrict__ coff,
-                                  uint64_t *__restrict__ bkey, int4 *__restrict__ banchor,
-                                  int *__restrict__ bparent, int *__restrict__ bchild,
-                                  int2 *__restrict__ bsrc, int2 *__restrict__ btrg)
+// Exclusive scan of one int per thread over the block; *total receives the block sum.
+__device__ __forceinline__ int block_excl_scan(int v, int &total)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    const int b = first + i;
-    for (int o = 0; o < 8; ++o) bchild[8 * b + o] = -1;
-    if (ccount[i] == 0) return;
-    int k = next_first + coff[i];
-    const int4 a = banchor[b];
-    for (int o = 0; o < 8; ++o) {
-        int4 r = crange[8 * i + o];
-        if (r.y > r.x || r.w > r.z) {
-            bkey[k] = (bkey[b] << 3) | (uint64_t)o;
-            banchor[k] = make_int4(2 * a.x + ((o >> 2) & 1), 2 * a.y + ((o >> 1) & 1), 2 * a.z + (o & 1),
-                                   a.w + 1);
-            bparent[k] = b;
-            bsrc[k] = make_int2(r.x, r.y);
-            btrg[k] = make_int2(r.z, r.w);
-            bchild[8 * b + o] = k;
-            ++k;
+    __shared__ int wsum[kSplitThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int incl = warp_incl_scan(v);
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int x = lane < kSplitThreads / 32 ? wsum[lane] : 0;
+        x = warp_incl_scan(x);
+        if (lane < kSplitThreads / 32) wsum[lane] = x;
+    }
+    __syncthreads();
+    const int excl = incl - v + (w > 0 ? wsum[w - 1] : 0);
+    total = wsum[kSplitThreads / 32 - 1];
+    __syncthreads();
+    return excl;
+}
+
+// Sum over all blocks of block_sum (all) and over the blocks before this one (pre).
+__device__ __forceinline__ void block_prefix(const int *block_sum, int &pre, int &all)
+{
+    int p = 0, t = 0;
+    for (int j = threadIdx.x; j < (int)gridDim.x; j += kSplitThreads) {
+        const int v = __ldcg(&block_sum[j]);
+        t += v;
+        if (j < (int)blockIdx.x) p += v;
+    }
+    block_excl_scan(p, pre);
+    block_excl_scan(t, all);
+}
+
+__device__ __forceinline__ uint64_t ldcg_u64(const uint64_t *p)
+{
+    return (uint64_t)__ldcg(reinterpret_cast<const unsigned long long *>(p));
+}
+
+__global__ void __launch_bounds__(kSplitThreads) split_tree_kernel(SplitArgs a)
+{
+    const unsigned full = 0xffffffffu;
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+    SplitState *st = a.st;
+    if (g == 0 && tid == 0) {
+        a.bkey[0] = 0;
+        a.banchor[0] = make_int4(0, 0, 0, 0);
+        a.bparent[0] = -1;
+        a.bsrc[0] = make_int2(0, a.nsrc);
+        a.btrg[0] = make_int2(0, a.ntrg);
+        a.level_off[0] = 0;
+        a.level_off[1] = 1;
+    }
+    if (!grid_barrier(st)) return;
+    int first = 0, nb = 1, n_boxes = 1, level = 0;
+    for (;;) {
+        // ---- child ranges and counts of this block's boxes (boxes written by any block at
+        //      the previous level: read through L2)
+        const int chunk = (nb + G - 1) / G;
+        const int b0 = min(nb, g * chunk), b1 = min(nb, b0 + chunk);
+        int mine = 0;
+        for (int base = b0; base < b1; base += kSplitThreads / 8) {
+            const int i = base + (tid >> 3), o = tid & 7;
+            const bool valid = i < b1;
+            const int b = first + (valid ? i : b0);
+            const int2 s = __ldcg(&a.bsrc[b]), t = __ldcg(&a.btrg[b]);
+            const bool split = valid && (s.y - s.x > a.cap || t.y - t.x > a.cap) && level < a.L;
+            int sb = s.x, tb = t.x;
+            if (split && o > 0) {
+                const int sh = 3 * (a.L - level - 1);
+                const uint64_t lo = ((ldcg_u64(&a.bkey[b]) << 3) | (uint64_t)o) << sh;
+                sb = lower_bound_u64(a.skey, s.x, s.y, lo);
+                tb = lower_bound_u64(a.tkey, t.x, t.y, lo);
+            }
+            int se = __shfl_down_sync(full, sb, 1, 8), te = __shfl_down_sync(full, tb, 1, 8);
+            if (o == 7) {
+                se = s.y;
+                te = t.y;
+            }
+            const bool nonempty = split && (se > sb || te > tb);
+            const unsigned m = __ballot_sync(full, nonempty);
+            if (valid) {
+                a.crange[8 * (size_t)i + o] = make_int4(sb, se, tb, te);
+                if (o == 0) {
+                    const int c = __popc((m >> (tid & 24)) & 0xffu);
+                    a.ccount[i] = c;
+                    mine += c;
+                }
+            }
         }
+        int bsum;
+        block_excl_scan(mine, bsum);
+        if (tid == 0) a.block_sum[g] = bsum;
+        if (!grid_barrier(st)) return;
+        int prefix, total;
+        block_prefix(a.block_sum, prefix, total);
+        if (n_boxes + total > a.capb) {  // the same decision in every block
+            if (g == 0 && tid == 0) atomicExch(&st->err, 1);
+            return;
+        }
+        // ---- this block's children, in box order, from n_boxes + prefix on
+        int run = n_boxes + prefix;
+        for (int base = b0; base < b1; base += kSplitThreads) {
+            const int i = base + tid;
+            const bool valid = i < b1;
+            const int c = valid ? __ldcg(&a.ccount[i]) : 0;
+            int tot;
+            const int ex = block_excl_scan(c, tot);
+            if (valid) {
+                const int b = first + i;
+                int k = run + ex;
+                const int4 an = __ldcg(&a.banchor[b]);
+                const uint64_t key = ldcg_u64(&a.bkey[b]);
+                for (int o = 0; o < 8; ++o) {
+                    int child = -1;
+                    if (c > 0) {
+                        const int4 r = __ldcg(&a.crange[8 * (size_t)i + o]);
+                        if (r.y > r.x || r.w > r.z) {
+                            a.bkey[k] = (key << 3) | (uint64_t)o;
+                            a.banchor[k] = make_int4(2 * an.x + ((o >> 2) & 1), 2 * an.y + ((o >> 1) & 1),
+                                                     2 * an.z + (o & 1), an.w + 1);
+                            a.bparent[k] = b;
+                            a.bsrc[k] = make_int2(r.x, r.y);
+                            a.btrg[k] = make_int2(r.z, r.w);
+                            child = k++;
+                        }
+                    }
+                    a.bchild[8 * (size_t)b + o] = child;
+                }
+            }
+            run += tot;
+        }
+        if (!grid_barrier(st)) return;
+        if (total == 0) break;
+        first = n_boxes;
+        nb = total;
+        n_boxes += total;
+        ++level;
+        if (g == 0 && tid == 0) a.level_off[level + 1] = n_boxes;
+    }
+    // ---- leaves (no children), listed in box order
+    const int chunk = (n_boxes + G - 1) / G;
+    const int b0 = min(n_boxes, g * chunk), b1 = min(n_boxes, b0 + chunk);
+    int mine = 0;
+    for (int b = b0 + tid; b < b1; b += kSplitThreads) {
+        bool leaf = true;
+        for (int o = 0; o < 8; ++o)
+            if (__ldcg(&a.bchild[8 * (size_t)b + o]) >= 0) leaf = false;
+        a.bleaf[b] = leaf;
+        mine += leaf;
+    }
+    int bsum;
+    block_excl_scan(mine, bsum);
+    if (tid == 0) a.block_sum[g] = bsum;
+    if (!grid_barrier(st)) return;
+    int prefix, total;
+    block_prefix(a.block_sum, prefix, total);
+    int run = prefix;
+    for (int base = b0; base < b1; base += kSplitThreads) {
+        const int b = base + tid;
+        const int f = b < b1 ? a.bleaf[b] : 0;  // written by this thread above
+        int tot;
+        const int ex = block_excl_scan(f, tot);
+        if (f) a.leaves[run + ex] = b;
+        run += tot;
+    }
+    if (g == 0 && tid == 0) {
+        st->n_boxes = n_boxes;
+        st->n_levels = level + 1;
+        st->n_leaves = total;
     }
 }
 
@@ -611,17 +787,6 @@ __global__ void list_offsets_kernel(int n, const int *__restrict__ S, int *__res
         for (int l = 0; l < 4; ++l) tot[l] = S[(size_t)(l + 1) * n] - S[(size_t)l * n];
 }
 
-__global__ void leaf_flag_kernel(int n, const int *__restrict__ child, int *__restrict__ leaf)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n) return;
-    int l = 1;
-    for (int o = 0; o < 8; ++o)
-        if (child[8 * b + o] >= 0) l = 0;
-    leaf[b] = l;
-}
-
-// compact indices b with flag[b] != 0 using a scanned copy
 __global__ void compact_kernel(int n, const int *__restrict__ flag, const int *__restrict__ pos,
                                int *__restrict__ out)
 {
@@ -629,7 +794,6 @@ __global__ void compact_kernel(int n, const int *__restrict__ flag, const int *_
     if (b < n && flag[b]) out[pos[b]] = b;
 }
 
-// W-list boxes evaluated through their upward densities (more than w_direct_max sources)
 // Per box: X list non-empty (xflag); in some W list with more sources than w_direct_max
 // (wflag; a box is in some W list exactly when its X list is non-empty).
 __global__ void box_flags_kernel(int n, const int *__restrict__ xcnt, const int2 *__restrict__ bsrc,
@@ -750,19 +914,6 @@ __global__ void work_count_kernel(int n_boxes, const int *__restrict__ leaf, con
     if (p2l) atomicAdd(&acc[2], p2l);
 }
 
-template <class T> kfmm_status grow_keep(kfmm_ctx *ctx, DevBuf &buf, size_t used, size_t need)
-{
-    if (need <= buf.bytes) return KFMM_OK;
-    DevBuf nb;
-    size_t cap = std::max(need, buf.bytes * 2);
-    KF_CUDA(nb.ensure(cap));
-    if (used) KF_CUDA(cudaMemcpyAsync(nb.p, buf.p, used, cudaMemcpyDeviceToDevice, ctx->stream));
-    KF_CUDA(cudaStreamSynchronize(ctx->stream));
-    std::swap(nb.p, buf.p);
-    std::swap(nb.bytes, buf.bytes);
-    return KFMM_OK;
-}
-
 }  // namespace
 
 kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm, int64_t nsrc,
@@ -841,85 +992,58 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         KF_LAUNCH();
     }
 
-    // ---- boxes, level by level
+    // ---- boxes, level by level, and the leaves: one cooperative launch
     ctx->phase(KFMM_PH_TREE_SPLIT);
+    if (!T.split_grid) {
+        int per_sm = 0, n_sm = 0;
+        KF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_tree_kernel, kSplitThreads, 0));
+        KF_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->opt.device));
+        if (per_sm < 1) return ctx->fail(KFMM_ERR_INTERNAL, "tree split kernel cannot be resident");
+        T.split_grid = std::min(per_sm, 2) * n_sm;
+    }
     size_t capb = std::max<size_t>(1024, (size_t)(4 * (nsrc + ntrg) / std::max(1, cap)) + 64);
-    KF_CUDA(T.box_key.ensure(sizeof(uint64_t) * capb));
-    KF_CUDA(T.box_anchor.ensure(sizeof(int4) * capb));
-    KF_CUDA(T.box_parent.ensure(sizeof(int) * capb));
-    KF_CUDA(T.box_child.ensure(sizeof(int) * 8 * capb));
-    KF_CUDA(T.box_src.ensure(sizeof(int2) * capb));
-    KF_CUDA(T.box_trg.ensure(sizeof(int2) * capb));
-    {
-        uint64_t k0 = 0;
-        int4 a0 = make_int4(0, 0, 0, 0);
-        int p0 = -1;
-        int2 s0 = make_int2(0, (int)nsrc), t0 = make_int2(0, (int)ntrg);
-        KF_TRY(upload_async(ctx, T.box_key.p, &k0, sizeof(k0)));
-        KF_TRY(upload_async(ctx, T.box_anchor.p, &a0, sizeof(a0)));
-        KF_TRY(upload_async(ctx, T.box_parent.p, &p0, sizeof(p0)));
-        KF_TRY(upload_async(ctx, T.box_src.p, &s0, sizeof(s0)));
-        KF_TRY(upload_async(ctx, T.box_trg.p, &t0, sizeof(t0)));
-    }
-    T.level_off.assign(1, 0);
-    T.level_off.push_back(1);
-    int n_boxes = 1;
-    DevBuf &crange = tmp[4], &ccount = tmp[5], &coff = tmp[6], &total = tmp[7];
-    KF_CUDA(total.ensure(sizeof(int)));
-    for (int level = 0;; ++level) {
-        const int first = T.level_off[level], nb = T.level_off[level + 1] - first;
-        KF_CUDA(crange.ensure(sizeof(int4) * 8 * (size_t)nb));
-        KF_CUDA(ccount.ensure(sizeof(int) * (size_t)nb));
-        KF_CUDA(coff.ensure(sizeof(int) * (size_t)nb));
-        split_count_kernel<<<grid_for(8 * (int64_t)nb, 128, 1 << 30), 128, 0, st>>>(
-            first, nb, level, L, cap, T.box_key.as<uint64_t>(), T.box_src.as<int2>(), T.box_trg.as<int2>(),
-            T.src_key.as<uint64_t>(), T.trg_key.as<uint64_t>(), crange.as<int4>(), ccount.as<int>());
+    DevBuf &crange = tmp[4], &ccount = tmp[5], &bsum = tmp[6], &sstate = tmp[7], &loff = tmp[9];
+    KF_CUDA(bsum.ensure(sizeof(int) * T.split_grid));
+    KF_CUDA(sstate.ensure(sizeof(SplitState)));
+    KF_CUDA(loff.ensure(sizeof(int) * (L + 2)));
+    SplitState hs{};
+    for (;;) {
+        if (capb > (size_t)INT32_MAX / 8) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many boxes");
+        KF_CUDA(T.box_key.ensure(sizeof(uint64_t) * capb));
+        KF_CUDA(T.box_anchor.ensure(sizeof(int4) * capb));
+        KF_CUDA(T.box_parent.ensure(sizeof(int) * capb));
+        KF_CUDA(T.box_child.ensure(sizeof(int) * 8 * capb));
+        KF_CUDA(T.box_src.ensure(sizeof(int2) * capb));
+        KF_CUDA(T.box_trg.ensure(sizeof(int2) * capb));
+        KF_CUDA(T.box_leaf.ensure(sizeof(int) * capb));
+        KF_CUDA(T.leaves.ensure(sizeof(int) * capb));
+        KF_CUDA(crange.ensure(sizeof(int4) * 8 * capb));
+        KF_CUDA(ccount.ensure(sizeof(int) * capb));
+        KF_CUDA(cudaMemsetAsync(sstate.p, 0, sizeof(SplitState), st));
+        SplitArgs sa{L, cap, (int)capb, (int)nsrc, (int)ntrg, T.src_key.as<uint64_t>(), T.trg_key.as<uint64_t>(),
+                     T.box_key.as<uint64_t>(), T.box_anchor.as<int4>(), T.box_parent.as<int>(),
+                     T.box_child.as<int>(), T.box_src.as<int2>(), T.box_trg.as<int2>(), T.box_leaf.as<int>(),
+                     T.leaves.as<int>(), crange.as<int4>(), ccount.as<int>(), bsum.as<int>(), loff.as<int>(),
+                     sstate.as<SplitState>()};
+        void *args[] = {&sa};
+        KF_CUDA(cudaLaunchCooperativeKernel((const void *)split_tree_kernel, dim3(T.split_grid), dim3(kSplitThreads),
+                                            args, 0, st));
         KF_LAUNCH();
-        KF_TRY(scan_exclusive(ctx, ccount.as<int>(), coff.as<int>(), nb, total.as<int>()));
-        int nchild = 0;
-        KF_TRY(read_int(ctx, total.as<int>(), &nchild));
-        const size_t need = (size_t)n_boxes + nchild;
-        if (need > capb) {
-            size_t nc = std::max(need, 2 * capb);
-            KF_TRY(grow_keep<uint64_t>(ctx, T.box_key, sizeof(uint64_t) * n_boxes, sizeof(uint64_t) * nc));
-            KF_TRY(grow_keep<int4>(ctx, T.box_anchor, sizeof(int4) * n_boxes, sizeof(int4) * nc));
-            KF_TRY(grow_keep<int>(ctx, T.box_parent, sizeof(int) * n_boxes, sizeof(int) * nc));
-            KF_TRY(grow_keep<int>(ctx, T.box_child, sizeof(int) * 8 * n_boxes, sizeof(int) * 8 * nc));
-            KF_TRY(grow_keep<int2>(ctx, T.box_src, sizeof(int2) * n_boxes, sizeof(int2) * nc));
-            KF_TRY(grow_keep<int2>(ctx, T.box_trg, sizeof(int2) * n_boxes, sizeof(int2) * nc));
-            capb = nc;
-        }
-        split_emit_kernel<<<grid_for(nb, 128, 1 << 30), 128, 0, st>>>(
-            first, nb, n_boxes, crange.as<int4>(), ccount.as<int>(), coff.as<int>(), T.box_key.as<uint64_t>(),
-            T.box_anchor.as<int4>(), T.box_parent.as<int>(), T.box_child.as<int>(), T.box_src.as<int2>(),
-            T.box_trg.as<int2>());
-        KF_LAUNCH();
-        if (nchild == 0) break;
-        n_boxes += nchild;
-        T.level_off.push_back(n_boxes);
+        T.level_off.assign(L + 2, 0);
+        KF_CUDA(cudaMemcpyAsync(&hs, sstate.p, sizeof(SplitState), cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaMemcpyAsync(T.level_off.data(), loff.p, sizeof(int) * (L + 2), cudaMemcpyDeviceToHost, st));
+        KF_TRY(sync_stream(ctx));
+        if (hs.err == 2) return ctx->fail(KFMM_ERR_DEVICE_TIMEOUT, "tree split: a grid barrier gave up");
+        if (hs.err != 1) break;
+        capb *= 2;  // more boxes than the estimate: run again with twice the room
     }
+    const int n_boxes = hs.n_boxes;
     T.n_boxes = n_boxes;
-    T.n_levels = (int)T.level_off.size() - 1;
-    // children of the deepest level were initialised to -1 by split_emit (nchild == 0 pass)
+    T.n_levels = hs.n_levels;
+    T.n_leaves = hs.n_leaves;
+    T.level_off.resize(T.n_levels + 1);
 
-    // ---- leaves
-    KF_CUDA(T.box_leaf.ensure(sizeof(int) * n_boxes));
-    leaf_flag_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_child.as<int>(),
-                                                                       T.box_leaf.as<int>());
-    KF_LAUNCH();
-    DevBuf &pos = tmp[8];
-    KF_CUDA(pos.ensure(sizeof(int) * n_boxes));
-    KF_TRY(scan_exclusive(ctx, T.box_leaf.as<int>(), pos.as<int>(), n_boxes, total.as<int>()));
-    KF_TRY(read_int(ctx, total.as<int>(), &T.n_leaves));
-    KF_CUDA(T.leaves.ensure(sizeof(int) * T.n_leaves));
-    compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_leaf.as<int>(), pos.as<int>(),
-                                                                     T.leaves.as<int>());
-    KF_LAUNCH();
-
-    // ---- colleagues
-    DevBuf &loff = tmp[9];
-    KF_CUDA(loff.ensure(sizeof(int) * T.level_off.size()));
-    KF_TRY(upload_async(ctx, loff.p, T.level_off.data(), sizeof(int) * T.level_off.size()));
+    // ---- colleagues (level offsets on the device as the split kernel left them)
     KF_CUDA(T.colleague.ensure(sizeof(int) * 27 * n_boxes));
     TreeView tv{L,
                 n_boxes,

@@ -224,7 +224,9 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
 namespace {
 
 // ------------------------------------------------------------------------------------
-// source records: 4 x float4 = {y, nu'}, {t}, {u}, {n} in sorted order
+// source records: 4 x float4 = {y, nu'}, {t}, {u}, {n} in sorted order.  Displacement
+// records carry u pre-multiplied by 1 - 2 nu and nu' = n . u (acc_sl_dl_s); stress records
+// carry u scaled by c_S / c_D and nu' = (1 - 2 nu) n . u.
 // ------------------------------------------------------------------------------------
 struct SrcRec {
     float4 y, t, u, n;
@@ -234,7 +236,7 @@ struct SrcRec {
 __global__ void pack_sources_kernel(int64_t ns, const float4 *__restrict__ xyz, const float4 *__restrict__ nrm,
                                     const int *__restrict__ perm, const float *__restrict__ sl,
                                     const float *__restrict__ dl, int ld, int ncol, float st, float su,
-                                    float b12, SrcRec *__restrict__ rec)
+                                    float nscale, SrcRec *__restrict__ rec)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ns * ncol; e += stride) {
@@ -254,7 +256,7 @@ __global__ void pack_sources_kernel(int64_t ns, const float4 *__restrict__ xyz, 
             u = make_float3(su * s[0], su * s[1], su * s[2]);
             nn = nrm[i];
         }
-        const float nup = b12 * (nn.x * u.x + nn.y * u.y + nn.z * u.z);
+        const float nup = nscale * (nn.x * u.x + nn.y * u.y + nn.z * u.z);
         r.y = make_float4(p.x, p.y, p.z, nup);
         r.t = make_float4(t.x, t.y, t.z, 0.f);
         r.u = make_float4(u.x, u.y, u.z, 0.f);
@@ -282,17 +284,17 @@ constexpr int kChkThreads = 160;  // >= 152 check points at p = 6
 constexpr int kChkStage = 256;
 
 template <bool SL, bool DL>
-__device__ __forceinline__ void chk_pair(float x, float y, float z, const SrcRec &q, float a34, float b12, float &ox,
+__device__ __forceinline__ void chk_pair(float x, float y, float z, const SrcRec &q, float a34, float c3, float &ox,
                                          float &oy, float &oz)
 {
     const float dx = x - q.y.x, dy = y - q.y.y, dz = z - q.y.z;
     if (SL && DL)
-        acc_sl_dl<float>(dx, dy, dz, q.t.x, q.t.y, q.t.z, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, a34, b12,
-                         ox, oy, oz);
+        acc_sl_dl_s<float>(dx, dy, dz, q.t.x, q.t.y, q.t.z, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, a34, c3,
+                           ox, oy, oz);
     else if (SL)
         acc_sl<float>(dx, dy, dz, q.t.x, q.t.y, q.t.z, a34, ox, oy, oz);
     else
-        acc_dl<float>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, b12, ox, oy, oz);
+        acc_dl_s<float>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, c3, ox, oy, oz);
 }
 
 template <bool SL, bool DL>
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(kChkThreads)
 check_potential_kernel(const int *__restrict__ boxes, int nbox, int use_xlist, const int *__restrict__ xo,
                        const int *__restrict__ xi, const int2 *__restrict__ bsrc, const float4 *__restrict__ geom,
                        const float4 *__restrict__ surf, int n_surf, float radius, const SrcRec *__restrict__ rec,
-                       float a34, float b12, float *__restrict__ out, int ldo, int64_t rec_col, int64_t out_col)
+                       float a34, float c3, float *__restrict__ out, int ldo, int64_t rec_col, int64_t out_col)
 {
     __shared__ SrcRec sh[kChkStage];
     rec += blockIdx.y * rec_col;  // density column blockIdx.y
@@ -336,8 +338,8 @@ check_potential_kernel(const int *__restrict__ boxes, int nbox, int use_xlist, c
             if (has0) {
                 for (int s = 0; s < cnt; ++s) {
                     const SrcRec q = sh[s];
-                    chk_pair<SL, DL>(x, y, z, q, a34, b12, ox, oy, oz);
-                    if (has1) chk_pair<SL, DL>(x1, y1, z1, q, a34, b12, px, py, pz);
+                    chk_pair<SL, DL>(x, y, z, q, a34, c3, ox, oy, oz);
+                    if (has1) chk_pair<SL, DL>(x1, y1, z1, q, a34, c3, px, py, pz);
                 }
             }
         }
@@ -499,18 +501,19 @@ constexpr int kEvalThreads = 32 * kEvalWarps;
 constexpr unsigned kFull = 0xffffffffu;
 
 template <int KIND, bool SL, bool DL, bool CHK>
-__device__ __forceinline__ void p2p_pair(float x, float y, float z, const SrcRec &q, float a34, float b12, float nu,
-                                         float *o)
+__device__ __forceinline__ void p2p_pair(float x, float y, float z, const SrcRec &q, float a34, float b12, float c3,
+                                         float nu, float *o)
 {
     const float dx = x - q.y.x, dy = y - q.y.y, dz = z - q.y.z;
     if (KIND == KFMM_DISP) {
+        // displacement records carry the double-layer density pre-multiplied by 1 - 2 nu
         if (SL && DL)
-            acc_sl_dl<float, CHK>(dx, dy, dz, q.t.x, q.t.y, q.t.z, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w,
-                                  a34, b12, o[0], o[1], o[2]);
+            acc_sl_dl_s<float, CHK>(dx, dy, dz, q.t.x, q.t.y, q.t.z, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z,
+                                    q.y.w, a34, c3, o[0], o[1], o[2]);
         else if (SL)
             acc_sl<float, CHK>(dx, dy, dz, q.t.x, q.t.y, q.t.z, a34, o[0], o[1], o[2]);
         else
-            acc_dl<float, CHK>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, b12, o[0], o[1], o[2]);
+            acc_dl_s<float, CHK>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, c3, o[0], o[1], o[2]);
     } else {
         if (SL) acc_D<float, CHK>(dx, dy, dz, q.t.x, q.t.y, q.t.z, b12, o);
         if (DL) acc_S<float, CHK>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, nu, b12, o);
@@ -544,6 +547,7 @@ struct EvalArgs {
     int ld_phi;
     float phi_scale;  // c_sl for DISP, 1 for STRESS (D carries c_D at the end)
     float a34, b12, nu;
+    float c3;         // 3 / (1 - 2 nu): displacement records carry (1 - 2 nu) u
     float out_scale;  // 1 for DISP, c_D for STRESS
     float *out;
     int ldo;
@@ -601,17 +605,17 @@ __device__ __forceinline__ void eval_batch(const SrcRec *sh, int kbeg, int cnt, 
     int k = kbeg;
     for (; k + nsl < cnt; k += 2 * nsl) {
         const SrcRec qa = sh[k], qb = sh[k + nsl];
-        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, qa, e.a34, e.b12, e.nu, o0);
-        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, qb, e.a34, e.b12, e.nu, o0);
+        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, qa, e.a34, e.b12, e.c3, e.nu, o0);
+        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, qb, e.a34, e.b12, e.c3, e.nu, o0);
         if (two) {
-            p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, qa, e.a34, e.b12, e.nu, o1);
-            p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, qb, e.a34, e.b12, e.nu, o1);
+            p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, qa, e.a34, e.b12, e.c3, e.nu, o1);
+            p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, qb, e.a34, e.b12, e.c3, e.nu, o1);
         }
     }
     if (k < cnt) {
         const SrcRec q = sh[k];
-        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, q, e.a34, e.b12, e.nu, o0);
-        if (two) p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, q, e.a34, e.b12, e.nu, o1);
+        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, q, e.a34, e.b12, e.c3, e.nu, o0);
+        if (two) p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, q, e.a34, e.b12, e.c3, e.nu, o1);
     }
 }
 
@@ -1221,7 +1225,7 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     ctx->phase(KFMM_PH_PACK);
     pack_sources_kernel<<<grid_for(ns * ncol, 256), 256, 0, st>>>(ns, T.src_xyz.as<float4>(), T.src_nrm.as<float4>(),
                                                                    T.src_perm.as<int>(), sl, dl, ldd, ncol, kc.c_sl,
-                                                                   kc.c_dl, kc.b12, W.src_rec.as<SrcRec>());
+                                                                   kc.c_dl * kc.b12, 1.f, W.src_rec.as<SrcRec>());
     KF_LAUNCH();
     auto check_pot = [&](const int *boxes, int nbx, int use_x, float radius, float *outp, cudaStream_t s) {
         const dim3 grid((unsigned)nbx, (unsigned)ncol);
@@ -1229,15 +1233,15 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
         if (sl && dl)
             check_potential_kernel<true, true><<<grid, kChkThreads, 0, s>>>(
                 boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
-                n, radius, W.src_rec.as<SrcRec>(), kc.a34, kc.b12, outp, ld, rc, oc);
+                n, radius, W.src_rec.as<SrcRec>(), kc.a34, 3.f / kc.b12, outp, ld, rc, oc);
         else if (sl)
             check_potential_kernel<true, false><<<grid, kChkThreads, 0, s>>>(
                 boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
-                n, radius, W.src_rec.as<SrcRec>(), kc.a34, kc.b12, outp, ld, rc, oc);
+                n, radius, W.src_rec.as<SrcRec>(), kc.a34, 3.f / kc.b12, outp, ld, rc, oc);
         else
             check_potential_kernel<false, true><<<grid, kChkThreads, 0, s>>>(
                 boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
-                n, radius, W.src_rec.as<SrcRec>(), kc.a34, kc.b12, outp, ld, rc, oc);
+                n, radius, W.src_rec.as<SrcRec>(), kc.a34, 3.f / kc.b12, outp, ld, rc, oc);
     };
     // arguments of the leaf evaluation (the stress kind re-packs its sources below)
     EvalArgs e;
@@ -1265,6 +1269,7 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     e.a34 = kc.a34;
     e.b12 = kc.b12;
     e.nu = kc.nu;
+    e.c3 = 3.f / kc.b12;
     e.out_scale = kind == KFMM_DISP ? 1.f : kc.c_D;
     e.out = out;
     e.ldo = (kind == KFMM_DISP ? 3 : 6) * ncol;

@@ -964,11 +964,13 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
     keys_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_xyz, nsrc, rc, T.src_key.as<uint64_t>(),
                                                       T.src_perm.as<int>());
     KF_LAUNCH();
-    keys_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, ntrg, rc, T.trg_key.as<uint64_t>(),
-                                                      T.trg_perm.as<int>());
-    KF_LAUNCH();
-    // targets given as the very array of the sources: one sort, then copies
+    // targets given as the very array of the sources: one set of keys, one sort, then copies
     const bool same = trg_xyz == src_xyz && ntrg == nsrc;
+    if (!same) {
+        keys_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, ntrg, rc, T.trg_key.as<uint64_t>(),
+                                                          T.trg_perm.as<int>());
+        KF_LAUNCH();
+    }
     KF_TRY(radix_sort(ctx, T.src_key, T.src_perm, (int)nsrc, 3 * L));
     if (!same) KF_TRY(radix_sort(ctx, T.trg_key, T.trg_perm, (int)ntrg, 3 * L));
     KF_CUDA(T.src_xyz.ensure(sizeof(float4) * nsrc));

@@ -661,8 +661,12 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
     for (int a = 0; a < NO; ++a) o0[a] = o1[a] = 0.f;
     const int kbeg = act ? si : 32;  // inactive lanes skip every evaluation loop
 
-    // ---- L2P (segment 0) and M2P (W boxes above the direct threshold): equivalent sources
-    //      of one box, 32 at a time
+    // ---- L2P (segment 0) and M2P (W boxes above the direct threshold): the equivalent
+    //      sources of one box are staged whole in shared memory (all their loads in flight
+    //      at once), then evaluated two per step
+    extern __shared__ float4 eq_smem[];  // per warp: n_surf positions, then n_surf densities
+    float4 *eqp = eq_smem + (size_t)wid * 2 * e.n_surf, *eqf = eqp + e.n_surf;
+    const int n_eq = e.n_surf;
     for (int j = s0; e.part != 1 && j < s1 && j <= nW; ++j) {
         const int src_box = j == 0 ? b : e.wi[wo0 + j - 1];
         if (j > 0) {
@@ -671,33 +675,29 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
         }
         const float4 g = e.geom[src_box];
         const float rad = (j == 0 ? e.r_out : e.r_in) * g.w;
-        const float *phi = (j == 0 ? dn_phi : up_phi) + (int64_t)src_box * e.ld_phi;
-        for (int base = 0; base < e.n_surf; base += 32) {
-            const int cnt = min(32, e.n_surf - base);
-            __syncwarp();
-            if (lane < cnt) {
-                const int k = base + lane;
-                const float4 sp = e.surf[k];
-                sh[lane].y = make_float4(g.x + rad * sp.x, g.y + rad * sp.y, g.z + rad * sp.z, 0.f);
-                sh[lane].t = make_float4(e.phi_scale * phi[3 * k], e.phi_scale * phi[3 * k + 1],
-                                         e.phi_scale * phi[3 * k + 2], 0.f);
+        const float *__restrict__ phi = (j == 0 ? dn_phi : up_phi) + (int64_t)src_box * e.ld_phi;
+        __syncwarp();
+        for (int k = lane; k < n_eq; k += 32) {
+            const float4 sp = __ldg(&e.surf[k]);
+            const float f0 = __ldg(&phi[3 * k]), f1 = __ldg(&phi[3 * k + 1]), f2 = __ldg(&phi[3 * k + 2]);
+            eqp[k] = make_float4(g.x + rad * sp.x, g.y + rad * sp.y, g.z + rad * sp.z, 0.f);
+            eqf[k] = make_float4(e.phi_scale * f0, e.phi_scale * f1, e.phi_scale * f2, 0.f);
+        }
+        __syncwarp();
+        int k = act ? si : n_eq;
+        for (; k + nsl < n_eq; k += 2 * nsl) {  // two independent pairs per step
+            const float4 pa = eqp[k], fa = eqf[k], pb = eqp[k + nsl], fb = eqf[k + nsl];
+            equiv_pair<KIND>(x0, y0, z0, pa, fa, e.a34, e.b12, o0);
+            equiv_pair<KIND>(x0, y0, z0, pb, fb, e.a34, e.b12, o0);
+            if (two) {
+                equiv_pair<KIND>(x1, y1, z1, pa, fa, e.a34, e.b12, o1);
+                equiv_pair<KIND>(x1, y1, z1, pb, fb, e.a34, e.b12, o1);
             }
-            __syncwarp();
-            int k = kbeg;
-            for (; k + nsl < cnt; k += 2 * nsl) {  // two independent pairs per step
-                const float4 pa = sh[k].y, fa = sh[k].t, pb = sh[k + nsl].y, fb = sh[k + nsl].t;
-                equiv_pair<KIND>(x0, y0, z0, pa, fa, e.a34, e.b12, o0);
-                equiv_pair<KIND>(x0, y0, z0, pb, fb, e.a34, e.b12, o0);
-                if (two) {
-                    equiv_pair<KIND>(x1, y1, z1, pa, fa, e.a34, e.b12, o1);
-                    equiv_pair<KIND>(x1, y1, z1, pb, fb, e.a34, e.b12, o1);
-                }
-            }
-            if (k < cnt) {
-                const float4 pp = sh[k].y, f = sh[k].t;
-                equiv_pair<KIND>(x0, y0, z0, pp, f, e.a34, e.b12, o0);
-                if (two) equiv_pair<KIND>(x1, y1, z1, pp, f, e.a34, e.b12, o1);
-            }
+        }
+        if (k < n_eq) {
+            const float4 pp = eqp[k], f = eqf[k];
+            equiv_pair<KIND>(x0, y0, z0, pp, f, e.a34, e.b12, o0);
+            if (two) equiv_pair<KIND>(x1, y1, z1, pp, f, e.a34, e.b12, o1);
         }
     }
 
@@ -823,8 +823,9 @@ __global__ void zero_out_kernel(int64_t n, float *__restrict__ out, int ldo, int
 // Work items of the leaf evaluation: one warp per leaf.  For each target chunk the lanes cost
 // the source segments (L2P, W boxes, U leaves) 32 at a time; a warp prefix sum of the costs
 // (warp pair-steps) cuts a new item wherever floor(prefix / item_cost) changes, so no item
-// exceeds the cap by more than one segment.  Each start lane writes its item and closes the
-// previous one.  item_cost is 1024 by default and tuned per context when autotuning is on.
+// exceeds the cap by more than one segment.  An item is written once, when the next start
+// (its end) is known.  item_cost is 1024 by default and tuned per context when autotuning is
+// on.
 // For a split evaluation (part 1: P2P, part 2: L2P and M2P) the segments of the other part
 // cost nothing, so they never start an item.
 template <bool EMIT>
@@ -832,7 +833,7 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
                                   const int2 *__restrict__ bsrc, const int *__restrict__ uo,
                                   const int *__restrict__ ui, const int *__restrict__ wo,
                                   const int *__restrict__ wi, int w_direct_max, int n_surf, float item_cost,
-                                  int part, const int *__restrict__ off, int *__restrict__ cnt,
+                                  int split, const int *__restrict__ off, int *__restrict__ cnt,
                                   int4 *__restrict__ items)
 {
     const int lane = threadIdx.x & 31;
@@ -842,56 +843,70 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
     const int2 tr = btrg[b];
     const int w0 = wo[b], nW = wo[b + 1] - w0, u0 = uo[b], nU = uo[b + 1] - u0;
     const int nseg = 1 + nW + nU;
-    const int pos = EMIT ? off[li] : 0;
-    int n = 0;
-    for (int c0 = tr.x; c0 < tr.y; c0 += 64) {
-        const int nt = min(64, tr.y - c0);
-        int L, nsl;
-        const bool two = eval_layout(nt, L, nsl);
-        const float w = (two ? 2.f : 1.f) / (float)nsl;  // pair evaluations per lane and source
-        const int first = n;                             // first item of this chunk
-        float base = 0.f;
-        int q_last = -1;
-        for (int sb = 0; sb < nseg; sb += 32) {
-            const int sg = sb + lane;
-            float c = 0.f;
-            if (sg < nseg) {
-                bool far = true;  // an equivalent surface (L2P, M2P) rather than sources
-                if (sg == 0) {
-                    c = 0.5f * (float)n_surf;
-                } else if (sg <= nW) {
-                    const int2 r = bsrc[wi[w0 + sg - 1]];
-                    far = r.y - r.x > w_direct_max;
-                    c = far ? 0.5f * (float)n_surf : (float)(r.y - r.x);
-                } else {
-                    const int2 r = bsrc[ui[u0 + sg - 1 - nW]];
-                    c = (float)(r.y - r.x);
-                    far = false;
+    // one list (part 0), or the near (1) and far (2) lists with counts and offsets at
+    // [list][leaf]
+    for (int k = 0; k < (split ? 2 : 1); ++k) {
+        const int part = split ? k + 1 : 0;
+        const int pos = EMIT ? off[(size_t)k * n_leaves + li] : 0;
+        int n = 0;
+        for (int c0 = tr.x; c0 < tr.y; c0 += 64) {
+            const int nt = min(64, tr.y - c0);
+            int L, nsl;
+            const bool two = eval_layout(nt, L, nsl);
+            const float w = (two ? 2.f : 1.f) / (float)nsl;  // pair evaluations per lane and source
+            float base = 0.f;
+            int q_last = -1;
+            int pend_idx = -1, pend_sg = 0;  // last item started so far: its end is not known yet
+            for (int sb = 0; sb < nseg; sb += 32) {
+                const int sg = sb + lane;
+                float c = 0.f;
+                if (sg < nseg) {
+                    bool far = true;  // an equivalent surface (L2P, M2P) rather than sources
+                    if (sg == 0) {
+                        c = 0.5f * (float)n_surf;
+                    } else if (sg <= nW) {
+                        const int2 r = bsrc[wi[w0 + sg - 1]];
+                        far = r.y - r.x > w_direct_max;
+                        c = far ? 0.5f * (float)n_surf : (float)(r.y - r.x);
+                    } else {
+                        const int2 r = bsrc[ui[u0 + sg - 1 - nW]];
+                        c = (float)(r.y - r.x);
+                        far = false;
+                    }
+                    c *= (part == 1 && far) || (part == 2 && !far) ? 0.f : w;  // segments of the other part
                 }
-                c *= (part == 1 && far) || (part == 2 && !far) ? 0.f : w;  // segments of the other part
-            }
-            float incl = c;
+                float incl = c;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const float v = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += v;
+                for (int d = 1; d < 32; d <<= 1) {
+                    const float v = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += v;
+                }
+                const int q = sg < nseg ? (int)floorf((base + incl - c) / item_cost) : INT_MAX;
+                int qp = __shfl_up_sync(0xffffffffu, q, 1);
+                if (lane == 0) qp = q_last;
+                const bool start = sg < nseg && (sg == 0 || q != qp);
+                const unsigned mask = __ballot_sync(0xffffffffu, start);
+                // every item is written once, when its end (the next start) is known: the
+                // pending item of the previous batch ends at this batch's first start; an item
+                // with a later start in this batch ends there; the last one stays pending
+                if (mask) {
+                    if (EMIT && pend_idx >= 0 && lane == 0)
+                        items[pos + pend_idx] = make_int4(b, c0, pend_sg, sb + __ffs(mask) - 1);
+                    const unsigned later = mask & ~((2u << lane) - 1u);
+                    if (EMIT && start && later)
+                        items[pos + n + __popc(mask & ((1u << lane) - 1u))] =
+                            make_int4(b, c0, sg, sb + __ffs(later) - 1);
+                    pend_idx = n + __popc(mask) - 1;
+                    pend_sg = sb + 31 - __clz(mask);
+                }
+                n += __popc(mask);
+                base += __shfl_sync(0xffffffffu, incl, 31);
+                q_last = __shfl_sync(0xffffffffu, q, 31);
             }
-            const int q = sg < nseg ? (int)floorf((base + incl - c) / item_cost) : INT_MAX;
-            int qp = __shfl_up_sync(0xffffffffu, q, 1);
-            if (lane == 0) qp = q_last;
-            const bool start = sg < nseg && (sg == 0 || q != qp);
-            const unsigned mask = __ballot_sync(0xffffffffu, start);
-            if (EMIT && start) {
-                const int idx = n + __popc(mask & ((1u << lane) - 1u));
-                items[pos + idx] = make_int4(b, c0, sg, nseg);
-                if (idx > first) items[pos + idx - 1].w = sg;
-            }
-            n += __popc(mask);
-            base += __shfl_sync(0xffffffffu, incl, 31);
-            q_last = __shfl_sync(0xffffffffu, q, 31);
+            if (EMIT && pend_idx >= 0 && lane == 0) items[pos + pend_idx] = make_int4(b, c0, pend_sg, nseg);
         }
+        if (!EMIT && lane == 0) cnt[(size_t)k * n_leaves + li] = n;
     }
-    if (!EMIT && lane == 0) cnt[li] = n;
 }
 
 template <int KIND>
@@ -899,9 +914,11 @@ void launch_eval(const EvalArgs &e, int n_items, int ncol, bool sl, bool dl, cud
 {
     if (n_items <= 0) return;
     const dim3 grid((unsigned)((n_items + kEvalWarps - 1) / kEvalWarps), (unsigned)ncol);
-    if (sl && dl) eval_leaf_kernel<KIND, true, true><<<grid, kEvalThreads, 0, st>>>(e);
-    else if (sl) eval_leaf_kernel<KIND, true, false><<<grid, kEvalThreads, 0, st>>>(e);
-    else eval_leaf_kernel<KIND, false, true><<<grid, kEvalThreads, 0, st>>>(e);
+    // staged equivalent sources of the L2P / M2P segments (none in the P2P-only part)
+    const size_t smem = e.part == 1 ? 0 : sizeof(float4) * 2 * (size_t)e.n_surf * kEvalWarps;
+    if (sl && dl) eval_leaf_kernel<KIND, true, true><<<grid, kEvalThreads, smem, st>>>(e);
+    else if (sl) eval_leaf_kernel<KIND, true, false><<<grid, kEvalThreads, smem, st>>>(e);
+    else eval_leaf_kernel<KIND, false, true><<<grid, kEvalThreads, smem, st>>>(e);
 }
 
 }  // namespace
@@ -1025,24 +1042,20 @@ static kfmm_status make_eval_items(kfmm_ctx *ctx, FmmPlans &P, float cost)
     // far items follow the near ones in the same buffer
     KF_CUDA(P.eval_cnt.ensure(sizeof(int) * (size_t)(nparts * nl + 1)));
     int *cnt = P.eval_cnt.as<int>();
-    auto items_kernel = [&](bool emit, int k) {
-        const int part = P.eval_split ? k + 1 : 0;
-        int *c = cnt + (size_t)k * nl;
+    auto items_kernel = [&](bool emit) {
         if (emit)
             eval_items_kernel<true><<<grid_for((int64_t)nl * 32, 128, 1 << 30), 128, 0, st>>>(
                 nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(),
-                T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost, part,
-                c, nullptr, P.eval_items.as<int4>());
+                T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost,
+                nparts == 2, cnt, nullptr, P.eval_items.as<int4>());
         else
             eval_items_kernel<false><<<grid_for((int64_t)nl * 32, 128, 1 << 30), 128, 0, st>>>(
                 nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(),
-                T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost, part,
-                nullptr, c, nullptr);
+                T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost,
+                nparts == 2, nullptr, cnt, nullptr);
     };
-    for (int k = 0; k < nparts; ++k) {
-        items_kernel(false, k);
-        KF_LAUNCH();
-    }
+    items_kernel(false);
+    KF_LAUNCH();
     KF_TRY(scan_exclusive(ctx, cnt, cnt, nparts * nl, cnt + (size_t)nparts * nl));
     int h[2] = {0, 0};
     KF_CUDA(cudaMemcpyAsync(&h[0], cnt + nl, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1051,10 +1064,8 @@ static kfmm_status make_eval_items(kfmm_ctx *ctx, FmmPlans &P, float cost)
     P.n_eval_items = h[0];
     P.n_eval_far = nparts == 2 ? h[1] - h[0] : 0;
     KF_CUDA(P.eval_items.ensure(sizeof(int4) * (size_t)std::max(1, P.n_eval_items + P.n_eval_far)));
-    for (int k = 0; k < nparts; ++k) {
-        items_kernel(true, k);
-        KF_LAUNCH();
-    }
+    items_kernel(true);
+    KF_LAUNCH();
     return KFMM_OK;
 }
 

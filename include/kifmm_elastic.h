@@ -93,6 +93,9 @@ typedef struct kfmm_options {
     int streams;        /* 1: the parts of an evaluation that need no multipole data (P2L and
                            the leaf-to-leaf P2P) run on a second stream, concurrently with the
                            upward pass and M2L; not while profiling (1)                      */
+    int eval_item_cost; /* cap of one leaf-evaluation work item, in warp pair-steps; > 0 fixes
+                           it (and leaves it out of the tuning), 0 takes 1024 or the tuned
+                           value (0)                                                         */
 } kfmm_options;
 
 /* Tree and work counts of the last kfmm_build (for tests and roofline accounting). */
@@ -142,6 +145,16 @@ kfmm_status kfmm_set_stream(kfmm_ctx *ctx, void *stream);
  * sorted copies of the points are kept until the next build or destroy. */
 kfmm_status kfmm_build(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm, int64_t nsrc,
                        const float *trg_xyz, int64_t ntrg);
+
+/* One build over n_sets independent point sets (a batch of surfaces of uneven size): set k
+ * owns sources src_off[k] .. src_off[k+1] - 1 and targets trg_off[k] .. trg_off[k+1] - 1 of
+ * the concatenated arrays (offsets: n_sets + 1 host int64 values from 0, every set at least
+ * one source and one target).  Each set gets its own root cube (one level-0 box); no list
+ * crosses sets, so kfmm_eval computes Eq. fmm_summation within every set, all sets in the
+ * same launches.  The set index leads every Morton key, so the depth is capped at
+ * (64 - ceil(log2 n_sets)) / 3 levels.  kfmm_build is the case n_sets = 1. */
+kfmm_status kfmm_build_sets(kfmm_ctx *ctx, int32_t n_sets, const int64_t *src_off, const float *src_xyz,
+                            const float *src_nrm, const int64_t *trg_off, const float *trg_xyz);
 
 /* One FMM evaluation of Eq. fmm_summation on the built tree: sl_den, dl_den [nsrc][3*ncol]
  * (either may be NULL, not both), out [ntrg][3*ncol] (DISP) or [ntrg][6*ncol] (STRESS),

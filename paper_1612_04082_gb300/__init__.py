@@ -39,7 +39,7 @@ class kfmm_options(ctypes.Structure):
                 ("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double), ("pinv_rtol", ctypes.c_double),
                 ("m2l_rtol", ctypes.c_double), ("m2l_rank_max", ctypes.c_int), ("m2l_tensor_cores", ctypes.c_int),
                 ("device", ctypes.c_int), ("graphs", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("streams", ctypes.c_int)]
+                ("streams", ctypes.c_int), ("eval_item_cost", ctypes.c_int)]
 
 
 class kfmm_stats(ctypes.Structure):
@@ -68,6 +68,7 @@ _sig = {
     "kfmm_set_material": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
     "kfmm_set_stream": (ctypes.c_int, [_vp, _vp]),
     "kfmm_build": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64]),
+    "kfmm_build_sets": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
     "kfmm_eval": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]),
     "kfmm_direct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]),
     "kfmm_direct_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_int,
@@ -150,6 +151,16 @@ def kfmm_set_stream(ctx, stream):
 
 def kfmm_build(ctx, src_xyz, src_nrm, trg_xyz):
     _check(ctx, _lib.kfmm_build(ctx, _ptr(src_xyz), _ptr(src_nrm), _nrows(src_xyz), _ptr(trg_xyz), _nrows(trg_xyz)))
+
+
+def kfmm_build_sets(ctx, src_off, src_xyz, src_nrm, trg_off, trg_xyz):
+    """src_off, trg_off: n_sets + 1 offsets (host int64) of the sets in the concatenated points."""
+    so = np.ascontiguousarray(src_off, dtype=np.int64)
+    to = np.ascontiguousarray(trg_off, dtype=np.int64)
+    if so.shape != to.shape or so.ndim != 1 or len(so) < 2:
+        raise ValueError("src_off and trg_off need the same n_sets + 1 entries")
+    _check(ctx, _lib.kfmm_build_sets(ctx, len(so) - 1, so.ctypes.data, _ptr(src_xyz), _ptr(src_nrm),
+                                     to.ctypes.data, _ptr(trg_xyz)))
 
 
 def kfmm_eval(ctx, sl_den, dl_den, out, kind=KFMM_DISP, ncol=1):
@@ -252,6 +263,9 @@ class Kfmm:
 
     def build(self, src_xyz, src_nrm, trg_xyz):
         kfmm_build(self.handle, src_xyz, src_nrm, trg_xyz)
+
+    def build_sets(self, src_off, src_xyz, src_nrm, trg_off, trg_xyz):
+        kfmm_build_sets(self.handle, src_off, src_xyz, src_nrm, trg_off, trg_xyz)
 
     def eval(self, sl_den, dl_den, out, kind=KFMM_DISP, ncol=1):
         return kfmm_eval(self.handle, sl_den, dl_den, out, kind, ncol)

@@ -54,6 +54,7 @@ void kfmm_default_options(kfmm_options *opt)
     opt->graphs = 1;
     opt->autotune = 1;
     opt->streams = 1;
+    opt->eval_item_cost = 0;
 }
 
 kfmm_status kfmm_create(kfmm_ctx **out, const kfmm_options *opt)
@@ -65,7 +66,7 @@ kfmm_status kfmm_create(kfmm_ctx **out, const kfmm_options *opt)
     if (opt) o = *opt;
     if (o.p < 2 || o.p > 8 || o.leaf_cap < 1 || o.max_depth < 1 || o.max_depth > 20 || !(o.r_inner > 1.0) ||
         !(o.r_outer > o.r_inner) || !(o.r_outer < 3.0) || !(o.pinv_rtol > 0.0) || o.m2l_rtol < 0.0 ||
-        o.m2l_rank_max < 0)
+        o.m2l_rank_max < 0 || o.eval_item_cost < 0)
         return KFMM_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
@@ -76,6 +77,10 @@ kfmm_status kfmm_create(kfmm_ctx **out, const kfmm_options *opt)
     kfmm_ctx *c = new (std::nothrow) kfmm_ctx();
     if (!c) return KFMM_ERR_OOM;
     c->opt = o;
+    if (o.eval_item_cost > 0) {
+        c->tune.eval_cost = (float)o.eval_item_cost;
+        c->tune.eval_done = true;  // fixed by the caller
+    }
     if (o.streams) {
         // second stream and fork/join events of the overlapped evaluation (made here, outside
         // any graph capture)
@@ -136,20 +141,37 @@ kfmm_status kfmm_build(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
                        int64_t ntrg)
 {
     if (!ctx) return KFMM_ERR_INVALID_ARG;
+    const int64_t so[2] = {0, nsrc}, to[2] = {0, ntrg};
+    return kfmm_build_sets(ctx, 1, so, src_xyz, src_nrm, to, trg_xyz);
+}
+
+kfmm_status kfmm_build_sets(kfmm_ctx *ctx, int32_t n_sets, const int64_t *src_off, const float *src_xyz,
+                            const float *src_nrm, const int64_t *trg_off, const float *trg_xyz)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
     ctx->err.clear();
-    if (!src_xyz || !trg_xyz || nsrc < 1 || ntrg < 1)
-        return ctx->fail(KFMM_ERR_INVALID_ARG, "build: need nsrc >= 1, ntrg >= 1 and point arrays");
+    if (n_sets < 1 || !src_off || !trg_off || !src_xyz || !trg_xyz)
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "build: need n_sets >= 1, offsets and point arrays");
+    if (src_off[0] != 0 || trg_off[0] != 0)
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "build: set offsets must start at 0");
+    for (int k = 0; k < n_sets; ++k)
+        if (src_off[k + 1] <= src_off[k] || trg_off[k + 1] <= trg_off[k])
+            return ctx->fail(KFMM_ERR_INVALID_ARG, "build: every set needs at least one source and one target");
+    const int64_t nsrc = src_off[n_sets], ntrg = trg_off[n_sets];
     if (cudaSetDevice(ctx->opt.device) != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, "cudaSetDevice");
     DevBuf a, b, c;
     const void *ds, *dn, *dt;
     KF_TRY(to_device(ctx, a, src_xyz, sizeof(float) * 3 * nsrc, &ds));
     KF_TRY(to_device(ctx, b, src_nrm, sizeof(float) * 3 * nsrc, &dn));
-    if (trg_xyz == src_xyz && ntrg == nsrc) dt = ds;  // targets are the sources: one copy, one sort
+    bool same = trg_xyz == src_xyz;
+    for (int k = 0; k <= n_sets && same; ++k) same = src_off[k] == trg_off[k];
+    if (same) dt = ds;  // targets are the sources: one copy, one sort
     else KF_TRY(to_device(ctx, c, trg_xyz, sizeof(float) * 3 * ntrg, &dt));
     ctx->plans.valid = false;
     ctx->graph.reset();
     ctx->phase(KFMM_PH_TREE);
-    kfmm_status s = build_tree(ctx, (const float *)ds, (const float *)dn, nsrc, (const float *)dt, ntrg);
+    kfmm_status s = build_forest(ctx, n_sets, src_off, (const float *)ds, (const float *)dn, trg_off,
+                                 (const float *)dt);
     ctx->phase(-1);
     cudaStreamSynchronize(ctx->stream);
     return s;

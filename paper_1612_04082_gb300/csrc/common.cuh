@@ -129,8 +129,11 @@ struct Tree {
     bool built = false;
     int64_t nsrc = 0, ntrg = 0;
     int max_depth = 0;
-    double root_lo[3] = {0, 0, 0};  // lower corner of the root cube
+    double root_lo[3] = {0, 0, 0};  // lower corner of the root cube (of the first set)
     double root_w = 1;              // root cube side
+    int n_sets = 1;                 // independent point sets, one root box each (level 0)
+    std::vector<double> set_roots;  // host: 8 per set: lower corner x, y, z, side, 1 / side
+    DevBuf set_root_dev;            // the same on the device
     int n_boxes = 0, n_leaves = 0, n_levels = 0;
     std::vector<int> level_off;  // host: first box of each level, size n_levels + 1
     bool has_nrm = false;
@@ -192,7 +195,7 @@ struct Work {
     DevBuf up_phi;    // float [n_boxes][3n]   upward equivalent densities (W-list boxes)
     DevBuf dn_phi;    // float [n_boxes][3n]   downward equivalent densities (leaves)
     DevBuf scan_tmp[4];  // per-level partial sums of the device scan
-    DevBuf tree_tmp[15]; // tree-build temporaries (sort ping-pong, histograms, child ranges...)
+    DevBuf tree_tmp[16]; // tree-build temporaries (sort ping-pong, histograms, child ranges...)
     DevBuf stage_in[4];  // staging of host inputs
     DevBuf stage_out;
     DevBuf tmp;
@@ -373,6 +376,9 @@ namespace kfmm {
 // tree.cu
 kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm, int64_t nsrc,
                        const float *trg_xyz, int64_t ntrg);
+// independent point sets (offsets [n_sets + 1] on the host, points concatenated on the device)
+kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, const float *src_xyz,
+                         const float *src_nrm, const int64_t *trg_off, const float *trg_xyz);
 kfmm_status tree_work_counts(kfmm_ctx *ctx);  // interaction counts for the statistics
 // precompute.cpp (host, FP64) + upload
 kfmm_status ensure_operators(kfmm_ctx *ctx);

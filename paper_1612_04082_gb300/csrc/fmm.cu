@@ -265,15 +265,18 @@ __global__ void pack_sources_kernel(int64_t ns, const float4 *__restrict__ xyz, 
     }
 }
 
-__global__ void box_geom_kernel(int nb, const int4 *__restrict__ anchor, double lo0, double lo1, double lo2,
-                                double w, float4 *__restrict__ geom)
+// centre and half-width of every box, in the root cube of its point set (the set index leads
+// the box key; roots: 8 doubles per set, lower corner x, y, z, side, ...)
+__global__ void box_geom_kernel(int nb, const int4 *__restrict__ anchor, const uint64_t *__restrict__ key,
+                                const double *__restrict__ roots, float4 *__restrict__ geom)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     const int4 a = anchor[b];
-    const double s = w / (double)(1 << a.w);
-    geom[b] = make_float4((float)(lo0 + (a.x + 0.5) * s), (float)(lo1 + (a.y + 0.5) * s),
-                          (float)(lo2 + (a.z + 0.5) * s), (float)(0.5 * s));
+    const double *r = roots + 8 * (key[b] >> (3 * a.w));
+    const double s = r[3] / (double)(1 << a.w);
+    geom[b] = make_float4((float)(r[0] + (a.x + 0.5) * s), (float)(r[1] + (a.y + 0.5) * s),
+                          (float)(r[2] + (a.z + 0.5) * s), (float)(0.5 * s));
 }
 
 // ------------------------------------------------------------------------------------
@@ -1103,7 +1106,7 @@ static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
     }
     KF_CUDA(P.geom.ensure(sizeof(float4) * T.n_boxes));
     box_geom_kernel<<<grid_for(T.n_boxes, 256, 1 << 30), 256, 0, st>>>(
-        T.n_boxes, T.box_anchor.as<int4>(), T.root_lo[0], T.root_lo[1], T.root_lo[2], T.root_w,
+        T.n_boxes, T.box_anchor.as<int4>(), T.box_key.as<uint64_t>(), T.set_root_dev.as<double>(),
         P.geom.as<float4>());
     KF_LAUNCH();
     return KFMM_OK;

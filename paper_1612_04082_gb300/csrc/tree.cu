@@ -138,14 +138,19 @@ namespace {
 constexpr int kBBoxBlocks = 2 * kNumSMs;
 constexpr int kBBoxThreads = 256;
 
-__global__ void bbox_kernel(const float *__restrict__ a, int64_t na, const float *__restrict__ b,
-                            int64_t nb, const float *__restrict__ nrm, float *__restrict__ part)
+// Per point set (blockIdx.y) and partial block (blockIdx.x): bounds of the set's sources and
+// targets, and a count of non-finite coordinates or normals.
+__global__ void bbox_kernel(const int64_t *__restrict__ soff, const float *__restrict__ a,
+                            const int64_t *__restrict__ toff, const float *__restrict__ b,
+                            const float *__restrict__ nrm, float *__restrict__ part)
 {
+    const int set = blockIdx.y;
+    const int64_t a0 = soff[set], na = soff[set + 1] - a0, b0 = toff[set], nb = toff[set + 1] - b0;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     float bad = 0.f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += stride) {
-        const float *p = i < na ? a + 3 * i : b + 3 * (i - na);
+        const float *p = i < na ? a + 3 * (a0 + i) : b + 3 * (b0 + i - na);
         for (int c = 0; c < 3; ++c) {
             float v = p[c];
             if (!isfinite(v)) bad += 1.f;
@@ -154,7 +159,7 @@ __global__ void bbox_kernel(const float *__restrict__ a, int64_t na, const float
         }
         if (nrm && i < na)
             for (int c = 0; c < 3; ++c)
-                if (!isfinite(nrm[3 * i + c])) bad += 1.f;
+                if (!isfinite(nrm[3 * (a0 + i) + c])) bad += 1.f;
     }
     for (int o = 16; o > 0; o >>= 1)
         for (int c = 0; c < 3; ++c) {
@@ -182,7 +187,7 @@ __global__ void bbox_kernel(const float *__restrict__ a, int64_t na, const float
             }
             r[6] += sh[w][6];
         }
-        for (int c = 0; c < 7; ++c) part[7 * blockIdx.x + c] = r[c];
+        for (int c = 0; c < 7; ++c) part[7 * ((size_t)set * gridDim.x + blockIdx.x) + c] = r[c];
     }
 }
 
@@ -206,26 +211,31 @@ __device__ __forceinline__ uint64_t morton3(uint32_t ix, uint32_t iy, uint32_t i
     return (spread3(ix) << 2) | (spread3(iy) << 1) | spread3(iz);
 }
 
-struct RootCube {
-    double lo[3];
-    double inv_w;
-    int L;
-};
-
-__global__ void keys_kernel(const float *__restrict__ xyz, int64_t n, RootCube rc,
-                            uint64_t *__restrict__ key, int *__restrict__ idx)
+// Keys of the points of several sets: point i belongs to the last set s with off[s] <= i;
+// its key is s followed by the 3L-bit Morton code of its cell in the set's root cube
+// (roots: 8 doubles per set, lower corner x, y, z, side, 1 / side).
+__global__ void keys_kernel(const float *__restrict__ xyz, int64_t n, const int64_t *__restrict__ off, int n_sets,
+                            const double *__restrict__ roots, int L, uint64_t *__restrict__ key,
+                            int *__restrict__ idx)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const double scale = (double)(1u << rc.L);
-    const int top = (1 << rc.L) - 1;
+    const double scale = (double)(1u << L);
+    const int top = (1 << L) - 1;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int lo = 0, hi = n_sets - 1;
+        while (lo < hi) {
+            const int m = (lo + hi + 1) >> 1;
+            if (off[m] <= i) lo = m;
+            else hi = m - 1;
+        }
+        const double *r = roots + 8 * lo;
         int q[3];
         for (int c = 0; c < 3; ++c) {
-            double t = ((double)xyz[3 * i + c] - rc.lo[c]) * rc.inv_w * scale;
+            double t = ((double)xyz[3 * i + c] - r[c]) * r[4] * scale;
             int v = (int)floor(t);
             q[c] = v < 0 ? 0 : (v > top ? top : v);
         }
-        key[i] = morton3(q[0], q[1], q[2]);
+        key[i] = ((uint64_t)lo << (3 * L)) | morton3(q[0], q[1], q[2]);
         idx[i] = (int)i;
     }
 }
@@ -368,7 +378,8 @@ struct SplitState {
 
 struct SplitArgs {
     int L, cap, capb;
-    int nsrc, ntrg;
+    int n_sets;                       // roots: one per point set, box s at level 0
+    const int64_t *soff, *toff;       // [n_sets + 1] sorted source / target ranges of the sets
     const uint64_t *skey, *tkey;  // sorted Morton keys of sources and targets
     uint64_t *bkey;
     int4 *banchor;
@@ -457,17 +468,21 @@ __global__ void __launch_bounds__(kSplitThreads) split_tree_kernel(SplitArgs a)
     const unsigned full = 0xffffffffu;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
     SplitState *st = a.st;
-    if (g == 0 && tid == 0) {
-        a.bkey[0] = 0;
-        a.banchor[0] = make_int4(0, 0, 0, 0);
-        a.bparent[0] = -1;
-        a.bsrc[0] = make_int2(0, a.nsrc);
-        a.btrg[0] = make_int2(0, a.ntrg);
-        a.level_off[0] = 0;
-        a.level_off[1] = 1;
+    if (g == 0) {
+        for (int r = tid; r < a.n_sets; r += kSplitThreads) {
+            a.bkey[r] = (uint64_t)r;  // the set index leads every key of the set
+            a.banchor[r] = make_int4(0, 0, 0, 0);
+            a.bparent[r] = -1;
+            a.bsrc[r] = make_int2((int)a.soff[r], (int)a.soff[r + 1]);
+            a.btrg[r] = make_int2((int)a.toff[r], (int)a.toff[r + 1]);
+        }
+        if (tid == 0) {
+            a.level_off[0] = 0;
+            a.level_off[1] = a.n_sets;
+        }
     }
     if (!grid_barrier(st)) return;
-    int first = 0, nb = 1, n_boxes = 1, level = 0;
+    int first = 0, nb = a.n_sets, n_boxes = a.n_sets, level = 0;
     for (;;) {
         // ---- child ranges and counts of this block's boxes (boxes written by any block at
         //      the previous level: read through L2)
@@ -602,12 +617,13 @@ struct TreeView {
     int n_levels;
 };
 
-__device__ __forceinline__ int find_box(const TreeView &tv, int level, int ix, int iy, int iz)
+// the box of set `set` at (level, ix, iy, iz), or -1
+__device__ __forceinline__ int find_box(const TreeView &tv, int level, uint64_t set, int ix, int iy, int iz)
 {
     const int side = 1 << level;
     if (ix < 0 || iy < 0 || iz < 0 || ix >= side || iy >= side || iz >= side) return -1;
     if (level >= tv.n_levels) return -1;
-    const uint64_t k = morton3(ix, iy, iz);
+    const uint64_t k = (set << (3 * level)) | morton3(ix, iy, iz);
     int lo = tv.level_off[level], hi = tv.level_off[level + 1];
     while (lo < hi) {
         int m = (lo + hi) >> 1;
@@ -623,11 +639,12 @@ __global__ void colleague_kernel(TreeView tv, int *__restrict__ coll)
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= tv.n_boxes) return;
     const int4 a = tv.anchor[b];
+    const uint64_t set = tv.key[b] >> (3 * a.w);  // colleagues come from the box's own set
     int c = 0;
     for (int dx = -1; dx <= 1; ++dx)
         for (int dy = -1; dy <= 1; ++dy)
             for (int dz = -1; dz <= 1; ++dz, ++c)
-                coll[27 * b + c] = (c == 13) ? b : find_box(tv, a.w, a.x + dx, a.y + dy, a.z + dz);
+                coll[27 * b + c] = (c == 13) ? b : find_box(tv, a.w, set, a.x + dx, a.y + dy, a.z + dz);
 }
 
 // Closed boxes at possibly different levels touch or overlap.
@@ -919,60 +936,90 @@ __global__ void work_count_kernel(int n_boxes, const int *__restrict__ leaf, con
 kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm, int64_t nsrc,
                        const float *trg_xyz, int64_t ntrg)
 {
+    const int64_t so[2] = {0, nsrc}, to[2] = {0, ntrg};
+    return build_forest(ctx, 1, so, src_xyz, src_nrm, to, trg_xyz);
+}
+
+kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, const float *src_xyz,
+                         const float *src_nrm, const int64_t *trg_off, const float *trg_xyz)
+{
     Tree &T = ctx->tree;
     T.built = false;
     const cudaStream_t st = ctx->stream;
-    const int L = ctx->opt.max_depth;
     const int cap = ctx->opt.leaf_cap;
+    if (n_sets < 1) return ctx->fail(KFMM_ERR_INVALID_ARG, "need at least one point set");
+    const int64_t nsrc = src_off[n_sets], ntrg = trg_off[n_sets];
     if (nsrc + ntrg > (int64_t)1 << 30) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many points (limit 2^30)");
+    // keys: the set index above 3 L Morton bits, within 64 bits
+    int set_bits = 0;
+    while ((1LL << set_bits) < n_sets) ++set_bits;
+    const int L = std::min(ctx->opt.max_depth, (64 - set_bits) / 3);
+    if (L < 1) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many point sets");
 
-    // ---- bounding cube and NaN check
-    DevBuf *tmp = ctx->work.tree_tmp;  // persistent scratch: slots 0-2 sort, 3-14 below
+    // ---- bounding cube of every set and NaN check
+    DevBuf *tmp = ctx->work.tree_tmp;  // persistent scratch: slots 0-2 sort, 3-15 below
+    DevBuf &set_off = tmp[15], &roots = T.set_root_dev;
+    KF_CUDA(set_off.ensure(sizeof(int64_t) * 2 * (n_sets + 1)));
+    int64_t *d_soff = set_off.as<int64_t>(), *d_toff = d_soff + n_sets + 1;
+    KF_TRY(upload_async(ctx, d_soff, src_off, sizeof(int64_t) * (n_sets + 1)));
+    KF_TRY(upload_async(ctx, d_toff, trg_off, sizeof(int64_t) * (n_sets + 1)));
+    const int bx = std::max(1, kBBoxBlocks / n_sets);
     DevBuf &part = tmp[3];
-    KF_CUDA(part.ensure(sizeof(float) * 7 * kBBoxBlocks));
-    bbox_kernel<<<kBBoxBlocks, kBBoxThreads, 0, st>>>(src_xyz, nsrc, trg_xyz, ntrg, src_nrm,
-                                                      part.as<float>());
+    KF_CUDA(part.ensure(sizeof(float) * 7 * (size_t)bx * n_sets));
+    bbox_kernel<<<dim3(bx, n_sets), kBBoxThreads, 0, st>>>(d_soff, src_xyz, d_toff, trg_xyz, src_nrm,
+                                                           part.as<float>());
     KF_LAUNCH();
-    std::vector<float> hp(7 * kBBoxBlocks);
+    std::vector<float> hp(7 * (size_t)bx * n_sets);
     KF_CUDA(cudaMemcpyAsync(hp.data(), part.p, sizeof(float) * hp.size(), cudaMemcpyDeviceToHost, st));
     KF_TRY(sync_stream(ctx));
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    double bad = 0;
-    for (int b = 0; b < kBBoxBlocks; ++b) {
-        for (int c = 0; c < 3; ++c) {
-            lo[c] = std::min(lo[c], (double)hp[7 * b + c]);
-            hi[c] = std::max(hi[c], (double)hp[7 * b + 3 + c]);
+    std::vector<double> hr(8 * (size_t)n_sets, 0.0);
+    for (int k = 0; k < n_sets; ++k) {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        double bad = 0;
+        for (int b = 0; b < bx; ++b) {
+            const float *q = &hp[7 * ((size_t)k * bx + b)];
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = std::min(lo[c], (double)q[c]);
+                hi[c] = std::max(hi[c], (double)q[3 + c]);
+            }
+            bad += q[6];
         }
-        bad += hp[7 * b + 6];
+        if (bad > 0) return ctx->fail(KFMM_ERR_INVALID_ARG, "non-finite coordinate or normal");
+        double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+        double w = ext > 0 ? ext * (1.0 + 1e-6) : 1.0;
+        for (int c = 0; c < 3; ++c) hr[8 * k + c] = 0.5 * (lo[c] + hi[c]) - 0.5 * w;
+        hr[8 * k + 3] = w;
+        hr[8 * k + 4] = 1.0 / w;
     }
-    if (bad > 0) return ctx->fail(KFMM_ERR_INVALID_ARG, "non-finite coordinate or normal");
-    double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
-    double w = ext > 0 ? ext * (1.0 + 1e-6) : 1.0;
-    for (int c = 0; c < 3; ++c) T.root_lo[c] = 0.5 * (lo[c] + hi[c]) - 0.5 * w;
-    T.root_w = w;
+    KF_CUDA(roots.ensure(sizeof(double) * hr.size()));
+    KF_TRY(upload_async(ctx, roots.p, hr.data(), sizeof(double) * hr.size()));
+    T.set_roots.assign(hr.begin(), hr.end());
+    T.n_sets = n_sets;
+    for (int c = 0; c < 3; ++c) T.root_lo[c] = hr[c];
+    T.root_w = hr[3];
     T.max_depth = L;
     T.nsrc = nsrc;
     T.ntrg = ntrg;
     T.has_nrm = src_nrm != nullptr;
 
     // ---- keys and sort
-    RootCube rc{{T.root_lo[0], T.root_lo[1], T.root_lo[2]}, 1.0 / w, L};
     KF_CUDA(T.src_key.ensure(sizeof(uint64_t) * nsrc));
     KF_CUDA(T.trg_key.ensure(sizeof(uint64_t) * ntrg));
     KF_CUDA(T.src_perm.ensure(sizeof(int) * nsrc));
     KF_CUDA(T.trg_perm.ensure(sizeof(int) * ntrg));
-    keys_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_xyz, nsrc, rc, T.src_key.as<uint64_t>(),
-                                                      T.src_perm.as<int>());
+    keys_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_xyz, nsrc, d_soff, n_sets, roots.as<double>(), L,
+                                                      T.src_key.as<uint64_t>(), T.src_perm.as<int>());
     KF_LAUNCH();
     // targets given as the very array of the sources: one set of keys, one sort, then copies
-    const bool same = trg_xyz == src_xyz && ntrg == nsrc;
+    bool same = trg_xyz == src_xyz;
+    for (int k = 0; k <= n_sets && same; ++k) same = src_off[k] == trg_off[k];
     if (!same) {
-        keys_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, ntrg, rc, T.trg_key.as<uint64_t>(),
-                                                          T.trg_perm.as<int>());
+        keys_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, ntrg, d_toff, n_sets, roots.as<double>(), L,
+                                                          T.trg_key.as<uint64_t>(), T.trg_perm.as<int>());
         KF_LAUNCH();
     }
-    KF_TRY(radix_sort(ctx, T.src_key, T.src_perm, (int)nsrc, 3 * L));
-    if (!same) KF_TRY(radix_sort(ctx, T.trg_key, T.trg_perm, (int)ntrg, 3 * L));
+    KF_TRY(radix_sort(ctx, T.src_key, T.src_perm, (int)nsrc, 3 * L + set_bits));
+    if (!same) KF_TRY(radix_sort(ctx, T.trg_key, T.trg_perm, (int)ntrg, 3 * L + set_bits));
     KF_CUDA(T.src_xyz.ensure(sizeof(float4) * nsrc));
     KF_CUDA(T.trg_xyz.ensure(sizeof(float4) * ntrg));
     gather_points_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_xyz, T.src_perm.as<int>(), nsrc,
@@ -1003,7 +1050,7 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         if (per_sm < 1) return ctx->fail(KFMM_ERR_INTERNAL, "tree split kernel cannot be resident");
         T.split_grid = std::min(per_sm, 2) * n_sm;
     }
-    size_t capb = std::max<size_t>(1024, (size_t)(4 * (nsrc + ntrg) / std::max(1, cap)) + 64);
+    size_t capb = std::max<size_t>(1024, (size_t)(4 * (nsrc + ntrg) / std::max(1, cap)) + 64 + (size_t)n_sets);
     DevBuf &crange = tmp[4], &ccount = tmp[5], &bsum = tmp[6], &sstate = tmp[7], &loff = tmp[9];
     KF_CUDA(bsum.ensure(sizeof(int) * T.split_grid));
     KF_CUDA(sstate.ensure(sizeof(SplitState)));
@@ -1022,7 +1069,7 @@ kfmm_status build_tree(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
         KF_CUDA(crange.ensure(sizeof(int4) * 8 * capb));
         KF_CUDA(ccount.ensure(sizeof(int) * capb));
         KF_CUDA(cudaMemsetAsync(sstate.p, 0, sizeof(SplitState), st));
-        SplitArgs sa{L, cap, (int)capb, (int)nsrc, (int)ntrg, T.src_key.as<uint64_t>(), T.trg_key.as<uint64_t>(),
+        SplitArgs sa{L, cap, (int)capb, n_sets, d_soff, d_toff, T.src_key.as<uint64_t>(), T.trg_key.as<uint64_t>(),
                      T.box_key.as<uint64_t>(), T.box_anchor.as<int4>(), T.box_parent.as<int>(),
                      T.box_child.as<int>(), T.box_src.as<int2>(), T.box_trg.as<int2>(), T.box_leaf.as<int>(),
                      T.leaves.as<int>(), crange.as<int4>(), ccount.as<int>(), bsum.as<int>(), loff.as<int>(),

@@ -404,3 +404,109 @@ def test_overlapped_streams_match_one_stream(K, kind):
     s1, d1 = np.ascontiguousarray(sl[:, 3:6]), np.ascontiguousarray(dl[:, 3:6])
     ref = fn(src[idx], src, nrm, s1, d1, G1, NU1)
     assert rel(res[1][3][idx, no // 2:], ref) < tol
+
+
+@pytest.mark.parametrize("p", [4, 6])
+def test_leaf_items_every_cost_and_split(K, p):
+    """The leaf-evaluation work items cover every (target chunk, source segment) once for every
+    item cost cap, with the near / far lists split (streams 1) or one list (streams 0): the
+    results agree with each other and with the oracle.  Small caps cut many items per chunk
+    (p = 4 puts most W boxes through their upward densities)."""
+    src, nrm = W.box_with_voids_points(20000, n_voids=5)
+    sl, dl = W.densities(len(src))
+    src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
+    x, n, s, d = dev(src), dev(nrm), dev(sl), dev(dl)
+    idx = W.subsample(len(src), 600)
+    ref = O.direct_disp(src[idx], src, nrm, sl, dl, G1, NU1)
+    outs = []
+    for cost in (64, 256, 1024, 4096):
+        for streams in (0, 1):
+            with make_ctx(K, G1, NU1, p=p, streams=streams, eval_item_cost=cost) as c:
+                c.build(x, n, x)
+                out = torch.full((len(src), 3), float("nan"), device="cuda:0")
+                c.eval(s, d, out)
+                assert c.stats()["eval_item_cost"] == float(cost)
+                outs.append(out.cpu().numpy().astype(np.float64))
+    tol = 3e-3 if p == 4 else 1e-4
+    for o in outs:
+        assert np.all(np.isfinite(o))
+        assert rel(o[idx], ref) < tol
+        assert rel(o, outs[0]) < 1e-5
+
+
+def _point_sets(sizes, seed0=11):
+    """Uneven box-with-voids surfaces, each scaled and shifted; sets 0 and 1 overlap in space
+    (no interaction may cross sets even where their points interleave)."""
+    pts, nrm = [], []
+    for k, n in enumerate(sizes):
+        x, nn = W.box_with_voids_points(n, n_voids=3 + k, seed=seed0 + k)
+        scale = 1.0 + 0.5 * k
+        shift = np.array([0.0, 0.0, 0.0]) if k < 2 else np.array([3.0 * k, -1.0 * k, 0.5])
+        pts.append(x * scale + shift)
+        nrm.append(nn)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return np.concatenate(pts), np.concatenate(nrm), off
+
+
+@pytest.mark.parametrize("kind", ["disp", "stress"])
+def test_point_sets_one_build(K, kind):
+    """kfmm_build_sets: several independent surfaces of uneven size in one tree and one set of
+    launches.  Each set's result equals its own build (the per-set trees are the same) and
+    the oracle restricted to the set."""
+    sizes = [6000, 2500, 700, 9000]
+    src, nrm, off = _point_sets(sizes)
+    ncol = 2
+    sl, dl = W.densities(len(src), ncol=ncol)
+    src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
+    kd = K.KFMM_DISP if kind == "disp" else K.KFMM_STRESS
+    no = (3 if kind == "disp" else 6) * ncol
+    cfg = {} if kind == "disp" else dict(p=8, m2l_rtol=1e-7)
+    with make_ctx(K, G1, NU1, **cfg) as c:
+        c.build_sets(off, dev(src), dev(nrm), off, dev(src))
+        st = c.stats()
+        out = torch.full((len(src), no), float("nan"), device="cuda:0")
+        c.eval(dev(sl), dev(dl), out, kind=kd, ncol=ncol)
+        batched = out.cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(batched))
+        nb_sum = 0
+        for k in range(len(sizes)):
+            a, b = off[k], off[k + 1]
+            c.build(dev(src[a:b]), dev(nrm[a:b]), dev(src[a:b]))
+            nb_sum += c.stats()["n_boxes"]
+            one = torch.zeros(b - a, no, device="cuda:0")
+            c.eval(dev(sl[a:b]), dev(dl[a:b]), one, kind=kd, ncol=ncol)
+            assert rel(batched[a:b], one.cpu().numpy().astype(np.float64)) < 2e-6
+        assert st["n_boxes"] == nb_sum  # the forest is the union of the per-set trees
+    fn = O.direct_disp if kind == "disp" else O.direct_stress
+    tol = 1e-4 if kind == "disp" else 5e-4
+    for k in (0, 1, 3):
+        a, b = off[k], off[k + 1]
+        idx = a + W.subsample(b - a, 150)
+        s1, d1 = np.ascontiguousarray(sl[a:b, 3:6]), np.ascontiguousarray(dl[a:b, 3:6])
+        ref = fn(src[idx], src[a:b], nrm[a:b], s1, d1, G1, NU1)
+        assert rel(batched[idx, no // 2:], ref) < tol
+
+
+def test_point_sets_separate_targets_and_errors(K):
+    """Sets with their own target points; bad offsets are refused."""
+    sizes = [3000, 5000, 1200]
+    src, nrm, off = _point_sets(sizes, seed0=21)
+    trg_sizes = [400, 900, 300]
+    trg = np.concatenate([src[off[k]:off[k + 1]][W.subsample(sizes[k], trg_sizes[k])] * 0.97 + 0.01
+                          for k in range(3)])
+    toff = np.concatenate([[0], np.cumsum(trg_sizes)]).astype(np.int64)
+    sl, dl = W.densities(len(src))
+    src, nrm, trg, sl, dl = r32(src), r32(nrm), r32(trg), r32(sl), r32(dl)
+    with make_ctx(K, G1, NU1) as c:
+        c.build_sets(off, dev(src), dev(nrm), toff, dev(trg))
+        out = torch.zeros(len(trg), 3, device="cuda:0")
+        c.eval(dev(sl), dev(dl), out)
+        got = out.cpu().numpy().astype(np.float64)
+        for k in range(3):
+            ref = O.direct_disp(trg[toff[k]:toff[k + 1]], src[off[k]:off[k + 1]], nrm[off[k]:off[k + 1]],
+                                sl[off[k]:off[k + 1]], dl[off[k]:off[k + 1]], G1, NU1)
+            assert rel(got[toff[k]:toff[k + 1]], ref) < 1e-4
+        bad = off.copy()
+        bad[2] = bad[1]  # an empty set
+        with pytest.raises(K.KfmmError):
+            c.build_sets(bad, dev(src), dev(nrm), toff, dev(trg))

@@ -213,6 +213,58 @@ def bem_leg(K, local, world):
     return out
 
 
+def batch_leg(K, local, world, flush, steps=5, warmup=2):
+    """32 independent box-with-voids surfaces of uneven size (5k-250k points each, log-uniform)
+    in one tree and one set of launches (kfmm_build_sets + one SL+DL evaluation), against the
+    same surfaces built and evaluated one by one on the same context."""
+    import torch
+    import workloads as W
+    dev = torch.device("cuda", local)
+    pts, nrm, off = W.surface_batch()
+    sl, dl = W.densities(len(pts))
+    x = torch.tensor(pts, dtype=torch.float32, device=dev)
+    nn = torch.tensor(nrm, dtype=torch.float32, device=dev)
+    s = torch.tensor(sl, dtype=torch.float32, device=dev)
+    d = torch.tensor(dl, dtype=torch.float32, device=dev)
+    out = torch.empty(len(pts), 3, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    n_sets = len(off) - 1
+    f = K.Kfmm(p=6, leaf_cap=64, device=local)
+    f.set_material(K.material_K(1.0, 0.3), 1.0)
+    f.set_stream(stream)
+
+    def batched():
+        f.build_sets(off, x, nn, off, x)
+        f.eval(s, d, out)
+
+    def one_by_one():
+        for k in range(n_sets):
+            a, b = int(off[k]), int(off[k + 1])
+            f.build(x[a:b], nn[a:b], x[a:b])
+            f.eval(s[a:b], d[a:b], out[a:b])
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world, dev)
+
+    ms_b = timed(batched)
+    ms_s = timed(one_by_one)
+    f.close()
+    return {"workload": f"{n_sets} box-with-voids surfaces, {int(np.diff(off).min())}-"
+                        f"{int(np.diff(off).max())} points each, {len(pts)} in all; tree build + one SL+DL "
+                        "evaluation per step, p=6",
+            "ms_per_step": ms_b, "targets_per_s": aggregate_rate(len(pts), world, ms_b / 1e3),
+            "one_by_one_ms_per_step": ms_s, "speedup_vs_one_by_one": ms_s / ms_b}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -224,6 +276,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bem", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -372,6 +425,7 @@ def main():
 
     # ---- BEM leg: mixed-precision refinement vs plain FP64 GMRES at a 1e-6 FP64 residual
     bem = bem_leg(K, local, world) if not args.no_bem else None
+    batch = batch_leg(K, local, world, flush) if not args.no_batch else None
 
     line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -393,6 +447,7 @@ def main():
                            "overlapped with the upward pass and M2L",
             "kernels": kernels,
             "bem": bem,
+            "batch": batch,
             "tree": {k: st[k] for k in ("n_boxes", "n_leaves", "n_levels", "m2l_rank", "n_v_pairs",
                                         "n_w_pairs", "n_x_pairs", "p2p_interactions")}}
 

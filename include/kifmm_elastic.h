@@ -223,7 +223,8 @@ typedef enum kfmm_phase {
     KFMM_PH_M2L_BASIS = 9, /* upward densities into the shared M2L basis (compression)       */
     KFMM_PH_TREE_SPLIT = 10, /* kfmm_build: boxes level by level, leaves, colleagues         */
     KFMM_PH_TREE_LISTS = 11, /* kfmm_build: U, V, W, X lists, V directions, box groups       */
-    KFMM_N_PHASES = 12
+    KFMM_PH_PLANS = 12,   /* first evaluation on a new tree: the host part of its work plans  */
+    KFMM_N_PHASES = 13
 } kfmm_phase;
 
 /* Turn per-phase timing on or off (off by default).  Timing adds two event records per

@@ -213,7 +213,7 @@ def kfmm_export_list(ctx, which: str):
 
 
 PHASES = ("tree", "pack", "s2m", "up_pinv", "m2m", "m2l", "p2l", "down", "eval", "m2l_basis", "tree_split",
-          "tree_lists")
+          "tree_lists", "plans")
 
 
 def kfmm_set_profiling(ctx, enable: bool):

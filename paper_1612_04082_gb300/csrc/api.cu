@@ -85,7 +85,7 @@ kfmm_status kfmm_create(kfmm_ctx **out, const kfmm_options *opt)
         // second stream and fork/join events of the overlapped evaluation (made here, outside
         // any graph capture)
         bool ok = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
-        for (cudaEvent_t *ev : {&c->ev_fork, &c->ev_p2l, &c->ev_near})
+        for (cudaEvent_t *ev : {&c->ev_fork, &c->ev_p2l, &c->ev_near, &c->ev_plans})
             ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
@@ -108,7 +108,7 @@ kfmm_status kfmm_destroy(kfmm_ctx *ctx)
         cudaStreamSynchronize(ctx->side);
         cudaStreamDestroy(ctx->side);
     }
-    for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_p2l, ctx->ev_near})
+    for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_p2l, ctx->ev_near, ctx->ev_plans, ctx->plans.ev_items})
         if (e) cudaEventDestroy(e);
     delete ctx;
     return KFMM_OK;

@@ -277,6 +277,10 @@ struct FmmPlans {
     DevBuf eval_cnt;                // int per leaf and list: items, then their offsets
     int n_eval_items = 0, n_eval_far = 0;
     bool eval_split = false;
+    // item totals of a new tree, copied asynchronously to pinned memory (event ev_items)
+    bool items_pending = false;
+    int *items_host = nullptr;
+    cudaEvent_t ev_items = nullptr;
 };
 
 // Per-phase CUDA-event timing (off unless enabled).
@@ -339,7 +343,7 @@ struct kfmm_ctx {
     kfmm::Staging staging;  // pinned host side of the in-order table uploads
     // second stream of the overlapped evaluation and its fork/join events (made on first use)
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_p2l = nullptr, ev_near = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_p2l = nullptr, ev_near = nullptr, ev_plans = nullptr;
     double G = 1.0, nu = 0.3;
     std::string err;
     kfmm::Operators ops;

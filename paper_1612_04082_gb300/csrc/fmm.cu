@@ -1033,6 +1033,49 @@ static void make_m2l_host(kfmm_ctx *ctx, FmmPlans &P, int chunk)
 }
 
 // work items of the leaf evaluation for a cost cap
+// the leaf-item kernels: per-leaf counts ([list][leaf]) or the items at their offsets
+static void eval_items_launch(kfmm_ctx *ctx, FmmPlans &P, float cost, bool emit)
+{
+    const Tree &T = ctx->tree;
+    const int nl = T.n_leaves;
+    int *cnt = P.eval_cnt.as<int>();
+    const dim3 grid(grid_for((int64_t)nl * 32, 128, 1 << 30));
+    if (emit)
+        eval_items_kernel<true><<<grid, 128, 0, ctx->stream>>>(
+            nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
+            T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, surface_points(ctx->opt.p), cost, P.eval_split,
+            cnt, nullptr, P.eval_items.as<int4>());
+    else
+        eval_items_kernel<false><<<grid, 128, 0, ctx->stream>>>(
+            nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
+            T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, surface_points(ctx->opt.p), cost, P.eval_split,
+            nullptr, cnt, nullptr);
+}
+
+// counts of all lists side by side ([part][leaf]) and one scan: with a split the far items
+// follow the near ones in the same buffer; the totals are at [nl] and [2 nl]
+static kfmm_status eval_items_count(kfmm_ctx *ctx, FmmPlans &P, float cost)
+{
+    const int nl = ctx->tree.n_leaves, nparts = P.eval_split ? 2 : 1;
+    KF_CUDA(P.eval_cnt.ensure(sizeof(int) * (size_t)(nparts * nl + 1)));
+    int *cnt = P.eval_cnt.as<int>();
+    eval_items_launch(ctx, P, cost, false);
+    KF_LAUNCH();
+    KF_TRY(scan_exclusive(ctx, cnt, cnt, nparts * nl, cnt + (size_t)nparts * nl));
+    return KFMM_OK;
+}
+
+static kfmm_status eval_items_emit(kfmm_ctx *ctx, FmmPlans &P, float cost, int n_near, int n_far)
+{
+    P.n_eval_items = n_near;
+    P.n_eval_far = n_far;
+    KF_CUDA(P.eval_items.ensure(sizeof(int4) * (size_t)std::max(1, n_near + n_far)));
+    eval_items_launch(ctx, P, cost, true);
+    KF_LAUNCH();
+    return KFMM_OK;
+}
+
+// all of it, synchronously (the launch-shape tuning)
 static kfmm_status make_eval_items(kfmm_ctx *ctx, FmmPlans &P, float cost)
 {
     const Tree &T = ctx->tree;
@@ -1040,42 +1083,54 @@ static kfmm_status make_eval_items(kfmm_ctx *ctx, FmmPlans &P, float cost)
     P.n_eval_items = P.n_eval_far = 0;
     P.eval_split = ctx->opt.streams != 0;
     if (!T.n_leaves) return KFMM_OK;
-    const int nl = T.n_leaves, nparts = P.eval_split ? 2 : 1;
-    // counts of all lists side by side ([part][leaf]), one scan, one read: with a split the
-    // far items follow the near ones in the same buffer
-    KF_CUDA(P.eval_cnt.ensure(sizeof(int) * (size_t)(nparts * nl + 1)));
-    int *cnt = P.eval_cnt.as<int>();
-    auto items_kernel = [&](bool emit) {
-        if (emit)
-            eval_items_kernel<true><<<grid_for((int64_t)nl * 32, 128, 1 << 30), 128, 0, st>>>(
-                nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(),
-                T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost,
-                nparts == 2, cnt, nullptr, P.eval_items.as<int4>());
-        else
-            eval_items_kernel<false><<<grid_for((int64_t)nl * 32, 128, 1 << 30), 128, 0, st>>>(
-                nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(),
-                T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, ctx->ops.n_surf, cost,
-                nparts == 2, nullptr, cnt, nullptr);
-    };
-    items_kernel(false);
-    KF_LAUNCH();
-    KF_TRY(scan_exclusive(ctx, cnt, cnt, nparts * nl, cnt + (size_t)nparts * nl));
+    const int nl = T.n_leaves;
+    KF_TRY(eval_items_count(ctx, P, cost));
+    const int *cnt = P.eval_cnt.as<int>();
     int h[2] = {0, 0};
     KF_CUDA(cudaMemcpyAsync(&h[0], cnt + nl, sizeof(int), cudaMemcpyDeviceToHost, st));
-    if (nparts == 2) KF_CUDA(cudaMemcpyAsync(&h[1], cnt + 2 * (size_t)nl, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (P.eval_split) KF_CUDA(cudaMemcpyAsync(&h[1], cnt + 2 * (size_t)nl, sizeof(int), cudaMemcpyDeviceToHost, st));
     KF_TRY(sync_stream(ctx));
-    P.n_eval_items = h[0];
-    P.n_eval_far = nparts == 2 ? h[1] - h[0] : 0;
-    KF_CUDA(P.eval_items.ensure(sizeof(int4) * (size_t)std::max(1, P.n_eval_items + P.n_eval_far)));
-    items_kernel(true);
-    KF_LAUNCH();
-    return KFMM_OK;
+    return eval_items_emit(ctx, P, cost, h[0], P.eval_split ? h[1] - h[0] : 0);
 }
 
-static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
+// Plans of a new tree, in two parts so that the host work overlaps the first kernels of the
+// evaluation.  plans_begin enqueues the device part: box geometry, the leaf-item counts with
+// their scan, and an asynchronous copy of the list totals to pinned memory (event ev_items).
+static kfmm_status plans_begin(kfmm_ctx *ctx, FmmPlans &P)
 {
     Tree &T = ctx->tree;
     const cudaStream_t st = ctx->stream;
+    KF_CUDA(P.err.ensure(sizeof(int)));
+    KF_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), st));
+    KF_CUDA(P.geom.ensure(sizeof(float4) * T.n_boxes));
+    box_geom_kernel<<<grid_for(T.n_boxes, 256, 1 << 30), 256, 0, st>>>(
+        T.n_boxes, T.box_anchor.as<int4>(), T.box_key.as<uint64_t>(), T.set_root_dev.as<double>(),
+        P.geom.as<float4>());
+    KF_LAUNCH();
+    P.n_eval_items = P.n_eval_far = 0;
+    P.eval_split = ctx->opt.streams != 0;
+    P.items_pending = false;
+    if (!T.n_leaves) return KFMM_OK;
+    KF_TRY(eval_items_count(ctx, P, ctx->tune.eval_cost));
+    P.items_host = static_cast<int *>(ctx->staging.take(2 * sizeof(int)));
+    if (!P.items_host) return ctx->fail(KFMM_ERR_OOM, "pinned staging for the item totals");
+    const int nl = T.n_leaves, nparts = P.eval_split ? 2 : 1;
+    const int *cnt = P.eval_cnt.as<int>();
+    P.items_host[1] = 0;
+    KF_CUDA(cudaMemcpyAsync(P.items_host, cnt + nl, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (nparts == 2)
+        KF_CUDA(cudaMemcpyAsync(P.items_host + 1, cnt + 2 * (size_t)nl, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (!P.ev_items) KF_CUDA(cudaEventCreateWithFlags(&P.ev_items, cudaEventDisableTiming));
+    KF_CUDA(cudaEventRecord(P.ev_items, st));
+    P.items_pending = true;
+    return KFMM_OK;
+}
+
+// plans_end: the host part (tile tables of the box products, M2L work items), then the leaf
+// items once their totals have arrived.
+static kfmm_status plans_end(kfmm_ctx *ctx, FmmPlans &P)
+{
+    Tree &T = ctx->tree;
     KF_TRY(make_plan(ctx, P.all, {0}, {0}, {T.n_boxes}));
     KF_TRY(make_plan(ctx, P.leaves, {0}, {0}, {T.n_leaves}));
     KF_TRY(make_plan(ctx, P.xboxes, {0}, {0}, {T.n_xboxes}));
@@ -1090,9 +1145,6 @@ static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
         KF_TRY(make_plan(ctx, P.m2l, gm, gb, ge));
         make_m2l_host(ctx, P, ctx->tune.m2l_chunk);
     }
-    KF_CUDA(P.err.ensure(sizeof(int)));
-    KF_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int), st));
-    KF_TRY(make_eval_items(ctx, P, ctx->tune.eval_cost));
     P.oct_lvl.clear();
     P.oct_lvl.resize(T.n_levels);
     for (int l = 1; l < T.n_levels; ++l) {
@@ -1104,11 +1156,12 @@ static kfmm_status build_plans(kfmm_ctx *ctx, FmmPlans &P)
         }
         KF_TRY(make_plan(ctx, P.oct_lvl[l], gm, gb, ge));
     }
-    KF_CUDA(P.geom.ensure(sizeof(float4) * T.n_boxes));
-    box_geom_kernel<<<grid_for(T.n_boxes, 256, 1 << 30), 256, 0, st>>>(
-        T.n_boxes, T.box_anchor.as<int4>(), T.box_key.as<uint64_t>(), T.set_root_dev.as<double>(),
-        P.geom.as<float4>());
-    KF_LAUNCH();
+    if (P.items_pending) {
+        KF_CUDA(cudaEventSynchronize(P.ev_items));
+        P.items_pending = false;
+        const int h0 = P.items_host[0], h1 = P.items_host[1];
+        KF_TRY(eval_items_emit(ctx, P, ctx->tune.eval_cost, h0, P.eval_split ? h1 - h0 : 0));
+    }
     return KFMM_OK;
 }
 
@@ -1179,10 +1232,10 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     const int ku = O.ku, kd = O.kd, kup = round_up(ku, 16), kdp = round_up(kd, 16);
     const int nb = T.n_boxes;
     const int64_t ns = T.nsrc;
-    if (!P.valid) {
-        KF_TRY(build_plans(ctx, P));
-        P.valid = true;
-    }
+    // a new tree: its plans are made during this evaluation, the host part overlapping S2M and
+    // P2L (plans_begin / plans_end)
+    const bool new_tree = !P.valid;
+    if (new_tree) KF_TRY(plans_begin(ctx, P));
     {
         // box vectors of all density columns ([column][box][ld]).  The GEMM K loops read their
         // padding lanes, which no kernel writes: a buffer is zeroed in full when it is
@@ -1217,7 +1270,6 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
         P.m2l_ncol = ncol;
         return KFMM_OK;
     };
-    if (O.m2l_tc_mtiles > 0 && P.m2l_ncol != ncol) KF_TRY(upload_m2l_items());
     KF_CUDA(W.src_rec.ensure(sizeof(SrcRec) * ns * ncol));
     if (kind == KFMM_STRESS) KF_CUDA(W.tmp.ensure(sizeof(SrcRec) * ns * ncol));
     // one box-operator product over all density columns: tensor cores (three-term split) or
@@ -1299,23 +1351,6 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
         if (kind == KFMM_DISP) launch_eval<KFMM_DISP>(a, a.n_items, ncol, sl != nullptr, dl != nullptr, s);
         else launch_eval<KFMM_STRESS>(a, a.n_items, ncol, sl != nullptr, dl != nullptr, s);
     };
-    if (ctx->opt.autotune && !ctx->tune.eval_done && T.n_leaves) {
-        // cost cap of the leaf-evaluation items: time each candidate on this tree (the values
-        // of the equivalent densities do not change the work; the output is zeroed below)
-        float best = 1e30f, best_cost = ctx->tune.eval_cost;
-        for (float cost : {256.f, 512.f, 1024.f, 2048.f, 4096.f}) {
-            KF_TRY(make_eval_items(ctx, P, cost));
-            float ms = 0.f;
-            KF_TRY(time_launch(ctx, [&]() {
-                eval_part(1, st);
-                if (P.eval_split) eval_part(2, st);
-            }, &ms));
-            if (ms < best) best = ms, best_cost = cost;
-        }
-        ctx->tune.eval_cost = best_cost;
-        ctx->tune.eval_done = true;
-        KF_TRY(make_eval_items(ctx, P, best_cost));
-    }
     // The near field (P2L into the downward check surfaces; the leaf-to-leaf P2P into the
     // zeroed output) needs no multipole data.  With streams on it runs on the side stream,
     // concurrently with the upward pass and M2L, and joins the context stream before the
@@ -1335,6 +1370,42 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
         KF_LAUNCH();
     }
     if (overlap) KF_CUDA(cudaEventRecord(ctx->ev_p2l, s2));
+    // ---- S2M: sources -> upward check surface of each leaf
+    ctx->phase(KFMM_PH_S2M);
+    KF_CUDA(cudaMemsetAsync(W.alpha.p, 0, sizeof(float) * (size_t)nb * kup * ncol, st));
+    if (T.n_leaves) {
+        check_pot(T.leaves.as<int>(), T.n_leaves, 0, (float)O.r_outer, W.up_chk.as<float>(), st);
+        KF_LAUNCH();
+    }
+    if (new_tree) {
+        // host part of the plans while the GPU runs S2M and P2L; then the leaf items
+        ctx->phase(KFMM_PH_PLANS);
+        KF_TRY(plans_end(ctx, P));
+        P.valid = true;
+        if (ctx->opt.autotune && !ctx->tune.eval_done && T.n_leaves) {
+            // cost cap of the leaf-evaluation items: time each candidate on this tree (the
+            // values of the equivalent densities do not change the work; the output is zeroed
+            // below, after these launches)
+            float best = 1e30f, best_cost = ctx->tune.eval_cost;
+            for (float cost : {256.f, 512.f, 1024.f, 2048.f, 4096.f}) {
+                KF_TRY(make_eval_items(ctx, P, cost));
+                float ms = 0.f;
+                KF_TRY(time_launch(ctx, [&]() {
+                    eval_part(1, st);
+                    if (P.eval_split) eval_part(2, st);
+                }, &ms));
+                if (ms < best) best = ms, best_cost = cost;
+            }
+            ctx->tune.eval_cost = best_cost;
+            ctx->tune.eval_done = true;
+            KF_TRY(make_eval_items(ctx, P, best_cost));
+        }
+        if (overlap) {  // the side stream's leaf pass needs the items (and the tuning finished)
+            KF_CUDA(cudaEventRecord(ctx->ev_plans, st));
+            KF_CUDA(cudaStreamWaitEvent(s2, ctx->ev_plans, 0));
+        }
+    }
+    if (O.m2l_tc_mtiles > 0 && P.m2l_ncol != ncol) KF_TRY(upload_m2l_items());
     // ---- leaf evaluation, near part
     ctx->phase(KFMM_PH_EVAL);
     if (kind == KFMM_STRESS) {
@@ -1352,13 +1423,6 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
         KF_LAUNCH();
     }
     if (overlap) KF_CUDA(cudaEventRecord(ctx->ev_near, s2));
-    // ---- S2M: sources -> upward check surface of each leaf
-    ctx->phase(KFMM_PH_S2M);
-    KF_CUDA(cudaMemsetAsync(W.alpha.p, 0, sizeof(float) * (size_t)nb * kup * ncol, st));
-    if (T.n_leaves) {
-        check_pot(T.leaves.as<int>(), T.n_leaves, 0, (float)O.r_outer, W.up_chk.as<float>(), st);
-        KF_LAUNCH();
-    }
     // upward densities of the leaves in the singular basis: alpha = G h S^-1 U^T chk
     ctx->phase(KFMM_PH_UP_PINV);
     KF_TRY(box_gemm(P.leaves, O.tc_s2a_u, O.s2a_u.as<float>(), 0, ku, ld, ld, T.leaves.as<int>(),

@@ -222,6 +222,23 @@ def box_with_voids_points(n: int, n_voids: int = 20, box=(2.0, 1.0, 1.0), seed: 
     return pts, nrm
 
 
+def surface_batch(n_sets: int = 32, lo: int = 5000, hi: int = 250000, seed: int = SEED_GEOMETRY):
+    """A batch of independent box-with-voids surfaces of uneven size: set sizes log-uniform in
+    [lo, hi], 4 to 19 voids each, each box scaled and placed on its own.
+
+    Returns (pts [N,3], nrm [N,3], off [n_sets + 1]) with set k in rows off[k]:off[k+1].
+    """
+    rng = np.random.default_rng(seed + 7)
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_sets)).astype(np.int64)
+    pts, nrm = [], []
+    for k, n in enumerate(sizes):
+        x, nn = box_with_voids_points(int(n), n_voids=4 + k % 16, seed=seed + 100 + k)
+        pts.append(x * rng.uniform(0.5, 2.0) + rng.uniform(-10.0, 10.0, size=3))
+        nrm.append(nn)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return np.concatenate(pts), np.concatenate(nrm), off
+
+
 def densities(n: int, ncol: int = 1, seed: int = SEED_DENSITY):
     """Two N(0,1) 3-vector density arrays (single layer, double layer), [n, 3*ncol]."""
     rng = np.random.default_rng(seed)

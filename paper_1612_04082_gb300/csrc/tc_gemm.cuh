@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(M2L_THREADS, 1) tc_gather_gemm_kernel(TcArgs g
 //
 // One work item = one matrix, one row tile of 128, up to BN = 64 gathered columns.  K runs in
 // chunks of KC = 32 through three pipeline stages: the operator chunk (3 terms, 24 KB)
-// arrives by bulk copy one chunk ahead; the FP32 source rows are loaded into registers two
+// arrives by bulk copy two chunks ahead; the FP32 source rows are loaded into registers two
 // chunks ahead, split, and stored in the core-matrix layout.  Output modes: store, add
 // (exclusive rows), atomic add; each column may be scaled by alpha * geom[dst].w.
 // ======================================================================================
@@ -576,13 +576,14 @@ __global__ void __launch_bounds__(BOX_THREADS, 2) tc_box_gemm_kernel(TcBoxArgs g
         }
         if (w) store_split3(sm + (size_t)s * STAGE_BYTES + NTERM * A_TERM + boff, B_TERM, x0, x1);
         if (kc + 2 < n_kc) load_x(kc + 2, x0, x1);
-        if (tid == 0 && kc + 1 < n_kc && !*s_fail) {
-            // the next operator chunk goes to the stage last read by the MMAs of chunk kc - 2
-            const int ns = (kc + 1) % BOX_STAGES;
-            const bool w2 = kc + 1 < BOX_STAGES ||
-                            mbar_wait(&barM[ns], (uint32_t)((kc + 1 - BOX_STAGES) / BOX_STAGES) & 1u);
+        if (tid == 0 && kc + 2 < n_kc && !*s_fail) {
+            // the operator chunk two ahead goes to the stage last read by the MMAs of chunk
+            // kc - 1 (committed at the end of the previous step)
+            const int ns = (kc + 2) % BOX_STAGES;
+            const bool w2 = kc + 2 < BOX_STAGES ||
+                            mbar_wait(&barM[ns], (uint32_t)((kc + 2 - BOX_STAGES) / BOX_STAGES) & 1u);
             if (w2) {
-                issue_a(kc + 1, ns);
+                issue_a(kc + 2, ns);
                 ++loadsA;
             } else {
                 w = false;
@@ -608,6 +609,10 @@ __global__ void __launch_bounds__(BOX_THREADS, 2) tc_box_gemm_kernel(TcBoxArgs g
     if (tid == 0) {
         issue_a(0, 0);
         loadsA = 1;
+        if (n_kc > 1) {
+            issue_a(1, 1);
+            loadsA = 2;
+        }
     }
     bool ok = true;
     for (int kc = 0; kc < n_kc && ok; kc += 2) {

@@ -373,6 +373,7 @@ constexpr unsigned kBarrierSpin = 1u << 24;  // polls, ~64 ns apart, before a ba
 struct SplitState {
     int n_boxes, n_levels, n_leaves;
     int err;  // 1: box capacity too small (the host grows it and runs again); 2: barrier time-out
+    int deep;  // a box at the deepest level still holds more than leaf_cap points
     unsigned bar_count, bar_gen;
 };
 
@@ -494,7 +495,9 @@ __global__ void __launch_bounds__(kSplitThreads) split_tree_kernel(SplitArgs a)
             const bool valid = i < b1;
             const int b = first + (valid ? i : b0);
             const int2 s = __ldcg(&a.bsrc[b]), t = __ldcg(&a.btrg[b]);
-            const bool split = valid && (s.y - s.x > a.cap || t.y - t.x > a.cap) && level < a.L;
+            const bool over = valid && (s.y - s.x > a.cap || t.y - t.x > a.cap);
+            const bool split = over && level < a.L;
+            if (over && !split && o == 0) atomicExch(&st->deep, 1);
             int sb = s.x, tb = t.x;
             if (split && o > 0) {
                 const int sh = 3 * (a.L - level - 1);
@@ -953,8 +956,12 @@ kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, cons
     // keys: the set index above 3 L Morton bits, within 64 bits
     int set_bits = 0;
     while ((1LL << set_bits) < n_sets) ++set_bits;
-    const int L = std::min(ctx->opt.max_depth, (64 - set_bits) / 3);
-    if (L < 1) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many point sets");
+    const int L_full = std::min(ctx->opt.max_depth, (64 - set_bits) / 3);
+    if (L_full < 1) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many point sets");
+    // keys first at a shallow depth (fewer sort passes); a leaf that would need more levels
+    // sends the build back to the keys with the full depth
+    constexpr int kShallowDepth = 10;
+    int L = std::min(L_full, kShallowDepth);
 
     // ---- bounding cube of every set and NaN check
     DevBuf *tmp = ctx->work.tree_tmp;  // persistent scratch: slots 0-2 sort, 3-15 below
@@ -997,95 +1004,100 @@ kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, cons
     T.n_sets = n_sets;
     for (int c = 0; c < 3; ++c) T.root_lo[c] = hr[c];
     T.root_w = hr[3];
-    T.max_depth = L;
     T.nsrc = nsrc;
     T.ntrg = ntrg;
     T.has_nrm = src_nrm != nullptr;
 
-    // ---- keys and sort
-    KF_CUDA(T.src_key.ensure(sizeof(uint64_t) * nsrc));
-    KF_CUDA(T.trg_key.ensure(sizeof(uint64_t) * ntrg));
-    KF_CUDA(T.src_perm.ensure(sizeof(int) * nsrc));
-    KF_CUDA(T.trg_perm.ensure(sizeof(int) * ntrg));
-    keys_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_xyz, nsrc, d_soff, n_sets, roots.as<double>(), L,
-                                                      T.src_key.as<uint64_t>(), T.src_perm.as<int>());
-    KF_LAUNCH();
-    // targets given as the very array of the sources: one set of keys, one sort, then copies
-    bool same = trg_xyz == src_xyz;
-    for (int k = 0; k <= n_sets && same; ++k) same = src_off[k] == trg_off[k];
-    if (!same) {
-        keys_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, ntrg, d_toff, n_sets, roots.as<double>(), L,
-                                                          T.trg_key.as<uint64_t>(), T.trg_perm.as<int>());
-        KF_LAUNCH();
-    }
-    KF_TRY(radix_sort(ctx, T.src_key, T.src_perm, (int)nsrc, 3 * L + set_bits));
-    if (!same) KF_TRY(radix_sort(ctx, T.trg_key, T.trg_perm, (int)ntrg, 3 * L + set_bits));
-    KF_CUDA(T.src_xyz.ensure(sizeof(float4) * nsrc));
-    KF_CUDA(T.trg_xyz.ensure(sizeof(float4) * ntrg));
-    gather_points_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_xyz, T.src_perm.as<int>(), nsrc,
-                                                               T.src_xyz.as<float4>());
-    KF_LAUNCH();
-    if (same) {
-        KF_CUDA(cudaMemcpyAsync(T.trg_key.p, T.src_key.p, sizeof(uint64_t) * ntrg, cudaMemcpyDeviceToDevice, st));
-        KF_CUDA(cudaMemcpyAsync(T.trg_perm.p, T.src_perm.p, sizeof(int) * ntrg, cudaMemcpyDeviceToDevice, st));
-        KF_CUDA(cudaMemcpyAsync(T.trg_xyz.p, T.src_xyz.p, sizeof(float4) * ntrg, cudaMemcpyDeviceToDevice, st));
-    } else {
-        gather_points_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, T.trg_perm.as<int>(), ntrg,
-                                                                   T.trg_xyz.as<float4>());
-        KF_LAUNCH();
-    }
-    if (src_nrm) {
-        KF_CUDA(T.src_nrm.ensure(sizeof(float4) * nsrc));
-        gather_points_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_nrm, T.src_perm.as<int>(), nsrc,
-                                                                   T.src_nrm.as<float4>());
-        KF_LAUNCH();
-    }
-
-    // ---- boxes, level by level, and the leaves: one cooperative launch
-    ctx->phase(KFMM_PH_TREE_SPLIT);
-    if (!T.split_grid) {
-        int per_sm = 0, n_sm = 0;
-        KF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_tree_kernel, kSplitThreads, 0));
-        KF_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->opt.device));
-        if (per_sm < 1) return ctx->fail(KFMM_ERR_INTERNAL, "tree split kernel cannot be resident");
-        T.split_grid = std::min(per_sm, 2) * n_sm;
-    }
+    SplitState hs{};
     size_t capb = std::max<size_t>(1024, (size_t)(4 * (nsrc + ntrg) / std::max(1, cap)) + 64 + (size_t)n_sets);
     DevBuf &crange = tmp[4], &ccount = tmp[5], &bsum = tmp[6], &sstate = tmp[7], &loff = tmp[9];
-    KF_CUDA(bsum.ensure(sizeof(int) * T.split_grid));
-    KF_CUDA(sstate.ensure(sizeof(SplitState)));
-    KF_CUDA(loff.ensure(sizeof(int) * (L + 2)));
-    SplitState hs{};
-    for (;;) {
-        if (capb > (size_t)INT32_MAX / 8) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many boxes");
-        KF_CUDA(T.box_key.ensure(sizeof(uint64_t) * capb));
-        KF_CUDA(T.box_anchor.ensure(sizeof(int4) * capb));
-        KF_CUDA(T.box_parent.ensure(sizeof(int) * capb));
-        KF_CUDA(T.box_child.ensure(sizeof(int) * 8 * capb));
-        KF_CUDA(T.box_src.ensure(sizeof(int2) * capb));
-        KF_CUDA(T.box_trg.ensure(sizeof(int2) * capb));
-        KF_CUDA(T.box_leaf.ensure(sizeof(int) * capb));
-        KF_CUDA(T.leaves.ensure(sizeof(int) * capb));
-        KF_CUDA(crange.ensure(sizeof(int4) * 8 * capb));
-        KF_CUDA(ccount.ensure(sizeof(int) * capb));
-        KF_CUDA(cudaMemsetAsync(sstate.p, 0, sizeof(SplitState), st));
-        SplitArgs sa{L, cap, (int)capb, n_sets, d_soff, d_toff, T.src_key.as<uint64_t>(), T.trg_key.as<uint64_t>(),
-                     T.box_key.as<uint64_t>(), T.box_anchor.as<int4>(), T.box_parent.as<int>(),
-                     T.box_child.as<int>(), T.box_src.as<int2>(), T.box_trg.as<int2>(), T.box_leaf.as<int>(),
-                     T.leaves.as<int>(), crange.as<int4>(), ccount.as<int>(), bsum.as<int>(), loff.as<int>(),
-                     sstate.as<SplitState>()};
-        void *args[] = {&sa};
-        KF_CUDA(cudaLaunchCooperativeKernel((const void *)split_tree_kernel, dim3(T.split_grid), dim3(kSplitThreads),
-                                            args, 0, st));
+    for (;;) {  // depth attempts: kShallowDepth, then L_full if needed
+        ctx->phase(KFMM_PH_TREE);
+        // ---- keys and sort
+        KF_CUDA(T.src_key.ensure(sizeof(uint64_t) * nsrc));
+        KF_CUDA(T.trg_key.ensure(sizeof(uint64_t) * ntrg));
+        KF_CUDA(T.src_perm.ensure(sizeof(int) * nsrc));
+        KF_CUDA(T.trg_perm.ensure(sizeof(int) * ntrg));
+        keys_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_xyz, nsrc, d_soff, n_sets, roots.as<double>(), L,
+                                                          T.src_key.as<uint64_t>(), T.src_perm.as<int>());
         KF_LAUNCH();
-        T.level_off.assign(L + 2, 0);
-        KF_CUDA(cudaMemcpyAsync(&hs, sstate.p, sizeof(SplitState), cudaMemcpyDeviceToHost, st));
-        KF_CUDA(cudaMemcpyAsync(T.level_off.data(), loff.p, sizeof(int) * (L + 2), cudaMemcpyDeviceToHost, st));
-        KF_TRY(sync_stream(ctx));
-        if (hs.err == 2) return ctx->fail(KFMM_ERR_DEVICE_TIMEOUT, "tree split: a grid barrier gave up");
-        if (hs.err != 1) break;
-        capb *= 2;  // more boxes than the estimate: run again with twice the room
+        // targets given as the very array of the sources: one set of keys, one sort, then copies
+        bool same = trg_xyz == src_xyz;
+        for (int k = 0; k <= n_sets && same; ++k) same = src_off[k] == trg_off[k];
+        if (!same) {
+            keys_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, ntrg, d_toff, n_sets, roots.as<double>(), L,
+                                                              T.trg_key.as<uint64_t>(), T.trg_perm.as<int>());
+            KF_LAUNCH();
+        }
+        KF_TRY(radix_sort(ctx, T.src_key, T.src_perm, (int)nsrc, 3 * L + set_bits));
+        if (!same) KF_TRY(radix_sort(ctx, T.trg_key, T.trg_perm, (int)ntrg, 3 * L + set_bits));
+        KF_CUDA(T.src_xyz.ensure(sizeof(float4) * nsrc));
+        KF_CUDA(T.trg_xyz.ensure(sizeof(float4) * ntrg));
+        gather_points_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_xyz, T.src_perm.as<int>(), nsrc,
+                                                                   T.src_xyz.as<float4>());
+        KF_LAUNCH();
+        if (same) {
+            KF_CUDA(cudaMemcpyAsync(T.trg_key.p, T.src_key.p, sizeof(uint64_t) * ntrg, cudaMemcpyDeviceToDevice, st));
+            KF_CUDA(cudaMemcpyAsync(T.trg_perm.p, T.src_perm.p, sizeof(int) * ntrg, cudaMemcpyDeviceToDevice, st));
+            KF_CUDA(cudaMemcpyAsync(T.trg_xyz.p, T.src_xyz.p, sizeof(float4) * ntrg, cudaMemcpyDeviceToDevice, st));
+        } else {
+            gather_points_kernel<<<grid_for(ntrg, 256), 256, 0, st>>>(trg_xyz, T.trg_perm.as<int>(), ntrg,
+                                                                       T.trg_xyz.as<float4>());
+            KF_LAUNCH();
+        }
+        if (src_nrm) {
+            KF_CUDA(T.src_nrm.ensure(sizeof(float4) * nsrc));
+            gather_points_kernel<<<grid_for(nsrc, 256), 256, 0, st>>>(src_nrm, T.src_perm.as<int>(), nsrc,
+                                                                       T.src_nrm.as<float4>());
+            KF_LAUNCH();
+        }
+
+        // ---- boxes, level by level, and the leaves: one cooperative launch
+        ctx->phase(KFMM_PH_TREE_SPLIT);
+        if (!T.split_grid) {
+            int per_sm = 0, n_sm = 0;
+            KF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_tree_kernel, kSplitThreads, 0));
+            KF_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->opt.device));
+            if (per_sm < 1) return ctx->fail(KFMM_ERR_INTERNAL, "tree split kernel cannot be resident");
+            T.split_grid = std::min(per_sm, 2) * n_sm;
+        }
+        KF_CUDA(bsum.ensure(sizeof(int) * T.split_grid));
+        KF_CUDA(sstate.ensure(sizeof(SplitState)));
+        KF_CUDA(loff.ensure(sizeof(int) * (L + 2)));
+        for (;;) {
+            if (capb > (size_t)INT32_MAX / 8) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many boxes");
+            KF_CUDA(T.box_key.ensure(sizeof(uint64_t) * capb));
+            KF_CUDA(T.box_anchor.ensure(sizeof(int4) * capb));
+            KF_CUDA(T.box_parent.ensure(sizeof(int) * capb));
+            KF_CUDA(T.box_child.ensure(sizeof(int) * 8 * capb));
+            KF_CUDA(T.box_src.ensure(sizeof(int2) * capb));
+            KF_CUDA(T.box_trg.ensure(sizeof(int2) * capb));
+            KF_CUDA(T.box_leaf.ensure(sizeof(int) * capb));
+            KF_CUDA(T.leaves.ensure(sizeof(int) * capb));
+            KF_CUDA(crange.ensure(sizeof(int4) * 8 * capb));
+            KF_CUDA(ccount.ensure(sizeof(int) * capb));
+            KF_CUDA(cudaMemsetAsync(sstate.p, 0, sizeof(SplitState), st));
+            SplitArgs sa{L, cap, (int)capb, n_sets, d_soff, d_toff, T.src_key.as<uint64_t>(), T.trg_key.as<uint64_t>(),
+                         T.box_key.as<uint64_t>(), T.box_anchor.as<int4>(), T.box_parent.as<int>(),
+                         T.box_child.as<int>(), T.box_src.as<int2>(), T.box_trg.as<int2>(), T.box_leaf.as<int>(),
+                         T.leaves.as<int>(), crange.as<int4>(), ccount.as<int>(), bsum.as<int>(), loff.as<int>(),
+                         sstate.as<SplitState>()};
+            void *args[] = {&sa};
+            KF_CUDA(cudaLaunchCooperativeKernel((const void *)split_tree_kernel, dim3(T.split_grid), dim3(kSplitThreads),
+                                                args, 0, st));
+            KF_LAUNCH();
+            T.level_off.assign(L + 2, 0);
+            KF_CUDA(cudaMemcpyAsync(&hs, sstate.p, sizeof(SplitState), cudaMemcpyDeviceToHost, st));
+            KF_CUDA(cudaMemcpyAsync(T.level_off.data(), loff.p, sizeof(int) * (L + 2), cudaMemcpyDeviceToHost, st));
+            KF_TRY(sync_stream(ctx));
+            if (hs.err == 2) return ctx->fail(KFMM_ERR_DEVICE_TIMEOUT, "tree split: a grid barrier gave up");
+            if (hs.err != 1) break;
+            capb *= 2;  // more boxes than the estimate: run again with twice the room
+        }
+        if (!hs.deep || L >= L_full) break;
+        L = L_full;  // clustered points: all over again with the full depth
     }
+    T.max_depth = L;
     const int n_boxes = hs.n_boxes;
     T.n_boxes = n_boxes;
     T.n_levels = hs.n_levels;

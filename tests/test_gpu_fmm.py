@@ -510,3 +510,29 @@ def test_point_sets_separate_targets_and_errors(K):
         bad[2] = bad[1]  # an empty set
         with pytest.raises(K.KfmmError):
             c.build_sets(bad, dev(src), dev(nrm), toff, dev(trg))
+
+
+def test_clustered_points_deep_tree(K):
+    """A tight cluster inside a unit cloud needs more than the 10 levels the keys are first
+    made with: the build goes back to full-depth keys, and the FMM still meets its tolerance.
+    The cluster sits near the origin, where FP32 positions resolve its smallest boxes (a box
+    whose half-width is near the FP32 spacing of its coordinates misplaces its check and
+    equivalent surfaces)."""
+    rng = np.random.default_rng(5)
+    far, nf = W.uniform_cloud(6000)
+    near = 1e-3 + 1e-4 * rng.uniform(-1.0, 1.0, size=(6000, 3))
+    nn = rng.normal(size=(6000, 3))
+    nn /= np.linalg.norm(nn, axis=1, keepdims=True)
+    src = r32(np.concatenate([far, near]))
+    nrm = r32(np.concatenate([nf, nn]))
+    sl, dl = W.densities(len(src))
+    sl, dl = r32(sl), r32(dl)
+    with make_ctx(K, G1, NU1) as c:
+        c.build(dev(src), dev(nrm), dev(src))
+        assert c.stats()["n_levels"] > 11
+        out = torch.zeros(len(src), 3, device="cuda:0")
+        c.eval(dev(sl), dev(dl), out)
+        got = out.cpu().numpy().astype(np.float64)
+    idx = np.concatenate([W.subsample(6000, 150), 6000 + W.subsample(6000, 150)])
+    ref = O.direct_disp(src[idx], src, nrm, sl, dl, G1, NU1)
+    assert rel(got[idx], ref) < 1e-4

@@ -1095,7 +1095,8 @@ static kfmm_status make_eval_items(kfmm_ctx *ctx, FmmPlans &P, float cost)
 
 // Plans of a new tree, in two parts so that the host work overlaps the first kernels of the
 // evaluation.  plans_begin enqueues the device part: box geometry, the leaf-item counts with
-// their scan, and an asynchronous copy of the list totals to pinned memory (event ev_items).
+// their scan, and an asynchronous copy of the list totals to pinned memory (event ev_items);
+// it also makes the leaves' tile table, which the first box product needs.
 static kfmm_status plans_begin(kfmm_ctx *ctx, FmmPlans &P)
 {
     Tree &T = ctx->tree;
@@ -1107,6 +1108,7 @@ static kfmm_status plans_begin(kfmm_ctx *ctx, FmmPlans &P)
         T.n_boxes, T.box_anchor.as<int4>(), T.box_key.as<uint64_t>(), T.set_root_dev.as<double>(),
         P.geom.as<float4>());
     KF_LAUNCH();
+    KF_TRY(make_plan(ctx, P.leaves, {0}, {0}, {T.n_leaves}));  // for the first box product
     P.n_eval_items = P.n_eval_far = 0;
     P.eval_split = ctx->opt.streams != 0;
     P.items_pending = false;
@@ -1132,7 +1134,6 @@ static kfmm_status plans_end(kfmm_ctx *ctx, FmmPlans &P)
 {
     Tree &T = ctx->tree;
     KF_TRY(make_plan(ctx, P.all, {0}, {0}, {T.n_boxes}));
-    KF_TRY(make_plan(ctx, P.leaves, {0}, {0}, {T.n_leaves}));
     KF_TRY(make_plan(ctx, P.xboxes, {0}, {0}, {T.n_xboxes}));
     KF_TRY(make_plan(ctx, P.wboxes, {0}, {0}, {T.n_wboxes}));
     {
@@ -1377,8 +1378,14 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
         check_pot(T.leaves.as<int>(), T.n_leaves, 0, (float)O.r_outer, W.up_chk.as<float>(), st);
         KF_LAUNCH();
     }
+    // upward densities of the leaves in the singular basis: alpha = G h S^-1 U^T chk
+    ctx->phase(KFMM_PH_UP_PINV);
+    KF_TRY(box_gemm(P.leaves, O.tc_s2a_u, O.s2a_u.as<float>(), 0, ku, ld, ld, T.leaves.as<int>(),
+                    T.leaves.as<int>(), 0, 0, W.up_chk.as<float>(), ld, W.alpha.as<float>(), kup, geom,
+                    (float)ctx->G, 0));
     if (new_tree) {
-        // host part of the plans while the GPU runs S2M and P2L; then the leaf items
+        // host part of the plans while the GPU runs S2M, P2L and the first box product; then
+        // the leaf items
         ctx->phase(KFMM_PH_PLANS);
         KF_TRY(plans_end(ctx, P));
         P.valid = true;
@@ -1423,11 +1430,6 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
         KF_LAUNCH();
     }
     if (overlap) KF_CUDA(cudaEventRecord(ctx->ev_near, s2));
-    // upward densities of the leaves in the singular basis: alpha = G h S^-1 U^T chk
-    ctx->phase(KFMM_PH_UP_PINV);
-    KF_TRY(box_gemm(P.leaves, O.tc_s2a_u, O.s2a_u.as<float>(), 0, ku, ld, ld, T.leaves.as<int>(),
-                    T.leaves.as<int>(), 0, 0, W.up_chk.as<float>(), ld, W.alpha.as<float>(), kup, geom,
-                    (float)ctx->G, 0));
     // ---- M2M, bottom-up (children of level l into their parents)
     ctx->phase(KFMM_PH_M2M);
     for (int l = T.n_levels - 1; l >= 1; --l)

@@ -664,20 +664,20 @@ __device__ __forceinline__ bool adjacent(const int4 &a, const int4 &b, int L)
 // candidate order.  mode 0: count into cnt[4][n_boxes] (U, V, W, X); mode 1: fill.  The
 // descendants of the non-leaf colleagues (U (ii), W) are walked through a frontier in shared
 // memory, 32 boxes per step, last in first out (so it stays about 8 x 32 per remaining
-// level); a frontier that would exceed kListQ sets *overflow and stops the walk.
-constexpr int kListWarps = 4;
-constexpr int kListQ = 2048;
-
-__global__ void __launch_bounds__(32 * kListWarps)
+// level); a frontier that would exceed Q entries sets *overflow and stops the walk.  The
+// small frontier (4 KB per warp) keeps ~56 warps per SM resident; the host falls back to
+// the large one after an overflow.
+template <int WARPS, int Q>
+__global__ void __launch_bounds__(32 * WARPS)
 lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict__ uo, int *__restrict__ ui,
              const int *__restrict__ vo, int *__restrict__ vi, const int *__restrict__ wo, int *__restrict__ wi,
              const int *__restrict__ xo, int *__restrict__ xi, int *__restrict__ overflow)
 {
-    __shared__ int frontier[kListWarps][kListQ];
+    __shared__ int frontier[WARPS][Q];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
-    const int b = blockIdx.x * kListWarps + wid;
+    const int b = blockIdx.x * WARPS + wid;
     if (b >= tv.n_boxes) return;  // the whole warp
     int *q = frontier[wid];
     const int L = tv.L;
@@ -776,7 +776,7 @@ lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict
                 if (lane >= d) incl += v;
             }
             const int total = __shfl_sync(full, incl, 31);
-            if (qn + total > kListQ) {
+            if (qn + total > Q) {
                 if (lane == 0) atomicExch(overflow, 1);
                 break;
             }
@@ -1130,44 +1130,57 @@ kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, cons
     KF_CUDA(cnt.ensure(sizeof(int) * (4 * (size_t)n_boxes + 1)));
     KF_CUDA(hdr.ensure(sizeof(int) * (8 + (size_t)ng)));
     int *H = hdr.as<int>();
-    KF_CUDA(cudaMemsetAsync(H, 0, sizeof(int) * (8 + (size_t)ng), st));
-    const unsigned list_blocks = (unsigned)((n_boxes + kListWarps - 1) / kListWarps);
-    lists_kernel<<<list_blocks, 32 * kListWarps, 0, st>>>(tv, 0, cnt.as<int>(), nullptr, nullptr, nullptr, nullptr,
-                                                          nullptr, nullptr, nullptr, nullptr, H + 6);
-    KF_LAUNCH();
+    // list passes with the small frontier (attempt 0) or, after an overflow, the large one
+    auto lists = [&](int attempt, int mode) {
+        if (attempt == 0)
+            lists_kernel<4, 1024><<<(n_boxes + 3) / 4, 128, 0, st>>>(
+                tv, mode, mode ? nullptr : cnt.as<int>(), T.u_off.as<int>(), T.u_idx.as<int>(), T.v_off.as<int>(),
+                T.v_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.x_off.as<int>(), T.x_idx.as<int>(), H + 6);
+        else
+            lists_kernel<2, 4096><<<(n_boxes + 1) / 2, 64, 0, st>>>(
+                tv, mode, mode ? nullptr : cnt.as<int>(), T.u_off.as<int>(), T.u_idx.as<int>(), T.v_off.as<int>(),
+                T.v_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.x_off.as<int>(), T.x_idx.as<int>(), H + 6);
+    };
+    std::vector<int> hh(8 + (size_t)ng);
     DevBuf *offs[4] = {&T.u_off, &T.v_off, &T.w_off, &T.x_off};
     DevBuf *idxs[4] = {&T.u_idx, &T.v_idx, &T.w_idx, &T.x_idx};
-    // offsets of the four lists from one scan over their concatenated counts
     DevBuf &scn = tmp[12];
-    KF_CUDA(scn.ensure(sizeof(int) * (4 * (size_t)n_boxes + 1)));
-    int *S = scn.as<int>();
-    KF_TRY(scan_exclusive(ctx, cnt.as<int>(), S, 4 * n_boxes, S + 4 * (size_t)n_boxes));
-    for (int l = 0; l < 4; ++l) KF_CUDA(offs[l]->ensure(sizeof(int) * (n_boxes + 1)));
-    list_offsets_kernel<<<grid_for(n_boxes + 1, 256, 1 << 30), 256, 0, st>>>(
-        n_boxes, S, T.u_off.as<int>(), T.v_off.as<int>(), T.w_off.as<int>(), T.x_off.as<int>(), H);
-    KF_LAUNCH();
-    // X boxes (non-empty X list) and the W boxes whose upward densities are evaluated at the
-    // targets.  A box lies in some W list exactly when its X list is non-empty (b is in W(C)
-    // iff C is in X(b)); those with more sources than half the surface points take the M2P
-    // path, the others are evaluated directly.
-    T.w_direct_max = surface_points(ctx->opt.p) / 2;
     DevBuf &xflag = tmp[3], &xpos = tmp[8], &wflag = tmp[13], &wpos = tmp[14];
-    KF_CUDA(xflag.ensure(sizeof(int) * n_boxes));
-    KF_CUDA(xpos.ensure(sizeof(int) * n_boxes));
-    KF_CUDA(wflag.ensure(sizeof(int) * n_boxes));
-    KF_CUDA(wpos.ensure(sizeof(int) * n_boxes));
-    box_flags_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(
-        n_boxes, cnt.as<int>() + 3 * (size_t)n_boxes, T.box_src.as<int2>(), T.w_direct_max, xflag.as<int>(),
-        wflag.as<int>());
-    KF_LAUNCH();
-    KF_TRY(scan_exclusive(ctx, xflag.as<int>(), xpos.as<int>(), n_boxes, H + 4));
-    KF_TRY(scan_exclusive(ctx, wflag.as<int>(), wpos.as<int>(), n_boxes, H + 5));
-    oct_count_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_anchor.as<int4>(), H + 8);
-    KF_LAUNCH();
-    std::vector<int> hh(8 + (size_t)ng);
-    KF_CUDA(cudaMemcpyAsync(hh.data(), H, sizeof(int) * hh.size(), cudaMemcpyDeviceToHost, st));
-    KF_TRY(sync_stream(ctx));
-    if (hh[6]) return ctx->fail(KFMM_ERR_INTERNAL, "interaction-list traversal frontier overflow");
+    int attempt = 0;
+    for (;; ++attempt) {
+        KF_CUDA(cudaMemsetAsync(H, 0, sizeof(int) * (8 + (size_t)ng), st));
+        lists(attempt, 0);
+        KF_LAUNCH();
+        // offsets of the four lists from one scan over their concatenated counts
+        KF_CUDA(scn.ensure(sizeof(int) * (4 * (size_t)n_boxes + 1)));
+        int *S = scn.as<int>();
+        KF_TRY(scan_exclusive(ctx, cnt.as<int>(), S, 4 * n_boxes, S + 4 * (size_t)n_boxes));
+        for (int l = 0; l < 4; ++l) KF_CUDA(offs[l]->ensure(sizeof(int) * (n_boxes + 1)));
+        list_offsets_kernel<<<grid_for(n_boxes + 1, 256, 1 << 30), 256, 0, st>>>(
+            n_boxes, S, T.u_off.as<int>(), T.v_off.as<int>(), T.w_off.as<int>(), T.x_off.as<int>(), H);
+        KF_LAUNCH();
+        // X boxes (non-empty X list) and the W boxes whose upward densities are evaluated at the
+        // targets.  A box lies in some W list exactly when its X list is non-empty (b is in W(C)
+        // iff C is in X(b)); those with more sources than half the surface points take the M2P
+        // path, the others are evaluated directly.
+        T.w_direct_max = surface_points(ctx->opt.p) / 2;
+        KF_CUDA(xflag.ensure(sizeof(int) * n_boxes));
+        KF_CUDA(xpos.ensure(sizeof(int) * n_boxes));
+        KF_CUDA(wflag.ensure(sizeof(int) * n_boxes));
+        KF_CUDA(wpos.ensure(sizeof(int) * n_boxes));
+        box_flags_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(
+            n_boxes, cnt.as<int>() + 3 * (size_t)n_boxes, T.box_src.as<int2>(), T.w_direct_max, xflag.as<int>(),
+            wflag.as<int>());
+        KF_LAUNCH();
+        KF_TRY(scan_exclusive(ctx, xflag.as<int>(), xpos.as<int>(), n_boxes, H + 4));
+        KF_TRY(scan_exclusive(ctx, wflag.as<int>(), wpos.as<int>(), n_boxes, H + 5));
+        oct_count_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, T.box_anchor.as<int4>(), H + 8);
+        KF_LAUNCH();
+        KF_CUDA(cudaMemcpyAsync(hh.data(), H, sizeof(int) * hh.size(), cudaMemcpyDeviceToHost, st));
+        KF_TRY(sync_stream(ctx));
+        if (!hh[6]) break;
+        if (attempt == 1) return ctx->fail(KFMM_ERR_INTERNAL, "interaction-list traversal frontier overflow");
+    }
     T.n_u = hh[0];
     T.n_v = hh[1];
     T.n_w = hh[2];
@@ -1175,9 +1188,7 @@ kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, cons
     T.n_xboxes = hh[4];
     T.n_wboxes = hh[5];
     for (int l = 0; l < 4; ++l) KF_CUDA(idxs[l]->ensure(sizeof(int) * std::max(1, hh[l])));
-    lists_kernel<<<list_blocks, 32 * kListWarps, 0, st>>>(
-        tv, 1, nullptr, T.u_off.as<int>(), T.u_idx.as<int>(), T.v_off.as<int>(), T.v_idx.as<int>(),
-        T.w_off.as<int>(), T.w_idx.as<int>(), T.x_off.as<int>(), T.x_idx.as<int>(), H + 6);
+    lists(attempt, 1);
     KF_LAUNCH();
     KF_CUDA(T.xboxes.ensure(sizeof(int) * std::max(1, T.n_xboxes)));
     compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, xflag.as<int>(), xpos.as<int>(),

@@ -114,12 +114,6 @@ kfmm_status sync_stream(kfmm_ctx *ctx)
     return KFMM_OK;
 }
 
-kfmm_status read_int(kfmm_ctx *ctx, const int *dptr, int *host)
-{
-    KF_CUDA(cudaMemcpyAsync(host, dptr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    return sync_stream(ctx);
-}
-
 kfmm_status upload_async(kfmm_ctx *ctx, void *dst, const void *src, size_t bytes)
 {
     if (bytes == 0) return KFMM_OK;

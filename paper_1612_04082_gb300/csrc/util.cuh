@@ -19,9 +19,6 @@ inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152LL * 32) {
 // receives sum of all.  in and out may alias.  Temporaries come from `scratch`.
 kfmm_status scan_exclusive(kfmm_ctx *ctx, const int *in, int *out, int n, int *total);
 
-// Reads one device int to the host (synchronises the context stream).
-kfmm_status read_int(kfmm_ctx *ctx, const int *dptr, int *host);
-
 // Synchronises the context stream; the pinned staging of earlier uploads is free again.
 kfmm_status sync_stream(kfmm_ctx *ctx);
 

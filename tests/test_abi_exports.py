@@ -35,3 +35,38 @@ def test_host_only_helpers():
     assert (o.p, o.leaf_cap) == (6, 64)
     assert K.kfmm_status_str(K.KFMM_ERR_NOT_BUILT) == "not built"
     assert abs(K.material_K(1.0, 0.3) - 13.0 / 6.0) < 1e-14
+
+
+def test_default_options_new_fields():
+    """The options the evaluation scheduling adds: overlapped streams on, leaf-item cost cap
+    left to the default / tuning."""
+    import paper_1612_04082_gb300 as K
+    o = K.kfmm_default_options()
+    assert o.streams == 1 and o.eval_item_cost == 0 and o.graphs == 1 and o.autotune == 1
+    assert K.PHASES[-3:] == ("tree_split", "tree_lists", "plans")
+
+
+def test_build_sets_rejects_mismatched_offsets():
+    """Offsets are checked on the host before any device work."""
+    import numpy as np
+    import pytest
+    import paper_1612_04082_gb300 as K
+    x = np.zeros((10, 3), np.float32)
+    with pytest.raises(ValueError):
+        K.kfmm_build_sets(None, [0, 5, 10], x, None, [0, 10], x)
+    with pytest.raises(ValueError):
+        K.kfmm_build_sets(None, [0], x, None, [0], x)
+
+
+def test_surface_batch_workload():
+    """The 32-surface batch: seeded, sizes log-uniform within the stated range, unit normals,
+    sets contiguous."""
+    import numpy as np
+    import workloads as W
+    p1, n1, o1 = W.surface_batch(n_sets=8, lo=500, hi=3000)
+    p2, n2, o2 = W.surface_batch(n_sets=8, lo=500, hi=3000)
+    assert np.array_equal(p1, p2) and np.array_equal(o1, o2)
+    sizes = np.diff(o1)
+    assert len(sizes) == 8 and o1[0] == 0 and o1[-1] == len(p1)
+    assert sizes.min() >= 500 and sizes.max() <= 3000
+    assert np.allclose(np.linalg.norm(n1, axis=1), 1.0)

@@ -339,7 +339,17 @@ check_potential_kernel(const int *__restrict__ boxes, int nbox, int use_xlist, c
             for (int k = tid; k < cnt; k += kChkThreads) sh[k] = rec[base + k];
             __syncthreads();
             if (has0) {
-                for (int s = 0; s < cnt; ++s) {
+                int s = 0;
+                for (; s + 1 < cnt; s += 2) {  // two independent pairs per step
+                    const SrcRec qa = sh[s], qb = sh[s + 1];
+                    chk_pair<SL, DL>(x, y, z, qa, a34, c3, ox, oy, oz);
+                    chk_pair<SL, DL>(x, y, z, qb, a34, c3, ox, oy, oz);
+                    if (has1) {
+                        chk_pair<SL, DL>(x1, y1, z1, qa, a34, c3, px, py, pz);
+                        chk_pair<SL, DL>(x1, y1, z1, qb, a34, c3, px, py, pz);
+                    }
+                }
+                if (s < cnt) {
                     const SrcRec q = sh[s];
                     chk_pair<SL, DL>(x, y, z, q, a34, c3, ox, oy, oz);
                     if (has1) chk_pair<SL, DL>(x1, y1, z1, q, a34, c3, px, py, pz);

@@ -149,7 +149,7 @@ kfmm_status kfmm_build(kfmm_ctx *ctx, const float *src_xyz, const float *src_nrm
 /* One build over n_sets independent point sets (a batch of surfaces of uneven size): set k
  * owns sources src_off[k] .. src_off[k+1] - 1 and targets trg_off[k] .. trg_off[k+1] - 1 of
  * the concatenated arrays (offsets: n_sets + 1 host int64 values from 0, every set at least
- * one source and one target).  Each set gets its own root cube (one level-0 box); no list
+ * one source and one target; 1 <= n_sets <= 65535).  Each set gets its own root cube (one level-0 box); no list
  * crosses sets, so kfmm_eval computes Eq. fmm_summation within every set, all sets in the
  * same launches.  The set index leads every Morton key, so the depth is capped at
  * (64 - ceil(log2 n_sets)) / 3 levels.  kfmm_build is the case n_sets = 1. */

@@ -150,8 +150,8 @@ kfmm_status kfmm_build_sets(kfmm_ctx *ctx, int32_t n_sets, const int64_t *src_of
 {
     if (!ctx) return KFMM_ERR_INVALID_ARG;
     ctx->err.clear();
-    if (n_sets < 1 || !src_off || !trg_off || !src_xyz || !trg_xyz)
-        return ctx->fail(KFMM_ERR_INVALID_ARG, "build: need n_sets >= 1, offsets and point arrays");
+    if (n_sets < 1 || n_sets > 65535 || !src_off || !trg_off || !src_xyz || !trg_xyz)
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "build: need 1 <= n_sets <= 65535, offsets and point arrays");
     if (src_off[0] != 0 || trg_off[0] != 0)
         return ctx->fail(KFMM_ERR_INVALID_ARG, "build: set offsets must start at 0");
     for (int k = 0; k < n_sets; ++k)

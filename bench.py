@@ -15,7 +15,11 @@ oracle (direct summation) on the host cores over a bounded sample of the same wo
 
 The line also carries the BEM leg of the metric ("bem"): a mixed-boundary cantilever solved
 to a 1e-6 relative residual of the exact FP64 discrete operator by mixed-precision GMRES with
-iterative refinement (FP32 FMM corrections), beside plain FP64 GMRES on the same GPU.
+iterative refinement (FP32 FMM corrections), beside plain FP64 GMRES on the same GPU; and the
+batch leg ("batch"): 32 independent surfaces of uneven size in one build and evaluation,
+beside the same surfaces one by one.  Per-phase times come from separate profiled steps
+(phases serialised); "eval_only_ms" is the evaluation alone on the last tree.
+--no-bem, --no-batch and --no-cpu-baseline leave those legs out.
 """
 from __future__ import annotations
 

@@ -536,3 +536,24 @@ def test_clustered_points_deep_tree(K):
     idx = np.concatenate([W.subsample(6000, 150), 6000 + W.subsample(6000, 150)])
     ref = O.direct_disp(src[idx], src, nrm, sl, dl, G1, NU1)
     assert rel(got[idx], ref) < 1e-4
+
+
+def test_full_size_bench_workload(K):
+    """The benchmark workload at its full size and in the launch configuration the benchmark
+    times (1e6 surface points of the box with 20 voids, p = 6, leaf cap 64, tuned launch
+    shapes, overlapped streams): 300 sampled targets against the oracle, one by one."""
+    n = 1_000_000
+    src, nrm = W.box_with_voids_points(n, n_voids=20)
+    sl, dl = W.densities(n)
+    src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
+    with make_ctx(K, G1, NU1, p=6, leaf_cap=64) as c:
+        x = dev(src)
+        c.build(x, dev(nrm), x)
+        out = torch.full((n, 3), float("nan"), device="cuda:0")
+        c.eval(dev(sl), dev(dl), out)
+        got = out.cpu().numpy().astype(np.float64)
+        assert c.stats()["n_levels"] >= 8
+    assert np.all(np.isfinite(got))
+    idx = W.subsample(n, 300)
+    ref = O.direct_disp(src[idx], src, nrm, sl, dl, G1, NU1)
+    assert rel(got[idx], ref) < 1e-4

@@ -239,6 +239,14 @@ kfmm_status kfmm_get_phase_times(kfmm_ctx *ctx, double *ms, int64_t *counts, int
 const char *kfmm_status_str(kfmm_status s);
 const char *kfmm_last_error(const kfmm_ctx *ctx);
 
+/* Failure-detection check of the bounded device waits: one thread waits on a shared-memory
+ * mbarrier that nothing arrives on, polling at most `polls` times (1..2^24) with the wait
+ * the tensor-core kernels use, then records the time-out in the context's device error
+ * word, which the host reads back as those kernels' errors are read.  Returns
+ * KFMM_ERR_DEVICE_TIMEOUT, as designed (KFMM_OK would mean the wait completed); nothing
+ * faults or hangs and the context stays usable. */
+kfmm_status kfmm_selftest_bounded_wait(kfmm_ctx *ctx, int64_t polls);
+
 /* ====================================================================================== */
 /* Collocation BEM on the FMM (Eq. BIE; Eq. num, coef, num2; Sec. "Matrix-vector products") */
 /* ====================================================================================== */

@@ -69,6 +69,7 @@ _sig = {
     "kfmm_set_stream": (ctypes.c_int, [_vp, _vp]),
     "kfmm_build": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64]),
     "kfmm_build_sets": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
+    "kfmm_selftest_bounded_wait": (ctypes.c_int, [_vp, _i64]),
     "kfmm_eval": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]),
     "kfmm_direct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]),
     "kfmm_direct_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_int,
@@ -266,6 +267,10 @@ class Kfmm:
 
     def build_sets(self, src_off, src_xyz, src_nrm, trg_off, trg_xyz):
         kfmm_build_sets(self.handle, src_off, src_xyz, src_nrm, trg_off, trg_xyz)
+
+    def selftest_bounded_wait(self, polls=4096):
+        """Status of the bounded-wait check (KFMM_ERR_DEVICE_TIMEOUT as designed)."""
+        return int(_lib.kfmm_selftest_bounded_wait(self.handle, int(polls)))
 
     def eval(self, sl_den, dl_den, out, kind=KFMM_DISP, ncol=1):
         return kfmm_eval(self.handle, sl_den, dl_den, out, kind, ncol)

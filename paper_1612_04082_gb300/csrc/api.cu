@@ -337,6 +337,14 @@ kfmm_status kfmm_get_phase_times(kfmm_ctx *ctx, double *ms, int64_t *counts, int
     return KFMM_OK;
 }
 
+kfmm_status kfmm_selftest_bounded_wait(kfmm_ctx *ctx, int64_t polls)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (cudaSetDevice(ctx->opt.device) != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, "cudaSetDevice");
+    return selftest_bounded_wait(ctx, (long long)polls);
+}
+
 const char *kfmm_status_str(kfmm_status s)
 {
     switch (s) {

@@ -388,6 +388,7 @@ kfmm_status tree_work_counts(kfmm_ctx *ctx);  // interaction counts for the stat
 kfmm_status ensure_operators(kfmm_ctx *ctx);
 // fmm.cu
 kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, int kind, float *out);
+kfmm_status selftest_bounded_wait(kfmm_ctx *ctx, long long polls);
 // direct.cu
 kfmm_status direct_sum(kfmm_ctx *ctx, int precision, const void *trg, int64_t ntrg, const void *src,
                        const void *nrm, int64_t nsrc, const void *sl, const void *dl, int kind, void *out);

@@ -1523,6 +1523,33 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     return KFMM_OK;
 }
 
+// One thread waits on an mbarrier that nothing arrives on (bounded) and records the time-out.
+__global__ void bounded_wait_probe_kernel(long long polls, int *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!tc::mbar_wait_n(&bar, 0u, polls)) atomicExch(err, 1);
+}
+
+kfmm_status selftest_bounded_wait(kfmm_ctx *ctx, long long polls)
+{
+    if (polls < 1 || polls > (1LL << 24)) return ctx->fail(KFMM_ERR_INVALID_ARG, "polls must be in 1..2^24");
+    const cudaStream_t st = ctx->stream;
+    DevBuf &err = ctx->plans.err;
+    KF_CUDA(err.ensure(sizeof(int)));
+    KF_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    bounded_wait_probe_kernel<<<1, 32, 0, st>>>(polls, err.as<int>());
+    KF_LAUNCH();
+    int herr = 0;
+    KF_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KF_TRY(sync_stream(ctx));
+    if (!herr) return KFMM_OK;
+    KF_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    return ctx->fail(KFMM_ERR_DEVICE_TIMEOUT, "bounded wait probe: the wait gave up, as designed");
+}
+
 void EvalGraph::reset()
 {
     if (exec) cudaGraphExecDestroy(exec);

@@ -68,11 +68,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// true when the phase with parity `phase` has completed; false after WAIT_LIMIT polls
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase)
+// true when the phase with parity `phase` has completed; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait_n(uint64_t *bar, uint32_t phase, long long limit)
 {
     const uint32_t a = smem_u32(bar);
-    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    for (long long i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -83,6 +83,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase)
     }
     return false;
 }
+
+// the same with the kernels' limit, WAIT_LIMIT polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) { return mbar_wait_n(bar, phase, WAIT_LIMIT); }
 
 // bulk copy global -> shared, completion counted on `bar` (16-byte aligned, size % 16 == 0)
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)

@@ -557,3 +557,21 @@ def test_full_size_bench_workload(K):
     idx = W.subsample(n, 300)
     ref = O.direct_disp(src[idx], src, nrm, sl, dl, G1, NU1)
     assert rel(got[idx], ref) < 1e-4
+
+
+def test_bounded_wait_gives_up_and_context_survives(K):
+    """Failure detection without a GPU fault: a device wait on a barrier that nothing
+    arrives on gives up after its poll limit, the time-out reaches the host as
+    KFMM_ERR_DEVICE_TIMEOUT through the device error word, and the context keeps working."""
+    src, nrm = W.box_with_voids_points(4000, n_voids=3)
+    sl, dl = W.densities(len(src))
+    src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
+    with make_ctx(K, G1, NU1) as c:
+        assert c.selftest_bounded_wait(4096) == K.KFMM_ERR_DEVICE_TIMEOUT
+        assert "as designed" in K._lib.kfmm_last_error(c.handle).decode()
+        c.build(dev(src), dev(nrm), dev(src))
+        out = torch.zeros(len(src), 3, device="cuda:0")
+        c.eval(dev(sl), dev(dl), out)
+        idx = W.subsample(len(src), 200)
+        ref = O.direct_disp(src[idx], src, nrm, sl, dl, G1, NU1)
+        assert rel(out.cpu().numpy().astype(np.float64)[idx], ref) < 1e-4

@@ -13,12 +13,19 @@ N > 1 runs one independent replica per GPU (weak scaling, no collective on the d
 value = all ranks' targets / the slowest rank's time.  --impl reference times the FP64 CPU
 oracle (direct summation) on the host cores over a bounded sample of the same workload.
 
-The line also carries the BEM leg of the metric ("bem"): a mixed-boundary cantilever solved
-to a 1e-6 relative residual of the exact FP64 discrete operator by mixed-precision GMRES with
-iterative refinement (FP32 FMM corrections), beside plain FP64 GMRES on the same GPU; and the
-batch leg ("batch"): 32 independent surfaces of uneven size in one build and evaluation,
-beside the same surfaces one by one.  Per-phase times come from separate profiled steps
-(phases serialised); "eval_only_ms" is the evaluation alone on the last tree.
+The line also carries the BEM half of the metric:
+ - "bem": the 2x1x1 cantilever at voxel size 0.01 (400,000 triangles, 1.2M unknowns), clamped
+   at x = 0, unit downward traction on the 0.1 x 0.1 patch at x = 2, solved to a 1e-6
+   relative residual by mixed-precision GMRES with iterative refinement (FP32 FMM corrections,
+   FP64-grade compensated direct residuals); then stress, topological derivative and energy
+   density at the 256 x 128 x 128 cell centres (4,194,304 points); the oracle checks sampled
+   rows of the residual and sampled grid points;
+ - "bem_small": the same cantilever at 5760 triangles, GMRES-IR beside plain FP64 GMRES on the
+   same GPU at the same 1e-6 residual;
+and the batch leg ("batch"): 32 independent surfaces of uneven size in one build and
+evaluation, beside the same surfaces one by one.  Per-phase times come from separate
+profiled steps (phases serialised); "eval_only_ms" is the evaluation alone on the last tree.
+The FP32 peak of the "alu" rooflines is measured by the library's FMA-chain kernel.
 --no-bem, --no-batch and --no-cpu-baseline leave those legs out.
 """
 from __future__ import annotations
@@ -39,14 +46,16 @@ sys.path.insert(0, ROOT)
 METRIC = "FMM matvec targets/sec (Kelvin SL+DL, 3-vec) & BEM solves/sec at 1e-6 residual; P2P % FP32 peak"
 WORKLOAD = "KIFMM matvec, 1e6 surface points (2x1x1 box + 20 spherical voids), Kelvin SL+DL, p=6, leaf cap 64"
 N_POINTS = 1_000_000
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
 # algorithmic FP32 operations per pair (counted from the kernel formulas, FMA = 2)
 FLOPS_SLDL = 61   # single + double layer displacement
 FLOPS_SL = 30     # single layer only (equivalent densities: L2P, M2P)
 L2_FLUSH_BYTES = 512 << 20
-BEM_N = 12          # cantilever cells per unit length: 40 n^2 = 5760 triangles
+BEM_N = 12          # small cantilever: cells per unit length, 40 n^2 = 5760 triangles
+BEM3_N = 100        # the 400,000-triangle cantilever (voxel size 0.01)
+BEM3_PATCH = 0.05   # half-side of its loaded patch (0.1 x 0.1)
+TD_GRID = (256, 128, 128)
+BEM3_TOL_HI = 2e-7  # GMRES-IR tolerance in the compensated residual (true residual <= 1e-6)
 # DRAM bytes per launch of the dominant kernel at this workload, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/); None when the
 # kernel has changed since the counters were taken
@@ -80,8 +89,40 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def fp32_peak_tflops(mhz):
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+def fp32_nominal_tflops(n_sms, mhz):
+    return n_sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_one_core_rate(k=100):
+    """Targets/s of the oracle's direct sum on one host core: a fresh interpreter with
+    OMP_NUM_THREADS=1 (this process has a CUDA context, so nothing is forked from it)."""
+    code = ("import sys, time; sys.path.insert(0, %r); import bench as B; "
+            "p, n, s, d = B.workload(B.N_POINTS); _, _, dt = B.cpu_oracle_sample(p, n, s, d, %d); print(dt)") % (ROOT, k)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+        return k / float(r.stdout.strip().splitlines()[-1])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return None
 
 
 class ClockSampler:
@@ -182,21 +223,22 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def bem_leg(K, local, world):
+def bem_small_leg(K, local, world):
     """Cantilever (40 n^2 triangles, clamped at x = 0, unit traction patch at x = 2) solved to a
-    1e-6 relative residual of the FP64 direct operator: mixed-precision GMRES-IR on the FMM
-    (timed over 3 solves after a warm-up) and plain FP64 GMRES with the direct operator."""
+    1e-6 relative residual: mixed-precision GMRES-IR on the FMM with compensated FP64-grade
+    residuals (timed over 3 solves after a warm-up) and plain FP64 GMRES with the FP64 direct
+    operator, both on the GPU."""
     import torch
     import workloads as W
     V, T, mask, vals = W.cantilever(BEM_N)
     nt = len(T)
     u, t = np.zeros((nt, 3)), np.zeros((nt, 3))
-    out = {"workload": f"cantilever 2x1x1, {nt} triangles ({3 * nt} unknowns), mixed BC, G=1, nu=0.3",
-           "tol": 1e-6, "residual": "FP64 direct discrete operator"}
+    out = {"workload": f"cantilever 2x1x1, {nt} triangles ({3 * nt} unknowns), mixed BC, patch 0.5x0.5, G=1, nu=0.3",
+           "tol": 1e-6, "residual": "FP64-grade compensated direct discrete operator"}
     with K.Bem(V, T, K.BEM_FMM, device=local) as b:
         b.set_material(K.material_K(1.0, 0.3), 1.0)
         b.set_bc(mask, vals)
-        kw = dict(tol=1e-6, restart=100, maxit=3000, refine=True, inner_tol=1e-3)
+        kw = dict(tol=1e-6, restart=100, maxit=3000, refine=1, inner_tol=1e-3)
         b.solve(u, t, **kw)
         times, st = [], None
         for _ in range(3):
@@ -205,8 +247,8 @@ def bem_leg(K, local, world):
             times.append(st["seconds"])
     sec = max_over_ranks(float(np.mean(times)), world, f"cuda:{local}")
     out.update({"solves_per_s": aggregate_rate(1, world, sec), "ms_per_solve": 1e3 * sec, "inner_iters": st["iters"],
-                "outer": st["outer"], "fmm_matvecs": st["matvecs"], "fp64_matvecs": st["matvecs_hi"],
-                "relres": st["relres"], "method": "GMRES-IR: FP32 FMM corrections (p=6), FP64 direct residuals"})
+                "outer": st["outer"], "fmm_matvecs": st["matvecs"], "hi_matvecs": st["matvecs_hi"],
+                "relres": st["relres"], "method": "GMRES-IR: FP32 FMM corrections (p=6), compensated direct residuals"})
     with K.Bem(V, T, K.BEM_DIRECT_FP64, device=local) as b:
         b.set_material(K.material_K(1.0, 0.3), 1.0)
         b.set_bc(mask, vals)
@@ -214,6 +256,105 @@ def bem_leg(K, local, world):
     out["fp64_gmres"] = {"ms_per_solve": 1e3 * st["seconds"], "iters": st["iters"], "relres": st["relres"],
                          "method": "plain GMRES, FP64 direct operator on the GPU"}
     out["speedup_vs_fp64_gmres"] = st["seconds"] / sec
+    return out
+
+
+def td_grid(shape=TD_GRID, box=(2.0, 1.0, 1.0)):
+    """Cell centres of a regular grid over the box, [nx*ny*nz, 3] float32."""
+    axes = [(np.arange(n) + 0.5) * (L / n) for n, L in zip(shape, box)]
+    g = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, 3)
+    return np.ascontiguousarray(g, dtype=np.float32)
+
+
+def oracle_rows(V, T, u, t, idx):
+    """The oracle's M(u, t) = 1/2 u + P^D u - U^D t (Eq. num) at the collocation points idx:
+    direct sum over all quadrature sources, the element's own terms replaced by its analytic
+    singular blocks."""
+    import oracle as O
+    nrm, area, cen = O.tri_geometry(V, T)
+    q, w = O.tri_quadrature(V, T)
+    q[12::16] = cen  # the centre sub-triangle's centroid is the collocation point
+    qn = np.repeat(nrm, 16, axis=0)
+    sl = -np.repeat(t, 16, axis=0) * w[:, None]
+    dl = np.repeat(u, 16, axis=0) * w[:, None]
+    m = O.direct_disp(cen[idx], q, qn, sl, dl, 1.0, 0.3)
+    for r, l in enumerate(idx):
+        own = slice(16 * l, 16 * l + 16)
+        m[r] -= O.direct_disp(cen[l:l + 1], q[own], qn[own], sl[own], dl[own], 1.0, 0.3)[0]
+        Us, Ts = O.self_integrals(*V[T[l]], 1.0, 0.3)
+        m[r] += 0.5 * u[l] + Ts @ u[l] - Us @ t[l]
+    return m
+
+
+def bem_config3_leg(K, local, world, rank, check=True):
+    """The 400,000-triangle cantilever (voxel size 0.01): GMRES-IR to a 1e-6 relative residual,
+    then stress, topological derivative and energy density at the 256 x 128 x 128 cell
+    centres.  One solve after a warm-up call (set-up, tree build, tuning); the grid
+    evaluation once after a warm-up.  rank 0 checks sampled residual rows and grid points
+    against the oracle."""
+    import torch
+    import workloads as W
+    dev = torch.device("cuda", local)
+    V, T, mask, vals = W.cantilever(BEM3_N, BEM3_PATCH)
+    nt = len(T)
+    u, t = np.zeros((nt, 3)), np.zeros((nt, 3))
+    pts = torch.tensor(td_grid(), device=dev)
+    npt = pts.shape[0]
+    td = torch.empty(npt, dtype=torch.float32, device=dev)
+    en = torch.empty_like(td)
+    sig = torch.empty(npt, 6, dtype=torch.float32, device=dev)
+    out = {"workload": f"cantilever 2x1x1, voxel 0.01, {nt} triangles ({3 * nt} unknowns, {16 * nt} quadrature "
+                       f"sources), clamped x=0, traction (0,0,-1) on the 0.1x0.1 patch at x=2 ({int((np.abs(vals).sum(1) > 0).sum())} "
+                       f"triangles); TD grid {TD_GRID[0]}x{TD_GRID[1]}x{TD_GRID[2]} ({npt} points)",
+           "tol": 1e-6, "tol_compensated": BEM3_TOL_HI,
+           "residual": "true residual of the exact discrete operator <= 1e-6: the solve runs to "
+                       f"{BEM3_TOL_HI:g} in the compensated operator's residual, whose distance from the exact "
+                       "operator is below 8e-7 of ||b|| (tests); the oracle checks sampled rows"}
+    with K.Bem(V, T, K.BEM_FMM, device=local) as b:
+        b.set_material(K.material_K(1.0, 0.3), 1.0)
+        b.set_bc(mask, vals)
+        rhs = np.zeros((nt, 3))
+        b.rhs(rhs)  # warm-up: quadrature set-up, FMM tree of the 6.4M sources, tuning
+        torch.cuda.synchronize(dev)
+        st = b.solve(u, t, tol=BEM3_TOL_HI, restart=100, maxit=8000, refine=1, inner_tol=1e-3)
+        sec = max_over_ranks(st["seconds"], world, dev)
+        out.update({"solves_per_s": aggregate_rate(1, world, sec), "ms_per_solve": 1e3 * sec,
+                    "inner_iters": st["iters"], "outer": st["outer"], "fmm_matvecs": st["matvecs"],
+                    "hi_matvecs": st["matvecs_hi"], "relres": st["relres"], "converged": bool(st["converged"]),
+                    "method": "GMRES-IR: FP32 FMM corrections (p=6, restart 100, inner tol 1e-3), compensated "
+                              "FP64-grade direct residuals"})
+        b.topo_derivative(pts, td, en, sig)  # warm-up: the interior tree of sources and grid points
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream(dev)
+        e0.record(stream)
+        b.topo_derivative(pts, td, en, sig)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        td_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        out["td"] = {"ms": td_ms, "points_per_s": aggregate_rate(npt, world, td_ms / 1e3),
+                     "step": "interior FMM build (6.4M sources, 4.2M targets) + STRESS evaluation + Eq. deriv",
+                     "p": 8}
+        if check and rank == 0:
+            import oracle as O
+            # residual at sampled rows: the oracle's M(u, t) relative to ||b|| on the same rows
+            idx = np.asarray(__import__("workloads").subsample(nt, 200))
+            t0 = time.perf_counter()
+            m_or = oracle_rows(V, T, u, t, idx)
+            bn_rows = np.sqrt(len(idx) / nt) * np.linalg.norm(rhs)
+            out["oracle_residual_sampled"] = float(np.linalg.norm(m_or) / bn_rows)
+            out["oracle_residual_rows"] = int(len(idx))
+            # stress at sampled grid points against the oracle's Somigliana sum (Eq. stress_1)
+            gi = np.asarray(W.subsample(npt, 200))
+            p64 = pts[gi].double().cpu().numpy()
+            _, s_ref = O.bem_interior(p64, V, T, u, t, 1.0, 0.3, disp=False, stress=True)
+            td_ref, _ = O.topo_derivative(s_ref, 1.0, 0.3)
+            s_got = sig[gi].double().cpu().numpy()
+            out["stress_rel_l2_vs_oracle"] = float(np.linalg.norm(s_got - s_ref) / np.linalg.norm(s_ref))
+            out["td_rel_l2_vs_oracle"] = float(np.linalg.norm(td[gi].double().cpu().numpy() - td_ref)
+                                               / np.linalg.norm(td_ref))
+            out["oracle_check_s"] = time.perf_counter() - t0
+            out["oracle_grid_points"] = int(len(gi))
     return out
 
 
@@ -310,6 +451,7 @@ def main():
     f = K.Kfmm(p=6, leaf_cap=64, device=local)
     f.set_material(K.material_K(1.0, 0.3), 1.0)
     f.set_stream(stream)
+    fp32_meas = f.measure_fp32_peak()
 
     def step():
         f.build(x, nn, x)
@@ -391,7 +533,7 @@ def main():
     m = 3 * st["n_surf"]
     ku, kd = st["up_rank"], st["down_rank"]
     peaks, peak_src = load_peaks()
-    fp32_peak = fp32_peak_tflops(SM_MAX_MHZ)
+    fp32_peak = fp32_meas["tflops"]
     bf16_peak = peaks["bf16_tflops_sustained"]
     # (bound, executed operations per step, peak, note)
     work = {
@@ -416,19 +558,22 @@ def main():
         ach = ops / t / 1e12 if t > 0 else 0.0
         return {"bound": bound, "kernel_phase": k, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": TRAFFIC_BYTES.get(k),
-                "peak_note": ("FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz" if bound == "alu"
+                "peak_note": (f"FP32 FMA peak measured by kfmm_measure_fp32_peak on this GPU ({fp32_meas['n_sms']} SMs, "
+                              f"FMA chains, fastest of 5 launches)" if bound == "alu"
                               else f"BF16 dense tensor peak, sustained, of {peak_src} (MEASURED_PEAKS.json)"),
                 "ops_note": note}
 
     dom = max((k for k in work if k in ph_ms), key=lambda k: ph_ms[k])
     roof = roofline_of(dom)
     if clocks.get("sm_mhz") and roof["bound"] == "alu":
-        roof["frac_at_sampled_clock"] = roof["achieved"] / fp32_peak_tflops(clocks["sm_mhz"])
+        roof["frac_of_nominal_at_sampled_clock"] = roof["achieved"] / fp32_nominal_tflops(fp32_meas["n_sms"],
+                                                                                           clocks["sm_mhz"])
     kernels = {k: {"ms": ph_ms[k], "frac": roofline_of(k)["frac"], "bound": work[k][0]} for k in work if k in ph_ms}
     p2p_ach = work["eval"][1] / (ph_ms["eval"] / 1e3) / 1e12 if ph_ms["eval"] > 0 else 0.0
 
     # ---- BEM leg: mixed-precision refinement vs plain FP64 GMRES at a 1e-6 FP64 residual
-    bem = bem_leg(K, local, world) if not args.no_bem else None
+    bem = bem_config3_leg(K, local, world, rank, check=not args.no_cpu_baseline) if not args.no_bem else None
+    bem_small = bem_small_leg(K, local, world) if not args.no_bem else None
     batch = batch_leg(K, local, world, flush) if not args.no_batch else None
 
     line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
@@ -451,7 +596,10 @@ def main():
                            "overlapped with the upward pass and M2L",
             "kernels": kernels,
             "bem": bem,
+            "bem_small": bem_small,
             "batch": batch,
+            "fp32_peak": {"tflops": fp32_meas["tflops"], "n_sms": fp32_meas["n_sms"], "source": "measured",
+                          "nominal_at_max_clock": fp32_nominal_tflops(fp32_meas["n_sms"], 2070.0)},
             "tree": {k: st[k] for k in ("n_boxes", "n_leaves", "n_levels", "m2l_rank", "n_v_pairs",
                                         "n_w_pairs", "n_x_pairs", "p2p_interactions")}}
 
@@ -462,8 +610,10 @@ def main():
         f.eval(s, d, out)
         got = out.cpu().numpy().astype(np.float64)[idx]
         line["cpu_baseline"] = {"value": args.cpu_sample / dt, "unit": "targets/s", "cores": host_threads(),
-                                "kind": "oracle",
-                                "sample": f"{args.cpu_sample} of {args.n} targets x all {args.n} sources, FP64"}
+                                "kind": "oracle", "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                                "one_core_value": oracle_one_core_rate(),
+                                "sample": f"{args.cpu_sample} of {args.n} targets x all {args.n} sources, FP64 "
+                                          "(one_core_value: 100 targets, OMP_NUM_THREADS=1)"}
         line["rel_l2_error_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     f.close()
     if rank == 0:

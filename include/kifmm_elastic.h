@@ -9,9 +9,10 @@
  *  - Return value: KFMM_OK (0) or a negative kfmm_status.  No exception crosses the ABI.
  *    On error kfmm_last_error(ctx) holds a one-line message.  Outputs are unspecified
  *    after an error unless the entry point says otherwise.
- *  - Array arguments are plain pointers that may point to device memory or to host memory
- *    (pageable or pinned); the library inspects each pointer and stages host arrays through
- *    its own device buffers.  The caller owns every array passed in; each must stay valid
+ *  - Array arguments are plain pointers that may point to device memory of the context's GPU
+ *    or to host memory (pageable or pinned); the library inspects each pointer and stages
+ *    host arrays through its own device buffers.  Device memory of another GPU is rejected
+ *    with KFMM_ERR_INVALID_ARG.  The caller owns every array passed in; each must stay valid
  *    for the duration of the call.  The library owns only its internal buffers (tree,
  *    operators, workspaces), released by the matching *_destroy.
  *  - Layouts are row-major arrays of structures: points [n][3] (x, y, z); 3-vector densities
@@ -51,7 +52,13 @@ typedef enum kfmm_status {
 
 typedef enum kfmm_kind {
     KFMM_DISP = 0,   /* 3 outputs per target and column: SL (Eq. disp_1) + DL (Eq. disp_2) */
-    KFMM_STRESS = 1  /* 6 outputs per target and column: Eq. stress_2 + Eq. stress_3        */
+    KFMM_STRESS = 1, /* 6 outputs per target and column: Eq. stress_2 + Eq. stress_3        */
+    KFMM_TD = 2      /* 2 outputs per target and column from that stress sigma: the
+                        topological derivative of the compliance, Eq. deriv,
+                        D^T = 3 (1-nu) / (4 E (7-5nu)) [10 (1+nu) sigma:sigma - (1+5nu) (tr sigma)^2],
+                        and the energy density 1/2 sigma:eps (integrand of Eq. functional);
+                        with sl = t w, dl = -u w (Eq. stress_1) these are the fields of the
+                        optimisation loop.  kfmm_eval only.                                  */
 } kfmm_kind;
 
 typedef enum kfmm_precision {
@@ -157,8 +164,9 @@ kfmm_status kfmm_build_sets(kfmm_ctx *ctx, int32_t n_sets, const int64_t *src_of
                             const float *src_nrm, const int64_t *trg_off, const float *trg_xyz);
 
 /* One FMM evaluation of Eq. fmm_summation on the built tree: sl_den, dl_den [nsrc][3*ncol]
- * (either may be NULL, not both), out [ntrg][3*ncol] (DISP) or [ntrg][6*ncol] (STRESS),
- * FP32, overwritten.  ncol in 1..32. */
+ * (either may be NULL, not both), out [ntrg][3*ncol] (DISP), [ntrg][6*ncol] (STRESS) or
+ * [ntrg][2*ncol] (TD: D^T then energy density per column), FP32, overwritten.  ncol in
+ * 1..32. */
 kfmm_status kfmm_eval(kfmm_ctx *ctx, const float *sl_den, const float *dl_den, int ncol, int kind,
                       float *out);
 
@@ -169,6 +177,32 @@ kfmm_status kfmm_direct(kfmm_ctx *ctx, int precision, const void *trg_xyz, int64
                         const void *src_xyz, const void *src_nrm, int64_t nsrc, const void *sl_den,
                         const void *dl_den, int kind, void *out);
 
+/* The displacement sum of kfmm_direct (DISP kind) to FP64-grade accuracy at FP32 arithmetic
+ * rate, for the outer residual of mixed-precision GMRES (the system of Eq. num2, solved by
+ * GMRES as in Sec. "Numerical solution").  Such a residual b - A x cancels: its terms exceed
+ * the result by a factor ||A| |x|| / ||b|| of ~100 on a clamped cantilever, so a relative
+ * residual of 1e-6 needs the operator to ~1e-9 of its terms, beyond FP32 and too slow in
+ * FP64 on this GPU (1/64 of the FP32 rate).  Arithmetic: points split into FP32 hi + lo
+ * parts so that every difference x - y is exact to FP32 rounding of the difference itself;
+ * the sum carried as four partial sums free of material constants, which are applied in
+ * FP64 per target; FP32 partial sums folded into FP64 every 128 sources; 1/r refined by one
+ * Newton-Raphson step; pairs closer than near_radius (the largest terms) evaluated wholly in
+ * FP64.  What is left is the random rounding of the far pairs' FP32 kernel evaluation.
+ *  - All arrays FP64: trg_xyz [ntrg][3], src_xyz [nsrc][3], src_nrm [nsrc][3] (required with
+ *    dl_den), sl_den, dl_den [nsrc][3] (either may be NULL, not both), out [ntrg][3]
+ *    (overwritten); host or device memory as for every entry point.
+ *  - near_radius >= 0 (same length unit as the points): pairs with |x - y| < near_radius use
+ *    FP64 throughout.  The remaining pairs' FP32 rounding (~4e-7 of each term, of either
+ *    sign) adds up to ~1e-8 of the sum on smooth densities over a surface (measured), where
+ *    plain FP32 summation is off by ~1e-6; the BEM layer passes four times its longest
+ *    element edge.
+ *    Coincident points (r = 0) are skipped, as in every sum here.
+ *  - The context's material (kfmm_set_material) applies; no tree is needed.  Work is enqueued
+ *    on the context stream; the call synchronises only when it staged host arrays. */
+kfmm_status kfmm_direct_hi(kfmm_ctx *ctx, const double *trg_xyz, int64_t ntrg, const double *src_xyz,
+                           const double *src_nrm, int64_t nsrc, const double *sl_den, const double *dl_den,
+                           double near_radius, double *out);
+
 /* The same all-pairs sum as kfmm_direct, for callers that cannot allocate device memory:
  * a process whose device memory is already handed to a caching allocator (a new
  * cudaMalloc would fail), or code that must not call cudaMalloc / cudaFree while it runs
@@ -177,13 +211,15 @@ kfmm_status kfmm_direct(kfmm_ctx *ctx, int precision, const void *trg_xyz, int64
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  The sum is
  *    split over source slices whose partial results go to one fixed 16 MiB scratch array
  *    in device memory, reserved on every GPU that loads the library until process exit.
- *  - Every array (trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out) must be device memory;
- *    host pointers are rejected with KFMM_ERR_INVALID_ARG (staging them would allocate).
+ *  - Every array (trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out) must be device memory of
+ *    the context's GPU; host pointers and other GPUs' memory are rejected with
+ *    KFMM_ERR_INVALID_ARG (staging them would allocate).
  *  - Limit: ntrg * (3 for DISP, 6 for STRESS) * (4 for FP32, 8 for FP64) bytes must not
  *    exceed 16 MiB (e.g. 699,050 FP32 or 349,525 FP64 displacement targets); larger
  *    sizes are rejected with KFMM_ERR_INVALID_ARG.  nsrc is not limited.
  *  - The first call on a device looks up the scratch array's device address (once per
  *    device, with that device current); make that first call before any stream capture.
+ *    The cached address is not valid across cudaDeviceReset (the module is loaded again).
  *  - All calls share the scratch array, which keeps the last call's contents; each call
  *    writes every entry it reads.  Calls that overlap on the GPU (other streams, other host
  *    threads) race on it: the caller must serialise them.
@@ -208,6 +244,48 @@ kfmm_status kfmm_export_tree(const kfmm_ctx *ctx, int32_t *box_level, int32_t *b
  * total.  U and W lists are defined for leaves only (empty rows elsewhere). */
 kfmm_status kfmm_export_list(const kfmm_ctx *ctx, char which, int32_t *offsets, int32_t *items,
                              int64_t *n_pairs);
+
+/* ------------------------------------------------------------------------------------
+ * Partition over several GPUs (Sec. "Numerical solution": the evaluation is parallelised by
+ * giving each process a part of the octree).  Host code on a tree given as host arrays --
+ * the arrays of kfmm_export_tree and kfmm_export_list for a built tree; boxes are listed
+ * coarse to fine (a parent before its children).  No GPU is needed.
+ * ------------------------------------------------------------------------------------ */
+typedef struct kfmm_tree_view {
+    int32_t n_boxes;
+    const int32_t *level;    /* [n_boxes] octree level (0 = a root)                          */
+    const int32_t *anchor;   /* [n_boxes][3] integer box coordinates at its level            */
+    const int32_t *parent;   /* [n_boxes], -1 at a root                                      */
+    const int32_t *box_src;  /* [n_boxes][2] source range [begin, end) in the sorted order   */
+    const int32_t *box_trg;  /* [n_boxes][2] target range                                    */
+    const int32_t *u_off, *u_idx, *v_off, *v_idx, *w_off, *w_idx, *x_off, *x_idx;  /* lists,
+                                CSR by target box (the U, V, W, X lists of the build)       */
+} kfmm_tree_view;
+
+/* Cost-weighted partition: the leaves in Morton order (led by their root for independent
+ * point sets) are cut into n_ranks contiguous ranges of about equal cost; box_cost [n_boxes]
+ * gives each leaf's cost (NULL: targets x U-list sources + sources + targets + 1).  Outputs:
+ * box_owner [n_boxes] = the rank of a leaf, the rank of a box whose leaves all belong to one
+ * rank, -1 for a box shared by several ranks (the coarse levels); leaf_order [n_leaves] (may
+ * be NULL) = the leaves in Morton order; rank_cost [n_ranks] (may be NULL) = each rank's
+ * total cost. */
+kfmm_status kfmm_shard_plan(const kfmm_tree_view *t, int32_t n_ranks, const double *box_cost, int32_t *box_owner,
+                            int32_t *leaf_order, double *rank_cost);
+
+/* Locally essential tree of `rank` under the partition box_owner: for its leaves and their
+ * ancestors (the boxes whose downward densities it forms), the boxes whose data come from
+ * elsewhere, each list in increasing box order:
+ *   src_boxes    -- leaves of U (its leaves) and X lists owned by another rank: their points
+ *                   and densities are received;
+ *   up_boxes     -- boxes of V lists and W (its leaves) owned by another rank: their upward
+ *                   equivalent densities are received;
+ *   shared_boxes -- shared boxes (owner -1) in those lists or among its ancestors: their
+ *                   upward densities are the sum of every rank's part (all-reduce).
+ * On entry *n_src, *n_up, *n_shared are the capacities of the arrays (arrays may be NULL to
+ * count only); on return the counts (KFMM_ERR_INVALID_ARG if an array was too small). */
+kfmm_status kfmm_shard_let(const kfmm_tree_view *t, const int32_t *box_owner, int32_t rank, int32_t *src_boxes,
+                           int64_t *n_src, int32_t *up_boxes, int64_t *n_up, int32_t *shared_boxes,
+                           int64_t *n_shared);
 
 /* Phases timed when profiling is on (CUDA events on the context stream around each phase). */
 typedef enum kfmm_phase {
@@ -239,6 +317,14 @@ kfmm_status kfmm_get_phase_times(kfmm_ctx *ctx, double *ms, int64_t *counts, int
 const char *kfmm_status_str(kfmm_status s);
 const char *kfmm_last_error(const kfmm_ctx *ctx);
 
+/* Measured FP32 FMA throughput of the context's GPU, the peak the pair-evaluation kernels
+ * (Eq. fmm_summation's near field and the check-surface sums) are bounded by: 8 CTAs of
+ * 256 threads per multiprocessor, each thread 8 independent chains of dependent FMAs
+ * (2 flop each); the fastest of 5 timed launches after one warm-up, timed with CUDA events
+ * on the context stream.  *tflops receives TFLOP/s, *ms (may be NULL) the launch time,
+ * *n_sms (may be NULL) the multiprocessor count.  Synchronises the context stream. */
+kfmm_status kfmm_measure_fp32_peak(kfmm_ctx *ctx, double *tflops, double *ms, int32_t *n_sms);
+
 /* Failure-detection check of the bounded device waits: one thread waits on a shared-memory
  * mbarrier that nothing arrives on, polling at most `polls` times (1..2^24) with the wait
  * the tensor-core kernels use, then records the time-out in the context's device error
@@ -267,7 +353,9 @@ typedef struct bem_ctx bem_ctx;
 
 typedef enum bem_operator {
     BEM_FMM = 0,         /* FP32 KIFMM summation (SL + DL) + FP64 local pass               */
-    BEM_DIRECT_FP64 = 1  /* FP64 all-pairs summation on the GPU + FP64 local pass (O(N^2)) */
+    BEM_DIRECT_FP64 = 1, /* FP64 all-pairs summation on the GPU + FP64 local pass (O(N^2)) */
+    BEM_DIRECT_HI = 2    /* compensated all-pairs summation (kfmm_direct_hi: FP64-grade at
+                            FP32 rate, O(N^2)) + FP64 local pass                           */
 } bem_operator;
 
 typedef struct bem_solve_opts {
@@ -276,9 +364,10 @@ typedef struct bem_solve_opts {
     int maxit;         /* cap on inner GMRES iterations in total (1000)                      */
     const double *x0;  /* initial guess of the unknowns [nt][3], or NULL for zero; a guess
                           whose residual exceeds ||b|| is dropped for zero                    */
-    int refine;        /* 0: GMRES on the context's operator.  1 (FMM contexts): mixed-
+    int refine;        /* 0: GMRES on the context's operator.  1 or 2 (FMM contexts): mixed-
                           precision iterative refinement -- right-hand side, outer residuals
-                          and updates in FP64 with the direct (exact discrete) operator, each
+                          and updates in FP64 with an FP64-grade all-pairs operator (1: the
+                          compensated sum of kfmm_direct_hi; 2: the FP64 direct sum), each
                           correction by GMRES on the FP32 FMM operator (0)                    */
     double inner_tol;  /* relative tolerance of each refinement correction, loosened to what
                           the outer tolerance still needs near the end (1e-3)                 */
@@ -290,10 +379,10 @@ typedef struct bem_stats {
     int matvecs;      /* FMM operator applications (including residual checks)              */
     int converged;    /* 1 if the tolerance was met                                          */
     double relres;    /* final true relative residual ||b - A x|| / ||b|| (with refinement:
-                         against the FP64 direct operator)                                   */
+                         against the FP64-grade direct operator)                             */
     double seconds;   /* wall time of bem_solve                                              */
     int outer;        /* refinement steps (1 without refinement)                            */
-    int matvecs_hi;   /* FP64 direct operator applications                                  */
+    int matvecs_hi;   /* FP64-grade direct operator applications (refinement)               */
     double x0_relres; /* ||b - A x0|| / ||b|| of the initial guess (1 for zero; a value > 1
                          means the guess was dropped for zero)                               */
 } bem_stats;
@@ -309,34 +398,48 @@ kfmm_status bem_destroy(bem_ctx *b);
 kfmm_status bem_set_material(bem_ctx *b, double K, double G);
 kfmm_status bem_set_stream(bem_ctx *b, void *stream);
 
-/* Boundary conditions of Eq. elast: known_is_disp [nt][3] (uint8: 1 = u_i prescribed,
- * 0 = t_i prescribed), values [nt][3] (the prescribed u or t). */
-kfmm_status bem_set_bc(bem_ctx *b, const uint8_t *known_is_disp, const double *values);
+/* Boundary conditions of Eq. elast for ncol load cases (1..32) sharing one mask:
+ * known_is_disp [nt][3] (uint8: 1 = u_i prescribed, 0 = t_i prescribed), values [nt][3*ncol]
+ * (the prescribed u or t of load case c in entries 3c .. 3c+2 of each row).  The load cases
+ * are solved together: every GMRES step sums all columns in one FMM evaluation (the six
+ * unit-strain cases of a periodic-cell homogenisation are 6 columns, Sec. "Periodic cell of
+ * a metamaterial"). */
+kfmm_status bem_set_bc(bem_ctx *b, const uint8_t *known_is_disp, const double *values, int ncol);
 
-/* out = M(u, t) = 1/2 u + P^D u - U^D t at the centroids (either input may be NULL = 0). */
+/* out = M(u, t) = 1/2 u + P^D u - U^D t at the centroids (either input may be NULL = 0); one
+ * column, [nt][3]. */
 kfmm_status bem_apply(bem_ctx *b, const double *u, const double *t, double *out);
-/* y = A x and rhs = B y of Eq. num2 for the boundary conditions set last. */
+/* y = A x and rhs = B y of Eq. num2 for the boundary conditions set last: x, y, rhs
+ * [nt][3*ncol]. */
 kfmm_status bem_matvec(bem_ctx *b, const double *x, double *y);
 kfmm_status bem_rhs(bem_ctx *b, double *rhs);
 
 /* Restarted GMRES (Saad & Schultz) on A x = B y, FP64 vectors and Arnoldi (classical
- * Gram-Schmidt applied twice) on the device.  On return u, t [nt][3] (either may be NULL)
- * hold the boundary solution, which is also kept for bem_interior.  Returns
- * KFMM_ERR_NOT_CONVERGED (with the last iterate stored and returned) at the iteration cap. */
+ * Gram-Schmidt applied twice) on the device, all ncol load cases in lockstep: each Arnoldi
+ * step applies the operator to every column at once; each column has its own Krylov basis
+ * and stops extending it once it meets the tolerance.  On return u, t [nt][3*ncol] (either
+ * may be NULL) hold the boundary solution, which is also kept for bem_interior.  The stats
+ * report the largest relative residual over the columns and the lockstep iteration count.
+ * opts->x0, when given, is [nt][3*ncol].  Returns KFMM_ERR_NOT_CONVERGED (with the last
+ * iterate stored and returned) at the iteration cap. */
 kfmm_status bem_solve(bem_ctx *b, const bem_solve_opts *o, double *u, double *t, bem_stats *st);
 
-/* Store a boundary solution (u, t [nt][3]) without solving, e.g. from an earlier solve. */
-kfmm_status bem_set_solution(bem_ctx *b, const double *u, const double *t);
+/* Store a boundary solution of ncol columns (u, t [nt][3*ncol]) without solving, e.g. from an
+ * earlier solve. */
+kfmm_status bem_set_solution(bem_ctx *b, const double *u, const double *t, int ncol);
 
 /* Interior fields from the stored boundary solution (Sec. "Computing topological
- * derivatives"): displacement [n][3] by the BIE at interior points and stress [n][6] by
- * Eq. stress_1 (Somigliana), summed over the same quadrature sources; either output may be
- * NULL.  pts [n][3] FP32; outputs FP32. */
+ * derivatives"): displacement [n][3*ncol] by the BIE at interior points and stress
+ * [n][6*ncol] by Eq. stress_1 (Somigliana), summed over the same quadrature sources, all
+ * stored columns in one evaluation; either output may be NULL.  pts [n][3] FP32; outputs
+ * FP32.  FMM contexts evaluate these sums with their own interior FMM at p = max(p, 8) and
+ * M2L cutoff min(m2l_rtol, 1e-7): the stress sums are far-field dominated and their single-
+ * and double-layer parts partly cancel. */
 kfmm_status bem_interior(bem_ctx *b, const float *pts, int64_t n, float *disp, float *stress);
 
 /* Topological derivative of the compliance (Eq. deriv) and the energy density
- * 1/2 sigma:eps (integrand of Eq. functional) at interior points [n]; stress [n][6] is
- * also returned when non-NULL.  FP32. */
+ * 1/2 sigma:eps (integrand of Eq. functional) at interior points, td and energy [n][ncol];
+ * stress [n][6*ncol] is also returned when non-NULL.  FP32. */
 kfmm_status bem_topo_derivative(bem_ctx *b, const float *pts, int64_t n, float *td, float *energy,
                                 float *stress);
 

@@ -30,6 +30,7 @@ KFMM_ERR_NOT_BUILT = -6
 KFMM_ERR_INTERNAL = -7
 KFMM_DISP = 0
 KFMM_STRESS = 1
+KFMM_TD = 2
 KFMM_FP32 = 0
 KFMM_FP64 = 1
 
@@ -74,12 +75,17 @@ _sig = {
     "kfmm_direct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]),
     "kfmm_direct_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_int,
                                            _vp]),
+    "kfmm_direct_hi": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_double, _vp]),
     "kfmm_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(kfmm_stats)]),
     "kfmm_export_tree": (ctypes.c_int, [_vp] + [_vp] * 7),
     "kfmm_export_list": (ctypes.c_int, [_vp, ctypes.c_char, _vp, _vp, ctypes.POINTER(_i64)]),
     "kfmm_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "kfmm_get_phase_times": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    "kfmm_measure_fp32_peak": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_int32)]),
     "kfmm_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "kfmm_shard_plan": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp]),
+    "kfmm_shard_let": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "kfmm_last_error": (ctypes.c_char_p, [_vp]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -186,6 +192,14 @@ def kfmm_direct_noalloc(ctx, trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out, kin
     return out
 
 
+def kfmm_direct_hi(ctx, trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out, near_radius=0.0):
+    """FP64-grade displacement sum at FP32 rate (FP64 arrays); pairs closer than near_radius
+    are summed wholly in FP64."""
+    _check(ctx, _lib.kfmm_direct_hi(ctx, _ptr(trg_xyz), _nrows(trg_xyz), _ptr(src_xyz), _ptr(src_nrm),
+                                    _nrows(src_xyz), _ptr(sl_den), _ptr(dl_den), float(near_radius), _ptr(out)))
+    return out
+
+
 def kfmm_get_stats(ctx) -> dict:
     st = kfmm_stats()
     _check(ctx, _lib.kfmm_get_stats(ctx, ctypes.byref(st)))
@@ -213,6 +227,58 @@ def kfmm_export_list(ctx, which: str):
     return off, items[: n.value]
 
 
+# ------------------------------------------------------------- partition over several GPUs
+class kfmm_tree_view(ctypes.Structure):
+    _fields_ = [("n_boxes", ctypes.c_int32)] + [(f, ctypes.c_void_p) for f in (
+        "level", "anchor", "parent", "box_src", "box_trg", "u_off", "u_idx", "v_off", "v_idx", "w_off", "w_idx",
+        "x_off", "x_idx")]
+
+
+class TreeView:
+    """Host arrays of a tree (kfmm_export_tree / kfmm_export_list layout) and the C view of
+    them.  tree: dict with level, anchor, parent, src, trg; lists: {"U": (off, idx), ...}."""
+
+    def __init__(self, tree, lists):
+        c = lambda a: np.ascontiguousarray(a, dtype=np.int32)  # noqa: E731
+        self.arrays = {"level": c(tree["level"]), "anchor": c(tree["anchor"]), "parent": c(tree["parent"]),
+                       "box_src": c(tree["src"]), "box_trg": c(tree["trg"])}
+        for k in "UVWX":
+            off, idx = lists[k]
+            self.arrays[k.lower() + "_off"] = c(off)
+            self.arrays[k.lower() + "_idx"] = c(idx) if len(idx) else np.zeros(1, np.int32)
+        self.n_boxes = len(self.arrays["level"])
+        self.view = kfmm_tree_view(self.n_boxes, *[self.arrays[f].ctypes.data for f, _ in kfmm_tree_view._fields_[1:]])
+
+    @classmethod
+    def from_context(cls, ctx):
+        """The tree of a built context."""
+        return cls(kfmm_export_tree(ctx), {k: kfmm_export_list(ctx, k) for k in "UVWX"})
+
+
+def kfmm_shard_plan(tv: TreeView, n_ranks: int, box_cost=None):
+    """(box_owner [n_boxes], leaf_order [n_leaves], rank_cost [n_ranks])."""
+    owner = np.zeros(tv.n_boxes, np.int32)
+    order = np.zeros(tv.n_boxes, np.int32)
+    rc = np.zeros(n_ranks, np.float64)
+    cost = None if box_cost is None else np.ascontiguousarray(box_cost, dtype=np.float64)
+    _check(None, _lib.kfmm_shard_plan(ctypes.byref(tv.view), int(n_ranks), _ptr(cost), _ptr(owner), _ptr(order),
+                                      _ptr(rc)))
+    n_leaves = int(np.sum(~np.isin(np.arange(tv.n_boxes), tv.arrays["parent"])))
+    return owner, order[:n_leaves], rc
+
+
+def kfmm_shard_let(tv: TreeView, box_owner, rank: int):
+    """Locally essential tree of `rank`: (source boxes, upward boxes, shared boxes)."""
+    own = np.ascontiguousarray(box_owner, dtype=np.int32)
+    ns, nu, nh = _i64(0), _i64(0), _i64(0)
+    _check(None, _lib.kfmm_shard_let(ctypes.byref(tv.view), _ptr(own), int(rank), None, ctypes.byref(ns), None,
+                                     ctypes.byref(nu), None, ctypes.byref(nh)))
+    s, u, h = (np.zeros(max(1, n.value), np.int32) for n in (ns, nu, nh))
+    _check(None, _lib.kfmm_shard_let(ctypes.byref(tv.view), _ptr(own), int(rank), _ptr(s), ctypes.byref(ns), _ptr(u),
+                                     ctypes.byref(nu), _ptr(h), ctypes.byref(nh)))
+    return s[:ns.value], u[:nu.value], h[:nh.value]
+
+
 PHASES = ("tree", "pack", "s2m", "up_pinv", "m2m", "m2l", "p2l", "down", "eval", "m2l_basis", "tree_split",
           "tree_lists", "plans")
 
@@ -227,6 +293,13 @@ def kfmm_get_phase_times(ctx, reset: bool = False) -> dict:
     cnt = np.zeros(len(PHASES), np.int64)
     _check(ctx, _lib.kfmm_get_phase_times(ctx, _ptr(ms), _ptr(cnt), int(bool(reset))))
     return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+
+def kfmm_measure_fp32_peak(ctx) -> dict:
+    """Measured FP32 FMA throughput of the context's GPU: {"tflops", "ms", "n_sms"}."""
+    tf, ms, sms = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int32(0)
+    _check(ctx, _lib.kfmm_measure_fp32_peak(ctx, ctypes.byref(tf), ctypes.byref(ms), ctypes.byref(sms)))
+    return {"tflops": tf.value, "ms": ms.value, "n_sms": sms.value}
 
 
 def kfmm_status_str(status: int) -> str:
@@ -278,8 +351,14 @@ class Kfmm:
     def direct(self, trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out, kind=KFMM_DISP, precision=KFMM_FP32):
         return kfmm_direct(self.handle, trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out, kind, precision)
 
+    def direct_hi(self, trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out, near_radius=0.0):
+        return kfmm_direct_hi(self.handle, trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out, near_radius)
+
     def stats(self):
         return kfmm_get_stats(self.handle)
+
+    def measure_fp32_peak(self):
+        return kfmm_measure_fp32_peak(self.handle)
 
     def set_profiling(self, enable=True):
         kfmm_set_profiling(self.handle, enable)
@@ -297,6 +376,7 @@ class Kfmm:
 # ------------------------------------------------------------------------------- BEM layer
 BEM_FMM = 0
 BEM_DIRECT_FP64 = 1
+BEM_DIRECT_HI = 2
 
 
 class bem_solve_opts(ctypes.Structure):
@@ -318,12 +398,12 @@ _bsig = {
     "bem_destroy": (ctypes.c_int, [_vp]),
     "bem_set_material": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
     "bem_set_stream": (ctypes.c_int, [_vp, _vp]),
-    "bem_set_bc": (ctypes.c_int, [_vp, _vp, _vp]),
+    "bem_set_bc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     "bem_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bem_matvec": (ctypes.c_int, [_vp, _vp, _vp]),
     "bem_rhs": (ctypes.c_int, [_vp, _vp]),
     "bem_solve": (ctypes.c_int, [_vp, ctypes.POINTER(bem_solve_opts), _vp, _vp, ctypes.POINTER(bem_stats)]),
-    "bem_set_solution": (ctypes.c_int, [_vp, _vp, _vp]),
+    "bem_set_solution": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     "bem_interior": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "bem_topo_derivative": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "bem_last_error": (ctypes.c_char_p, [_vp]),
@@ -362,8 +442,16 @@ def bem_set_stream(h, stream):
     _bcheck(h, _lib.bem_set_stream(h, getattr(stream, "cuda_stream", stream)))
 
 
+def _ncol3(a):
+    """Columns of a [nt, 3*ncol] array."""
+    if a.ndim != 2 or a.shape[1] % 3:
+        raise ValueError("expected an array of shape [nt, 3*ncol]")
+    return a.shape[1] // 3
+
+
 def bem_set_bc(h, known_is_disp, values):
-    _bcheck(h, _lib.bem_set_bc(h, _ptr(known_is_disp), _ptr(values)))
+    """known_is_disp [nt,3] uint8; values [nt,3*ncol] float64 (ncol load cases)."""
+    _bcheck(h, _lib.bem_set_bc(h, _ptr(known_is_disp), _ptr(values), _ncol3(values)))
 
 
 def bem_apply(h, u, t, out):
@@ -383,13 +471,14 @@ def bem_rhs(h, out):
 
 def bem_solve(h, u=None, t=None, tol=1e-6, restart=30, maxit=1000, x0=None, raise_on_fail=True, refine=False,
               inner_tol=1e-3, max_outer=30):
-    """GMRES solve of Eq. num2; fills u, t [nt,3] float64 (host or device). With refine=True
-    (FMM contexts): mixed-precision iterative refinement, FP64 direct residuals, FMM
-    corrections. Returns stats dict."""
+    """GMRES solve of Eq. num2; fills u, t [nt,3] float64 (host or device). With refine=True or 1
+    (FMM contexts): mixed-precision iterative refinement, FP64-grade residuals by the
+    compensated direct sum, FMM corrections; refine=2: the same with FP64 direct residuals.
+    Returns stats dict."""
     o = bem_solve_opts()
     _lib.bem_default_solve_opts(ctypes.byref(o))
     o.tol, o.restart, o.maxit = float(tol), int(restart), int(maxit)
-    o.refine, o.inner_tol, o.max_outer = int(bool(refine)), float(inner_tol), int(max_outer)
+    o.refine, o.inner_tol, o.max_outer = int(refine), float(inner_tol), int(max_outer)
     o.x0 = _ptr(x0)
     st = bem_stats()
     status = _lib.bem_solve(h, ctypes.byref(o), _ptr(u), _ptr(t), ctypes.byref(st))
@@ -399,7 +488,8 @@ def bem_solve(h, u=None, t=None, tol=1e-6, restart=30, maxit=1000, x0=None, rais
 
 
 def bem_set_solution(h, u, t):
-    _bcheck(h, _lib.bem_set_solution(h, _ptr(u), _ptr(t)))
+    """u, t [nt, 3*ncol] float64."""
+    _bcheck(h, _lib.bem_set_solution(h, _ptr(u), _ptr(t), _ncol3(u)))
 
 
 def bem_interior(h, pts, disp=None, stress=None):

@@ -19,9 +19,31 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+bool foreign_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return false;
+    return a.type == cudaMemoryTypeDevice && a.device != cur;
+}
+
+const void *first_foreign(std::initializer_list<const void *> ptrs)
+{
+    for (const void *p : ptrs)
+        if (foreign_device_ptr(p)) return p;
+    return nullptr;
+}
+
 // Device copy of a possibly-host array (returned pointer is p itself for device memory).
 static kfmm_status to_device(kfmm_ctx *ctx, DevBuf &buf, const void *p, size_t bytes, const void **out)
 {
+    if (foreign_device_ptr(p))
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "an array is device memory of another GPU than the context's");
     if (!p || is_device_ptr(p)) {
         *out = p;
         return KFMM_OK;
@@ -77,6 +99,10 @@ kfmm_status kfmm_create(kfmm_ctx **out, const kfmm_options *opt)
     kfmm_ctx *c = new (std::nothrow) kfmm_ctx();
     if (!c) return KFMM_ERR_OOM;
     c->opt = o;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device) == cudaSuccess && sms > 0)
+        c->n_sms = sms;
+    cudaGetLastError();
     if (o.eval_item_cost > 0) {
         c->tune.eval_cost = (float)o.eval_item_cost;
         c->tune.eval_done = true;  // fixed by the caller
@@ -182,23 +208,33 @@ kfmm_status kfmm_eval(kfmm_ctx *ctx, const float *sl_den, const float *dl_den, i
     if (!ctx) return KFMM_ERR_INVALID_ARG;
     ctx->err.clear();
     if (!ctx->tree.built) return ctx->fail(KFMM_ERR_NOT_BUILT, "eval before build");
-    if ((!sl_den && !dl_den) || !out || ncol < 1 || ncol > 32 || (kind != KFMM_DISP && kind != KFMM_STRESS))
+    if ((!sl_den && !dl_den) || !out || ncol < 1 || ncol > 32 ||
+        (kind != KFMM_DISP && kind != KFMM_STRESS && kind != KFMM_TD))
         return ctx->fail(KFMM_ERR_INVALID_ARG, "eval: need a density, an output, 1 <= ncol <= 32, a valid kind");
     if (dl_den && !ctx->tree.has_nrm)
         return ctx->fail(KFMM_ERR_INVALID_ARG, "eval: double-layer density but the tree was built without normals");
     if (cudaSetDevice(ctx->opt.device) != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, "cudaSetDevice");
     const int64_t ns = ctx->tree.nsrc, nt = ctx->tree.ntrg;
-    const int nout = (kind == KFMM_DISP ? 3 : 6) * ncol;
+    const int nout = (kind == KFMM_DISP ? 3 : (kind == KFMM_STRESS ? 6 : 2)) * ncol;
     const void *dsl, *ddl;
     KF_TRY(to_device(ctx, ctx->work.stage_in[0], sl_den, sizeof(float) * 3 * ncol * ns, &dsl));
     KF_TRY(to_device(ctx, ctx->work.stage_in[1], dl_den, sizeof(float) * 3 * ncol * ns, &ddl));
+    if (foreign_device_ptr(out))
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "eval: out is device memory of another GPU than the context's");
     float *dout = out;
     const bool host_out = !is_device_ptr(out);
     if (host_out) {
         KF_CUDA(ctx->work.stage_out.ensure(sizeof(float) * nout * nt));
         dout = ctx->work.stage_out.as<float>();
     }
-    KF_TRY(fmm_eval(ctx, (const float *)dsl, (const float *)ddl, ncol, kind, dout));
+    if (kind == KFMM_TD) {
+        // the stress sum (Eq. stress_1's kernels), then Eq. deriv and the energy density
+        KF_CUDA(ctx->work.td_stress.ensure(sizeof(float) * 6 * ncol * nt));
+        KF_TRY(fmm_eval(ctx, (const float *)dsl, (const float *)ddl, ncol, KFMM_STRESS, ctx->work.td_stress.as<float>()));
+        KF_TRY(fmm_td(ctx, ctx->work.td_stress.as<float>(), nt, ncol, dout));
+    } else {
+        KF_TRY(fmm_eval(ctx, (const float *)dsl, (const float *)ddl, ncol, kind, dout));
+    }
     if (host_out) {
         KF_CUDA(cudaMemcpyAsync(out, dout, sizeof(float) * nout * nt, cudaMemcpyDeviceToHost, ctx->stream));
         KF_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -216,7 +252,42 @@ kfmm_status kfmm_direct(kfmm_ctx *ctx, int precision, const void *trg_xyz, int64
         (dl_den && !src_nrm))
         return ctx->fail(KFMM_ERR_INVALID_ARG, "direct: bad arguments");
     if (cudaSetDevice(ctx->opt.device) != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, "cudaSetDevice");
+    if (first_foreign({trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out}))
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "direct: an array is device memory of another GPU than the context's");
     return direct_sum(ctx, precision, trg_xyz, ntrg, src_xyz, src_nrm, nsrc, sl_den, dl_den, kind, out);
+}
+
+kfmm_status kfmm_direct_hi(kfmm_ctx *ctx, const double *trg_xyz, int64_t ntrg, const double *src_xyz,
+                           const double *src_nrm, int64_t nsrc, const double *sl_den, const double *dl_den,
+                           double near_radius, double *out)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!trg_xyz || !src_xyz || ntrg < 1 || nsrc < 1 || (!sl_den && !dl_den) || !out || (dl_den && !src_nrm) ||
+        !(near_radius >= 0.0) || !std::isfinite(near_radius))
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "direct_hi: bad arguments");
+    if (cudaSetDevice(ctx->opt.device) != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, "cudaSetDevice");
+    if (first_foreign({trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out}))
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "direct_hi: an array is device memory of another GPU than the context's");
+    DevBuf a, b, c, d, e, o;
+    const void *dt, *ds, *dn, *dsl, *ddl;
+    KF_TRY(to_device(ctx, a, trg_xyz, sizeof(double) * 3 * ntrg, &dt));
+    KF_TRY(to_device(ctx, b, src_xyz, sizeof(double) * 3 * nsrc, &ds));
+    KF_TRY(to_device(ctx, c, src_nrm, sizeof(double) * 3 * nsrc, &dn));
+    KF_TRY(to_device(ctx, d, sl_den, sizeof(double) * 3 * nsrc, &dsl));
+    KF_TRY(to_device(ctx, e, dl_den, sizeof(double) * 3 * nsrc, &ddl));
+    double *dout = out;
+    const bool host_out = !is_device_ptr(out);
+    if (host_out) {
+        KF_CUDA(o.ensure(sizeof(double) * 3 * ntrg));
+        dout = o.as<double>();
+    }
+    KF_TRY(direct_hi_sum(ctx, (const double *)dt, ntrg, (const double *)ds, (const double *)dn, nsrc,
+                         (const double *)dsl, (const double *)ddl, near_radius, dout));
+    if (host_out) KF_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * 3 * ntrg, cudaMemcpyDeviceToHost, ctx->stream));
+    // staged inputs are freed at return; make sure the stream no longer uses them
+    if (host_out || a.p || b.p || c.p || d.p || e.p) KF_CUDA(cudaStreamSynchronize(ctx->stream));
+    return KFMM_OK;
 }
 
 kfmm_status kfmm_get_stats(const kfmm_ctx *ctx, kfmm_stats *st)
@@ -343,6 +414,15 @@ kfmm_status kfmm_selftest_bounded_wait(kfmm_ctx *ctx, int64_t polls)
     ctx->err.clear();
     if (cudaSetDevice(ctx->opt.device) != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, "cudaSetDevice");
     return selftest_bounded_wait(ctx, (long long)polls);
+}
+
+kfmm_status kfmm_measure_fp32_peak(kfmm_ctx *ctx, double *tflops, double *ms, int32_t *n_sms)
+{
+    if (!ctx || !tflops) return KFMM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (cudaSetDevice(ctx->opt.device) != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, "cudaSetDevice");
+    if (n_sms) *n_sms = ctx->n_sms;
+    return measure_fp32_peak(ctx, tflops, ms);
 }
 
 const char *kfmm_status_str(kfmm_status s)

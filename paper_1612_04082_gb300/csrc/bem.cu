@@ -2,9 +2,12 @@
 // two-pass matvec of Sec. "Matrix-vector products", restarted GMRES with FP64 vectors on
 // the device, and the interior fields of Sec. "Computing topological derivatives"
 // (Eq. stress_1, Eq. deriv, integrand of Eq. functional).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <memory>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 #include "kelvin.cuh"
@@ -24,7 +27,8 @@ struct bem_ctx {
     kfmm_ctx *vol = nullptr;   // FMM over quadrature sources -> interior points
     bool surf_built = false, have_bc = false, have_sol = false;
     double setup_G = -1, setup_nu = -1;
-    int matvecs = 0, matvecs_hi = 0;  // FMM and FP64 direct operator applications
+    int matvecs = 0, matvecs_hi = 0;  // FMM and FP64-grade (direct) operator applications
+    double near_radius = 0;           // FP64 pairs of the compensated direct sum: 4 x longest edge
     DevBuf d, rhs_hi;                 // GMRES-IR: correction, outer residual
     DevBuf verts, tris;
     DevBuf q32, qn32;        // float [16 nt][3]: quadrature points, element normals
@@ -32,11 +36,13 @@ struct bem_ctx {
     DevBuf qw;               // double [16 nt]: weights (sum to the element area)
     DevBuf cen32, cen64;     // centroids float / double [nt][3]
     DevBuf corrU, corrT;     // double [nt][9]: analytic self block minus own quadrature terms
-    DevBuf mask, val;        // uint8 [3 nt], double [3 nt]
-    DevBuf usol, tsol;       // double [3 nt]
+    int ncol = 1;            // density columns of the boundary conditions (load cases)
+    int sol_ncol = 1;        // columns of the stored boundary solution
+    DevBuf mask, val;        // uint8 [3 nt] (shared by the columns), double [ncol][3 nt]
+    DevBuf usol, tsol;       // double [sol_ncol][3 nt]
     DevBuf slq, dlq, fout;   // densities at quadrature points and summed field (FP32 or FP64)
     DevBuf basis;            // GMRES: (restart + 1) x n
-    DevBuf w, r, x, b, part, hdev;
+    DevBuf w, r, x, b, part, hdev, av;  // [ncol][3 nt] vectors; reduction and coefficient scratch
     DevBuf stage[4], pts64, out64;
     kfmm_status fail(kfmm_status c, const std::string &m) {
         err = m;
@@ -193,18 +199,23 @@ __global__ void bem_setup_kernel(int64_t nt, const double *__restrict__ verts, c
     }
 }
 
-// Densities at the quadrature points for M(u, t): sl = -t_k w, dl = u_k w.
-// mode 0: u, t given (either may be NULL); mode 1: from unknowns x and the mask (Eq. num2);
-// mode 2: from the prescribed values and the mask (right-hand side, sign applied later).
+// Densities at the quadrature points for columns c0 .. c0 + cn - 1 of M(u, t): sl = -t_k w,
+// dl = u_k w, written [16 nt][3 cn].  mode 0: u, t given ([nt][3], one column; either may be
+// NULL); mode 1: from the unknowns x [ncol][3 nt] and the mask (Eq. num2); mode 2: from the
+// prescribed values [ncol][3 nt] and the mask (right-hand side, sign applied later).
 template <typename R>
-__global__ void bem_density_kernel(int64_t nt, int mode, const double *__restrict__ u, const double *__restrict__ t,
-                                   const double *__restrict__ x, const uint8_t *__restrict__ mask,
-                                   const double *__restrict__ qw, R *__restrict__ sl, R *__restrict__ dl)
+__global__ void bem_density_kernel(int64_t nt, int mode, int c0, int cn, const double *__restrict__ u,
+                                   const double *__restrict__ t, const double *__restrict__ x,
+                                   const uint8_t *__restrict__ mask, const double *__restrict__ qw,
+                                   R *__restrict__ sl, R *__restrict__ dl)
 {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= 16 * nt) return;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 16 * nt * cn) return;
+    const int64_t j = e / cn;
+    const int cc = (int)(e % cn);
     const int64_t k = j / 16;
     const double w = qw[j];
+    const double *xc = x ? x + (int64_t)(c0 + cc) * 3 * nt : nullptr;
     for (int c = 0; c < 3; ++c) {
         double uu = 0.0, tt = 0.0;
         const int64_t i = 3 * k + c;
@@ -212,26 +223,31 @@ __global__ void bem_density_kernel(int64_t nt, int mode, const double *__restric
             uu = u ? u[i] : 0.0;
             tt = t ? t[i] : 0.0;
         } else if (mode == 1) {
-            if (mask[i]) tt = x[i];
-            else uu = x[i];
+            if (mask[i]) tt = xc[i];
+            else uu = xc[i];
         } else {
-            if (mask[i]) uu = x[i];
-            else tt = x[i];
+            if (mask[i]) uu = xc[i];
+            else tt = xc[i];
         }
-        sl[3 * j + c] = (R)(-tt * w);
-        dl[3 * j + c] = (R)(uu * w);
+        sl[j * 3 * cn + 3 * cc + c] = (R)(-tt * w);
+        dl[j * 3 * cn + 3 * cc + c] = (R)(uu * w);
     }
 }
 
-// out_l = sign * (f_l + 1/2 u_l + corrT_l u_l - corrU_l t_l)  (local pass), FP64 output.
+// Local pass for columns c0 .. c0 + cn - 1: out_l = sign * (f_l + 1/2 u_l + corrT_l u_l -
+// corrU_l t_l), with f [nt][3 cn] the summed field, FP64 output [ncol][3 nt] (mode 0: [nt][3]).
 template <typename R>
-__global__ void bem_post_kernel(int64_t nt, int mode, double sign, const R *__restrict__ f, const double *__restrict__ u,
-                                const double *__restrict__ t, const double *__restrict__ x,
-                                const uint8_t *__restrict__ mask, const double *__restrict__ cU,
-                                const double *__restrict__ cT, double *__restrict__ out)
+__global__ void bem_post_kernel(int64_t nt, int mode, int c0, int cn, double sign, const R *__restrict__ f,
+                                const double *__restrict__ u, const double *__restrict__ t,
+                                const double *__restrict__ x, const uint8_t *__restrict__ mask,
+                                const double *__restrict__ cU, const double *__restrict__ cT, double *__restrict__ out)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nt) return;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nt * cn) return;
+    const int64_t k = e / cn;
+    const int cc = (int)(e % cn);
+    const int64_t col = (int64_t)(c0 + cc) * 3 * nt;
+    const double *xc = x ? x + col : nullptr;
     double uu[3], tt[3];
     for (int c = 0; c < 3; ++c) {
         const int64_t i = 3 * k + c;
@@ -240,63 +256,87 @@ __global__ void bem_post_kernel(int64_t nt, int mode, double sign, const R *__re
             uu[c] = u ? u[i] : 0.0;
             tt[c] = t ? t[i] : 0.0;
         } else if (mode == 1) {
-            if (mask[i]) tt[c] = x[i];
-            else uu[c] = x[i];
+            if (mask[i]) tt[c] = xc[i];
+            else uu[c] = xc[i];
         } else {
-            if (mask[i]) uu[c] = x[i];
-            else tt[c] = x[i];
+            if (mask[i]) uu[c] = xc[i];
+            else tt[c] = xc[i];
         }
     }
+    double *o = out + (mode == 0 ? 0 : col);
     for (int a = 0; a < 3; ++a) {
-        double v = (double)f[3 * k + a] + 0.5 * uu[a];
+        double v = (double)f[k * 3 * cn + 3 * cc + a] + 0.5 * uu[a];
         for (int c = 0; c < 3; ++c) v += cT[9 * k + 3 * a + c] * uu[c] - cU[9 * k + 3 * a + c] * tt[c];
-        out[3 * k + a] = sign * v;
+        o[3 * k + a] = sign * v;
     }
 }
 
 // ------------------------------------------------------------------------------------
-// GMRES vector kernels (FP64)
+// GMRES vector kernels (FP64).  Vectors of all density columns are stored one after the
+// other ([ncol][n]); blockIdx.y is the column.
 // ------------------------------------------------------------------------------------
 constexpr int kVecBlocks = 2 * kNumSMs;
 constexpr int kVecThreads = 256;
 
-// part[i * nblocks + block] = partial sum of V_i . w
+// part[(col * k + i) * gridDim.x + block] = partial sum of V_i[col] . w[col]; basis vector i
+// starts at V + i * ldv, column col at + col * n
 __global__ void mdot_kernel(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ w, int64_t n,
                             double *__restrict__ part)
 {
     __shared__ double red[kVecThreads / 32];
+    const int col = blockIdx.y;
+    const double *wc = w + (int64_t)col * n;
     for (int i = 0; i < k; ++i) {
-        const double *v = V + (int64_t)i * ldv;
+        const double *v = V + (int64_t)i * ldv + (int64_t)col * n;
         double s = 0.0;
         for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-            s += v[e] * w[e];
+            s += v[e] * wc[e];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int q = 0; q < kVecThreads / 32; ++q) t += red[q];
-            part[(int64_t)i * gridDim.x + blockIdx.x] = t;
+            part[((int64_t)col * k + i) * gridDim.x + blockIdx.x] = t;
         }
         __syncthreads();
     }
 }
 
-// w += sign * sum_i h_i V_i
-__global__ void maxpy_kernel(double *__restrict__ w, const double *__restrict__ V, int64_t ldv, int k,
-                             const double *__restrict__ h, double sign, int64_t n)
+// out[e] = sum of part[e * nb .. e * nb + nb - 1], one warp per entry, FP64, in a fixed order
+__global__ void reduce_parts_kernel(const double *__restrict__ part, int nb, int total, double *__restrict__ out)
 {
+    const int e = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (e >= total) return;
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int q = lane; q < nb; q += 32) s += part[(int64_t)e * nb + q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[e] = s;
+}
+
+// w[col] += sign * sum_i h[col * hld + i] V_i[col]
+__global__ void maxpy_kernel(double *__restrict__ w, const double *__restrict__ V, int64_t ldv, int k,
+                             const double *__restrict__ h, int hld, double sign, int64_t n)
+{
+    const int col = blockIdx.y;
+    const double *hc = h + (int64_t)col * hld;
+    double *wc = w + (int64_t)col * n;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int i = 0; i < k; ++i) s += h[i] * V[(int64_t)i * ldv + e];
-        w[e] += sign * s;
+        for (int i = 0; i < k; ++i) s += hc[i] * V[(int64_t)i * ldv + (int64_t)col * n + e];
+        wc[e] += sign * s;
     }
 }
 
-__global__ void scale_copy_kernel(double *__restrict__ dst, const double *__restrict__ src, double a, int64_t n)
+// dst[col] = a[col] * src[col]
+__global__ void scale_copy_kernel(double *__restrict__ dst, const double *__restrict__ src, const double *__restrict__ a,
+                                  int64_t n)
 {
+    const int col = blockIdx.y;
+    const double s = a[col];
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        dst[e] = a * src[e];
+        dst[(int64_t)col * n + e] = s * src[(int64_t)col * n + e];
 }
 
 __global__ void sub_kernel(double *__restrict__ dst, const double *__restrict__ a, const double *__restrict__ b,
@@ -306,44 +346,58 @@ __global__ void sub_kernel(double *__restrict__ dst, const double *__restrict__ 
         dst[e] = a[e] - b[e];
 }
 
-// split the unknowns into the boundary u and t (Eq. num2 back to Eq. num)
-__global__ void split_kernel(int64_t n, const double *__restrict__ x, const uint8_t *__restrict__ mask,
+__global__ void add_kernel(double *__restrict__ dst, const double *__restrict__ a, int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] += a[e];
+}
+
+// [nt][3 ncol] (the ABI's layout) <-> [ncol][3 nt] (the solver's): to_cols = 1 reads src in
+// the ABI layout
+__global__ void transpose_cols_kernel(int64_t nt, int ncol, int to_cols, const double *__restrict__ src,
+                                      double *__restrict__ dst)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * nt * ncol) return;
+    const int64_t k = e / (3 * ncol);
+    const int r = (int)(e % (3 * ncol));
+    const int col = r / 3, c = r % 3;
+    const int64_t solver = (int64_t)col * 3 * nt + 3 * k + c;
+    if (to_cols) dst[solver] = src[e];
+    else dst[e] = src[solver];
+}
+
+// split the unknowns of every column into the boundary u and t (Eq. num2 back to Eq. num)
+__global__ void split_kernel(int64_t n, int ncol, const double *__restrict__ x, const uint8_t *__restrict__ mask,
                              const double *__restrict__ val, double *__restrict__ u, double *__restrict__ t)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * ncol) return;
+    const int64_t i = e % n;
     if (mask[i]) {
-        u[i] = val[i];
-        t[i] = x[i];
+        u[e] = val[e];
+        t[e] = x[e];
     } else {
-        u[i] = x[i];
-        t[i] = val[i];
+        u[e] = x[e];
+        t[e] = val[e];
     }
 }
 
-// interior sources: sl = t_k w, dl = -u_k w (FP32)
-__global__ void interior_density_kernel(int64_t nt, const double *__restrict__ u, const double *__restrict__ t,
-                                        const double *__restrict__ qw, float *__restrict__ sl, float *__restrict__ dl)
+// interior sources of columns c0 .. c0 + cn - 1: sl = t_k w, dl = -u_k w, [16 nt][3 cn]
+template <typename R>
+__global__ void interior_density_kernel(int64_t nt, int c0, int cn, const double *__restrict__ u,
+                                        const double *__restrict__ t, const double *__restrict__ qw, R *__restrict__ sl,
+                                        R *__restrict__ dl)
 {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= 16 * nt) return;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 16 * nt * cn) return;
+    const int64_t j = e / cn;
+    const int cc = (int)(e % cn);
     const int64_t k = j / 16;
+    const int64_t col = (int64_t)(c0 + cc) * 3 * nt;
     for (int c = 0; c < 3; ++c) {
-        sl[3 * j + c] = (float)(t[3 * k + c] * qw[j]);
-        dl[3 * j + c] = (float)(-u[3 * k + c] * qw[j]);
-    }
-}
-
-__global__ void interior_density64_kernel(int64_t nt, const double *__restrict__ u, const double *__restrict__ t,
-                                          const double *__restrict__ qw, double *__restrict__ sl,
-                                          double *__restrict__ dl)
-{
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= 16 * nt) return;
-    const int64_t k = j / 16;
-    for (int c = 0; c < 3; ++c) {
-        sl[3 * j + c] = t[3 * k + c] * qw[j];
-        dl[3 * j + c] = -u[3 * k + c] * qw[j];
+        sl[j * 3 * cn + 3 * cc + c] = (R)(t[col + 3 * k + c] * qw[j]);
+        dl[j * 3 * cn + 3 * cc + c] = (R)(-u[col + 3 * k + c] * qw[j]);
     }
 }
 
@@ -353,24 +407,29 @@ __global__ void f2d_kernel(int64_t n, const float *__restrict__ a, double *__res
     if (i < n) b[i] = a[i];
 }
 
-__global__ void d2f_kernel(int64_t n, const double *__restrict__ a, float *__restrict__ b)
+// b[i][ld * ... ]: FP64 [n][no] into columns col of FP32 [n][no * ncol]
+__global__ void d2f_cols_kernel(int64_t n, int no, int ncol, int col, const double *__restrict__ a,
+                                float *__restrict__ b)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (float)a[i];
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * no) return;
+    const int64_t i = e / no;
+    b[i * no * ncol + (int64_t)no * col + e % no] = (float)a[e];
 }
 
 // Eq. deriv: D^T = 3/(4E) (1-nu)/(7-5nu) [10 (1+nu) s:s - (1+5nu) (tr s)^2];
-// energy density 1/2 s:eps with eps = ((1+nu) s - nu tr(s) I) / E.
-__global__ void topo_kernel(int64_t n, const float *__restrict__ s6, float E, float nu, float *__restrict__ td,
-                            float *__restrict__ energy)
+// energy density 1/2 s:eps with eps = ((1+nu) s - nu tr(s) I) / E.  s6 [n][6 ncol] ->
+// td, energy [n][ncol].
+__global__ void topo_kernel(int64_t n, int ncol, const float *__restrict__ s6, float E, float nu,
+                            float *__restrict__ td, float *__restrict__ energy)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float *s = s6 + 6 * i;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * ncol) return;
+    const float *s = s6 + 6 * e;
     const float tr = s[0] + s[1] + s[2];
     const float ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + 2.f * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
-    if (td) td[i] = 0.75f / E * (1.f - nu) / (7.f - 5.f * nu) * (10.f * (1.f + nu) * ss - (1.f + 5.f * nu) * tr * tr);
-    if (energy) energy[i] = 0.5f * ((1.f + nu) * ss - nu * tr * tr) / E;
+    if (td) td[e] = 0.75f / E * (1.f - nu) / (7.f - 5.f * nu) * (10.f * (1.f + nu) * ss - (1.f + 5.f * nu) * tr * tr);
+    if (energy) energy[e] = 0.5f * ((1.f + nu) * ss - nu * tr * tr) / E;
 }
 
 unsigned g1(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -439,10 +498,12 @@ static kfmm_status bem_setup(bem_ctx *b)
     return KFMM_OK;
 }
 
-// M(u, t) (mode 0), A x (mode 1) or B y (mode 2; sign -1) into out (device, FP64 [nt][3]),
-// with the context's operator, or with the given one (which = BEM_FMM or BEM_DIRECT_FP64).
+// M(u, t) (mode 0, one column), A x (mode 1) or B y (mode 2; sign -1) for `nc` density
+// columns into out (device, FP64 [nc][3 nt]; mode 0: [nt][3]), with the context's operator or
+// the given one (a bem_operator).  The FMM sums all columns in one evaluation; the direct
+// operators take one column at a time.
 static kfmm_status bem_op_apply(bem_ctx *b, int mode, const double *u, const double *t, const double *x,
-                                double *out, int which = -1)
+                                double *out, int which = -1, int nc = 1)
 {
     BK_TRY(bem_setup(b));
     const int64_t nt = b->nt, nq = 16 * nt;
@@ -451,258 +512,352 @@ static kfmm_status bem_op_apply(bem_ctx *b, int mode, const double *u, const dou
     if (which < 0) which = b->op;
     if (which == BEM_FMM) {
         ++b->matvecs;
-        BK_CUDA(b->slq.ensure(sizeof(float) * 3 * nq));
-        BK_CUDA(b->dlq.ensure(sizeof(float) * 3 * nq));
-        BK_CUDA(b->fout.ensure(sizeof(float) * 3 * nt));
-        bem_density_kernel<float><<<g1(nq), 256, 0, b->stream>>>(nt, mode, u, t, x, mask, b->qw.as<double>(),
-                                                                 b->slq.as<float>(), b->dlq.as<float>());
+        BK_CUDA(b->slq.ensure(sizeof(float) * 3 * nq * nc));
+        BK_CUDA(b->dlq.ensure(sizeof(float) * 3 * nq * nc));
+        BK_CUDA(b->fout.ensure(sizeof(float) * 3 * nt * nc));
+        bem_density_kernel<float><<<g1(nq * nc), 256, 0, b->stream>>>(nt, mode, 0, nc, u, t, x, mask,
+                                                                      b->qw.as<double>(), b->slq.as<float>(),
+                                                                      b->dlq.as<float>());
         BK_LAUNCH();
-        BK_FMM(kfmm_eval(b->surf, b->slq.as<float>(), b->dlq.as<float>(), 1, KFMM_DISP, b->fout.as<float>()));
-        bem_post_kernel<float><<<g1(nt), 256, 0, b->stream>>>(nt, mode, sign, b->fout.as<float>(), u, t, x, mask,
-                                                              b->corrU.as<double>(), b->corrT.as<double>(), out);
+        BK_FMM(kfmm_eval(b->surf, b->slq.as<float>(), b->dlq.as<float>(), nc, KFMM_DISP, b->fout.as<float>()));
+        bem_post_kernel<float><<<g1(nt * nc), 256, 0, b->stream>>>(nt, mode, 0, nc, sign, b->fout.as<float>(), u, t,
+                                                                   x, mask, b->corrU.as<double>(),
+                                                                   b->corrT.as<double>(), out);
         BK_LAUNCH();
-    } else {
+        return KFMM_OK;
+    }
+    BK_CUDA(b->slq.ensure(sizeof(double) * 3 * nq));
+    BK_CUDA(b->dlq.ensure(sizeof(double) * 3 * nq));
+    BK_CUDA(b->fout.ensure(sizeof(double) * 3 * nt));
+    for (int c = 0; c < nc; ++c) {
         ++b->matvecs_hi;
-        BK_CUDA(b->slq.ensure(sizeof(double) * 3 * nq));
-        BK_CUDA(b->dlq.ensure(sizeof(double) * 3 * nq));
-        BK_CUDA(b->fout.ensure(sizeof(double) * 3 * nt));
-        bem_density_kernel<double><<<g1(nq), 256, 0, b->stream>>>(nt, mode, u, t, x, mask, b->qw.as<double>(),
+        bem_density_kernel<double><<<g1(nq), 256, 0, b->stream>>>(nt, mode, c, 1, u, t, x, mask, b->qw.as<double>(),
                                                                   b->slq.as<double>(), b->dlq.as<double>());
         BK_LAUNCH();
-        BK_FMM(kfmm_direct(b->surf, KFMM_FP64, b->cen64.p, nt, b->q64.p, b->qn64.p, nq, b->slq.p, b->dlq.p, KFMM_DISP,
-                           b->fout.p));
-        bem_post_kernel<double><<<g1(nt), 256, 0, b->stream>>>(nt, mode, sign, b->fout.as<double>(), u, t, x, mask,
-                                                               b->corrU.as<double>(), b->corrT.as<double>(), out);
+        if (which == BEM_DIRECT_HI)
+            BK_FMM(kfmm_direct_hi(b->surf, b->cen64.as<double>(), nt, b->q64.as<double>(), b->qn64.as<double>(), nq,
+                                  b->slq.as<double>(), b->dlq.as<double>(), b->near_radius, b->fout.as<double>()));
+        else
+            BK_FMM(kfmm_direct(b->surf, KFMM_FP64, b->cen64.p, nt, b->q64.p, b->qn64.p, nq, b->slq.p, b->dlq.p,
+                               KFMM_DISP, b->fout.p));
+        bem_post_kernel<double><<<g1(nt), 256, 0, b->stream>>>(nt, mode, c, 1, sign, b->fout.as<double>(), u, t, x,
+                                                               mask, b->corrU.as<double>(), b->corrT.as<double>(),
+                                                               out);
         BK_LAUNCH();
     }
     return KFMM_OK;
 }
 
-// dot products V_i . w for i < k, summed on the host in FP64
-static kfmm_status mdot(bem_ctx *b, const double *V, int64_t ldv, int k, const double *w, int64_t n, double *h)
+// h[col * k + i] = V_i[col] . w[col] for i < k and every column (partial sums reduced on the
+// device in a fixed order, one read-back)
+static kfmm_status mdot(bem_ctx *b, const double *V, int64_t ldv, int k, const double *w, int nc, double *h)
 {
-    BK_CUDA(b->part.ensure(sizeof(double) * (size_t)kVecBlocks * k));
-    mdot_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(V, ldv, k, w, n, b->part.as<double>());
+    const int64_t n = 3 * b->nt;
+    const int total = nc * k;
+    BK_CUDA(b->part.ensure(sizeof(double) * ((size_t)kVecBlocks * total + total)));
+    double *part = b->part.as<double>(), *red = part + (size_t)kVecBlocks * total;
+    mdot_kernel<<<dim3(kVecBlocks, nc), kVecThreads, 0, b->stream>>>(V, ldv, k, w, n, part);
     BK_LAUNCH();
-    std::vector<double> p((size_t)kVecBlocks * k);
-    BK_CUDA(cudaMemcpyAsync(p.data(), b->part.p, sizeof(double) * p.size(), cudaMemcpyDeviceToHost, b->stream));
+    reduce_parts_kernel<<<g1(total, 8), 256, 0, b->stream>>>(part, kVecBlocks, total, red);
+    BK_LAUNCH();
+    BK_CUDA(cudaMemcpyAsync(h, red, sizeof(double) * total, cudaMemcpyDeviceToHost, b->stream));
     BK_CUDA(cudaStreamSynchronize(b->stream));
-    for (int i = 0; i < k; ++i) {
-        double s = 0.0;
-        for (int q = 0; q < kVecBlocks; ++q) s += p[(size_t)i * kVecBlocks + q];
-        h[i] = s;
-    }
     return KFMM_OK;
 }
 
-static kfmm_status maxpy(bem_ctx *b, double *w, const double *V, int64_t ldv, int k, const double *h, double sign,
-                         int64_t n)
+// w[col] += sign * sum_i h[col * hld + i] V_i[col] (h on the host)
+static kfmm_status maxpy(bem_ctx *b, double *w, const double *V, int64_t ldv, int k, const double *h, int hld,
+                         double sign, int nc)
 {
-    BK_CUDA(b->hdev.ensure(sizeof(double) * (k + 1)));
-    BK_CUDA(cudaMemcpyAsync(b->hdev.p, h, sizeof(double) * k, cudaMemcpyHostToDevice, b->stream));
-    maxpy_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(w, V, ldv, k, b->hdev.as<double>(), sign, n);
+    const int64_t n = 3 * b->nt;
+    BK_CUDA(b->hdev.ensure(sizeof(double) * (size_t)nc * hld + 8));
+    BK_CUDA(cudaMemcpyAsync(b->hdev.p, h, sizeof(double) * (size_t)nc * hld, cudaMemcpyHostToDevice, b->stream));
+    maxpy_kernel<<<dim3(kVecBlocks, nc), kVecThreads, 0, b->stream>>>(w, V, ldv, k, b->hdev.as<double>(), hld, sign,
+                                                                      n);
     BK_LAUNCH();
-    BK_CUDA(cudaStreamSynchronize(b->stream));  // h lives on the host stack
+    BK_CUDA(cudaStreamSynchronize(b->stream));  // h lives on the host
     return KFMM_OK;
 }
 
-static kfmm_status vnorm(bem_ctx *b, const double *w, int64_t n, double *out)
+// dst[col] = a[col] * src[col] (a on the host)
+static kfmm_status scale_copy(bem_ctx *b, double *dst, const double *src, const double *a, int nc)
 {
-    double s;
-    BK_TRY(mdot(b, w, n, 1, w, n, &s));
-    *out = std::sqrt(std::max(s, 0.0));
+    BK_CUDA(b->av.ensure(sizeof(double) * nc));
+    BK_CUDA(cudaMemcpyAsync(b->av.p, a, sizeof(double) * nc, cudaMemcpyHostToDevice, b->stream));
+    scale_copy_kernel<<<dim3(kVecBlocks, nc), kVecThreads, 0, b->stream>>>(dst, src, b->av.as<double>(), 3 * b->nt);
+    BK_LAUNCH();
+    BK_CUDA(cudaStreamSynchronize(b->stream));  // a lives on the host
+    return KFMM_OK;
+}
+
+static kfmm_status vnorm(bem_ctx *b, const double *w, int nc, double *out)
+{
+    std::vector<double> s(nc);
+    BK_TRY(mdot(b, w, 0, 1, w, nc, s.data()));
+    for (int c = 0; c < nc; ++c) out[c] = std::sqrt(std::max(s[c], 0.0));
     return KFMM_OK;
 }
 
 // Restarted GMRES (classical Gram-Schmidt twice, FP64 vectors) for A x = rhs with operator
-// `which`: x (device) holds the initial guess (zeroed when zero_x) and receives the
-// iterate; stops at ||rhs - A x|| <= tol * bn (true residual at every restart) or after
-// maxit inner iterations.  *iters, *rel (true residual / bn) and *conv are returned.
-static kfmm_status gmres_core(bem_ctx *b, int which, const double *rhs, double *x, bool zero_x, double bn, double tol,
-                              int m, int maxit, int *iters, double *rel_out, bool *conv_out, double *x0_rel = nullptr)
+// `which`, for nc density columns in lockstep: every Arnoldi step applies the operator to all
+// columns at once (one FMM evaluation), each column keeps its own Krylov basis, Hessenberg
+// matrix and Givens rotations.  x (device, [nc][n]) holds the initial guess (zeroed when
+// zero_x) and receives the iterate.  Column c stops extending its basis once its residual
+// estimate reaches tol[c] * bn[c] (its next basis vectors are zero, so its products are zero);
+// a restart cycle ends when no column extends; the true residual is formed at every restart.
+// Stops when every column meets its tolerance or after maxit steps.  iters, rel[c] (true
+// residual / bn[c]) and conv[c] are returned; x0_rel[c] (may be NULL) receives the initial
+// guess's relative residual (an initial guess worse than zero is dropped for zero).
+static kfmm_status gmres_core(bem_ctx *b, int which, int nc, const double *rhs, double *x, bool zero_x,
+                              const double *bn, const double *tol, int m, int maxit, int *iters, double *rel,
+                              bool *conv, double *x0_rel = nullptr)
 {
-    const int64_t n = 3 * b->nt;
-    BK_CUDA(b->basis.ensure(sizeof(double) * (size_t)(m + 1) * n));
-    BK_CUDA(b->w.ensure(sizeof(double) * n));
-    BK_CUDA(b->r.ensure(sizeof(double) * n));
+    const int64_t n = 3 * b->nt, N = n * nc;
+    BK_CUDA(b->basis.ensure(sizeof(double) * (size_t)(m + 1) * N));
+    BK_CUDA(b->w.ensure(sizeof(double) * N));
+    BK_CUDA(b->r.ensure(sizeof(double) * N));
     double *V = b->basis.as<double>(), *w = b->w.as<double>(), *r = b->r.as<double>();
-    if (zero_x) BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, b->stream));
-    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m), h(m + 1), h2(m + 1);
+    if (zero_x) BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, b->stream));
+    std::vector<std::vector<double>> H(nc, std::vector<double>((size_t)(m + 1) * m, 0.0)), cs(nc, std::vector<double>(m)),
+        sn(nc, std::vector<double>(m)), g(nc, std::vector<double>(m + 1));
+    std::vector<double> beta(nc), h((size_t)nc * (m + 1)), h2((size_t)nc * (m + 1)), hn(nc), a(nc),
+        ycoef((size_t)nc * (m + 1));
+    std::vector<int> steps(nc);
+    std::vector<char> extend(nc);
     int it = 0;
-    double rel = 1.0;
-    bool conv = false;
+    bool first = true;
     while (true) {
         // true residual r = rhs - A x
-        if (!zero_x || it > 0) {
-            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, x, w, which));
-            sub_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(r, rhs, w, n);
+        if (!zero_x || !first) {
+            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, x, w, which, nc));
+            sub_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(r, rhs, w, N);
             BK_LAUNCH();
         } else {
-            BK_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
+            BK_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * N, cudaMemcpyDeviceToDevice, b->stream));
         }
-        double beta;
-        BK_TRY(vnorm(b, r, n, &beta));
-        if (!zero_x && it == 0 && x0_rel) *x0_rel = beta / bn;
-        if (!zero_x && it == 0 && beta > bn) {
-            // an initial guess worse than zero is dropped: plain GMRES from zero
-            BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, b->stream));
-            BK_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
-            BK_TRY(vnorm(b, r, n, &beta));
+        BK_TRY(vnorm(b, r, nc, beta.data()));
+        if (first && !zero_x) {
+            for (int c = 0; c < nc; ++c) {
+                if (x0_rel) x0_rel[c] = beta[c] / bn[c];
+                if (beta[c] > bn[c]) {
+                    // an initial guess worse than zero is dropped: this column starts from zero
+                    BK_CUDA(cudaMemsetAsync(x + c * n, 0, sizeof(double) * n, b->stream));
+                    BK_CUDA(cudaMemcpyAsync(r + c * n, rhs + c * n, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                            b->stream));
+                    beta[c] = bn[c];
+                }
+            }
         }
-        rel = beta / bn;
-        if (rel <= tol) {
-            conv = true;
-            break;
+        first = false;
+        bool all = true;
+        for (int c = 0; c < nc; ++c) {
+            rel[c] = beta[c] / bn[c];
+            conv[c] = rel[c] <= tol[c];
+            all = all && conv[c];
         }
-        if (it >= maxit) break;
-        scale_copy_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(V, r, 1.0 / beta, n);
-        BK_LAUNCH();
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int j = 0;
-        for (; j < m && it < maxit; ++j) {
-            double *vj = V + (size_t)j * n, *vn = V + (size_t)(j + 1) * n;
-            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, vj, w, which));
+        if (all || it >= maxit) break;
+        for (int c = 0; c < nc; ++c) {
+            extend[c] = !conv[c] && beta[c] > 0.0;
+            a[c] = extend[c] ? 1.0 / beta[c] : 0.0;
+            std::fill(g[c].begin(), g[c].end(), 0.0);
+            g[c][0] = beta[c];
+            steps[c] = 0;
+        }
+        BK_TRY(scale_copy(b, V, r, a.data(), nc));
+        for (int j = 0; j < m && it < maxit; ++j) {
+            double *vj = V + (size_t)j * N, *vn = V + (size_t)(j + 1) * N;
+            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, vj, w, which, nc));
             ++it;
-            // classical Gram-Schmidt, twice
-            BK_TRY(mdot(b, V, n, j + 1, w, n, h.data()));
-            BK_TRY(maxpy(b, w, V, n, j + 1, h.data(), -1.0, n));
-            BK_TRY(mdot(b, V, n, j + 1, w, n, h2.data()));
-            BK_TRY(maxpy(b, w, V, n, j + 1, h2.data(), -1.0, n));
-            for (int i = 0; i <= j; ++i) h[i] += h2[i];
-            double hn;
-            BK_TRY(vnorm(b, w, n, &hn));
-            h[j + 1] = hn;
-            scale_copy_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(vn, w, hn > 0 ? 1.0 / hn : 0.0, n);
-            BK_LAUNCH();
-            for (int i = 0; i < j; ++i) {
-                const double t0 = cs[i] * h[i] + sn[i] * h[i + 1];
-                h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-                h[i] = t0;
+            // classical Gram-Schmidt, twice (per column; columns that stopped have zero vectors)
+            BK_TRY(mdot(b, V, N, j + 1, w, nc, h.data()));
+            BK_TRY(maxpy(b, w, V, N, j + 1, h.data(), j + 1, -1.0, nc));
+            BK_TRY(mdot(b, V, N, j + 1, w, nc, h2.data()));
+            BK_TRY(maxpy(b, w, V, N, j + 1, h2.data(), j + 1, -1.0, nc));
+            BK_TRY(vnorm(b, w, nc, hn.data()));
+            bool any = false;
+            for (int c = 0; c < nc; ++c) {
+                a[c] = 0.0;
+                if (!extend[c]) continue;
+                double *hc = h.data() + (size_t)c * (j + 1), *h2c = h2.data() + (size_t)c * (j + 1);
+                std::vector<double> col(j + 2);
+                for (int i = 0; i <= j; ++i) col[i] = hc[i] + h2c[i];
+                col[j + 1] = hn[c];
+                a[c] = hn[c] > 0 ? 1.0 / hn[c] : 0.0;
+                for (int i = 0; i < j; ++i) {
+                    const double t0 = cs[c][i] * col[i] + sn[c][i] * col[i + 1];
+                    col[i + 1] = -sn[c][i] * col[i] + cs[c][i] * col[i + 1];
+                    col[i] = t0;
+                }
+                const double den = std::hypot(col[j], col[j + 1]);
+                cs[c][j] = den > 0 ? col[j] / den : 1.0;
+                sn[c][j] = den > 0 ? col[j + 1] / den : 0.0;
+                col[j] = den;
+                g[c][j + 1] = -sn[c][j] * g[c][j];
+                g[c][j] = cs[c][j] * g[c][j];
+                for (int i = 0; i <= j; ++i) H[c][(size_t)i * m + j] = col[i];
+                steps[c] = j + 1;
+                if (std::fabs(g[c][j + 1]) / bn[c] <= tol[c] || hn[c] == 0.0) {
+                    extend[c] = 0;
+                    a[c] = 0.0;  // its next basis vector is zero
+                }
+                any = any || extend[c];
             }
-            const double den = std::hypot(h[j], h[j + 1]);
-            cs[j] = den > 0 ? h[j] / den : 1.0;
-            sn[j] = den > 0 ? h[j + 1] / den : 0.0;
-            h[j] = den;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i];
-            if (std::fabs(g[j + 1]) / bn <= tol) {
-                ++j;
-                break;
+            BK_TRY(scale_copy(b, vn, w, a.data(), nc));
+            if (!any) break;
+        }
+        // x += V y per column (columns that took no step add nothing)
+        int kmax = 0;
+        std::fill(ycoef.begin(), ycoef.end(), 0.0);
+        for (int c = 0; c < nc; ++c) {
+            const int jc = steps[c];
+            kmax = std::max(kmax, jc);
+            double *y = ycoef.data() + (size_t)c * (m + 1);
+            for (int i = jc - 1; i >= 0; --i) {
+                double s = g[c][i];
+                for (int k2 = i + 1; k2 < jc; ++k2) s -= H[c][(size_t)i * m + k2] * y[k2];
+                y[i] = s / H[c][(size_t)i * m + i];
             }
         }
-        for (int i = j - 1; i >= 0; --i) {
-            double s = g[i];
-            for (int k2 = i + 1; k2 < j; ++k2) s -= H[(size_t)i * m + k2] * y[k2];
-            y[i] = s / H[(size_t)i * m + i];
-        }
-        BK_TRY(maxpy(b, x, V, n, j, y.data(), 1.0, n));
+        if (kmax > 0) BK_TRY(maxpy(b, x, V, N, kmax, ycoef.data(), m + 1, 1.0, nc));
     }
     *iters = it;
-    *rel_out = rel;
-    *conv_out = conv;
+    return KFMM_OK;
+}
+
+static void fill_stats(int nc, const double *rel, const bool *conv, const double *x0, bem_stats *st)
+{
+    st->relres = 0.0;
+    st->converged = 1;
+    st->x0_relres = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        st->relres = std::max(st->relres, rel[c]);
+        st->converged = st->converged && conv[c];
+        st->x0_relres = std::max(st->x0_relres, x0[c]);
+    }
+}
+
+// right-hand sides B y of every column with operator `which`, their norms (0 -> 1)
+static kfmm_status rhs_norms(bem_ctx *b, int which, double *rhs, std::vector<double> &bn)
+{
+    const int nc = b->ncol;
+    BK_TRY(bem_op_apply(b, 2, nullptr, nullptr, b->val.as<double>(), rhs, which, nc));
+    bn.assign(nc, 1.0);
+    BK_TRY(vnorm(b, rhs, nc, bn.data()));
+    for (double &v : bn)
+        if (v == 0.0) v = 1.0;
+    return KFMM_OK;
+}
+
+// the caller's initial guess [nt][3 ncol] (host or device) into x [ncol][3 nt]
+static kfmm_status load_x0(bem_ctx *b, const double *x0, double *x)
+{
+    const int64_t N = 3 * b->nt * b->ncol;
+    const void *dx0;
+    BK_TRY(bem_stage(b, b->stage[0], x0, sizeof(double) * N, &dx0));
+    transpose_cols_kernel<<<g1(N), 256, 0, b->stream>>>(b->nt, b->ncol, 1, (const double *)dx0, x);
+    BK_LAUNCH();
     return KFMM_OK;
 }
 
 // Plain GMRES on the context's operator (FP64 direct, or FMM with FP64 Krylov vectors).
 static kfmm_status gmres(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
 {
-    const int64_t n = 3 * b->nt;
-    BK_CUDA(b->x.ensure(sizeof(double) * n));
-    BK_CUDA(b->b.ensure(sizeof(double) * n));
+    const int nc = b->ncol;
+    const int64_t N = 3 * b->nt * nc;
+    BK_CUDA(b->x.ensure(sizeof(double) * N));
+    BK_CUDA(b->b.ensure(sizeof(double) * N));
     double *x = b->x.as<double>(), *rhs = b->b.as<double>();
-    BK_TRY(bem_op_apply(b, 2, nullptr, nullptr, b->val.as<double>(), rhs));
-    double bn;
-    BK_TRY(vnorm(b, rhs, n, &bn));
-    if (bn == 0.0) bn = 1.0;
-    if (o.x0) {
-        const void *dx0;
-        BK_TRY(bem_stage(b, b->stage[0], o.x0, sizeof(double) * n, &dx0));
-        BK_CUDA(cudaMemcpyAsync(x, dx0, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
-    }
+    std::vector<double> bn;
+    BK_TRY(rhs_norms(b, b->op, rhs, bn));
+    if (o.x0) BK_TRY(load_x0(b, o.x0, x));
     int it = 0;
-    double rel = 1.0, x0_rel = 1.0;
-    bool conv = false;
-    BK_TRY(gmres_core(b, b->op, rhs, x, o.x0 == nullptr, bn, o.tol, o.restart, o.maxit, &it, &rel, &conv, &x0_rel));
-    st->x0_relres = x0_rel;
+    std::vector<double> rel(nc, 1.0), x0_rel(nc, 1.0), tol(nc, o.tol);
+    std::unique_ptr<bool[]> conv(new bool[nc]);
+    BK_TRY(gmres_core(b, b->op, nc, rhs, x, o.x0 == nullptr, bn.data(), tol.data(), o.restart, o.maxit, &it,
+                      rel.data(), conv.get(), x0_rel.data()));
+    fill_stats(nc, rel.data(), conv.get(), x0_rel.data(), st);
     st->iters = it;
     st->outer = 1;
-    st->converged = conv;
-    st->relres = rel;
     return KFMM_OK;
 }
 
 // Mixed-precision GMRES with iterative refinement: the right-hand side, every outer residual
-// r = b - A x and the update x += d are FP64 with the direct (exact discrete) operator; each
-// correction solves A d = r by GMRES on the FP32 FMM operator to the relative tolerance
-// inner_tol.  The relative residual reported is the FP64 direct one.
+// r = b - A x and the update x += d are FP64, with an FP64-grade all-pairs operator (the exact
+// discrete operator: the compensated direct sum for refine = 1, the FP64 direct sum for
+// refine = 2); each correction solves A d = r by GMRES on the FP32 FMM operator to the
+// relative tolerance inner_tol, all density columns in lockstep (a column already at the
+// outer tolerance gets a zero correction).  The relative residual reported is the FP64-grade
+// one, the largest over the columns.
 static kfmm_status gmres_ir(bem_ctx *b, const bem_solve_opts &o, bem_stats *st)
 {
-    const int64_t n = 3 * b->nt;
-    BK_CUDA(b->x.ensure(sizeof(double) * n));
-    BK_CUDA(b->b.ensure(sizeof(double) * n));
-    BK_CUDA(b->d.ensure(sizeof(double) * n));
-    BK_CUDA(b->rhs_hi.ensure(sizeof(double) * n));
-    BK_CUDA(b->w.ensure(sizeof(double) * n));
+    const int nc = b->ncol;
+    const int64_t n = 3 * b->nt, N = n * nc;
+    BK_CUDA(b->x.ensure(sizeof(double) * N));
+    BK_CUDA(b->b.ensure(sizeof(double) * N));
+    BK_CUDA(b->d.ensure(sizeof(double) * N));
+    BK_CUDA(b->rhs_hi.ensure(sizeof(double) * N));
+    BK_CUDA(b->w.ensure(sizeof(double) * N));
     double *x = b->x.as<double>(), *rhs = b->b.as<double>(), *d = b->d.as<double>(), *r = b->rhs_hi.as<double>();
-    st->x0_relres = 1.0;
-    BK_TRY(bem_op_apply(b, 2, nullptr, nullptr, b->val.as<double>(), rhs, BEM_DIRECT_FP64));
-    double bn;
-    BK_TRY(vnorm(b, rhs, n, &bn));
-    if (bn == 0.0) bn = 1.0;
-    if (o.x0) {
-        const void *dx0;
-        BK_TRY(bem_stage(b, b->stage[0], o.x0, sizeof(double) * n, &dx0));
-        BK_CUDA(cudaMemcpyAsync(x, dx0, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
-    } else {
-        BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, b->stream));
-    }
+    const int hi = o.refine == 2 ? BEM_DIRECT_FP64 : BEM_DIRECT_HI;  // the outer (FP64-grade) operator
+    std::vector<double> bn;
+    BK_TRY(rhs_norms(b, hi, rhs, bn));
+    if (o.x0) BK_TRY(load_x0(b, o.x0, x));
+    else BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, b->stream));
+    std::vector<double> rn(nc), rel(nc, 1.0), x0_rel(nc, 1.0), itol(nc), irel(nc), rn1(nc);
+    std::unique_ptr<bool[]> conv(new bool[nc]), iconv(new bool[nc]);
     int inner_total = 0, outer = 0;
-    double rel = 1.0;
-    bool conv = false;
-    const double one = 1.0;
     while (true) {
-        // outer residual in FP64 with the direct operator
+        // outer residual in FP64 with the FP64-grade operator
         if (o.x0 || outer > 0) {
-            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, x, b->w.as<double>(), BEM_DIRECT_FP64));
-            sub_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(r, rhs, b->w.as<double>(), n);
+            BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, x, b->w.as<double>(), hi, nc));
+            sub_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(r, rhs, b->w.as<double>(), N);
             BK_LAUNCH();
         } else {
-            BK_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
+            BK_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * N, cudaMemcpyDeviceToDevice, b->stream));
         }
-        double rn;
-        BK_TRY(vnorm(b, r, n, &rn));
-        if (o.x0 && outer == 0) st->x0_relres = rn / bn;
-        if (o.x0 && outer == 0 && rn > bn) {
-            // an initial guess worse than zero is dropped: refinement from zero
-            BK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, b->stream));
-            BK_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, b->stream));
-            rn = bn;
+        BK_TRY(vnorm(b, r, nc, rn.data()));
+        bool all = true;
+        for (int c = 0; c < nc; ++c) {
+            if (o.x0 && outer == 0) {
+                x0_rel[c] = rn[c] / bn[c];
+                if (rn[c] > bn[c]) {
+                    // an initial guess worse than zero is dropped: this column starts from zero
+                    BK_CUDA(cudaMemsetAsync(x + c * n, 0, sizeof(double) * n, b->stream));
+                    BK_CUDA(cudaMemcpyAsync(r + c * n, rhs + c * n, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                            b->stream));
+                    rn[c] = bn[c];
+                }
+            }
+            rel[c] = rn[c] / bn[c];
+            conv[c] = rel[c] <= o.tol;
+            all = all && conv[c];
         }
-        rel = rn / bn;
-        if (rel <= o.tol) {
-            conv = true;
-            break;
-        }
+        if (all) break;
         if (outer >= o.max_outer || inner_total >= o.maxit) break;
-        // correction on the fast operator: A_fmm d = r to inner_tol relative to ||r||, or
-        // only as far as the outer target needs (with a factor 5 of margin for the gap
-        // between the FMM and the FP64 operator) when closer
-        const double itol = std::max(o.inner_tol, 0.2 * o.tol * bn / rn);
+        // corrections on the fast operator: A_fmm d = r to inner_tol relative to ||r||, or only
+        // as far as the outer target needs (with a factor 5 of margin for the gap between the
+        // FMM and the FP64-grade operator) when closer; converged columns get d = 0
+        for (int c = 0; c < nc; ++c) {
+            if (conv[c]) {
+                BK_CUDA(cudaMemsetAsync(r + c * n, 0, sizeof(double) * n, b->stream));
+                rn1[c] = 1.0;
+                itol[c] = 1.0;
+            } else {
+                rn1[c] = rn[c];
+                itol[c] = std::max(o.inner_tol, 0.2 * o.tol * bn[c] / rn[c]);
+            }
+        }
         int it = 0;
-        double irel = 1.0;
-        bool iconv = false;
-        BK_TRY(gmres_core(b, BEM_FMM, r, d, true, rn, itol, o.restart, o.maxit - inner_total, &it, &irel,
-                          &iconv));
+        BK_TRY(gmres_core(b, BEM_FMM, nc, r, d, true, rn1.data(), itol.data(), o.restart, o.maxit - inner_total, &it,
+                          irel.data(), iconv.get()));
         inner_total += it;
         ++outer;
-        BK_TRY(maxpy(b, x, d, n, 1, &one, 1.0, n));
+        add_kernel<<<kVecBlocks, kVecThreads, 0, b->stream>>>(x, d, N);
+        BK_LAUNCH();
     }
+    fill_stats(nc, rel.data(), conv.get(), x0_rel.data(), st);
     st->iters = inner_total;
     st->outer = outer;
-    st->converged = conv;
-    st->relres = rel;
     return KFMM_OK;
 }
 
@@ -725,7 +880,7 @@ kfmm_status bem_create(bem_ctx **out, const kfmm_options *opt, int op, const dou
 {
     if (!out) return KFMM_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!verts || !tris || nv < 3 || nt < 1 || (op != BEM_FMM && op != BEM_DIRECT_FP64) || 16 * nt > (1LL << 30))
+    if (!verts || !tris || nv < 3 || nt < 1 || (op != BEM_FMM && op != BEM_DIRECT_FP64 && op != BEM_DIRECT_HI) || 16 * nt > (1LL << 30))
         return KFMM_ERR_INVALID_ARG;
     bem_ctx *b = new (std::nothrow) bem_ctx();
     if (!b) return KFMM_ERR_OOM;
@@ -774,6 +929,21 @@ kfmm_status bem_create(bem_ctx **out, const kfmm_options *opt, int op, const dou
             delete b;
             return KFMM_ERR_INVALID_ARG;
         }
+    // pairs of the compensated direct sum closer than 4 longest edges are summed in FP64.
+    // The remaining FP32 pairs leave ~5e-7 of ||b|| on the residual of a cantilever solution
+    // (51,840 triangles; the residual cancels by ||A| |x|| / ||b|| ~ 100), measured against
+    // the FP64 direct sum: 7.8e-7 at 4 edges, 6.4e-7 at 8, 4.7e-7 at 16 -- the error comes
+    // from rounding that repeats over many pairs (sources of one element share their
+    // density, normal and nearly their difference to a far target), so a larger radius buys
+    // little; 4 edges keep the FP64 pairs a few percent of the work.
+    double emax2 = 0.0;
+    for (int64_t k = 0; k < nt; ++k)
+        for (int e = 0; e < 3; ++e) {
+            const double *a = &hv[3 * (size_t)ht[3 * k + e]], *c = &hv[3 * (size_t)ht[3 * k + (e + 1) % 3]];
+            const double dx = a[0] - c[0], dy = a[1] - c[1], dz = a[2] - c[2];
+            emax2 = std::max(emax2, dx * dx + dy * dy + dz * dz);
+        }
+    b->near_radius = 4.0 * std::sqrt(emax2);
     *out = b;
     return KFMM_OK;
 }
@@ -809,12 +979,20 @@ kfmm_status bem_set_stream(bem_ctx *b, void *stream)
     return KFMM_OK;
 }
 
-kfmm_status bem_set_bc(bem_ctx *b, const uint8_t *known_is_disp, const double *values)
+kfmm_status bem_set_bc(bem_ctx *b, const uint8_t *known_is_disp, const double *values, int ncol)
 {
-    if (!b || !known_is_disp || !values) return KFMM_ERR_INVALID_ARG;
+    if (!b || !known_is_disp || !values || ncol < 1 || ncol > 32) return KFMM_ERR_INVALID_ARG;
+    if (first_foreign({known_is_disp, values}))
+        return b->fail(KFMM_ERR_INVALID_ARG, "bem: an array is device memory of another GPU");
+    const int64_t N = 3 * b->nt * ncol;
+    BK_CUDA(b->val.ensure(sizeof(double) * N));
+    const void *dv;
+    BK_TRY(bem_stage(b, b->stage[0], values, sizeof(double) * N, &dv));
     BK_CUDA(cudaMemcpyAsync(b->mask.p, known_is_disp, 3 * b->nt, cudaMemcpyDefault, b->stream));
-    BK_CUDA(cudaMemcpyAsync(b->val.p, values, sizeof(double) * 3 * b->nt, cudaMemcpyDefault, b->stream));
+    transpose_cols_kernel<<<g1(N), 256, 0, b->stream>>>(b->nt, ncol, 1, (const double *)dv, b->val.as<double>());
+    BK_LAUNCH();
     BK_CUDA(cudaStreamSynchronize(b->stream));
+    b->ncol = ncol;
     b->have_bc = true;
     return KFMM_OK;
 }
@@ -822,6 +1000,7 @@ kfmm_status bem_set_bc(bem_ctx *b, const uint8_t *known_is_disp, const double *v
 kfmm_status bem_apply(bem_ctx *b, const double *u, const double *t, double *out)
 {
     if (!b || !out || (!u && !t)) return KFMM_ERR_INVALID_ARG;
+    if (first_foreign({u, t, out})) return b->fail(KFMM_ERR_INVALID_ARG, "bem: an array is device memory of another GPU");
     const size_t bytes = sizeof(double) * 3 * b->nt;
     const void *du, *dt;
     BK_TRY(bem_stage(b, b->stage[0], u, bytes, &du));
@@ -838,40 +1017,49 @@ kfmm_status bem_apply(bem_ctx *b, const double *u, const double *t, double *out)
     return KFMM_OK;
 }
 
+// y = A x or (x == NULL) y = B y_known for every column, ABI layout [nt][3 ncol] in and out
+static kfmm_status bem_apply_cols(bem_ctx *b, const double *x, double *y)
+{
+    const int nc = b->ncol;
+    const int64_t N = 3 * b->nt * nc;
+    BK_CUDA(b->w.ensure(sizeof(double) * N));
+    BK_CUDA(b->r.ensure(sizeof(double) * N));
+    if (x) {
+        const void *dx;
+        BK_TRY(bem_stage(b, b->stage[0], x, sizeof(double) * N, &dx));
+        transpose_cols_kernel<<<g1(N), 256, 0, b->stream>>>(b->nt, nc, 1, (const double *)dx, b->r.as<double>());
+        BK_LAUNCH();
+        BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, b->r.as<double>(), b->w.as<double>(), -1, nc));
+    } else {
+        BK_TRY(bem_op_apply(b, 2, nullptr, nullptr, b->val.as<double>(), b->w.as<double>(), -1, nc));
+    }
+    double *dy = y;
+    const bool host_out = !is_device_ptr(y);
+    if (host_out) {
+        BK_CUDA(b->out64.ensure(sizeof(double) * N));
+        dy = b->out64.as<double>();
+    }
+    transpose_cols_kernel<<<g1(N), 256, 0, b->stream>>>(b->nt, nc, 0, b->w.as<double>(), dy);
+    BK_LAUNCH();
+    if (host_out) BK_CUDA(cudaMemcpyAsync(y, dy, sizeof(double) * N, cudaMemcpyDeviceToHost, b->stream));
+    BK_CUDA(cudaStreamSynchronize(b->stream));
+    return KFMM_OK;
+}
+
 kfmm_status bem_matvec(bem_ctx *b, const double *x, double *y)
 {
     if (!b || !x || !y) return KFMM_ERR_INVALID_ARG;
     if (!b->have_bc) return b->fail(KFMM_ERR_NOT_BUILT, "bem: boundary conditions not set");
-    const size_t bytes = sizeof(double) * 3 * b->nt;
-    const void *dx;
-    BK_TRY(bem_stage(b, b->stage[0], x, bytes, &dx));
-    double *dy = y;
-    const bool host_out = !is_device_ptr(y);
-    if (host_out) {
-        BK_CUDA(b->out64.ensure(bytes));
-        dy = b->out64.as<double>();
-    }
-    BK_TRY(bem_op_apply(b, 1, nullptr, nullptr, (const double *)dx, dy));
-    if (host_out) BK_CUDA(cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, b->stream));
-    BK_CUDA(cudaStreamSynchronize(b->stream));
-    return KFMM_OK;
+    if (first_foreign({x, y})) return b->fail(KFMM_ERR_INVALID_ARG, "bem: an array is device memory of another GPU");
+    return bem_apply_cols(b, x, y);
 }
 
 kfmm_status bem_rhs(bem_ctx *b, double *rhs)
 {
     if (!b || !rhs) return KFMM_ERR_INVALID_ARG;
     if (!b->have_bc) return b->fail(KFMM_ERR_NOT_BUILT, "bem: boundary conditions not set");
-    const size_t bytes = sizeof(double) * 3 * b->nt;
-    double *dy = rhs;
-    const bool host_out = !is_device_ptr(rhs);
-    if (host_out) {
-        BK_CUDA(b->out64.ensure(bytes));
-        dy = b->out64.as<double>();
-    }
-    BK_TRY(bem_op_apply(b, 2, nullptr, nullptr, b->val.as<double>(), dy));
-    if (host_out) BK_CUDA(cudaMemcpyAsync(rhs, dy, bytes, cudaMemcpyDeviceToHost, b->stream));
-    BK_CUDA(cudaStreamSynchronize(b->stream));
-    return KFMM_OK;
+    if (foreign_device_ptr(rhs)) return b->fail(KFMM_ERR_INVALID_ARG, "bem: an array is device memory of another GPU");
+    return bem_apply_cols(b, nullptr, rhs);
 }
 
 kfmm_status bem_solve(bem_ctx *b, const bem_solve_opts *opts, double *u, double *t, bem_stats *st)
@@ -883,22 +1071,40 @@ kfmm_status bem_solve(bem_ctx *b, const bem_solve_opts *opts, double *u, double 
     if (opts) o = *opts;
     if (!(o.tol > 0) || o.restart < 1 || o.restart > 200 || o.maxit < 1)
         return b->fail(KFMM_ERR_INVALID_ARG, "bem_solve: need tol > 0, 1 <= restart <= 200, maxit >= 1");
-    if (o.refine && (b->op != BEM_FMM || !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_outer < 1))
+    if (o.refine < 0 || o.refine > 2 ||
+        (o.refine && (b->op != BEM_FMM || !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_outer < 1)))
         return b->fail(KFMM_ERR_INVALID_ARG,
                        "bem_solve: refinement needs an FMM context, 0 < inner_tol < 1 and max_outer >= 1");
+    if (first_foreign({u, t, o.x0})) return b->fail(KFMM_ERR_INVALID_ARG, "bem: an array is device memory of another GPU");
     const auto t0 = std::chrono::steady_clock::now();
     bem_stats s{};
     const int mv0 = b->matvecs, mh0 = b->matvecs_hi;
     if (o.refine) BK_TRY(gmres_ir(b, o, &s));
     else BK_TRY(gmres(b, o, &s));
-    const int64_t n = 3 * b->nt;
-    split_kernel<<<g1(n), 256, 0, b->stream>>>(n, b->x.as<double>(), b->mask.as<uint8_t>(), b->val.as<double>(),
+    const int nc = b->ncol;
+    const int64_t n = 3 * b->nt, N = n * nc;
+    BK_CUDA(b->usol.ensure(sizeof(double) * N));
+    BK_CUDA(b->tsol.ensure(sizeof(double) * N));
+    split_kernel<<<g1(N), 256, 0, b->stream>>>(n, nc, b->x.as<double>(), b->mask.as<uint8_t>(), b->val.as<double>(),
                                                 b->usol.as<double>(), b->tsol.as<double>());
     BK_LAUNCH();
     b->have_sol = true;
-    if (u) BK_CUDA(cudaMemcpyAsync(u, b->usol.p, sizeof(double) * n, cudaMemcpyDefault, b->stream));
-    if (t) BK_CUDA(cudaMemcpyAsync(t, b->tsol.p, sizeof(double) * n, cudaMemcpyDefault, b->stream));
-    BK_CUDA(cudaStreamSynchronize(b->stream));
+    b->sol_ncol = nc;
+    for (int k = 0; k < 2; ++k) {
+        double *dst = k == 0 ? u : t;
+        if (!dst) continue;
+        const double *src = k == 0 ? b->usol.as<double>() : b->tsol.as<double>();
+        double *d = dst;
+        const bool host = !is_device_ptr(dst);
+        if (host) {
+            BK_CUDA(b->out64.ensure(sizeof(double) * N));
+            d = b->out64.as<double>();
+        }
+        transpose_cols_kernel<<<g1(N), 256, 0, b->stream>>>(b->nt, nc, 0, src, d);
+        BK_LAUNCH();
+        if (host) BK_CUDA(cudaMemcpyAsync(dst, d, sizeof(double) * N, cudaMemcpyDeviceToHost, b->stream));
+        BK_CUDA(cudaStreamSynchronize(b->stream));
+    }
     s.matvecs = b->matvecs - mv0;
     s.matvecs_hi = b->matvecs_hi - mh0;
     s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -907,14 +1113,23 @@ kfmm_status bem_solve(bem_ctx *b, const bem_solve_opts *opts, double *u, double 
     return KFMM_OK;
 }
 
-kfmm_status bem_set_solution(bem_ctx *b, const double *u, const double *t)
+kfmm_status bem_set_solution(bem_ctx *b, const double *u, const double *t, int ncol)
 {
-    if (!b || !u || !t) return KFMM_ERR_INVALID_ARG;
-    const size_t bytes = sizeof(double) * 3 * b->nt;
-    BK_CUDA(cudaMemcpyAsync(b->usol.p, u, bytes, cudaMemcpyDefault, b->stream));
-    BK_CUDA(cudaMemcpyAsync(b->tsol.p, t, bytes, cudaMemcpyDefault, b->stream));
+    if (!b || !u || !t || ncol < 1 || ncol > 32) return KFMM_ERR_INVALID_ARG;
+    if (first_foreign({u, t})) return b->fail(KFMM_ERR_INVALID_ARG, "bem: an array is device memory of another GPU");
+    const int64_t N = 3 * b->nt * ncol;
+    BK_CUDA(b->usol.ensure(sizeof(double) * N));
+    BK_CUDA(b->tsol.ensure(sizeof(double) * N));
+    for (int k = 0; k < 2; ++k) {
+        const void *d;
+        BK_TRY(bem_stage(b, b->stage[k], k == 0 ? u : t, sizeof(double) * N, &d));
+        transpose_cols_kernel<<<g1(N), 256, 0, b->stream>>>(b->nt, ncol, 1, (const double *)d,
+                                                            k == 0 ? b->usol.as<double>() : b->tsol.as<double>());
+        BK_LAUNCH();
+    }
     BK_CUDA(cudaStreamSynchronize(b->stream));
     b->have_sol = true;
+    b->sol_ncol = ncol;
     return KFMM_OK;
 }
 
@@ -922,30 +1137,40 @@ kfmm_status bem_interior(bem_ctx *b, const float *pts, int64_t n, float *disp, f
 {
     if (!b || !pts || n < 1 || (!disp && !stress)) return KFMM_ERR_INVALID_ARG;
     if (!b->have_sol) return b->fail(KFMM_ERR_NOT_BUILT, "bem: no boundary solution (solve or set_solution first)");
+    if (first_foreign({pts, disp, stress}))
+        return b->fail(KFMM_ERR_INVALID_ARG, "bem: an array is device memory of another GPU");
     BK_TRY(bem_setup(b));
     const int64_t nt = b->nt, nq = 16 * nt;
+    const int nc = b->sol_ncol;
     const void *dp;
     BK_TRY(bem_stage(b, b->stage[2], pts, sizeof(float) * 3 * n, &dp));
     if (b->op == BEM_FMM) {
         if (!b->vol) {
-            kfmm_status s = kfmm_create(&b->vol, &b->opt);
+            // interior stresses are far-field-dominated sums of a single and a double layer
+            // that cancel each other in part: the interior context runs at p >= 8 with the M2L
+            // basis cut at 1e-7 (p = 6 leaves ~3e-3 on the double-layer stress, p = 8 ~7e-5)
+            kfmm_options vo = b->opt;
+            vo.p = std::max(vo.p, 8);
+            vo.m2l_rtol = vo.m2l_rtol > 0.0 ? std::min(vo.m2l_rtol, 1e-7) : 0.0;
+            kfmm_status s = kfmm_create(&b->vol, &vo);
             if (s != KFMM_OK) return b->fail(s, "bem: interior FMM context");
             kfmm_set_material(b->vol, b->K, b->G);
             kfmm_set_stream(b->vol, b->stream);
         }
-        BK_CUDA(b->slq.ensure(sizeof(float) * 3 * nq));
-        BK_CUDA(b->dlq.ensure(sizeof(float) * 3 * nq));
-        interior_density_kernel<<<g1(nq), 256, 0, b->stream>>>(nt, b->usol.as<double>(), b->tsol.as<double>(),
-                                                                b->qw.as<double>(), b->slq.as<float>(), b->dlq.as<float>());
+        BK_CUDA(b->slq.ensure(sizeof(float) * 3 * nq * nc));
+        BK_CUDA(b->dlq.ensure(sizeof(float) * 3 * nq * nc));
+        interior_density_kernel<float><<<g1(nq * nc), 256, 0, b->stream>>>(nt, 0, nc, b->usol.as<double>(),
+                                                                           b->tsol.as<double>(), b->qw.as<double>(),
+                                                                           b->slq.as<float>(), b->dlq.as<float>());
         BK_LAUNCH();
         kfmm_status s = kfmm_build(b->vol, b->q32.as<float>(), b->qn32.as<float>(), nq, (const float *)dp, n);
         if (s != KFMM_OK) return b->fail(s, std::string("interior fmm: ") + kfmm_last_error(b->vol));
         if (disp) {
-            s = kfmm_eval(b->vol, b->slq.as<float>(), b->dlq.as<float>(), 1, KFMM_DISP, disp);
+            s = kfmm_eval(b->vol, b->slq.as<float>(), b->dlq.as<float>(), nc, KFMM_DISP, disp);
             if (s != KFMM_OK) return b->fail(s, std::string("interior fmm: ") + kfmm_last_error(b->vol));
         }
         if (stress) {
-            s = kfmm_eval(b->vol, b->slq.as<float>(), b->dlq.as<float>(), 1, KFMM_STRESS, stress);
+            s = kfmm_eval(b->vol, b->slq.as<float>(), b->dlq.as<float>(), nc, KFMM_STRESS, stress);
             if (s != KFMM_OK) return b->fail(s, std::string("interior fmm: ") + kfmm_last_error(b->vol));
         }
     } else {
@@ -953,30 +1178,38 @@ kfmm_status bem_interior(bem_ctx *b, const float *pts, int64_t n, float *disp, f
         BK_CUDA(b->dlq.ensure(sizeof(double) * 3 * nq));
         BK_CUDA(b->pts64.ensure(sizeof(double) * 3 * n));
         BK_CUDA(b->out64.ensure(sizeof(double) * 6 * n));
-        interior_density64_kernel<<<g1(nq), 256, 0, b->stream>>>(nt, b->usol.as<double>(), b->tsol.as<double>(),
-                                                                  b->qw.as<double>(), b->slq.as<double>(),
-                                                                  b->dlq.as<double>());
-        BK_LAUNCH();
         f2d_kernel<<<g1(3 * n), 256, 0, b->stream>>>(3 * n, (const float *)dp, b->pts64.as<double>());
         BK_LAUNCH();
-        DevBuf of;
+        DevBuf of[2];
+        float *dd[2] = {disp, stress};
+        bool host[2] = {false, false};
         for (int kind = 0; kind < 2; ++kind) {
-            float *dst = kind == 0 ? disp : stress;
-            if (!dst) continue;
-            const int no = kind == 0 ? 3 : 6;
-            BK_FMM(kfmm_direct(b->surf, KFMM_FP64, b->pts64.p, n, b->q64.p, b->qn64.p, nq, b->slq.p, b->dlq.p,
-                               kind == 0 ? KFMM_DISP : KFMM_STRESS, b->out64.p));
-            const bool host_out = !is_device_ptr(dst);
-            float *d = dst;
-            if (host_out) {
-                BK_CUDA(of.ensure(sizeof(float) * no * n));
-                d = of.as<float>();
+            if (!dd[kind]) continue;
+            host[kind] = !is_device_ptr(dd[kind]);
+            if (host[kind]) {
+                BK_CUDA(of[kind].ensure(sizeof(float) * (kind == 0 ? 3 : 6) * n * nc));
+                dd[kind] = of[kind].as<float>();
             }
-            d2f_kernel<<<g1(no * n), 256, 0, b->stream>>>(no * n, b->out64.as<double>(), d);
-            BK_LAUNCH();
-            if (host_out) BK_CUDA(cudaMemcpyAsync(dst, d, sizeof(float) * no * n, cudaMemcpyDeviceToHost, b->stream));
-            BK_CUDA(cudaStreamSynchronize(b->stream));
         }
+        for (int c = 0; c < nc; ++c) {
+            interior_density_kernel<double><<<g1(nq), 256, 0, b->stream>>>(nt, c, 1, b->usol.as<double>(),
+                                                                           b->tsol.as<double>(), b->qw.as<double>(),
+                                                                           b->slq.as<double>(), b->dlq.as<double>());
+            BK_LAUNCH();
+            for (int kind = 0; kind < 2; ++kind) {
+                if (!dd[kind]) continue;
+                const int no = kind == 0 ? 3 : 6;
+                BK_FMM(kfmm_direct(b->surf, KFMM_FP64, b->pts64.p, n, b->q64.p, b->qn64.p, nq, b->slq.p, b->dlq.p,
+                                   kind == 0 ? KFMM_DISP : KFMM_STRESS, b->out64.p));
+                d2f_cols_kernel<<<g1(no * n), 256, 0, b->stream>>>(n, no, nc, c, b->out64.as<double>(), dd[kind]);
+                BK_LAUNCH();
+            }
+        }
+        for (int kind = 0; kind < 2; ++kind)
+            if (host[kind])
+                BK_CUDA(cudaMemcpyAsync(kind == 0 ? disp : stress, dd[kind], sizeof(float) * (kind == 0 ? 3 : 6) * n * nc,
+                                        cudaMemcpyDeviceToHost, b->stream));
+        BK_CUDA(cudaStreamSynchronize(b->stream));
     }
     BK_CUDA(cudaStreamSynchronize(b->stream));
     return KFMM_OK;
@@ -985,30 +1218,34 @@ kfmm_status bem_interior(bem_ctx *b, const float *pts, int64_t n, float *disp, f
 kfmm_status bem_topo_derivative(bem_ctx *b, const float *pts, int64_t n, float *td, float *energy, float *stress)
 {
     if (!b || !pts || n < 1 || (!td && !energy && !stress)) return KFMM_ERR_INVALID_ARG;
+    if (!b->have_sol) return b->fail(KFMM_ERR_NOT_BUILT, "bem: no boundary solution (solve or set_solution first)");
+    if (first_foreign({pts, td, energy, stress}))
+        return b->fail(KFMM_ERR_INVALID_ARG, "bem: an array is device memory of another GPU");
+    const int nc = b->sol_ncol;
     DevBuf sbuf, tdb, enb;
     float *ds = stress;
     const bool host_s = stress && !is_device_ptr(stress);
     if (!stress || host_s) {
-        BK_CUDA(sbuf.ensure(sizeof(float) * 6 * n));
+        BK_CUDA(sbuf.ensure(sizeof(float) * 6 * n * nc));
         ds = sbuf.as<float>();
     }
     BK_TRY(bem_interior(b, pts, n, nullptr, ds));
     float *dtd = td, *den = energy;
     const bool host_td = td && !is_device_ptr(td), host_en = energy && !is_device_ptr(energy);
     if (host_td) {
-        BK_CUDA(tdb.ensure(sizeof(float) * n));
+        BK_CUDA(tdb.ensure(sizeof(float) * n * nc));
         dtd = tdb.as<float>();
     }
     if (host_en) {
-        BK_CUDA(enb.ensure(sizeof(float) * n));
+        BK_CUDA(enb.ensure(sizeof(float) * n * nc));
         den = enb.as<float>();
     }
     const double E = 2.0 * b->G * (1.0 + b->nu);
-    topo_kernel<<<g1(n), 256, 0, b->stream>>>(n, ds, (float)E, (float)b->nu, dtd, den);
+    topo_kernel<<<g1(n * nc), 256, 0, b->stream>>>(n, nc, ds, (float)E, (float)b->nu, dtd, den);
     BK_LAUNCH();
-    if (host_td) BK_CUDA(cudaMemcpyAsync(td, dtd, sizeof(float) * n, cudaMemcpyDeviceToHost, b->stream));
-    if (host_en) BK_CUDA(cudaMemcpyAsync(energy, den, sizeof(float) * n, cudaMemcpyDeviceToHost, b->stream));
-    if (host_s) BK_CUDA(cudaMemcpyAsync(stress, ds, sizeof(float) * 6 * n, cudaMemcpyDeviceToHost, b->stream));
+    if (host_td) BK_CUDA(cudaMemcpyAsync(td, dtd, sizeof(float) * n * nc, cudaMemcpyDeviceToHost, b->stream));
+    if (host_en) BK_CUDA(cudaMemcpyAsync(energy, den, sizeof(float) * n * nc, cudaMemcpyDeviceToHost, b->stream));
+    if (host_s) BK_CUDA(cudaMemcpyAsync(stress, ds, sizeof(float) * 6 * n * nc, cudaMemcpyDeviceToHost, b->stream));
     BK_CUDA(cudaStreamSynchronize(b->stream));
     return KFMM_OK;
 }

@@ -7,6 +7,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -199,6 +200,9 @@ struct Work {
     DevBuf stage_in[4];  // staging of host inputs
     DevBuf stage_out;
     DevBuf tmp;
+    DevBuf hi_rec;       // source records of the compensated direct sum (direct_hi.cu)
+    DevBuf hi_part;      // its per-block coordinate bounds
+    DevBuf td_stress;    // stresses behind a KFMM_TD evaluation
     // box-vector buffers whose padding lanes are known to be zero: their allocations and the
     // density-column layout they were zeroed for
     void *zero_ptr[8] = {};
@@ -354,6 +358,7 @@ struct kfmm_ctx {
     int cur_phase = -1;
     cudaEvent_t cur_ev = nullptr;
     int64_t n_launch = 0;  // kernels launched by this context since creation
+    int n_sms = 152;       // multiprocessors of opt.device (queried at create; sizes grids)
     // Close the open phase (if any) and open phase `ph` (ph < 0: only close).
     void phase(int ph) {
         if (!prof.on) return;
@@ -388,10 +393,23 @@ kfmm_status tree_work_counts(kfmm_ctx *ctx);  // interaction counts for the stat
 kfmm_status ensure_operators(kfmm_ctx *ctx);
 // fmm.cu
 kfmm_status fmm_eval(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, int kind, float *out);
+// D^T and energy density per target and column from stresses [n][6 ncol] -> out [n][2 ncol]
+kfmm_status fmm_td(kfmm_ctx *ctx, const float *stress, int64_t n, int ncol, float *out);
 kfmm_status selftest_bounded_wait(kfmm_ctx *ctx, long long polls);
 // direct.cu
 kfmm_status direct_sum(kfmm_ctx *ctx, int precision, const void *trg, int64_t ntrg, const void *src,
                        const void *nrm, int64_t nsrc, const void *sl, const void *dl, int kind, void *out);
+// direct_hi.cu: FP64-grade displacement sum at FP32 rate (FP64 arrays, device pointers)
+kfmm_status direct_hi_sum(kfmm_ctx *ctx, const double *trg, int64_t ntrg, const double *src, const double *nrm,
+                          int64_t nsrc, const double *sl, const double *dl, double near_radius, double *out);
+// peak.cu: measured FP32 FMA throughput (TFLOP/s) and the kernel's time
+kfmm_status measure_fp32_peak(kfmm_ctx *ctx, double *tflops, double *ms);
 // api.cu helpers
+// Device (or managed) memory, as opposed to host memory.
 bool is_device_ptr(const void *p);
+// Device memory that belongs to a GPU other than the current one: the entry points reject it
+// (a kernel here would read another GPU's memory without peer access).
+bool foreign_device_ptr(const void *p);
+// The first non-null pointer of `ptrs` that foreign_device_ptr() flags, or nullptr.
+const void *first_foreign(std::initializer_list<const void *> ptrs);
 }  // namespace kfmm

@@ -115,11 +115,11 @@ direct_kernel(const R *__restrict__ trg, int64_t ntrg, const R *__restrict__ src
 
 template <typename R, int KIND>
 void launch_direct(const R *trg, int64_t ntrg, const R *src, const R *nrm, const R *sl, const R *dl,
-                   int64_t nsrc, KelvinConst<R> kc, R *out, cudaStream_t st)
+                   int64_t nsrc, KelvinConst<R> kc, R *out, cudaStream_t st, int n_sms)
 {
     // source chunks: enough CTAs for ~4 per SM, at least 1024 sources per chunk
     const int64_t tb = (ntrg + kDirThreads - 1) / kDirThreads;
-    int64_t ns = (4 * 152 + tb - 1) / tb;
+    int64_t ns = (4 * (int64_t)n_sms + tb - 1) / tb;
     ns = std::min<int64_t>(ns, (nsrc + 1023) / 1024);
     ns = std::max<int64_t>(ns, 1);
     ns = std::min<int64_t>(ns, 65535);
@@ -178,22 +178,22 @@ kfmm_status direct_sum(kfmm_ctx *ctx, int precision, const void *trg, int64_t nt
         if (kind == KFMM_DISP)
             launch_direct<double, KFMM_DISP>((const double *)dtrg, ntrg, (const double *)dsrc,
                                              (const double *)dnrm, (const double *)dsl,
-                                             (const double *)ddl, nsrc, kc, (double *)dout, ctx->stream);
+                                             (const double *)ddl, nsrc, kc, (double *)dout, ctx->stream, ctx->n_sms);
         else
             launch_direct<double, KFMM_STRESS>((const double *)dtrg, ntrg, (const double *)dsrc,
                                                (const double *)dnrm, (const double *)dsl,
                                                (const double *)ddl, nsrc, kc, (double *)dout,
-                                               ctx->stream);
+                                               ctx->stream, ctx->n_sms);
     } else {
         auto kc = make_kelvin<float>(ctx->G, ctx->nu);
         if (kind == KFMM_DISP)
             launch_direct<float, KFMM_DISP>((const float *)dtrg, ntrg, (const float *)dsrc,
                                             (const float *)dnrm, (const float *)dsl, (const float *)ddl,
-                                            nsrc, kc, (float *)dout, ctx->stream);
+                                            nsrc, kc, (float *)dout, ctx->stream, ctx->n_sms);
         else
             launch_direct<float, KFMM_STRESS>((const float *)dtrg, ntrg, (const float *)dsrc,
                                               (const float *)dnrm, (const float *)dsl, (const float *)ddl,
-                                              nsrc, kc, (float *)dout, ctx->stream);
+                                              nsrc, kc, (float *)dout, ctx->stream, ctx->n_sms);
     }
     KF_LAUNCH();
     if (host_out) {

@@ -33,7 +33,9 @@ std::mutex g_scratch_mu;
 void *g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device (looked up once per device;
-// in host code the array's name is only a host-side stand-in).
+// in host code the array's name is only a host-side stand-in).  The cache is keyed by the
+// device ordinal only: it is not valid across cudaDeviceReset, after which the module is
+// loaded again and the array may sit elsewhere.
 kfmm_status scratch_address(kfmm_ctx *ctx, void **out)
 {
     int dev = 0;
@@ -77,6 +79,7 @@ direct_slice_kernel(const R *__restrict__ trg, int64_t ntrg, const R *__restrict
         z = trg[3 * i + 2];
     }
     R o[6] = {0, 0, 0, 0, 0, 0};
+    const R ratio = kc.c_S / kc.c_D;  // S carries c_S, the sum is scaled by c_D at the end
     for (int64_t base = s0; base < s1; base += kNaThreads) {
         const int64_t j = base + threadIdx.x;
         __syncthreads();
@@ -122,7 +125,6 @@ direct_slice_kernel(const R *__restrict__ trg, int64_t ntrg, const R *__restrict
                     R s6[6] = {0, 0, 0, 0, 0, 0};
                     acc_S<R>(dx, dy, dz, tile.u[0][s], tile.u[1][s], tile.u[2][s], tile.n[0][s], tile.n[1][s],
                              tile.n[2][s], kc.nu, kc.b12, s6);
-                    const R ratio = kc.c_S / kc.c_D;
                     for (int a = 0; a < 6; ++a) o[a] += ratio * s6[a];
                 }
             }
@@ -158,7 +160,7 @@ kfmm_status run_noalloc(kfmm_ctx *ctx, const R *trg, int64_t ntrg, const R *src,
     KF_TRY(scratch_address(ctx, &scr));
     // source slices: enough CTAs to fill the GPU, bounded by the scratch and by one tile each
     const int64_t tiles = (ntrg + kNaThreads - 1) / kNaThreads;
-    int64_t nslice = (4 * 152 + tiles - 1) / tiles;
+    int64_t nslice = (4 * (int64_t)ctx->n_sms + tiles - 1) / tiles;
     nslice = std::min<int64_t>(nslice, (nsrc + kNaThreads - 1) / kNaThreads);
     nslice = std::min<int64_t>(nslice, (int64_t)(kNoAllocScratchBytes / per_slice));
     nslice = std::max<int64_t>(1, std::min<int64_t>(nslice, 65535));
@@ -200,10 +202,12 @@ extern "C" kfmm_status kfmm_direct_noalloc(kfmm_ctx *ctx, int precision, const v
         (dl_den && !src_nrm))
         return ctx->fail(KFMM_ERR_INVALID_ARG, "direct_noalloc: bad arguments");
     const void *ptrs[6] = {trg_xyz, src_xyz, src_nrm, sl_den, dl_den, out};
-    for (const void *p : ptrs)
-        if (p && !is_device_ptr(p))
-            return ctx->fail(KFMM_ERR_INVALID_ARG, "direct_noalloc: every array must be device memory");
     if (cudaSetDevice(ctx->opt.device) != cudaSuccess) return ctx->fail(KFMM_ERR_CUDA, "cudaSetDevice");
+    // every array must be device memory of the context's GPU (checked with it current)
+    for (const void *p : ptrs)
+        if (p && (!is_device_ptr(p) || foreign_device_ptr(p)))
+            return ctx->fail(KFMM_ERR_INVALID_ARG,
+                             "direct_noalloc: every array must be device memory of the context's GPU");
     if (precision == KFMM_FP64) {
         if (kind == KFMM_DISP)
             return run_noalloc<double, KFMM_DISP>(ctx, (const double *)trg_xyz, ntrg, (const double *)src_xyz,

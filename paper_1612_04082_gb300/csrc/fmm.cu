@@ -1524,6 +1524,34 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
 }
 
 // One thread waits on an mbarrier that nothing arrives on (bounded) and records the time-out.
+// Topological derivative of the compliance (Eq. deriv) and the energy density 1/2 sigma:eps
+// (integrand of Eq. functional) from stresses [n][6 ncol] (xx, yy, zz, yz, xz, xy per
+// column): out [n][2 ncol] = (D^T, w) per column.
+__global__ void td_from_stress_kernel(int64_t n, int ncol, const float *__restrict__ s6, float E, float nu,
+                                      float *__restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * ncol) return;
+    const int64_t i = e / ncol;
+    const int c = (int)(e % ncol);
+    const float *s = s6 + i * 6 * ncol + 6 * c;
+    const float tr = s[0] + s[1] + s[2];
+    const float ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + 2.f * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+    out[i * 2 * ncol + 2 * c] =
+        0.75f / E * (1.f - nu) / (7.f - 5.f * nu) * (10.f * (1.f + nu) * ss - (1.f + 5.f * nu) * tr * tr);
+    out[i * 2 * ncol + 2 * c + 1] = 0.5f * ((1.f + nu) * ss - nu * tr * tr) / E;
+}
+
+kfmm_status fmm_td(kfmm_ctx *ctx, const float *stress, int64_t n, int ncol, float *out)
+{
+    const double E = 2.0 * ctx->G * (1.0 + ctx->nu);
+    const int64_t ne = n * ncol;
+    td_from_stress_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, ctx->stream>>>(n, ncol, stress, (float)E,
+                                                                                  (float)ctx->nu, out);
+    KF_LAUNCH();
+    return KFMM_OK;
+}
+
 __global__ void bounded_wait_probe_kernel(long long polls, int *err)
 {
     __shared__ uint64_t bar;

@@ -160,7 +160,7 @@ def test_mixed_bc_cantilever_refined(K):
         b.set_material(K.material_K(G0, NU0), G0)
         b.set_bc(mask, vals)
         u, t = np.zeros((len(T), 3)), np.zeros((len(T), 3))
-        st = b.solve(u, t, tol=1e-8, restart=100, maxit=2000, refine=True, inner_tol=1e-3)
+        st = b.solve(u, t, tol=1e-8, restart=100, maxit=2000, refine=2, inner_tol=1e-3)
     assert st["converged"] and st["relres"] <= 1e-8
     assert st["outer"] >= 1 and st["matvecs_hi"] == st["outer"] + 1
     assert rel(u, u_ref) < 1e-6 and rel(t, t_ref) < 1e-5
@@ -179,7 +179,7 @@ def test_lame_sphere_refined(K, sphere):
         b.set_material(K.material_K(G0, NU0), G0)
         b.set_bc(mask, nrm)
         u = np.zeros((len(T), 3))
-        st = b.solve(u, None, tol=1e-8, restart=60, refine=True, inner_tol=1e-3)
+        st = b.solve(u, None, tol=1e-8, restart=60, refine=2, inner_tol=1e-3)
     assert st["converged"] and st["relres"] <= 1e-8
     assert rel(O.remove_rigid_modes(u, cen, area), u_ref) < 1e-6
 
@@ -196,16 +196,19 @@ def test_refine_arguments(K, sphere):
     with K.Bem(V, T, K.BEM_FMM) as b:
         b.set_material(K.material_K(G0, NU0), G0)
         b.set_bc(mask, nrm)
-        for kw in ({"inner_tol": 0.0}, {"inner_tol": 1.5}, {"max_outer": 0}):
+        for kw in ({"inner_tol": 0.0}, {"inner_tol": 1.5}, {"max_outer": 0}, {"refine": 3}):
             with pytest.raises(K.KfmmError) as e:
-                b.solve(np.zeros((len(T), 3)), refine=True, **kw)
+                b.solve(np.zeros((len(T), 3)), **{"refine": True, **kw})
             assert e.value.status == K.KFMM_ERR_INVALID_ARG
 
 
 def test_interior_stress_and_td(K):
-    """Uniform tension of the benchmark cube (E = 1, nu = 0.3): interior stress and D^T from
-    the GPU (FMM and FP64 direct) against the oracle's Somigliana sums on the same boundary
-    solution, and the closed form D^T = 1.00227."""
+    """Uniform tension of the benchmark cube (E = 1, nu = 0.3): interior displacement, stress,
+    D^T (Eq. deriv) and energy density from the GPU (FMM at its default interior order, and
+    FP64 direct) against the oracle's sums on the same boundary solution (Eq. stress_1), each
+    at 1e-4 relative L2 (FMM) or 1e-6 (direct), and the closed form D^T = 1.00227.  The points
+    include 48 at 1/16 from the faces (a quarter of a voxel), where the element-wise error is
+    reported as well."""
     E, nu = 1.0, 0.3
     G = E / (2 * (1 + nu))
     V, T = W.cube_mesh(4)
@@ -214,19 +217,14 @@ def test_interior_stress_and_td(K):
     mask = np.zeros((len(T), 3), np.uint8)
     u, t, info = O.bem_solve_dense(V, T, mask, trac, G, nu, tol=1e-10, restart=100)
     rng = np.random.default_rng(4)
-    pts = rng.uniform(0.2, 0.8, size=(500, 3)).astype(np.float32)
+    deep = rng.uniform(0.2, 0.8, size=(452, 3))
+    near = rng.uniform(0.1, 0.9, size=(48, 3))
+    near[np.arange(48), np.arange(48) % 3] = np.where(np.arange(48) % 2 == 0, 1.0 / 16, 1 - 1.0 / 16)
+    pts = np.concatenate([deep, near]).astype(np.float32)
     ref_d, ref_s = O.bem_interior(pts.astype(np.float64), V, T, u, t, G, nu)
     ref_td, ref_en = O.topo_derivative(ref_s, G, nu)
-    # the representation is the difference of a single- and a double-layer sum; the FMM's
-    # relative error applies to each, so the tolerance grows with their cancellation
-    q, w = O.tri_quadrature(V, T)
-    qn = np.repeat(nrm, 16, axis=0)
-    sl_d = O.direct_disp(pts.astype(np.float64), q, qn, np.repeat(t, 16, axis=0) * w[:, None], None, G, nu)
-    canc = (np.linalg.norm(sl_d) + np.linalg.norm(ref_d - sl_d)) / np.linalg.norm(ref_d)
-    # far-field-dominated double layers and stresses need p = 8 for 1e-4 (p = 6 gives ~5e-4
-    # on this mesh); the displacement path meets it at p = 6 as well
-    for op, tol in ((K.BEM_DIRECT_FP64, 1e-6), (K.BEM_FMM, 1e-4 * max(1.0, canc))):
-        with K.Bem(V, T, op, p=8, m2l_rtol=1e-7) as b:
+    for op, tol in ((K.BEM_DIRECT_FP64, 1e-6), (K.BEM_FMM, 1e-4)):
+        with K.Bem(V, T, op) as b:
             b.set_material(K.material_K(G, nu), G)
             b.set_solution(u, t)
             dsp = np.zeros((len(pts), 3), np.float32)
@@ -235,9 +233,47 @@ def test_interior_stress_and_td(K):
             td = np.zeros(len(pts), np.float32)
             en = np.zeros(len(pts), np.float32)
             b.topo_derivative(pts, td, en)
-        assert rel(dsp, ref_d) < tol and rel(sig, ref_s) < tol
-        assert rel(td, ref_td) < 5 * tol and rel(en, ref_en) < 5 * tol
-    assert np.abs(td / 1.0022727272727273 - 1).max() < 0.06
+        errs = {"disp": rel(dsp, ref_d), "stress": rel(sig, ref_s), "td": rel(td, ref_td), "energy": rel(en, ref_en)}
+        worst_near = float(np.abs(sig[452:] - ref_s[452:]).max() / np.abs(ref_s[452:]).max())
+        print(op, {k: f"{v:.1e}" for k, v in errs.items()}, f"near-surface max {worst_near:.1e}")
+        assert all(v < tol for v in errs.values()), errs
+        assert worst_near < 10 * tol
+    assert np.abs(td[:452] / 1.0022727272727273 - 1).max() < 0.06
+
+
+def test_interior_layers_separately(K):
+    """The two sums the interior stress is made of (Eq. stress_1: D t w and S u w over the
+    quadrature sources of the cube's boundary solution), each evaluated alone by the FMM at the
+    interior order (p = 8, M2L cutoff 1e-7) against the oracle's direct sums, at 1e-4 relative
+    L2 each.  Their cancellation is a property of the solution, not of the FMM."""
+    E, nu = 1.0, 0.3
+    G = E / (2 * (1 + nu))
+    V, T = W.cube_mesh(4)
+    nrm, area, cen = O.tri_geometry(V, T)
+    trac = nrm @ np.diag([1.0, 0.0, 0.0]).T
+    mask = np.zeros((len(T), 3), np.uint8)
+    u, t, info = O.bem_solve_dense(V, T, mask, trac, G, nu, tol=1e-10, restart=100)
+    q, w = O.tri_quadrature(V, T)
+    qn = np.repeat(nrm, 16, axis=0)
+    sl = np.repeat(t, 16, axis=0) * w[:, None]
+    dl = -np.repeat(u, 16, axis=0) * w[:, None]
+    rng = np.random.default_rng(4)
+    pts = rng.uniform(0.2, 0.8, size=(500, 3))
+    f32 = lambda a: np.ascontiguousarray(a, np.float32)  # noqa: E731
+    qf, nf, slf, dlf, pf = (f32(a) for a in (q, qn, sl, dl, pts))
+    with K.Kfmm(p=8, m2l_rtol=1e-7) as f:
+        f.set_material(K.material_K(G, nu), G)
+        f.build(qf, nf, pf)
+        for name, s_, d_ in (("single", slf, None), ("double", None, dlf)):
+            for kind, no, ref in ((K.KFMM_DISP, 3, O.direct_disp), (K.KFMM_STRESS, 6, O.direct_stress)):
+                out = np.zeros((len(pts), no), np.float32)
+                f.eval(s_, d_, out, kind)
+                r = ref(pf.astype(np.float64), qf.astype(np.float64), nf.astype(np.float64),
+                        None if s_ is None else slf.astype(np.float64),
+                        None if d_ is None else dlf.astype(np.float64), G, nu)
+                e = rel(out, r)
+                print(name, kind, f"{e:.1e}")
+                assert e < 1e-4, (name, kind, e)
 
 
 def test_bem_errors(K):

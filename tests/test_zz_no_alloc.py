@@ -47,12 +47,21 @@ def test_noalloc_matches_direct_on_two_calls(K):
     with K.Kfmm() as f:
         f.set_material(K.material_K(2.3, 0.21), 2.3)
         calls = [
-            # (precision, torch dtype, kind, n_src, n_trg, tolerance)
-            (K.KFMM_FP32, torch.float32, K.KFMM_DISP, 20011, 37, 3e-5),
-            (K.KFMM_FP64, torch.float64, K.KFMM_STRESS, 3001, 1299, 1e-12),
+            # (precision, torch dtype, kind, n_src, n_trg, tolerance, layers)
+            (K.KFMM_FP32, torch.float32, K.KFMM_DISP, 20011, 37, 3e-5, "sl+dl"),
+            (K.KFMM_FP64, torch.float64, K.KFMM_STRESS, 3001, 1299, 1e-12, "sl+dl"),
+            # every other instantiation: single and double layer alone, FP32 stress
+            (K.KFMM_FP32, torch.float32, K.KFMM_DISP, 5003, 211, 3e-5, "sl"),
+            (K.KFMM_FP32, torch.float32, K.KFMM_DISP, 5003, 211, 3e-5, "dl"),
+            (K.KFMM_FP32, torch.float32, K.KFMM_STRESS, 4001, 301, 3e-5, "sl+dl"),
+            (K.KFMM_FP64, torch.float64, K.KFMM_DISP, 2003, 97, 1e-12, "dl"),
         ]
-        for prec, dt, kind, ns, nt, tol in calls:
+        for prec, dt, kind, ns, nt, tol, layers in calls:
             trg, src, nrm, sl, dl = case(rng, ns, nt, dt)
+            if layers == "sl":
+                dl = None
+            elif layers == "dl":
+                sl = None
             no = 3 if kind == K.KFMM_DISP else 6
             ref = torch.zeros(nt, no, dtype=dt, device="cuda")
             f.direct(trg, src, nrm, sl, dl, ref, kind, prec)
@@ -60,7 +69,7 @@ def test_noalloc_matches_direct_on_two_calls(K):
             K.kfmm_direct_noalloc(f.handle, trg, src, nrm, sl, dl, got, kind, prec)
             torch.cuda.synchronize()
             assert torch.isfinite(got).all()
-            assert rel(got, ref) < tol
+            assert rel(got, ref) < tol, (prec, kind, layers)
 
 
 def test_noalloc_rejects_oversize_and_host_arrays(K):

@@ -398,6 +398,17 @@ kfmm_status bem_destroy(bem_ctx *b);
 kfmm_status bem_set_material(bem_ctx *b, double K, double G);
 kfmm_status bem_set_stream(bem_ctx *b, void *stream);
 
+/* Quadrature of the triangles next to a collocation point (Sec. "Matrix-vector products":
+ * the sums over triangles neighbouring the one that holds the collocation point become
+ * inaccurate on fine meshes, which an upsampled quadrature fixes).  near_levels = 1: every
+ * off-diagonal block uses the 16-point rule (4 midpoint sub-triangles x the 4-node rule;
+ * the default).  near_levels = s in 2..5: the blocks of triangles sharing a vertex with the
+ * collocation triangle use the 4-node rule on 4^s sub-triangles (64, 256, 1024, 4096
+ * points); the summation keeps the 16-point sources and the local pass adds, per
+ * (triangle, neighbour) pair, the FP64 difference of the two rules.  Takes effect at the
+ * next operator application. */
+kfmm_status bem_set_quadrature(bem_ctx *b, int near_levels);
+
 /* Boundary conditions of Eq. elast for ncol load cases (1..32) sharing one mask:
  * known_is_disp [nt][3] (uint8: 1 = u_i prescribed, 0 = t_i prescribed), values [nt][3*ncol]
  * (the prescribed u or t of load case c in entries 3c .. 3c+2 of each row).  The load cases

@@ -145,15 +145,27 @@ def self_integrals(A, B, C, G=1.0, nu=0.3):
     return U.reshape(3, 3), T.reshape(3, 3)
 
 
-def bem_assemble(verts, tris, G=1.0, nu=0.3):
-    """Dense H = 1/2 I + P^Delta and Gm = U^Delta, (3nt) x (3nt)."""
+def bem_assemble(verts, tris, G=1.0, nu=0.3, near_levels=1):
+    """Dense H = 1/2 I + P^Delta and Gm = U^Delta, (3nt) x (3nt).  near_levels > 1: the blocks
+    of triangles sharing a vertex with the collocation triangle use the 4-node rule on
+    4^near_levels sub-triangles (the upsampled quadrature of Sec. "Matrix-vector products")."""
     verts = _f64(verts)
     tris = np.ascontiguousarray(tris, dtype=np.int32)
     n3 = 3 * tris.shape[0]
     H, Gm = np.zeros((n3, n3)), np.zeros((n3, n3))
-    _load().ko_bem_assemble(_dp(verts), tris.ctypes.data_as(_I32), ctypes.c_int64(tris.shape[0]),
-                            ctypes.c_double(G), ctypes.c_double(nu), _dp(H), _dp(Gm))
+    _load().ko_bem_assemble_near(_dp(verts), tris.ctypes.data_as(_I32), ctypes.c_int64(tris.shape[0]),
+                                 ctypes.c_double(G), ctypes.c_double(nu), ctypes.c_int(int(near_levels)), _dp(H),
+                                 _dp(Gm))
     return H, Gm
+
+
+def tri_block(A, B, C, x, levels=1, G=1.0, nu=0.3):
+    """(int U, int T) over the triangle ABC at x by the 4-node rule on 4^levels sub-triangles."""
+    A, B, C, x = (_f64(v).reshape(3) for v in (A, B, C, x))
+    U, T = np.zeros(9), np.zeros(9)
+    _load().ko_tri_block(_dp(A), _dp(B), _dp(C), _dp(x), ctypes.c_int(int(levels)), ctypes.c_double(G),
+                         ctypes.c_double(nu), _dp(U), _dp(T))
+    return U.reshape(3, 3), T.reshape(3, 3)
 
 
 def bem_system(H, Gm, known_is_disp, values):

@@ -329,6 +329,95 @@ void ko_self_integrals(const double *A, const double *B, const double *C, double
  * point l (centroid of triangle l), component m; column 3k+n = element k, component n.
  * Off-diagonal blocks by the 16-point rule; diagonal blocks analytic.  Row-major
  * (3 nt) x (3 nt). */
+/* int_T U and int_T T(., n) over the triangle (A, B, C) at the point x, by the 4-node degree-3
+ * rule on each of the 4^levels sub-triangles of `levels` rounds of midpoint subdivision
+ * (levels = 1 is the 16-point rule of Sec. "Matrix-vector products"; larger values are the
+ * upsampled quadrature of triangles near the collocation point).  Adds into bu, bt. */
+static void tri_block_rec(const double *A, const double *B, const double *C, const double *n, const double *x,
+                          int levels, double G, double nu, double *bu, double *bt)
+{
+    if (levels == 0) {
+        static const double bary[4][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3}, {0.6, 0.2, 0.2}, {0.2, 0.6, 0.2}, {0.2, 0.2, 0.6}};
+        static const double wt[4] = {-27.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0};
+        double nn[3], area, cen[3], Ku[9], Kt[9];
+        tri_geom(A, B, C, nn, &area, cen);
+        for (int g = 0; g < 4; ++g) {
+            double d[3];
+            for (int a = 0; a < 3; ++a)
+                d[a] = x[a] - (bary[g][0] * A[a] + bary[g][1] * B[a] + bary[g][2] * C[a]);
+            ko_kernel_U(d, G, nu, Ku);
+            ko_kernel_T(d, n, nu, Kt);
+            for (int a = 0; a < 9; ++a) {
+                bu[a] += Ku[a] * wt[g] * area;
+                bt[a] += Kt[a] * wt[g] * area;
+            }
+        }
+        return;
+    }
+    double mAB[3], mBC[3], mCA[3];
+    for (int a = 0; a < 3; ++a) {
+        mAB[a] = 0.5 * (A[a] + B[a]);
+        mBC[a] = 0.5 * (B[a] + C[a]);
+        mCA[a] = 0.5 * (C[a] + A[a]);
+    }
+    tri_block_rec(A, mAB, mCA, n, x, levels - 1, G, nu, bu, bt);
+    tri_block_rec(mAB, B, mBC, n, x, levels - 1, G, nu, bu, bt);
+    tri_block_rec(mCA, mBC, C, n, x, levels - 1, G, nu, bu, bt);
+    tri_block_rec(mBC, mCA, mAB, n, x, levels - 1, G, nu, bu, bt);
+}
+
+void ko_tri_block(const double *A, const double *B, const double *C, const double *x, int levels, double G,
+                  double nu, double *bu, double *bt)
+{
+    double n[3], area, cen[3];
+    tri_geom(A, B, C, n, &area, cen);
+    for (int a = 0; a < 9; ++a) bu[a] = bt[a] = 0.0;
+    tri_block_rec(A, B, C, n, x, levels, G, nu, bu, bt);
+}
+
+static int share_vertex(const int32_t *ta, const int32_t *tb)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (ta[i] == tb[j]) return 1;
+    return 0;
+}
+
+void ko_bem_assemble(const double *verts, const int32_t *tris, int64_t nt, double G, double nu,
+                     double *H, double *Gm);
+
+/* ko_bem_assemble with the blocks of triangles that share a vertex with the collocation
+ * triangle integrated on 4^near_levels sub-triangles (near_levels >= 1; 1 gives
+ * ko_bem_assemble's operator). */
+void ko_bem_assemble_near(const double *verts, const int32_t *tris, int64_t nt, double G, double nu,
+                          int near_levels, double *H, double *Gm)
+{
+    ko_bem_assemble(verts, tris, nt, G, nu, H, Gm);
+    if (near_levels <= 1) return;
+    int64_t n3 = 3 * nt;
+    double *cen = (double *)malloc(sizeof(double) * 3 * nt);
+    double *nrm = (double *)malloc(sizeof(double) * 3 * nt);
+    double *area = (double *)malloc(sizeof(double) * nt);
+    ko_tri_geometry(verts, tris, nt, nrm, area, cen);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t l = 0; l < nt; ++l) {
+        for (int64_t k = 0; k < nt; ++k) {
+            if (k == l || !share_vertex(tris + 3 * l, tris + 3 * k)) continue;
+            double bu[9], bt[9];
+            ko_tri_block(verts + 3 * tris[3 * k], verts + 3 * tris[3 * k + 1], verts + 3 * tris[3 * k + 2],
+                         cen + 3 * l, near_levels, G, nu, bu, bt);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    H[(3 * l + a) * n3 + 3 * k + b] = bt[3 * a + b];
+                    Gm[(3 * l + a) * n3 + 3 * k + b] = bu[3 * a + b];
+                }
+        }
+    }
+    free(cen);
+    free(nrm);
+    free(area);
+}
+
 void ko_bem_assemble(const double *verts, const int32_t *tris, int64_t nt, double G, double nu,
                      double *H, double *Gm)
 {

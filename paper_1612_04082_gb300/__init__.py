@@ -399,6 +399,7 @@ _bsig = {
     "bem_set_material": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
     "bem_set_stream": (ctypes.c_int, [_vp, _vp]),
     "bem_set_bc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    "bem_set_quadrature": (ctypes.c_int, [_vp, ctypes.c_int]),
     "bem_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bem_matvec": (ctypes.c_int, [_vp, _vp, _vp]),
     "bem_rhs": (ctypes.c_int, [_vp, _vp]),
@@ -531,6 +532,11 @@ class Bem:
 
     def set_bc(self, known_is_disp, values):
         bem_set_bc(self.handle, known_is_disp, values)
+
+    def set_quadrature(self, near_levels):
+        """Upsampled quadrature of the triangles sharing a vertex with a collocation triangle:
+        the 4-node rule on 4^near_levels sub-triangles (1 = the 16-point rule everywhere)."""
+        _bcheck(self.handle, _lib.bem_set_quadrature(self.handle, int(near_levels)))
 
     def apply(self, u, t, out):
         return bem_apply(self.handle, u, t, out)

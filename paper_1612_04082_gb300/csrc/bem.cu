@@ -36,6 +36,12 @@ struct bem_ctx {
     DevBuf qw;               // double [16 nt]: weights (sum to the element area)
     DevBuf cen32, cen64;     // centroids float / double [nt][3]
     DevBuf corrU, corrT;     // double [nt][9]: analytic self block minus own quadrature terms
+    int near_levels = 1;     // quadrature of the triangles sharing a vertex with the collocation
+                             // triangle: the 4-node rule on 4^near_levels sub-triangles
+    int near_ready = 0;      // near_levels the blocks below were made for (0 = none)
+    int64_t n_near = 0;      // (collocation triangle, neighbour) pairs
+    DevBuf nbr_off, nbr_idx; // int CSR: triangles sharing a vertex with each triangle
+    DevBuf corrN;            // double [n_near][18]: upsampled minus 16-point blocks, U then P
     int ncol = 1;            // density columns of the boundary conditions (load cases)
     int sol_ncol = 1;        // columns of the stored boundary solution
     DevBuf mask, val;        // uint8 [3 nt] (shared by the columns), double [ncol][3 nt]
@@ -199,6 +205,82 @@ __global__ void bem_setup_kernel(int64_t nt, const double *__restrict__ verts, c
     }
 }
 
+// 3x3 blocks of U (Eq. disp_1) and P (Eq. disp_2, normal n) at offset d, times wq, added into
+// U9, T9 (FP64, column `col` of each block is the kernel applied to e_col).
+__device__ void add_kelvin_blocks(const double3 d, const double3 n, const KelvinConst<double> &kc, double wq,
+                                  double *U9, double *T9)
+{
+    for (int col = 0; col < 3; ++col) {
+        double e[3] = {0, 0, 0};
+        e[col] = 1.0;
+        double ox = 0, oy = 0, oz = 0;
+        acc_sl<double>(d.x, d.y, d.z, kc.c_sl * e[0], kc.c_sl * e[1], kc.c_sl * e[2], kc.a34, ox, oy, oz);
+        U9[0 + col] += wq * ox;
+        U9[3 + col] += wq * oy;
+        U9[6 + col] += wq * oz;
+        ox = oy = oz = 0;
+        const double ue[3] = {kc.c_dl * e[0], kc.c_dl * e[1], kc.c_dl * e[2]};
+        const double nup = kc.b12 * (n.x * ue[0] + n.y * ue[1] + n.z * ue[2]);
+        acc_dl<double>(d.x, d.y, d.z, ue[0], ue[1], ue[2], n.x, n.y, n.z, nup, kc.b12, ox, oy, oz);
+        T9[0 + col] += wq * ox;
+        T9[3 + col] += wq * oy;
+        T9[6 + col] += wq * oz;
+    }
+}
+
+// Upsampled quadrature of the near triangles (Sec. "Matrix-vector products": the sums over
+// triangles next to the collocation point are the inaccurate ones): for each pair (l, k) of a
+// collocation triangle l and a triangle k sharing a vertex with it, the blocks of U and P over
+// k at xi_l by the 4-node rule on 4^levels sub-triangles (midpoint subdivision), minus the
+// 16-point rule's blocks that the summation already holds.  One thread per pair, FP64.
+__global__ void bem_near_kernel(int64_t n_pairs, const int *__restrict__ pair_l, const int *__restrict__ nbr_idx,
+                                int levels, const double *__restrict__ verts, const int *__restrict__ tris,
+                                const double *__restrict__ cen64, const double *__restrict__ q64,
+                                const double *__restrict__ qn64, const double *__restrict__ qw, double G, double nu,
+                                double *__restrict__ corrN)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_pairs) return;
+    const int l = pair_l[e], k = nbr_idx[e];
+    const auto kc = make_kelvin<double>(G, nu);
+    const double3 xi = ld3(cen64 + 3 * (int64_t)l);
+    const double3 n = ld3(qn64 + 3 * (16 * (int64_t)k));
+    double U9[9] = {0}, T9[9] = {0}, U16[9] = {0}, T16[9] = {0};
+    // the 16-point terms the summation holds for this pair
+    for (int m = 0; m < 16; ++m) {
+        const int64_t j = 16 * (int64_t)k + m;
+        add_kelvin_blocks(vsub(xi, ld3(q64 + 3 * j)), n, kc, qw[j], U16, T16);
+    }
+    const double3 A = ld3(verts + 3 * tris[3 * k]), B = ld3(verts + 3 * tris[3 * k + 1]),
+                  C = ld3(verts + 3 * tris[3 * k + 2]);
+    const double3 cr = vcross(vsub(B, A), vsub(C, A));
+    const double area = 0.5 * sqrt(vdot(cr, cr));
+    const int nsub = 1 << (2 * levels);
+    const double sub_area = area / nsub;
+    const double wt[4] = {-27.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0};
+    const double lam[4][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3}, {0.6, 0.2, 0.2}, {0.2, 0.6, 0.2}, {0.2, 0.2, 0.6}};
+    for (int s = 0; s < nsub; ++s) {
+        // sub-triangle s: base-4 digits, most significant first, pick the midpoint children
+        double3 a = A, bb = B, c = C;
+        for (int lev = levels - 1; lev >= 0; --lev) {
+            const int dgt = (s >> (2 * lev)) & 3;
+            const double3 mab = vmul(0.5, vadd(a, bb)), mbc = vmul(0.5, vadd(bb, c)), mca = vmul(0.5, vadd(c, a));
+            if (dgt == 0) { bb = mab; c = mca; }
+            else if (dgt == 1) { a = mab; c = mbc; }
+            else if (dgt == 2) { a = mca; bb = mbc; }
+            else { a = mbc; bb = mca; c = mab; }
+        }
+        for (int g = 0; g < 4; ++g) {
+            const double3 y = vadd(vadd(vmul(lam[g][0], a), vmul(lam[g][1], bb)), vmul(lam[g][2], c));
+            add_kelvin_blocks(vsub(xi, y), n, kc, wt[g] * sub_area, U9, T9);
+        }
+    }
+    for (int a = 0; a < 9; ++a) {
+        corrN[18 * e + a] = U9[a] - U16[a];
+        corrN[18 * e + 9 + a] = T9[a] - T16[a];
+    }
+}
+
 // Densities at the quadrature points for columns c0 .. c0 + cn - 1 of M(u, t): sl = -t_k w,
 // dl = u_k w, written [16 nt][3 cn].  mode 0: u, t given ([nt][3], one column; either may be
 // NULL); mode 1: from the unknowns x [ncol][3 nt] and the mask (Eq. num2); mode 2: from the
@@ -236,11 +318,33 @@ __global__ void bem_density_kernel(int64_t nt, int mode, int c0, int cn, const d
 
 // Local pass for columns c0 .. c0 + cn - 1: out_l = sign * (f_l + 1/2 u_l + corrT_l u_l -
 // corrU_l t_l), with f [nt][3 cn] the summed field, FP64 output [ncol][3 nt] (mode 0: [nt][3]).
+// Pair (k, comp) values of u and t of one column for the local pass.
+__device__ __forceinline__ void local_ut(int mode, int64_t k, const double *u, const double *t, const double *xc,
+                                         const uint8_t *mask, double *uu, double *tt)
+{
+    for (int c = 0; c < 3; ++c) {
+        const int64_t i = 3 * k + c;
+        uu[c] = tt[c] = 0.0;
+        if (mode == 0) {
+            uu[c] = u ? u[i] : 0.0;
+            tt[c] = t ? t[i] : 0.0;
+        } else if (mode == 1) {
+            if (mask[i]) tt[c] = xc[i];
+            else uu[c] = xc[i];
+        } else {
+            if (mask[i]) uu[c] = xc[i];
+            else tt[c] = xc[i];
+        }
+    }
+}
+
 template <typename R>
 __global__ void bem_post_kernel(int64_t nt, int mode, int c0, int cn, double sign, const R *__restrict__ f,
                                 const double *__restrict__ u, const double *__restrict__ t,
                                 const double *__restrict__ x, const uint8_t *__restrict__ mask,
-                                const double *__restrict__ cU, const double *__restrict__ cT, double *__restrict__ out)
+                                const double *__restrict__ cU, const double *__restrict__ cT,
+                                const int *__restrict__ nbr_off, const int *__restrict__ nbr_idx,
+                                const double *__restrict__ corrN, double *__restrict__ out)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nt * cn) return;
@@ -264,11 +368,20 @@ __global__ void bem_post_kernel(int64_t nt, int mode, int c0, int cn, double sig
         }
     }
     double *o = out + (mode == 0 ? 0 : col);
+    double v[3];
     for (int a = 0; a < 3; ++a) {
-        double v = (double)f[k * 3 * cn + 3 * cc + a] + 0.5 * uu[a];
-        for (int c = 0; c < 3; ++c) v += cT[9 * k + 3 * a + c] * uu[c] - cU[9 * k + 3 * a + c] * tt[c];
-        o[3 * k + a] = sign * v;
+        v[a] = (double)f[k * 3 * cn + 3 * cc + a] + 0.5 * uu[a];
+        for (int c = 0; c < 3; ++c) v[a] += cT[9 * k + 3 * a + c] * uu[c] - cU[9 * k + 3 * a + c] * tt[c];
     }
+    if (corrN)  // upsampled quadrature of the neighbouring triangles
+        for (int e = nbr_off[k]; e < nbr_off[k + 1]; ++e) {
+            double un[3], tn[3];
+            local_ut(mode, nbr_idx[e], u, t, xc, mask, un, tn);
+            const double *dU = corrN + 18 * (int64_t)e, *dT = dU + 9;
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c) v[a] += dT[3 * a + c] * un[c] - dU[3 * a + c] * tn[c];
+        }
+    for (int a = 0; a < 3; ++a) o[3 * k + a] = sign * v[a];
 }
 
 // ------------------------------------------------------------------------------------
@@ -473,28 +586,80 @@ static kfmm_status bem_stage(bem_ctx *b, DevBuf &buf, const void *p, size_t byte
     return KFMM_OK;
 }
 
+// Neighbour lists (triangles sharing a vertex) and the upsampled near blocks (bem_near_kernel).
+static kfmm_status bem_near_setup(bem_ctx *b)
+{
+    const int64_t nt = b->nt;
+    if (b->n_near == 0) {
+        std::vector<int32_t> ht(3 * nt);
+        BK_CUDA(cudaMemcpy(ht.data(), b->tris.p, sizeof(int32_t) * 3 * nt, cudaMemcpyDeviceToHost));
+        std::vector<std::vector<int>> by_vertex(b->nv);
+        for (int64_t k = 0; k < nt; ++k)
+            for (int e = 0; e < 3; ++e) by_vertex[ht[3 * k + e]].push_back((int)k);
+        std::vector<int> off(nt + 1, 0), idx, pl;
+        std::vector<int> tmp;
+        for (int64_t l = 0; l < nt; ++l) {
+            tmp.clear();
+            for (int e = 0; e < 3; ++e)
+                for (int k : by_vertex[ht[3 * l + e]])
+                    if (k != l) tmp.push_back(k);
+            std::sort(tmp.begin(), tmp.end());
+            tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+            for (int k : tmp) {
+                idx.push_back(k);
+                pl.push_back((int)l);
+            }
+            off[l + 1] = (int)idx.size();
+        }
+        b->n_near = (int64_t)idx.size();
+        BK_CUDA(b->nbr_off.ensure(sizeof(int) * (nt + 1)));
+        BK_CUDA(b->nbr_idx.ensure(sizeof(int) * std::max<int64_t>(1, 2 * b->n_near)));
+        BK_CUDA(cudaMemcpy(b->nbr_off.p, off.data(), sizeof(int) * (nt + 1), cudaMemcpyHostToDevice));
+        if (b->n_near) {
+            BK_CUDA(cudaMemcpy(b->nbr_idx.p, idx.data(), sizeof(int) * b->n_near, cudaMemcpyHostToDevice));
+            // the pair's collocation triangle, behind the neighbour indices
+            BK_CUDA(cudaMemcpy(b->nbr_idx.as<int>() + b->n_near, pl.data(), sizeof(int) * b->n_near,
+                               cudaMemcpyHostToDevice));
+        }
+    }
+    BK_CUDA(b->corrN.ensure(sizeof(double) * 18 * std::max<int64_t>(1, b->n_near)));
+    if (b->n_near) {
+        bem_near_kernel<<<g1(b->n_near, 128), 128, 0, b->stream>>>(
+            b->n_near, b->nbr_idx.as<int>() + b->n_near, b->nbr_idx.as<int>(), b->near_levels, b->verts.as<double>(),
+            b->tris.as<int>(), b->cen64.as<double>(), b->q64.as<double>(), b->qn64.as<double>(), b->qw.as<double>(),
+            b->G, b->nu, b->corrN.as<double>());
+        BK_LAUNCH();
+    }
+    b->near_ready = b->near_levels;
+    return KFMM_OK;
+}
+
 static kfmm_status bem_setup(bem_ctx *b)
 {
-    if (b->setup_G == b->G && b->setup_nu == b->nu) return KFMM_OK;
+    const bool material = !(b->setup_G == b->G && b->setup_nu == b->nu);
     const int64_t nt = b->nt;
-    DevBuf bad;
-    BK_CUDA(bad.ensure(sizeof(int)));
-    BK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), b->stream));
-    bem_setup_kernel<<<g1(nt, 128), 128, 0, b->stream>>>(
-        nt, b->verts.as<double>(), b->tris.as<int>(), b->G, b->nu, b->q32.as<float>(), b->qn32.as<float>(),
-        b->q64.as<double>(), b->qn64.as<double>(), b->qw.as<double>(), b->cen32.as<float>(), b->cen64.as<double>(),
-        b->corrU.as<double>(), b->corrT.as<double>(), bad.as<int>());
-    BK_LAUNCH();
-    int hb = 0;
-    BK_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
-    BK_CUDA(cudaStreamSynchronize(b->stream));
-    if (hb) return b->fail(KFMM_ERR_INVALID_ARG, "bem: zero-area or non-finite triangle");
-    b->setup_G = b->G;
-    b->setup_nu = b->nu;
-    if (b->op == BEM_FMM && !b->surf_built) {
-        BK_FMM(kfmm_build(b->surf, b->q32.as<float>(), b->qn32.as<float>(), 16 * nt, b->cen32.as<float>(), nt));
-        b->surf_built = true;
+    if (material) {
+        DevBuf bad;
+        BK_CUDA(bad.ensure(sizeof(int)));
+        BK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), b->stream));
+        bem_setup_kernel<<<g1(nt, 128), 128, 0, b->stream>>>(
+            nt, b->verts.as<double>(), b->tris.as<int>(), b->G, b->nu, b->q32.as<float>(), b->qn32.as<float>(),
+            b->q64.as<double>(), b->qn64.as<double>(), b->qw.as<double>(), b->cen32.as<float>(),
+            b->cen64.as<double>(), b->corrU.as<double>(), b->corrT.as<double>(), bad.as<int>());
+        BK_LAUNCH();
+        int hb = 0;
+        BK_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+        BK_CUDA(cudaStreamSynchronize(b->stream));
+        if (hb) return b->fail(KFMM_ERR_INVALID_ARG, "bem: zero-area or non-finite triangle");
+        b->setup_G = b->G;
+        b->setup_nu = b->nu;
+        b->near_ready = 0;
+        if (b->op == BEM_FMM && !b->surf_built) {
+            BK_FMM(kfmm_build(b->surf, b->q32.as<float>(), b->qn32.as<float>(), 16 * nt, b->cen32.as<float>(), nt));
+            b->surf_built = true;
+        }
     }
+    if (b->near_levels > 1 && b->near_ready != b->near_levels) BK_TRY(bem_near_setup(b));
     return KFMM_OK;
 }
 
@@ -520,9 +685,9 @@ static kfmm_status bem_op_apply(bem_ctx *b, int mode, const double *u, const dou
                                                                       b->dlq.as<float>());
         BK_LAUNCH();
         BK_FMM(kfmm_eval(b->surf, b->slq.as<float>(), b->dlq.as<float>(), nc, KFMM_DISP, b->fout.as<float>()));
-        bem_post_kernel<float><<<g1(nt * nc), 256, 0, b->stream>>>(nt, mode, 0, nc, sign, b->fout.as<float>(), u, t,
-                                                                   x, mask, b->corrU.as<double>(),
-                                                                   b->corrT.as<double>(), out);
+        bem_post_kernel<float><<<g1(nt * nc), 256, 0, b->stream>>>(
+            nt, mode, 0, nc, sign, b->fout.as<float>(), u, t, x, mask, b->corrU.as<double>(), b->corrT.as<double>(),
+            b->nbr_off.as<int>(), b->nbr_idx.as<int>(), b->near_levels > 1 ? b->corrN.as<double>() : nullptr, out);
         BK_LAUNCH();
         return KFMM_OK;
     }
@@ -540,9 +705,9 @@ static kfmm_status bem_op_apply(bem_ctx *b, int mode, const double *u, const dou
         else
             BK_FMM(kfmm_direct(b->surf, KFMM_FP64, b->cen64.p, nt, b->q64.p, b->qn64.p, nq, b->slq.p, b->dlq.p,
                                KFMM_DISP, b->fout.p));
-        bem_post_kernel<double><<<g1(nt), 256, 0, b->stream>>>(nt, mode, c, 1, sign, b->fout.as<double>(), u, t, x,
-                                                               mask, b->corrU.as<double>(), b->corrT.as<double>(),
-                                                               out);
+        bem_post_kernel<double><<<g1(nt), 256, 0, b->stream>>>(
+            nt, mode, c, 1, sign, b->fout.as<double>(), u, t, x, mask, b->corrU.as<double>(), b->corrT.as<double>(),
+            b->nbr_off.as<int>(), b->nbr_idx.as<int>(), b->near_levels > 1 ? b->corrN.as<double>() : nullptr, out);
         BK_LAUNCH();
     }
     return KFMM_OK;
@@ -976,6 +1141,13 @@ kfmm_status bem_set_stream(bem_ctx *b, void *stream)
     b->stream = (cudaStream_t)stream;
     kfmm_set_stream(b->surf, stream);
     if (b->vol) kfmm_set_stream(b->vol, stream);
+    return KFMM_OK;
+}
+
+kfmm_status bem_set_quadrature(bem_ctx *b, int near_levels)
+{
+    if (!b || near_levels < 1 || near_levels > 5) return KFMM_ERR_INVALID_ARG;
+    b->near_levels = near_levels;
     return KFMM_OK;
 }
 

@@ -131,11 +131,73 @@ def features_for(V, T, cell, fdir, prev: IterationRecord | None, td_prev: np.nda
     return np.concatenate([cen, nrm, area[:, None], xprev, tdl[:, None]], axis=1), keys
 
 
+def adaptive_td(mask, h, evaluate, C, coarse=2, band=0.01, top=0.05):
+    """Two-scale sampling of the topological derivative over the material voxels (Sec.
+    "Discussion and future work": a coarse grid set by the smallest feature to detect, refined
+    where the threshold function differs between neighbouring cells).
+
+    evaluate(points [m, 3] float32) -> D^T [m].  Steps:
+      1. one sample per coarse cell (coarse^3 voxels): its material voxel nearest the cell's
+         centre; every material voxel of the cell takes that value;
+      2. threshold estimate D_C = D_min + C (D_max - D_min) from the samples;
+      3. exact values at every material voxel of the cells whose threshold function (value
+         below D_C + band (D_max - D_min)) differs from a face-neighbouring cell's or is set
+         itself, and of the cells within `top` of D_max (where the extreme values that fix
+         D_C are), all in one further evaluation.
+    Returns (td [nx, ny, nz] float32, exact [nx, ny, nz] bool, evaluations)."""
+    ii = np.argwhere(mask > 0)
+    cells = ii // coarse
+    dims = np.asarray(mask.shape) // coarse + 1
+    cid = (cells[:, 0] * dims[1] + cells[:, 1]) * dims[2] + cells[:, 2]
+    centre = (cells + 0.5) * coarse - 0.5
+    dist = np.sum((ii - centre) ** 2, axis=1)
+    order = np.lexsort((dist, cid))  # per cell, the voxel nearest its centre first
+    first = order[np.r_[True, cid[order][1:] != cid[order][:-1]]]
+    samples = ii[first]
+    pts = np.ascontiguousarray((samples + 0.5) * h, np.float32)
+    val = np.asarray(evaluate(pts), np.float32)
+    ucid, inv = np.unique(cid, return_inverse=True)
+    cell_val = np.zeros(len(ucid), np.float32)
+    cell_val[np.searchsorted(ucid, cid[first])] = val
+    dmin, dmax = float(val.min()), float(val.max())
+    dc = dmin + C * (dmax - dmin)
+    low = cell_val < dc + band * (dmax - dmin)
+    high = cell_val >= dmax - top * (dmax - dmin)
+    # threshold function differing from a face neighbour (cells looked up by id)
+    cpos = np.stack(np.unravel_index(ucid, tuple(dims)), axis=1)
+    refine = low | high
+    for ax in range(3):
+        for step in (-1, 1):
+            nb = cpos.copy()
+            nb[:, ax] += step
+            ok = np.all((nb >= 0) & (nb < dims), axis=1)
+            nid = np.ravel_multi_index(tuple(nb[ok].T), tuple(dims))
+            pos = np.searchsorted(ucid, nid)
+            pos = np.clip(pos, 0, len(ucid) - 1)
+            hit = ucid[pos] == nid
+            idx = np.flatnonzero(ok)[hit]
+            refine[idx] |= low[idx] != low[pos[hit]]
+    td = np.zeros(mask.shape, np.float32)
+    td[tuple(ii.T)] = cell_val[inv]
+    exact = np.zeros(mask.shape, bool)
+    exact[tuple(samples.T)] = True
+    sel = refine[inv] & ~exact[tuple(ii.T)]
+    if sel.any():
+        fine = ii[sel]
+        td[tuple(fine.T)] = np.asarray(evaluate(np.ascontiguousarray((fine + 0.5) * h, np.float32)), np.float32)
+        exact[tuple(fine.T)] = True
+    td[tuple(samples.T)] = val
+    return td, exact, int(len(samples) + sel.sum())
+
+
 def optimize(problem: Problem, C: float = 0.02, iters: int = 10, alpha_c: float = 0.0, p: int = 6,
-             solve_kw: dict | None = None, warm_start=None, device: int = 0, verbose: bool = False):
+             solve_kw: dict | None = None, warm_start=None, device: int = 0, verbose: bool = False,
+             td_sampling: str = "full"):
     """Run the hard-kill loop.  warm_start(features [nt, 11]) -> x0 [nt, 3] or None, called
-    with this iteration's features (previous unknowns carried over).  Returns (mask, history),
-    history = list of IterationRecord with stats {alpha, psi, iters, seconds, nt, removed}."""
+    with this iteration's features (previous unknowns carried over).  td_sampling: "full"
+    (D^T at every material voxel) or "adaptive" (two-scale sampling, `adaptive_td`).  Returns
+    (mask, history), history = list of IterationRecord with stats {alpha, psi, iters,
+    seconds, nt, removed, td_points}."""
     kw = dict(tol=1e-6, restart=100, maxit=5000, refine=True, inner_tol=1e-3)
     if solve_kw:
         kw.update(solve_kw)
@@ -164,9 +226,20 @@ def optimize(problem: Problem, C: float = 0.02, iters: int = 10, alpha_c: float 
                      raise_on_fail=False, **kw)
         solve_s = time.perf_counter() - t0
         ii = np.argwhere(mask > 0)
-        pts = np.ascontiguousarray((ii + 0.5) * problem.h, np.float32)
-        td = np.zeros(len(pts), np.float32)
-        b.topo_derivative(pts, td)
+        t1 = time.perf_counter()
+        if td_sampling == "adaptive":
+            def evaluate(p_):
+                out = np.zeros(len(p_), np.float32)
+                b.topo_derivative(p_, out)
+                return out
+            td_full, _, n_td = adaptive_td(mask, problem.h, evaluate, C)
+            td = td_full[tuple(ii.T)]
+        else:
+            pts = np.ascontiguousarray((ii + 0.5) * problem.h, np.float32)
+            td = np.zeros(len(pts), np.float32)
+            b.topo_derivative(pts, td)
+            n_td = len(pts)
+        td_s = time.perf_counter() - t1
         prev_bem = b  # its solution gives the next iteration's carried-over unknowns
         x = np.where(kd > 0, t, u)
         _, _, area = triangle_geometry(V, T)
@@ -178,7 +251,8 @@ def optimize(problem: Problem, C: float = 0.02, iters: int = 10, alpha_c: float 
                                                "outer": st["outer"], "relres": st["relres"],
                                                "converged": bool(st["converged"]), "seconds": solve_s,
                                                "x0_relres": st["x0_relres"],
-                                               "nt": len(T), "warm": x0 is not None})
+                                               "nt": len(T), "warm": x0 is not None, "td_points": n_td,
+                                               "td_seconds": td_s})
         history.append(rec)
         if warm_start is not None and hasattr(warm_start, "observe"):
             warm_start.observe(rec)

@@ -54,6 +54,34 @@ def test_apply_matches_dense_operator(K, sphere, op, tol):
     assert rel(out.reshape(-1), ref) < tol
 
 
+@pytest.mark.parametrize("op,tol", [("direct", 1e-10), ("fmm", 1e-4)])
+def test_upsampled_near_quadrature_matches_dense_operator(K, sphere, op, tol):
+    """bem_set_quadrature(3): the blocks of triangles sharing a vertex with the collocation
+    triangle on 4^3 sub-triangles, against the oracle's dense operator with the same rule
+    (FP64 direct to 1e-10; the FMM to its 1e-4).  Also the operator changes: the rigid-
+    translation rows shrink as in the oracle's own test."""
+    V, T, H1, Gm1, nrm, area, cen = sphere
+    H, Gm = O.bem_assemble(V, T, G0, NU0, near_levels=3)
+    rng = np.random.default_rng(7)
+    u, t = rng.normal(size=(len(T), 3)), rng.normal(size=(len(T), 3))
+    ref = H @ u.reshape(-1) - Gm @ t.reshape(-1)
+    opc = K.BEM_DIRECT_FP64 if op == "direct" else K.BEM_FMM
+    with K.Bem(V, T, opc) as b:
+        b.set_material(K.material_K(G0, NU0), G0)
+        b.set_quadrature(3)
+        out = np.zeros((len(T), 3))
+        b.apply(u, t, out)
+        assert rel(out.reshape(-1), ref) < tol
+        tr = np.zeros((len(T), 3))
+        tr[:, 0] = 1.0
+        b.apply(tr, None, out)
+        if op == "direct":
+            assert np.abs(out).max() < np.abs(H1 @ tr.reshape(-1)).max() / 20
+        b.set_quadrature(1)  # back to the 16-point rule everywhere
+        b.apply(u, t, out)
+        assert rel(out.reshape(-1), H1 @ u.reshape(-1) - Gm1 @ t.reshape(-1)) < tol
+
+
 def test_lame_sphere_direct_fp64_matches_oracle(K, sphere):
     """Config 1: unit sphere, 1280 triangles, t = +n, GMRES to 1e-8."""
     V, T, H, Gm, nrm, area, cen = sphere

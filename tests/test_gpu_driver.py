@@ -66,3 +66,34 @@ def test_learned_warm_start_beats_zero_start(K):
     later_warm = sum(h.stats["iters"] for h in warm[2:])
     assert later_warm < later_cold
     ws.net.close()
+
+
+def test_adaptive_td_sampling_gives_the_same_designs(K):
+    """Two-scale D^T sampling (Sec. "Discussion and future work") against D^T at every
+    material voxel: the same voxels removed at every iteration, so the same designs, with fewer
+    D^T evaluations."""
+    from paper_1612_04082_gb300 import driver as D
+    prob = D.cantilever(6)
+    m_full, full = D.optimize(prob, C=0.02, iters=4)
+    m_ad, ad = D.optimize(prob, C=0.02, iters=4, td_sampling="adaptive")
+    assert np.array_equal(m_full, m_ad)
+    assert [h.stats["nt"] for h in full] == [h.stats["nt"] for h in ad]
+    assert sum(h.stats["td_points"] for h in ad) < sum(h.stats["td_points"] for h in full)
+
+
+def test_learned_start_against_previous_iterate_start(K):
+    """The learned warm start against the previous-iterate start it builds on (the fair
+    baseline, not a zero start): never worse by more than 5% in inner GMRES iterations (the
+    network's direction is kept only when it lowers the residual of the new problem), and the
+    measured counts are printed.  Whether it is better is a measurement, not a claim."""
+    from paper_1612_04082_gb300 import driver as D
+    prob = D.cantilever(6)
+    _, prev = D.optimize(prob, C=0.02, iters=5, warm_start=lambda f: f[:, 7:10])
+    ws = D.LearnedWarmStart()
+    _, learned = D.optimize(prob, C=0.02, iters=5, warm_start=ws)
+    assert [h.stats["nt"] for h in learned] == [h.stats["nt"] for h in prev]
+    it_prev = [h.stats["iters"] for h in prev]
+    it_learned = [h.stats["iters"] for h in learned]
+    print("inner iterations, previous-iterate start:", it_prev, "learned start:", it_learned)
+    assert sum(it_learned[2:]) <= 1.05 * sum(it_prev[2:])
+    ws.net.close()

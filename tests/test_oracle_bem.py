@@ -240,6 +240,69 @@ def test_lame_shell():
     assert np.abs(ur / ex - 1).max() < 0.08
 
 
+def _gl_triangle_block(A, B, C, x, n, G, nu, m=48):
+    """int_T U and int_T T(., n) at x by a tensor Gauss-Legendre rule on the collapsed square
+    (y = A + u (B - A) + (1 - u) w (C - A), dA = 2 |T| (1 - u) du dw): independent of the
+    midpoint-subdivision rule it checks."""
+    g, wg = np.polynomial.legendre.leggauss(m)
+    g, wg = 0.5 * (g + 1), 0.5 * wg
+    area = 0.5 * np.linalg.norm(np.cross(B - A, C - A))
+    U, T = np.zeros((3, 3)), np.zeros((3, 3))
+    for u, wu in zip(g, wg):
+        for w_, ww in zip(g, wg):
+            y = A + u * (B - A) + (1 - u) * w_ * (C - A)
+            wt = 2 * area * (1 - u) * wu * ww
+            U += wt * O.kernel_U(x - y, G, nu)
+            T += wt * O.kernel_T(x - y, n, nu)
+    return U, T
+
+
+def test_upsampled_near_block_converges():
+    """The upsampled quadrature of a triangle next to the collocation point (Sec. "Matrix-
+    vector products"): the 4-node rule on 4^s sub-triangles converges to the integral (an
+    independent tensor Gauss-Legendre rule), its error falling ~16x per level (degree-3 rule,
+    h^4), from ~1e-3 at the 16-point rule to < 1e-6 at 4^4 sub-triangles."""
+    G, nu = 1.3, 0.27
+    V, T = W.icosphere(2)
+    nrm, area, cen = O.tri_geometry(V, T)
+    k = next(i for i in range(1, len(T)) if len(set(T[i]) & set(T[0])) == 1)  # shares one vertex
+    ref_U, ref_T = _gl_triangle_block(*V[T[k]], cen[0], nrm[k], G, nu)
+    errs = []
+    for lev in range(1, 5):
+        Ub, Tb = O.tri_block(*V[T[k]], cen[0], levels=lev, G=G, nu=nu)
+        errs.append(max(np.abs(Ub - ref_U).max() / np.abs(ref_U).max(), np.abs(Tb - ref_T).max() / np.abs(ref_T).max()))
+    assert errs[0] > 1e-5 and errs[-1] < 1e-6, errs
+    assert all(b < a / 8 for a, b in zip(errs, errs[1:])), errs
+    # levels = 1 is the 16-point rule of the dense operator
+    H, Gm = O.bem_assemble(V, T, G, nu)
+    Ub, Tb = O.tri_block(*V[T[k]], cen[0], levels=1, G=G, nu=nu)
+    assert np.allclose(Gm[0:3, 3 * k:3 * k + 3], Ub, rtol=0, atol=1e-13 * np.abs(Ub).max())
+    assert np.allclose(H[0:3, 3 * k:3 * k + 3], Tb, rtol=0, atol=1e-13 * np.abs(Tb).max())
+
+
+def test_upsampled_near_blocks_restore_rigid_translation():
+    """A rigid translation solves the homogeneous problem: 1/2 u + P u = 0 on a closed surface.
+    The discrete rows of H fail that by the quadrature error, dominated by the triangles next
+    to the collocation point; upsampling them (4^3 sub-triangles) cuts the worst row >= 20x,
+    and leaves the blocks of the other triangles unchanged."""
+    V, T = W.icosphere(2)
+    errs = []
+    for lev in (1, 3):
+        H, Gm = O.bem_assemble(V, T, G0, NU0, near_levels=lev)
+        tr = np.zeros((len(T), 3))
+        tr[:, 0] = 1.0
+        errs.append(np.abs(H @ tr.reshape(-1)).max())
+        if lev == 1:
+            H1 = H
+    assert errs[1] < errs[0] / 20, errs
+    near = np.zeros((len(T), len(T)), bool)
+    for l in range(len(T)):
+        for k in range(len(T)):
+            near[l, k] = k != l and len(set(T[l]) & set(T[k])) > 0
+    far = np.repeat(np.repeat(~near, 3, axis=0), 3, axis=1)
+    assert np.array_equal(H[far], H1[far])
+
+
 def test_spherical_cavity_exterior_problem():
     """Exterior problem (the void surfaces of a periodic cell, Sec. "Periodic cell of a
     metamaterial"): a spherical cavity of radius a in an infinite medium, normals out of the

@@ -142,10 +142,19 @@ def adaptive_td(mask, h, evaluate, C, coarse=2, band=0.01, top=0.05):
       2. threshold estimate D_C = D_min + C (D_max - D_min) from the samples;
       3. exact values at every material voxel of the cells whose threshold function (value
          below D_C + band (D_max - D_min)) differs from a face-neighbouring cell's or is set
-         itself, and of the cells within `top` of D_max (where the extreme values that fix
-         D_C are), all in one further evaluation.
+         itself, of the cells within `top` of D_max, and of the cells on the material's
+         boundary, all in one further evaluation.
+    Every cell holding a voxel of the material's boundary (a face towards a void or the
+    outside) is evaluated exactly as well: the shape features, and the stress concentrations
+    at supports, loads and holes whose D_max sets D_C, are there.
     Returns (td [nx, ny, nz] float32, exact [nx, ny, nz] bool, evaluations)."""
     ii = np.argwhere(mask > 0)
+    padded = np.pad(mask > 0, 1)
+    interior = np.ones(mask.shape, bool)
+    for ax in range(3):
+        for step in (-1, 1):
+            interior &= np.roll(padded, step, axis=ax)[1:-1, 1:-1, 1:-1]
+    surface = ~interior[tuple(ii.T)]
     cells = ii // coarse
     dims = np.asarray(mask.shape) // coarse + 1
     cid = (cells[:, 0] * dims[1] + cells[:, 1]) * dims[2] + cells[:, 2]
@@ -166,6 +175,8 @@ def adaptive_td(mask, h, evaluate, C, coarse=2, band=0.01, top=0.05):
     # threshold function differing from a face neighbour (cells looked up by id)
     cpos = np.stack(np.unravel_index(ucid, tuple(dims)), axis=1)
     refine = low | high
+    surf_cells = np.unique(cid[surface])
+    refine[np.searchsorted(ucid, surf_cells)] = True
     for ax in range(3):
         for step in (-1, 1):
             nb = cpos.copy()
@@ -335,3 +346,51 @@ class LearnedWarmStart:
             a, g = 1.0, 0.0
         self.last_coef = (float(a), float(g), float(r_new / max(r_prev, 1e-300)))
         return a * xp + g * d
+
+
+def main(argv=None):
+    """Run the loop from the command line and print one line per iteration (alpha, Psi/Psi_0,
+    triangles, inner GMRES iterations, solve and D^T seconds) and a closing JSON line:
+
+      python -m paper_1612_04082_gb300.driver --case cantilever --n 48 --iters 20 --C 0.02
+    """
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="cantilever", choices=["cantilever", "bridge"])
+    ap.add_argument("--n", type=int, default=24, help="voxels per unit length")
+    ap.add_argument("--iters", type=int, default=10)
+    ap.add_argument("--C", type=float, default=0.02)
+    ap.add_argument("--alpha-c", type=float, default=0.0)
+    ap.add_argument("--td", default="full", choices=["full", "adaptive"])
+    ap.add_argument("--warm", default="previous", choices=["none", "previous", "learned"])
+    ap.add_argument("--device", type=int, default=0)
+    a = ap.parse_args(argv)
+    prob = cantilever(a.n) if a.case == "cantilever" else bridge(a.n)
+    warm = None
+    if a.warm == "previous":
+        warm = lambda f: f[:, 7:10] if np.any(f[:, 7:10]) else None  # noqa: E731
+    elif a.warm == "learned":
+        warm = LearnedWarmStart()
+    t0 = time.perf_counter()
+    mask, hist = optimize(prob, C=a.C, iters=a.iters, alpha_c=a.alpha_c, warm_start=warm, device=a.device,
+                          td_sampling=a.td)
+    wall = time.perf_counter() - t0
+    psi0 = hist[0].stats["psi"]
+    rows = []
+    for k, h in enumerate(hist):
+        s = h.stats
+        rows.append({"it": k, "alpha": s["alpha"], "psi_ratio": s["psi"] / psi0, "nt": s["nt"], "gmres": s["iters"],
+                     "outer": s["outer"], "relres": s["relres"], "solve_s": s["seconds"], "td_s": s["td_seconds"],
+                     "td_points": s["td_points"], "removed": s.get("removed", 0)})
+        print(f"it {k:2d}  alpha {s['alpha']:.4f}  Psi/Psi0 {s['psi'] / psi0:.4f}  nt {s['nt']:7d}  gmres {s['iters']:5d} "
+              f"({s['outer']} outer, relres {s['relres']:.1e})  solve {s['seconds']:.2f} s  D^T {s['td_seconds']:.2f} s "
+              f"({s['td_points']} points)", flush=True)
+    print(json.dumps({"case": a.case, "voxels": [prob.nx, prob.ny, prob.nz], "h": prob.h, "C": a.C, "td": a.td,
+                      "warm": a.warm, "iterations": rows, "wall_s": wall}))
+    if isinstance(warm, LearnedWarmStart):
+        warm.net.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,7 +1,9 @@
 """Two-scale sampling of the topological derivative (Sec. "Discussion and future work": a
-coarse grid, refined where the threshold function differs between neighbouring cells), on
-synthetic D^T fields: the voxels the hard-kill update removes (D^T below D_C = D_min +
-C (D_max - D_min)) are the same as with D^T at every voxel, with far fewer evaluations."""
+coarse grid, refined where the threshold function differs between neighbouring cells and on
+the material's boundary), on synthetic D^T fields: the voxels the hard-kill update removes
+(D^T below D_C = D_min + C (D_max - D_min)) are the same as with D^T at every voxel, with fewer
+evaluations (the saving grows with the ratio of volume to surface voxels, as the paper notes:
+here 48 x 24 x 24 voxels)."""
 import os
 import sys
 
@@ -21,10 +23,10 @@ def field(p):
             + 0.4 * (z - 0.5) ** 2 + 0.05 * np.sin(7 * y) + 0.02 * x)
 
 
-@pytest.mark.parametrize("C,holes,frac", [(0.02, 0, 0.6), (0.05, 40, 0.75), (0.1, 120, 0.85), (0.02, 300, 0.6)])
+@pytest.mark.parametrize("C,holes,frac", [(0.02, 0, 0.7), (0.05, 40, 0.8), (0.1, 120, 0.9), (0.02, 300, 0.8)])
 def test_adaptive_removal_set_matches_full(C, holes, frac):
     from paper_1612_04082_gb300.driver import adaptive_td
-    n = 12
+    n = 24
     h = 1.0 / n
     mask = np.ones((2 * n, n, n), np.uint8)
     rng = np.random.default_rng(holes)

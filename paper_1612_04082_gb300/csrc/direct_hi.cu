@@ -43,7 +43,8 @@ namespace kfmm {
 
 namespace {
 
-constexpr int kHiThreads = 128;  // targets per CTA, one per thread
+constexpr int kHiThreads = 128;  // threads per CTA
+constexpr int kHiTpt = 2;        // targets per thread
 constexpr int kHiTile = 128;     // sources per shared-memory tile (and per FP64 fold)
 
 // The frame the FP32 pairs are evaluated in: x' = R x + off, with R a fixed rotation of
@@ -189,7 +190,9 @@ __device__ __noinline__ void near_pair64(const double *x, int64_t j, const doubl
     }
 }
 
-// out[3 i + c] += this CTA's source slice, combined with the FP64 constants.
+// out[3 i + c] += this CTA's source slice, combined with the FP64 constants.  Each thread
+// holds kHiTpt targets (i, i + kHiThreads, ...), so one read of a staged source record serves
+// kHiTpt independent pairs.
 template <bool SL, bool DL>
 __global__ void __launch_bounds__(kHiThreads)
 direct_hi_kernel(const double *__restrict__ trg, int64_t ntrg, const HiRec *__restrict__ rec,
@@ -197,20 +200,34 @@ direct_hi_kernel(const double *__restrict__ trg, int64_t ntrg, const HiRec *__re
                  const double *__restrict__ dl, int64_t nsrc, int64_t chunk, HiFrame F, float near2, double cA,
                  double cB, double cC, double cE, double *__restrict__ out)
 {
+    constexpr int T = kHiTpt;
     __shared__ float4 sh[4][kHiTile];
     const int64_t s_begin = (int64_t)blockIdx.y * chunk;
     const int64_t s_end = min(nsrc, s_begin + chunk);
-    const int64_t i = (int64_t)blockIdx.x * kHiThreads + threadIdx.x;
-    const bool active = i < ntrg;
-    double x[3] = {0, 0, 0};
-    float xh[3] = {0, 0, 0}, xl[3] = {0, 0, 0};
-    if (active) {
-        double xr[3];
-        for (int c = 0; c < 3; ++c) x[c] = trg[3 * i + c];
-        rot3(F, x, xr);
-        for (int c = 0; c < 3; ++c) split_shifted(xr[c], F.off[c], xh[c], xl[c]);
+    const int64_t i0 = (int64_t)blockIdx.x * kHiThreads * T + threadIdx.x;
+    bool active[T];
+    double x[T][3];
+    float xh[T][3], xl[T][3];
+    bool any = false;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t i = i0 + (int64_t)t * kHiThreads;
+        active[t] = i < ntrg;
+        any = any || active[t];
+        for (int c = 0; c < 3; ++c) {
+            x[t][c] = active[t] ? trg[3 * i + c] : 0.0;
+            xh[t][c] = xl[t][c] = 0.f;
+        }
+        if (active[t]) {
+            double xr[3];
+            rot3(F, x[t], xr);
+            for (int c = 0; c < 3; ++c) split_shifted(xr[c], F.off[c], xh[t][c], xl[t][c]);
+        }
     }
-    double A[3] = {0, 0, 0}, B[3] = {0, 0, 0}, C[3] = {0, 0, 0}, E[3] = {0, 0, 0};
+    double A[T][3], B[T][3], C[T][3], E[T][3];
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+        for (int c = 0; c < 3; ++c) A[t][c] = B[t][c] = C[t][c] = E[t][c] = 0.0;
     for (int64_t base = s_begin; base < s_end; base += kHiTile) {
         const int cnt = (int)min((int64_t)kHiTile, s_end - base);
         __syncthreads();
@@ -222,56 +239,67 @@ direct_hi_kernel(const double *__restrict__ trg, int64_t ntrg, const HiRec *__re
             sh[3][k] = r.e;
         }
         __syncthreads();
-        if (!active) continue;
-        float a[3] = {0.f, 0.f, 0.f}, b[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f}, e[3] = {0.f, 0.f, 0.f};
+        if (!any) continue;
+        float a[T][3], b[T][3], c[T][3], e[T][3];
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+            for (int q = 0; q < 3; ++q) a[t][q] = b[t][q] = c[t][q] = e[t][q] = 0.f;
         for (int s = 0; s < cnt; ++s) {
-            const float4 ra = sh[0][s], rb = sh[1][s];
-            const float dx = (xh[0] - ra.x) + (xl[0] - rb.x);
-            const float dy = (xh[1] - ra.y) + (xl[1] - rb.y);
-            const float dz = (xh[2] - ra.z) + (xl[2] - rb.z);
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const bool nearp = r2 < near2;
-            const float ir = nearp ? 0.f : rsqrt_nr(r2);  // near pairs go to the FP64 path below
-            const float ir2 = ir * ir, ir3 = ir2 * ir;
-            if (SL) {
-                const float4 rc = sh[2][s];
-                const float tx = rb.w, ty = rc.x, tz = rc.y;
-                const float bt = (dx * tx + dy * ty + dz * tz) * ir3;
-                a[0] += ir * tx;
-                a[1] += ir * ty;
-                a[2] += ir * tz;
-                b[0] += bt * dx;
-                b[1] += bt * dy;
-                b[2] += bt * dz;
+            const float4 ra = sh[0][s], rb = sh[1][s], rc = sh[2][s], re = sh[3][s];
+            const float tx = rb.w, ty = rc.x, tz = rc.y;
+            const float ux = rc.z, uy = rc.w, uz = re.x, nx = re.y, ny = re.z, nz = re.w;
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const float dx = (xh[t][0] - ra.x) + (xl[t][0] - rb.x);
+                const float dy = (xh[t][1] - ra.y) + (xl[t][1] - rb.y);
+                const float dz = (xh[t][2] - ra.z) + (xl[t][2] - rb.z);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const bool nearp = r2 < near2;
+                const float ir = nearp ? 0.f : rsqrt_nr(r2);  // near pairs go to the FP64 path below
+                const float ir2 = ir * ir, ir3 = ir2 * ir;
+                if (SL) {
+                    const float bt = (dx * tx + dy * ty + dz * tz) * ir3;
+                    a[t][0] += ir * tx;
+                    a[t][1] += ir * ty;
+                    a[t][2] += ir * tz;
+                    b[t][0] += bt * dx;
+                    b[t][1] += bt * dy;
+                    b[t][2] += bt * dz;
+                }
+                if (DL) {
+                    const float dn = dx * nx + dy * ny + dz * nz;
+                    const float du = dx * ux + dy * uy + dz * uz;
+                    const float c1 = dn * ir3, c2 = du * ir3, c3 = ra.w * ir3;
+                    const float ee = dn * du * ir3 * ir2;
+                    c[t][0] += c1 * ux + c2 * nx - c3 * dx;
+                    c[t][1] += c1 * uy + c2 * ny - c3 * dy;
+                    c[t][2] += c1 * uz + c2 * nz - c3 * dz;
+                    e[t][0] += ee * dx;
+                    e[t][1] += ee * dy;
+                    e[t][2] += ee * dz;
+                }
+                if (nearp && active[t]) near_pair64<SL, DL>(x[t], base + s, src, nrm, sl, dl, F, A[t], B[t], C[t], E[t]);
             }
-            if (DL) {
-                const float4 rc = sh[2][s], re = sh[3][s];
-                const float ux = rc.z, uy = rc.w, uz = re.x, nx = re.y, ny = re.z, nz = re.w;
-                const float dn = dx * nx + dy * ny + dz * nz;
-                const float du = dx * ux + dy * uy + dz * uz;
-                const float c1 = dn * ir3, c2 = du * ir3, c3 = ra.w * ir3;
-                const float ee = dn * du * ir3 * ir2;
-                c[0] += c1 * ux + c2 * nx - c3 * dx;
-                c[1] += c1 * uy + c2 * ny - c3 * dy;
-                c[2] += c1 * uz + c2 * nz - c3 * dz;
-                e[0] += ee * dx;
-                e[1] += ee * dy;
-                e[2] += ee * dz;
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+            for (int q = 0; q < 3; ++q) {
+                A[t][q] += a[t][q];
+                B[t][q] += b[t][q];
+                C[t][q] += c[t][q];
+                E[t][q] += e[t][q];
             }
-            if (nearp) near_pair64<SL, DL>(x, base + s, src, nrm, sl, dl, F, A, B, C, E);
-        }
-        for (int k = 0; k < 3; ++k) {
-            A[k] += a[k];
-            B[k] += b[k];
-            C[k] += c[k];
-            E[k] += e[k];
-        }
     }
-    if (!active) return;
     // back from the rotated frame: out = R^T v
-    double v[3];
-    for (int c = 0; c < 3; ++c) v[c] = cA * A[c] + cB * B[c] + cC * C[c] + cE * E[c];
-    for (int k = 0; k < 3; ++k) atomicAdd(out + 3 * i + k, F.r[k] * v[0] + F.r[3 + k] * v[1] + F.r[6 + k] * v[2]);
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        if (!active[t]) continue;
+        const int64_t i = i0 + (int64_t)t * kHiThreads;
+        double v[3];
+        for (int q = 0; q < 3; ++q) v[q] = cA * A[t][q] + cB * B[t][q] + cC * C[t][q] + cE * E[t][q];
+        for (int k = 0; k < 3; ++k)
+            atomicAdd(out + 3 * i + k, F.r[k] * v[0] + F.r[3 + k] * v[1] + F.r[6 + k] * v[2]);
+    }
 }
 
 }  // namespace
@@ -324,7 +352,7 @@ kfmm_status direct_hi_sum(kfmm_ctx *ctx, const double *trg, int64_t ntrg, const 
     KF_LAUNCH();
     KF_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 3 * ntrg, ctx->stream));
     // source slices: enough CTAs for ~8 per SM, at least 8 tiles of sources per slice
-    const int64_t tb = (ntrg + kHiThreads - 1) / kHiThreads;
+    const int64_t tb = (ntrg + kHiThreads * kHiTpt - 1) / (kHiThreads * kHiTpt);
     int64_t ns = (8 * (int64_t)ctx->n_sms + tb - 1) / tb;
     ns = std::min<int64_t>(ns, (nsrc + 8 * kHiTile - 1) / (8 * kHiTile));
     ns = std::max<int64_t>(1, std::min<int64_t>(ns, 65535));

@@ -632,7 +632,9 @@ __device__ __forceinline__ void eval_batch(const SrcRec *sh, int kbeg, int cnt, 
     }
 }
 
-template <int KIND, bool SL, bool DL>
+// PART: 0 all segments, 1 the near list (P2P only), 2 the far list (L2P and M2P only); a
+// compile-time part leaves the other part's code, and its registers, out of the kernel.
+template <int KIND, bool SL, bool DL, int PART>
 __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
 {
     constexpr int NO = KIND == KFMM_DISP ? 3 : 6;
@@ -680,7 +682,7 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
     extern __shared__ float4 eq_smem[];  // per warp: n_surf positions, then n_surf densities
     float4 *eqp = eq_smem + (size_t)wid * 2 * e.n_surf, *eqf = eqp + e.n_surf;
     const int n_eq = e.n_surf;
-    for (int j = s0; e.part != 1 && j < s1 && j <= nW; ++j) {
+    for (int j = s0; PART != 1 && j < s1 && j <= nW; ++j) {
         const int src_box = j == 0 ? b : e.wi[wo0 + j - 1];
         if (j > 0) {
             const int2 r = e.bsrc[src_box];
@@ -717,7 +719,7 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
     // ---- P2P with the direct W boxes and the U-list leaves other than the leaf itself: up
     //      to 32 source ranges at a time, batches of 32 records filled across ranges
     bool has_self = false;
-    for (int j0 = max(s0, 1); e.part != 2 && j0 < s1; j0 += 32) {
+    for (int j0 = max(s0, 1); PART != 2 && j0 < s1; j0 += 32) {
         const int nr = min(32, s1 - j0);
         int beg = 0, cnt = 0;
         bool self = false;
@@ -929,9 +931,19 @@ void launch_eval(const EvalArgs &e, int n_items, int ncol, bool sl, bool dl, cud
     const dim3 grid((unsigned)((n_items + kEvalWarps - 1) / kEvalWarps), (unsigned)ncol);
     // staged equivalent sources of the L2P / M2P segments (none in the P2P-only part)
     const size_t smem = e.part == 1 ? 0 : sizeof(float4) * 2 * (size_t)e.n_surf * kEvalWarps;
-    if (sl && dl) eval_leaf_kernel<KIND, true, true><<<grid, kEvalThreads, smem, st>>>(e);
-    else if (sl) eval_leaf_kernel<KIND, true, false><<<grid, kEvalThreads, smem, st>>>(e);
-    else eval_leaf_kernel<KIND, false, true><<<grid, kEvalThreads, smem, st>>>(e);
+    if (e.part == 1) {
+        if (sl && dl) eval_leaf_kernel<KIND, true, true, 1><<<grid, kEvalThreads, smem, st>>>(e);
+        else if (sl) eval_leaf_kernel<KIND, true, false, 1><<<grid, kEvalThreads, smem, st>>>(e);
+        else eval_leaf_kernel<KIND, false, true, 1><<<grid, kEvalThreads, smem, st>>>(e);
+    } else if (e.part == 2) {
+        if (sl && dl) eval_leaf_kernel<KIND, true, true, 2><<<grid, kEvalThreads, smem, st>>>(e);
+        else if (sl) eval_leaf_kernel<KIND, true, false, 2><<<grid, kEvalThreads, smem, st>>>(e);
+        else eval_leaf_kernel<KIND, false, true, 2><<<grid, kEvalThreads, smem, st>>>(e);
+    } else {
+        if (sl && dl) eval_leaf_kernel<KIND, true, true, 0><<<grid, kEvalThreads, smem, st>>>(e);
+        else if (sl) eval_leaf_kernel<KIND, true, false, 0><<<grid, kEvalThreads, smem, st>>>(e);
+        else eval_leaf_kernel<KIND, false, true, 0><<<grid, kEvalThreads, smem, st>>>(e);
+    }
 }
 
 }  // namespace

@@ -58,11 +58,11 @@ BEM3_N = 100        # the 400,000-triangle cantilever (voxel size 0.01)
 BEM3_PATCH = 0.05   # half-side of its loaded patch (0.1 x 0.1)
 TD_GRID = (256, 128, 128)
 BEM3_TOL_HI = 2e-7  # GMRES-IR tolerance in the compensated residual (true residual <= 1e-6)
-HOMOG_N = 150       # periodic cell voxels per side: ~209k void-surface triangles
+HOMOG_N = 175       # periodic cell voxels per side: ~200k void-surface triangles
 # DRAM bytes per launch of the dominant kernel at this workload, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/); None when the
 # kernel has changed since the counters were taken
-TRAFFIC_BYTES = {"m2l": 412841728 + 153561856}
+TRAFFIC_BYTES = {"m2l": None}
 
 
 def max_over_ranks(x, world, device):
@@ -404,14 +404,14 @@ def homogenisation_leg(K, local, world, tol=1e-5):
         b.rhs(rhs)  # warm-up: set-up, tree, tuning
         u = np.zeros((nt, 18))
         torch.cuda.synchronize()
-        st = b.solve(u, None, tol=tol, restart=60, maxit=1000)
+        st = b.solve(u, None, tol=tol, restart=100, maxit=3000)
         sec = max_over_ranks(st["seconds"], world, f"cuda:{local}")
         one = 0.0
         its = []
         for c in range(6):
             b.set_bc(mask, np.ascontiguousarray(vals[:, 3 * c:3 * c + 3]))
             u1 = np.zeros((nt, 3))
-            s1 = b.solve(u1, None, tol=tol, restart=60, maxit=1000)
+            s1 = b.solve(u1, None, tol=tol, restart=100, maxit=3000)
             one += s1["seconds"]
             its.append(s1["iters"])
             if c == 0:
@@ -637,10 +637,18 @@ def main():
     p2p_ach = work["eval"][1] / (ph_ms["eval"] / 1e3) / 1e12 if ph_ms["eval"] > 0 else 0.0
 
     # ---- BEM leg: mixed-precision refinement vs plain FP64 GMRES at a 1e-6 FP64 residual
-    bem = bem_config3_leg(K, local, world, rank, check=not args.no_cpu_baseline) if not args.no_bem else None
-    bem_small = bem_small_leg(K, local, world) if not args.no_bem else None
-    homog = homogenisation_leg(K, local, world) if not args.no_bem else None
-    batch = batch_leg(K, local, world, flush) if not args.no_batch else None
+    def leg(fn, *a, **kw):
+        # a side leg that fails (e.g. a solve that does not converge) is reported in its own
+        # key; the headline line is still printed
+        try:
+            return fn(*a, **kw)
+        except Exception as exc:  # noqa: BLE001
+            return {"error": f"{type(exc).__name__}: {exc}"}
+
+    bem = leg(bem_config3_leg, K, local, world, rank, check=not args.no_cpu_baseline) if not args.no_bem else None
+    bem_small = leg(bem_small_leg, K, local, world) if not args.no_bem else None
+    homog = leg(homogenisation_leg, K, local, world) if not args.no_bem else None
+    batch = leg(batch_leg, K, local, world, flush) if not args.no_batch else None
 
     line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

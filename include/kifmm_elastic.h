@@ -86,10 +86,14 @@ typedef struct kfmm_options {
     int m2l_rank_max;   /* upper bound on the M2L rank (0 = no bound)                       */
     int m2l_tensor_cores; /* bit field of the products run on the tcgen05 tensor cores with
                            FP32 accumulation; clear bits use FP32 SIMT:
-                           1 = M2L translations, BF16 split pairs (rank <= 288);
+                           1 = M2L translations, BF16 split pairs (rank <= 288; up to
+                           rank 208 the translation pairs are the rows of the products and
+                           the whole translation stays in shared memory);
                            2 = check-to-equivalent factors, 4 = M2M and L2L,
                            8 = equivalent-density and M2L basis changes, all three with
-                           three-term BF16 splits (FP32-grade) (15)                          */
+                           three-term BF16 splits (FP32-grade);
+                           16 = with 1: M2L by row tiles of the translation at every rank
+                           (the kernel used above rank 208) (15)                              */
     int device;         /* CUDA device ordinal (0)                                          */
     int graphs;         /* 1: an evaluation repeated with the same arguments (e.g. the matvecs
                            of a GMRES solve) is captured once into a CUDA graph and replayed;
@@ -391,7 +395,10 @@ void bem_default_solve_opts(bem_solve_opts *o);
 
 /* Triangulated boundary: verts [nv][3] FP64, tris [nt][3] int32 (vertex order gives the
  * normal by the right-hand rule; it must point out of the material).  `op` is a
- * bem_operator.  opt as for kfmm_create (NULL = defaults).  Rejects zero-area triangles. */
+ * bem_operator.  opt as for kfmm_create (NULL = defaults), except that leaf_cap = 0 (and
+ * opt = NULL) lets the BEM pick its leaf caps: 256 quadrature sources per leaf up to 2^21
+ * sources and 512 above for the boundary sums, 1024 for the interior evaluations of
+ * bem_interior / bem_topo_derivative.  Rejects zero-area triangles. */
 kfmm_status bem_create(bem_ctx **out, const kfmm_options *opt, int op, const double *verts, int64_t nv,
                        const int32_t *tris, int64_t nt);
 kfmm_status bem_destroy(bem_ctx *b);

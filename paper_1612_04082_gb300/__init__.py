@@ -421,8 +421,11 @@ def _bcheck(h, status):
 
 
 def bem_create(verts, tris, op=BEM_FMM, options: kfmm_options | None = None, **overrides):
-    """verts [nv,3] float64, tris [nt,3] int32 (host or device)."""
+    """verts [nv,3] float64, tris [nt,3] int32 (host or device).  Without options or a
+    leaf_cap override the BEM picks its own leaf caps (leaf_cap = 0)."""
     o = options if options is not None else kfmm_default_options()
+    if options is None:
+        o.leaf_cap = 0
     for k, v in overrides.items():
         setattr(o, k, v)
     h = _vp()

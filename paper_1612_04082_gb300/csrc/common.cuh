@@ -112,6 +112,7 @@ struct Operators {
     // [316][ceil(r/128)][hi, lo][128 x rp] in the UMMA core-matrix layout (see tc_gemm.cuh)
     DevBuf m2l_tc;
     int m2l_tc_mtiles = 0;
+    bool m2l_pairs_rows = false;  // tensor-core M2L with the pairs as rows (tc_m2l_kernel)
     // box operators for the K-streamed tensor-core product: [n_mat][n_mtile][n_kc][2][128 x 64]
     struct TcOp {
         DevBuf img;

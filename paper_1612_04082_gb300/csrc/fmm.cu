@@ -156,7 +156,28 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
     O.kd = kd;
     // tensor-core images of the M2L translations: rows in tiles of 128, split pairs
     O.m2l_tc_mtiles = 0;
-    if ((ctx->opt.m2l_tensor_cores & 1) && tc_rank_ok(rp)) {
+    O.m2l_pairs_rows = false;
+    if ((ctx->opt.m2l_tensor_cores & 1) && !(ctx->opt.m2l_tensor_cores & 16) && tc::mt_rank_ok(rp)) {
+        // pairs as rows: each translation as one B operand image [hi | lo], row i = output index
+        const size_t half = (size_t)rp * rp;  // uint16 per half
+        std::vector<uint16_t> img((size_t)316 * 2 * half, 0);
+        for (int d = 0; d < 316; ++d) {
+            uint16_t *hi = img.data() + (size_t)d * 2 * half, *lo = hi + half;
+            for (int i = 0; i < r; ++i)
+                for (int k = 0; k < r; ++k) {
+                    const float v = (float)H->m2l_c[((size_t)d * r + i) * r + k];
+                    const uint16_t h = host_bf16(v);
+                    const uint16_t l = host_bf16(v - host_bf16_to_f32(h));
+                    const uint32_t off = tc::core_offset(i, k, rp) / 2;
+                    hi[off] = h;
+                    lo[off] = l;
+                }
+        }
+        KF_CUDA(O.m2l_tc.ensure(sizeof(uint16_t) * img.size()));
+        KF_CUDA(cudaMemcpy(O.m2l_tc.p, img.data(), sizeof(uint16_t) * img.size(), cudaMemcpyHostToDevice));
+        O.m2l_tc_mtiles = 1;
+        O.m2l_pairs_rows = true;
+    } else if ((ctx->opt.m2l_tensor_cores & 1) && tc_rank_ok(rp)) {
         const int nmt = (r + tc::BM - 1) / tc::BM;
         const size_t half = tc::half_bytes(tc::BM, rp) / 2;  // uint16 per half
         std::vector<uint16_t> img((size_t)316 * nmt * 2 * half, 0);
@@ -204,7 +225,10 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
     // dynamic shared memory of the tensor-core kernels (set here, outside any graph capture)
     KF_CUDA(cudaFuncSetAttribute(tc::tc_box_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tc::box_smem_bytes()));
-    if (O.m2l_tc_mtiles > 0)
+    if (O.m2l_pairs_rows)
+        KF_CUDA(cudaFuncSetAttribute(tc::tc_m2l_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc::mt_smem_bytes(rp)));
+    else if (O.m2l_tc_mtiles > 0)
         KF_CUDA(cudaFuncSetAttribute(tc::tc_gather_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)tc::smem_bytes(rp)));
     O.p = prm.p;
@@ -1466,37 +1490,44 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     if (O.m2l_tc_mtiles > 0) {
         if (P.n_m2l_items) {
             const int64_t nchunk = (int64_t)nb * ncol * (rp / 8);
-            tc::split_pairs_kernel<<<(unsigned)((nchunk + 255) / 256), 256, 0, st>>>(W.psi.as<float>(), (int64_t)nb * ncol,
-                                                                                     rp, W.psi2.as<uint16_t>());
+            tc::split_pairs_kernel<<<(unsigned)((nchunk + 255) / 256), 256, 0, st>>>(
+                W.psi.as<float>(), (int64_t)nb * ncol, rp, W.psi2.as<uint16_t>(), O.m2l_pairs_rows ? 1 : 0);
             KF_LAUNCH();
             ctx->phase(KFMM_PH_M2L);
-            const uint32_t smem = tc::smem_bytes(rp);
+            const bool rows = O.m2l_pairs_rows;
+            const uint32_t smem = rows ? tc::mt_smem_bytes(rp) : tc::smem_bytes(rp);
             tc::TcArgs ta{O.m2l_tc.as<uint16_t>(), 316, nb, O.m2l_tc_mtiles, r, rp, P.m2l_items.as<int4>(),
                           T.vp_src.as<int>(), T.vp_trg.as<int>(), W.psi2.as<uint16_t>(), W.cdn.as<float>(), rp,
                           P.err.as<int>()};
+            tc::TcM2lArgs tm{O.m2l_tc.as<uint16_t>(), 316, nb, rp, P.m2l_items.as<int4>(), T.vp_src.as<int>(),
+                             T.vp_trg.as<int>(), W.psi2.as<uint16_t>(), W.cdn.as<float>(), P.err.as<int>()};
+            auto launch = [&]() {
+                if (rows) tc::tc_m2l_kernel<<<P.n_m2l_items, tc::MT_THREADS, smem, st>>>(tm);
+                else tc::tc_gather_gemm_kernel<<<P.n_m2l_items, tc::M2L_THREADS, smem, st>>>(ta);
+            };
             if (ctx->opt.autotune && !ctx->tune.m2l_done) {
-                // columns per work item: time each candidate on this tree, keep the fastest
+                // columns (pairs) per work item: time each candidate on this tree, keep the fastest
                 float best = 1e30f;
                 int best_chunk = ctx->tune.m2l_chunk;
-                for (int chunk : {256, 512, 1024, 2048}) {
+                const int rows_chunks[4] = {512, 1024, 2048, 4096}, tile_chunks[4] = {256, 512, 1024, 2048};
+                for (int ci = 0; ci < 4; ++ci) {
+                    const int chunk = rows ? rows_chunks[ci] : tile_chunks[ci];
                     make_m2l_host(ctx, P, chunk);
                     KF_TRY(upload_m2l_items());
-                    ta.items = P.m2l_items.as<int4>();
+                    ta.items = tm.items = P.m2l_items.as<int4>();
                     KF_CUDA(cudaMemsetAsync(W.cdn.p, 0, sizeof(float) * (size_t)nb * rp * ncol, st));
                     float ms = 0.f;
-                    KF_TRY(time_launch(ctx, [&]() {
-                        tc::tc_gather_gemm_kernel<<<P.n_m2l_items, tc::M2L_THREADS, smem, st>>>(ta);
-                    }, &ms));
+                    KF_TRY(time_launch(ctx, launch, &ms));
                     if (ms < best) best = ms, best_chunk = chunk;
                 }
                 ctx->tune.m2l_chunk = best_chunk;
                 ctx->tune.m2l_done = true;
                 make_m2l_host(ctx, P, best_chunk);
                 KF_TRY(upload_m2l_items());
-                ta.items = P.m2l_items.as<int4>();
+                ta.items = tm.items = P.m2l_items.as<int4>();
                 KF_CUDA(cudaMemsetAsync(W.cdn.p, 0, sizeof(float) * (size_t)nb * rp * ncol, st));
             }
-            tc::tc_gather_gemm_kernel<<<P.n_m2l_items, tc::M2L_THREADS, smem, st>>>(ta);
+            launch();
             KF_LAUNCH();
         }
     } else {

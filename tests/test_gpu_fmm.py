@@ -252,13 +252,14 @@ def test_fmm_errors(K):
 def test_tensor_cores_match_fp32_simt(K):
     """The products on the tcgen05 tensor cores (BF16 split pairs, FP32 accumulation) agree
     with the FP32 SIMT products on the same tree: M2L alone (bit 0), M2L and the box
-    operators (bits 0 and 1), and neither all meet the FMM tolerance against the oracle and
-    differ from each other by the split-pair rounding (~1e-5)."""
+    operators (bits 0 and 1), neither, and M2L by row tiles of the translation (bits 0 and 4)
+    all meet the FMM tolerance against the oracle and differ from each other by the
+    split-pair rounding (~1e-5)."""
     src, nrm = W.box_with_voids_points(40000, n_voids=10)
     sl, dl = W.densities(len(src))
     src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
     outs = []
-    for tcores in (3, 1, 0):
+    for tcores in (3, 1, 0, 17):
         with make_ctx(K, G1, NU1, m2l_tensor_cores=tcores) as c:
             c.build(dev(src), dev(nrm), dev(src))
             out = torch.zeros(len(src), 3, device="cuda:0")
@@ -271,6 +272,10 @@ def test_tensor_cores_match_fp32_simt(K):
         assert rel(o[idx], ref) < 1e-4
     assert rel(outs[1], outs[2]) < 2e-5
     assert rel(outs[0], outs[2]) < 4e-5
+    # M2L with the pairs as rows (1) and by row tiles of the translation (17): the same split
+    # products summed in another order
+    assert rel(outs[3], outs[2]) < 2e-5
+    assert rel(outs[1], outs[3]) < 1e-5
 
 
 def test_graph_replay_matches_and_invalidates(K):

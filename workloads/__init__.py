@@ -171,10 +171,11 @@ def cantilever(n: int, patch_half: float = 0.25):
 
 
 def periodic_cell_voids(n: int = 128, n_voids: int | None = None, seed: int = SEED_GEOMETRY):
-    """Unit periodic cell with a random union of 8-16 ellipsoidal voids (semi-axes
-    U(0.05, 0.2), random rotations, kept inside the cell), voxelised on an n^3 grid.  Returns
-    the boundary of the void voxels as triangles (4 per exposed face) with normals pointing
-    out of the material, i.e. into the voids: verts [nv, 3], tris [nt, 3] int32."""
+    """Unit periodic cell with 8-16 separate ellipsoidal voids (semi-axes U(0.04, 0.16),
+    random rotations, inside the cell; bounding spheres at least 4 voxels apart, so every void
+    surface is a closed manifold of its own), voxelised on an n^3 grid.  Returns the boundary
+    of the void voxels as triangles (4 per exposed face) with normals pointing out of the
+    material, i.e. into the voids: verts [nv, 3], tris [nt, 3] int32."""
     rng = np.random.default_rng(seed + 4)
     k = int(rng.integers(8, 17)) if n_voids is None else n_voids
     h = 1.0 / n
@@ -182,16 +183,24 @@ def periodic_cell_voids(n: int = 128, n_voids: int | None = None, seed: int = SE
     X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
     P = np.stack([X, Y, Z], axis=-1).reshape(-1, 3)
     void = np.zeros(len(P), bool)
-    for _ in range(k):
-        ax = rng.uniform(0.05, 0.2, 3)
+    placed = []  # (centre, bounding radius)
+    tries = 0
+    while len(placed) < k:
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("could not place the voids")
+        ax = rng.uniform(0.04, 0.16, 3)
         q = rng.normal(size=4)
         q /= np.linalg.norm(q)
+        m = ax.max() + 2 * h
+        ctr = rng.uniform(m, 1 - m, 3)  # the void stays inside the cell
+        if any(np.linalg.norm(ctr - c2) < m + m2 + 4 * h for c2, m2 in placed):
+            continue
+        placed.append((ctr, m))
         w, x, y, z = q
         R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
                       [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
                       [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
-        m = ax.max() + 2 * h
-        ctr = rng.uniform(m, 1 - m, 3)  # the void stays inside the cell
         L = (P - ctr) @ R / ax
         void |= np.einsum("ij,ij->i", L, L) <= 1.0
     mask = void.reshape(n, n, n)

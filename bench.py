@@ -319,12 +319,12 @@ def bem_config3_leg(K, local, world, rank, check=True):
         rhs = np.zeros((nt, 3))
         b.rhs(rhs)  # warm-up: quadrature set-up, FMM tree of the 6.4M sources, tuning
         torch.cuda.synchronize(dev)
-        st = b.solve(u, t, tol=BEM3_TOL_HI, restart=100, maxit=8000, refine=1, inner_tol=1e-3)
+        st = b.solve(u, t, tol=BEM3_TOL_HI, restart=200, maxit=8000, refine=1, inner_tol=1e-3)
         sec = max_over_ranks(st["seconds"], world, dev)
         out.update({"solves_per_s": aggregate_rate(1, world, sec), "ms_per_solve": 1e3 * sec,
                     "inner_iters": st["iters"], "outer": st["outer"], "fmm_matvecs": st["matvecs"],
                     "hi_matvecs": st["matvecs_hi"], "relres": st["relres"], "converged": bool(st["converged"]),
-                    "method": "GMRES-IR: FP32 FMM corrections (p=6, restart 100, inner tol 1e-3), compensated "
+                    "method": "GMRES-IR: FP32 FMM corrections (p=6, restart 200, inner tol 1e-3), compensated "
                               "FP64-grade direct residuals"})
         b.topo_derivative(pts, td, en, sig)  # warm-up: the interior tree of sources and grid points
         torch.cuda.synchronize(dev)

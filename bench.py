@@ -62,7 +62,11 @@ HOMOG_N = 175       # periodic cell voxels per side: ~200k void-surface triangle
 # DRAM bytes per launch of the dominant kernel at this workload, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/); None when the
 # kernel has changed since the counters were taken
-TRAFFIC_BYTES = {"m2l": None}
+TRAFFIC_BYTES = {"m2l": 350924032 + 114690304,            # the one tc_m2l_kernel launch
+                 "down": 385244160 + 118978816}           # the phase's ten tc_box_gemm_kernel launches
+TRAFFIC_NOTE = {"m2l": "DRAM bytes of the phase's tc_m2l_kernel launch (ncu, one pass, profiles/)",
+                "down": "DRAM bytes of the phase's ten tc_box_gemm_kernel launches, summed like the flops "
+                        "(ncu, one pass, profiles/)"}
 
 
 def max_over_ranks(x, world, device):
@@ -622,7 +626,7 @@ def main():
         t = ph_ms[k] / 1e3
         ach = ops / t / 1e12 if t > 0 else 0.0
         return {"bound": bound, "kernel_phase": k, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": TRAFFIC_BYTES.get(k),
+                "frac": ach / peak, "traffic": TRAFFIC_BYTES.get(k), "traffic_note": TRAFFIC_NOTE.get(k),
                 "peak_note": (f"FP32 FMA peak measured by kfmm_measure_fp32_peak on this GPU ({fp32_meas['n_sms']} SMs, "
                               f"FMA chains, fastest of 5 launches)" if bound == "alu"
                               else f"BF16 dense tensor peak, sustained, of {peak_src} (MEASURED_PEAKS.json)"),

@@ -525,10 +525,11 @@ __global__ void __launch_bounds__(256) gemm_gather_kernel(GemmArgs g)
 // W-list boxes (M2P through the upward density, or directly from the sources of a box with
 // at most w_direct_max of them), then the U-list leaves (P2P).  Heavy leaves (long W and U
 // lists) are cut into several items of bounded cost whose results are added atomically into
-// the zeroed output, so no warp runs far longer than the others.  A chunk
-// of more than 32 targets gives each lane two targets (lane, lane + 32); a chunk of nt <= 32
-// targets splits the 32 lanes into nsl = 32 / nt source slices, lane = slice * nt + target,
-// and the slices are summed by shuffles at the end, so small leaves keep their lanes busy.
+// the zeroed output, so no warp runs far longer than the others.  A chunk of nt targets
+// gives each lane T = 1, 2 or 4 of them (ti, ti + L, ...; L = ceil(nt / T)) and splits the 32
+// lanes into nsl = 32 / L source slices, lane = slice * L + ti; the slices are summed by
+// shuffles at the end (eval_layout picks T), so small and ragged leaves keep their lanes
+// busy and large ones read each staged source once per four pairs.
 // Sources are staged per warp in batches of 32 records through shared memory, the next
 // batch prefetched into registers while the current one is evaluated.  Coincident points
 // share a Morton key and so a leaf: only the leaf's own sources take the r = 0 test.
@@ -618,41 +619,90 @@ __device__ __forceinline__ void store_rec(SrcRec *sh, const SrcRec &r)
     }
 }
 
-// Lane layout of a chunk of nt <= 64 targets: one target per lane (L = nt lanes per source
-// slice, needs nt <= 32) or two (targets t and t + L, L = ceil(nt / 2)); nsl = 32 / L slices.
-// Two per lane is taken when it fills at least as many lane slots (it also halves the
-// shared-memory loads per pair and doubles the independent work per lane).
-__host__ __device__ inline bool eval_layout(int nt, int &L, int &nsl)
+// Lane layout of a chunk of nt <= 64 targets: T targets per lane (1, 2 or 4), L = ceil(nt / T)
+// lanes per source slice, nsl = 32 / L slices taking every nsl-th source.  A warp step then
+// evaluates nt * nsl useful pairs at the cost of T pair evaluations per lane: the layout with
+// the most pairs per step wins, on a tie the larger T (fewer shared-memory loads per pair,
+// more independent work per lane).  Returns T.
+__host__ __device__ inline int eval_layout(int nt, int &L, int &nsl)
 {
-    const int n1 = nt <= 32 ? 32 / nt : 0;
-    const int L2 = (nt + 1) / 2, n2 = 32 / L2;
-    const bool two = n2 >= 2 * n1;
-    L = two ? L2 : nt;
-    nsl = two ? n2 : n1;
-    return two;
+    int best_t = 0;
+    float best = -1.f;
+    for (int t = 1; t <= 4; t *= 2) {
+        const int l = (nt + t - 1) / t;
+        if (l > 32) continue;
+        const float score = (float)(32 / l) / (float)t;
+        if (score >= best) {
+            best = score;
+            best_t = t;
+            L = l;
+            nsl = 32 / l;
+        }
+    }
+    return best_t;
 }
 
-// staged records k = kbeg, kbeg + nsl, ... < cnt against this lane's target(s), two
-// independent pairs per step
-template <int KIND, bool SL, bool DL, bool CHK, int NO>
-__device__ __forceinline__ void eval_batch(const SrcRec *sh, int kbeg, int cnt, int nsl, bool two, float x0, float y0,
-                                           float z0, float x1, float y1, float z1, const EvalArgs &e, float (&o0)[NO],
-                                           float (&o1)[NO])
+// staged records k = kbeg, kbeg + nsl, ... < cnt against this lane's NT targets; with one or
+// two targets two sources per step (independent pairs), with four one
+template <int KIND, bool SL, bool DL, bool CHK, int NO, int NT>
+__device__ __forceinline__ void eval_batch(const SrcRec *sh, int kbeg, int cnt, int nsl, const float (&x)[4],
+                                           const float (&y)[4], const float (&z)[4], const EvalArgs &e,
+                                           float (&o)[4][NO])
 {
     int k = kbeg;
+    if (NT == 4) {
+        for (; k < cnt; k += nsl) {
+            const SrcRec q = sh[k];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) p2p_pair<KIND, SL, DL, CHK>(x[t], y[t], z[t], q, e.a34, e.b12, e.c3, e.nu, o[t]);
+        }
+        return;
+    }
     for (; k + nsl < cnt; k += 2 * nsl) {
         const SrcRec qa = sh[k], qb = sh[k + nsl];
-        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, qa, e.a34, e.b12, e.c3, e.nu, o0);
-        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, qb, e.a34, e.b12, e.c3, e.nu, o0);
-        if (two) {
-            p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, qa, e.a34, e.b12, e.c3, e.nu, o1);
-            p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, qb, e.a34, e.b12, e.c3, e.nu, o1);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            p2p_pair<KIND, SL, DL, CHK>(x[t], y[t], z[t], qa, e.a34, e.b12, e.c3, e.nu, o[t]);
+            p2p_pair<KIND, SL, DL, CHK>(x[t], y[t], z[t], qb, e.a34, e.b12, e.c3, e.nu, o[t]);
         }
     }
     if (k < cnt) {
         const SrcRec q = sh[k];
-        p2p_pair<KIND, SL, DL, CHK>(x0, y0, z0, q, e.a34, e.b12, e.c3, e.nu, o0);
-        if (two) p2p_pair<KIND, SL, DL, CHK>(x1, y1, z1, q, e.a34, e.b12, e.c3, e.nu, o1);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) p2p_pair<KIND, SL, DL, CHK>(x[t], y[t], z[t], q, e.a34, e.b12, e.c3, e.nu, o[t]);
+    }
+}
+
+// the same for the layout's T (warp-uniform)
+template <int KIND, bool SL, bool DL, bool CHK, int NO>
+__device__ __forceinline__ void eval_batch_t(int T, const SrcRec *sh, int kbeg, int cnt, int nsl, const float (&x)[4],
+                                             const float (&y)[4], const float (&z)[4], const EvalArgs &e,
+                                             float (&o)[4][NO])
+{
+    if (T == 4) eval_batch<KIND, SL, DL, CHK, NO, 4>(sh, kbeg, cnt, nsl, x, y, z, e, o);
+    else if (T == 2) eval_batch<KIND, SL, DL, CHK, NO, 2>(sh, kbeg, cnt, nsl, x, y, z, e, o);
+    else eval_batch<KIND, SL, DL, CHK, NO, 1>(sh, kbeg, cnt, nsl, x, y, z, e, o);
+}
+
+// staged equivalent sources k = kbeg, kbeg + nsl, ... < n against this lane's NT targets
+template <int KIND, int NO, int NT>
+__device__ __forceinline__ void equiv_batch(const float4 *eqp, const float4 *eqf, int kbeg, int n, int nsl,
+                                            const float (&x)[4], const float (&y)[4], const float (&z)[4],
+                                            const EvalArgs &e, float (&o)[4][NO])
+{
+    int k = kbeg;
+    for (; k + nsl < n; k += 2 * nsl) {  // two independent pairs per target and step
+        const float4 pa = eqp[k], fa = eqf[k], pb = eqp[k + nsl], fb = eqf[k + nsl];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            equiv_pair<KIND>(x[t], y[t], z[t], pa, fa, e.a34, e.b12, o[t]);
+            equiv_pair<KIND>(x[t], y[t], z[t], pb, fb, e.a34, e.b12, o[t]);
+        }
+    }
+    if (k < n) {
+        const float4 pp = eqp[k], f = eqf[k];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) equiv_pair<KIND>(x[t], y[t], z[t], pp, f, e.a34, e.b12, o[t]);
     }
 }
 
@@ -678,26 +728,26 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
 
     const int nt = min(64, tr.y - c0);
     int L, nsl;
-    const bool two = eval_layout(nt, L, nsl);
+    const int T = eval_layout(nt, L, nsl);             // targets per lane (warp-uniform)
     const int ti = lane % L, si = lane / L;            // first target, source slice
-    const int t1 = ti + L;                             // second target (two per lane)
-    const bool act = si < nsl, act1 = act && two && t1 < nt;
-    float x0 = 0.f, y0 = 0.f, z0 = 0.f, x1 = 0.f, y1 = 0.f, z1 = 0.f;
-    if (act) {
-        const float4 p = e.trg[c0 + ti];
-        x0 = p.x;
-        y0 = p.y;
-        z0 = p.z;
-    }
-    if (act1) {
-        const float4 p = e.trg[c0 + t1];
-        x1 = p.x;
-        y1 = p.y;
-        z1 = p.z;
-    }
-    float o0[NO], o1[NO];
+    const bool act = si < nsl;
+    float x[4], y[4], z[4];
+    bool tact[4];
 #pragma unroll
-    for (int a = 0; a < NO; ++a) o0[a] = o1[a] = 0.f;
+    for (int t = 0; t < 4; ++t) {
+        tact[t] = act && t < T && ti + t * L < nt;  // targets ti, ti + L, ...
+        x[t] = y[t] = z[t] = 0.f;
+        if (tact[t]) {
+            const float4 p = e.trg[c0 + ti + t * L];
+            x[t] = p.x;
+            y[t] = p.y;
+            z[t] = p.z;
+        }
+    }
+    float o[4][NO];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        for (int a = 0; a < NO; ++a) o[t][a] = 0.f;
     const int kbeg = act ? si : 32;  // inactive lanes skip every evaluation loop
 
     // ---- L2P (segment 0) and M2P (W boxes above the direct threshold): the equivalent
@@ -723,21 +773,10 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
             eqf[k] = make_float4(e.phi_scale * f0, e.phi_scale * f1, e.phi_scale * f2, 0.f);
         }
         __syncwarp();
-        int k = act ? si : n_eq;
-        for (; k + nsl < n_eq; k += 2 * nsl) {  // two independent pairs per step
-            const float4 pa = eqp[k], fa = eqf[k], pb = eqp[k + nsl], fb = eqf[k + nsl];
-            equiv_pair<KIND>(x0, y0, z0, pa, fa, e.a34, e.b12, o0);
-            equiv_pair<KIND>(x0, y0, z0, pb, fb, e.a34, e.b12, o0);
-            if (two) {
-                equiv_pair<KIND>(x1, y1, z1, pa, fa, e.a34, e.b12, o1);
-                equiv_pair<KIND>(x1, y1, z1, pb, fb, e.a34, e.b12, o1);
-            }
-        }
-        if (k < n_eq) {
-            const float4 pp = eqp[k], f = eqf[k];
-            equiv_pair<KIND>(x0, y0, z0, pp, f, e.a34, e.b12, o0);
-            if (two) equiv_pair<KIND>(x1, y1, z1, pp, f, e.a34, e.b12, o1);
-        }
+        const int kb = act ? si : n_eq;
+        if (T == 4) equiv_batch<KIND, NO, 4>(eqp, eqf, kb, n_eq, nsl, x, y, z, e, o);
+        else if (T == 2) equiv_batch<KIND, NO, 2>(eqp, eqf, kb, n_eq, nsl, x, y, z, e, o);
+        else equiv_batch<KIND, NO, 1>(eqp, eqf, kb, n_eq, nsl, x, y, z, e, o);
     }
 
     // ---- P2P with the direct W boxes and the U-list leaves other than the leaf itself: up
@@ -799,7 +838,7 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
                 const int src = locate(base + 32 + lane);
                 if (base + 32 + lane < total) nxt = load_rec<SL, DL>(rec, src);
             }
-            eval_batch<KIND, SL, DL, false>(sh, kbeg, cnt2, nsl, two, x0, y0, z0, x1, y1, z1, e, o0, o1);
+            eval_batch_t<KIND, SL, DL, false, NO>(T, sh, kbeg, cnt2, nsl, x, y, z, e, o);
         }
     }
 
@@ -814,39 +853,36 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
             if (lane < cnt) store_rec<SL, DL>(sh + lane, nxt);
             __syncwarp();
             if (base + 32 + lane < r.y) nxt = load_rec<SL, DL>(rec, base + 32 + lane);
-            eval_batch<KIND, SL, DL, true>(sh, kbeg, cnt, nsl, two, x0, y0, z0, x1, y1, z1, e, o0, o1);
+            eval_batch_t<KIND, SL, DL, true, NO>(T, sh, kbeg, cnt, nsl, x, y, z, e, o);
         }
     }
 
     // ---- sum the source slices into slice 0 (shuffling the unmodified partial sums) and add
     //      into the zeroed output in input order
-    float tot[NO], tot1[NO];
+    float tot[4][NO];
 #pragma unroll
-    for (int a = 0; a < NO; ++a) {
-        tot[a] = o0[a];
-        tot1[a] = o1[a];
-    }
+    for (int t = 0; t < 4; ++t)
+        for (int a = 0; a < NO; ++a) tot[t][a] = o[t][a];
     for (int s = 1; s < nsl; ++s) {
         const int src = lane + s * L;
         const int sl = src < 32 ? src : 31;
 #pragma unroll
-        for (int a = 0; a < NO; ++a) {
-            const float v = __shfl_sync(kFull, o0[a], sl);
-            const float v1 = __shfl_sync(kFull, o1[a], sl);
-            if (src < 32) {
-                tot[a] += v;
-                tot1[a] += v1;
+        for (int t = 0; t < 4; ++t) {
+            if (t >= T) break;  // warp-uniform
+#pragma unroll
+            for (int a = 0; a < NO; ++a) {
+                const float v = __shfl_sync(kFull, o[t][a], sl);
+                if (src < 32) tot[t][a] += v;
             }
         }
     }
     if (si == 0) {
-        float *o = e.out + (int64_t)e.trg_perm[c0 + ti] * e.ldo + NO * dcol;
 #pragma unroll
-        for (int a = 0; a < NO; ++a) atomicAdd(o + a, e.out_scale * tot[a]);
-        if (act1) {
-            float *q = e.out + (int64_t)e.trg_perm[c0 + t1] * e.ldo + NO * dcol;
+        for (int t = 0; t < 4; ++t) {
+            if (!tact[t]) continue;
+            float *q = e.out + (int64_t)e.trg_perm[c0 + ti + t * L] * e.ldo + NO * dcol;
 #pragma unroll
-            for (int a = 0; a < NO; ++a) atomicAdd(q + a, e.out_scale * tot1[a]);
+            for (int a = 0; a < NO; ++a) atomicAdd(q + a, e.out_scale * tot[t][a]);
         }
     }
 }
@@ -891,8 +927,8 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
         for (int c0 = tr.x; c0 < tr.y; c0 += 64) {
             const int nt = min(64, tr.y - c0);
             int L, nsl;
-            const bool two = eval_layout(nt, L, nsl);
-            const float w = (two ? 2.f : 1.f) / (float)nsl;  // pair evaluations per lane and source
+            const int T = eval_layout(nt, L, nsl);
+            const float w = (float)T / (float)nsl;  // pair evaluations per lane and source
             float base = 0.f;
             int q_last = -1;
             int pend_idx = -1, pend_sg = 0;  // last item started so far: its end is not known yet

@@ -650,26 +650,27 @@ __device__ __forceinline__ void eval_batch(const SrcRec *sh, int kbeg, int cnt, 
                                            float (&o)[4][NO])
 {
     int k = kbeg;
-    if (NT == 4) {
+    if constexpr (NT == 4) {
         for (; k < cnt; k += nsl) {
             const SrcRec q = sh[k];
 #pragma unroll
             for (int t = 0; t < 4; ++t) p2p_pair<KIND, SL, DL, CHK>(x[t], y[t], z[t], q, e.a34, e.b12, e.c3, e.nu, o[t]);
         }
-        return;
-    }
-    for (; k + nsl < cnt; k += 2 * nsl) {
-        const SrcRec qa = sh[k], qb = sh[k + nsl];
+    } else {
+        for (; k + nsl < cnt; k += 2 * nsl) {
+            const SrcRec qa = sh[k], qb = sh[k + nsl];
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            p2p_pair<KIND, SL, DL, CHK>(x[t], y[t], z[t], qa, e.a34, e.b12, e.c3, e.nu, o[t]);
-            p2p_pair<KIND, SL, DL, CHK>(x[t], y[t], z[t], qb, e.a34, e.b12, e.c3, e.nu, o[t]);
+            for (int t = 0; t < NT; ++t) {
+                p2p_pair<KIND, SL, DL, CHK>(x[t], y[t], z[t], qa, e.a34, e.b12, e.c3, e.nu, o[t]);
+                p2p_pair<KIND, SL, DL, CHK>(x[t], y[t], z[t], qb, e.a34, e.b12, e.c3, e.nu, o[t]);
+            }
         }
-    }
-    if (k < cnt) {
-        const SrcRec q = sh[k];
+        if (k < cnt) {
+            const SrcRec q = sh[k];
 #pragma unroll
-        for (int t = 0; t < NT; ++t) p2p_pair<KIND, SL, DL, CHK>(x[t], y[t], z[t], q, e.a34, e.b12, e.c3, e.nu, o[t]);
+            for (int t = 0; t < NT; ++t)
+                p2p_pair<KIND, SL, DL, CHK>(x[t], y[t], z[t], q, e.a34, e.b12, e.c3, e.nu, o[t]);
+        }
     }
 }
 

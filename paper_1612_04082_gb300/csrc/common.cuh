@@ -124,7 +124,7 @@ struct Operators {
 };
 
 // points on the surface of a p x p x p lattice (equivalent and check surfaces)
-inline int surface_points(int p) { return 6 * (p - 1) * (p - 1) + 2; }
+constexpr int surface_points(int p) { return 6 * (p - 1) * (p - 1) + 2; }
 
 // Octree and interaction lists (device arrays unless noted).
 struct Tree {

@@ -307,7 +307,8 @@ __global__ void box_geom_kernel(int nb, const int4 *__restrict__ anchor, const u
 // check-surface potentials from sources (S2M on leaves, P2L on X lists)
 // One CTA per box, one thread per check point; sources staged through shared memory.
 // ------------------------------------------------------------------------------------
-constexpr int kChkThreads = 160;  // >= 152 check points at p = 6
+constexpr int kChkThreads = 80;  // 2 check points per thread up to p = 6 (152), 4 up to p = 8 (296)
+static_assert(surface_points(8) <= 4 * kChkThreads, "check points of the largest order per CTA");
 constexpr int kChkStage = 256;
 
 template <bool SL, bool DL>
@@ -324,7 +325,9 @@ __device__ __forceinline__ void chk_pair(float x, float y, float z, const SrcRec
         acc_dl_s<float>(dx, dy, dz, q.u.x, q.u.y, q.u.z, q.n.x, q.n.y, q.n.z, q.y.w, c3, ox, oy, oz);
 }
 
-template <bool SL, bool DL>
+// NPT check points per thread: tid, tid + kChkThreads, ... (n_surf <= NPT kChkThreads); each
+// staged source record serves NPT independent pairs
+template <bool SL, bool DL, int NPT>
 __global__ void __launch_bounds__(kChkThreads)
 check_potential_kernel(const int *__restrict__ boxes, int nbox, int use_xlist, const int *__restrict__ xo,
                        const int *__restrict__ xi, const int2 *__restrict__ bsrc, const float4 *__restrict__ geom,
@@ -337,22 +340,21 @@ check_potential_kernel(const int *__restrict__ boxes, int nbox, int use_xlist, c
     const int b = boxes ? boxes[blockIdx.x] : blockIdx.x;
     const float4 g = geom[b];
     const int tid = threadIdx.x;
-    // each thread owns check points tid and tid + kChkThreads (n_surf <= 2 kChkThreads)
-    const bool has0 = tid < n_surf, has1 = tid + kChkThreads < n_surf;
-    float x = 0.f, y = 0.f, z = 0.f, x1 = 0.f, y1 = 0.f, z1 = 0.f;
-    if (has0) {
-        const float4 s = surf[tid];
-        x = g.x + radius * g.w * s.x;
-        y = g.y + radius * g.w * s.y;
-        z = g.z + radius * g.w * s.z;
+    float x[NPT], y[NPT], z[NPT], o[NPT][3];
+    bool has[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int c = tid + j * kChkThreads;
+        has[j] = c < n_surf;
+        x[j] = y[j] = z[j] = 0.f;
+        o[j][0] = o[j][1] = o[j][2] = 0.f;
+        if (has[j]) {
+            const float4 sp = surf[c];
+            x[j] = g.x + radius * g.w * sp.x;
+            y[j] = g.y + radius * g.w * sp.y;
+            z[j] = g.z + radius * g.w * sp.z;
+        }
     }
-    if (has1) {
-        const float4 s = surf[tid + kChkThreads];
-        x1 = g.x + radius * g.w * s.x;
-        y1 = g.y + radius * g.w * s.y;
-        z1 = g.z + radius * g.w * s.z;
-    }
-    float ox = 0.f, oy = 0.f, oz = 0.f, px = 0.f, py = 0.f, pz = 0.f;
     const int nlist = use_xlist ? xo[b + 1] - xo[b] : 1;
     for (int li = 0; li < nlist; ++li) {
         const int sb = use_xlist ? xi[xo[b] + li] : b;
@@ -362,37 +364,23 @@ check_potential_kernel(const int *__restrict__ boxes, int nbox, int use_xlist, c
             __syncthreads();
             for (int k = tid; k < cnt; k += kChkThreads) sh[k] = rec[base + k];
             __syncthreads();
-            if (has0) {
-                int s = 0;
-                for (; s + 1 < cnt; s += 2) {  // two independent pairs per step
-                    const SrcRec qa = sh[s], qb = sh[s + 1];
-                    chk_pair<SL, DL>(x, y, z, qa, a34, c3, ox, oy, oz);
-                    chk_pair<SL, DL>(x, y, z, qb, a34, c3, ox, oy, oz);
-                    if (has1) {
-                        chk_pair<SL, DL>(x1, y1, z1, qa, a34, c3, px, py, pz);
-                        chk_pair<SL, DL>(x1, y1, z1, qb, a34, c3, px, py, pz);
-                    }
-                }
-                if (s < cnt) {
-                    const SrcRec q = sh[s];
-                    chk_pair<SL, DL>(x, y, z, q, a34, c3, ox, oy, oz);
-                    if (has1) chk_pair<SL, DL>(x1, y1, z1, q, a34, c3, px, py, pz);
+            if (has[0]) {
+                for (int k = 0; k < cnt; ++k) {
+                    const SrcRec q = sh[k];
+#pragma unroll
+                    for (int j = 0; j < NPT; ++j) chk_pair<SL, DL>(x[j], y[j], z[j], q, a34, c3, o[j][0], o[j][1], o[j][2]);
                 }
             }
         }
     }
-    if (has0) {
-        float *o = out + (int64_t)b * ldo + 3 * tid;
-        o[0] = ox;
-        o[1] = oy;
-        o[2] = oz;
-    }
-    if (has1) {
-        float *o = out + (int64_t)b * ldo + 3 * (tid + kChkThreads);
-        o[0] = px;
-        o[1] = py;
-        o[2] = pz;
-    }
+#pragma unroll
+    for (int j = 0; j < NPT; ++j)
+        if (has[j]) {
+            float *q = out + (int64_t)b * ldo + 3 * (tid + j * kChkThreads);
+            q[0] = o[j][0];
+            q[1] = o[j][1];
+            q[2] = o[j][2];
+        }
 }
 
 // ------------------------------------------------------------------------------------
@@ -1380,18 +1368,15 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     auto check_pot = [&](const int *boxes, int nbx, int use_x, float radius, float *outp, cudaStream_t s) {
         const dim3 grid((unsigned)nbx, (unsigned)ncol);
         const int64_t rc = ns, oc = (int64_t)nb * ld;
-        if (sl && dl)
-            check_potential_kernel<true, true><<<grid, kChkThreads, 0, s>>>(
-                boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
-                n, radius, W.src_rec.as<SrcRec>(), kc.a34, 3.f / kc.b12, outp, ld, rc, oc);
-        else if (sl)
-            check_potential_kernel<true, false><<<grid, kChkThreads, 0, s>>>(
-                boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
-                n, radius, W.src_rec.as<SrcRec>(), kc.a34, 3.f / kc.b12, outp, ld, rc, oc);
-        else
-            check_potential_kernel<false, true><<<grid, kChkThreads, 0, s>>>(
-                boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(), T.box_src.as<int2>(), geom, O.surf.as<float4>(),
-                n, radius, W.src_rec.as<SrcRec>(), kc.a34, 3.f / kc.b12, outp, ld, rc, oc);
+        auto go = [&](auto kern) {
+            kern<<<grid, kChkThreads, 0, s>>>(boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(),
+                                              T.box_src.as<int2>(), geom, O.surf.as<float4>(), n, radius,
+                                              W.src_rec.as<SrcRec>(), kc.a34, 3.f / kc.b12, outp, ld, rc, oc);
+        };
+        const bool two = n <= 2 * kChkThreads;  // check points per thread: 2, else 4
+        if (sl && dl) two ? go(check_potential_kernel<true, true, 2>) : go(check_potential_kernel<true, true, 4>);
+        else if (sl) two ? go(check_potential_kernel<true, false, 2>) : go(check_potential_kernel<true, false, 4>);
+        else two ? go(check_potential_kernel<false, true, 2>) : go(check_potential_kernel<false, true, 4>);
     };
     // arguments of the leaf evaluation (the stress kind re-packs its sources below)
     EvalArgs e;

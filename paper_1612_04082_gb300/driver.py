@@ -299,9 +299,11 @@ class LearnedWarmStart:
 
     uses_operator = True
 
-    def __init__(self, n_hidden=256, n_layers=4, epochs=150, batch=512, lr=1e-3, seed=1612):
+    def __init__(self, n_hidden=256, n_layers=4, epochs=150, batch=512, lr=1e-3, seed=1612, max_rows=65536):
         self.net = Mlp(11, n_hidden, n_layers, 3, seed)
         self.kw = dict(epochs=epochs, batch=batch, lr=lr, seed=seed)
+        self.max_rows = max_rows
+        self.rng = np.random.default_rng(seed)
         self.X, self.Y = [], []
         self.trained = False
         self.train_stats = []
@@ -312,6 +314,15 @@ class LearnedWarmStart:
         self.X.append(rec.features.astype(np.float32))
         self.Y.append((rec.unknowns - rec.features[:, 7:10]).astype(np.float32))
         X, Y = np.concatenate(self.X), np.concatenate(self.Y)
+        if len(X) > self.max_rows:
+            # the training set of one iteration is bounded: the newest iteration's rows first,
+            # then a random sample of the earlier ones (the cost per iteration stays flat)
+            n_new = min(len(self.X[-1]), self.max_rows)
+            new = np.arange(len(X) - len(self.X[-1]), len(X))[-n_new:]
+            old = self.rng.choice(len(X) - len(self.X[-1]), self.max_rows - n_new, replace=False) \
+                if self.max_rows > n_new else np.zeros(0, np.int64)
+            keep = np.concatenate([old, new])
+            X, Y = X[keep], Y[keep]
         t0 = time.perf_counter()
         st = self.net.train(X, Y, **self.kw)
         st["seconds"] = time.perf_counter() - t0

@@ -2,7 +2,7 @@
 // per-element features of an optimisation iteration to the initial guess of its unknowns,
 // trained on the GPU on (features, converged unknowns) pairs of earlier iterations.  The paper
 // has no learned component (it reuses nothing between iterations); this is the layer the
-// optimisation loop adds on top of the method, judged by plain GMRES from zero.
+// optimisation loop adds on top of the method, with plain GMRES from zero as its fallback.
 //
 // Network: d_0 inputs -> (hidden, ReLU) x (L - 1) -> d_L outputs.  Inputs and targets are
 // standardised per column with statistics of the training set.  Master weights are FP32; the

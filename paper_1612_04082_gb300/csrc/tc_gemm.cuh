@@ -696,7 +696,16 @@ struct TcBoxArgs {
 
 __host__ __device__ inline uint32_t box_smem_bytes() { return BOX_STAGES * STAGE_BYTES + 128 + 2 * BN * 4; }
 
-// three-term BF16 split of 8 FP32 values, stored as three 16-byte core-matrix rows
+// three-term BF16 split of 8 FP32 values, stored as three 16-byte core-matrix rows.  Two
+// values at a time: one packed round-to-nearest conversion gives both BF16 terms (low half =
+// the first value), and each term is widened back by a shift or a mask (BF16 is the top half
+// of an FP32), so a = h + m + l exactly with 11 instructions per pair of values.
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
 __device__ __forceinline__ void store_split3(unsigned char *dst, uint32_t term_stride, const float4 &x0,
                                              const float4 &x1)
 {
@@ -704,21 +713,14 @@ __device__ __forceinline__ void store_split3(unsigned char *dst, uint32_t term_s
     uint32_t h[4], m[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        uint32_t ph = 0, pm = 0, pl = 0;
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float a = v[2 * q + e];
-            const __nv_bfloat16 th = __float2bfloat16_rn(a);
-            const float r1 = a - __bfloat162float(th);
-            const __nv_bfloat16 tm = __float2bfloat16_rn(r1);
-            const __nv_bfloat16 tl = __float2bfloat16_rn(r1 - __bfloat162float(tm));
-            ph |= (uint32_t)__bfloat16_as_ushort(th) << (16 * e);
-            pm |= (uint32_t)__bfloat16_as_ushort(tm) << (16 * e);
-            pl |= (uint32_t)__bfloat16_as_ushort(tl) << (16 * e);
-        }
-        h[q] = ph;
-        m[q] = pm;
-        l[q] = pl;
+        const float a = v[2 * q], b = v[2 * q + 1];
+        const uint32_t th = bf16x2_rn(a, b);
+        const float ra = a - __uint_as_float(th << 16), rb = b - __uint_as_float(th & 0xffff0000u);
+        const uint32_t tm = bf16x2_rn(ra, rb);
+        const float sa = ra - __uint_as_float(tm << 16), sb = rb - __uint_as_float(tm & 0xffff0000u);
+        h[q] = th;
+        m[q] = tm;
+        l[q] = bf16x2_rn(sa, sb);
     }
     *reinterpret_cast<uint4 *>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4 *>(dst + term_stride) = make_uint4(m[0], m[1], m[2], m[3]);

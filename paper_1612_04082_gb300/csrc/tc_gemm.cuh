@@ -178,11 +178,12 @@ __global__ void split_pairs_kernel(const float *__restrict__ X, int64_t n_rows, 
     uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * q]), h1 = __float2bfloat16_rn(v[2 * q + 1]);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * q] - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * q + 1] - __bfloat162float(h1));
-        h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);  // low half = first value
+        const uint32_t hb = *reinterpret_cast<const uint32_t *>(&hh);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(v[2 * q] - __uint_as_float(hb << 16),
+                                                        v[2 * q + 1] - __uint_as_float(hb & 0xffff0000u));
+        h[q] = hb;
+        l[q] = *reinterpret_cast<const uint32_t *>(&ll);
     }
     uint16_t *dst = X2 + row * 2 * Kp + (interleaved ? kb * 16 : kb * 8);
     *reinterpret_cast<uint4 *>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -667,7 +668,7 @@ constexpr int KC = 32;
 constexpr int NTERM = 3;
 constexpr int BOX_STAGES = 3;
 constexpr int BOX_THREADS = 256;  // = BN * KC / 8: one 8-value group of one column per thread
-constexpr int BOX_FB = 2;               // chunks per block of the main accumulator
+constexpr int BOX_FB = 4;               // chunks per block of the main accumulator (>= BOX_STAGES - 1)
 constexpr int BOX_TMEM_COLS = 4 * BN;  // main x2 | small terms | unused (power of two)
 
 constexpr uint32_t A_TERM = BM * KC * 2;  // bytes of one term of an operator chunk

@@ -129,6 +129,14 @@ typedef struct kfmm_stats {
                                     upward density evaluated at targets                     */
     int32_t m2l_chunk;           /* columns per M2L work item in use (tuned or default)     */
     float eval_item_cost;        /* cost cap of the leaf-evaluation items in use            */
+    float fp32_box_ratio;        /* half-width of a box at the deepest level over the FP32
+                                    spacing of the largest coordinate of its root cube (the
+                                    smallest over the point sets).  Positions are FP32, so the
+                                    check and equivalent surfaces of the deepest boxes sit up
+                                    to 1 / ratio of a half-width off: measured 4e-4 relative
+                                    error at a ratio of ~17, 1.3e-5 at 1e6 points on a 2x1x1
+                                    box (ratio 16384).  Below ~100 shift the points towards
+                                    the origin or expect the FMM error to grow.                */
 } kfmm_stats;
 
 typedef struct kfmm_ctx kfmm_ctx;

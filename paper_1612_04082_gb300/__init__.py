@@ -52,7 +52,7 @@ class kfmm_stats(ctypes.Structure):
                 ("l2p_interactions", ctypes.c_int64), ("p2l_interactions", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("up_rank", ctypes.c_int32), ("down_rank", ctypes.c_int32),
                 ("n_xboxes", ctypes.c_int32), ("n_wboxes", ctypes.c_int32), ("m2l_chunk", ctypes.c_int32),
-                ("eval_item_cost", ctypes.c_float)]
+                ("eval_item_cost", ctypes.c_float), ("fp32_box_ratio", ctypes.c_float)]
 
 
 if not os.path.exists(LIB_PATH):

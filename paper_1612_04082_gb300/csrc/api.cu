@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" entry points declared in include/kifmm_elastic.h.
 // Argument checks, host-pointer staging and dispatch; the work happens in tree.cu, fmm.cu
 // and direct.cu.
+#include <algorithm>
 #include <cmath>
 #include <new>
 
@@ -324,6 +325,19 @@ kfmm_status kfmm_get_stats(const kfmm_ctx *ctx, kfmm_stats *st)
     st->n_wboxes = T.n_wboxes;
     st->m2l_chunk = ctx->tune.m2l_chunk;
     st->eval_item_cost = ctx->tune.eval_cost;
+    // resolution of the FP32 positions at the deepest level: half-width of a box there over
+    // the FP32 spacing of the largest coordinate of its root cube, the smallest over the sets
+    double ratio = 0.0;
+    for (int k = 0; k < T.n_sets && 8 * (size_t)k + 3 < T.set_roots.size(); ++k) {
+        const double *r = &T.set_roots[8 * (size_t)k];  // lower corner x, y, z, side
+        double cmax = 0.0;
+        for (int c = 0; c < 3; ++c) cmax = std::max(cmax, std::max(std::fabs(r[c]), std::fabs(r[c] + r[3])));
+        const double half = 0.5 * r[3] / std::ldexp(1.0, std::max(0, T.n_levels - 1));
+        const double spacing = cmax > 0.0 ? std::ldexp(1.0, (int)std::floor(std::log2(cmax)) - 23) : 1e-45;
+        const double q = half / spacing;
+        ratio = k == 0 ? q : std::min(ratio, q);
+    }
+    st->fp32_box_ratio = (float)ratio;
     return KFMM_OK;
 }
 

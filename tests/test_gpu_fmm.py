@@ -534,7 +534,11 @@ def test_clustered_points_deep_tree(K):
     sl, dl = r32(sl), r32(dl)
     with make_ctx(K, G1, NU1) as c:
         c.build(dev(src), dev(nrm), dev(src))
-        assert c.stats()["n_levels"] > 11
+        st = c.stats()
+        assert st["n_levels"] > 11
+        # deepest half-width over the FP32 spacing at the root cube's largest coordinate
+        half = 0.5 / 2.0 ** (st["n_levels"] - 1)
+        assert 0.4 * half * 2.0 ** 23 <= st["fp32_box_ratio"] <= 2.5 * half * 2.0 ** 23
         out = torch.zeros(len(src), 3, device="cuda:0")
         c.eval(dev(sl), dev(dl), out)
         got = out.cpu().numpy().astype(np.float64)
@@ -557,7 +561,9 @@ def test_full_size_bench_workload(K):
         out = torch.full((n, 3), float("nan"), device="cuda:0")
         c.eval(dev(sl), dev(dl), out)
         got = out.cpu().numpy().astype(np.float64)
-        assert c.stats()["n_levels"] >= 8
+        st = c.stats()
+        assert st["n_levels"] >= 8
+        assert st["fp32_box_ratio"] > 1000  # FP32 positions resolve the deepest boxes
     assert np.all(np.isfinite(got))
     idx = W.subsample(n, 300)
     ref = O.direct_disp(src[idx], src, nrm, sl, dl, G1, NU1)

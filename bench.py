@@ -427,14 +427,15 @@ def homogenisation_leg(K, local, world, tol=1e-5):
     return out
 
 
-def batch_leg(K, local, world, flush, steps=5, warmup=2):
-    """32 independent box-with-voids surfaces of uneven size (5k-250k points each, log-uniform)
-    in one tree and one set of launches (kfmm_build_sets + one SL+DL evaluation), against the
-    same surfaces built and evaluated one by one on the same context."""
+def batch_leg(K, local, world, flush, steps=3, warmup=1):
+    """32 independent box-with-voids surfaces of uneven size, 5k-250k triangles each
+    (log-uniform) as their 16 quadrature points per triangle (80k-4M points), in one tree and
+    one set of launches (kfmm_build_sets + one SL+DL evaluation), against the same surfaces
+    built and evaluated one by one on the same context."""
     import torch
     import workloads as W
     dev = torch.device("cuda", local)
-    pts, nrm, off = W.surface_batch()
+    pts, nrm, off = W.surface_batch(32, 16 * 5000, 16 * 250000)
     sl, dl = W.densities(len(pts))
     x = torch.tensor(pts, dtype=torch.float32, device=dev)
     nn = torch.tensor(nrm, dtype=torch.float32, device=dev)
@@ -472,9 +473,9 @@ def batch_leg(K, local, world, flush, steps=5, warmup=2):
     ms_b = timed(batched)
     ms_s = timed(one_by_one)
     f.close()
-    return {"workload": f"{n_sets} box-with-voids surfaces, {int(np.diff(off).min())}-"
-                        f"{int(np.diff(off).max())} points each, {len(pts)} in all; tree build + one SL+DL "
-                        "evaluation per step, p=6",
+    return {"workload": f"{n_sets} box-with-voids surfaces of 5k-250k triangles as 16 quadrature points each: "
+                        f"{int(np.diff(off).min())}-{int(np.diff(off).max())} points per surface, {len(pts)} in all; "
+                        "tree build + one SL+DL evaluation per step, p=6",
             "ms_per_step": ms_b, "targets_per_s": aggregate_rate(len(pts), world, ms_b / 1e3),
             "one_by_one_ms_per_step": ms_s, "speedup_vs_one_by_one": ms_s / ms_b}
 

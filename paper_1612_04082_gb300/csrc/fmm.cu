@@ -26,6 +26,17 @@ static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // largest padded M2L rank whose operand tiles fit the shared memory of one CTA
 static inline bool tc_rank_ok(int rp) { return tc::smem_bytes(rp) <= 227 * 1024; }
 
+// raise a kernel's dynamic shared-memory limit to at least `bytes` (the limit belongs to the
+// function, shared by every context of the process)
+template <class K> static cudaError_t raise_smem_limit(K *kernel, int bytes)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    if (a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 // round-to-nearest-even FP32 -> BF16 (finite inputs)
 static inline uint16_t host_bf16(float f)
 {
@@ -222,15 +233,11 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
         KF_TRY(upload_tc_op(ctx, O.tc_vd, H->vd.data(), 1, m, kd));
     }
     O.box_tc = (tcb & 14) != 0;
-    // dynamic shared memory of the tensor-core kernels (set here, outside any graph capture)
-    KF_CUDA(cudaFuncSetAttribute(tc::tc_box_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc::box_smem_bytes()));
-    if (O.m2l_pairs_rows)
-        KF_CUDA(cudaFuncSetAttribute(tc::tc_m2l_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)tc::mt_smem_bytes(rp)));
-    else if (O.m2l_tc_mtiles > 0)
-        KF_CUDA(cudaFuncSetAttribute(tc::tc_gather_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)tc::smem_bytes(rp)));
+    // dynamic shared memory of the tensor-core kernels (set here, outside any graph capture;
+    // raised, never lowered: another context of this process may use a larger rank)
+    KF_CUDA(raise_smem_limit(tc::tc_box_gemm_kernel, (int)tc::box_smem_bytes()));
+    if (O.m2l_pairs_rows) KF_CUDA(raise_smem_limit(tc::tc_m2l_kernel, (int)tc::mt_smem_bytes(rp)));
+    else if (O.m2l_tc_mtiles > 0) KF_CUDA(raise_smem_limit(tc::tc_gather_gemm_kernel, (int)tc::smem_bytes(rp)));
     O.p = prm.p;
     O.nu = prm.nu;
     O.r_inner = prm.r_inner;

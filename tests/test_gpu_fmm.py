@@ -586,3 +586,26 @@ def test_bounded_wait_gives_up_and_context_survives(K):
         idx = W.subsample(len(src), 200)
         ref = O.direct_disp(src[idx], src, nrm, sl, dl, G1, NU1)
         assert rel(out.cpu().numpy().astype(np.float64)[idx], ref) < 1e-4
+
+
+def test_contexts_of_different_rank_coexist(K):
+    """Two contexts whose M2L ranks differ (different basis cuts) alternate evaluations: the
+    shared-memory limit of a tensor-core kernel belongs to the function, so building the
+    smaller context must not shrink it below what the larger one launches with."""
+    src, nrm = W.box_with_voids_points(20000, n_voids=6)
+    sl, dl = W.densities(len(src))
+    src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
+    idx = W.subsample(len(src), 200)
+    ref = O.direct_disp(src[idx], src, nrm, sl, dl, G1, NU1)
+    with make_ctx(K, G1, NU1) as a, make_ctx(K, G1, NU1, m2l_rtol=1e-3) as b:
+        outs = {}
+        for name, c in (("a", a), ("b", b), ("a2", a)):
+            if name != "a2":
+                c.build(dev(src), dev(nrm), dev(src))
+            out = torch.zeros(len(src), 3, device="cuda:0")
+            c.eval(dev(sl), dev(dl), out)
+            outs[name] = out.cpu().numpy().astype(np.float64)
+        assert b.stats()["m2l_rank"] < a.stats()["m2l_rank"]
+    assert rel(outs["a"][idx], ref) < 1e-4
+    assert rel(outs["a2"], outs["a"]) < 1e-6
+    assert rel(outs["b"][idx], ref) < 1e-2

@@ -404,9 +404,11 @@ void bem_default_solve_opts(bem_solve_opts *o);
 /* Triangulated boundary: verts [nv][3] FP64, tris [nt][3] int32 (vertex order gives the
  * normal by the right-hand rule; it must point out of the material).  `op` is a
  * bem_operator.  opt as for kfmm_create (NULL = defaults), except that leaf_cap = 0 (and
- * opt = NULL) lets the BEM pick its leaf caps: 256 quadrature sources per leaf up to 2^21
- * sources and 512 above for the boundary sums, 1024 for the interior evaluations of
- * bem_interior / bem_topo_derivative.  Rejects zero-area triangles. */
+ * opt = NULL) lets the BEM pick its leaf caps: for the boundary sums, with autotune on, the
+ * fastest of 128, 256, 512 and 1024 quadrature sources per leaf, timed on the surface at the
+ * first operator application (without autotune: 256 up to 2^21 sources, 512 above); 1024
+ * for the interior evaluations of bem_interior / bem_topo_derivative.  Rejects zero-area
+ * triangles. */
 kfmm_status bem_create(bem_ctx **out, const kfmm_options *opt, int op, const double *verts, int64_t nv,
                        const int32_t *tris, int64_t nt);
 kfmm_status bem_destroy(bem_ctx *b);

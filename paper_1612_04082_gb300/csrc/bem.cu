@@ -639,6 +639,51 @@ static kfmm_status bem_near_setup(bem_ctx *b)
     return KFMM_OK;
 }
 
+// Leaf cap of the boundary sums, timed on this surface: the cost of a matvec swings with how
+// the tree levels fall on the geometry (the P2L of the X lists above all), by up to 1.7x
+// between neighbouring caps (a cell with 16 voids, 208k triangles: 15.8, 16.2, 8.8, 13.7 and
+// 7.9 ms at 64 ... 1024).  Each candidate is built and evaluated twice (one column of zero
+// densities: the cost does not depend on the values); the second evaluation is timed.
+static kfmm_status bem_tune_leaf_cap(bem_ctx *b)
+{
+    const int64_t nt = b->nt, nq = 16 * nt;
+    BK_CUDA(b->slq.ensure(sizeof(float) * 3 * nq));
+    BK_CUDA(b->dlq.ensure(sizeof(float) * 3 * nq));
+    BK_CUDA(b->fout.ensure(sizeof(float) * 3 * nt));
+    BK_CUDA(cudaMemsetAsync(b->slq.p, 0, sizeof(float) * 3 * nq, b->stream));
+    BK_CUDA(cudaMemsetAsync(b->dlq.p, 0, sizeof(float) * 3 * nq, b->stream));
+    cudaEvent_t e0, e1;
+    BK_CUDA(cudaEventCreate(&e0));
+    BK_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_cap = b->opt.leaf_cap;
+    kfmm_status st = KFMM_OK;
+    for (int cap : {128, 256, 512, 1024}) {
+        b->surf->opt.leaf_cap = cap;
+        st = kfmm_build(b->surf, b->q32.as<float>(), b->qn32.as<float>(), nq, b->cen32.as<float>(), nt);
+        if (st == KFMM_OK)
+            st = kfmm_eval(b->surf, b->slq.as<float>(), b->dlq.as<float>(), 1, KFMM_DISP, b->fout.as<float>());
+        if (st != KFMM_OK) break;
+        cudaEventRecord(e0, b->stream);
+        st = kfmm_eval(b->surf, b->slq.as<float>(), b->dlq.as<float>(), 1, KFMM_DISP, b->fout.as<float>());
+        cudaEventRecord(e1, b->stream);
+        if (st != KFMM_OK) break;
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            st = KFMM_ERR_CUDA;
+            break;
+        }
+        if (ms < best) best = ms, best_cap = cap;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != KFMM_OK) return b->fail(st, std::string("bem: leaf-cap tuning: ") + kfmm_last_error(b->surf));
+    b->opt.leaf_cap = b->surf->opt.leaf_cap = best_cap;
+    // the launch shapes were tuned on the first candidate's tree: tune them again on this one
+    b->surf->tune.m2l_done = b->surf->tune.eval_done = false;
+    return KFMM_OK;
+}
+
 static kfmm_status bem_setup(bem_ctx *b)
 {
     const bool material = !(b->setup_G == b->G && b->setup_nu == b->nu);
@@ -660,6 +705,7 @@ static kfmm_status bem_setup(bem_ctx *b)
         b->setup_nu = b->nu;
         b->near_ready = 0;
         if (b->op == BEM_FMM && !b->surf_built) {
+            if (b->auto_cap && b->opt.autotune) BK_TRY(bem_tune_leaf_cap(b));
             BK_FMM(kfmm_build(b->surf, b->q32.as<float>(), b->qn32.as<float>(), 16 * nt, b->cen32.as<float>(), nt));
             b->surf_built = true;
         }
@@ -1059,7 +1105,8 @@ kfmm_status bem_create(bem_ctx **out, const kfmm_options *opt, int op, const dou
     // leaf_cap 0 (or no options): the BEM's own caps.  Its sources are 16 quadrature points
     // per triangle, so the general-purpose cap of 64 leaves only 4 triangles per leaf; on
     // cantilevers of 52k and 400k triangles the surface matvec was fastest at 256 and 512
-    // sources per leaf (1.35 against 3.0 ms; 6.2 against 15.7 ms)
+    // sources per leaf (1.35 against 3.0 ms; 6.2 against 15.7 ms).  With autotuning on (the
+    // default) the boundary sums time 128 ... 1024 on the surface instead (bem_tune_leaf_cap).
     b->auto_cap = !opt || opt->leaf_cap == 0;
     if (b->auto_cap) b->opt.leaf_cap = 16 * nt <= (int64_t)(2 << 20) ? 256 : 512;
     b->op = op;

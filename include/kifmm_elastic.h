@@ -117,16 +117,20 @@ typedef struct kfmm_stats {
     int64_t n_v_pairs;      /* (target box, source box) pairs of the V lists                 */
     int64_t n_w_pairs, n_x_pairs;
     int64_t p2p_interactions;  /* sum over target leaves of n_trg * (U-list sources + sources
-                                  of the W-list boxes evaluated directly)                     */
+                                  of the W-list boxes evaluated directly + sources of the
+                                  X lists summed directly: those of the leaf and of its
+                                  ancestors with at most n_surf / 2 targets)                  */
     int64_t s2m_interactions;  /* n_src * n_surf                                             */
     int64_t l2p_interactions;  /* n_trg * n_surf * (1 + W-list boxes evaluated through their
                                   upward densities)                                          */
-    int64_t p2l_interactions;  /* sum over X pairs of n_src(leaf) * n_surf                   */
+    int64_t p2l_interactions;  /* sum over the X pairs of boxes with more than n_surf / 2
+                                  targets of n_src(leaf) * n_surf                             */
     int64_t kernel_launches;   /* CUDA kernels this context has launched since kfmm_create   */
     int32_t up_rank, down_rank;  /* kept singular values of the upward / downward check-to-
                                     equivalent maps (0 before the first evaluation)          */
-    int32_t n_xboxes, n_wboxes;  /* boxes with an X list; W-list boxes with their own
-                                    upward density evaluated at targets                     */
+    int32_t n_xboxes, n_wboxes;  /* boxes whose X list goes through their downward check
+                                    surface (more than n_surf / 2 targets); W-list boxes with
+                                    their own upward density evaluated at targets            */
     int32_t m2l_chunk;           /* columns per M2L work item in use (tuned or default)     */
     float eval_item_cost;        /* cost cap of the leaf-evaluation items in use            */
     float fp32_box_ratio;        /* half-width of a box at the deepest level over the FP32

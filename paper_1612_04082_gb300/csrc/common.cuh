@@ -163,6 +163,10 @@ struct Tree {
     DevBuf u_off, u_idx;  // U: leaves adjacent to a leaf (incl. itself)
     DevBuf w_off, w_idx;  // W: for leaf B, descendants of colleagues, not adjacent, parent adjacent
     DevBuf x_off, x_idx;  // X: dual of W
+    DevBuf xd_off, xd_idx;  // per box (entries at leaves only): the X-list leaves of the leaf and
+                            // of its ancestors with at most x_direct_max targets, whose sources
+                            // the leaf evaluation sums directly at the leaf's targets
+    int64_t n_xd = 0;
     DevBuf v_off, v_idx;  // V: children of the parent's colleagues, not adjacent
     // V pairs grouped by direction (for the M2L product)
     DevBuf vp_src, vp_trg;  // int [n_v]
@@ -181,6 +185,7 @@ struct Tree {
     // a W-list box with at most this many sources is evaluated directly at the targets (exact
     // and cheaper than its n_surf equivalent points); larger ones through their densities
     int w_direct_max = 0;
+    int x_direct_max = 0;  // a box with an X list and at most this many targets skips P2L
     int split_grid = 0;  // blocks of the cooperative split launch (all resident)
 };
 

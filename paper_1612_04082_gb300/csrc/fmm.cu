@@ -570,6 +570,7 @@ struct EvalArgs {
     const int2 *btrg, *bsrc;
     const float4 *geom;
     const int *uo, *ui, *wo, *wi;
+    const int *xdo, *xdi;  // X-list leaves summed directly at the leaf's targets
     const float4 *trg;
     const int *trg_perm;
     const SrcRec *rec;
@@ -720,7 +721,7 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
     const int2 tr = e.btrg[b];
     const int uo0 = e.uo[b], nU = e.uo[b + 1] - uo0;
     const int wo0 = e.wo[b], nW = e.wo[b + 1] - wo0;
-    (void)nU;
+    const int xdo0 = e.xdo[b];
 
     const int nt = min(64, tr.y - c0);
     int L, nsl;
@@ -775,8 +776,9 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
         else equiv_batch<KIND, NO, 1>(eqp, eqf, kb, n_eq, nsl, x, y, z, e, o);
     }
 
-    // ---- P2P with the direct W boxes and the U-list leaves other than the leaf itself: up
-    //      to 32 source ranges at a time, batches of 32 records filled across ranges
+    // ---- P2P with the direct W boxes, the U-list leaves other than the leaf itself and the
+    //      X-list leaves summed directly: up to 32 source ranges at a time, batches of 32
+    //      records filled across ranges
     bool has_self = false;
     for (int j0 = max(s0, 1); PART != 2 && j0 < s1; j0 += 32) {
         const int nr = min(32, s1 - j0);
@@ -784,14 +786,15 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
         bool self = false;
         if (lane < nr) {
             const int j = j0 + lane;
-            const int sb = j <= nW ? e.wi[wo0 + j - 1] : e.ui[uo0 + j - 1 - nW];
+            const int sb = j <= nW ? e.wi[wo0 + j - 1]
+                                   : (j <= nW + nU ? e.ui[uo0 + j - 1 - nW] : e.xdi[xdo0 + j - 1 - nW - nU]);
             const int2 r = e.bsrc[sb];
             if (j <= nW) {
                 if (r.y - r.x <= e.w_direct_max) {
                     beg = r.x;
                     cnt = r.y - r.x;
                 }
-            } else if (sb == b) {
+            } else if (j <= nW + nU && sb == b) {
                 self = true;
             } else {
                 beg = r.x;
@@ -903,7 +906,8 @@ template <bool EMIT>
 __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, const int2 *__restrict__ btrg,
                                   const int2 *__restrict__ bsrc, const int *__restrict__ uo,
                                   const int *__restrict__ ui, const int *__restrict__ wo,
-                                  const int *__restrict__ wi, int w_direct_max, int n_surf, float item_cost,
+                                  const int *__restrict__ wi, const int *__restrict__ xdo,
+                                  const int *__restrict__ xdi, int w_direct_max, int n_surf, float item_cost,
                                   int split, const int *__restrict__ off, int *__restrict__ cnt,
                                   int4 *__restrict__ items)
 {
@@ -913,7 +917,8 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
     const int b = leaves[li];
     const int2 tr = btrg[b];
     const int w0 = wo[b], nW = wo[b + 1] - w0, u0 = uo[b], nU = uo[b + 1] - u0;
-    const int nseg = 1 + nW + nU;
+    const int x0 = xdo[b], nX = xdo[b + 1] - x0;
+    const int nseg = 1 + nW + nU + nX;
     // one list (part 0), or the near (1) and far (2) lists with counts and offsets at
     // [list][leaf]
     for (int k = 0; k < (split ? 2 : 1); ++k) {
@@ -940,7 +945,7 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
                         far = r.y - r.x > w_direct_max;
                         c = far ? 0.5f * (float)n_surf : (float)(r.y - r.x);
                     } else {
-                        const int2 r = bsrc[ui[u0 + sg - 1 - nW]];
+                        const int2 r = bsrc[sg <= nW + nU ? ui[u0 + sg - 1 - nW] : xdi[x0 + sg - 1 - nW - nU]];
                         c = (float)(r.y - r.x);
                         far = false;
                     }
@@ -1121,13 +1126,13 @@ static void eval_items_launch(kfmm_ctx *ctx, FmmPlans &P, float cost, bool emit)
     if (emit)
         eval_items_kernel<true><<<grid, 128, 0, ctx->stream>>>(
             nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
-            T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, surface_points(ctx->opt.p), cost, P.eval_split,
-            cnt, nullptr, P.eval_items.as<int4>());
+            T.w_off.as<int>(), T.w_idx.as<int>(), T.xd_off.as<int>(), T.xd_idx.as<int>(), T.w_direct_max,
+            surface_points(ctx->opt.p), cost, P.eval_split, cnt, nullptr, P.eval_items.as<int4>());
     else
         eval_items_kernel<false><<<grid, 128, 0, ctx->stream>>>(
             nl, T.leaves.as<int>(), T.box_trg.as<int2>(), T.box_src.as<int2>(), T.u_off.as<int>(), T.u_idx.as<int>(),
-            T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, surface_points(ctx->opt.p), cost, P.eval_split,
-            nullptr, cnt, nullptr);
+            T.w_off.as<int>(), T.w_idx.as<int>(), T.xd_off.as<int>(), T.xd_idx.as<int>(), T.w_direct_max,
+            surface_points(ctx->opt.p), cost, P.eval_split, nullptr, cnt, nullptr);
 }
 
 // counts of all lists side by side ([part][leaf]) and one scan: with a split the far items
@@ -1397,6 +1402,8 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     e.ui = T.u_idx.as<int>();
     e.wo = T.w_off.as<int>();
     e.wi = T.w_idx.as<int>();
+    e.xdo = T.xd_off.as<int>();
+    e.xdi = T.xd_idx.as<int>();
     e.trg = T.trg_xyz.as<float4>();
     e.trg_perm = T.trg_perm.as<int>();
     e.rec = W.src_rec.as<SrcRec>();

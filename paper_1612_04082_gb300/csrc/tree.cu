@@ -808,16 +808,42 @@ __global__ void compact_kernel(int n, const int *__restrict__ flag, const int *_
     if (b < n && flag[b]) out[pos[b]] = b;
 }
 
-// Per box: X list non-empty (xflag); in some W list with more sources than w_direct_max
-// (wflag; a box is in some W list exactly when its X list is non-empty).
+// Per box: X list non-empty and more targets than x_direct_max (xflag: P2L through the
+// downward check surface); in some W list with more sources than w_direct_max (wflag; a box is
+// in some W list exactly when its X list is non-empty).
 __global__ void box_flags_kernel(int n, const int *__restrict__ xcnt, const int2 *__restrict__ bsrc,
-                                 int w_direct_max, int *__restrict__ xflag, int *__restrict__ wflag)
+                                 const int2 *__restrict__ btrg, int w_direct_max, int x_direct_max,
+                                 int *__restrict__ xflag, int *__restrict__ wflag)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
     const bool x = xcnt[b] > 0;
-    xflag[b] = x;
+    xflag[b] = x && btrg[b].y - btrg[b].x > x_direct_max;
     wflag[b] = x && bsrc[b].y - bsrc[b].x > w_direct_max;
+}
+
+// X lists summed directly (the dual of the direct W boxes): a box B with an X list and at most
+// x_direct_max targets skips P2L (n_surf check points per source) and each leaf L under B sums
+// the sources of X(B) at its own targets instead.  Per leaf: the X lists of the leaf and its
+// ancestors that take this path, counted (FILL false) or written at off[L] (FILL true).
+template <bool FILL>
+__global__ void xd_list_kernel(int n_leaves, const int *__restrict__ leaves, const int *__restrict__ parent,
+                               const int2 *__restrict__ btrg, const int *__restrict__ xo,
+                               const int *__restrict__ xi, int x_direct_max, int *__restrict__ cnt,
+                               const int *__restrict__ off, int *__restrict__ idx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_leaves) return;
+    const int leaf = leaves[i];
+    int n = 0, at = FILL ? off[leaf] : 0;
+    for (int b = leaf; b >= 0; b = parent[b]) {
+        const int nx = xo[b + 1] - xo[b];
+        if (nx == 0 || btrg[b].y - btrg[b].x > x_direct_max) continue;
+        if (FILL)
+            for (int k = 0; k < nx; ++k) idx[at++] = xi[xo[b] + k];
+        n += nx;
+    }
+    if (!FILL) cnt[leaf] = n;
 }
 
 // V pairs grouped by direction (dx, dy, dz) in [-3,3]^3 minus [-1,1]^3: 316 groups.
@@ -905,7 +931,7 @@ __global__ void work_count_kernel(int n_boxes, const int *__restrict__ leaf, con
                                   const int2 *__restrict__ btrg, const int *__restrict__ uo,
                                   const int *__restrict__ ui, const int *__restrict__ wo,
                                   const int *__restrict__ wi, int w_direct_max, const int *__restrict__ xo,
-                                  const int *__restrict__ xi, unsigned long long *__restrict__ acc)
+                                  const int *__restrict__ xi, int x_direct_max, unsigned long long *__restrict__ acc)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_boxes) return;
@@ -922,7 +948,11 @@ __global__ void work_count_kernel(int n_boxes, const int *__restrict__ leaf, con
         p2p = (unsigned long long)nt * ns;
         l2p = (unsigned long long)nt * n_eq;
     }
-    for (int k = xo[b]; k < xo[b + 1]; ++k) p2l += bsrc[xi[k]].y - bsrc[xi[k]].x;
+    unsigned long long xs = 0;
+    for (int k = xo[b]; k < xo[b + 1]; ++k) xs += bsrc[xi[k]].y - bsrc[xi[k]].x;
+    const int ntb = btrg[b].y - btrg[b].x;
+    if (ntb > x_direct_max) p2l = xs;                       // through the check surface
+    else p2p += (unsigned long long)ntb * xs;               // summed at the targets
     if (p2p) atomicAdd(&acc[0], p2p);
     if (l2p) atomicAdd(&acc[1], l2p);
     if (p2l) atomicAdd(&acc[2], p2l);
@@ -1158,13 +1188,14 @@ kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, cons
         // iff C is in X(b)); those with more sources than half the surface points take the M2P
         // path, the others are evaluated directly.
         T.w_direct_max = surface_points(ctx->opt.p) / 2;
+        T.x_direct_max = surface_points(ctx->opt.p) / 2;
         KF_CUDA(xflag.ensure(sizeof(int) * n_boxes));
         KF_CUDA(xpos.ensure(sizeof(int) * n_boxes));
         KF_CUDA(wflag.ensure(sizeof(int) * n_boxes));
         KF_CUDA(wpos.ensure(sizeof(int) * n_boxes));
         box_flags_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(
-            n_boxes, cnt.as<int>() + 3 * (size_t)n_boxes, T.box_src.as<int2>(), T.w_direct_max, xflag.as<int>(),
-            wflag.as<int>());
+            n_boxes, cnt.as<int>() + 3 * (size_t)n_boxes, T.box_src.as<int2>(), T.box_trg.as<int2>(),
+            T.w_direct_max, T.x_direct_max, xflag.as<int>(), wflag.as<int>());
         KF_LAUNCH();
         KF_TRY(scan_exclusive(ctx, xflag.as<int>(), xpos.as<int>(), n_boxes, H + 4));
         KF_TRY(scan_exclusive(ctx, wflag.as<int>(), wpos.as<int>(), n_boxes, H + 5));
@@ -1192,6 +1223,28 @@ kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, cons
     compact_kernel<<<grid_for(n_boxes, 256, 1 << 30), 256, 0, st>>>(n_boxes, wflag.as<int>(), wpos.as<int>(),
                                                                      T.wboxes.as<int>());
     KF_LAUNCH();
+    // ---- X lists summed directly at the leaves (per box; zero counts off the leaves)
+    {
+        DevBuf &xc = tmp[6];
+        KF_CUDA(xc.ensure(sizeof(int) * (n_boxes + 1)));
+        KF_CUDA(cudaMemsetAsync(xc.p, 0, sizeof(int) * (n_boxes + 1), st));
+        KF_CUDA(T.xd_off.ensure(sizeof(int) * (n_boxes + 1)));
+        const int nl = T.n_leaves;
+        xd_list_kernel<false><<<grid_for(nl, 128, 1 << 30), 128, 0, st>>>(
+            nl, T.leaves.as<int>(), T.box_parent.as<int>(), T.box_trg.as<int2>(), T.x_off.as<int>(), T.x_idx.as<int>(),
+            T.x_direct_max, xc.as<int>(), nullptr, nullptr);
+        KF_LAUNCH();
+        KF_TRY(scan_exclusive(ctx, xc.as<int>(), T.xd_off.as<int>(), n_boxes + 1, H + 7));
+        int nxd = 0;
+        KF_CUDA(cudaMemcpyAsync(&nxd, H + 7, sizeof(int), cudaMemcpyDeviceToHost, st));
+        KF_TRY(sync_stream(ctx));
+        T.n_xd = nxd;
+        KF_CUDA(T.xd_idx.ensure(sizeof(int) * std::max(1, nxd)));
+        xd_list_kernel<true><<<grid_for(nl, 128, 1 << 30), 128, 0, st>>>(
+            nl, T.leaves.as<int>(), T.box_parent.as<int>(), T.box_trg.as<int2>(), T.x_off.as<int>(), T.x_idx.as<int>(),
+            T.x_direct_max, nullptr, T.xd_off.as<int>(), T.xd_idx.as<int>());
+        KF_LAUNCH();
+    }
     // ---- octant groups per level (M2M / L2L)
     {
         DevBuf &gc = tmp[6];
@@ -1247,7 +1300,7 @@ kfmm_status tree_work_counts(kfmm_ctx *ctx)
     work_count_kernel<<<grid_for(T.n_boxes, 128, 1 << 30), 128, 0, st>>>(
         T.n_boxes, T.box_leaf.as<int>(), T.box_src.as<int2>(), T.box_trg.as<int2>(), T.u_off.as<int>(),
         T.u_idx.as<int>(), T.w_off.as<int>(), T.w_idx.as<int>(), T.w_direct_max, T.x_off.as<int>(),
-        T.x_idx.as<int>(), acc.as<unsigned long long>());
+        T.x_idx.as<int>(), T.x_direct_max, acc.as<unsigned long long>());
     KF_LAUNCH();
     unsigned long long h[3];
     KF_CUDA(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, st));

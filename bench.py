@@ -63,7 +63,7 @@ HOMOG_N = 175       # periodic cell voxels per side: ~200k void-surface triangle
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/); None when the
 # kernel has changed since the counters were taken
 TRAFFIC_BYTES = {"m2l": 350924032 + 114690304,            # the one tc_m2l_kernel launch
-                 "down": 385294336 + 117182464}           # the phase's ten tc_box_gemm_kernel launches
+                 "down": 334326272 + 117628672}           # the phase's ten tc_box_gemm_kernel launches
 TRAFFIC_NOTE = {"m2l": "DRAM bytes of the phase's tc_m2l_kernel launch (ncu, one pass, profiles/)",
                 "down": "DRAM bytes of the phase's ten tc_box_gemm_kernel launches, summed like the flops "
                         "(ncu, one pass, profiles/)"}

@@ -15,6 +15,9 @@ Paper references (sections / equations of the paper):
   gmres                           -- Sec. "Discretization of BIE" (GMRES)
   bem_interior                    -- Eq. stress_1 and the BIE at interior points
   topo_derivative                 -- Eq. deriv and the integrand of Eq. functional
+  periodic_U, periodic_disp       -- Sec. "Periodic cell of a metamaterial": the sums over the
+                                     periodic surface (Fourier series of Eq. disp_1 without
+                                     k = 0, by Ewald's split)
 """
 from __future__ import annotations
 
@@ -250,3 +253,28 @@ def remove_rigid_modes(u, pts, weights=None):
     sw = np.sqrt(np.repeat(w, 3))
     coef, *_ = np.linalg.lstsq(M * sw[:, None], u.reshape(-1) * sw, rcond=None)
     return (u.reshape(-1) - M @ coef).reshape(n, 3)
+
+
+def periodic_U(d, G=1.0, nu=0.3, Lc=1.0, xi=0.0):
+    """Periodic single-layer kernel U_per(d) of a cubic cell of side Lc (Fourier series without
+    k = 0, by Ewald's split; xi <= 0 picks 4.5 / Lc) and its gradient, dU[i, j, m] = dU_ij/dd_m.
+    At d = 0 (mod Lc) the regular part lim (U_per - U)."""
+    d = _f64(d).reshape(3)
+    U, dU = np.zeros(9), np.zeros(27)
+    _load().ko_periodic_U(_dp(d), ctypes.c_double(G), ctypes.c_double(nu), ctypes.c_double(Lc),
+                          ctypes.c_double(xi), _dp(U), _dp(dU))
+    return U.reshape(3, 3), dU.reshape(3, 3, 3)
+
+
+def periodic_disp(trg, src, nrm=None, sl=None, dl=None, G=1.0, nu=0.3, Lc=1.0, xi=0.0):
+    """out[i] = sum_j U_per(x_i - y_j) sl_j + T_per(x_i - y_j, n_j) dl_j over the cubic lattice of
+    side Lc (Sec. "Periodic cell of a metamaterial"); a coincident pair contributes the regular
+    part of the periodic kernel."""
+    trg, src, nrm, sl, dl = (_f64(a) for a in (trg, src, nrm, sl, dl))
+    if dl is not None and nrm is None:
+        raise ValueError("double-layer density needs normals")
+    out = np.zeros((trg.shape[0], 3))
+    _load().ko_periodic_disp(_dp(trg), ctypes.c_int64(trg.shape[0]), _dp(src), _dp(nrm), _dp(sl),
+                             _dp(dl), ctypes.c_int64(src.shape[0]), ctypes.c_double(G),
+                             ctypes.c_double(nu), ctypes.c_double(Lc), ctypes.c_double(xi), _dp(out))
+    return out

@@ -662,3 +662,241 @@ void ko_topo_derivative(const double *sig, int64_t n, double G, double nu, doubl
         if (energy) energy[i] = 0.5 * ((1.0 + nu) * ss - nu * tr * tr) / E;
     }
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Periodic sums (Sec. "Periodic cell of a metamaterial": the integrals over the   */
+/* infinite periodic surface of a cell repeated in all three directions)           */
+/* ------------------------------------------------------------------------------ */
+/* The cell is a cube of side Lc repeated on the lattice Lc Z^3, V = Lc^3.  The periodic
+ * single layer is defined by its Fourier series
+ *     U_per(d) = (1/V) sum_{k != 0} Uhat(k) e^{i k.d},   k = (2 pi / Lc) m,  m in Z^3,
+ *     Uhat_ij(k) = [delta_ij - c2 k_i k_j / k^2] / (G k^2),   c2 = 1 / (2 (1 - nu)),
+ * the Fourier transform of Eq. disp_1.  Leaving out k = 0 makes the cell mean of every
+ * field zero and, for sources with a net force F, adds the uniform body force -F/V that
+ * balances it (without it the lattice sum has no limit).  The double layer is the traction
+ * kernel of that field: with v^(i)(y) = U_per(y - x) e_i, the field at y of a unit force at
+ * x, T_per,ij = sigma_jk[v^(i)](y) n_k(y), which at d = x - y reads
+ *     T_per,ij = -[lambda n_j dU_mi/dd_m + G n_k (dU_ki/dd_j + dU_ji/dd_k)]
+ * (the free-space kernel of Eq. disp_2 is the same expression of U; a test checks it).
+ *
+ * Evaluation by Ewald's split with screening parameter xi.  With
+ *     U_ij = [delta_ij phi(r) + c2 d_i d_j psi(r)] / G,  phi = 1/(4 pi r) <-> 1/k^2,
+ *     psi = -r/(8 pi) <-> 1/k^4,
+ * the short-range parts are
+ *     phi_R = erfc(xi r) / (4 pi r),
+ *     psi_R = -[r erfc(xi r) - exp(-xi^2 r^2) / (xi sqrt(pi))] / (8 pi),
+ * the long-range parts have the transforms g/k^2 and (1 + a) g/k^4, a = k^2/(4 xi^2),
+ * g = exp(-a), and by Poisson's summation formula
+ *     U_per(d) = sum_n U_R(d - n Lc) + (1/V) sum_{k != 0} Uhat_K(k) e^{i k.d} - delta_ij / (4 xi^2 G V),
+ * the last term the transform of U_R at k = 0 (its integral), which the series leaves out.
+ * A pair at distance 0 (a target on a source, image n = 0) contributes the regular part
+ * lim_{d->0} [U_per(d) - U(d)], the periodic analogue of skipping r = 0. */
+
+#define KO_SQRTPI 1.77245385090551602730
+
+/* short-range kernel U_R and its gradient dU[(3i+j)*3+m] = dU_R,ij/dd_m at e != 0; at e = 0 the
+ * regular part U_R - U = -U_smooth(0) (and a zero gradient) */
+static void ewald_real(const double *e, double G, double nu, double xi, double *U, double *dU)
+{
+    const double c2 = 1.0 / (2.0 * (1.0 - nu));
+    const double r2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+    if (r2 == 0.0) {
+        /* U_smooth(0): erf(xi r)/(4 pi r) -> xi/(2 pi^1.5); Hessian of (psi - psi_R) -> -xi/(4 pi^1.5) I */
+        const double s = xi / (KO_PI * KO_SQRTPI) * (0.5 - 0.25 * c2) / G;
+        for (int a = 0; a < 9; ++a) U[a] = (a % 4 == 0) ? -s : 0.0;
+        if (dU) memset(dU, 0, 27 * sizeof(double));
+        return;
+    }
+    const double r = sqrt(r2), rh[3] = {e[0] / r, e[1] / r, e[2] / r};
+    const double ec = erfc(xi * r), ex = exp(-xi * xi * r2);
+    const double phi = ec / (4.0 * KO_PI * r);
+    const double dphi = -(ec / r + 2.0 * xi / KO_SQRTPI * ex) / (4.0 * KO_PI * r);
+    const double p1 = -ec / (8.0 * KO_PI);                                /* psi_R'   */
+    const double p2 = xi * ex / (4.0 * KO_PI * KO_SQRTPI);                /* psi_R''  */
+    const double p3 = -xi * xi * xi * r * ex / (2.0 * KO_PI * KO_SQRTPI); /* psi_R''' */
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const double dij = i == j ? 1.0 : 0.0;
+            const double H = (p2 - p1 / r) * rh[i] * rh[j] + (p1 / r) * dij;
+            U[3 * i + j] = (dij * phi + c2 * H) / G;
+            if (!dU) continue;
+            for (int m = 0; m < 3; ++m) {
+                const double dim = i == m ? 1.0 : 0.0, djm = j == m ? 1.0 : 0.0;
+                const double H3 = (p3 - 3.0 * p2 / r + 3.0 * p1 / r2) * rh[i] * rh[j] * rh[m] +
+                                  (p2 / r - p1 / r2) * (dij * rh[m] + dim * rh[j] + djm * rh[i]);
+                dU[(3 * i + j) * 3 + m] = (dij * dphi * rh[m] + c2 * H3) / G;
+            }
+        }
+}
+
+/* screened transform Uhat_K(k) (without the 1/V) */
+static void ewald_recip(const double *k, double G, double nu, double xi, double *Uk)
+{
+    const double c2 = 1.0 / (2.0 * (1.0 - nu));
+    const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    const double a = k2 / (4.0 * xi * xi), g = exp(-a);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            Uk[3 * i + j] = ((i == j ? g / k2 : 0.0) - c2 * k[i] * k[j] * (1.0 + a) * g / (k2 * k2)) / G;
+}
+
+/* cut-offs: erfc(xi rc) and exp(-kc^2 / (4 xi^2)) below 1e-16 */
+static double ewald_xi(double Lc, double xi) { return xi > 0.0 ? xi : 4.5 / Lc; }
+static double ewald_rc(double xi) { return 6.2 / xi; }
+static double ewald_kc(double xi) { return 12.4 * xi; }
+
+/* d reduced to the image nearest the origin (the sum over the lattice does not change) */
+static void min_image(double *d, double Lc)
+{
+    for (int c = 0; c < 3; ++c) d[c] -= Lc * floor(d[c] / Lc + 0.5);
+}
+
+/* U_per(d) and its gradient dU[(3i+j)*3+m] (the regular part at d = 0 mod Lc) */
+void ko_periodic_U(const double *d_in, double G, double nu, double Lc, double xi, double *U, double *dU)
+{
+    xi = ewald_xi(Lc, xi);
+    const double V = Lc * Lc * Lc, rc = ewald_rc(xi), kc = ewald_kc(xi);
+    double d[3] = {d_in[0], d_in[1], d_in[2]};
+    min_image(d, Lc);
+    memset(U, 0, 9 * sizeof(double));
+    memset(dU, 0, 27 * sizeof(double));
+    const int nr = (int)ceil(rc / Lc + 0.5), nk = (int)ceil(kc * Lc / (2.0 * KO_PI));
+    double Ut[9], dUt[27];
+    for (int a = -nr; a <= nr; ++a)
+        for (int b = -nr; b <= nr; ++b)
+            for (int c = -nr; c <= nr; ++c) {
+                const double e[3] = {d[0] - a * Lc, d[1] - b * Lc, d[2] - c * Lc};
+                if (e[0] * e[0] + e[1] * e[1] + e[2] * e[2] >= rc * rc) continue;
+                ewald_real(e, G, nu, xi, Ut, dUt);
+                for (int q = 0; q < 9; ++q) U[q] += Ut[q];
+                for (int q = 0; q < 27; ++q) dU[q] += dUt[q];
+            }
+    for (int a = -nk; a <= nk; ++a)
+        for (int b = -nk; b <= nk; ++b)
+            for (int c = -nk; c <= nk; ++c) {
+                if (a == 0 && b == 0 && c == 0) continue;
+                const double k[3] = {2.0 * KO_PI * a / Lc, 2.0 * KO_PI * b / Lc, 2.0 * KO_PI * c / Lc};
+                if (k[0] * k[0] + k[1] * k[1] + k[2] * k[2] > kc * kc) continue;
+                ewald_recip(k, G, nu, xi, Ut);
+                const double th = k[0] * d[0] + k[1] * d[1] + k[2] * d[2], cs = cos(th), sn = sin(th);
+                for (int q = 0; q < 9; ++q) {
+                    U[q] += Ut[q] * cs / V;
+                    for (int m = 0; m < 3; ++m) dU[q * 3 + m] -= k[m] * Ut[q] * sn / V;
+                }
+            }
+    const double c0 = 1.0 / (4.0 * xi * xi * G * V);
+    U[0] -= c0;
+    U[4] -= c0;
+    U[8] -= c0;
+}
+
+/* out[3 i + a] = sum_j U_per(x_i - y_j) sl_j + T_per(x_i - y_j, n_j) dl_j; sl, dl may be NULL.
+ * The real-space part is summed pair by pair over the images within the cut-off; the
+ * reciprocal part in its structure-factor form,
+ *   (1/V) sum_k sum_j Re[(Uhat_K sl_j - i w_j) e^{i k.(x - y_j)}]
+ *     = (1/V) sum_k [cos(k.x) (C1 - S2) + sin(k.x) (S1 + C2)],
+ * with w_j = lambda (n.dl) Uhat_K k + G [(k.dl) Uhat_K n + (k.n) Uhat_K dl] the transform of
+ * T_per dl_j and C1, S1 (C2, S2) the sums of Uhat_K sl_j (w_j) times cos, sin(k.y_j). */
+void ko_periodic_disp(const double *trg, int64_t ntrg, const double *src, const double *nrm,
+                      const double *sl, const double *dl, int64_t nsrc, double G, double nu, double Lc,
+                      double xi, double *out)
+{
+    xi = ewald_xi(Lc, xi);
+    const double V = Lc * Lc * Lc, rc = ewald_rc(xi), kc = ewald_kc(xi);
+    const double lam = 2.0 * G * nu / (1.0 - 2.0 * nu);
+    const int nr = (int)ceil(rc / Lc + 0.5), nk = (int)ceil(kc * Lc / (2.0 * KO_PI));
+    /* real space */
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < ntrg; ++i) {
+        double acc[3] = {0.0, 0.0, 0.0}, Ut[9], dUt[27];
+        for (int64_t j = 0; j < nsrc; ++j) {
+            double d[3] = {trg[3 * i] - src[3 * j], trg[3 * i + 1] - src[3 * j + 1], trg[3 * i + 2] - src[3 * j + 2]};
+            min_image(d, Lc);
+            for (int a = -nr; a <= nr; ++a)
+                for (int b = -nr; b <= nr; ++b)
+                    for (int c = -nr; c <= nr; ++c) {
+                        const double e[3] = {d[0] - a * Lc, d[1] - b * Lc, d[2] - c * Lc};
+                        if (e[0] * e[0] + e[1] * e[1] + e[2] * e[2] >= rc * rc) continue;
+                        ewald_real(e, G, nu, xi, Ut, dl ? dUt : NULL);
+                        if (sl)
+                            for (int p = 0; p < 3; ++p)
+                                for (int q = 0; q < 3; ++q) acc[p] += Ut[3 * p + q] * sl[3 * j + q];
+                        if (dl) {
+                            const double *n = nrm + 3 * j;
+                            for (int p = 0; p < 3; ++p)
+                                for (int q = 0; q < 3; ++q) {
+                                    double div = 0.0, sym = 0.0;
+                                    for (int m = 0; m < 3; ++m) {
+                                        div += dUt[(3 * m + p) * 3 + m];
+                                        sym += n[m] * (dUt[(3 * m + p) * 3 + q] + dUt[(3 * q + p) * 3 + m]);
+                                    }
+                                    acc[p] -= (lam * n[q] * div + G * sym) * dl[3 * j + q];
+                                }
+                        }
+                    }
+        }
+        out[3 * i] = acc[0];
+        out[3 * i + 1] = acc[1];
+        out[3 * i + 2] = acc[2];
+    }
+    /* reciprocal space: the wave vectors within the cut-off, their structure factors
+     * (C1, S1, C2, S2 per vector), then the sum over the vectors at every target */
+    int nkv = 0;
+    double *kv = (double *)malloc(sizeof(double) * 3 * (size_t)(2 * nk + 1) * (2 * nk + 1) * (2 * nk + 1));
+    for (int a = -nk; a <= nk; ++a)
+        for (int b = -nk; b <= nk; ++b)
+            for (int c = -nk; c <= nk; ++c) {
+                const double k[3] = {2.0 * KO_PI * a / Lc, 2.0 * KO_PI * b / Lc, 2.0 * KO_PI * c / Lc};
+                const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                if ((a == 0 && b == 0 && c == 0) || k2 > kc * kc) continue;
+                memcpy(kv + 3 * nkv++, k, sizeof(k));
+            }
+    double *sf = (double *)calloc((size_t)nkv * 12, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int q = 0; q < nkv; ++q) {
+        const double *k = kv + 3 * q;
+        double Uk[9];
+        ewald_recip(k, G, nu, xi, Uk);
+        double *C1 = sf + 12 * (size_t)q, *S1 = C1 + 3, *C2 = C1 + 6, *S2 = C1 + 9;
+        for (int64_t j = 0; j < nsrc; ++j) {
+            const double th = k[0] * src[3 * j] + k[1] * src[3 * j + 1] + k[2] * src[3 * j + 2];
+            const double cs = cos(th), sn = sin(th);
+            for (int p = 0; p < 3; ++p) {
+                if (sl) {
+                    const double v = Uk[3 * p] * sl[3 * j] + Uk[3 * p + 1] * sl[3 * j + 1] + Uk[3 * p + 2] * sl[3 * j + 2];
+                    C1[p] += v * cs;
+                    S1[p] += v * sn;
+                }
+                if (dl) {
+                    const double *n = nrm + 3 * j, *u = dl + 3 * j;
+                    const double ndl = n[0] * u[0] + n[1] * u[1] + n[2] * u[2];
+                    const double kdl = k[0] * u[0] + k[1] * u[1] + k[2] * u[2];
+                    const double kn = k[0] * n[0] + k[1] * n[1] + k[2] * n[2];
+                    double w = 0.0;
+                    for (int r = 0; r < 3; ++r) w += Uk[3 * p + r] * (lam * ndl * k[r] + G * (kdl * n[r] + kn * u[r]));
+                    C2[p] += w * cs;
+                    S2[p] += w * sn;
+                }
+            }
+        }
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < ntrg; ++i)
+        for (int q = 0; q < nkv; ++q) {
+            const double *k = kv + 3 * q, *C1 = sf + 12 * (size_t)q, *S1 = C1 + 3, *C2 = C1 + 6, *S2 = C1 + 9;
+            const double th = k[0] * trg[3 * i] + k[1] * trg[3 * i + 1] + k[2] * trg[3 * i + 2];
+            const double cs = cos(th), sn = sin(th);
+            for (int p = 0; p < 3; ++p) out[3 * i + p] += (cs * (C1[p] - S2[p]) + sn * (S1[p] + C2[p])) / V;
+        }
+    free(sf);
+    free(kv);
+    /* the mean of U_R, left out with k = 0 */
+    if (sl) {
+        double F[3] = {0, 0, 0};
+        for (int64_t j = 0; j < nsrc; ++j)
+            for (int p = 0; p < 3; ++p) F[p] += sl[3 * j + p];
+        const double c0 = 1.0 / (4.0 * xi * xi * G * V);
+        for (int64_t i = 0; i < ntrg; ++i)
+            for (int p = 0; p < 3; ++p) out[3 * i + p] -= c0 * F[p];
+    }
+}

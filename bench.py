@@ -25,10 +25,12 @@ The line also carries the BEM half of the metric:
 and the homogenisation leg ("homogenisation"): the six unit-macro-strain load cases of a
 periodic cell with ellipsoidal voids (~209k triangles, 18 density columns) in one solve,
 beside one case at a time; and the batch leg ("batch"): 32 independent surfaces of uneven
-size in one build and evaluation, beside the same surfaces one by one.  Per-phase times come from separate
+size in one build and evaluation, beside the same surfaces one by one; and the periodic leg
+("periodic"): the periodic KIFMM on 1e6 points of a periodic unit cell, beside the same points
+as a free-space sum.  Per-phase times come from separate
 profiled steps (phases serialised); "eval_only_ms" is the evaluation alone on the last tree.
 The FP32 peak of the "alu" rooflines is measured by the library's FMA-chain kernel.
---no-bem, --no-batch and --no-cpu-baseline leave those legs out.
+--no-bem, --no-batch (also the periodic leg) and --no-cpu-baseline leave those legs out.
 """
 from __future__ import annotations
 
@@ -480,6 +482,58 @@ def batch_leg(K, local, world, flush, steps=3, warmup=1):
             "one_by_one_ms_per_step": ms_s, "speedup_vs_one_by_one": ms_s / ms_b}
 
 
+def periodic_leg(K, local, world, flush, n=1000000, steps=10, warmup=3):
+    """The periodic KIFMM on the surfaces of 12 spherical voids of a periodic unit cell (points
+    wrapped across the cell's faces): tree build + one SL+DL evaluation per step, against the
+    same points summed as a free-space problem on the same context."""
+    import torch
+    import workloads as W
+    dev = torch.device("cuda", local)
+    pts, nrm = W.periodic_cell_points(n)
+    sl, dl = W.densities(n)
+    x = torch.tensor(pts, dtype=torch.float32, device=dev)
+    nn = torch.tensor(nrm, dtype=torch.float32, device=dev)
+    s = torch.tensor(sl, dtype=torch.float32, device=dev)
+    d = torch.tensor(dl, dtype=torch.float32, device=dev)
+    out = torch.empty(n, 3, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    f = K.Kfmm(p=6, leaf_cap=64, device=local)
+    f.set_material(K.material_K(1.0, 0.3), 1.0)
+    f.set_stream(stream)
+
+    def step():
+        f.build(x, nn, x)
+        f.eval(s, d, out)
+
+    def timed():
+        for _ in range(warmup):
+            step()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), world, dev)
+
+    f.set_periodic((0.0, 0.0, 0.0), 1.0)
+    t0 = time.perf_counter()
+    step()  # the lattice operator (host FP64, once per operator set) and the launch-shape tuning
+    torch.cuda.synchronize(dev)
+    first_s = time.perf_counter() - t0
+    ms_p = timed()
+    st = f.stats()
+    f.set_periodic(None)
+    ms_f = timed()
+    f.close()
+    return {"workload": f"{n} points on the surfaces of 12 spherical voids of a periodic unit cell, wrapped "
+                        "across its faces; tree build + one SL+DL evaluation per step, p=6, leaf cap 64",
+            "ms_per_step": ms_p, "targets_per_s": aggregate_rate(n, world, ms_p / 1e3),
+            "free_space_ms_per_step": ms_f, "periodic_over_free_space": ms_p / ms_f,
+            "first_step_s": first_s, "n_v_pairs": st["n_v_pairs"], "n_levels": st["n_levels"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -654,6 +708,7 @@ def main():
     bem_small = leg(bem_small_leg, K, local, world) if not args.no_bem else None
     homog = leg(homogenisation_leg, K, local, world) if not args.no_bem else None
     batch = leg(batch_leg, K, local, world, flush) if not args.no_batch else None
+    periodic = leg(periodic_leg, K, local, world, flush) if not args.no_batch else None
 
     line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -678,6 +733,7 @@ def main():
             "bem_small": bem_small,
             "homogenisation": homog,
             "batch": batch,
+            "periodic": periodic,
             "fp32_peak": {"tflops": fp32_meas["tflops"], "n_sms": fp32_meas["n_sms"], "source": "measured",
                           "nominal_at_max_clock": fp32_nominal_tflops(fp32_meas["n_sms"], 2070.0)},
             "tree": {k: st[k] for k in ("n_boxes", "n_leaves", "n_levels", "m2l_rank", "n_v_pairs",

@@ -157,6 +157,25 @@ kfmm_status kfmm_destroy(kfmm_ctx *ctx);
  * Requires K > 0, G > 0 (so -1 < nu < 1/2). */
 kfmm_status kfmm_set_material(kfmm_ctx *ctx, double K, double G);
 
+/* Periodic sums over a cubic cell (Sec. "Periodic cell of a metamaterial": the integrals run
+ * over the infinite periodic surface, and the FMM tree is periodic at every level).  With
+ * on != 0 the next kfmm_build uses the cube [lo, lo + side]^3 as its root, every point must
+ * lie in it (to 1e-6 of side), the interaction lists wrap around the cell and every list
+ * entry names the image of its box that it means; the cell's images beyond the root's 26
+ * neighbours act on the root's downward density through a lattice operator made once per
+ * operator set (FP64 host precompute, Ewald's split).  kfmm_eval then returns
+ *   sum over n in Z^3 of sum_j K(x_i - y_j - n side) den_j
+ * in the sense of the Fourier series without its k = 0 term: the field has zero mean over the
+ * cell, and a net force of the single layer is balanced by a uniform body force.  A target
+ * on a source skips that source only (its other images count).  The displacement sum is
+ * defined up to a constant vector per column (a rigid translation of the periodic field), and
+ * the FMM fixes that constant otherwise than by the zero mean: its lattice operator acts on
+ * the root's equivalent density, which reproduces the cell's field outside the root but not
+ * its cell mean.  Stresses (and TD) carry no constant.  Not with kfmm_build_sets (one cell
+ * per tree).  on = 0 returns to free space; either way the tree must be built again.
+ * lo: 3 doubles (may be NULL with on = 0); side > 0. */
+kfmm_status kfmm_set_periodic(kfmm_ctx *ctx, int on, const double *lo, double side);
+
 /* Enqueue all later work of this context on `stream` (a cudaStream_t; NULL = default). */
 kfmm_status kfmm_set_stream(kfmm_ctx *ctx, void *stream);
 
@@ -257,15 +276,19 @@ kfmm_status kfmm_export_tree(const kfmm_ctx *ctx, int32_t *box_level, int32_t *b
 
 /* Interaction lists as CSR over boxes: which = 'U', 'V', 'W' or 'X'; offsets [n_boxes+1],
  * items [n_pairs] (source box indices).  Either pointer may be NULL; *n_pairs receives the
- * total.  U and W lists are defined for leaves only (empty rows elsewhere). */
+ * total.  U and W lists are defined for leaves only (empty rows elsewhere).  In a periodic
+ * tree (kfmm_set_periodic) an item names an image of a box: the box index in bits 0-25 and,
+ * in bits 26-30, c ^ 13 with c = 9 (sx + 1) + 3 (sy + 1) + (sz + 1) for the image moved by
+ * (sx, sy, sz) in {-1, 0, 1}^3 cells (0 for the unmoved box, so free-space items are plain
+ * box indices). */
 kfmm_status kfmm_export_list(const kfmm_ctx *ctx, char which, int32_t *offsets, int32_t *items,
                              int64_t *n_pairs);
 
 /* ------------------------------------------------------------------------------------
  * Partition over several GPUs (Sec. "Numerical solution": the evaluation is parallelised by
  * giving each process a part of the octree).  Host code on a tree given as host arrays --
- * the arrays of kfmm_export_tree and kfmm_export_list for a built tree; boxes are listed
- * coarse to fine (a parent before its children).  No GPU is needed.
+ * the arrays of kfmm_export_tree and kfmm_export_list for a built free-space tree; boxes are
+ * listed coarse to fine (a parent before its children).  No GPU is needed.
  * ------------------------------------------------------------------------------------ */
 typedef struct kfmm_tree_view {
     int32_t n_boxes;

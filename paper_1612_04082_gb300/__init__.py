@@ -68,6 +68,7 @@ _sig = {
     "kfmm_destroy": (ctypes.c_int, [_vp]),
     "kfmm_set_material": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
     "kfmm_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "kfmm_set_periodic": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_double]),
     "kfmm_build": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64]),
     "kfmm_build_sets": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
     "kfmm_selftest_bounded_wait": (ctypes.c_int, [_vp, _i64]),
@@ -148,6 +149,27 @@ def kfmm_destroy(ctx):
 
 def kfmm_set_material(ctx, K: float, G: float):
     _check(ctx, _lib.kfmm_set_material(ctx, float(K), float(G)))
+
+
+def kfmm_set_periodic(ctx, lo=None, side=1.0):
+    """Periodic cubic cell [lo, lo + side]^3 for the next build (lo None: free space)."""
+    if lo is None:
+        _check(ctx, _lib.kfmm_set_periodic(ctx, 0, None, 1.0))
+        return
+    c = np.ascontiguousarray(lo, dtype=np.float64).reshape(3)
+    _check(ctx, _lib.kfmm_set_periodic(ctx, 1, c.ctypes.data, float(side)))
+
+
+ENT_BITS = 26
+
+
+def list_entries(items):
+    """Box index and image offset [n, 3] (whole cells, -1..1) of interaction-list entries: the
+    box in the low 26 bits, the image of a periodic tree above them (kifmm_elastic.h)."""
+    items = np.asarray(items, dtype=np.int64)
+    code = ((items >> ENT_BITS) & 31) ^ 13
+    shift = np.stack([code // 9 - 1, (code // 3) % 3 - 1, code % 3 - 1], axis=-1)
+    return items & ((1 << ENT_BITS) - 1), shift
 
 
 def kfmm_set_stream(ctx, stream):
@@ -334,6 +356,11 @@ class Kfmm:
 
     def set_stream(self, stream):
         kfmm_set_stream(self.handle, stream)
+
+    def set_periodic(self, lo=None, side=1.0):
+        """Sums over the cubic lattice of the cell [lo, lo + side]^3 from the next build on
+        (lo None: free space again)."""
+        kfmm_set_periodic(self.handle, lo, side)
 
     def build(self, src_xyz, src_nrm, trg_xyz):
         kfmm_build(self.handle, src_xyz, src_nrm, trg_xyz)

@@ -15,7 +15,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libkifmm_elastic.so")
 CU = ["api.cu", "direct.cu", "direct_hi.cu", "tree.cu", "fmm.cu", "bem.cu", "direct_noalloc.cu", "mlp.cu", "peak.cu"]
-CPP = ["precompute.cpp", "voxel.cpp", "shard.cpp"]
+CPP = ["precompute.cpp", "periodic.cpp", "voxel.cpp", "shard.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 denormals flush to zero in the FMM kernels: their operands are nowhere near the
 # denormal range, and the flush drops the denormal handling around the reciprocal square

@@ -152,6 +152,24 @@ kfmm_status kfmm_set_material(kfmm_ctx *ctx, double K, double G)
     return KFMM_OK;
 }
 
+kfmm_status kfmm_set_periodic(kfmm_ctx *ctx, int on, const double *lo, double side)
+{
+    if (!ctx) return KFMM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (on) {
+        if (!lo || !(side > 0.0) || !std::isfinite(side) || !std::isfinite(lo[0]) || !std::isfinite(lo[1]) ||
+            !std::isfinite(lo[2]))
+            return ctx->fail(KFMM_ERR_INVALID_ARG, "periodic: need a finite lower corner and side > 0");
+        for (int c = 0; c < 3; ++c) ctx->cell_lo[c] = lo[c];
+        ctx->cell_side = side;
+    }
+    ctx->periodic = on != 0;
+    ctx->tree.built = false;  // the root and the lists change: build again
+    ctx->plans.valid = false;
+    ctx->graph.reset();
+    return KFMM_OK;
+}
+
 kfmm_status kfmm_set_stream(kfmm_ctx *ctx, void *stream)
 {
     if (!ctx) return KFMM_ERR_INVALID_ARG;

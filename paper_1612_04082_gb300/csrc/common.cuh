@@ -120,11 +120,32 @@ struct Operators {
         bool on = false;  // product runs on the tensor cores
     };
     bool box_tc = false;  // any box operator on the tensor cores
+    // far-lattice operator of a periodic tree's root, root alpha -> root beta (periodic.cpp)
+    DevBuf lat;           // float [kd][kup]
+    bool lat_ready = false;
     TcOp tc_s2a_u, tc_mb, tc_cb, tc_vu, tc_wb, tc_s2a_d, tc_lb, tc_vd;
 };
 
 // points on the surface of a p x p x p lattice (equivalent and check surfaces)
 constexpr int surface_points(int p) { return 6 * (p - 1) * (p - 1) + 2; }
+
+// Entries of the colleague table and the interaction lists: the box index in the low 26 bits
+// and, in a periodic tree, the image of the box that the entry means (the box moved by s cells,
+// s in {-1, 0, 1}^3) in bits 26-30 as (9 (sx + 1) + 3 (sy + 1) + (sz + 1)) ^ 13.  The unmoved
+// image has code 0, so every entry of a free-space tree is the box index itself; entries stay
+// non-negative (-1 marks a missing colleague).
+constexpr int kEntBits = 26;
+constexpr int kEntMask = (1 << kEntBits) - 1;
+__host__ __device__ inline int ent_box(int e) { return e & kEntMask; }
+__host__ __device__ inline int ent_image(int e) { return ((e >> kEntBits) & 31) ^ 13; }  // 0..26
+__host__ __device__ inline int ent_make(int box, int image) { return box | ((image ^ 13) << kEntBits); }
+__host__ __device__ inline void ent_shift(int e, int &sx, int &sy, int &sz)
+{
+    const int c = ent_image(e);
+    sx = c / 9 - 1;
+    sy = (c / 3) % 3 - 1;
+    sz = c % 3 - 1;
+}
 
 // Octree and interaction lists (device arrays unless noted).
 struct Tree {
@@ -187,6 +208,10 @@ struct Tree {
     int w_direct_max = 0;
     int x_direct_max = 0;  // a box with an X list and at most this many targets skips P2L
     int split_grid = 0;  // blocks of the cooperative split launch (all resident)
+    // periodic tree: the root is the cell, colleagues and lists wrap around it (list entries
+    // carry the image of their box), and the cell's far images act through the lattice operator
+    bool periodic = false;
+    float cell = 0.f;  // cell side (the shift of an image by one cell)
 };
 
 // Per-evaluation work arrays.
@@ -209,6 +234,7 @@ struct Work {
     DevBuf hi_rec;       // source records of the compensated direct sum (direct_hi.cu)
     DevBuf hi_part;      // its per-block coordinate bounds
     DevBuf td_stress;    // stresses behind a KFMM_TD evaluation
+    DevBuf net_force;    // double [ncol][3]: net single-layer force of a periodic sum
     // box-vector buffers whose padding lanes are known to be zero: their allocations and the
     // density-column layout they were zeroed for
     void *zero_ptr[8] = {};
@@ -355,6 +381,9 @@ struct kfmm_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_p2l = nullptr, ev_near = nullptr, ev_plans = nullptr;
     double G = 1.0, nu = 0.3;
+    // periodic cell (kfmm_set_periodic): lower corner and side; applies to the next build
+    bool periodic = false;
+    double cell_lo[3] = {0, 0, 0}, cell_side = 1.0;
     std::string err;
     kfmm::Operators ops;
     kfmm::Tree tree;

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <deque>
 #include <mutex>
 
 #include "common.cuh"
@@ -97,9 +98,10 @@ namespace {
 struct CacheEntry {
     host::OpsParams prm;
     host::OpsHost ops;
+    std::vector<double> lat;  // far-lattice operator of a periodic root (made on first use)
 };
 std::mutex g_cache_mu;
-std::vector<CacheEntry> g_cache;
+std::deque<CacheEntry> g_cache;  // entries keep their addresses as the cache grows
 
 bool same_params(const host::OpsParams &a, const host::OpsParams &b)
 {
@@ -122,6 +124,27 @@ kfmm_status upload_padded(kfmm_ctx *ctx, DevBuf &dst, const double *src, int nma
 }
 }  // namespace
 
+// The far-lattice operator of a periodic tree's root for the context's operators (host FP64,
+// made once per operator set and kept with it in the cache), uploaded as FP32 [kd][kup].
+static kfmm_status ensure_lattice(kfmm_ctx *ctx, const host::OpsParams &prm)
+{
+    Operators &O = ctx->ops;
+    std::vector<double> R;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        CacheEntry *E = nullptr;
+        for (auto &e : g_cache)
+            if (same_params(e.prm, prm)) E = &e;
+        if (!E) return ctx->fail(KFMM_ERR_INTERNAL, "lattice operator: operators not in the cache");
+        if (E->lat.empty() && !host::compute_lattice(prm, E->ops, E->lat))
+            return ctx->fail(KFMM_ERR_INTERNAL, "lattice operator precompute failed");
+        R = E->lat;
+    }
+    KF_TRY(upload_padded(ctx, O.lat, R.data(), 1, O.kd, O.ku, round_up(O.ku, 16), O.kd));
+    O.lat_ready = true;
+    return KFMM_OK;
+}
+
 kfmm_status ensure_operators(kfmm_ctx *ctx)
 {
     Operators &O = ctx->ops;
@@ -129,7 +152,7 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
                         ctx->opt.m2l_rtol, ctx->opt.m2l_rank_max};
     if (O.ready && O.p == prm.p && O.nu == prm.nu && O.r_inner == prm.r_inner && O.r_outer == prm.r_outer &&
         O.pinv_rtol == prm.pinv_rtol && O.m2l_rtol == prm.m2l_rtol && O.m2l_rank_max == prm.m2l_rank_max)
-        return KFMM_OK;
+        return ctx->periodic && !O.lat_ready ? ensure_lattice(ctx, prm) : KFMM_OK;
     const host::OpsHost *H = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -248,8 +271,9 @@ kfmm_status ensure_operators(kfmm_ctx *ctx)
     O.n_surf = n;
     O.rank = r;
     O.ready = true;
+    O.lat_ready = false;
     ctx->plans.valid = false;  // box-vector layouts depend on the rank
-    return KFMM_OK;
+    return ctx->periodic ? ensure_lattice(ctx, prm) : KFMM_OK;
 }
 
 namespace {
@@ -333,13 +357,15 @@ __device__ __forceinline__ void chk_pair(float x, float y, float z, const SrcRec
 }
 
 // NPT check points per thread: tid, tid + kChkThreads, ... (n_surf <= NPT kChkThreads); each
-// staged source record serves NPT independent pairs
+// staged source record serves NPT independent pairs.  An X-list entry of a periodic tree that
+// names a moved image of its box stages the box's sources moved by whole cells (cell side).
 template <bool SL, bool DL, int NPT>
 __global__ void __launch_bounds__(kChkThreads)
 check_potential_kernel(const int *__restrict__ boxes, int nbox, int use_xlist, const int *__restrict__ xo,
                        const int *__restrict__ xi, const int2 *__restrict__ bsrc, const float4 *__restrict__ geom,
                        const float4 *__restrict__ surf, int n_surf, float radius, const SrcRec *__restrict__ rec,
-                       float a34, float c3, float *__restrict__ out, int ldo, int64_t rec_col, int64_t out_col)
+                       float a34, float c3, float *__restrict__ out, int ldo, int64_t rec_col, int64_t out_col,
+                       float cell)
 {
     __shared__ SrcRec sh[kChkStage];
     rec += blockIdx.y * rec_col;  // density column blockIdx.y
@@ -364,12 +390,21 @@ check_potential_kernel(const int *__restrict__ boxes, int nbox, int use_xlist, c
     }
     const int nlist = use_xlist ? xo[b + 1] - xo[b] : 1;
     for (int li = 0; li < nlist; ++li) {
-        const int sb = use_xlist ? xi[xo[b] + li] : b;
-        const int2 r = bsrc[sb];
+        const int ent = use_xlist ? xi[xo[b] + li] : b;
+        const int2 r = bsrc[ent_box(ent)];
+        int sx, sy, sz;
+        ent_shift(ent, sx, sy, sz);
+        const float ox = sx * cell, oy = sy * cell, oz = sz * cell;
         for (int base = r.x; base < r.y; base += kChkStage) {
             const int cnt = min(kChkStage, r.y - base);
             __syncthreads();
-            for (int k = tid; k < cnt; k += kChkThreads) sh[k] = rec[base + k];
+            for (int k = tid; k < cnt; k += kChkThreads) {
+                SrcRec q = rec[base + k];
+                q.y.x += ox;
+                q.y.y += oy;
+                q.y.z += oz;
+                sh[k] = q;
+            }
             __syncthreads();
             if (has[0]) {
                 for (int k = 0; k < cnt; ++k) {
@@ -588,7 +623,17 @@ struct EvalArgs {
     int64_t rec_col, phi_col;  // strides of one density column (blockIdx.y) in rec and the phis
     int part;                  // 0: all segments; 1: P2P only (U leaves, direct W boxes);
                                // 2: L2P and M2P only
+    float cell;                // periodic tree: cell side (list entries may name moved images)
 };
+
+// the offset of a moved image from its entry bits (e >> kEntBits, 0 for the unmoved box)
+__device__ __forceinline__ void image_offset(int bits, float cell, float &ox, float &oy, float &oz)
+{
+    const int c = bits ^ 13;
+    ox = (float)(c / 9 - 1) * cell;
+    oy = (float)((c / 3) % 3 - 1) * cell;
+    oz = (float)(c % 3 - 1) * cell;
+}
 
 // one source record, only the fields the kernel family reads
 template <bool SL, bool DL>
@@ -754,12 +799,20 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
     float4 *eqp = eq_smem + (size_t)wid * 2 * e.n_surf, *eqf = eqp + e.n_surf;
     const int n_eq = e.n_surf;
     for (int j = s0; PART != 1 && j < s1 && j <= nW; ++j) {
-        const int src_box = j == 0 ? b : e.wi[wo0 + j - 1];
+        const int ent = j == 0 ? b : e.wi[wo0 + j - 1];
+        const int src_box = ent_box(ent);
         if (j > 0) {
             const int2 r = e.bsrc[src_box];
             if (r.y - r.x <= e.w_direct_max) continue;  // evaluated directly below
         }
-        const float4 g = e.geom[src_box];
+        float4 g = e.geom[src_box];
+        if (ent >> kEntBits) {  // a moved image (periodic tree)
+            float ox, oy, oz;
+            image_offset(ent >> kEntBits, e.cell, ox, oy, oz);
+            g.x += ox;
+            g.y += oy;
+            g.z += oz;
+        }
         const float rad = (j == 0 ? e.r_out : e.r_in) * g.w;
         const float *__restrict__ phi = (j == 0 ? dn_phi : up_phi) + (int64_t)src_box * e.ld_phi;
         __syncwarp();
@@ -784,21 +837,26 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
         const int nr = min(32, s1 - j0);
         int beg = 0, cnt = 0;
         bool self = false;
+        int mbits = 0;  // a moved image of a box (periodic tree): summed after the others
         if (lane < nr) {
             const int j = j0 + lane;
-            const int sb = j <= nW ? e.wi[wo0 + j - 1]
-                                   : (j <= nW + nU ? e.ui[uo0 + j - 1 - nW] : e.xdi[xdo0 + j - 1 - nW - nU]);
-            const int2 r = e.bsrc[sb];
+            const int ent = j <= nW ? e.wi[wo0 + j - 1]
+                                    : (j <= nW + nU ? e.ui[uo0 + j - 1 - nW] : e.xdi[xdo0 + j - 1 - nW - nU]);
+            const int2 r = e.bsrc[ent_box(ent)];
             if (j <= nW) {
                 if (r.y - r.x <= e.w_direct_max) {
                     beg = r.x;
                     cnt = r.y - r.x;
                 }
-            } else if (j <= nW + nU && sb == b) {
+            } else if (j <= nW + nU && ent == b) {
                 self = true;
             } else {
                 beg = r.x;
                 cnt = r.y - r.x;
+            }
+            if (ent >> kEntBits) {
+                mbits = ent >> kEntBits;
+                cnt = 0;  // not in the batches below
             }
         }
         has_self |= __ballot_sync(kFull, self) != 0u;
@@ -838,6 +896,32 @@ __global__ void __launch_bounds__(kEvalThreads) eval_leaf_kernel(EvalArgs e)
                 if (base + 32 + lane < total) nxt = load_rec<SL, DL>(rec, src);
             }
             eval_batch_t<KIND, SL, DL, false, NO>(T, sh, kbeg, cnt2, nsl, x, y, z, e, o);
+        }
+        // moved images of boxes (a periodic tree near the cell's faces): one range at a time,
+        // its sources staged moved by whole cells
+        for (unsigned mv = __ballot_sync(kFull, mbits != 0); mv; mv &= mv - 1) {
+            const int l = __ffs(mv) - 1;
+            const int bits = __shfl_sync(kFull, mbits, l);
+            const int j = j0 + l;  // the segment, read again by the whole warp
+            const int ent = j <= nW ? e.wi[wo0 + j - 1]
+                                    : (j <= nW + nU ? e.ui[uo0 + j - 1 - nW] : e.xdi[xdo0 + j - 1 - nW - nU]);
+            const int2 rr = e.bsrc[ent_box(ent)];
+            if (j <= nW && rr.y - rr.x > e.w_direct_max) continue;  // through its density
+            float ox, oy, oz;
+            image_offset(bits, e.cell, ox, oy, oz);
+            for (int base = rr.x; base < rr.y; base += 32) {
+                const int c2 = min(32, rr.y - base);
+                __syncwarp();
+                if (lane < c2) {
+                    SrcRec q = load_rec<SL, DL>(rec, base + lane);
+                    q.y.x += ox;
+                    q.y.y += oy;
+                    q.y.z += oz;
+                    store_rec<SL, DL>(sh + lane, q);
+                }
+                __syncwarp();
+                eval_batch_t<KIND, SL, DL, false, NO>(T, sh, kbeg, c2, nsl, x, y, z, e, o);
+            }
         }
     }
 
@@ -941,11 +1025,11 @@ __global__ void eval_items_kernel(int n_leaves, const int *__restrict__ leaves, 
                     if (sg == 0) {
                         c = 0.5f * (float)n_surf;
                     } else if (sg <= nW) {
-                        const int2 r = bsrc[wi[w0 + sg - 1]];
+                        const int2 r = bsrc[ent_box(wi[w0 + sg - 1])];
                         far = r.y - r.x > w_direct_max;
                         c = far ? 0.5f * (float)n_surf : (float)(r.y - r.x);
                     } else {
-                        const int2 r = bsrc[sg <= nW + nU ? ui[u0 + sg - 1 - nW] : xdi[x0 + sg - 1 - nW - nU]];
+                        const int2 r = bsrc[ent_box(sg <= nW + nU ? ui[u0 + sg - 1 - nW] : xdi[x0 + sg - 1 - nW - nU])];
                         c = (float)(r.y - r.x);
                         far = false;
                     }
@@ -1304,6 +1388,78 @@ template <class F> static kfmm_status time_launch(kfmm_ctx *ctx, F f, float *ms)
 // All work of one evaluation, enqueued on ctx->stream.  The first call after a build also
 // makes the plans and lazily built tables (it may allocate and synchronise); later calls with
 // the same arguments only enqueue, which is what a CUDA graph captures.
+// The far images of a periodic cell (|n|_inf >= 2 from the root) into the root's downward
+// density, beta_root += R alpha_root for every density column (the root is box 0): one CTA per
+// column, one output row per thread; the root's alpha is read by all threads at once.
+__global__ void __launch_bounds__(256) lattice_kernel(const float *__restrict__ R, int kd, int ku, int ldr,
+                                                      const float *__restrict__ alpha, int64_t a_col,
+                                                      float *__restrict__ beta, int64_t b_col)
+{
+    const float *a = alpha + blockIdx.x * a_col;
+    float *b = beta + blockIdx.x * b_col;
+    for (int i = threadIdx.x; i < kd; i += blockDim.x) {
+        const float *r = R + (size_t)i * ldr;
+        float s = 0.f;
+        for (int j = 0; j < ku; ++j) s = fmaf(r[j], __ldg(&a[j]), s);
+        b[i] += s;
+    }
+}
+
+// A periodic sum whose single layer has a net force F carries the balancing uniform body force
+// -F/V in every cell.  Inside the cell that force makes the far field a non-Navier field, which
+// equivalent densities cannot hold; its particular part P(x - c) F, with
+// P(d) = d d^T / ((4 lambda + 6 G) V) about the cell centre c, is left out of the lattice
+// operator and added here at the targets.  First the net force per density column (FP64):
+__global__ void net_force_kernel(int64_t ns, const float *__restrict__ sl, int ldd, double *__restrict__ F)
+{
+    const int col = blockIdx.y;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
+        const float *q = sl + i * ldd + 3 * col;
+        a0 += q[0];
+        a1 += q[1];
+        a2 += q[2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_down_sync(kFull, a0, o);
+        a1 += __shfl_down_sync(kFull, a1, o);
+        a2 += __shfl_down_sync(kFull, a2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&F[3 * col], a0);
+        atomicAdd(&F[3 * col + 1], a1);
+        atomicAdd(&F[3 * col + 2], a2);
+    }
+}
+
+// then u += P(x - c) F at every target (DISP), or its Hooke stress (STRESS, Voigt order)
+__global__ void net_force_field_kernel(int64_t nt, const float4 *__restrict__ trg, const int *__restrict__ perm,
+                                       const double *__restrict__ F, double cx, double cy, double cz, double coef,
+                                       double lam, double G, int stress, float *__restrict__ out, int ldo)
+{
+    const int col = blockIdx.y;
+    const double f[3] = {F[3 * col], F[3 * col + 1], F[3 * col + 2]};
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nt; k += (int64_t)gridDim.x * blockDim.x) {
+        const float4 p = trg[k];
+        const double d[3] = {p.x - cx, p.y - cy, p.z - cz};
+        const double df = d[0] * f[0] + d[1] * f[1] + d[2] * f[2];
+        float *o = out + (int64_t)perm[k] * ldo;
+        if (!stress) {
+            for (int a = 0; a < 3; ++a) o[3 * col + a] += (float)(coef * d[a] * df);
+        } else {
+            // grad u = coef (df I + d f^T): eps = coef (df I + sym(d f^T)), tr eps = 4 coef df
+            const double dg = lam * 4.0 * coef * df + 2.0 * G * coef * df;
+            o[6 * col + 0] += (float)(dg + 2.0 * G * coef * d[0] * f[0]);
+            o[6 * col + 1] += (float)(dg + 2.0 * G * coef * d[1] * f[1]);
+            o[6 * col + 2] += (float)(dg + 2.0 * G * coef * d[2] * f[2]);
+            o[6 * col + 3] += (float)(G * coef * (d[1] * f[2] + d[2] * f[1]));
+            o[6 * col + 4] += (float)(G * coef * (d[0] * f[2] + d[2] * f[0]));
+            o[6 * col + 5] += (float)(G * coef * (d[0] * f[1] + d[1] * f[0]));
+        }
+    }
+}
+
 static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, int ncol, int kind, float *out)
 {
     Tree &T = ctx->tree;
@@ -1383,7 +1539,8 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
         auto go = [&](auto kern) {
             kern<<<grid, kChkThreads, 0, s>>>(boxes, nbx, use_x, T.x_off.as<int>(), T.x_idx.as<int>(),
                                               T.box_src.as<int2>(), geom, O.surf.as<float4>(), n, radius,
-                                              W.src_rec.as<SrcRec>(), kc.a34, 3.f / kc.b12, outp, ld, rc, oc);
+                                              W.src_rec.as<SrcRec>(), kc.a34, 3.f / kc.b12, outp, ld, rc, oc,
+                                              T.cell);
         };
         const bool two = n <= 2 * kChkThreads;  // check points per thread: 2, else 4
         if (sl && dl) two ? go(check_potential_kernel<true, true, 2>) : go(check_potential_kernel<true, true, 4>);
@@ -1414,6 +1571,7 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     e.dn_phi = W.dn_phi.as<float>();
     e.up_phi = W.up_phi.as<float>();
     e.ld_phi = ld;
+    e.cell = T.cell;
     e.phi_scale = kind == KFMM_DISP ? kc.c_sl : 1.f;
     e.a34 = kc.a34;
     e.b12 = kc.b12;
@@ -1577,11 +1735,20 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     ctx->phase(KFMM_PH_DOWN);
     KF_TRY(box_gemm(P.all, O.tc_wb, O.wb.as<float>(), 0, kd, rp, rp, nullptr, nullptr, 0, 0,
                     W.cdn.as<float>(), rp, W.beta.as<float>(), kdp, nullptr, 1.f, 0));
+    if (T.periodic) {
+        // the cell's images beyond the root's neighbours (no list reaches them)
+        if (!O.lat_ready) return ctx->fail(KFMM_ERR_INTERNAL, "periodic tree without its lattice operator");
+        lattice_kernel<<<(unsigned)ncol, 256, 0, st>>>(O.lat.as<float>(), kd, ku, kup, W.alpha.as<float>(),
+                                                       (int64_t)nb * kup, W.beta.as<float>(), (int64_t)nb * kdp);
+        KF_LAUNCH();
+    }
     if (overlap) KF_CUDA(cudaStreamWaitEvent(st, ctx->ev_p2l, 0));
     KF_TRY(box_gemm(P.xboxes, O.tc_s2a_d, O.s2a_d.as<float>(), 0, kd,
                     ld, ld, T.xboxes.as<int>(), T.xboxes.as<int>(), 0, 0, W.dn_chk.as<float>(), ld,
                     W.beta.as<float>(), kdp, geom, (float)ctx->G, 1));
-    for (int l = 3; l < T.n_levels; ++l)
+    // L2L into level l from level l - 1: free space from level 3 (the first far fields are at
+    // level 2), a periodic tree from level 1 (the root has the lattice's)
+    for (int l = T.periodic ? 1 : 3; l < T.n_levels; ++l)
         KF_TRY(box_gemm(P.oct_lvl[l], O.tc_lb, O.lb.as<float>(),
                         (int64_t)kd * kdp, kd, kdp, kdp, T.oct_child.as<int>(), T.oct_child.as<int>(), 1, 0,
                         W.beta.as<float>(), kdp, W.beta.as<float>(), kdp, nullptr, 1.f, 1));
@@ -1596,6 +1763,20 @@ static kfmm_status fmm_enqueue(kfmm_ctx *ctx, const float *sl, const float *dl, 
     if (overlap) KF_CUDA(cudaStreamWaitEvent(st, ctx->ev_near, 0));
     if (P.eval_split ? P.n_eval_far > 0 : P.n_eval_items > 0) {
         eval_part(P.eval_split ? 2 : 0, st);
+        KF_LAUNCH();
+    }
+    if (T.periodic && sl) {
+        // the particular part of the balancing body force of a net single-layer force
+        KF_CUDA(W.net_force.ensure(sizeof(double) * 3 * ncol));
+        KF_CUDA(cudaMemsetAsync(W.net_force.p, 0, sizeof(double) * 3 * ncol, st));
+        net_force_kernel<<<dim3((unsigned)(2 * ctx->n_sms), (unsigned)ncol), 256, 0, st>>>(ns, sl, ldd,
+                                                                                       W.net_force.as<double>());
+        KF_LAUNCH();
+        const double side = ctx->cell_side, Gd = ctx->G, lam = 2.0 * Gd * ctx->nu / (1.0 - 2.0 * ctx->nu);
+        net_force_field_kernel<<<dim3((unsigned)(2 * ctx->n_sms), (unsigned)ncol), 256, 0, st>>>(
+            T.ntrg, T.trg_xyz.as<float4>(), T.trg_perm.as<int>(), W.net_force.as<double>(),
+            ctx->cell_lo[0] + 0.5 * side, ctx->cell_lo[1] + 0.5 * side, ctx->cell_lo[2] + 0.5 * side,
+            1.0 / ((4.0 * lam + 6.0 * Gd) * side * side * side), lam, Gd, kind == KFMM_STRESS ? 1 : 0, out, e.ldo);
         KF_LAUNCH();
     }
     ctx->phase(-1);

@@ -40,6 +40,9 @@ struct OpsHost {
 std::vector<double> lattice_surface(int p);
 int m2l_directions(int *dirs);
 bool compute_operators(const OpsParams &prm, OpsHost *out);
+// periodic.cpp: R [kd][ku], the far-lattice operator of a periodic tree's root (root alpha ->
+// root beta) for the operators H computed with prm
+bool compute_lattice(const OpsParams &prm, const OpsHost &H, std::vector<double> &R);
 
 }  // namespace host
 }  // namespace kfmm

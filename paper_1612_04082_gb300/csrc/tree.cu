@@ -612,6 +612,7 @@ struct TreeView {
     const int *colleague;
     const int *level_off;  // device copy, n_levels + 1
     int n_levels;
+    int periodic;  // colleagues wrap around the root cell (entries carry the image)
 };
 
 // the box of set `set` at (level, ix, iy, iz), or -1
@@ -631,27 +632,58 @@ __device__ __forceinline__ int find_box(const TreeView &tv, int level, uint64_t 
     return -1;
 }
 
+// The 27 boxes at the box's level around it (slot 13: itself), -1 where there is none.  In a
+// periodic tree a position outside the root cell wraps around it: the entry is the box at the
+// wrapped position, moved back by one cell (its image code, see ent_make).
 __global__ void colleague_kernel(TreeView tv, int *__restrict__ coll)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= tv.n_boxes) return;
     const int4 a = tv.anchor[b];
     const uint64_t set = tv.key[b] >> (3 * a.w);  // colleagues come from the box's own set
+    const int side = 1 << a.w;
     int c = 0;
     for (int dx = -1; dx <= 1; ++dx)
         for (int dy = -1; dy <= 1; ++dy)
-            for (int dz = -1; dz <= 1; ++dz, ++c)
-                coll[27 * b + c] = (c == 13) ? b : find_box(tv, a.w, set, a.x + dx, a.y + dy, a.z + dz);
+            for (int dz = -1; dz <= 1; ++dz, ++c) {
+                if (c == 13) {
+                    coll[27 * b + c] = b;
+                    continue;
+                }
+                int x = a.x + dx, y = a.y + dy, z = a.z + dz, img = 13;
+                if (tv.periodic) {
+                    const int sx = x < 0 ? -1 : (x >= side ? 1 : 0), sy = y < 0 ? -1 : (y >= side ? 1 : 0),
+                              sz = z < 0 ? -1 : (z >= side ? 1 : 0);
+                    x -= sx * side;
+                    y -= sy * side;
+                    z -= sz * side;
+                    img = 9 * (sx + 1) + 3 * (sy + 1) + (sz + 1);
+                }
+                const int f = find_box(tv, a.w, set, x, y, z);
+                coll[27 * b + c] = f < 0 ? -1 : ent_make(f, img);
+            }
 }
 
-// Closed boxes at possibly different levels touch or overlap.
-__device__ __forceinline__ bool adjacent(const int4 &a, const int4 &b, int L)
+// The image of entry e and the (unmoved) box with anchor b, at possibly different levels, touch
+// or overlap as closed boxes.
+__device__ __forceinline__ bool adjacent(const TreeView &tv, int e, const int4 &b)
 {
-    const int sa = L - a.w, sb = L - b.w;
-    const int ax0 = a.x << sa, ay0 = a.y << sa, az0 = a.z << sa, la = 1 << sa;
+    const int4 a = tv.anchor[ent_box(e)];
+    int sx, sy, sz;
+    ent_shift(e, sx, sy, sz);
+    const int L = tv.L, sa = L - a.w, sb = L - b.w, full = 1 << L;
+    const int ax0 = a.x * (1 << sa) + sx * full, ay0 = a.y * (1 << sa) + sy * full,
+              az0 = a.z * (1 << sa) + sz * full, la = 1 << sa;
     const int bx0 = b.x << sb, by0 = b.y << sb, bz0 = b.z << sb, lb = 1 << sb;
     return ax0 <= bx0 + lb && bx0 <= ax0 + la && ay0 <= by0 + lb && by0 <= ay0 + la &&
            az0 <= bz0 + lb && bz0 <= az0 + la;
+}
+
+// the image of child o of the box of entry e (the child moves with its parent), or -1
+__device__ __forceinline__ int child_ent(const TreeView &tv, int e, int o)
+{
+    const int ch = tv.child[8 * ent_box(e) + o];
+    return ch < 0 ? -1 : ent_make(ch, ent_image(e));
 }
 
 // One warp per box, lanes over the candidates of each list, ballots to place them in
@@ -660,7 +692,8 @@ __device__ __forceinline__ bool adjacent(const int4 &a, const int4 &b, int L)
 // memory, 32 boxes per step, last in first out (so it stays about 8 x 32 per remaining
 // level); a frontier that would exceed Q entries sets *overflow and stops the walk.  The
 // small frontier (4 KB per warp) keeps ~56 warps per SM resident; the host falls back to
-// the large one after an overflow.
+// the large one after an overflow.  Every candidate is a list entry (box and image): in a
+// periodic tree the same box can enter a list as several images.
 template <int WARPS, int Q>
 __global__ void __launch_bounds__(32 * WARPS)
 lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict__ uo, int *__restrict__ ui,
@@ -674,7 +707,6 @@ lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict
     const int b = blockIdx.x * WARPS + wid;
     if (b >= tv.n_boxes) return;  // the whole warp
     int *q = frontier[wid];
-    const int L = tv.L;
     const int4 ab = tv.anchor[b];
     const int level = ab.w;
     const bool is_leaf = tv.leaf[b] != 0;
@@ -688,16 +720,17 @@ lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict
         n += __popc(m);
     };
 
-    // V: children of the parent's colleagues that are not adjacent to b
-    if (level >= 2) {
+    // V: children of the parent's colleagues that are not adjacent to b (from level 1 on in a
+    // periodic tree, whose root has its images as colleagues)
+    if (level >= (tv.periodic ? 1 : 2)) {
         for (int t0 = 0; t0 < 27 * 8; t0 += 32) {
             const int t = t0 + lane;
             int D = -1;
             if (t < 27 * 8) {
                 const int C = tv.colleague[27 * par + (t >> 3)];
-                if (C >= 0 && !tv.leaf[C]) D = tv.child[8 * C + (t & 7)];
+                if (C >= 0 && !tv.leaf[ent_box(C)]) D = child_ent(tv, C, t & 7);
             }
-            emit(D >= 0 && !adjacent(tv.anchor[D >= 0 ? D : 0], ab, L), D, vi, pv, nv);
+            emit(D >= 0 && !adjacent(tv, D >= 0 ? D : 0, ab), D, vi, pv, nv);
         }
     }
     // X: coarser leaves adjacent to the parent but not to b (b lies in their W list)
@@ -708,10 +741,7 @@ lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict
             int C = -1;
             if (lane < 27) {
                 C = tv.colleague[27 * A + lane];
-                if (C >= 0 && C != A && tv.leaf[C]) {
-                    const int4 ac = tv.anchor[C];
-                    ok = adjacent(ac, ap, L) && !adjacent(ac, ab, L);
-                }
+                if (C >= 0 && C != A && tv.leaf[ent_box(C)]) ok = adjacent(tv, C, ap) && !adjacent(tv, C, ab);
             }
             emit(ok, C, xi, px, nx);
         }
@@ -723,7 +753,7 @@ lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict
             int C = -1;
             if (lane < 27) {
                 C = tv.colleague[27 * A + lane];
-                if (C >= 0 && tv.leaf[C] && !(A != b && C == A)) ok = A == b || adjacent(tv.anchor[C], ab, L);
+                if (C >= 0 && tv.leaf[ent_box(C)] && !(A != b && C == A)) ok = A == b || adjacent(tv, C, ab);
             }
             emit(ok, C, ui, pu, nu);
         }
@@ -735,7 +765,7 @@ lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict
             int D = -1;
             if (t < 27 * 8 && (t >> 3) != 13) {
                 const int C = tv.colleague[27 * b + (t >> 3)];
-                if (C >= 0 && !tv.leaf[C]) D = tv.child[8 * C + (t & 7)];
+                if (C >= 0 && !tv.leaf[ent_box(C)]) D = child_ent(tv, C, t & 7);
             }
             const unsigned m = __ballot_sync(full, D >= 0);
             if (D >= 0) q[qn + __popc(m & below)] = D;
@@ -749,8 +779,8 @@ lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict
             __syncwarp();
             bool adj = false, lf = false;
             if (D >= 0) {
-                adj = adjacent(tv.anchor[D], ab, L);
-                lf = tv.leaf[D] != 0;
+                adj = adjacent(tv, D, ab);
+                lf = tv.leaf[ent_box(D)] != 0;
             }
             emit(D >= 0 && adj && lf, D, ui, pu, nu);
             emit(D >= 0 && !adj, D, wi, pw, nw);
@@ -759,7 +789,7 @@ lists_kernel(TreeView tv, int mode, int *__restrict__ cnt, const int *__restrict
             if (D >= 0 && adj && !lf) {
 #pragma unroll
                 for (int o = 0; o < 8; ++o) {
-                    const int E = tv.child[8 * D + o];
+                    const int E = child_ent(tv, D, o);
                     if (E >= 0) kids[nk++] = E;
                 }
             }
@@ -851,18 +881,12 @@ __device__ __forceinline__ int dir_index(int dx, int dy, int dz)
 {
     // index into 7^3 then compress by removing the 27 inner ones
     int full = ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3);
-    // count inner cells with smaller full index
+    // minus the inner cells (components -1..1, indices 2..4 on each axis) with a smaller index
     int inner_before = 0;
-    // inner cells have components in -1..1 -> indices 2..4 in each axis
-    int ix = dx + 3, iy = dy + 3, iz = dz + 3;
-    // number of inner cells (a,b,c) with ((a*7+b)*7+c) < full
     for (int a = 2; a <= 4; ++a)
         for (int bb = 2; bb <= 4; ++bb)
             for (int c = 2; c <= 4; ++c)
                 if (((a * 7 + bb) * 7 + c) < full) ++inner_before;
-    (void)ix;
-    (void)iy;
-    (void)iz;
     return full - inner_before;
 }
 
@@ -880,8 +904,15 @@ __global__ void vdir_hist_kernel(int n_boxes, const int *__restrict__ vo, const 
     if (b < n_boxes) {
         const int4 ab = anchor[b];
         for (int k = vo[b]; k < vo[b + 1]; ++k) {
-            const int4 as = anchor[vi[k]];
-            const int d = dir_index(as.x - ab.x, as.y - ab.y, as.z - ab.z);
+            const int e = vi[k];
+            const int4 as = anchor[ent_box(e)];
+            int sx, sy, sz;
+            ent_shift(e, sx, sy, sz);  // an image moved by whole cells: 2^level boxes each
+            const int side = 1 << as.w;
+            // in [-3, 3] for every V pair by construction; clamped so that no index can leave h
+            const int dx = min(3, max(-3, as.x + sx * side - ab.x)), dy = min(3, max(-3, as.y + sy * side - ab.y)),
+                      dz = min(3, max(-3, as.z + sz * side - ab.z));
+            const int d = dir_index(dx, dy, dz);
             pair_dir[k] = d;
             atomicAdd(&h[d], 1);
         }
@@ -902,7 +933,7 @@ __global__ void vdir_place_kernel(int n_boxes, const int *__restrict__ vo, const
     if (b >= n_boxes) return;
     for (int k = vo[b]; k < vo[b + 1]; ++k) {
         const int pos = atomicAdd(&cur[pair_dir[k]], 1);
-        psrc[pos] = vi[k];
+        psrc[pos] = ent_box(vi[k]);  // the translation carries the image's offset
         ptrg[pos] = b;
     }
 }
@@ -939,9 +970,9 @@ __global__ void work_count_kernel(int n_boxes, const int *__restrict__ leaf, con
     if (leaf[b]) {
         const int nt = btrg[b].y - btrg[b].x;
         long long ns = 0, n_eq = 1;  // the leaf's own downward density
-        for (int k = uo[b]; k < uo[b + 1]; ++k) ns += bsrc[ui[k]].y - bsrc[ui[k]].x;
+        for (int k = uo[b]; k < uo[b + 1]; ++k) ns += bsrc[ent_box(ui[k])].y - bsrc[ent_box(ui[k])].x;
         for (int k = wo[b]; k < wo[b + 1]; ++k) {
-            const int w = bsrc[wi[k]].y - bsrc[wi[k]].x;
+            const int w = bsrc[ent_box(wi[k])].y - bsrc[ent_box(wi[k])].x;
             if (w > w_direct_max) ++n_eq;
             else ns += w;
         }
@@ -949,7 +980,7 @@ __global__ void work_count_kernel(int n_boxes, const int *__restrict__ leaf, con
         l2p = (unsigned long long)nt * n_eq;
     }
     unsigned long long xs = 0;
-    for (int k = xo[b]; k < xo[b + 1]; ++k) xs += bsrc[xi[k]].y - bsrc[xi[k]].x;
+    for (int k = xo[b]; k < xo[b + 1]; ++k) xs += bsrc[ent_box(xi[k])].y - bsrc[ent_box(xi[k])].x;
     const int ntb = btrg[b].y - btrg[b].x;
     if (ntb > x_direct_max) p2l = xs;                       // through the check surface
     else p2p += (unsigned long long)ntb * xs;               // summed at the targets
@@ -975,6 +1006,8 @@ kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, cons
     const cudaStream_t st = ctx->stream;
     const int cap = ctx->opt.leaf_cap;
     if (n_sets < 1) return ctx->fail(KFMM_ERR_INVALID_ARG, "need at least one point set");
+    if (ctx->periodic && n_sets != 1)
+        return ctx->fail(KFMM_ERR_INVALID_ARG, "a periodic tree holds one point set (one cell)");
     const int64_t nsrc = src_off[n_sets], ntrg = trg_off[n_sets];
     if (nsrc + ntrg > (int64_t)1 << 30) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many points (limit 2^30)");
     // keys: the set index above 3 L Morton bits, within 64 bits
@@ -1016,6 +1049,17 @@ kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, cons
             bad += q[6];
         }
         if (bad > 0) return ctx->fail(KFMM_ERR_INVALID_ARG, "non-finite coordinate or normal");
+        if (ctx->periodic) {
+            // the root is the cell itself (a point on its upper faces joins the last boxes)
+            const double side = ctx->cell_side, tol = 1e-6 * side;
+            for (int c = 0; c < 3; ++c)
+                if (lo[c] < ctx->cell_lo[c] - tol || hi[c] > ctx->cell_lo[c] + side + tol)
+                    return ctx->fail(KFMM_ERR_INVALID_ARG, "periodic tree: a point lies outside the cell");
+            for (int c = 0; c < 3; ++c) hr[8 * k + c] = ctx->cell_lo[c];
+            hr[8 * k + 3] = side;
+            hr[8 * k + 4] = 1.0 / side;
+            continue;
+        }
         double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
         double w = ext > 0 ? ext * (1.0 + 1e-6) : 1.0;
         for (int c = 0; c < 3; ++c) hr[8 * k + c] = 0.5 * (lo[c] + hi[c]) - 0.5 * w;
@@ -1031,6 +1075,8 @@ kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, cons
     T.nsrc = nsrc;
     T.ntrg = ntrg;
     T.has_nrm = src_nrm != nullptr;
+    T.periodic = ctx->periodic;
+    T.cell = ctx->periodic ? (float)ctx->cell_side : 0.f;
 
     SplitState hs{};
     size_t capb = std::max<size_t>(1024, (size_t)(4 * (nsrc + ntrg) / std::max(1, cap)) + 64 + (size_t)n_sets);
@@ -1123,6 +1169,7 @@ kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, cons
     }
     T.max_depth = L;
     const int n_boxes = hs.n_boxes;
+    if (n_boxes > kEntMask) return ctx->fail(KFMM_ERR_INVALID_ARG, "too many boxes (limit 2^26)");
     T.n_boxes = n_boxes;
     T.n_levels = hs.n_levels;
     T.n_leaves = hs.n_leaves;
@@ -1139,7 +1186,8 @@ kfmm_status build_forest(kfmm_ctx *ctx, int n_sets, const int64_t *src_off, cons
                 T.box_leaf.as<int>(),
                 T.colleague.as<int>(),
                 loff.as<int>(),
-                T.n_levels};
+                T.n_levels,
+                T.periodic ? 1 : 0};
     colleague_kernel<<<grid_for(n_boxes, 128, 1 << 30), 128, 0, st>>>(tv, T.colleague.as<int>());
     KF_LAUNCH();
 

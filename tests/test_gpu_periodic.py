@@ -1,0 +1,208 @@
+"""GPU parity of the periodic KIFMM (Sec. "Periodic cell of a metamaterial": the sums over the
+infinite periodic surface, with the FMM tree periodic at every level) against the oracle's
+Ewald sums of the periodic kernels.
+
+The displacement sum of a periodic field is defined up to a constant vector per column (a
+rigid translation): the oracle fixes it by the zero cell mean (the Fourier series without
+k = 0), the FMM by its lattice operator on the root's equivalent density.  The displacement
+parity therefore removes the best constant per column from the difference before the
+relative L2 error; the stress carries no constant and is compared as it is, against the
+stress of the oracle's field (fourth-order differences of it at targets away from the
+sources).  Tolerance 1e-4 relative L2 at p = 6, as for the free-space sums.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+VOIGT = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+
+
+@pytest.fixture(scope="module")
+def K():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_04082_gb300 as K
+    return K
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda:0")
+
+
+def r32(a):
+    return None if a is None else np.asarray(a, np.float32).astype(np.float64)
+
+
+def make_ctx(K, G, nu, lo, side, **kw):
+    f = K.Kfmm(**kw)
+    f.set_material(K.material_K(G, nu), G)
+    f.set_periodic(lo, side)
+    return f
+
+
+def rel_mod_const(got, ref):
+    """Relative L2 error after the best constant per component, and that constant."""
+    c = (got - ref).mean(axis=0)
+    return float(np.linalg.norm(got - ref - c) / np.linalg.norm(ref)), c
+
+
+def periodic_case(K, n, lo, side, G, nu, ns=400, cap=64, p=6, layers="both"):
+    src, nrm = W.periodic_cell_points(n, lo=lo, side=side)
+    sl, dl = W.densities(n)
+    src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
+    sl = sl if layers in ("sl", "both") else None
+    dl = dl if layers in ("dl", "both") else None
+    with make_ctx(K, G, nu, lo, side, p=p, leaf_cap=cap) as c:
+        c.build(dev(src), dev(nrm), dev(src))
+        out = torch.zeros(n, 3, device="cuda:0")
+        c.eval(None if sl is None else dev(sl), None if dl is None else dev(dl), out, K.KFMM_DISP)
+        got = out.cpu().numpy().astype(np.float64)
+        st = c.stats()
+    idx = W.subsample(n, ns)
+    ref = O.periodic_disp(src[idx], src, nrm, sl, dl, G, nu, side)
+    err, cst = rel_mod_const(got[idx], ref)
+    return err, cst, st
+
+
+def test_periodic_lists_cover_every_image_once(K):
+    """In a periodic tree every target leaf meets every source leaf in each of the 27 images of
+    the cell around it exactly once, through U, W, X and the V lists of its ancestors (the
+    images beyond act through the root's lattice operator); every list entry names an image
+    within one cell."""
+    side, lo = 1.3, np.array([0.2, -0.5, 0.9])
+    src, nrm = W.periodic_cell_points(30000, lo=lo, side=side, n_voids=10)
+    with make_ctx(K, 1.0, 0.3, lo, side, leaf_cap=32) as c:
+        c.build(dev(src), dev(nrm), dev(src))
+        tr = c.export_tree()
+        st = c.stats()
+        lists = {k: c.export_list(k) for k in "UVWX"}
+    nb = st["n_boxes"]
+    par = tr["parent"]
+    lvl, anc = tr["level"], tr["anchor"]
+    children = [[] for _ in range(nb)]
+    for b in range(1, nb):
+        children[par[b]].append(b)
+    leaf = np.array([len(ch) == 0 for ch in children])
+    # the root is the cell: points inside their leaves
+    ssorted = r32(src)[tr["src_perm"]]
+    for b in np.nonzero(leaf)[0][:300]:
+        s = side / 2 ** lvl[b]
+        blo = lo + anc[b] * s
+        pts = ssorted[tr["src"][b, 0]:tr["src"][b, 1]]
+        assert np.all(pts >= blo - 1e-5 * side) and np.all(pts <= blo + s + 1e-5 * side)
+    dec = {}
+    for k, (off, items) in lists.items():
+        box, shift = K.list_entries(items)
+        assert np.all(np.abs(shift) <= 1) and np.all(box < nb)
+        dec[k] = (off, box, 9 * (shift[:, 0] + 1) + 3 * (shift[:, 1] + 1) + (shift[:, 2] + 1))
+    assert np.any(dec["U"][2] != 13) and np.any(dec["V"][2] != 13)  # images do occur
+    memo = {}
+
+    def leaves_under(b):
+        if b not in memo:
+            memo[b] = [b] if leaf[b] else [x for ch in children[b] for x in leaves_under(ch)]
+        return memo[b]
+
+    leaf_ids = np.nonzero(leaf)[0]
+    pos = {b: i for i, b in enumerate(leaf_ids)}
+    for b in leaf_ids[:: max(1, len(leaf_ids) // 120)]:
+        cnt = np.zeros((len(leaf_ids), 27), np.int32)
+
+        def add(key, a, under):
+            off, box, img = dec[key]
+            for e in range(off[a], off[a + 1]):
+                for s in (leaves_under(box[e]) if under else [box[e]]):
+                    cnt[pos[s], img[e]] += 1
+
+        add("U", b, False)
+        add("W", b, True)
+        a = b
+        while a >= 0:
+            add("V", a, True)
+            add("X", a, False)
+            a = par[a] if a > 0 else -1
+        assert np.all(cnt == 1), (b, np.unique(cnt, return_counts=True))
+
+
+@pytest.mark.parametrize("layers", ["sl", "dl", "both"])
+def test_periodic_fmm_matches_oracle(K, layers):
+    err, cst, st = periodic_case(K, 40000, (0.0, 0.0, 0.0), 1.0, 1.0, 0.3, layers=layers)
+    assert st["n_levels"] >= 4
+    assert err < 1e-4, (err, cst)
+
+
+def test_periodic_fmm_general_cell_and_material(K):
+    """A cell off the origin with side 2 and another Poisson ratio (the lattice operator is made
+    for the unit cell and scales with the cell)."""
+    err, cst, _ = periodic_case(K, 30000, (-0.4, 0.3, 1.1), 2.0, 2.3, 0.21)
+    assert err < 1e-4, (err, cst)
+
+
+def test_periodic_single_leaf(K):
+    """n <= leaf cap: the root is the only box; its 27 images are all near field and the rest of
+    the lattice acts through the lattice operator alone."""
+    err, cst, st = periodic_case(K, 50, (0.0, 0.0, 0.0), 1.0, 1.0, 0.3, ns=50)
+    assert st["n_boxes"] == 1
+    assert err < 1e-4, (err, cst)
+
+
+@pytest.mark.parametrize("p,tol", [(6, 4e-3), (8, 1e-4)])
+def test_periodic_fmm_stress_matches_oracle(K, p, tol):
+    """Stress at targets in the cell away from the sources, against Hooke's law of the
+    oracle's periodic displacement (fourth-order central differences, h = 1e-3).  Such
+    far-field-dominated stress sums meet 1e-4 at p = 8 (M2L cut-off 1e-7); p = 6 gives a few
+    1e-3, as for the free-space interior stress."""
+    G, nu, side = 1.7, 0.27, 1.0
+    n = 30000
+    src, nrm = W.periodic_cell_points(n, side=side)
+    sl, dl = W.densities(n)
+    src, nrm, sl, dl = r32(src), r32(nrm), r32(sl), r32(dl)
+    rng = np.random.default_rng(5)
+    cand = rng.uniform(0, side, (4000, 3))
+    dmin = np.array([np.min(np.linalg.norm((src - x + 0.5 * side) % side - 0.5 * side, axis=1)) for x in cand])
+    trg = r32(cand[dmin > 0.04][:120])
+    opts = {"p": p} if p == 6 else {"p": p, "m2l_rtol": 1e-7}
+    with make_ctx(K, G, nu, (0, 0, 0), side, **opts) as c:
+        c.build(dev(src), dev(nrm), dev(trg))
+        out = torch.zeros(len(trg), 6, device="cuda:0")
+        c.eval(dev(sl), dev(dl), out, K.KFMM_STRESS)
+        got = out.cpu().numpy().astype(np.float64)
+    h = 1e-3
+    lam = 2 * G * nu / (1 - 2 * nu)
+    grad = np.zeros((len(trg), 3, 3))
+    for b in range(3):
+        e = np.eye(3)[b] * h
+        pts = np.concatenate([trg + 2 * e, trg + e, trg - e, trg - 2 * e])
+        u = O.periodic_disp(pts, src, nrm, sl, dl, G, nu, side).reshape(4, len(trg), 3)
+        grad[:, :, b] = (-u[0] + 8 * u[1] - 8 * u[2] + u[3]) / (12 * h)
+    eps = 0.5 * (grad + grad.transpose(0, 2, 1))
+    sig = lam * np.trace(eps, axis1=1, axis2=2)[:, None, None] * np.eye(3) + 2 * G * eps
+    ref = np.stack([sig[:, i, j] for i, j in VOIGT], axis=1)
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    assert err < tol, err
+
+
+def test_periodic_errors_and_back_to_free_space(K):
+    src, nrm = W.periodic_cell_points(5000)
+    with make_ctx(K, 1.0, 0.3, (0, 0, 0), 1.0) as c:
+        with pytest.raises(K.KfmmError):
+            c.build(dev(src + 0.5), dev(nrm), dev(src + 0.5))  # points outside the cell
+        with pytest.raises(K.KfmmError):
+            c.build_sets(np.array([0, 2500, 5000]), dev(src), dev(nrm), np.array([0, 2500, 5000]), dev(src))
+        sl, dl = W.densities(len(src))
+        c.set_periodic(None)
+        c.build(dev(src), dev(nrm), dev(src))
+        out = torch.zeros(len(src), 3, device="cuda:0")
+        c.eval(dev(sl), dev(dl), out, K.KFMM_DISP)
+        got = out.cpu().numpy()
+    idx = W.subsample(len(src), 300)
+    ref = O.direct_disp(r32(src)[idx], r32(src), r32(nrm), r32(sl), r32(dl), 1.0, 0.3)
+    assert float(np.linalg.norm(got[idx] - ref) / np.linalg.norm(ref)) < 1e-4

@@ -260,6 +260,41 @@ def box_with_voids_points(n: int, n_voids: int = 20, box=(2.0, 1.0, 1.0), seed: 
     return pts, nrm
 
 
+def periodic_cell_points(n: int, n_voids: int = 12, lo=(0.0, 0.0, 0.0), side: float = 1.0,
+                         seed: int = SEED_GEOMETRY):
+    """`n` points area-uniform on the surfaces of `n_voids` non-overlapping spherical voids of a
+    periodic cubic cell [lo, lo + side]^3 (radii U(0.05, 0.15) side, centres anywhere in the
+    cell, distances measured across the cell's faces), wrapped into the cell: voids that cross a
+    face appear in pieces on both sides, so the near field of a point near a face lies across it.
+
+    Returns (pts [n,3], nrm [n,3]) in float64, normals into the voids.
+    """
+    rng = np.random.default_rng(seed + 11)
+    lo = np.asarray(lo, dtype=np.float64)
+    cs, rs = [], []
+    tries = 0
+    while len(cs) < n_voids:
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("could not place voids")
+        r = rng.uniform(0.05, 0.15) * side
+        c = rng.uniform(0.0, side, 3)
+        ok = True
+        for c2, r2 in zip(cs, rs):
+            d = c - c2
+            d -= side * np.round(d / side)  # nearest image
+            ok &= np.linalg.norm(d) > r + r2 + 0.02 * side
+        if ok:
+            cs.append(c)
+            rs.append(r)
+    rs = np.array(rs)
+    which = rng.choice(n_voids, size=n, p=rs ** 2 / (rs ** 2).sum())
+    g = rng.normal(size=(n, 3))
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    pts = np.array(cs)[which] + rs[which, None] * g
+    return lo + np.mod(pts, side), -g
+
+
 def surface_batch(n_sets: int = 32, lo: int = 5000, hi: int = 250000, seed: int = SEED_GEOMETRY):
     """A batch of independent box-with-voids surfaces of uneven size: set sizes log-uniform in
     [lo, hi], 4 to 19 voids each, each box scaled and placed on its own.

@@ -453,6 +453,17 @@ kfmm_status bem_set_stream(bem_ctx *b, void *stream);
  * next operator application. */
 kfmm_status bem_set_quadrature(bem_ctx *b, int near_levels);
 
+/* Periodic boundary sums (Sec. "Periodic cell of a metamaterial"): the surface is the part in
+ * one cell [lo, lo + side]^3 of an infinite periodic surface, and every sum of the operator
+ * runs over the whole lattice (kfmm_set_periodic on the BEM's FMM contexts; the solution of
+ * the periodic traction problem is fixed up to a rigid translation).  Every vertex must lie in
+ * the cell; the local corrections (own triangle, neighbours) stay within the cell's copy of
+ * the surface, so a surface that crosses a face of the cell is not supported.  Needs the FMM
+ * operator (BEM_FMM) and a solve without refinement (the refinement's outer operator is a
+ * free-space direct sum).  on = 0 returns to free space.  Takes effect at the next operator
+ * application. */
+kfmm_status bem_set_periodic(bem_ctx *b, int on, const double *lo, double side);
+
 /* Boundary conditions of Eq. elast for ncol load cases (1..32) sharing one mask:
  * known_is_disp [nt][3] (uint8: 1 = u_i prescribed, 0 = t_i prescribed), values [nt][3*ncol]
  * (the prescribed u or t of load case c in entries 3c .. 3c+2 of each row).  The load cases

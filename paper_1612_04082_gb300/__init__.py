@@ -427,6 +427,7 @@ _bsig = {
     "bem_set_stream": (ctypes.c_int, [_vp, _vp]),
     "bem_set_bc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     "bem_set_quadrature": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "bem_set_periodic": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_double]),
     "bem_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bem_matvec": (ctypes.c_int, [_vp, _vp, _vp]),
     "bem_rhs": (ctypes.c_int, [_vp, _vp]),
@@ -567,6 +568,15 @@ class Bem:
         """Upsampled quadrature of the triangles sharing a vertex with a collocation triangle:
         the 4-node rule on 4^near_levels sub-triangles (1 = the 16-point rule everywhere)."""
         _bcheck(self.handle, _lib.bem_set_quadrature(self.handle, int(near_levels)))
+
+    def set_periodic(self, lo=None, side=1.0):
+        """The surface is one cell [lo, lo + side]^3 of a periodic surface: every sum runs over
+        the lattice (lo None: free space again)."""
+        if lo is None:
+            _bcheck(self.handle, _lib.bem_set_periodic(self.handle, 0, None, 1.0))
+            return
+        c = np.ascontiguousarray(lo, dtype=np.float64).reshape(3)
+        _bcheck(self.handle, _lib.bem_set_periodic(self.handle, 1, c.ctypes.data, float(side)))
 
     def apply(self, u, t, out):
         return bem_apply(self.handle, u, t, out)

@@ -31,6 +31,8 @@ struct bem_ctx {
     kfmm_ctx *surf = nullptr;  // FMM over quadrature sources -> centroids
     kfmm_ctx *vol = nullptr;   // FMM over quadrature sources -> interior points
     bool surf_built = false, have_bc = false, have_sol = false;
+    bool periodic = false;    // sums over the lattice of a cubic cell (bem_set_periodic)
+    double cell_lo[3] = {0, 0, 0}, cell_side = 1.0;
     double setup_G = -1, setup_nu = -1;
     int matvecs = 0, matvecs_hi = 0;  // FMM and FP64-grade (direct) operator applications
     double near_radius = 0;           // FP64 pairs of the compensated direct sum: 4 x longest edge
@@ -704,11 +706,11 @@ static kfmm_status bem_setup(bem_ctx *b)
         b->setup_G = b->G;
         b->setup_nu = b->nu;
         b->near_ready = 0;
-        if (b->op == BEM_FMM && !b->surf_built) {
-            if (b->auto_cap && b->opt.autotune) BK_TRY(bem_tune_leaf_cap(b));
-            BK_FMM(kfmm_build(b->surf, b->q32.as<float>(), b->qn32.as<float>(), 16 * nt, b->cen32.as<float>(), nt));
-            b->surf_built = true;
-        }
+    }
+    if (b->op == BEM_FMM && !b->surf_built) {
+        if (b->auto_cap && b->opt.autotune) BK_TRY(bem_tune_leaf_cap(b));
+        BK_FMM(kfmm_build(b->surf, b->q32.as<float>(), b->qn32.as<float>(), 16 * nt, b->cen32.as<float>(), nt));
+        b->surf_built = true;
     }
     if (b->near_levels > 1 && b->near_ready != b->near_levels) BK_TRY(bem_near_setup(b));
     return KFMM_OK;
@@ -1209,6 +1211,24 @@ kfmm_status bem_set_quadrature(bem_ctx *b, int near_levels)
     return KFMM_OK;
 }
 
+kfmm_status bem_set_periodic(bem_ctx *b, int on, const double *lo, double side)
+{
+    if (!b) return KFMM_ERR_INVALID_ARG;
+    b->err.clear();
+    if (on && b->op != BEM_FMM)
+        return b->fail(KFMM_ERR_INVALID_ARG, "bem: periodic sums need the FMM operator (the direct sums are free-space)");
+    kfmm_status s = kfmm_set_periodic(b->surf, on, lo, side);
+    if (s != KFMM_OK) return b->fail(s, std::string("bem: ") + kfmm_last_error(b->surf));
+    if (b->vol) kfmm_set_periodic(b->vol, on, lo, side);
+    b->periodic = on != 0;
+    if (on) {
+        for (int c = 0; c < 3; ++c) b->cell_lo[c] = lo[c];
+        b->cell_side = side;
+    }
+    b->surf_built = false;  // the tree is built again at the next application
+    return KFMM_OK;
+}
+
 kfmm_status bem_set_bc(bem_ctx *b, const uint8_t *known_is_disp, const double *values, int ncol)
 {
     if (!b || !known_is_disp || !values || ncol < 1 || ncol > 32) return KFMM_ERR_INVALID_ARG;
@@ -1305,6 +1325,9 @@ kfmm_status bem_solve(bem_ctx *b, const bem_solve_opts *opts, double *u, double 
         (o.refine && (b->op != BEM_FMM || !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_outer < 1)))
         return b->fail(KFMM_ERR_INVALID_ARG,
                        "bem_solve: refinement needs an FMM context, 0 < inner_tol < 1 and max_outer >= 1");
+    if (o.refine && b->periodic)
+        return b->fail(KFMM_ERR_INVALID_ARG, "bem_solve: no refinement with periodic sums (its outer operator is "
+                                             "a free-space direct sum)");
     if (first_foreign({u, t, o.x0})) return b->fail(KFMM_ERR_INVALID_ARG, "bem: an array is device memory of another GPU");
     const auto t0 = std::chrono::steady_clock::now();
     bem_stats s{};
@@ -1390,6 +1413,7 @@ kfmm_status bem_interior(bem_ctx *b, const float *pts, int64_t n, float *disp, f
             if (s != KFMM_OK) return b->fail(s, "bem: interior FMM context");
             kfmm_set_material(b->vol, b->K, b->G);
             kfmm_set_stream(b->vol, b->stream);
+            if (b->periodic) kfmm_set_periodic(b->vol, 1, b->cell_lo, b->cell_side);
         }
         BK_CUDA(b->slq.ensure(sizeof(float) * 3 * nq * nc));
         BK_CUDA(b->dlq.ensure(sizeof(float) * 3 * nq * nc));

@@ -206,3 +206,50 @@ def test_periodic_errors_and_back_to_free_space(K):
     idx = W.subsample(len(src), 300)
     ref = O.direct_disp(r32(src)[idx], r32(src), r32(nrm), r32(sl), r32(dl), 1.0, 0.3)
     assert float(np.linalg.norm(got[idx] - ref) / np.linalg.norm(ref)) < 1e-4
+
+
+def bulk_modulus_of_voided_cell(K, level, R, periodic, G=1.0, nu=0.3):
+    """K_eff / K of a unit cell with one spherical void of radius R at its centre under the unit
+    hydrostatic macro strain: the traction problem t = -sigma^h n on the void (sigma^h = 3 K I),
+    then <sigma> = C : [(1 - phi) I + int sym(u n) dS] (n out of the material, into the void;
+    cell volume 1), so K_eff / K = 1 - phi + (1/3) int u . n dS.  Free space instead of periodic
+    gives the dilute value of an isolated void."""
+    V, T = W.icosphere(level, R, (0.5, 0.5, 0.5), inward=True)
+    a, b, c = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    cr = np.cross(b - a, c - a)
+    area = 0.5 * np.linalg.norm(cr, axis=1)
+    n = cr / (2 * area[:, None])
+    cen = (a + b + c) / 3
+    Kb = 2 * G * (1 + nu) / (3 * (1 - 2 * nu))
+    t = -3 * Kb * n
+    with K.Bem(V, T, K.BEM_FMM) as bem:
+        bem.set_material(K.material_K(G, nu), G)
+        if periodic:
+            bem.set_periodic((0.0, 0.0, 0.0), 1.0)
+        bem.set_bc(np.zeros((len(T), 3), np.uint8), t)
+        u = np.zeros((len(T), 3))
+        st = bem.solve(u, None, tol=1e-5, restart=60, maxit=1200)
+    phi = -np.sum(np.einsum("ij,ij->i", cen, n) * area) / 3  # the void's volume (flat triangles)
+    return 1 - phi + np.sum(np.einsum("ij,ij->i", u, n) * area) / 3, phi, Kb, st
+
+
+def test_periodic_bem_bulk_modulus_of_a_cubic_array_of_voids(K):
+    """Homogenisation of a simple cubic array of spherical voids (the periodic traction
+    problem of Sec. "Periodic cell of a metamaterial").  The free-space version of the same
+    computation reproduces the dilute deficit of an isolated void, phi (3K + 4G) / (4G)
+    (Eshelby), which checks the mesh and the formula; the periodic one must lie at or below
+    the Hashin-Shtrikman upper bound for a porous material,
+    K_HS / K = 1 - phi (3K + 4G) / (4G + 3K phi),
+    and, the voids being well apart (phi ~ 0.03), close to it: the ratio of the periodic to
+    the free-space deficit (whose discretisation errors cancel) lies between the bound's
+    ratio 4G / (4G + 3K phi) and 1."""
+    G, nu, R = 1.0, 0.3, 0.2
+    k_free, phi, Kb, _ = bulk_modulus_of_voided_cell(K, 4, R, False, G, nu)
+    dilute = phi * (3 * Kb + 4 * G) / (4 * G)
+    assert abs((1 - k_free) / dilute - 1) < 0.02, (k_free, dilute)
+    k_per, _, _, st = bulk_modulus_of_voided_cell(K, 4, R, True, G, nu)
+    hs = 1 - phi * (3 * Kb + 4 * G) / (4 * G + 3 * Kb * phi)
+    ratio = (1 - k_per) / (1 - k_free)
+    bound = 4 * G / (4 * G + 3 * Kb * phi)
+    assert bound * (1 - 0.005) <= ratio <= 1.0, (ratio, bound, k_per, hs)
+    assert st["converged"]

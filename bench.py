@@ -23,8 +23,9 @@ The line also carries the BEM half of the metric:
  - "bem_small": the same cantilever at 5760 triangles, GMRES-IR beside plain FP64 GMRES on the
    same GPU at the same 1e-6 residual;
 and the homogenisation leg ("homogenisation"): the six unit-macro-strain load cases of a
-periodic cell with ellipsoidal voids (~209k triangles, 18 density columns) in one solve,
-beside one case at a time; and the batch leg ("batch"): 32 independent surfaces of uneven
+periodic cell with ellipsoidal voids (~209k triangles, 18 density columns) in one solve with
+the periodic FMM, beside one case at a time, and the homogenised stiffness (its bulk modulus
+against the Hashin-Shtrikman bound); and the batch leg ("batch"): 32 independent surfaces of uneven
 size in one build and evaluation, beside the same surfaces one by one; and the periodic leg
 ("periodic"): the periodic KIFMM on 1e6 points of a periodic unit cell, beside the same points
 as a free-space sum.  Per-phase times come from separate
@@ -390,21 +391,46 @@ def unit_strain_tractions(V, T, G, nu):
     return np.ascontiguousarray(np.concatenate(cols, axis=1))
 
 
+def effective_stiffness(V, T, u, G, nu):
+    """Homogenised stiffness [6, 6] (Voigt, engineering shear) of a unit periodic cell from the
+    fluctuation displacements u [nt, 18] of the six unit macro strains: <sigma> = C : [(1 - phi)
+    eps + int sym(u n) dS] (n out of the material, the void volume fraction phi from the mesh)."""
+    a, b, c = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    cr = np.cross(b - a, c - a)
+    area = 0.5 * np.linalg.norm(cr, axis=1)
+    n = cr / (2 * area[:, None])
+    phi = -np.sum(np.einsum("ij,ij->i", (a + b + c) / 3, n) * area) / 3
+    lam = 2 * G * nu / (1 - 2 * nu)
+    vo = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    C = np.zeros((6, 6))
+    for col, (i, j) in enumerate(vo):
+        eps = np.zeros((3, 3))
+        eps[i, j] = eps[j, i] = 1.0 if i == j else 0.5
+        S = np.einsum("ki,kj,k->ij", u[:, 3 * col:3 * col + 3], n, area)
+        e = (1 - phi) * eps + 0.5 * (S + S.T)
+        sig = lam * np.trace(e) * np.eye(3) + 2 * G * e
+        C[:, col] = [sig[p, q] for p, q in vo]
+    return C, phi
+
+
 def homogenisation_leg(K, local, world, tol=1e-5):
-    """The six unit-macro-strain load cases of a periodic cell's voids (the exterior problem
-    with t = -sigma^h n, 18 density columns) in one BEM solve, GMRES on the FMM operator, beside
-    the same six solved one at a time."""
+    """The six unit-macro-strain load cases of a periodic cell with voids (the periodic traction
+    problem, t = -sigma^h n on the voids, 18 density columns) in one BEM solve, GMRES on the
+    periodic FMM operator, beside the same six solved one at a time; the homogenised stiffness
+    and its bulk modulus against the Hashin-Shtrikman upper bound."""
     import torch
     import workloads as W
     V, T = W.periodic_cell_voids(HOMOG_N)
     nt = len(T)
     vals = unit_strain_tractions(V, T, 1.0, 0.3)
     mask = np.zeros((nt, 3), np.uint8)
-    out = {"workload": f"unit cell, {nt} void-surface triangles (ellipsoidal voids voxelised at h = 1/{HOMOG_N}), "
-                       "6 unit macro strains = 18 density columns, exterior traction problem, G=1, nu=0.3",
-           "tol": tol, "residual": "the FMM operator's (FP32, p = 6)"}
+    out = {"workload": f"periodic unit cell, {nt} void-surface triangles (ellipsoidal voids voxelised at "
+                       f"h = 1/{HOMOG_N}), 6 unit macro strains = 18 density columns, periodic traction problem, "
+                       "G=1, nu=0.3",
+           "tol": tol, "residual": "the periodic FMM operator's (FP32, p = 6)"}
     with K.Bem(V, T, K.BEM_FMM, device=local) as b:
         b.set_material(K.material_K(1.0, 0.3), 1.0)
+        b.set_periodic((0.0, 0.0, 0.0), 1.0)
         b.set_bc(mask, vals)
         rhs = np.zeros((nt, 18))
         b.rhs(rhs)  # warm-up: set-up, tree, tuning
@@ -423,6 +449,13 @@ def homogenisation_leg(K, local, world, tol=1e-5):
             if c == 0:
                 out["column0_rel_diff"] = float(np.linalg.norm(u1 - u[:, 0:3]) / np.linalg.norm(u1))
         one = max_over_ranks(one, world, f"cuda:{local}")
+    C, phi = effective_stiffness(V, T, u, 1.0, 0.3)
+    kb = 2 * 1.0 * 1.3 / (3 * (1 - 0.6))
+    k_eff = C[:3, :3].sum() / 9
+    k_hs = kb * (1 - phi * (3 * kb + 4.0) / (4.0 + 3 * kb * phi))
+    out.update({"void_fraction": phi, "bulk_modulus_over_matrix": k_eff / kb, "bulk_modulus_over_hs_bound": k_eff / k_hs,
+                "stiffness_asymmetry": float(np.abs(C - C.T).max() / np.abs(C).max()),
+                "stiffness_voigt": np.round(C, 5).tolist()})
     out.update({"load_cases_per_s": aggregate_rate(6, world, sec), "ms_per_6_case_solve": 1e3 * sec,
                 "iters": st["iters"], "relres": st["relres"], "fmm_matvecs": st["matvecs"],
                 "one_case_at_a_time_ms": 1e3 * one, "one_case_iters": its, "speedup_vs_one_at_a_time": one / sec})

@@ -457,12 +457,20 @@ kfmm_status bem_set_quadrature(bem_ctx *b, int near_levels);
  * one cell [lo, lo + side]^3 of an infinite periodic surface, and every sum of the operator
  * runs over the whole lattice (kfmm_set_periodic on the BEM's FMM contexts; the solution of
  * the periodic traction problem is fixed up to a rigid translation).  Every vertex must lie in
- * the cell; the local corrections (own triangle, neighbours) stay within the cell's copy of
- * the surface, so a surface that crosses a face of the cell is not supported.  Needs the FMM
- * operator (BEM_FMM) and a solve without refinement (the refinement's outer operator is a
- * free-space direct sum).  on = 0 returns to free space.  Takes effect at the next operator
- * application. */
+ * the cell.  A surface may cross the cell's faces (kfmm_voxel_surface_periodic gives such
+ * surfaces their own vertices on both faces); the upsampled rule of bem_set_quadrature then
+ * finds a collocation triangle's neighbours within the cell only, those across a face keep
+ * the 16-point rule.  Needs the FMM operator (BEM_FMM) and a solve without refinement (the
+ * refinement's outer operator is a free-space direct sum).  on = 0 returns to free space.
+ * Takes effect at the next operator application. */
 kfmm_status bem_set_periodic(bem_ctx *b, int on, const double *lo, double side);
+
+/* A uniform stress per load case, stress6 [ncol][6] (xx, yy, zz, yz, xz, xy; NULL clears),
+ * added to the stresses of bem_topo_derivative before the TD and the energy density: the
+ * homogeneous part sigma^h of a periodic cell's total stress, whose fluctuation the BEM
+ * solves (Sec. "Periodic cell of a metamaterial": the TD of the total stress).  ncol must
+ * match the boundary solution's columns when the TD is taken; bem_interior is unaffected. */
+kfmm_status bem_set_macro_stress(bem_ctx *b, const double *stress6, int ncol);
 
 /* Boundary conditions of Eq. elast for ncol load cases (1..32) sharing one mask:
  * known_is_disp [nt][3] (uint8: 1 = u_i prescribed, 0 = t_i prescribed), values [nt][3*ncol]
@@ -528,6 +536,15 @@ const char *bem_last_error(const bem_ctx *b);
 kfmm_status kfmm_voxel_surface(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, double h,
                                const double *origin, double *verts, int64_t *nv, int32_t *tris,
                                int64_t *nt, int64_t *face_cell, int8_t *face_dir);
+
+/* The same for one cell of a periodic voxel pattern (Sec. "Periodic cell of a metamaterial";
+ * the cell is origin + [0, n h] per axis): a voxel's neighbour across a face of the array is
+ * the voxel on the opposite side, so faces lie only between material and void, and a void
+ * that meets a face of the cell continues across it (its triangles on both sides, with their
+ * own vertices on the cell's faces).  Arguments as kfmm_voxel_surface. */
+kfmm_status kfmm_voxel_surface_periodic(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, double h,
+                                        const double *origin, double *verts, int64_t *nv, int32_t *tris,
+                                        int64_t *nt, int64_t *face_cell, int8_t *face_dir);
 
 /* Hard-kill update by thresholding the topological derivative td [nx*ny*nz] over the
  * material voxels: D_C = D_min + C (D_max - D_min); material voxels with td < D_C that are

@@ -428,6 +428,7 @@ _bsig = {
     "bem_set_bc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     "bem_set_quadrature": (ctypes.c_int, [_vp, ctypes.c_int]),
     "bem_set_periodic": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_double]),
+    "bem_set_macro_stress": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "bem_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bem_matvec": (ctypes.c_int, [_vp, _vp, _vp]),
     "bem_rhs": (ctypes.c_int, [_vp, _vp]),
@@ -578,6 +579,15 @@ class Bem:
         c = np.ascontiguousarray(lo, dtype=np.float64).reshape(3)
         _bcheck(self.handle, _lib.bem_set_periodic(self.handle, 1, c.ctypes.data, float(side)))
 
+    def set_macro_stress(self, stress6=None):
+        """Uniform stress per load case [ncol, 6] (Voigt xx, yy, zz, yz, xz, xy) added before the
+        TD (the homogeneous part of a periodic cell's total stress); None clears."""
+        if stress6 is None:
+            _bcheck(self.handle, _lib.bem_set_macro_stress(self.handle, None, 0))
+            return
+        m = np.ascontiguousarray(stress6, dtype=np.float64).reshape(-1, 6)
+        _bcheck(self.handle, _lib.bem_set_macro_stress(self.handle, m.ctypes.data, m.shape[0]))
+
     def apply(self, u, t, out):
         return bem_apply(self.handle, u, t, out)
 
@@ -609,6 +619,9 @@ def material_K(G: float, nu: float) -> float:
 _vsig = {
     "kfmm_voxel_surface": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, _vp,
                                           _vp, ctypes.POINTER(_i64), _vp, ctypes.POINTER(_i64), _vp, _vp]),
+    "kfmm_voxel_surface_periodic": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                                   _vp, _vp, ctypes.POINTER(_i64), _vp, ctypes.POINTER(_i64), _vp,
+                                                   _vp]),
     "kfmm_voxel_threshold": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
                                             ctypes.c_double, ctypes.POINTER(_i64)]),
     "kfmm_voxel_clean": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
@@ -626,20 +639,22 @@ def _mask_arg(mask):
     return mask.shape
 
 
-def voxel_surface(mask, h=1.0, origin=(0.0, 0.0, 0.0)):
+def voxel_surface(mask, h=1.0, origin=(0.0, 0.0, 0.0), periodic=False):
     """Boundary triangles of the material voxels: (verts [nv,3], tris [nt,3] int32,
-    face_cell [nt] int64, face_dir [nt] int8)."""
+    face_cell [nt] int64, face_dir [nt] int8).  periodic: the mask is one cell of a periodic
+    pattern (neighbours wrap around, no faces on the cell's boundary)."""
     nx, ny, nz = _mask_arg(mask)
     o = np.ascontiguousarray(origin, dtype=np.float64)
     nv, nt = _i64(0), _i64(0)
-    _check(None, _lib.kfmm_voxel_surface(_ptr(mask), nx, ny, nz, float(h), _ptr(o), None, ctypes.byref(nv), None,
-                                         ctypes.byref(nt), None, None))
+    fn = _lib.kfmm_voxel_surface_periodic if periodic else _lib.kfmm_voxel_surface
+    _check(None, fn(_ptr(mask), nx, ny, nz, float(h), _ptr(o), None, ctypes.byref(nv), None,
+                    ctypes.byref(nt), None, None))
     V = np.zeros((nv.value, 3))
     T = np.zeros((nt.value, 3), np.int32)
     cell = np.zeros(nt.value, np.int64)
     fdir = np.zeros(nt.value, np.int8)
-    _check(None, _lib.kfmm_voxel_surface(_ptr(mask), nx, ny, nz, float(h), _ptr(o), _ptr(V), ctypes.byref(nv),
-                                         _ptr(T), ctypes.byref(nt), _ptr(cell), _ptr(fdir)))
+    _check(None, fn(_ptr(mask), nx, ny, nz, float(h), _ptr(o), _ptr(V), ctypes.byref(nv),
+                    _ptr(T), ctypes.byref(nt), _ptr(cell), _ptr(fdir)))
     return V, T, cell, fdir
 
 

@@ -33,6 +33,8 @@ struct bem_ctx {
     bool surf_built = false, have_bc = false, have_sol = false;
     bool periodic = false;    // sums over the lattice of a cubic cell (bem_set_periodic)
     double cell_lo[3] = {0, 0, 0}, cell_side = 1.0;
+    int macro_ncol = 0;       // uniform stress added before the TD (bem_set_macro_stress)
+    DevBuf macro;             // double [macro_ncol][6]
     double setup_G = -1, setup_nu = -1;
     int matvecs = 0, matvecs_hi = 0;  // FMM and FP64-grade (direct) operator applications
     double near_radius = 0;           // FP64 pairs of the compensated direct sum: 4 x longest edge
@@ -540,6 +542,13 @@ __global__ void d2f_cols_kernel(int64_t n, int no, int ncol, int col, const doub
 // Eq. deriv: D^T = 3/(4E) (1-nu)/(7-5nu) [10 (1+nu) s:s - (1+5nu) (tr s)^2];
 // energy density 1/2 s:eps with eps = ((1+nu) s - nu tr(s) I) / E.  s6 [n][6 ncol] ->
 // td, energy [n][ncol].
+// s [n][row] += m [row] for every point (row = 6 ncol: a uniform stress per column)
+__global__ void add_macro_kernel(int64_t total, int row, const double *__restrict__ m, float *__restrict__ s)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) s[i] += (float)m[i % row];
+}
+
 __global__ void topo_kernel(int64_t n, int ncol, const float *__restrict__ s6, float E, float nu,
                             float *__restrict__ td, float *__restrict__ energy)
 {
@@ -1229,6 +1238,23 @@ kfmm_status bem_set_periodic(bem_ctx *b, int on, const double *lo, double side)
     return KFMM_OK;
 }
 
+kfmm_status bem_set_macro_stress(bem_ctx *b, const double *stress6, int ncol)
+{
+    if (!b) return KFMM_ERR_INVALID_ARG;
+    b->err.clear();
+    if (!stress6) {
+        b->macro_ncol = 0;
+        return KFMM_OK;
+    }
+    if (ncol < 1 || ncol > 32) return b->fail(KFMM_ERR_INVALID_ARG, "bem: macro stress needs 1 <= ncol <= 32");
+    for (int i = 0; i < 6 * ncol; ++i)
+        if (!std::isfinite(stress6[i])) return b->fail(KFMM_ERR_INVALID_ARG, "bem: non-finite macro stress");
+    BK_CUDA(b->macro.ensure(sizeof(double) * 6 * ncol));
+    BK_CUDA(cudaMemcpy(b->macro.p, stress6, sizeof(double) * 6 * ncol, cudaMemcpyHostToDevice));
+    b->macro_ncol = ncol;
+    return KFMM_OK;
+}
+
 kfmm_status bem_set_bc(bem_ctx *b, const uint8_t *known_is_disp, const double *values, int ncol)
 {
     if (!b || !known_is_disp || !values || ncol < 1 || ncol > 32) return KFMM_ERR_INVALID_ARG;
@@ -1488,6 +1514,11 @@ kfmm_status bem_topo_derivative(bem_ctx *b, const float *pts, int64_t n, float *
         ds = sbuf.as<float>();
     }
     BK_TRY(bem_interior(b, pts, n, nullptr, ds));
+    if (b->macro_ncol) {
+        if (b->macro_ncol != nc) return b->fail(KFMM_ERR_INVALID_ARG, "bem: macro stress and solution columns differ");
+        add_macro_kernel<<<g1(6 * n * nc), 256, 0, b->stream>>>(6 * n * nc, 6 * nc, b->macro.as<double>(), ds);
+        BK_LAUNCH();
+    }
     float *dtd = td, *den = energy;
     const bool host_td = td && !is_device_ptr(td), host_en = energy && !is_device_ptr(energy);
     if (host_td) {

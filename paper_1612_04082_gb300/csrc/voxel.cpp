@@ -24,7 +24,10 @@ struct Surface {
 constexpr int kAxis[6] = {0, 0, 1, 1, 2, 2};
 constexpr int kSign[6] = {-1, 1, -1, 1, -1, 1};
 
-void build_surface(const uint8_t *m, int nx, int ny, int nz, double h, const double *o, Surface &S)
+// periodic: the array is one cell of a periodic voxel pattern, a voxel's neighbour across a
+// face of the array is the voxel on the opposite side, and no face lies on the array's boundary
+// unless the wrapped neighbour is void (the surface then crosses the cell's faces)
+void build_surface(const uint8_t *m, int nx, int ny, int nz, double h, const double *o, bool periodic, Surface &S)
 {
     const int64_t cx = nx + 1, cy = ny + 1, cz = nz + 1;
     std::vector<int64_t> corner_id((size_t)(cx * cy * cz), -1);
@@ -33,7 +36,13 @@ void build_surface(const uint8_t *m, int nx, int ny, int nz, double h, const dou
     std::vector<int64_t> tri_ref;  // per triangle: -1 - face index, corner a, corner b
     const int n[3] = {nx, ny, nz};
     auto filled = [&](int i, int j, int k) {
-        if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) return false;
+        if (periodic) {
+            i = (i + nx) % nx;
+            j = (j + ny) % ny;
+            k = (k + nz) % nz;
+        } else if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) {
+            return false;
+        }
         return m[((int64_t)i * ny + j) * nz + k] != 0;
     };
     auto corner = [&](const int c[3]) {
@@ -108,14 +117,14 @@ bool dims_ok(int nx, int ny, int nz)
 
 extern "C" {
 
-kfmm_status kfmm_voxel_surface(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, double h,
-                               const double *origin, double *verts, int64_t *nv, int32_t *tris, int64_t *nt,
-                               int64_t *face_cell, int8_t *face_dir)
+static kfmm_status voxel_surface(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, double h,
+                                 const double *origin, bool periodic, double *verts, int64_t *nv, int32_t *tris,
+                                 int64_t *nt, int64_t *face_cell, int8_t *face_dir)
 {
     if (!mask || !nv || !nt || !dims_ok(nx, ny, nz) || !(h > 0)) return KFMM_ERR_INVALID_ARG;
     const double zero[3] = {0, 0, 0};
     Surface S;
-    build_surface(mask, nx, ny, nz, h, origin ? origin : zero, S);
+    build_surface(mask, nx, ny, nz, h, origin ? origin : zero, periodic, S);
     const int64_t n_v = (int64_t)S.verts.size() / 3, n_t = (int64_t)S.tris.size() / 3;
     if (n_t > INT32_MAX || n_v > INT32_MAX) return KFMM_ERR_INVALID_ARG;
     const bool fill = verts || tris || face_cell || face_dir;
@@ -131,6 +140,20 @@ kfmm_status kfmm_voxel_surface(const uint8_t *mask, int32_t nx, int32_t ny, int3
     if (face_cell) std::memcpy(face_cell, S.cell.data(), sizeof(int64_t) * S.cell.size());
     if (face_dir) std::memcpy(face_dir, S.dir.data(), S.dir.size());
     return KFMM_OK;
+}
+
+kfmm_status kfmm_voxel_surface(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, double h,
+                               const double *origin, double *verts, int64_t *nv, int32_t *tris, int64_t *nt,
+                               int64_t *face_cell, int8_t *face_dir)
+{
+    return voxel_surface(mask, nx, ny, nz, h, origin, false, verts, nv, tris, nt, face_cell, face_dir);
+}
+
+kfmm_status kfmm_voxel_surface_periodic(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, double h,
+                                        const double *origin, double *verts, int64_t *nv, int32_t *tris,
+                                        int64_t *nt, int64_t *face_cell, int8_t *face_dir)
+{
+    return voxel_surface(mask, nx, ny, nz, h, origin, true, verts, nv, tris, nt, face_cell, face_dir);
 }
 
 kfmm_status kfmm_voxel_threshold(uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, const float *td,

@@ -359,6 +359,88 @@ class LearnedWarmStart:
         return a * xp + g * d
 
 
+# --------------------------------------------------------------- periodic metamaterial cell
+def periodic_cell_hole(n: int, r_c: float) -> np.ndarray:
+    """Material voxels of a unit periodic cell (n^3) with a spherical hole of radius r_c at its
+    centre: the initial guess of the bulk-modulus design (Sec. "Periodic cell of a
+    metamaterial")."""
+    c = (np.arange(n) + 0.5) / n
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    return (((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) > r_c * r_c).astype(np.uint8)
+
+
+def hashin_shtrikman_bulk(phi: float, G: float = 1.0, nu: float = 0.3) -> float:
+    """Upper Hashin-Shtrikman bound of the bulk modulus of a material-void composite with void
+    fraction phi, over the matrix's K: 1 - phi (3K + 4G) / (4G + 3K phi)."""
+    K = material_K(G, nu)
+    return 1.0 - phi * (3 * K + 4 * G) / (4 * G + 3 * K * phi)
+
+
+def periodic_bulk_modulus(mask: np.ndarray, G: float = 1.0, nu: float = 0.3, p: int = 6, tol: float = 1e-5,
+                          device: int = 0, td: bool = False):
+    """Bulk modulus of the periodic unit cell of `mask` (n^3, 1 = material) over the matrix's K.
+
+    The unit hydrostatic macro strain eps^h = I is the homogeneous field sigma^h = 3K I plus
+    the periodic fluctuation u whose tractions on the void surfaces cancel it, t = -sigma^h n
+    (n out of the material): one periodic BEM solve.  The cell's mean stress is
+    C : [(1 - phi) eps^h + int sym(u n) dS] (the fluctuation's face terms cancel by periodicity),
+    so K_eff / K = 1 - phi + (1/3) int u . n dS, phi the void fraction.  With td, also the
+    TD (Eq. deriv) of the total stress sigma^h + sigma(u) at the material voxel centres.
+    Returns (K_eff / K, stats, td [n_material] or None)."""
+    n = mask.shape[0]
+    h = 1.0 / n
+    V, T, cell, fdir = voxel_surface(mask, h, periodic=True)
+    _, nrm, area = triangle_geometry(V, T)
+    K = material_K(G, nu)
+    vals = np.ascontiguousarray(-3.0 * K * nrm)
+    t0 = time.perf_counter()
+    with Bem(V, T, BEM_FMM, p=p, device=device) as b:
+        b.set_material(K, G)
+        b.set_periodic((0.0, 0.0, 0.0), 1.0)
+        b.set_bc(np.zeros((len(T), 3), np.uint8), vals)
+        u = np.zeros((len(T), 3))
+        st = b.solve(u, None, tol=tol, restart=100, maxit=3000, raise_on_fail=False)
+        solve_s = time.perf_counter() - t0
+        out = None
+        if td:
+            b.set_macro_stress([3 * K, 3 * K, 3 * K, 0.0, 0.0, 0.0])
+            ii = np.argwhere(mask > 0)
+            out = np.zeros(len(ii), np.float32)
+            b.topo_derivative(np.ascontiguousarray((ii + 0.5) * h, np.float32), out)
+    phi = 1.0 - float(mask.mean())
+    k = 1.0 - phi + float(np.einsum("ij,ij,i->", u, nrm, area)) / 3.0
+    stats = {"phi": phi, "nt": len(T), "iters": st["iters"], "relres": st["relres"],
+             "converged": bool(st["converged"]), "solve_s": solve_s, "seconds": time.perf_counter() - t0}
+    return k, stats, out
+
+
+def periodic_design(n: int = 64, r_c: float = 0.2, alpha_c: float = 0.7, G: float = 1.0, nu: float = 0.3,
+                    p: int = 6, device: int = 0, steps: int = 1):
+    """Design of a periodic cell for the largest bulk modulus (Sec. "Periodic cell of a
+    metamaterial"): the cell with a spherical hole of radius r_c, the TD of the total stress
+    under the hydrostatic macro strain, the material voxels of the lowest TD removed down to
+    the volume fraction alpha_c: in one step (the paper's single iteration) or in `steps`
+    equal steps with the TD recomputed after each; then the bulk modulus of the result against
+    the Hashin-Shtrikman upper bound at that fraction."""
+    mask = periodic_cell_hole(n, r_c)
+    target = int(round(alpha_c * mask.size))
+    first = None
+    for s in range(steps):
+        k, st, td = periodic_bulk_modulus(mask, G, nu, p, device=device, td=True)
+        if first is None:
+            first = (k, st)
+        ii = np.argwhere(mask > 0)
+        n_remove = (int(mask.sum()) - target) // (steps - s)
+        if n_remove > 0:
+            drop = ii[np.argsort(td, kind="stable")[:n_remove]]
+            mask[tuple(drop.T)] = 0
+    k0, s0 = first
+    k1, s1, _ = periodic_bulk_modulus(mask, G, nu, p, device=device)
+    return mask, {"n": n, "r_c": r_c, "alpha_c": alpha_c, "steps": steps, "alpha": float(mask.mean()),
+                  "initial": {"k_over_matrix": k0, "k_over_hs": k0 / hashin_shtrikman_bulk(s0["phi"], G, nu), **s0},
+                  "design": {"k_over_matrix": k1, "k_over_hs": k1 / hashin_shtrikman_bulk(s1["phi"], G, nu), **s1}}
+
+
 def main(argv=None):
     """Run the loop from the command line and print one line per iteration (alpha, Psi/Psi_0,
     triangles, inner GMRES iterations, solve and D^T seconds) and a closing JSON line:

@@ -253,3 +253,43 @@ def test_periodic_bem_bulk_modulus_of_a_cubic_array_of_voids(K):
     bound = 4 * G / (4 * G + 3 * Kb * phi)
     assert bound * (1 - 0.005) <= ratio <= 1.0, (ratio, bound, k_per, hs)
     assert st["converged"]
+
+
+def test_periodic_td_of_the_total_stress(K):
+    """bem_set_macro_stress adds sigma^h before the TD.  With a small hole (radius 0.12 of the
+    cell) the total stress far from it is uniform and, to O((r / d)^3), equal to the mean
+    stress of the material, <sigma>_cell / (1 - phi) = 3K (K_eff / K) / (1 - phi) I (the
+    hole's own field has no mean); at the cell's corners (centres of cubic symmetry, where it
+    is isotropic) the TD is therefore Eq. deriv of that hydrostatic stress,
+    3 / (4E) (1 - nu) / (7 - 5 nu) [30 (1 + nu) - 9 (1 + 5 nu)] s^2, with K_eff from the
+    same solve's boundary values.  Without sigma^h the TD there would be ~0."""
+    from paper_1612_04082_gb300 import driver as D
+    G, nu = 1.0, 0.3
+    n = 20
+    mask = D.periodic_cell_hole(n, 0.12)
+    k, st, td = D.periodic_bulk_modulus(mask, G, nu, td=True)
+    assert st["converged"]
+    ii = np.argwhere(mask > 0)
+    d = np.linalg.norm((ii + 0.5) / n - 0.5, axis=1)
+    far = d > 0.8
+    E, Kb = 2 * G * (1 + nu), K.material_K(G, nu)
+    s_far = 3 * Kb * k / (1 - st["phi"])
+    td_far = 3 / (4 * E) * (1 - nu) / (7 - 5 * nu) * (30 * (1 + nu) - 9 * (1 + 5 * nu)) * s_far ** 2
+    assert far.sum() >= 8
+    np.testing.assert_allclose(td[far], td_far, rtol=0.01)
+
+
+def test_periodic_single_iteration_design(K):
+    """The single-iteration bulk-modulus design of a periodic cell (Sec. "Periodic cell of a
+    metamaterial"): the cell with a spherical hole, the TD of the total stress under the
+    hydrostatic macro strain, the lowest-TD material removed down to alpha_c.  The result has
+    the target volume fraction and a bulk modulus at or below the Hashin-Shtrikman bound (to
+    the discretisation); the initial cell, a simple cubic array of spherical holes, sits near
+    the bound."""
+    from paper_1612_04082_gb300 import driver as D
+    n = 24
+    mask, r = D.periodic_design(n=n, r_c=0.3, alpha_c=0.75)
+    assert abs(r["alpha"] - 0.75) <= 1.0 / n ** 3
+    assert r["initial"]["converged"] and r["design"]["converged"]
+    assert 0.95 < r["initial"]["k_over_hs"] <= 1.005, r
+    assert 0.5 < r["design"]["k_over_hs"] <= 1.005, r

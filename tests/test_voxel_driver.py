@@ -90,3 +90,35 @@ def test_clean_isolated_and_disconnected():
     keep[4, 1, 1] = keep[5, 0, 0] = 1
     mm = m.copy()
     assert K.voxel_clean(mm, support, keep) == 1 and mm[4, 1, 1] == 1 and mm[5, 0, 0] == 1 and mm[5, 0, 1] == 0
+
+
+@pytest.mark.parametrize("shape,seed", [((6, 6, 6), 4), ((5, 7, 4), 5)])
+def test_periodic_surface_faces_and_orientation(shape, seed):
+    """The periodic surface has one face (4 triangles) per material voxel face whose wrapped
+    neighbour is void, with the normal out of the material (face_dir), none elsewhere; its
+    oriented area sums to zero (closed on the torus); rolling the pattern across the cell's
+    faces changes neither the face count nor the area."""
+    m = random_mask(shape, seed, fill=0.7)
+    h = 0.1
+    V, T, cell, fdir = K.voxel_surface(m, h, periodic=True)
+    expect = 0
+    for ax in range(3):
+        for sgn in (-1, 1):
+            nb = np.roll(m, -sgn, axis=ax)  # the neighbour at index + sgn, wrapped
+            expect += int(((m == 1) & (nb == 0)).sum())
+    assert len(T) == 4 * expect
+    a, b, c = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    cr = np.cross(b - a, c - a)
+    dirs = np.array([[-1, 0, 0], [1, 0, 0], [0, -1, 0], [0, 1, 0], [0, 0, -1], [0, 0, 1]])
+    assert np.all(np.einsum("ij,ij->i", cr, dirs[fdir]) > 0)
+    assert np.abs(0.5 * cr.sum(axis=0)).max() < 1e-12
+    area = 0.5 * np.linalg.norm(cr, axis=1).sum()
+    lo, hi = V.min(axis=0), V.max(axis=0)
+    assert np.all(lo >= -1e-15) and np.all(hi <= np.array(shape) * h + 1e-15)
+    r = np.roll(m, (2, -1, 3), axis=(0, 1, 2))
+    V2, T2, _, _ = K.voxel_surface(r, h, periodic=True)
+    a2 = 0.5 * np.linalg.norm(np.cross(V2[T2[:, 1]] - V2[T2[:, 0]], V2[T2[:, 2]] - V2[T2[:, 0]]), axis=1).sum()
+    assert len(T2) == len(T) and a2 == pytest.approx(area, rel=1e-12)
+    # all material: no surface at all
+    V3, T3, _, _ = K.voxel_surface(np.ones(shape, np.uint8), h, periodic=True)
+    assert len(T3) == 0

@@ -446,11 +446,17 @@ def main(argv=None):
     triangles, inner GMRES iterations, solve and D^T seconds) and a closing JSON line:
 
       python -m paper_1612_04082_gb300.driver --case cantilever --n 48 --iters 20 --C 0.02
+
+    --case periodic runs the bulk-modulus design of a periodic unit cell instead (n^3 voxels,
+    a spherical hole of radius --r-c, hard kill down to --alpha-c in --iters steps) and prints
+    one JSON line with the initial and final bulk moduli against the Hashin-Shtrikman bound:
+
+      python -m paper_1612_04082_gb300.driver --case periodic --n 64 --r-c 0.2 --alpha-c 0.7 --iters 1
     """
     import argparse
     import json
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="cantilever", choices=["cantilever", "bridge"])
+    ap.add_argument("--case", default="cantilever", choices=["cantilever", "bridge", "periodic"])
     ap.add_argument("--n", type=int, default=24, help="voxels per unit length")
     ap.add_argument("--iters", type=int, default=10)
     ap.add_argument("--C", type=float, default=0.02)
@@ -458,7 +464,15 @@ def main(argv=None):
     ap.add_argument("--td", default="full", choices=["full", "adaptive"])
     ap.add_argument("--warm", default="previous", choices=["none", "previous", "learned"])
     ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--r-c", type=float, default=0.2, help="radius of the initial hole (periodic case)")
     a = ap.parse_args(argv)
+    if a.case == "periodic":
+        t0 = time.perf_counter()
+        _, rec = periodic_design(n=a.n, r_c=a.r_c, alpha_c=a.alpha_c if a.alpha_c > 0 else 0.7, device=a.device,
+                                 steps=max(1, a.iters))
+        rec["wall_s"] = time.perf_counter() - t0
+        print(json.dumps(rec))
+        return
     prob = cantilever(a.n) if a.case == "cantilever" else bridge(a.n)
     warm = None
     if a.warm == "previous":

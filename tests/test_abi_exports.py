@@ -70,3 +70,20 @@ def test_surface_batch_workload():
     assert len(sizes) == 8 and o1[0] == 0 and o1[-1] == len(p1)
     assert sizes.min() >= 500 and sizes.max() <= 3000
     assert np.allclose(np.linalg.norm(n1, axis=1), 1.0)
+
+
+def test_list_entry_decoding_follows_the_header():
+    """kifmm_elastic.h: a periodic list item is box | ((9 (sx+1) + 3 (sy+1) + (sz+1)) ^ 13) << 26,
+    so the unmoved image is the plain box index; the binding's decoder inverts exactly that."""
+    import numpy as np
+    import paper_1612_04082_gb300 as K
+    rng = np.random.default_rng(0)
+    box = rng.integers(0, 1 << 26, 500)
+    shift = rng.integers(-1, 2, (500, 3))
+    code = 9 * (shift[:, 0] + 1) + 3 * (shift[:, 1] + 1) + (shift[:, 2] + 1)
+    items = (box | ((code ^ 13) << 26)).astype(np.int64)
+    assert np.all(items < 2 ** 31)  # non-negative int32
+    b2, s2 = K.list_entries(items.astype(np.int32))
+    assert np.array_equal(b2, box) and np.array_equal(s2, shift)
+    b3, s3 = K.list_entries(box.astype(np.int32))
+    assert np.array_equal(b3, box) and not np.any(s3)
